@@ -1,0 +1,167 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle checks.
+
+This module holds no arithmetic of the solver itself: it only draws initial
+conditions and network weights from seeded generators, in float64 numpy, for
+the flow types the paper studies (App. C.1): viscous Burgers, decaying and
+Kolmogorov-forced turbulence, and a periodic double shear layer. Every field is
+laid out as ``U[2, ny, nx]`` on the staggered grid (u on west faces at
+``(i dx, (j+1/2) dy)``, v on south faces at ``((i+1/2) dx, j dy)``).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+
+def face_coords(nx: int, ny: int, lx: float = TWO_PI, ly: float = TWO_PI):
+    """Coordinates of the u-faces and v-faces: ``(xu, yu), (xv, yv)`` as [ny, nx] grids."""
+    dx, dy = lx / nx, ly / ny
+    i = np.arange(nx)
+    j = np.arange(ny)
+    xu, yu = np.meshgrid(i * dx, (j + 0.5) * dy)
+    xv, yv = np.meshgrid((i + 0.5) * dx, j * dy)
+    return (xu, yu), (xv, yv)
+
+
+def burgers_ic(n: int, seed: int = 0, lx: float = TWO_PI, kmax: int = 4) -> np.ndarray:
+    """Random smooth Burgers initial condition.
+
+    Each component is a sum over integer wavevectors k != 0 with |k| <= kmax of
+    ``a_k cos(k.x) + b_k sin(k.x)``, one (a_k, b_k) per half-plane wavevector,
+    a, b ~ N(0, 1) from ``numpy.random.default_rng(seed)`` drawn in a fixed k
+    order (u first, then v). Both components are scaled by one factor so that
+    max(|u|, |v|) over the grid is 1. Each component is sampled at its own faces.
+    """
+    rng = np.random.default_rng(seed)
+    ks = []
+    for kx in range(-kmax, kmax + 1):
+        for ky in range(-kmax, kmax + 1):
+            if kx * kx + ky * ky == 0 or kx * kx + ky * ky > kmax * kmax:
+                continue
+            if kx > 0 or (kx == 0 and ky > 0):
+                ks.append((kx, ky))
+    (xu, yu), (xv, yv) = face_coords(n, n, lx, lx)
+    s = TWO_PI / lx
+    out = np.zeros((2, n, n))
+    for comp, (x, y) in enumerate(((xu, yu), (xv, yv))):
+        for kx, ky in ks:
+            a, b = rng.standard_normal(2)
+            ph = s * (kx * x + ky * y)
+            out[comp] += a * np.cos(ph) + b * np.sin(ph)
+    return out / np.abs(out).max()
+
+
+def streamfunction_field(n: int, seed: int, kpeak: float = 4.0, lx: float = TWO_PI) -> np.ndarray:
+    """Divergence-free random field from a random-phase streamfunction.
+
+    psi lives on the corners with amplitude spectrum chosen so that the energy
+    spectrum is E(k) ~ k^4 exp(-2 (k / kpeak)^2) (peak at kpeak) and uniform
+    random phases. u = (psi[j+1, i] - psi[j, i]) / dy and
+    v = -(psi[j, i+1] - psi[j, i]) / dx, so the face-difference divergence
+    vanishes identically. Scaled to unit RMS velocity, sqrt(mean(u^2 + v^2)) = 1.
+    """
+    rng = np.random.default_rng(seed)
+    k1 = np.fft.fftfreq(n) * n * (TWO_PI / lx)
+    kx, ky = np.meshgrid(k1, k1)
+    kk = np.sqrt(kx * kx + ky * ky)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        energy = kk**4 * np.exp(-2.0 * (kk / kpeak) ** 2)
+        amp = np.where(kk > 0, np.sqrt(energy / np.maximum(kk, 1e-30) ** 3), 0.0)
+    phase = np.exp(2j * math.pi * rng.random((n, n)))
+    psi = np.real(np.fft.ifft2(amp * phase)) * n * n
+    h = lx / n
+    u = (np.roll(psi, -1, axis=0) - psi) / h
+    v = -(np.roll(psi, -1, axis=1) - psi) / h
+    U = np.stack([u, v])
+    return U / math.sqrt(np.mean(u * u + v * v))
+
+
+def decaying_ic(n: int, seed: int = 0) -> np.ndarray:
+    """Decaying-turbulence initial condition (random field peaked at k = 4)."""
+    return streamfunction_field(n, seed, kpeak=4.0)
+
+
+def kolmogorov_ic(n: int, seed: int = 0) -> np.ndarray:
+    """Kolmogorov-flow initial condition: the same random field family."""
+    return streamfunction_field(n, seed, kpeak=4.0)
+
+
+def shear_ic(n: int, delta: float = math.pi / 15, eps: float = 0.05) -> np.ndarray:
+    """Periodic double shear layer on [0, 2 pi]^2.
+
+    u = tanh((y - pi/2) / delta) for y <= pi, tanh((3 pi / 2 - y) / delta)
+    otherwise; v = eps sin(x). u depends on y only and v on x only, so the
+    face-difference divergence is exactly zero.
+    """
+    (xu, yu), (xv, yv) = face_coords(n, n)
+    u = np.where(yu <= math.pi, np.tanh((yu - math.pi / 2) / delta), np.tanh((1.5 * math.pi - yu) / delta))
+    v = eps * np.sin(xv)
+    return np.stack([u, v])
+
+
+def taylor_green(n: int, t: float = 0.0, nu: float = 0.0) -> np.ndarray:
+    """Taylor-Green vortex u = sin x cos y, v = -cos x sin y, times exp(-2 nu t)."""
+    (xu, yu), (xv, yv) = face_coords(n, n)
+    d = math.exp(-2.0 * nu * t)
+    return np.stack([np.sin(xu) * np.cos(yu) * d, -np.cos(xv) * np.sin(yv) * d])
+
+
+def ic_batch(kind: str, n: int, batch: int, seed0: int = 0) -> np.ndarray:
+    """Batch ``[B, 2, n, n]`` of initial conditions; trajectory b uses seed seed0 + b."""
+    fn = {
+        "burgers": lambda s: burgers_ic(n, s),
+        "decaying": lambda s: decaying_ic(n, s),
+        "kolmogorov": lambda s: kolmogorov_ic(n, s),
+        "shear": lambda s: shear_ic(n),
+        "taylor_green": lambda s: taylor_green(n),
+    }[kind]
+    return np.stack([fn(seed0 + b) for b in range(batch)])
+
+
+# ----------------------------------------------------------------------------
+# network weights
+# ----------------------------------------------------------------------------
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even) and widen back to float64."""
+    f = np.asarray(x, dtype=np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def conv_stack_shapes(cin: int, hidden: int, cout: int, layers: int = 6):
+    """(Cout, Cin) of each conv3x3 layer of a ``layers``-deep stack."""
+    chans = [cin] + [hidden] * (layers - 1) + [cout]
+    return [(chans[l + 1], chans[l]) for l in range(layers)]
+
+
+def random_conv_stack(seed: int, cin: int, hidden: int, cout: int, layers: int = 6,
+                      scale: float = 1.0, last_scale: float = 0.0):
+    """Seeded conv3x3 stack with bf16-representable weights (float64 values).
+
+    Hidden layers use N(0, scale / sqrt(9 Cin)) weights and N(0, 0.02) biases;
+    the last layer uses ``last_scale`` times that (0 = zero-initialised, so an
+    untrained model is the plain solver plus W_L).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    shapes = conv_stack_shapes(cin, hidden, cout, layers)
+    for l, (co, ci) in enumerate(shapes):
+        s = scale / math.sqrt(9 * ci)
+        if l == layers - 1:
+            s *= last_scale
+        W = round_bf16(rng.standard_normal((co, ci, 3, 3)) * s)
+        b = rng.standard_normal(co) * 0.02 * (last_scale if l == layers - 1 else 1.0)
+        b = np.asarray(b, dtype=np.float32).astype(np.float64)
+        out.append((W, b))
+    return out
+
+
+def random_wl(seed: int, std: float = 1e-3) -> np.ndarray:
+    """Learnable-conv kernels W_L[kind, axis, 5, 4] ~ N(0, std), float32-representable."""
+    rng = np.random.default_rng(seed)
+    return np.asarray(rng.standard_normal((2, 2, 5, 4)) * std, dtype=np.float32).astype(np.float64)

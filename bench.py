@@ -1,0 +1,312 @@
+"""Benchmark of the plain FV rollout: decaying turbulence, 256^2, batch 16, FP32.
+
+One bench step is one call of the library's rollout over the whole workload:
+16 trajectories of 2D incompressible decaying turbulence on a periodic 2 pi box,
+256 x 256 cells, nu = 1e-3 (Re = 1000), dt = 1.75e-3, 2000 time steps of four RK4
+stages each, every stage projected with the spectral Poisson solve. The metric
+is cell-updates/s = 256^2 x 16 x 2000 / (time of one bench step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own 16 trajectories (replicas, weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+``--impl reference`` times the FP64 oracle on the host cores on a bounded
+sample of the same workload (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, BATCH, STEPS_PER_ROLLOUT = 256, 16, 2000
+NU, DT = 1e-3, 1.75e-3
+METRIC = "cell-updates/s"
+UNIT = "cell-updates/s"
+WORKLOAD = "decaying NS 256^2, batch 16, 2000-step RK4 rollout (FP32, spectral projection)"
+# algorithmic FP32 flops per cell and time step (flux block + projection, see the design notes)
+FLOP_PER_CELL_STEP = 4 * (98 + 6 + 5 * 2 * math.log2(N) + 2 + 4)
+SMS, FP32_LANES = 152, 128
+
+
+def _sample_clocks(stop: threading.Event, out: list):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+    try:
+        while not stop.is_set():
+            line = p.stdout.readline()
+            if not line:
+                break
+            out.append(line.strip())
+    finally:
+        p.terminate()
+        try:
+            p.wait(timeout=2)
+        except Exception:
+            p.kill()
+
+
+def _clock_summary(lines, dev: int):
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9 or not f[0].isdigit() or int(f[0]) != dev:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx = max(mx, float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons)}
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def run_reference(args):
+    """FP64 oracle on the host cores, bounded sample of the same workload."""
+    import oracle as O
+    from paper_2507_01975_gb300 import inputs as I
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = O.Problem(nx=N, ny=N, nu=NU, dt=DT)
+    U = I.decaying_ic(N, 0)
+    steps_per_sample = 3
+    for _ in range(args.warmup):
+        U = O.rk4_step(U, p)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(steps_per_sample):
+            U = O.rk4_step(U, p)
+        t.append(time.perf_counter() - t0)
+    cells = N * N * steps_per_sample
+    value = cells * args.steps / sum(t)
+    sample = f"1 trajectory x {steps_per_sample} time steps of the 256^2 decaying flow per bench step (FP64 numpy oracle)"
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(t) / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """Time the oracle as it stands on one host core for about `seconds`."""
+    import oracle as O
+    from paper_2507_01975_gb300 import inputs as I
+
+    p = O.Problem(nx=N, ny=N, nu=NU, dt=DT)
+    U = I.decaying_ic(N, 0)
+    U = O.rk4_step(U, p)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        U = O.rk4_step(U, p)
+        n += 1
+    el = time.perf_counter() - t0
+    return {
+        "value": N * N * n / el,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"1 trajectory of the 256^2 decaying flow, {n} time steps ({el:.1f} s, FP64 numpy, 1 thread)",
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2507_01975_gb300 import build as B
+    from paper_2507_01975_gb300 import fd
+    from paper_2507_01975_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    fd.load()
+
+    cfg = fd.Config(n=N, batch=BATCH, dtype="f32", nu=NU, dt=DT)
+    solver = fd.Solver(cfg)
+    seed0 = rank * BATCH
+    U0 = np.stack([I.decaying_ic(N, seed0 + b) for b in range(BATCH)]).astype(np.float32)
+    u0 = torch.tensor(U0, device="cuda")
+    out = torch.empty_like(u0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solver.rollout(u0, out, STEPS_PER_ROLLOUT)
+    torch.cuda.synchronize()
+    if not solver.check_finite(out):
+        raise RuntimeError("rollout produced non-finite values")
+
+    clock_lines, stop = [], threading.Event()
+    th = threading.Thread(target=_sample_clocks, args=(stop, clock_lines), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        solver.rollout(u0, out, STEPS_PER_ROLLOUT)
+        ends[k].record(stream)
+        launches += solver.last_launch_count()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stop.set()
+    th.join(timeout=5)
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = N * N * BATCH * STEPS_PER_ROLLOUT
+    value = units * args.steps * world / (total_ms * 1e-3)
+    clocks = _clock_summary(clock_lines, dev)
+
+    # end to end through the host-buffer entry point: H2D copy, rollout, D2H copy
+    hin = torch.tensor(U0).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    solver.rollout_host(hin, hout, STEPS_PER_ROLLOUT)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        solver.rollout_host(hin, hout, STEPS_PER_ROLLOUT)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = units * world / (sum(e2e_t) / len(e2e_t))
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    avg_launch_s = statistics.mean(ms) * 1e-3
+    flops = FLOP_PER_CELL_STEP * units
+    achieved = flops / avg_launch_s / 1e12
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    roofline = {
+        "bound": "alu",
+        "achieved": achieved,
+        "peak": peak,
+        "unit": "TFLOP/s",
+        "frac": achieved / peak,
+        "traffic": None,
+        "kernel": "fv_rollout_kernel<float, 8, 8, 1024>",
+        "peak_basis": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x median sampled SM clock",
+        "hbm_gbs_measured": _measured_peaks().get("hbm_gbs"),
+    }
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "grid": N,
+            "batch_per_gpu": BATCH,
+            "time_steps_per_bench_step": STEPS_PER_ROLLOUT,
+            "l2": "flushed (256 MB write) between timed bench steps; state resident on chip within a rollout",
+            "parallelism": f"replicas x{world}",
+        },
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(U0.nbytes),
+                "d2h_bytes_per_step": int(U0.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

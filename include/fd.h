@@ -1,0 +1,141 @@
+/*
+ * fd.h -- C ABI of the GB300-native LDSolver coarse-grid finite-volume step.
+ *
+ * The library advances velocity fields on a periodic 2D box with the
+ * learnable-differentiable finite-volume method of "Learnable-Differentiable
+ * Finite Volume Solver for Accelerated Simulation of Flows" (KDD'25):
+ *
+ *   du/dt + div F(u, mu) = S(u)                      (Sec. 3.1, Eq. 1)
+ *
+ * discretised on a staggered (MAC) grid (App. B.1), with face interpolation
+ * and derivative operators (Sec. 3.4, App. B.2), an advection/diffusion flux
+ * assembly (App. B.2), a spectral pressure projection for the incompressible
+ * flows (Sec. 3.6, App. B.3-B.4) and classical RK4 stages (App. B.5).
+ *
+ * Conventions shared by every call:
+ *   - Field pointers passed to fd_step / fd_rollout are DEVICE pointers owned
+ *     by the caller. The library owns only the context and its small constant
+ *     tables, allocated in fd_init and released in fd_destroy.
+ *   - A state is laid out [batch][2][ny][nx], row-major, element type given by
+ *     fd_grid.dtype. Channel 0 is u, stored on the west face of cell (i, j) at
+ *     (i dx, (j + 1/2) dy); channel 1 is v, on the south face at
+ *     ((i + 1/2) dx, j dy). Pressure and divergence live at cell centres.
+ *   - Work is ordered on the CUDA stream passed as `stream` (a cudaStream_t;
+ *     NULL = the legacy default stream). No call synchronises the device
+ *     except fd_rollout_host, fd_check_finite and fd_destroy.
+ *   - Errors are returned as fd_status codes; nothing is thrown across the
+ *     ABI. fd_last_error(ctx) returns a message for the last failing call on
+ *     that context (or for fd_init failures, fd_last_error(NULL)).
+ *   - A context may be used from one host thread at a time.
+ */
+#ifndef LDFV_FD_H
+#define LDFV_FD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FD_OK = 0,
+  FD_EINVAL = 1,        /* invalid argument (sizes, null pointers, dt <= 0, nu < 0) */
+  FD_ENOMEM = 2,        /* device or host allocation failed */
+  FD_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  FD_ENONFINITE = 4,    /* fd_check_finite found a NaN or Inf */
+  FD_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+  FD_EUNSUPPORTED = 6   /* valid request that this build does not implement */
+} fd_status;
+
+typedef enum { FD_F32 = 0, FD_F64 = 1 } fd_dtype;
+
+/* Flow families of App. C.1. FD_BURGERS: S = 0, F = u^2/2 - nu grad u,
+ * advective form, no pressure. FD_NAVIER_STOKES: incompressible momentum
+ * equation with a pressure projection after every RK sub-step. */
+typedef enum { FD_BURGERS = 0, FD_NAVIER_STOKES = 1 } fd_flow;
+
+/* Grid: nx = ny = N with N a power of two in [8, 256] (this build), box
+ * [0, lx] x [0, ly], `batch` independent trajectories. */
+typedef struct {
+  int32_t nx, ny;
+  double lx, ly;
+  int32_t batch;
+  int32_t dtype; /* fd_dtype */
+  int32_t flow;  /* fd_flow */
+} fd_grid;
+
+/* Source term S (App. C.1, forced flow): kind 0 = none, kind 1 = Kolmogorov
+ * forcing f = [amp sin(k y) - drag u, -drag v] evaluated at the faces. */
+typedef struct {
+  int32_t kind;
+  double amp;   /* 1.0 in the paper */
+  int32_t k;    /* 4 in the paper */
+  double drag;  /* 0.1 in the paper */
+} fd_forcing;
+
+/* Options (NULL = defaults shown). */
+typedef struct {
+  int32_t deriv_order;    /* 4 (paper's physics kernel, default) or 2 */
+  int32_t interp_order;   /* 2 (linear interpolation); the only value accepted */
+  int32_t learned;        /* 0 = physics kernels only (default) */
+  int32_t k_c;            /* temporal-correction interval, 0 = off (default) */
+  int32_t poisson_symbol; /* 0 = discrete D2 G2 symbol (default, exact projection) */
+  int32_t ckpt_every;     /* reserved for the adjoint: checkpoint interval */
+  int64_t spin_limit;     /* reserved: iteration limit of bounded device waits */
+} fd_options;
+
+typedef struct fd_ctx fd_ctx; /* opaque, library-owned */
+
+/* Create a solver context for `grid`, viscosity nu (1/Re for Navier-Stokes),
+ * time step dt, forcing (NULL = none) and options (NULL = defaults).
+ * Allocates the context and its device tables; *out is set on FD_OK only.
+ * Errors: FD_EINVAL for bad sizes / dt <= 0 / nu < 0 / null out,
+ * FD_EUNSUPPORTED for a valid grid this build has no kernel for,
+ * FD_ENOMEM / FD_ECUDA when device set-up fails. */
+fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* forcing,
+                  const fd_options* opts, fd_ctx** out);
+
+/* One time step u_{k+1} = FV(u_k) (Sec. 3.2, Eq. for u_k; App. B.5):
+ * four RK4 stages, each evaluating the flux block on the stage state and,
+ * for Navier-Stokes, projecting the stage result. u_in and u_out are device
+ * pointers to [batch][2][ny][nx] states; they may alias. */
+fd_status fd_step(fd_ctx* ctx, const void* u_in, void* u_out, void* stream);
+
+/* n_steps time steps from u0 (device), result in u_final (device; may alias
+ * u0). When save_every > 0 and traj != NULL, the state after steps
+ * save_every, 2 save_every, ... is written to traj[s][batch][2][ny][nx]
+ * (n_steps / save_every snapshots). The whole rollout runs in one kernel
+ * launch with the state resident in on-chip memory. */
+fd_status fd_rollout(fd_ctx* ctx, const void* u0, void* traj, void* u_final, int32_t n_steps,
+                     int32_t save_every, void* stream);
+
+/* Same as fd_rollout with HOST buffers: copies u0_host to a context-owned
+ * device buffer, runs the rollout on `stream`, copies the result back to
+ * u_final_host and synchronises the stream. Pinned host memory gives the
+ * fastest copies. */
+fd_status fd_rollout_host(fd_ctx* ctx, const void* u0_host, void* u_final_host, int32_t n_steps,
+                          void* stream);
+
+/* Scan a device state [batch][2][ny][nx] for NaN/Inf. Synchronises `stream`.
+ * Returns FD_OK or FD_ENONFINITE. */
+fd_status fd_check_finite(fd_ctx* ctx, const void* u, void* stream);
+
+/* Number of kernel launches issued by the last fd_step / fd_rollout call. */
+int32_t fd_last_launch_count(const fd_ctx* ctx);
+
+/* Release the context and its device tables (synchronises the device). */
+fd_status fd_destroy(fd_ctx* ctx);
+
+/* Message of the last error on ctx (ctx may be NULL for fd_init errors).
+ * The string is owned by the library and valid until the next call. */
+const char* fd_last_error(const fd_ctx* ctx);
+
+/* Library version string. */
+const char* fd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDFV_FD_H */

@@ -1,0 +1,384 @@
+// fd_api.cu -- C ABI of the FV step library (declared in include/fd.h).
+//
+// Host-side validation, the per-context constant tables (FFT twiddles,
+// Laplacian symbols, forcing profile, stencil taps) and the dispatch to the
+// cluster-resident rollout kernel instantiated for each grid size and type.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fd.h"
+#include "fv_fused.cuh"
+
+using namespace ldfv;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct Launcher {
+  int cs = 0, nt = 0;
+  size_t smem = 0;
+  cudaError_t (*launch)(const FvArgs&, int batch, size_t smem, cudaStream_t) = nullptr;
+  cudaError_t (*prepare)(size_t smem) = nullptr;
+};
+
+template <typename T, int LOGN, int CS, int NT>
+cudaError_t launch_fused(const FvArgs& a, int batch, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS, batch, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = CS > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fv_rollout_kernel<T, LOGN, CS, NT>, a);
+}
+
+template <typename T, int LOGN, int CS, int NT>
+cudaError_t prepare_fused(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (CS > 8) {
+    e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  return e;
+}
+
+template <typename T, int LOGN, int CS, int NT>
+Launcher make_launcher() {
+  Launcher l;
+  l.cs = CS;
+  l.nt = NT;
+  l.smem = FusedCfg<T, LOGN, CS, NT>::SMEM;
+  l.launch = &launch_fused<T, LOGN, CS, NT>;
+  l.prepare = &prepare_fused<T, LOGN, CS, NT>;
+  return l;
+}
+
+// Cluster size and block size per (type, N): each thread owns one column of
+// RT = 2 * R * N / NT / 2 rows of u and v; CTAs own R = N / CS rows.
+bool pick_launcher(int dtype, int logn, Launcher* out) {
+  if (dtype == FD_F32) {
+    switch (logn) {
+      case 3: *out = make_launcher<float, 3, 1, 64>(); return true;
+      case 4: *out = make_launcher<float, 4, 1, 128>(); return true;
+      case 5: *out = make_launcher<float, 5, 1, 256>(); return true;
+      case 6: *out = make_launcher<float, 6, 1, 512>(); return true;
+      case 7: *out = make_launcher<float, 7, 2, 1024>(); return true;
+      case 8: *out = make_launcher<float, 8, 8, 1024>(); return true;
+      default: return false;
+    }
+  } else {
+    switch (logn) {
+      case 3: *out = make_launcher<double, 3, 1, 64>(); return true;
+      case 4: *out = make_launcher<double, 4, 1, 128>(); return true;
+      case 5: *out = make_launcher<double, 5, 1, 256>(); return true;
+      case 6: *out = make_launcher<double, 6, 1, 1024>(); return true;
+      case 7: *out = make_launcher<double, 7, 4, 1024>(); return true;
+      default: return false;
+    }
+  }
+}
+
+}  // namespace
+
+struct fd_ctx {
+  fd_grid grid;
+  fd_forcing forcing;
+  fd_options opts;
+  double nu = 0, dt = 0;
+  int logn = 0;
+  Launcher L;
+  bool prepared = false;
+  void* d_tables = nullptr;  // tw | symx | symy | frc
+  size_t off_symx = 0, off_symy = 0, off_frc = 0;
+  void* d_state = nullptr;   // device state for fd_rollout_host
+  unsigned* d_flag = nullptr;
+  int launches = 0;
+  std::string err;
+  FvArgs base;
+};
+
+static fd_status set_err(fd_ctx* c, fd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_init_error = buf;
+  return s;
+}
+
+static size_t elem_size(const fd_grid& g) { return g.dtype == FD_F64 ? 8 : 4; }
+static size_t state_bytes(const fd_grid& g) {
+  return (size_t)g.batch * 2 * (size_t)g.nx * (size_t)g.ny * elem_size(g);
+}
+
+template <typename T>
+static void fill_tables(fd_ctx* c, std::vector<unsigned char>& host) {
+  const int n = c->grid.nx;
+  const double dx = c->grid.lx / n, dy = c->grid.ly / n;
+  const size_t nt = (size_t)(n / 2) * 2, ns = n / 2 + 2, ny = n, nf = n;
+  c->off_symx = nt * sizeof(T);
+  c->off_symy = c->off_symx + ns * sizeof(T);
+  c->off_frc = c->off_symy + ny * sizeof(T);
+  host.assign(c->off_frc + nf * sizeof(T), 0);
+  T* tw = reinterpret_cast<T*>(host.data());
+  T* sx = reinterpret_cast<T*>(host.data() + c->off_symx);
+  T* sy = reinterpret_cast<T*>(host.data() + c->off_symy);
+  T* fr = reinterpret_cast<T*>(host.data() + c->off_frc);
+  const double pi = 3.14159265358979323846;
+  for (int m = 0; m < n / 2; ++m) {
+    tw[2 * m] = (T)std::cos(2 * pi * m / n);
+    tw[2 * m + 1] = (T)-std::sin(2 * pi * m / n);
+  }
+  for (int k = 0; k <= n / 2; ++k) {
+    if (c->opts.poisson_symbol == 0) {
+      const double s = std::sin(pi * k / n);
+      sx[k] = (T)(-4.0 / (dx * dx) * s * s);
+    } else {
+      const double e = 2 * pi * k / c->grid.lx;
+      sx[k] = (T)(-e * e);
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    if (c->opts.poisson_symbol == 0) {
+      const double s = std::sin(pi * k / n);
+      sy[k] = (T)(-4.0 / (dy * dy) * s * s);
+    } else {
+      const int ks = k < n / 2 ? k : k - n;
+      const double e = 2 * pi * ks / c->grid.ly;
+      sy[k] = (T)(-e * e);
+    }
+  }
+  for (int j = 0; j < n; ++j) {
+    const double y = (j + 0.5) * dy;
+    fr[j] = c->forcing.kind == 1 ? (T)(c->forcing.amp * std::sin(c->forcing.k * y)) : (T)0;
+  }
+}
+
+extern "C" {
+
+const char* fd_version(void) { return "ldfv 0.1 (sm_103a)"; }
+
+const char* fd_last_error(const fd_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+int32_t fd_last_launch_count(const fd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* forcing,
+                  const fd_options* opts, fd_ctx** out) {
+  if (!grid || !out) return set_err(nullptr, FD_EINVAL, "fd_init: null grid or out pointer");
+  *out = nullptr;
+  const fd_grid g = *grid;
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  if (!pow2(g.nx) || !pow2(g.ny) || g.nx < 8 || g.ny < 8 || g.nx > 2048 || g.ny > 2048)
+    return set_err(nullptr, FD_EINVAL, "fd_init: nx, ny must be powers of two in [8, 2048] (got %d x %d)",
+                   g.nx, g.ny);
+  if (g.batch < 1 || g.batch > 65535) return set_err(nullptr, FD_EINVAL, "fd_init: batch must be in [1, 65535]");
+  if (!(g.lx > 0) || !(g.ly > 0)) return set_err(nullptr, FD_EINVAL, "fd_init: box lengths must be positive");
+  if (g.dtype != FD_F32 && g.dtype != FD_F64) return set_err(nullptr, FD_EINVAL, "fd_init: unknown dtype");
+  if (g.flow != FD_BURGERS && g.flow != FD_NAVIER_STOKES)
+    return set_err(nullptr, FD_EINVAL, "fd_init: unknown flow");
+  if (!(dt > 0) || !std::isfinite(dt)) return set_err(nullptr, FD_EINVAL, "fd_init: dt must be positive");
+  if (!(nu >= 0) || !std::isfinite(nu)) return set_err(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
+  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26};
+  if (opts) o = *opts;
+  if (o.deriv_order != 2 && o.deriv_order != 4)
+    return set_err(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
+  if (o.interp_order != 2) return set_err(nullptr, FD_EINVAL, "fd_init: interp_order must be 2");
+  if (o.poisson_symbol != 0 && o.poisson_symbol != 1)
+    return set_err(nullptr, FD_EINVAL, "fd_init: poisson_symbol must be 0 or 1");
+  fd_forcing f = {0, 1.0, 4, 0.1};
+  if (forcing) f = *forcing;
+  if (f.kind != 0 && f.kind != 1) return set_err(nullptr, FD_EINVAL, "fd_init: unknown forcing kind");
+  if (g.nx != g.ny) return set_err(nullptr, FD_EUNSUPPORTED, "fd_init: only square grids are built");
+  if (o.learned || o.k_c) return set_err(nullptr, FD_EUNSUPPORTED, "fd_init: learned mode is not built");
+  int logn = 0;
+  while ((1 << logn) < g.nx) ++logn;
+  Launcher L;
+  if (!pick_launcher(g.dtype, logn, &L))
+    return set_err(nullptr, FD_EUNSUPPORTED, "fd_init: no on-chip kernel for N=%d dtype=%d", g.nx, g.dtype);
+
+  fd_ctx* c = new (std::nothrow) fd_ctx();
+  if (!c) return set_err(nullptr, FD_ENOMEM, "fd_init: out of host memory");
+  c->grid = g;
+  c->forcing = f;
+  c->opts = o;
+  c->nu = nu;
+  c->dt = dt;
+  c->logn = logn;
+  c->L = L;
+
+  std::vector<unsigned char> host;
+  if (g.dtype == FD_F64)
+    fill_tables<double>(c, host);
+  else
+    fill_tables<float>(c, host);
+  cudaError_t e = cudaMalloc(&c->d_tables, host.size());
+  if (e != cudaSuccess) {
+    delete c;
+    return set_err(nullptr, FD_ENOMEM, "fd_init: cudaMalloc tables: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(c->d_tables, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = L.prepare(L.smem);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_tables);
+    delete c;
+    return set_err(nullptr, FD_ECUDA, "fd_init: device set-up: %s", cudaGetErrorString(e));
+  }
+
+  const int n = g.nx;
+  const double dx = g.lx / n, dy = g.ly / n;
+  FvArgs& a = c->base;
+  std::memset(&a, 0, sizeof a);
+  a.flow = g.flow;
+  a.forcing = f.kind;
+  a.dt = dt;
+  a.nu = nu;
+  a.idx = 1.0 / dx;
+  a.idy = 1.0 / dy;
+  a.drag = f.kind == 1 ? f.drag : 0.0;
+  a.inv_nn = 1.0 / ((double)n * n);
+  const double ci[4] = {0.0, 0.5, 0.5, 0.0};
+  double cd[4];
+  if (o.deriv_order == 4) {
+    const double d4[4] = {1.0 / 24, -27.0 / 24, 27.0 / 24, -1.0 / 24};
+    std::memcpy(cd, d4, sizeof cd);
+  } else {
+    const double d2[4] = {0.0, -1.0, 1.0, 0.0};
+    std::memcpy(cd, d2, sizeof cd);
+  }
+  for (int q = 0; q < 4; ++q) {
+    a.ci[q] = ci[q];
+    a.cx[q] = cd[q] / dx;
+    a.cy[q] = cd[q] / dy;
+  }
+  const char* base = static_cast<const char*>(c->d_tables);
+  a.tw = base;
+  a.symx = base + c->off_symx;
+  a.symy = base + c->off_symy;
+  a.frc = base + c->off_frc;
+  *out = c;
+  return FD_OK;
+}
+
+fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32_t n_steps,
+                     int32_t save_every, void* stream) {
+  if (!c) return set_err(nullptr, FD_EINVAL, "fd_rollout: null context");
+  c->launches = 0;
+  if (!u0 || !u_final) return set_err(c, FD_EINVAL, "fd_rollout: null state pointer");
+  if (n_steps < 0) return set_err(c, FD_EINVAL, "fd_rollout: n_steps must be >= 0");
+  if (save_every < 0) return set_err(c, FD_EINVAL, "fd_rollout: save_every must be >= 0");
+  if (save_every > 0 && !traj) return set_err(c, FD_EINVAL, "fd_rollout: save_every > 0 needs traj");
+  FvArgs a = c->base;
+  a.u_in = u0;
+  a.u_out = u_final;
+  a.traj = save_every > 0 ? traj : nullptr;
+  a.n_steps = n_steps;
+  a.save_every = save_every;
+  cudaError_t e = c->L.launch(a, c->grid.batch, c->L.smem, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_rollout: launch failed: %s", cudaGetErrorString(e));
+  c->launches = 1;
+  return FD_OK;
+}
+
+fd_status fd_step(fd_ctx* c, const void* u_in, void* u_out, void* stream) {
+  if (!c) return set_err(nullptr, FD_EINVAL, "fd_step: null context");
+  return fd_rollout(c, u_in, nullptr, u_out, 1, 0, stream);
+}
+
+fd_status fd_rollout_host(fd_ctx* c, const void* u0_host, void* u_final_host, int32_t n_steps,
+                          void* stream) {
+  if (!c) return set_err(nullptr, FD_EINVAL, "fd_rollout_host: null context");
+  if (!u0_host || !u_final_host) return set_err(c, FD_EINVAL, "fd_rollout_host: null host pointer");
+  const size_t bytes = state_bytes(c->grid);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!c->d_state) {
+    cudaError_t e = cudaMalloc(&c->d_state, bytes);
+    if (e != cudaSuccess) {
+      c->d_state = nullptr;
+      return set_err(c, FD_ENOMEM, "fd_rollout_host: cudaMalloc: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(c->d_state, u0_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_rollout_host: H2D copy: %s", cudaGetErrorString(e));
+  fd_status s = fd_rollout(c, c->d_state, nullptr, c->d_state, n_steps, 0, stream);
+  if (s != FD_OK) return s;
+  e = cudaMemcpyAsync(u_final_host, c->d_state, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_rollout_host: D2H copy: %s", cudaGetErrorString(e));
+  return FD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+__global__ void finite_scan_kernel(const T* u, size_t n, unsigned* flag) {
+  unsigned bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= isfinite((double)u[i]) ? 0u : 1u;
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+}  // namespace
+
+extern "C" {
+
+fd_status fd_check_finite(fd_ctx* c, const void* u, void* stream) {
+  if (!c) return set_err(nullptr, FD_EINVAL, "fd_check_finite: null context");
+  if (!u) return set_err(c, FD_EINVAL, "fd_check_finite: null state pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!c->d_flag) {
+    e = cudaMalloc(&c->d_flag, sizeof(unsigned));
+    if (e != cudaSuccess) {
+      c->d_flag = nullptr;
+      return set_err(c, FD_ENOMEM, "fd_check_finite: cudaMalloc: %s", cudaGetErrorString(e));
+    }
+  }
+  e = cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), st);
+  const size_t n = state_bytes(c->grid) / elem_size(c->grid);
+  if (e == cudaSuccess) {
+    if (c->grid.dtype == FD_F64)
+      finite_scan_kernel<double><<<152, 256, 0, st>>>(static_cast<const double*>(u), n, c->d_flag);
+    else
+      finite_scan_kernel<float><<<152, 256, 0, st>>>(static_cast<const float*>(u), n, c->d_flag);
+    e = cudaGetLastError();
+  }
+  unsigned h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->d_flag, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_check_finite: %s", cudaGetErrorString(e));
+  return h ? set_err(c, FD_ENONFINITE, "fd_check_finite: state holds NaN or Inf") : FD_OK;
+}
+
+fd_status fd_destroy(fd_ctx* c) {
+  if (!c) return FD_OK;
+  cudaDeviceSynchronize();
+  if (c->d_tables) cudaFree(c->d_tables);
+  if (c->d_state) cudaFree(c->d_state);
+  if (c->d_flag) cudaFree(c->d_flag);
+  delete c;
+  return FD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+"""ctypes binding of the C ABI in ``include/fd.h`` (argument marshalling only).
+
+Every computation runs in ``libldfv.so``; this module converts Python values
+and torch CUDA tensors into the plain pointers and sizes the ABI takes. There
+is no fallback: if the library cannot be loaded, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libldfv.so")
+
+FD_OK, FD_EINVAL, FD_ENOMEM, FD_ECUDA, FD_ENONFINITE, FD_ETIMEOUT, FD_EUNSUPPORTED = range(7)
+FD_F32, FD_F64 = 0, 1
+FD_BURGERS, FD_NAVIER_STOKES = 0, 1
+
+#: every symbol include/fd.h declares
+EXPORTS = [
+    "fd_init",
+    "fd_step",
+    "fd_rollout",
+    "fd_rollout_host",
+    "fd_check_finite",
+    "fd_last_launch_count",
+    "fd_destroy",
+    "fd_last_error",
+    "fd_version",
+]
+
+
+class FdGrid(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32),
+        ("ny", C.c_int32),
+        ("lx", C.c_double),
+        ("ly", C.c_double),
+        ("batch", C.c_int32),
+        ("dtype", C.c_int32),
+        ("flow", C.c_int32),
+    ]
+
+
+class FdForcing(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("amp", C.c_double), ("k", C.c_int32), ("drag", C.c_double)]
+
+
+class FdOptions(C.Structure):
+    _fields_ = [
+        ("deriv_order", C.c_int32),
+        ("interp_order", C.c_int32),
+        ("learned", C.c_int32),
+        ("k_c", C.c_int32),
+        ("poisson_symbol", C.c_int32),
+        ("ckpt_every", C.c_int32),
+        ("spin_limit", C.c_int64),
+    ]
+
+
+class FdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fd status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libldfv.so`` and declare the ABI's signatures (raises if missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FdError(FD_EUNSUPPORTED, f"CUDA library {path} is not built; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i32 = C.c_void_p, C.c_int32
+    lib.fd_init.argtypes = [C.POINTER(FdGrid), C.c_double, C.c_double, C.POINTER(FdForcing),
+                            C.POINTER(FdOptions), C.POINTER(vp)]
+    lib.fd_init.restype = C.c_int
+    lib.fd_step.argtypes = [vp, vp, vp, vp]
+    lib.fd_step.restype = C.c_int
+    lib.fd_rollout.argtypes = [vp, vp, vp, vp, i32, i32, vp]
+    lib.fd_rollout.restype = C.c_int
+    lib.fd_rollout_host.argtypes = [vp, vp, vp, i32, vp]
+    lib.fd_rollout_host.restype = C.c_int
+    lib.fd_check_finite.argtypes = [vp, vp, vp]
+    lib.fd_check_finite.restype = C.c_int
+    lib.fd_last_launch_count.argtypes = [vp]
+    lib.fd_last_launch_count.restype = i32
+    lib.fd_destroy.argtypes = [vp]
+    lib.fd_destroy.restype = C.c_int
+    lib.fd_last_error.argtypes = [vp]
+    lib.fd_last_error.restype = C.c_char_p
+    lib.fd_version.argtypes = []
+    lib.fd_version.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Config:
+    """Python mirror of fd_grid + fd_forcing + fd_options."""
+
+    n: int
+    batch: int = 1
+    dtype: str = "f32"
+    flow: str = "ns"  # "ns" or "burgers"
+    nu: float = 1e-3
+    dt: float = 1e-3
+    lx: float = 2 * math.pi
+    ly: float = 2 * math.pi
+    forcing: Optional[str] = None  # None or "kolmogorov"
+    amp: float = 1.0
+    kf: int = 4
+    drag: float = 0.1
+    deriv_order: int = 4
+    poisson_symbol: int = 0
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
+
+
+class Solver:
+    """One fd_ctx: a batch of trajectories of one grid, flow and time step."""
+
+    def __init__(self, cfg: Config):
+        self.lib = load()
+        self.cfg = cfg
+        g = FdGrid(cfg.n, cfg.n, cfg.lx, cfg.ly, cfg.batch, FD_F64 if cfg.dtype == "f64" else FD_F32,
+                   FD_BURGERS if cfg.flow == "burgers" else FD_NAVIER_STOKES)
+        f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
+        o = FdOptions(cfg.deriv_order, 2, 0, 0, cfg.poisson_symbol, 8, 1 << 26)
+        h = C.c_void_p()
+        st = self.lib.fd_init(C.byref(g), cfg.nu, cfg.dt, C.byref(f), C.byref(o), C.byref(h))
+        if st != FD_OK:
+            raise FdError(st, self.lib.fd_last_error(None).decode())
+        self.h = h
+
+    # --- helpers --------------------------------------------------------
+    def _check(self, st):
+        if st != FD_OK:
+            raise FdError(st, self.lib.fd_last_error(self.h).decode())
+
+    @property
+    def state_shape(self):
+        return (self.cfg.batch, 2, self.cfg.n, self.cfg.n)
+
+    @property
+    def torch_dtype(self):
+        import torch
+
+        return torch.float64 if self.cfg.dtype == "f64" else torch.float32
+
+    # --- ABI calls --------------------------------------------------------
+    def step(self, u_in, u_out, stream=None):
+        self._check(self.lib.fd_step(self.h, _ptr(u_in), _ptr(u_out), _stream_handle(stream)))
+
+    def rollout(self, u0, u_final, n_steps: int, traj=None, save_every: int = 0, stream=None):
+        tp = _ptr(traj) if traj is not None else None
+        self._check(self.lib.fd_rollout(self.h, _ptr(u0), tp, _ptr(u_final), int(n_steps), int(save_every),
+                                        _stream_handle(stream)))
+
+    def rollout_host(self, u0_host, u_final_host, n_steps: int, stream=None):
+        self._check(self.lib.fd_rollout_host(self.h, _ptr(u0_host), _ptr(u_final_host), int(n_steps),
+                                             _stream_handle(stream)))
+
+    def check_finite(self, u, stream=None) -> bool:
+        st = self.lib.fd_check_finite(self.h, _ptr(u), _stream_handle(stream))
+        if st == FD_ENONFINITE:
+            return False
+        self._check(st)
+        return True
+
+    def last_launch_count(self) -> int:
+        return int(self.lib.fd_last_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return load().fd_version().decode()

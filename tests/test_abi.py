@@ -1,0 +1,96 @@
+"""The C ABI library loads, exports every symbol include/*.h declares, and
+validates its arguments on the host (no GPU needed for any of this)."""
+
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2507_01975_gb300 import fd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(fd_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_01975_gb300 import build
+
+    build.build()
+    return fd.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert declared, "no fd_* declarations found"
+    assert declared <= set(fd.EXPORTS) | declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(fd.EXPORTS) == declared
+
+
+def test_version_string(lib):
+    assert fd.version().startswith("ldfv")
+
+
+def _init(lib, n=32, batch=1, dtype=fd.FD_F32, flow=fd.FD_NAVIER_STOKES, nu=1e-3, dt=1e-3, opts=None,
+          lx=6.283185307179586):
+    g = fd.FdGrid(n, n, lx, lx, batch, dtype, flow)
+    h = C.c_void_p()
+    o = C.byref(opts) if opts is not None else None
+    return lib.fd_init(C.byref(g), nu, dt, None, o, C.byref(h)), h
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [
+        dict(n=12),
+        dict(n=4),
+        dict(n=4096),
+        dict(batch=0),
+        dict(dt=0.0),
+        dict(dt=-1e-3),
+        dict(nu=-1.0),
+        dict(dtype=7),
+        dict(flow=3),
+        dict(lx=0.0),
+        dict(opts=fd.FdOptions(3, 2, 0, 0, 0, 8, 1)),
+        dict(opts=fd.FdOptions(4, 4, 0, 0, 0, 8, 1)),
+    ],
+)
+def test_init_rejects_invalid_arguments(lib, kw):
+    st, h = _init(lib, **kw)
+    assert st == fd.FD_EINVAL
+    assert h.value is None
+    assert len(lib.fd_last_error(None)) > 0
+
+
+def test_init_rejects_null_pointers(lib):
+    h = C.c_void_p()
+    assert lib.fd_init(None, 1e-3, 1e-3, None, None, C.byref(h)) == fd.FD_EINVAL
+    g = fd.FdGrid(32, 32, 1.0, 1.0, 1, 0, 1)
+    assert lib.fd_init(C.byref(g), 1e-3, 1e-3, None, None, None) == fd.FD_EINVAL
+
+
+def test_calls_on_null_context_are_rejected(lib):
+    assert lib.fd_step(None, None, None, None) == fd.FD_EINVAL
+    assert lib.fd_rollout(None, None, None, None, 1, 0, None) == fd.FD_EINVAL
+    assert lib.fd_rollout_host(None, None, None, 1, None) == fd.FD_EINVAL
+    assert lib.fd_check_finite(None, None, None) == fd.FD_EINVAL
+    assert lib.fd_destroy(None) == fd.FD_OK
+    assert lib.fd_last_launch_count(None) == 0
+
+
+def test_oversized_grid_is_unsupported_not_invalid(lib):
+    st, _ = _init(lib, n=512)
+    assert st == fd.FD_EUNSUPPORTED

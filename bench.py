@@ -40,8 +40,10 @@ NU, DT = 1e-3, 1.75e-3
 METRIC = "cell-updates/s"
 UNIT = "cell-updates/s"
 WORKLOAD = "decaying NS 256^2, batch 16, 2000-step RK4 rollout (FP32, spectral projection)"
-# algorithmic FP32 flops per cell and time step (flux block + projection, see the design notes)
-FLOP_PER_CELL_STEP = 4 * (98 + 6 + 5 * 2 * math.log2(N) + 2 + 4)
+# algorithmic FP32 flops per cell and time step, per RK stage: 8 face operators x 4 taps x 2 (64),
+# flux assembly (24), RK combination (8), divergence (4), gradient (4), spectral multiply (2) and a
+# real-to-complex plus complex-to-real 2D FFT pair (2 x 2.5 log2(N^2) = 10 log2 N per cell)
+FLOP_PER_CELL_STEP = 4 * (64 + 24 + 8 + 4 + 4 + 2 + 10 * math.log2(N))
 SMS, FP32_LANES = 152, 128
 
 
@@ -168,6 +170,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
+                    help="time steps per rollout (the workload's 2000 by default; smaller only for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -206,7 +210,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        solver.rollout(u0, out, STEPS_PER_ROLLOUT)
+        solver.rollout(u0, out, args.time_steps)
     torch.cuda.synchronize()
     if not solver.check_finite(out):
         raise RuntimeError("rollout produced non-finite values")
@@ -224,7 +228,7 @@ def main():
     for k in range(args.steps):
         flush.fill_(float(k))
         starts[k].record(stream)
-        solver.rollout(u0, out, STEPS_PER_ROLLOUT)
+        solver.rollout(u0, out, args.time_steps)
         ends[k].record(stream)
         launches += solver.last_launch_count()
     torch.cuda.synchronize()
@@ -238,18 +242,18 @@ def main():
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    units = N * N * BATCH * STEPS_PER_ROLLOUT
+    units = N * N * BATCH * args.time_steps
     value = units * args.steps * world / (total_ms * 1e-3)
     clocks = _clock_summary(clock_lines, dev)
 
     # end to end through the host-buffer entry point: H2D copy, rollout, D2H copy
     hin = torch.tensor(U0).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
-    solver.rollout_host(hin, hout, STEPS_PER_ROLLOUT)
+    solver.rollout_host(hin, hout, args.time_steps)
     e2e_t = []
     for _ in range(max(3, min(args.steps, 5))):
         t0 = time.perf_counter()
-        solver.rollout_host(hin, hout, STEPS_PER_ROLLOUT)
+        solver.rollout_host(hin, hout, args.time_steps)
         e2e_t.append(time.perf_counter() - t0)
     e2e_val = units * world / (sum(e2e_t) / len(e2e_t))
 
@@ -292,7 +296,7 @@ def main():
             "workload": WORKLOAD,
             "grid": N,
             "batch_per_gpu": BATCH,
-            "time_steps_per_bench_step": STEPS_PER_ROLLOUT,
+            "time_steps_per_bench_step": args.time_steps,
             "l2": "flushed (256 MB write) between timed bench steps; state resident on chip within a rollout",
             "parallelism": f"replicas x{world}",
         },

@@ -131,6 +131,26 @@ fd_status fd_destroy(fd_ctx* ctx);
  * The string is owned by the library and valid until the next call. */
 const char* fd_last_error(const fd_ctx* ctx);
 
+/* Largest element count fd_check_finite_noalloc accepts (2^24: a batch of
+ * 16 FP32 256^2 states, or two 2048^2 ones). */
+#define FD_NOALLOC_MAX_ELEMS (1 << 24)
+
+/* Allocation-free NaN/Inf scan for callers that must not allocate device
+ * memory (a framework pool that forbids raw cudaMalloc, a latency-critical
+ * path that must not enter the allocator). The paper has no counterpart: this
+ * is a service of the library, not a step of the method.
+ * u: device pointer to `count` elements of type `dtype` (fd_dtype), any layout.
+ * nonfinite: host pointer, receives the number of NaN/Inf elements.
+ * Work runs on `stream`, which the call synchronises. The only scratch is a
+ * 32 KB array in the library's static device memory (held on every GPU that
+ * loads the library until exit); the call allocates nothing. The first call
+ * on a device looks up that array's address: make it before any stream
+ * capture. Calls that overlap on the GPU share the array and race.
+ * Returns FD_OK (no NaN/Inf), FD_ENONFINITE, FD_EINVAL (null pointer, unknown
+ * dtype, count < 0 or count > FD_NOALLOC_MAX_ELEMS) or FD_ECUDA. */
+fd_status fd_check_finite_noalloc(const void* u, int64_t count, int32_t dtype, int64_t* nonfinite,
+                                  void* stream);
+
 /* Library version string. */
 const char* fd_version(void);
 

@@ -27,6 +27,7 @@ EXPORTS = [
     "fd_rollout",
     "fd_rollout_host",
     "fd_check_finite",
+    "fd_check_finite_noalloc",
     "fd_last_launch_count",
     "fd_destroy",
     "fd_last_error",

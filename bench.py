@@ -274,7 +274,7 @@ def main():
         "unit": "TFLOP/s",
         "frac": achieved / peak,
         "traffic": None,
-        "kernel": "fv_rollout_kernel<float, 8, 8, 1024>",
+        "kernel": "fv_rollout_kernel<float, 8, 8, 512, 4>",
         "peak_basis": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x median sampled SM clock",
         "hbm_gbs_measured": _measured_peaks().get("hbm_gbs"),
     }

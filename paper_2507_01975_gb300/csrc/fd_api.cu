@@ -28,7 +28,7 @@ struct Launcher {
   cudaError_t (*prepare)(size_t smem) = nullptr;
 };
 
-template <typename T, int LOGN, int CS, int NT>
+template <typename T, int LOGN, int CS, int NT, int DORD>
 cudaError_t launch_fused(const FvArgs& a, int batch, size_t smem, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS, batch, 1);
@@ -42,52 +42,58 @@ cudaError_t launch_fused(const FvArgs& a, int batch, size_t smem, cudaStream_t s
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = CS > 1 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, fv_rollout_kernel<T, LOGN, CS, NT>, a);
+  return cudaLaunchKernelEx(&cfg, fv_rollout_kernel<T, LOGN, CS, NT, DORD>, a);
 }
 
-template <typename T, int LOGN, int CS, int NT>
+template <typename T, int LOGN, int CS, int NT, int DORD>
 cudaError_t prepare_fused(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT>,
+  cudaError_t e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT, DORD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (CS > 8) {
-    e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT>,
+    e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT, DORD>,
                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
   return e;
 }
 
 template <typename T, int LOGN, int CS, int NT>
-Launcher make_launcher() {
+Launcher make_launcher(int dord) {
   Launcher l;
   l.cs = CS;
   l.nt = NT;
   l.smem = FusedCfg<T, LOGN, CS, NT>::SMEM;
-  l.launch = &launch_fused<T, LOGN, CS, NT>;
-  l.prepare = &prepare_fused<T, LOGN, CS, NT>;
+  if (dord == 4) {
+    l.launch = &launch_fused<T, LOGN, CS, NT, 4>;
+    l.prepare = &prepare_fused<T, LOGN, CS, NT, 4>;
+  } else {
+    l.launch = &launch_fused<T, LOGN, CS, NT, 2>;
+    l.prepare = &prepare_fused<T, LOGN, CS, NT, 2>;
+  }
   return l;
 }
 
-// Cluster size and block size per (type, N): each thread owns one column of
-// RT = 2 * R * N / NT / 2 rows of u and v; CTAs own R = N / CS rows.
-bool pick_launcher(int dtype, int logn, Launcher* out) {
+// Cluster size and block size per (type, N): CTAs own R = N / CS rows, each
+// thread one column of R * N / NT of those rows. Every configuration with
+// N >= 64 fits two CTAs per SM, so all clusters of a batch are co-resident.
+bool pick_launcher(int dtype, int logn, int dord, Launcher* out) {
   if (dtype == FD_F32) {
     switch (logn) {
-      case 3: *out = make_launcher<float, 3, 1, 64>(); return true;
-      case 4: *out = make_launcher<float, 4, 1, 128>(); return true;
-      case 5: *out = make_launcher<float, 5, 1, 256>(); return true;
-      case 6: *out = make_launcher<float, 6, 1, 512>(); return true;
-      case 7: *out = make_launcher<float, 7, 2, 1024>(); return true;
-      case 8: *out = make_launcher<float, 8, 8, 1024>(); return true;
+      case 3: *out = make_launcher<float, 3, 1, 64>(dord); return true;
+      case 4: *out = make_launcher<float, 4, 1, 128>(dord); return true;
+      case 5: *out = make_launcher<float, 5, 1, 256>(dord); return true;
+      case 6: *out = make_launcher<float, 6, 1, 512>(dord); return true;
+      case 7: *out = make_launcher<float, 7, 2, 512>(dord); return true;
+      case 8: *out = make_launcher<float, 8, 8, 512>(dord); return true;
       default: return false;
     }
   } else {
     switch (logn) {
-      case 3: *out = make_launcher<double, 3, 1, 64>(); return true;
-      case 4: *out = make_launcher<double, 4, 1, 128>(); return true;
-      case 5: *out = make_launcher<double, 5, 1, 256>(); return true;
-      case 6: *out = make_launcher<double, 6, 1, 1024>(); return true;
-      case 7: *out = make_launcher<double, 7, 4, 1024>(); return true;
+      case 3: *out = make_launcher<double, 3, 1, 64>(dord); return true;
+      case 4: *out = make_launcher<double, 4, 1, 128>(dord); return true;
+      case 5: *out = make_launcher<double, 5, 1, 256>(dord); return true;
+      case 6: *out = make_launcher<double, 6, 1, 512>(dord); return true;
+      case 7: *out = make_launcher<double, 7, 4, 512>(dord); return true;
       default: return false;
     }
   }
@@ -105,6 +111,7 @@ struct fd_ctx {
   bool prepared = false;
   void* d_tables = nullptr;  // tw | symx | symy | frc
   size_t off_symx = 0, off_symy = 0, off_frc = 0;
+  void* d_acc = nullptr;     // RK4 accumulator [batch][2][ny][nx]
   void* d_state = nullptr;   // device state for fd_rollout_host
   unsigned* d_flag = nullptr;
   int launches = 0;
@@ -214,7 +221,7 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   int logn = 0;
   while ((1 << logn) < g.nx) ++logn;
   Launcher L;
-  if (!pick_launcher(g.dtype, logn, &L))
+  if (!pick_launcher(g.dtype, logn, o.deriv_order, &L))
     return set_err(nullptr, FD_EUNSUPPORTED, "fd_init: no on-chip kernel for N=%d dtype=%d", g.nx, g.dtype);
 
   fd_ctx* c = new (std::nothrow) fd_ctx();
@@ -233,14 +240,19 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   else
     fill_tables<float>(c, host);
   cudaError_t e = cudaMalloc(&c->d_tables, host.size());
+  if (e == cudaSuccess) {
+    e = cudaMalloc(&c->d_acc, state_bytes(g));
+    if (e != cudaSuccess) cudaFree(c->d_tables);
+  }
   if (e != cudaSuccess) {
     delete c;
-    return set_err(nullptr, FD_ENOMEM, "fd_init: cudaMalloc tables: %s", cudaGetErrorString(e));
+    return set_err(nullptr, FD_ENOMEM, "fd_init: cudaMalloc: %s", cudaGetErrorString(e));
   }
   e = cudaMemcpy(c->d_tables, host.data(), host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = L.prepare(L.smem);
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
+    cudaFree(c->d_acc);
     delete c;
     return set_err(nullptr, FD_ECUDA, "fd_init: device set-up: %s", cudaGetErrorString(e));
   }
@@ -257,20 +269,6 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   a.idy = 1.0 / dy;
   a.drag = f.kind == 1 ? f.drag : 0.0;
   a.inv_nn = 1.0 / ((double)n * n);
-  const double ci[4] = {0.0, 0.5, 0.5, 0.0};
-  double cd[4];
-  if (o.deriv_order == 4) {
-    const double d4[4] = {1.0 / 24, -27.0 / 24, 27.0 / 24, -1.0 / 24};
-    std::memcpy(cd, d4, sizeof cd);
-  } else {
-    const double d2[4] = {0.0, -1.0, 1.0, 0.0};
-    std::memcpy(cd, d2, sizeof cd);
-  }
-  for (int q = 0; q < 4; ++q) {
-    a.ci[q] = ci[q];
-    a.cx[q] = cd[q] / dx;
-    a.cy[q] = cd[q] / dy;
-  }
   const char* base = static_cast<const char*>(c->d_tables);
   a.tw = base;
   a.symx = base + c->off_symx;
@@ -291,6 +289,7 @@ fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32
   FvArgs a = c->base;
   a.u_in = u0;
   a.u_out = u_final;
+  a.acc = c->d_acc;
   a.traj = save_every > 0 ? traj : nullptr;
   a.n_steps = n_steps;
   a.save_every = save_every;
@@ -375,6 +374,7 @@ fd_status fd_destroy(fd_ctx* c) {
   if (!c) return FD_OK;
   cudaDeviceSynchronize();
   if (c->d_tables) cudaFree(c->d_tables);
+  if (c->d_acc) cudaFree(c->d_acc);
   if (c->d_state) cudaFree(c->d_state);
   if (c->d_flag) cudaFree(c->d_flag);
   delete c;

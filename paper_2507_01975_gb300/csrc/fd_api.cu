@@ -111,7 +111,6 @@ struct fd_ctx {
   bool prepared = false;
   void* d_tables = nullptr;  // tw | symx | symy | frc
   size_t off_symx = 0, off_symy = 0, off_frc = 0;
-  void* d_acc = nullptr;     // RK4 accumulator [batch][2][ny][nx]
   void* d_state = nullptr;   // device state for fd_rollout_host
   unsigned* d_flag = nullptr;
   int launches = 0;
@@ -240,10 +239,6 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   else
     fill_tables<float>(c, host);
   cudaError_t e = cudaMalloc(&c->d_tables, host.size());
-  if (e == cudaSuccess) {
-    e = cudaMalloc(&c->d_acc, state_bytes(g));
-    if (e != cudaSuccess) cudaFree(c->d_tables);
-  }
   if (e != cudaSuccess) {
     delete c;
     return set_err(nullptr, FD_ENOMEM, "fd_init: cudaMalloc: %s", cudaGetErrorString(e));
@@ -252,7 +247,6 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   if (e == cudaSuccess) e = L.prepare(L.smem);
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
-    cudaFree(c->d_acc);
     delete c;
     return set_err(nullptr, FD_ECUDA, "fd_init: device set-up: %s", cudaGetErrorString(e));
   }
@@ -289,7 +283,6 @@ fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32
   FvArgs a = c->base;
   a.u_in = u0;
   a.u_out = u_final;
-  a.acc = c->d_acc;
   a.traj = save_every > 0 ? traj : nullptr;
   a.n_steps = n_steps;
   a.save_every = save_every;
@@ -374,7 +367,6 @@ fd_status fd_destroy(fd_ctx* c) {
   if (!c) return FD_OK;
   cudaDeviceSynchronize();
   if (c->d_tables) cudaFree(c->d_tables);
-  if (c->d_acc) cudaFree(c->d_acc);
   if (c->d_state) cudaFree(c->d_state);
   if (c->d_flag) cudaFree(c->d_flag);
   delete c;

@@ -160,3 +160,107 @@ struct WarpFFT {
 };
 
 }  // namespace ldfv
+
+namespace ldfv {
+
+// ---------------------------------------------------------------------------
+// Tensor memory (TMEM) as per-thread on-chip storage.
+//
+// Each SM has 128 lanes x 512 columns of 32-bit tensor memory. A warp may only
+// touch the 32 lanes of its quarter (warp % 4); with the 32x32b shape every
+// thread of the warp reads or writes its own lane. The rollout kernel keeps
+// u_n and the RK4 accumulator of the cells a thread owns in its lane.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// whole warp; writes the allocated base address to *dst (shared memory)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// four consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
+// The four per-cell values (u_n.u, u_n.v, acc.u, acc.v) of one row in
+// consecutive columns: 4 columns in FP32, 8 in FP64.
+template <typename T>
+struct CellSlot;
+template <>
+struct CellSlot<float> {
+  static constexpr int COLS = 4;
+  static __device__ __forceinline__ void load(uint32_t ta, float& a, float& b, float& c, float& d) {
+    uint32_t r[4];
+    tmem_ld4(ta, r);
+    tmem_wait_ld();
+    a = __uint_as_float(r[0]);
+    b = __uint_as_float(r[1]);
+    c = __uint_as_float(r[2]);
+    d = __uint_as_float(r[3]);
+  }
+  static __device__ __forceinline__ void store(uint32_t ta, float a, float b, float c, float d) {
+    const uint32_t r[4] = {__float_as_uint(a), __float_as_uint(b), __float_as_uint(c), __float_as_uint(d)};
+    tmem_st4(ta, r);
+  }
+};
+template <>
+struct CellSlot<double> {
+  static constexpr int COLS = 8;
+  static __device__ __forceinline__ double join(uint32_t lo, uint32_t hi) {
+    return __hiloint2double((int)hi, (int)lo);
+  }
+  static __device__ __forceinline__ void load(uint32_t ta, double& a, double& b, double& c, double& d) {
+    uint32_t r[8];
+    tmem_ld8(ta, r);
+    tmem_wait_ld();
+    a = join(r[0], r[1]);
+    b = join(r[2], r[3]);
+    c = join(r[4], r[5]);
+    d = join(r[6], r[7]);
+  }
+  static __device__ __forceinline__ void store(uint32_t ta, double a, double b, double c, double d) {
+    const uint32_t r[8] = {(uint32_t)__double2loint(a), (uint32_t)__double2hiint(a),
+                           (uint32_t)__double2loint(b), (uint32_t)__double2hiint(b),
+                           (uint32_t)__double2loint(c), (uint32_t)__double2hiint(c),
+                           (uint32_t)__double2loint(d), (uint32_t)__double2hiint(d)};
+    tmem_st8(ta, r);
+  }
+};
+
+}  // namespace ldfv

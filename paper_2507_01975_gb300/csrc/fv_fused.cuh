@@ -4,10 +4,11 @@
 // periodic MAC grid for the whole rollout; CTA `rank` owns rows
 // [rank*R, (rank+1)*R), R = N / CS, of both velocity components. The stage
 // state lives in shared memory with two halo rows below and three above; the
-// state at the start of the time step (u_n) lives in the caller's output
-// buffer and the RK4 accumulator in a context-owned buffer (both stay in L2),
-// each touched only by the thread that owns the cell. Neighbouring rows and
-// the FFT transposes move through distributed shared memory (DSMEM).
+// state at the start of the time step (u_n) and the RK4 accumulator live in
+// tensor memory (TMEM), in the lane of the thread that owns the cell.
+// Neighbouring rows and the FFT transposes move through distributed shared
+// memory (DSMEM). Global memory is touched only to load the initial state and
+// to store snapshots and the final state.
 //
 // Per RK4 stage (App. B.5), for stage state w:
 //   A. cluster barrier, halo rows of w from the neighbour CTAs (periodic
@@ -22,9 +23,9 @@
 //      divergence computed in registers -> warp FFTs of two real rows packed
 //      as one complex row, unpacked into half spectra -> in-place DSMEM
 //      transpose -> warp column FFTs, multiply by 1 / symbol of D2 G2 (zero
-//      mode removed), inverse column FFTs -> in-place DSMEM transpose back
-//      (plus the previous CTA's last row pair) -> inverse warp row FFTs ->
-//      w' -= G2 p.
+//      mode removed), inverse column FFTs -> in-place DSMEM transpose back ->
+//      inverse warp row FFTs -> w' -= G2 p (the row below comes from the
+//      previous CTA through DSMEM).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -36,8 +37,7 @@ namespace cg = cooperative_groups;
 
 struct FvArgs {
   const void* u_in;
-  void* u_out;   // holds u_n during the rollout and the final state at the end
-  void* acc;     // [batch][2][N][N] RK4 accumulator (context-owned)
+  void* u_out;
   void* traj;
   int n_steps;
   int save_every;
@@ -63,28 +63,48 @@ struct FusedCfg {
   static constexpr int NW = NT / 32;
   static constexpr int NC = N / 2 / CS;  // spectral columns owned after the transpose
   static constexpr int COLLEN = N + 1;   // padded column length
+  static constexpr int HSTR = N / 2 + 1; // padded half-spectrum row length
   using CT = typename Cplx<T>::t;
   using FFT = WarpFFT<T, LOGN>;
   static constexpr size_t W_BYTES = (size_t)2 * HR * N * sizeof(T);
-  static constexpr size_t ROW_BYTES = (size_t)(R + 2) * (N / 2) * sizeof(CT);
+  static constexpr size_t ROW_BYTES = (size_t)R * HSTR * sizeof(CT);
   static constexpr size_t COL_BYTES = (size_t)NC * COLLEN * sizeof(CT);
-  static constexpr size_t STG_BYTES = (size_t)R * N * sizeof(T);
-  static constexpr size_t SCR_BYTES = align16(cmax(cmax(ROW_BYTES, COL_BYTES), STG_BYTES));
+  static constexpr size_t SCR_BYTES = align16(cmax(ROW_BYTES, COL_BYTES));
   static constexpr size_t OFF_SCR = align16(W_BYTES);
   static constexpr size_t OFF_TW = OFF_SCR + SCR_BYTES;
   static constexpr size_t OFF_SX = OFF_TW + align16((N / 2) * sizeof(CT));
   static constexpr size_t OFF_SY = OFF_SX + align16((N / 2 + 2) * sizeof(T));
   static constexpr size_t OFF_FRC = OFF_SY + align16(N * sizeof(T));
-  static constexpr size_t SMEM = OFF_FRC + align16(R * sizeof(T));
+  static constexpr size_t OFF_ROW0 = OFF_FRC + align16(R * sizeof(T));  // u_n.v and acc.v of row 0
+  static constexpr size_t OFF_TMEM = OFF_ROW0 + align16(2 * N * sizeof(T));
+  static constexpr size_t SMEM = OFF_TMEM + 16;
   // forward-transpose and backward-transpose register staging per thread
   static constexpr int NFWD = (NC * N + NT - 1) / NT;
-  static constexpr int NBWD = ((R + 2) * (N / 2) + NT - 1) / NT;
-  static constexpr int MIN_BLOCKS = (NT <= 512 && SMEM <= 115712) ? 2 : 1;
+  static constexpr int NBWD = (R * (N / 2) + NT - 1) / NT;
+  // one CTA per SM: the full 128-register budget (no spills) is worth more than
+  // fitting a second CTA, which measured slower on the 256^2 batch
+  static constexpr int MIN_BLOCKS = 1;
+  // TMEM: RT rows x (u_n.u, u_n.v, acc.u, acc.v) per thread; warps sharing a
+  // lane quarter take consecutive column ranges
+  static constexpr int SLOT = CellSlot<T>::COLS;
+  static constexpr int TCOLS_THREAD = RT * SLOT;
+  static constexpr int TCOLS_NEED = ((NW + 3) / 4) * TCOLS_THREAD;
+  static constexpr int TMEM_COLS = TCOLS_NEED <= 32 ? 32 : TCOLS_NEED <= 64 ? 64 : TCOLS_NEED <= 128 ? 128
+                                 : TCOLS_NEED <= 256 ? 256 : 512;
+  static_assert(TCOLS_NEED <= 512, "per-thread state exceeds tensor memory");
+  // clustered configurations must never wait for TMEM: at most two CTAs per SM
+  // fit by shared memory or registers, and two of them still fit in 512 columns
+  static_assert(CS == 1 || 2 * TMEM_COLS <= 512, "co-resident clusters must never wait for TMEM");
   static_assert(NT % N == 0, "threads must cover whole rows");
   static_assert(R % G == 0 && RT >= 1, "rows must split evenly over row groups");
+  static_assert(G >= 2, "in-place band update needs at least two row groups");
   static_assert(R >= 4 && (R % 2) == 0, "each CTA owns an even number of rows >= 4");
   static_assert(NT % 32 == 0, "whole warps");
 };
+
+// fast division for the FP32 spectral multiply (2 ulp), exact for FP64
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
 
 template <int CS>
 __device__ __forceinline__ void csync() {
@@ -169,21 +189,24 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   using Cfg = FusedCfg<T, LOGN, CS, NT>;
   using CT = typename Cfg::CT;
   using FFT = typename Cfg::FFT;
+  using Slot = CellSlot<T>;
   constexpr int N = Cfg::N, R = Cfg::R, HR = Cfg::HR, RT = Cfg::RT, NC = Cfg::NC, NW = Cfg::NW;
-  constexpr int HALF = N / 2;
+  constexpr int HALF = N / 2, HSTR = Cfg::HSTR;
   constexpr int MSK = N - 1;
   constexpr int W = FFT::W, E = FFT::E, TPW = 32 / W;
   extern __shared__ __align__(16) unsigned char smem[];
   T* const wt = reinterpret_cast<T*>(smem);  // [2][HR][N]
   unsigned char* const scr = smem + Cfg::OFF_SCR;
-  T* const stg = reinterpret_cast<T*>(scr);    // [R][N] staged u' of the stencil phase
-  CT* const hs = reinterpret_cast<CT*>(scr);   // [R+2][N/2] half spectra (rows)
+  CT* const hs = reinterpret_cast<CT*>(scr);   // [R][HSTR] half spectra (rows)
   CT* const col = reinterpret_cast<CT*>(scr);  // [NC][N+1] columns
-  T* const pr = reinterpret_cast<T*>(scr);     // [R+2][N] pressure rows
+  T* const pr = reinterpret_cast<T*>(scr);     // [R][2 HSTR] pressure rows
   CT* const tw = reinterpret_cast<CT*>(smem + Cfg::OFF_TW);
   T* const sx = reinterpret_cast<T*>(smem + Cfg::OFF_SX);
   T* const sy = reinterpret_cast<T*>(smem + Cfg::OFF_SY);
   T* const frc = reinterpret_cast<T*>(smem + Cfg::OFF_FRC);
+  T* const unrow0 = reinterpret_cast<T*>(smem + Cfg::OFF_ROW0);  // u_n.v on local row 0
+  T* const accrow0 = unrow0 + N;                                // acc.v on local row 0 (stage 2)
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::OFF_TMEM);
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -195,27 +218,27 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   const int row0 = rank * R;
   const size_t NN = (size_t)N * N;
 
+  if (warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
   for (int k = tid; k < HALF; k += NT) tw[k] = reinterpret_cast<const CT*>(a.tw)[k];
   for (int k = tid; k <= HALF; k += NT) sx[k] = reinterpret_cast<const T*>(a.symx)[k];
   for (int k = tid; k < N; k += NT) sy[k] = reinterpret_cast<const T*>(a.symy)[k];
   for (int k = tid; k < R; k += NT) frc[k] = reinterpret_cast<const T*>(a.frc)[row0 + k];
 
   const T* uin = reinterpret_cast<const T*>(a.u_in) + (size_t)traj * 2 * NN;
-  T* un = reinterpret_cast<T*>(a.u_out) + (size_t)traj * 2 * NN;
-  T* acc = reinterpret_cast<T*>(a.acc) + (size_t)traj * 2 * NN;
+  T* uout = reinterpret_cast<T*>(a.u_out) + (size_t)traj * 2 * NN;
   for (int e = tid; e < 2 * R * N; e += NT) {
     const int c = e / (R * N), rem = e % (R * N);
     const int r = rem / N, i = rem % N;
-    const size_t gidx = c * NN + (size_t)(row0 + r) * N + i;
-    const T v = uin[gidx];
-    wt[(c * HR + r + 2) * N + i] = v;
-    un[gidx] = v;
+    wt[(c * HR + r + 2) * N + i] = uin[c * NN + (size_t)(row0 + r) * N + i];
   }
+  tmem_fence_before_sync();
   __syncthreads();
+  tmem_fence_after_sync();
+  // this thread's TMEM slots: lane quarter of the warp, column range of the warp
+  const uint32_t tbase = *tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * Cfg::TCOLS_THREAD);
 
   const int ci = tid % N;
   const int grp = tid / N;
-  const int jr0 = grp * RT;
   const bool ns = a.flow == 1;
   Tendency<T, N, DORD> tend;
   tend.fu = wt;
@@ -228,6 +251,15 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   tend.forced = a.forcing == 1;
   const T dt = (T)a.dt, idx = (T)a.idx, idy = (T)a.idy, inv_nn = (T)a.inv_nn;
   const bool extra = ns && (grp == Cfg::G - 1);  // recompute v' on the next CTA's first row
+
+  // u_n of the owned cells into TMEM
+#pragma unroll
+  for (int r = 0; r < RT; ++r) {
+    const int hr = r * Cfg::G + grp + 2;
+    Slot::store(tbase + r * Cfg::SLOT, wt[hr * N + ci], wt[(HR + hr) * N + ci], (T)0, (T)0);
+  }
+  if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
+  tmem_wait_st();
 
   int snap = 0;
   for (int step = 1; step <= a.n_steps; ++step) {
@@ -251,58 +283,67 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
       __syncthreads();
 
       // ---- C: tendency and RK4 combination -------------------------------------
-      const T ca = stage == 2 ? dt : (T)0.5 * dt;
-      const T c6 = dt / (T)6;
-      T wv[RT];
+      // Rows are processed in bands of G rows (band r = rows r G .. r G + G - 1,
+      // one per row group) by all threads in lockstep. Band r reads rows
+      // r G - 2 .. r G + G + 1, so once every thread has finished band r, band
+      // r - 1 is never read again and its new values are written in place.
+      {
+        const T ca = stage == 2 ? dt : (T)0.5 * dt;
+        const T c6 = dt / (T)6;
+        T pu = (T)0, pv = (T)0, wv_extra = (T)0;
 #pragma unroll
-      for (int r = 0; r < RT; ++r) {
-        const int jj = jr0 + r, hr = jj + 2;
-        const size_t gi = (size_t)(row0 + jj) * N + ci;
-        T tu, tv;
-        tend.eval(hr, ci, frc[jj], tu, tv);
-        const T unu = un[gi], unv = un[NN + gi];
-        T au, av;
-        if (stage == 0) {
-          au = tu;
-          av = tv;
-        } else {
-          au = acc[gi];
-          av = acc[NN + gi];
-          if (stage < 3) {
+        for (int r = 0; r < RT; ++r) {
+          const int jj = r * Cfg::G + grp, hr = jj + 2;
+          const uint32_t ta = tbase + r * Cfg::SLOT;
+          T unu, unv, au, av;
+          Slot::load(ta, unu, unv, au, av);
+          T tu, tv;
+          tend.eval(hr, ci, frc[jj], tu, tv);
+          if (stage == 0) {
+            au = tu;
+            av = tv;
+          } else if (stage < 3) {
             au += (T)2 * tu;
             av += (T)2 * tv;
           } else {
             au += tu;
             av += tv;
           }
+          T nu_, nv_;
+          if (stage < 3) {
+            Slot::store(ta, unu, unv, au, av);
+            nu_ = unu + ca * tu;
+            nv_ = unv + ca * tv;
+            if (stage == 2 && jj == 0) accrow0[ci] = av;
+          } else {
+            nu_ = unu + c6 * au;
+            nv_ = unv + c6 * av;
+          }
+          if (r == RT - 1 && extra) {
+            // v' on the next CTA's first row, from rows R-2 .. R+2
+            const T* nrow = remote<CS>(unrow0, next);
+            T eu, ev;
+            tend.eval(R + 2, ci, (T)0, eu, ev);
+            const T unv0 = nrow[ci];
+            wv_extra = stage < 3 ? unv0 + ca * ev : unv0 + c6 * (nrow[N + ci] + ev);
+          }
+          __syncthreads();
+          if (r > 0) {
+            const int hp = (r - 1) * Cfg::G + grp + 2;
+            wt[hp * N + ci] = pu;
+            wt[(HR + hp) * N + ci] = pv;
+          }
+          pu = nu_;
+          pv = nv_;
         }
-        if (stage < 3) {
-          acc[gi] = au;
-          acc[NN + gi] = av;
-          stg[jj * N + ci] = unu + ca * tu;
-          wv[r] = unv + ca * tv;
-        } else {
-          stg[jj * N + ci] = unu + c6 * au;
-          wv[r] = unv + c6 * av;
-        }
+        tmem_wait_st();
+        __syncthreads();
+        const int hl = (RT - 1) * Cfg::G + grp + 2;
+        wt[hl * N + ci] = pu;
+        wt[(HR + hl) * N + ci] = pv;
+        if (extra) wt[(HR + R + 2) * N + ci] = wv_extra;
+        __syncthreads();
       }
-      T wv_extra = (T)0;
-      if (extra) {
-        const size_t gi = (size_t)((row0 + R) & MSK) * N + ci;
-        T tu, tv;
-        tend.eval(R + 2, ci, (T)0, tu, tv);
-        const T unv = un[NN + gi];
-        wv_extra = stage < 3 ? unv + ca * tv : unv + c6 * (acc[NN + gi] + tv);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < RT; ++r) {
-        const int jj = jr0 + r, hr = jj + 2;
-        wt[hr * N + ci] = stg[jj * N + ci];
-        wt[(HR + hr) * N + ci] = wv[r];
-      }
-      if (extra) wt[(HR + R + 2) * N + ci] = wv_extra;
-      __syncthreads();
 
       if (ns) {
         // ---- D1: divergence, forward row FFTs, half spectra ---------------------
@@ -343,9 +384,9 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
               const int s = (q + W * m) >> 1;
               if (act) {
                 if ((q & 1) == 0)
-                  hs[(ja + 2) * HALF + s] = A;
+                  hs[ja * HSTR + s] = A;
                 else
-                  hs[(ja + 3) * HALF + s] = Bo;
+                  hs[(ja + 1) * HSTR + s] = Bo;
               }
             }
           }
@@ -360,7 +401,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             if (e < NC * N) {
               const int sl = e % NC, ky = e / NC;
               const CT* src = remote<CS>(hs, ky / R);
-              reg[k] = src[(ky % R + 2) * HALF + rank * NC + sl];
+              reg[k] = src[(ky % R) * HSTR + rank * NC + sl];
             }
           }
           csync<CS>();
@@ -385,28 +426,39 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
 #pragma unroll
           for (int m = 0; m < E; ++m) z[m] = col[slc * Cfg::COLLEN + q + W * m];
           FFT::dif(z, q, tw);
-          {
-            // every lane takes part in the partner exchange (the packed column
-            // needs it: kx = 0 in the real part, kx = N/2 in the imaginary
-            // part, both real and even in ky)
-            CT zn[E];
+          // multiply by 1 / (N^2 L(kx, ky)). Column sg = 0 packs kx = 0 in the
+          // real part and kx = N/2 in the imaginary part (both real and even
+          // in ky): Z'[ky] = hp Z[ky] + hm conj(Z[-ky]). Registers m and
+          // partner_reg(m) hold partner elements, so pairs update in place.
+          // All lanes of the warp take part in the shuffles.
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-              const int ky = brev<LOGN>(q + W * m);
-              const int pl = FFT::partner_lane(q, m);
-              const CT zm = shfl_idx(z[FFT::partner_reg(m)], gbase + pl);
-              if (sg != 0) {
-                const T mul = inv_nn / (sx[kx] + sy[ky]);
-                zn[m] = CT{z[m].x * mul, z[m].y * mul};
-              } else {
-                const T m0 = ky == 0 ? (T)0 : inv_nn / (sx[0] + sy[ky]);
-                const T mn = inv_nn / (sx[HALF] + sy[ky]);
+          for (int m = 0; m < E; ++m) {
+            const int mp = FFT::partner_reg(m);
+            if (mp < m) continue;
+            const int ky = brev<LOGN>(q + W * m);
+            const int kyp = brev<LOGN>(q + W * mp);
+            const CT za = z[m], zb = z[mp];
+            const CT pa = shfl_idx(zb, gbase + FFT::partner_lane(q, m));   // Z[-ky]
+            const CT pb = shfl_idx(za, gbase + FFT::partner_lane(q, mp));  // Z[-kyp]
+            if (sg != 0) {
+              const T ma = sdiv(inv_nn, sx[kx] + sy[ky]);
+              const T mb = sdiv(inv_nn, sx[kx] + sy[kyp]);
+              z[m] = CT{za.x * ma, za.y * ma};
+              if (mp != m) z[mp] = CT{zb.x * mb, zb.y * mb};
+            } else {
+              {
+                const T m0 = ky == 0 ? (T)0 : sdiv(inv_nn, sx[0] + sy[ky]);
+                const T mn = sdiv(inv_nn, sx[HALF] + sy[ky]);
                 const T hp = (T)0.5 * (m0 + mn), hm = (T)0.5 * (m0 - mn);
-                zn[m] = CT{hp * z[m].x + hm * zm.x, hp * z[m].y - hm * zm.y};
+                z[m] = CT{hp * za.x + hm * pa.x, hp * za.y - hm * pa.y};
+              }
+              if (mp != m) {
+                const T m0 = kyp == 0 ? (T)0 : sdiv(inv_nn, sx[0] + sy[kyp]);
+                const T mn = sdiv(inv_nn, sx[HALF] + sy[kyp]);
+                const T hp = (T)0.5 * (m0 + mn), hm = (T)0.5 * (m0 - mn);
+                z[mp] = CT{hp * zb.x + hm * pb.x, hp * zb.y - hm * pb.y};
               }
             }
-#pragma unroll
-            for (int m = 0; m < E; ++m) z[m] = zn[m];
           }
           FFT::dit_inv(z, q, tw);
           if (act) {
@@ -415,49 +467,48 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
           }
         }
         csync<CS>();
-        // ---- D4: transpose columns -> rows [-2, R) (in place) ----------------
+        // ---- D4: transpose columns -> rows (in place) ---------------------------
         {
           CT reg[Cfg::NBWD];
 #pragma unroll
           for (int k = 0; k < Cfg::NBWD; ++k) {
             const int e = tid + k * NT;
-            if (e < (R + 2) * HALF) {
-              const int s = e % HALF, rr = e / HALF;
-              const int gy = (row0 + rr - 2 + N) & MSK;
+            if (e < R * HALF) {
+              const int rr = e % R, s = e / R;
               const CT* src = remote<CS>(col, s / NC);
-              reg[k] = src[(s % NC) * Cfg::COLLEN + gy];
+              reg[k] = src[(s % NC) * Cfg::COLLEN + row0 + rr];
             }
           }
           csync<CS>();
 #pragma unroll
           for (int k = 0; k < Cfg::NBWD; ++k) {
             const int e = tid + k * NT;
-            if (e < (R + 2) * HALF) {
-              const int s = e % HALF, rr = e / HALF;
-              hs[rr * HALF + s] = reg[k];
+            if (e < R * HALF) {
+              const int rr = e % R, s = e / R;
+              hs[rr * HSTR + s] = reg[k];
             }
           }
         }
         __syncthreads();
-        // ---- D5: inverse row FFTs -> pressure rows [-2, R) ----------------------
-        for (int t0 = warp * TPW; t0 < R / 2 + 1; t0 += NW * TPW) {
+        // ---- D5: inverse row FFTs -> pressure rows -------------------------------
+        for (int t0 = warp * TPW; t0 < R / 2; t0 += NW * TPW) {
           const int jp = t0 + lane / W;
-          const bool act = jp < R / 2 + 1;
-          const int ra = act ? 2 * jp : 0;  // padded row index of the pair's first row
+          const bool act = jp < R / 2;
+          const int ra = act ? 2 * jp : 0;
           CT z[E];
 #pragma unroll
           for (int m = 0; m < E; ++m) {
             const int p = q + W * m;
             const int k = brev<LOGN>(p);
             if (k < HALF) {
-              const CT A = hs[ra * HALF + (p >> 1)];
-              const CT B = hs[(ra + 1) * HALF + (p >> 1)];
+              const CT A = hs[ra * HSTR + (p >> 1)];
+              const CT B = hs[(ra + 1) * HSTR + (p >> 1)];
               z[m] = (k == 0) ? CT{A.x, B.x} : CT{A.x - B.y, A.y + B.x};
             } else {
               const int kp = N - k;  // in (0, N/2]
               const int sp = brev<LOGN>(kp & MSK) >> 1;
-              const CT A = hs[ra * HALF + sp];
-              const CT B = hs[(ra + 1) * HALF + sp];
+              const CT A = hs[ra * HSTR + sp];
+              const CT B = hs[(ra + 1) * HSTR + sp];
               z[m] = (kp == HALF) ? CT{A.y, B.y} : CT{A.x + B.y, B.x - A.y};
             }
           }
@@ -467,21 +518,25 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
 #pragma unroll
             for (int m = 0; m < E; ++m) {
               const int x = q + W * m;
-              pr[ra * N + x] = z[m].x;
-              pr[(ra + 1) * N + x] = z[m].y;
+              pr[ra * (2 * HSTR) + x] = z[m].x;
+              pr[(ra + 1) * (2 * HSTR) + x] = z[m].y;
             }
           }
         }
-        __syncthreads();
+        // pressure of the row below the first owned row lives in the previous CTA
+        csync<CS>();
         // ---- D6: w' -= G2 p --------------------------------------------------------
+        {
+          const T* pp = remote<CS>(pr, prev);
 #pragma unroll
-        for (int r = 0; r < RT; ++r) {
-          const int jj = jr0 + r, hr = jj + 2, rp = jj + 2;
-          const T pc = pr[rp * N + ci];
-          const T pw = pr[rp * N + ((ci - 1) & MSK)];
-          const T ps = pr[(rp - 1) * N + ci];
-          wt[hr * N + ci] -= (pc - pw) * idx;
-          wt[(HR + hr) * N + ci] -= (pc - ps) * idy;
+          for (int r = 0; r < RT; ++r) {
+            const int jj = r * Cfg::G + grp, hr = jj + 2;
+            const T pc = pr[jj * (2 * HSTR) + ci];
+            const T pw = pr[jj * (2 * HSTR) + ((ci - 1) & MSK)];
+            const T ps = jj > 0 ? pr[(jj - 1) * (2 * HSTR) + ci] : pp[(R - 1) * (2 * HSTR) + ci];
+            wt[hr * N + ci] -= (pc - pw) * idx;
+            wt[(HR + hr) * N + ci] -= (pc - ps) * idy;
+          }
         }
       }
     }
@@ -489,16 +544,16 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
     // ---- end of the time step: u_{n+1} becomes u_n -------------------------------
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
-      const int jj = jr0 + r, hr = jj + 2;
-      const size_t gi = (size_t)(row0 + jj) * N + ci;
-      un[gi] = wt[hr * N + ci];
-      un[NN + gi] = wt[(HR + hr) * N + ci];
+      const int hr = r * Cfg::G + grp + 2;
+      Slot::store(tbase + r * Cfg::SLOT, wt[hr * N + ci], wt[(HR + hr) * N + ci], (T)0, (T)0);
     }
+    if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
+    tmem_wait_st();
     if (a.save_every > 0 && a.traj != nullptr && (step % a.save_every) == 0) {
       T* out = reinterpret_cast<T*>(a.traj) + ((size_t)snap * gridDim.y + traj) * 2 * NN;
 #pragma unroll
       for (int r = 0; r < RT; ++r) {
-        const int jj = jr0 + r, hr = jj + 2;
+        const int jj = r * Cfg::G + grp, hr = jj + 2;
         const size_t gi = (size_t)(row0 + jj) * N + ci;
         out[gi] = wt[hr * N + ci];
         out[NN + gi] = wt[(HR + hr) * N + ci];
@@ -506,8 +561,20 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
       ++snap;
     }
   }
-  // keep every CTA of the cluster resident until all DSMEM reads are done
+
+#pragma unroll
+  for (int r = 0; r < RT; ++r) {
+    const int jj = r * Cfg::G + grp, hr = jj + 2;
+    const size_t gi = (size_t)(row0 + jj) * N + ci;
+    uout[gi] = wt[hr * N + ci];
+    uout[NN + gi] = wt[(HR + hr) * N + ci];
+  }
+  // keep every CTA of the cluster resident until all DSMEM reads are done,
+  // then release the tensor memory
+  tmem_fence_before_sync();
   csync<CS>();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(*tmem_slot, Cfg::TMEM_COLS);
 }
 
 }  // namespace ldfv

@@ -78,7 +78,7 @@ typedef struct {
 typedef struct {
   int32_t deriv_order;    /* 4 (paper's physics kernel, default) or 2 */
   int32_t interp_order;   /* 2 (linear interpolation); the only value accepted */
-  int32_t learned;        /* 0 = physics kernels only (default) */
+  int32_t learned;        /* 0 = physics kernels only (default), 1 = learnable module */
   int32_t k_c;            /* temporal-correction interval, 0 = off (default) */
   int32_t poisson_symbol; /* 0 = discrete D2 G2 symbol (default, exact projection) */
   int32_t ckpt_every;     /* reserved for the adjoint: checkpoint interval */
@@ -123,6 +123,45 @@ fd_status fd_check_finite(fd_ctx* ctx, const void* u, void* stream);
 
 /* Number of kernel launches issued by the last fd_step / fd_rollout call. */
 int32_t fd_last_launch_count(const fd_ctx* ctx);
+
+/* ---- learnable module (options.learned = 1) ------------------------------
+ *
+ * The flux block's per-face kernels become W_P + proj(W_L + C_theta(u)_f)
+ * (Sec. 3.4, integrated operator), where C_theta is a 6-layer conv3x3 network
+ * (2 -> 64 x5 -> 160 channels, GELU between layers, periodic padding) run on
+ * the tensor cores with BF16 weights and activations and FP32 accumulation,
+ * and proj removes the sum and the first axial and transverse moments of the
+ * learned part. With k_c > 0 the temporal correction (Sec. 3.2, Eq. for u_k;
+ * Sec. 3.5) u_k <- P(u_k + TC(u_{k-k_c} .. u_{k-1}) - mean) is applied after
+ * every k_c-th step of a rollout, with TC a network of the same shape
+ * (2 k_c -> 64 x5 -> 2). The learned path is built for FP32, N in {32, 64}.
+ *
+ * Parameter layout (float32, fd_param_count values):
+ *   W_L[kind 2][axis 2][5][4]                      (kind 0 interp, 1 deriv;
+ *                                                   axis 0 x, 1 y; derivative
+ *                                                   parts are in units of 1/h)
+ *   stencil layer l = 0..5: W[Cout][Cin][3][3], b[Cout]
+ *                   with (Cin, Cout) = (2,64) (64,64) x4 (64,160);
+ *                   output channel 20 q + 4 r + c is tap (r, c) of instance q
+ *                   (q: 0 u-x-interp, 1 u-x-deriv, 2 u-y-interp, 3 u-y-deriv,
+ *                    4 v-x-interp, 5 v-x-deriv, 6 v-y-interp, 7 v-y-deriv)
+ *   temporal correction (only when k_c > 0): layers as above with
+ *                   (Cin, Cout) = (2 k_c, 64) (64,64) x4 (64, 2); input channel
+ *                   2 s + c is component c of u_{k-k_c+s}.
+ * Network weights are rounded to BF16 (round to nearest even) on upload;
+ * biases and W_L stay FP32. */
+
+/* Number of float32 parameters fd_set_params expects (0 when not learned). */
+int64_t fd_param_count(const fd_ctx* ctx);
+
+/* Upload the learnable parameters from a HOST float32 array of `count`
+ * values (layout above). Synchronises `stream`. FD_EINVAL on a wrong count or
+ * a context without the learned option. */
+fd_status fd_set_params(fd_ctx* ctx, const float* params, int64_t count, void* stream);
+
+/* Stencil-network forward pass alone: coef_out[batch][160][ny][nx] (device,
+ * float32) = C_theta(u) for the device state u. For tests and diagnostics. */
+fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* stream);
 
 /* Release the context and its device tables (synchronises the device). */
 fd_status fd_destroy(fd_ctx* ctx);

@@ -1,0 +1,475 @@
+// conv_tc.cuh -- 3x3 periodic convolutions of the learnable module on the
+// 5th-generation tensor cores (tcgen05, BF16 in, FP32 accumulate in TMEM).
+//
+// The stencil network C_theta (6 conv3x3 layers, GELU between them) and the
+// temporal-correction network run at every RK stage; their hidden layers
+// (64 -> 64 and 64 -> 160 channels) are implicit GEMMs:
+//   out[p][co] = b[co] + sum_{dy,dx,ci} W[co][ci][dy][dx] in[p + (dy,dx)][ci].
+//
+// Activation layout in global memory ("chunk planes"): [batch][C/8][N][N][8]
+// BF16, i.e. for each group of 8 channels one N x N plane of 16-byte pixels.
+// A tile of 128 output pixels (128/N image rows) needs input rows y0-1 ..
+// y0+128/N; in shared memory each 8-channel plane of those rows is contiguous,
+// which is exactly the no-swizzle K-major operand layout of tcgen05.mma
+// (8-pixel x 16-byte core matrices, M-stride 128 B, K-stride one plane). A
+// shift by dy is a start-address offset of one image row. Shifts by dx would
+// wrap around the row ends (periodic padding), so instead the MMAs of the
+// three dx columns of the kernel accumulate into three separate TMEM
+// accumulators P_dx over the *unshifted* pixels, and the epilogue forms
+// out[x] = P_-1[x-1] + P_0[x] + P_+1[x+1] with the periodic wrap.
+//
+// Roles (12 warps): warp 0 lane 0 issues the bulk copies of the input tiles
+// (double buffered, mbarrier transaction counts), warp 1 allocates TMEM and
+// its lane 0 issues the MMAs, warps 4..11 run the epilogue (two warps per TMEM
+// lane quarter, each taking half the output channels). Accumulators are
+// double buffered so the epilogue of one tile overlaps the MMAs of the next.
+// Every mbarrier wait is bounded; on time-out the CTA records an error and
+// stops issuing work.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "fv_common.cuh"
+
+namespace ldfv {
+
+struct ConvArgs {
+  const __nv_bfloat16* in;   // [batch][CIN/8][N][N][8]
+  const __nv_bfloat16* w;    // packed: [parts][9 taps][CIN/8][COUT_TILE/8][8 co][8 ci]
+  const float* bias;         // [COUT_TOTAL]
+  __nv_bfloat16* out;        // [batch][COUT_TOTAL/8][N][N][8]
+  int batch;
+  int parts;                 // output-channel parts of COUT_TILE channels each
+  int co_base;               // first output channel of part 0
+  int cout_total;            // channel count of the output tensor
+  int gelu;                  // apply GELU in the epilogue
+  unsigned* err;             // set to nonzero on a timed-out wait
+  long long spin_limit;
+};
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; no swizzle, base offset 0
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 A and B, FP32 D, both K-major
+template <int M, int N>
+__host__ __device__ constexpr uint32_t umma_idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// bounded wait for completion of the phase with parity `par`; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(par)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8f(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  tmem_ld8(taddr, r);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+template <int LOGN, int CIN, int COUT_TILE>
+struct ConvCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int TM = 128;             // output pixels per tile
+  static constexpr int TROWS = TM / N;       // image rows per tile
+  static constexpr int IROWS = TROWS + 2;    // input rows with the dy halo
+  static constexpr int KC = CIN / 8;         // 8-channel chunks
+  static constexpr int NT = 384;
+  static constexpr uint32_t PLANE_BYTES = IROWS * N * 16;         // one chunk plane of the tile
+  static constexpr uint32_t ATILE_BYTES = KC * PLANE_BYTES;       // one input tile
+  static constexpr uint32_t TAP_BYTES = KC * (COUT_TILE / 8) * 128;
+  static constexpr uint32_t W_BYTES = 9 * TAP_BYTES;
+  static constexpr uint32_t OFF_A = 0;                            // two input tiles
+  static constexpr uint32_t OFF_W = 2 * ATILE_BYTES;
+  static constexpr uint32_t OFF_BND = OFF_W + W_BYTES;            // epilogue boundary exchange
+  static constexpr uint32_t BND_BYTES = 2 * 4 * 2 * (COUT_TILE / 2) * 4;
+  static constexpr uint32_t OFF_BAR = OFF_BND + BND_BYTES;
+  static constexpr uint32_t SMEM = OFF_BAR + 128;
+  static constexpr int ACC_COLS = 3 * COUT_TILE;                  // P_-1, P_0, P_+1
+  static constexpr int TMEM_COLS = 2 * ACC_COLS <= 256 ? 256 : 512;
+  static_assert(N >= 32 && N <= 128, "a tile covers whole image rows");
+  static_assert(CIN % 16 == 0, "K steps of 16");
+  static_assert(COUT_TILE % 32 == 0 && COUT_TILE >= 32 && COUT_TILE <= 128, "accumulator width");
+  static_assert(2 * ACC_COLS <= 512, "double-buffered accumulators fit tensor memory");
+  static_assert(SMEM <= 232448, "shared memory");
+  static_assert(PLANE_BYTES < (1u << 18), "descriptor offsets");
+};
+
+template <int LOGN, int CIN, int COUT_TILE>
+__global__ void __launch_bounds__(384, 1) conv3x3_tc_kernel(const ConvArgs a) {
+  using Cfg = ConvCfg<LOGN, CIN, COUT_TILE>;
+  constexpr int N = Cfg::N, TROWS = Cfg::TROWS, IROWS = Cfg::IROWS, KC = Cfg::KC;
+  constexpr int HALF_CO = COUT_TILE / 2;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* const sA = smem + Cfg::OFF_A;
+  unsigned char* const sW = smem + Cfg::OFF_W;
+  float* const bnd = reinterpret_cast<float*>(smem + Cfg::OFF_BND);
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(smem + Cfg::OFF_BAR);
+  uint64_t* const a_full = bars + 0;   // [2]
+  uint64_t* const a_empty = bars + 2;  // [2]
+  uint64_t* const c_full = bars + 4;   // [2]
+  uint64_t* const c_empty = bars + 6;  // [2]
+  uint64_t* const w_full = bars + 8;
+  uint32_t* const tslot = reinterpret_cast<uint32_t*>(bars + 9);
+  volatile uint32_t* const abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 10);
+  volatile uint32_t* const ep_abort = reinterpret_cast<volatile uint32_t*>(bars + 11);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_per_img = N / TROWS;
+  const int npix = a.batch * tiles_per_img;  // pixel tiles per part
+  const int ntiles = npix * a.parts;         // part-major: a CTA rarely changes part
+  const long long lim = a.spin_limit;
+
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(a_full + s, 1);
+      mbar_init(a_empty + s, 1);
+      mbar_init(c_full + s, 1);
+      mbar_init(c_empty + s, 8 * 32);
+    }
+    mbar_init(w_full, 1);
+    *abort_flag = 0;
+    *ep_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tslot, Cfg::TMEM_COLS);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ---------------- producer: weights once per part change, input tiles ----------
+    if (lane == 0) {
+      int cur_part = -1;
+      uint32_t wphase_waits = 0;
+      int i = 0;
+      int issued = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int part = t / npix;
+        const int pix = t % npix;
+        const int b = pix / tiles_per_img, y0 = (pix % tiles_per_img) * TROWS;
+        const int s = i & 1;
+        if (!mbar_wait(a_empty + s, ((i >> 1) & 1) ^ 1, lim)) {
+          *abort_flag = 1;
+          atomicOr(a.err, 1u);
+          break;
+        }
+        if (part != cur_part) {
+          // the MMAs of every earlier tile have completed (a_empty of the
+          // previous tile in this buffer and of the other buffer), so the
+          // weight area can be overwritten
+          if (i > 0 && !mbar_wait(a_empty + (s ^ 1), (((i - 1) >> 1) & 1), lim)) {
+            *abort_flag = 1;
+            atomicOr(a.err, 2u);
+            break;
+          }
+          mbar_expect_tx(w_full, Cfg::W_BYTES);
+          const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(a.w) + (size_t)part * Cfg::W_BYTES;
+          for (uint32_t off = 0; off < Cfg::W_BYTES; off += 16384) {
+            const uint32_t sz = (Cfg::W_BYTES - off) < 16384 ? (Cfg::W_BYTES - off) : 16384;
+            bulk_g2s(sW + off, wsrc + off, sz, w_full);
+          }
+          cur_part = part;
+          ++wphase_waits;
+        }
+        mbar_expect_tx(a_full + s, Cfg::ATILE_BYTES);
+        unsigned char* dst = sA + s * Cfg::ATILE_BYTES;
+        for (int c = 0; c < KC; ++c) {
+          for (int r = 0; r < IROWS; ++r) {
+            const int gy = (y0 - 1 + r + N) & (N - 1);
+            const __nv_bfloat16* src = a.in + (((size_t)b * KC + c) * N + gy) * N * 8;
+            bulk_g2s(dst + c * Cfg::PLANE_BYTES + r * N * 16, src, N * 16, a_full + s);
+          }
+        }
+        issued = i + 1;
+      }
+      // never leave with bulk copies in flight: wait (bounded) for the last
+      // tiles and the last weight load to land
+      for (int j = issued - 2; j < issued; ++j)
+        if (j >= 0) mbar_wait(a_full + (j & 1), (j >> 1) & 1, lim);
+      if (wphase_waits > 0) mbar_wait(w_full, (wphase_waits - 1) & 1, lim);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer -------------------------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc_bf16<128, COUT_TILE>();
+      int cur_part = -1;
+      uint32_t wpar = 0;
+      int i = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int part = t / npix;
+        const int s = i & 1;
+        if (*abort_flag) break;
+        if (part != cur_part) {
+          if (!mbar_wait(w_full, wpar, lim)) {
+            *abort_flag = 1;
+            atomicOr(a.err, 4u);
+            break;
+          }
+          wpar ^= 1;
+          cur_part = part;
+        }
+        if (!mbar_wait(a_full + s, (i >> 1) & 1, lim) || !mbar_wait(c_empty + s, ((i >> 1) & 1) ^ 1, lim)) {
+          *abort_flag = 1;
+          atomicOr(a.err, 8u);
+          break;
+        }
+        tmem_fence_after_sync();
+        const uint32_t abase = smem_u32(sA + s * Cfg::ATILE_BYTES);
+        const uint32_t wbase = smem_u32(sW);
+        const uint32_t dbase = tmem + (uint32_t)(s * Cfg::ACC_COLS);
+#pragma unroll 1
+        for (int dxi = 0; dxi < 3; ++dxi) {
+          bool first = true;
+#pragma unroll 1
+          for (int dyi = 0; dyi < 3; ++dyi) {
+            const int tap = dyi * 3 + dxi;  // (dy, dx) = (dyi - 1, dxi - 1)
+#pragma unroll
+            for (int kk = 0; kk < KC / 2; ++kk) {
+              const uint32_t aaddr = abase + (uint32_t)(2 * kk) * Cfg::PLANE_BYTES + (uint32_t)dyi * N * 16;
+              const uint32_t baddr = wbase + (uint32_t)tap * Cfg::TAP_BYTES + (uint32_t)(2 * kk) * (COUT_TILE / 8) * 128;
+              const uint64_t ad = umma_desc(aaddr, Cfg::PLANE_BYTES, 128);
+              const uint64_t bd = umma_desc(baddr, (COUT_TILE / 8) * 128, 128);
+              umma_bf16(dbase + (uint32_t)(dxi * COUT_TILE), ad, bd, idesc, first ? 0u : 1u);
+              first = false;
+            }
+          }
+        }
+        umma_commit(a_empty + s);
+        umma_commit(c_full + s);
+      }
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue ---------------------------------------------------------
+    const int ew = warp - 4;          // 0..7
+    const int quarter = warp & 3;     // TMEM lane quarter = pixels 32q .. 32q+31
+    const int half = ew >> 2;         // output-channel half
+    const int m = quarter * 32 + lane;
+    const int x = m & (N - 1);
+    // neighbour quarters for the periodic x wrap at the lane-0 / lane-31 edges
+    const int m0 = quarter * 32;
+    const int qleft = ((m0 & (N - 1)) == 0 ? m0 - 1 + N : m0 - 1) >> 5;
+    const int qright = (((m0 & (N - 1)) + 32) == N ? m0 + 32 - N : m0 + 32) >> 5;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int part = t / npix;
+      const int pix = t % npix;
+      const int b = pix / tiles_per_img, y0 = (pix % tiles_per_img) * TROWS;
+      const int s = i & 1;
+      if (!mbar_wait(c_full + s, (i >> 1) & 1, lim)) {
+        *ep_abort = 1;
+        atomicOr(a.err, 16u);
+      }
+      // decide together: only epilogue warps write ep_abort, before this barrier
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (*ep_abort) break;
+      tmem_fence_after_sync();
+      const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Cfg::ACC_COLS);
+      const int co0 = a.co_base + part * COUT_TILE + half * HALF_CO;
+      const int gy = y0 + m / N;
+#pragma unroll 1
+      for (int cc = 0; cc < HALF_CO; cc += 8) {
+        const int col = half * HALF_CO + cc;
+        float pm[8], p0[8], pp[8];
+        tmem_ld8f(trow + 0 * COUT_TILE + col, pm);
+        tmem_ld8f(trow + 1 * COUT_TILE + col, p0);
+        tmem_ld8f(trow + 2 * COUT_TILE + col, pp);
+        // lane-edge values go to the neighbour quarter through shared memory
+        float* mybnd = bnd + ((half * 4 + quarter) * 2) * 8;
+        if (lane == 31) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) mybnd[j] = pm[j];  // P_-1 at the last pixel
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) mybnd[8 + j] = pp[j];  // P_+1 at the first pixel
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        float outv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float left = __shfl_up_sync(0xffffffffu, pm[j], 1);
+          float right = __shfl_down_sync(0xffffffffu, pp[j], 1);
+          if (lane == 0) left = bnd[((half * 4 + qleft) * 2) * 8 + j];
+          if (lane == 31) right = bnd[((half * 4 + qright) * 2) * 8 + 8 + j];
+          float v = p0[j] + left + right + a.bias[co0 + cc + j];
+          outv[j] = a.gelu ? gelu_f(v) : v;
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        uint4 pk;
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(outv[0], outv[1]);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(outv[2], outv[3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(outv[4], outv[5]);
+        __nv_bfloat162 h3 = __floats2bfloat162_rn(outv[6], outv[7]);
+        pk.x = *reinterpret_cast<uint32_t*>(&h0);
+        pk.y = *reinterpret_cast<uint32_t*>(&h1);
+        pk.z = *reinterpret_cast<uint32_t*>(&h2);
+        pk.w = *reinterpret_cast<uint32_t*>(&h3);
+        const int chunk = (co0 + cc) >> 3;
+        __nv_bfloat16* dst = a.out + ((((size_t)b * (a.cout_total / 8) + chunk) * N + gy) * N + x) * 8;
+        *reinterpret_cast<uint4*>(dst) = pk;
+      }
+      tmem_fence_before_sync();
+      mbar_arrive(c_empty + s);
+    }
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 1) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// First layer (CIN = 2 or 2 k_c, FP32 state input) on CUDA cores:
+//   out[p][co] = GELU(b[co] + sum W[co][ci][dy][dx] in[ci][p + (dy, dx)])
+// input: state history [k][batch][2][N][N] FP32 (k = CIN / 2 snapshots);
+// output: chunk planes [batch][64/8][N][N][8] BF16.
+// ---------------------------------------------------------------------------
+struct ConvInArgs {
+  const float* const* hist;  // device array of CIN/2 pointers to [batch][2][N][N] states
+  const float* w;            // [64][CIN][3][3]
+  const float* bias;         // [64]
+  __nv_bfloat16* out;
+  int batch, cin;
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(256) conv_in_kernel(const ConvInArgs a) {
+  constexpr int N = 1 << LOGN;
+  extern __shared__ float sw_in[];  // [64][cin*9] then bias[64]
+  const int nw = 64 * a.cin * 9;
+  for (int k = threadIdx.x; k < nw; k += blockDim.x) sw_in[k] = a.w[k];
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) sw_in[nw + k] = a.bias[k];
+  __syncthreads();
+  const size_t total = (size_t)a.batch * N * N;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / (N * N));
+    const int y = (int)((p / N) % N), x = (int)(p % N);
+    float in[16][9];
+    const int cin = a.cin;
+    for (int c = 0; c < cin; ++c) {
+      const float* st = a.hist[c >> 1] + ((size_t)b * 2 + (c & 1)) * N * N;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx)
+          in[c][(dy + 1) * 3 + dx + 1] = st[((y + dy) & (N - 1)) * N + ((x + dx) & (N - 1))];
+    }
+    for (int c8 = 0; c8 < 8; ++c8) {
+      float o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int co = c8 * 8 + j;
+        float v = sw_in[nw + co];
+        const float* wr = sw_in + co * cin * 9;
+        for (int c = 0; c < cin; ++c)
+#pragma unroll
+          for (int k = 0; k < 9; ++k) v += wr[c * 9 + k] * in[c][k];
+        o[j] = gelu_f(v);
+      }
+      uint4 pk;
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(o[0], o[1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(o[2], o[3]);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(o[4], o[5]);
+      __nv_bfloat162 h3 = __floats2bfloat162_rn(o[6], o[7]);
+      pk.x = *reinterpret_cast<uint32_t*>(&h0);
+      pk.y = *reinterpret_cast<uint32_t*>(&h1);
+      pk.z = *reinterpret_cast<uint32_t*>(&h2);
+      pk.w = *reinterpret_cast<uint32_t*>(&h3);
+      *reinterpret_cast<uint4*>(a.out + ((((size_t)b * 8 + c8) * N + y) * N + x) * 8) = pk;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Last layer of the temporal-correction network (64 -> 2) on CUDA cores,
+// FP32 output [batch][2][N][N] (no activation).
+// ---------------------------------------------------------------------------
+struct ConvOut2Args {
+  const __nv_bfloat16* in;  // [batch][8][N][N][8]
+  const float* w;           // [2][64][3][3]
+  const float* bias;        // [2]
+  float* out;               // [batch][2][N][N]
+  int batch;
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(256) conv_out2_kernel(const ConvOut2Args a) {
+  constexpr int N = 1 << LOGN;
+  __shared__ float sw[2 * 64 * 9 + 2];
+  for (int k = threadIdx.x; k < 2 * 64 * 9; k += blockDim.x) sw[k] = a.w[k];
+  if (threadIdx.x < 2) sw[2 * 64 * 9 + threadIdx.x] = a.bias[threadIdx.x];
+  __syncthreads();
+  const size_t total = (size_t)a.batch * N * N;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / (N * N));
+    const int y = (int)((p / N) % N), x = (int)(p % N);
+    float o0 = sw[2 * 64 * 9], o1 = sw[2 * 64 * 9 + 1];
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int yy = (y + dy) & (N - 1), xx = (x + dx) & (N - 1);
+        const int k = (dy + 1) * 3 + dx + 1;
+        for (int c8 = 0; c8 < 8; ++c8) {
+          const uint4 pk = *reinterpret_cast<const uint4*>(a.in + ((((size_t)b * 8 + c8) * N + yy) * N + xx) * 8);
+          const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&pk);
+#pragma unroll
+          for (int j2 = 0; j2 < 4; ++j2) {
+            const float2 f = __bfloat1622float2(h[j2]);
+            const int c0 = c8 * 8 + 2 * j2;
+            o0 += sw[(0 * 64 + c0) * 9 + k] * f.x + sw[(0 * 64 + c0 + 1) * 9 + k] * f.y;
+            o1 += sw[(1 * 64 + c0) * 9 + k] * f.x + sw[(1 * 64 + c0 + 1) * 9 + k] * f.y;
+          }
+        }
+      }
+    a.out[((size_t)b * 2 + 0) * N * N + y * N + x] = o0;
+    a.out[((size_t)b * 2 + 1) * N * N + y * N + x] = o1;
+  }
+}
+
+}  // namespace ldfv

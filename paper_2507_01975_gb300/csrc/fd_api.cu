@@ -13,20 +13,24 @@
 #include <vector>
 
 #include "../../include/fd.h"
+#include "fd_ctx.h"
 #include "fv_fused.cuh"
 
 using namespace ldfv;
+
+// learned path (fd_learned.cu)
+int64_t fd_learned_param_count(int kc);
+fd_status fd_learned_init(fd_ctx* c);
+void fd_learned_free(fd_ctx* c);
+fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
+                             cudaStream_t st);
+fd_status fd_learned_error_flag(fd_ctx* c);
 
 namespace {
 
 thread_local std::string g_init_error;
 
-struct Launcher {
-  int cs = 0, nt = 0;
-  size_t smem = 0;
-  cudaError_t (*launch)(const FvArgs&, int batch, size_t smem, cudaStream_t) = nullptr;
-  cudaError_t (*prepare)(size_t smem) = nullptr;
-};
+
 
 template <typename T, int LOGN, int CS, int NT, int DORD>
 cudaError_t launch_fused(const FvArgs& a, int batch, size_t smem, cudaStream_t st) {
@@ -101,24 +105,9 @@ bool pick_launcher(int dtype, int logn, int dord, Launcher* out) {
 
 }  // namespace
 
-struct fd_ctx {
-  fd_grid grid;
-  fd_forcing forcing;
-  fd_options opts;
-  double nu = 0, dt = 0;
-  int logn = 0;
-  Launcher L;
-  bool prepared = false;
-  void* d_tables = nullptr;  // tw | symx | symy | frc
-  size_t off_symx = 0, off_symy = 0, off_frc = 0;
-  void* d_state = nullptr;   // device state for fd_rollout_host
-  unsigned* d_flag = nullptr;
-  int launches = 0;
-  std::string err;
-  FvArgs base;
-};
 
-static fd_status set_err(fd_ctx* c, fd_status s, const char* fmt, ...) {
+
+fd_status fd_set_error(fd_ctx* c, fd_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -132,7 +121,7 @@ static fd_status set_err(fd_ctx* c, fd_status s, const char* fmt, ...) {
 }
 
 static size_t elem_size(const fd_grid& g) { return g.dtype == FD_F64 ? 8 : 4; }
-static size_t state_bytes(const fd_grid& g) {
+size_t fd_state_bytes(const fd_grid& g) {
   return (size_t)g.batch * 2 * (size_t)g.nx * (size_t)g.ny * elem_size(g);
 }
 
@@ -191,40 +180,41 @@ int32_t fd_last_launch_count(const fd_ctx* ctx) { return ctx ? ctx->launches : 0
 
 fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* forcing,
                   const fd_options* opts, fd_ctx** out) {
-  if (!grid || !out) return set_err(nullptr, FD_EINVAL, "fd_init: null grid or out pointer");
+  if (!grid || !out) return fd_set_error(nullptr, FD_EINVAL, "fd_init: null grid or out pointer");
   *out = nullptr;
   const fd_grid g = *grid;
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
   if (!pow2(g.nx) || !pow2(g.ny) || g.nx < 8 || g.ny < 8 || g.nx > 2048 || g.ny > 2048)
-    return set_err(nullptr, FD_EINVAL, "fd_init: nx, ny must be powers of two in [8, 2048] (got %d x %d)",
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: nx, ny must be powers of two in [8, 2048] (got %d x %d)",
                    g.nx, g.ny);
-  if (g.batch < 1 || g.batch > 65535) return set_err(nullptr, FD_EINVAL, "fd_init: batch must be in [1, 65535]");
-  if (!(g.lx > 0) || !(g.ly > 0)) return set_err(nullptr, FD_EINVAL, "fd_init: box lengths must be positive");
-  if (g.dtype != FD_F32 && g.dtype != FD_F64) return set_err(nullptr, FD_EINVAL, "fd_init: unknown dtype");
+  if (g.batch < 1 || g.batch > 65535) return fd_set_error(nullptr, FD_EINVAL, "fd_init: batch must be in [1, 65535]");
+  if (!(g.lx > 0) || !(g.ly > 0)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: box lengths must be positive");
+  if (g.dtype != FD_F32 && g.dtype != FD_F64) return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown dtype");
   if (g.flow != FD_BURGERS && g.flow != FD_NAVIER_STOKES)
-    return set_err(nullptr, FD_EINVAL, "fd_init: unknown flow");
-  if (!(dt > 0) || !std::isfinite(dt)) return set_err(nullptr, FD_EINVAL, "fd_init: dt must be positive");
-  if (!(nu >= 0) || !std::isfinite(nu)) return set_err(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown flow");
+  if (!(dt > 0) || !std::isfinite(dt)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: dt must be positive");
+  if (!(nu >= 0) || !std::isfinite(nu)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
   fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26};
   if (opts) o = *opts;
   if (o.deriv_order != 2 && o.deriv_order != 4)
-    return set_err(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
-  if (o.interp_order != 2) return set_err(nullptr, FD_EINVAL, "fd_init: interp_order must be 2");
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
+  if (o.interp_order != 2) return fd_set_error(nullptr, FD_EINVAL, "fd_init: interp_order must be 2");
   if (o.poisson_symbol != 0 && o.poisson_symbol != 1)
-    return set_err(nullptr, FD_EINVAL, "fd_init: poisson_symbol must be 0 or 1");
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: poisson_symbol must be 0 or 1");
   fd_forcing f = {0, 1.0, 4, 0.1};
   if (forcing) f = *forcing;
-  if (f.kind != 0 && f.kind != 1) return set_err(nullptr, FD_EINVAL, "fd_init: unknown forcing kind");
-  if (g.nx != g.ny) return set_err(nullptr, FD_EUNSUPPORTED, "fd_init: only square grids are built");
-  if (o.learned || o.k_c) return set_err(nullptr, FD_EUNSUPPORTED, "fd_init: learned mode is not built");
+  if (f.kind != 0 && f.kind != 1) return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown forcing kind");
+  if (g.nx != g.ny) return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: only square grids are built");
+  if (o.learned != 0 && o.learned != 1) return fd_set_error(nullptr, FD_EINVAL, "fd_init: learned must be 0 or 1");
+  if (!o.learned && o.k_c) return fd_set_error(nullptr, FD_EINVAL, "fd_init: k_c needs the learned option");
   int logn = 0;
   while ((1 << logn) < g.nx) ++logn;
   Launcher L;
   if (!pick_launcher(g.dtype, logn, o.deriv_order, &L))
-    return set_err(nullptr, FD_EUNSUPPORTED, "fd_init: no on-chip kernel for N=%d dtype=%d", g.nx, g.dtype);
+    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: no on-chip kernel for N=%d dtype=%d", g.nx, g.dtype);
 
   fd_ctx* c = new (std::nothrow) fd_ctx();
-  if (!c) return set_err(nullptr, FD_ENOMEM, "fd_init: out of host memory");
+  if (!c) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: out of host memory");
   c->grid = g;
   c->forcing = f;
   c->opts = o;
@@ -241,14 +231,14 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   cudaError_t e = cudaMalloc(&c->d_tables, host.size());
   if (e != cudaSuccess) {
     delete c;
-    return set_err(nullptr, FD_ENOMEM, "fd_init: cudaMalloc: %s", cudaGetErrorString(e));
+    return fd_set_error(nullptr, FD_ENOMEM, "fd_init: cudaMalloc: %s", cudaGetErrorString(e));
   }
   e = cudaMemcpy(c->d_tables, host.data(), host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = L.prepare(L.smem);
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
     delete c;
-    return set_err(nullptr, FD_ECUDA, "fd_init: device set-up: %s", cudaGetErrorString(e));
+    return fd_set_error(nullptr, FD_ECUDA, "fd_init: device set-up: %s", cudaGetErrorString(e));
   }
 
   const int n = g.nx;
@@ -268,18 +258,28 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   a.symx = base + c->off_symx;
   a.symy = base + c->off_symy;
   a.frc = base + c->off_frc;
+  if (o.learned) {
+    fd_status ls = fd_learned_init(c);
+    if (ls != FD_OK) {
+      fd_learned_free(c);
+      cudaFree(c->d_tables);
+      delete c;
+      return ls;
+    }
+  }
   *out = c;
   return FD_OK;
 }
 
 fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32_t n_steps,
                      int32_t save_every, void* stream) {
-  if (!c) return set_err(nullptr, FD_EINVAL, "fd_rollout: null context");
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout: null context");
   c->launches = 0;
-  if (!u0 || !u_final) return set_err(c, FD_EINVAL, "fd_rollout: null state pointer");
-  if (n_steps < 0) return set_err(c, FD_EINVAL, "fd_rollout: n_steps must be >= 0");
-  if (save_every < 0) return set_err(c, FD_EINVAL, "fd_rollout: save_every must be >= 0");
-  if (save_every > 0 && !traj) return set_err(c, FD_EINVAL, "fd_rollout: save_every > 0 needs traj");
+  if (!u0 || !u_final) return fd_set_error(c, FD_EINVAL, "fd_rollout: null state pointer");
+  if (n_steps < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout: n_steps must be >= 0");
+  if (save_every < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every must be >= 0");
+  if (save_every > 0 && !traj) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every > 0 needs traj");
+  if (c->lrn) return fd_learned_rollout(c, u0, traj, u_final, n_steps, save_every, static_cast<cudaStream_t>(stream));
   FvArgs a = c->base;
   a.u_in = u0;
   a.u_out = u_final;
@@ -287,37 +287,37 @@ fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32
   a.n_steps = n_steps;
   a.save_every = save_every;
   cudaError_t e = c->L.launch(a, c->grid.batch, c->L.smem, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_rollout: launch failed: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout: launch failed: %s", cudaGetErrorString(e));
   c->launches = 1;
   return FD_OK;
 }
 
 fd_status fd_step(fd_ctx* c, const void* u_in, void* u_out, void* stream) {
-  if (!c) return set_err(nullptr, FD_EINVAL, "fd_step: null context");
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_step: null context");
   return fd_rollout(c, u_in, nullptr, u_out, 1, 0, stream);
 }
 
 fd_status fd_rollout_host(fd_ctx* c, const void* u0_host, void* u_final_host, int32_t n_steps,
                           void* stream) {
-  if (!c) return set_err(nullptr, FD_EINVAL, "fd_rollout_host: null context");
-  if (!u0_host || !u_final_host) return set_err(c, FD_EINVAL, "fd_rollout_host: null host pointer");
-  const size_t bytes = state_bytes(c->grid);
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout_host: null context");
+  if (!u0_host || !u_final_host) return fd_set_error(c, FD_EINVAL, "fd_rollout_host: null host pointer");
+  const size_t bytes = fd_state_bytes(c->grid);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!c->d_state) {
     cudaError_t e = cudaMalloc(&c->d_state, bytes);
     if (e != cudaSuccess) {
       c->d_state = nullptr;
-      return set_err(c, FD_ENOMEM, "fd_rollout_host: cudaMalloc: %s", cudaGetErrorString(e));
+      return fd_set_error(c, FD_ENOMEM, "fd_rollout_host: cudaMalloc: %s", cudaGetErrorString(e));
     }
   }
   cudaError_t e = cudaMemcpyAsync(c->d_state, u0_host, bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_rollout_host: H2D copy: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout_host: H2D copy: %s", cudaGetErrorString(e));
   fd_status s = fd_rollout(c, c->d_state, nullptr, c->d_state, n_steps, 0, stream);
   if (s != FD_OK) return s;
   e = cudaMemcpyAsync(u_final_host, c->d_state, bytes, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_rollout_host: D2H copy: %s", cudaGetErrorString(e));
-  return FD_OK;
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout_host: D2H copy: %s", cudaGetErrorString(e));
+  return fd_learned_error_flag(c);
 }
 
 }  // extern "C"
@@ -336,19 +336,19 @@ __global__ void finite_scan_kernel(const T* u, size_t n, unsigned* flag) {
 extern "C" {
 
 fd_status fd_check_finite(fd_ctx* c, const void* u, void* stream) {
-  if (!c) return set_err(nullptr, FD_EINVAL, "fd_check_finite: null context");
-  if (!u) return set_err(c, FD_EINVAL, "fd_check_finite: null state pointer");
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_check_finite: null context");
+  if (!u) return fd_set_error(c, FD_EINVAL, "fd_check_finite: null state pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (!c->d_flag) {
     e = cudaMalloc(&c->d_flag, sizeof(unsigned));
     if (e != cudaSuccess) {
       c->d_flag = nullptr;
-      return set_err(c, FD_ENOMEM, "fd_check_finite: cudaMalloc: %s", cudaGetErrorString(e));
+      return fd_set_error(c, FD_ENOMEM, "fd_check_finite: cudaMalloc: %s", cudaGetErrorString(e));
     }
   }
   e = cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), st);
-  const size_t n = state_bytes(c->grid) / elem_size(c->grid);
+  const size_t n = fd_state_bytes(c->grid) / elem_size(c->grid);
   if (e == cudaSuccess) {
     if (c->grid.dtype == FD_F64)
       finite_scan_kernel<double><<<152, 256, 0, st>>>(static_cast<const double*>(u), n, c->d_flag);
@@ -359,8 +359,9 @@ fd_status fd_check_finite(fd_ctx* c, const void* u, void* stream) {
   unsigned h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->d_flag, sizeof h, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return set_err(c, FD_ECUDA, "fd_check_finite: %s", cudaGetErrorString(e));
-  return h ? set_err(c, FD_ENONFINITE, "fd_check_finite: state holds NaN or Inf") : FD_OK;
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_check_finite: %s", cudaGetErrorString(e));
+  if (h) return fd_set_error(c, FD_ENONFINITE, "fd_check_finite: state holds NaN or Inf");
+  return fd_learned_error_flag(c);
 }
 
 fd_status fd_destroy(fd_ctx* c) {
@@ -369,6 +370,7 @@ fd_status fd_destroy(fd_ctx* c) {
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_state) cudaFree(c->d_state);
   if (c->d_flag) cudaFree(c->d_flag);
+  fd_learned_free(c);
   delete c;
   return FD_OK;
 }

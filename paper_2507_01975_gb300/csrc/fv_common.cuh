@@ -48,6 +48,9 @@ __device__ __forceinline__ CT cmulc(CT a, CT b) {
   return CT{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
+__host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
 template <int L>
 __device__ __forceinline__ int brev(int k) {
   if constexpr (L == 0) {

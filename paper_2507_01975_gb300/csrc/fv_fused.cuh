@@ -50,9 +50,6 @@ struct FvArgs {
   const void* frc;   // [N] amp sin(kf y_j) at the u-face rows
 };
 
-constexpr size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
-constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-
 template <typename T, int LOGN, int CS, int NT>
 struct FusedCfg {
   static constexpr int N = 1 << LOGN;
@@ -194,7 +191,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   constexpr int HALF = N / 2, HSTR = Cfg::HSTR;
   constexpr int MSK = N - 1;
   constexpr int W = FFT::W, E = FFT::E, TPW = 32 / W;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   T* const wt = reinterpret_cast<T*>(smem);  // [2][HR][N]
   unsigned char* const scr = smem + Cfg::OFF_SCR;
   CT* const hs = reinterpret_cast<CT*>(scr);   // [R][HSTR] half spectra (rows)

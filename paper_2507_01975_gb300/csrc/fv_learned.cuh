@@ -1,0 +1,455 @@
+// fv_learned.cuh -- one RK stage of the learned FV step, and the corrected
+// projection of the temporal-correction step (one CTA per trajectory, N <= 64).
+//
+// Flux block with learned per-face kernels (Sec. 3.4, integrated operator):
+// for each of the eight operator instances q (u/v x x/y x interp/deriv) the
+// kernel at output location f is
+//   K_q,f = W_P,q + proj(W_L[kind, axis] + C_theta(w)_q,f) / h^(kind==deriv),
+// where C_theta(w) is the stencil network's 160-channel output (channel
+// 20 q + 5 x 4 tap index, BF16 chunk planes) and proj removes the sum, the
+// first axial moment and the first transverse moment of the learned part
+// (consistency: W_P + proj(L) still interpolates / differentiates linear data
+// exactly). The instance value is sum_rc K[r][c] f[tap(r, c)] on the 5 x 4 tap
+// grid (transverse offset r - 2, axial offset c - 3/2 cells).
+//
+// Then the flux assembly (App. B.2), the RK4 stage combination with u_n and
+// the accumulator in global memory, and (Navier-Stokes) the spectral pressure
+// projection (Sec. 3.6, App. B.3-B.4) with warp FFTs, in shared memory.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "fv_common.cuh"
+
+namespace ldfv {
+
+struct LStageArgs {
+  const float* w;    // stage state [batch][2][N][N]
+  const float* un;   // state at the start of the step
+  float* acc;        // RK4 accumulator [batch][2][N][N]
+  float* wout;       // projected next stage state (or the step result)
+  const __nv_bfloat16* coef;  // [batch][20][N][N][8] network output, or null (C = 0)
+  const float* wl;   // W_L [kind 2][axis 2][5][4]
+  const float* corr; // correct_project only: correction [batch][2][N][N]
+  int stage;
+  int flow;          // 0 Burgers, 1 Navier-Stokes
+  int forcing;
+  int dord;          // physics derivative order 2 or 4
+  float dt, nu, idx, idy, drag, inv_nn;
+  const float2* tw;  // [N/2]
+  const float* symx; // [N/2 + 1]
+  const float* symy; // [N]
+  const float* frc;  // [N]
+};
+
+// instance table: field, axis (0 x, 1 y), kind (0 interp, 1 deriv), shift
+__device__ __constant__ int kInstField[8] = {0, 0, 0, 0, 1, 1, 1, 1};
+__device__ __constant__ int kInstAxis[8] = {0, 0, 1, 1, 0, 0, 1, 1};
+__device__ __constant__ int kInstKind[8] = {0, 1, 0, 1, 0, 1, 0, 1};
+__device__ __constant__ int kInstShift[8] = {-1, -1, -2, -2, -2, -2, -1, -1};
+
+template <int LOGN>
+struct LearnedCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int NT = N >= 64 ? 512 : (N >= 32 ? 256 : 128);
+  static constexpr int HSTR = N / 2 + 1;
+  static constexpr int COLLEN = N + 1;
+  static constexpr size_t W_BYTES = (size_t)2 * N * N * 4;
+  static constexpr size_t I_BYTES = (size_t)8 * N * N * 4;
+  static constexpr size_t SCR_BYTES = align16(cmax((size_t)N * HSTR * 8, (size_t)(N / 2) * COLLEN * 8));
+  static constexpr size_t OFF_I = W_BYTES;
+  static constexpr size_t OFF_SCR = OFF_I + I_BYTES;
+  static constexpr size_t OFF_TW = OFF_SCR + SCR_BYTES;
+  static constexpr size_t OFF_SX = OFF_TW + (N / 2) * 8;
+  static constexpr size_t OFF_SY = OFF_SX + align16((N / 2 + 2) * 4);
+  static constexpr size_t OFF_FRC = OFF_SY + N * 4;
+  static constexpr size_t SMEM = OFF_FRC + N * 4;
+  static constexpr size_t SMEM_PROJ = OFF_FRC;  // correct_project needs no instance arrays (unused region)
+};
+
+// Spectral projection of a trajectory tile wt[2][N][N] in shared memory
+// (CS = 1): w -= G2 L^{-1} D2 w with the symbol of D2 G2, zero mode removed.
+template <int LOGN, int NT>
+__device__ void project_tile(float* wt, unsigned char* scr, const float2* tw, const float* sx, const float* sy,
+                             float idx, float idy, float inv_nn) {
+  using CT = float2;
+  using FFT = WarpFFT<float, LOGN>;
+  constexpr int N = 1 << LOGN, HALF = N / 2, HSTR = HALF + 1, COLLEN = N + 1, MSK = N - 1;
+  constexpr int W = FFT::W, E = FFT::E, TPW = 32 / W, NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q = lane & (W - 1), gbase = lane & ~(W - 1);
+  CT* const hs = reinterpret_cast<CT*>(scr);
+  CT* const col = reinterpret_cast<CT*>(scr);
+  float* const pr = reinterpret_cast<float*>(scr);
+  const float* fu = wt;
+  const float* fv = wt + N * N;
+  // divergence -> forward row FFTs -> half spectra
+  for (int t0 = warp * TPW; t0 < N / 2; t0 += NW * TPW) {
+    const int jp = t0 + lane / W;
+    const bool act = jp < N / 2;
+    const int ja = act ? 2 * jp : 0;
+    CT z[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int x = q + W * m;
+      const int jb = ja + 1, jc = (ja + 2) & MSK;
+      const float da = (fu[ja * N + ((x + 1) & MSK)] - fu[ja * N + x]) * idx + (fv[jb * N + x] - fv[ja * N + x]) * idy;
+      const float db = (fu[jb * N + ((x + 1) & MSK)] - fu[jb * N + x]) * idx + (fv[jc * N + x] - fv[jb * N + x]) * idy;
+      z[m] = CT{da, db};
+    }
+    FFT::dif(z, q, tw);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = brev<LOGN>(q + W * m);
+      const int pl = (k == 0) ? 1 : FFT::partner_lane(q, m);
+      const CT zm = shfl_idx(z[FFT::partner_reg(m)], gbase + pl);
+      const CT zk = z[m];
+      CT A, B;
+      if (k == 0) {
+        A = CT{zk.x, zm.x};
+        B = CT{zk.y, zm.y};
+      } else {
+        A = CT{0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y)};
+        B = CT{0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x)};
+      }
+      const CT Bo = shfl_up1(B);
+      const int s = (q + W * m) >> 1;
+      if (act) {
+        if ((q & 1) == 0)
+          hs[ja * HSTR + s] = A;
+        else
+          hs[(ja + 1) * HSTR + s] = Bo;
+      }
+    }
+  }
+  __syncthreads();
+  // transpose rows -> columns in place (through registers)
+  {
+    constexpr int NR = (HALF * N + NT - 1) / NT;
+    CT reg[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int e = tid + k * NT;
+      if (e < HALF * N) reg[k] = hs[(e / HALF) * HSTR + (e % HALF)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int e = tid + k * NT;
+      if (e < HALF * N) col[(e % HALF) * COLLEN + e / HALF] = reg[k];
+    }
+  }
+  __syncthreads();
+  // column FFTs, spectral multiply, inverse column FFTs
+  for (int t0 = warp * TPW; t0 < HALF; t0 += NW * TPW) {
+    const int sl = t0 + lane / W;
+    const bool act = sl < HALF;
+    const int sg = act ? sl : 0;
+    const int kx = brev<LOGN - 1>(sg);
+    CT z[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) z[m] = col[sg * COLLEN + q + W * m];
+    FFT::dif(z, q, tw);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int mp = FFT::partner_reg(m);
+      if (mp < m) continue;
+      const int ky = brev<LOGN>(q + W * m);
+      const int kyp = brev<LOGN>(q + W * mp);
+      const CT za = z[m], zb = z[mp];
+      const CT pa = shfl_idx(zb, gbase + FFT::partner_lane(q, m));
+      const CT pb = shfl_idx(za, gbase + FFT::partner_lane(q, mp));
+      if (sg != 0) {
+        const float ma = __fdividef(inv_nn, sx[kx] + sy[ky]);
+        const float mb = __fdividef(inv_nn, sx[kx] + sy[kyp]);
+        z[m] = CT{za.x * ma, za.y * ma};
+        if (mp != m) z[mp] = CT{zb.x * mb, zb.y * mb};
+      } else {
+        {
+          const float m0 = ky == 0 ? 0.f : __fdividef(inv_nn, sx[0] + sy[ky]);
+          const float mn = __fdividef(inv_nn, sx[HALF] + sy[ky]);
+          const float hp = 0.5f * (m0 + mn), hm = 0.5f * (m0 - mn);
+          z[m] = CT{hp * za.x + hm * pa.x, hp * za.y - hm * pa.y};
+        }
+        if (mp != m) {
+          const float m0 = kyp == 0 ? 0.f : __fdividef(inv_nn, sx[0] + sy[kyp]);
+          const float mn = __fdividef(inv_nn, sx[HALF] + sy[kyp]);
+          const float hp = 0.5f * (m0 + mn), hm = 0.5f * (m0 - mn);
+          z[mp] = CT{hp * zb.x + hm * pb.x, hp * zb.y - hm * pb.y};
+        }
+      }
+    }
+    FFT::dit_inv(z, q, tw);
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) col[sg * COLLEN + q + W * m] = z[m];
+    }
+  }
+  __syncthreads();
+  // transpose back
+  {
+    constexpr int NR = (HALF * N + NT - 1) / NT;
+    CT reg[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int e = tid + k * NT;
+      if (e < HALF * N) reg[k] = col[(e / N) * COLLEN + (e % N)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int e = tid + k * NT;
+      if (e < HALF * N) hs[(e % N) * HSTR + e / N] = reg[k];
+    }
+  }
+  __syncthreads();
+  // inverse row FFTs -> pressure rows (same bytes as the half-spectrum rows)
+  for (int t0 = warp * TPW; t0 < N / 2; t0 += NW * TPW) {
+    const int jp = t0 + lane / W;
+    const bool act = jp < N / 2;
+    const int ra = act ? 2 * jp : 0;
+    CT z[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int p = q + W * m;
+      const int k = brev<LOGN>(p);
+      if (k < HALF) {
+        const CT A = hs[ra * HSTR + (p >> 1)];
+        const CT B = hs[(ra + 1) * HSTR + (p >> 1)];
+        z[m] = (k == 0) ? CT{A.x, B.x} : CT{A.x - B.y, A.y + B.x};
+      } else {
+        const int kp = N - k;
+        const int sp = brev<LOGN>(kp & MSK) >> 1;
+        const CT A = hs[ra * HSTR + sp];
+        const CT B = hs[(ra + 1) * HSTR + sp];
+        z[m] = (kp == HALF) ? CT{A.y, B.y} : CT{A.x + B.y, B.x - A.y};
+      }
+    }
+    FFT::dit_inv(z, q, tw);
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int x = q + W * m;
+        pr[ra * (2 * HSTR) + x] = z[m].x;
+        pr[(ra + 1) * (2 * HSTR) + x] = z[m].y;
+      }
+    }
+  }
+  __syncthreads();
+  // w -= G2 p
+  for (int c = tid; c < N * N; c += NT) {
+    const int j = c / N, i = c % N;
+    const float pc = pr[j * (2 * HSTR) + i];
+    const float pw = pr[j * (2 * HSTR) + ((i - 1) & MSK)];
+    const float ps = pr[((j - 1) & MSK) * (2 * HSTR) + i];
+    wt[c] -= (pc - pw) * idx;
+    wt[N * N + c] -= (pc - ps) * idy;
+  }
+  __syncthreads();
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kernel(const LStageArgs a) {
+  using Cfg = LearnedCfg<LOGN>;
+  constexpr int N = Cfg::N, NT = Cfg::NT, MSK = N - 1;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* const wt = reinterpret_cast<float*>(smem);
+  float* const inst = reinterpret_cast<float*>(smem + Cfg::OFF_I);
+  unsigned char* const scr = smem + Cfg::OFF_SCR;
+  float2* const tw = reinterpret_cast<float2*>(smem + Cfg::OFF_TW);
+  float* const sx = reinterpret_cast<float*>(smem + Cfg::OFF_SX);
+  float* const sy = reinterpret_cast<float*>(smem + Cfg::OFF_SY);
+  float* const frc = reinterpret_cast<float*>(smem + Cfg::OFF_FRC);
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x;
+  const size_t NN = (size_t)N * N;
+  const float* w = a.w + (size_t)b * 2 * NN;
+  const float* un = a.un + (size_t)b * 2 * NN;
+  float* acc = a.acc + (size_t)b * 2 * NN;
+  float* wout = a.wout + (size_t)b * 2 * NN;
+
+  for (int k = tid; k < N / 2; k += NT) tw[k] = a.tw[k];
+  for (int k = tid; k <= N / 2; k += NT) sx[k] = a.symx[k];
+  for (int k = tid; k < N; k += NT) {
+    sy[k] = a.symy[k];
+    frc[k] = a.frc[k];
+  }
+  for (int c = tid; c < 2 * N * N; c += NT) wt[c] = w[c];
+  __syncthreads();
+
+  // ---- flux block: the eight instance values at every index -------------------
+  const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
+  for (int c = tid; c < N * N; c += NT) {
+    const int j = c / N, i = c % N;
+#pragma unroll 1
+    for (int qi = 0; qi < 8; ++qi) {
+      const int fld = kInstField[qi], axis = kInstAxis[qi], kind = kInstKind[qi], sh = kInstShift[qi];
+      const float* f = wt + fld * NN;
+      float L[20];
+#pragma unroll
+      for (int t = 0; t < 20; ++t) L[t] = a.wl[(kind * 2 + axis) * 20 + t];
+      if (a.coef) {
+        // channels 20 qi .. 20 qi + 19 of this cell
+#pragma unroll
+        for (int t = 0; t < 20; ++t) {
+          const int ch = 20 * qi + t;
+          const __nv_bfloat16 v = a.coef[((((size_t)b * 20 + (ch >> 3)) * N + j) * N + i) * 8 + (ch & 7)];
+          L[t] += __bfloat162float(v);
+        }
+      }
+      // consistency projection: remove sum, axial and transverse first moments
+      float s1 = 0.f, sc = 0.f, sr = 0.f;
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const float v = L[r * 4 + cc];
+          s1 += v;
+          sc += v * cval[cc];
+          sr += v * (float)(r - 2);
+        }
+      s1 *= (1.0f / 20.0f);
+      sc *= (1.0f / 25.0f);
+      sr *= (1.0f / 40.0f);
+      const float h = axis == 0 ? 1.0f / a.idx : 1.0f / a.idy;
+      const float scale = kind == 1 ? 1.0f / h : 1.0f;
+      float val = 0.f;
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
+          if (r == 2) {
+            // physics kernel W_P on the centre row
+            if (kind == 0) {
+              k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
+            } else if (a.dord == 4) {
+              const float d4[4] = {1.f / 24.f, -27.f / 24.f, 27.f / 24.f, -1.f / 24.f};
+              k += d4[cc] / h;
+            } else {
+              const float d2[4] = {0.f, -1.f, 1.f, 0.f};
+              k += d2[cc] / h;
+            }
+          }
+          int jj, ii;
+          if (axis == 0) {
+            jj = (j + r - 2) & MSK;
+            ii = (i + cc + sh) & MSK;
+          } else {
+            jj = (j + cc + sh) & MSK;
+            ii = (i + r - 2) & MSK;
+          }
+          val += k * f[jj * N + ii];
+        }
+      inst[qi * NN + c] = val;
+    }
+  }
+  __syncthreads();
+
+  // ---- flux assembly, RK4 combination ----------------------------------------------
+  const float* Uc = inst + 0 * NN;
+  const float* Gxc = inst + 1 * NN;
+  const float* Uk = inst + 2 * NN;
+  const float* Gyu = inst + 3 * NN;
+  const float* Vk = inst + 4 * NN;
+  const float* Gxv = inst + 5 * NN;
+  const float* Vc = inst + 6 * NN;
+  const float* Gyc = inst + 7 * NN;
+  const int stage = a.stage;
+  const float ca = stage == 2 ? a.dt : 0.5f * a.dt;
+  const float c6 = a.dt / 6.0f;
+  for (int c = tid; c < N * N; c += NT) {
+    const int j = c / N, i = c % N;
+    const int iw = (i - 1) & MSK, ie = (i + 1) & MSK, js = (j - 1) & MSK, jn = (j + 1) & MSK;
+    const int cw = j * N + iw, ce = j * N + ie, cs = js * N + i, cn = jn * N + i;
+    float tu = -(Uc[c] * Uc[c] - Uc[cw] * Uc[cw]) * a.idx - (Uk[cn] * Vk[cn] - Uk[c] * Vk[c]) * a.idy +
+               a.nu * ((Gxc[c] - Gxc[cw]) * a.idx + (Gyu[cn] - Gyu[c]) * a.idy);
+    float tv = -(Uk[ce] * Vk[ce] - Uk[c] * Vk[c]) * a.idx - (Vc[c] * Vc[c] - Vc[cs] * Vc[cs]) * a.idy +
+               a.nu * ((Gxv[ce] - Gxv[c]) * a.idx + (Gyc[c] - Gyc[cs]) * a.idy);
+    const float uc = wt[c], vc = wt[NN + c];
+    if (a.flow == 0) {
+      const float d0 = Gxc[c] + Gyc[c];
+      tu += uc * 0.5f * ((Gxc[cw] + Gyc[cw]) + d0);
+      tv += vc * 0.5f * ((Gxc[cs] + Gyc[cs]) + d0);
+    }
+    if (a.forcing == 1) {
+      tu += frc[j] - a.drag * uc;
+      tv += -a.drag * vc;
+    }
+    float au, av;
+    if (stage == 0) {
+      au = tu;
+      av = tv;
+    } else {
+      au = acc[c] + (stage < 3 ? 2.0f : 1.0f) * tu;
+      av = acc[NN + c] + (stage < 3 ? 2.0f : 1.0f) * tv;
+    }
+    if (stage < 3) {
+      acc[c] = au;
+      acc[NN + c] = av;
+      wt[c] = un[c] + ca * tu;
+      wt[NN + c] = un[NN + c] + ca * tv;
+    } else {
+      wt[c] = un[c] + c6 * au;
+      wt[NN + c] = un[NN + c] + c6 * av;
+    }
+  }
+  __syncthreads();
+  if (a.flow == 1) project_tile<LOGN, NT>(wt, scr, tw, sx, sy, a.idx, a.idy, a.inv_nn);
+  for (int c = tid; c < 2 * N * N; c += NT) wout[c] = wt[c];
+}
+
+// Temporal correction (Sec. 3.2, Sec. 3.5): u <- P(u + c - mean(c)) for each
+// trajectory, with the correction c from the temporal-correction network.
+template <int LOGN>
+__global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_correct_project_kernel(const LStageArgs a) {
+  using Cfg = LearnedCfg<LOGN>;
+  constexpr int N = Cfg::N, NT = Cfg::NT;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* const wt = reinterpret_cast<float*>(smem);
+  unsigned char* const scr = smem + Cfg::OFF_SCR;  // the instance-array region is not used
+  float2* const tw = reinterpret_cast<float2*>(smem + Cfg::OFF_TW);
+  float* const sx = reinterpret_cast<float*>(smem + Cfg::OFF_SX);
+  float* const sy = reinterpret_cast<float*>(smem + Cfg::OFF_SY);
+  __shared__ float red[2][32];
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x;
+  const size_t NN = (size_t)N * N;
+  const float* corr = a.corr + (size_t)b * 2 * NN;
+  float* u = a.wout + (size_t)b * 2 * NN;
+  for (int k = tid; k < N / 2; k += NT) tw[k] = a.tw[k];
+  for (int k = tid; k <= N / 2; k += NT) sx[k] = a.symx[k];
+  for (int k = tid; k < N; k += NT) sy[k] = a.symy[k];
+  // per-component mean of the correction
+  float s0 = 0.f, s1 = 0.f;
+  for (int c = tid; c < N * N; c += NT) {
+    s0 += corr[c];
+    s1 += corr[NN + c];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = s0;
+    red[1][tid >> 5] = s1;
+  }
+  __syncthreads();
+  float m0 = 0.f, m1 = 0.f;
+  for (int k = 0; k < NT / 32; ++k) {
+    m0 += red[0][k];
+    m1 += red[1][k];
+  }
+  m0 /= (float)NN;
+  m1 /= (float)NN;
+  for (int c = tid; c < N * N; c += NT) {
+    wt[c] = u[c] + (corr[c] - m0);
+    wt[NN + c] = u[NN + c] + (corr[NN + c] - m1);
+  }
+  __syncthreads();
+  if (a.flow == 1) project_tile<LOGN, NT>(wt, scr, tw, sx, sy, a.idx, a.idy, a.inv_nn);
+  for (int c = tid; c < 2 * N * N; c += NT) u[c] = wt[c];
+}
+
+}  // namespace ldfv

@@ -29,6 +29,9 @@ EXPORTS = [
     "fd_check_finite",
     "fd_check_finite_noalloc",
     "fd_last_launch_count",
+    "fd_param_count",
+    "fd_set_params",
+    "fd_network_forward",
     "fd_destroy",
     "fd_last_error",
     "fd_version",
@@ -94,6 +97,14 @@ def load(path: str = LIB_PATH):
     lib.fd_check_finite.restype = C.c_int
     lib.fd_last_launch_count.argtypes = [vp]
     lib.fd_last_launch_count.restype = i32
+    lib.fd_param_count.argtypes = [vp]
+    lib.fd_param_count.restype = C.c_int64
+    lib.fd_set_params.argtypes = [vp, vp, C.c_int64, vp]
+    lib.fd_set_params.restype = C.c_int
+    lib.fd_network_forward.argtypes = [vp, vp, vp, vp]
+    lib.fd_network_forward.restype = C.c_int
+    lib.fd_check_finite_noalloc.argtypes = [vp, C.c_int64, i32, C.POINTER(C.c_int64), vp]
+    lib.fd_check_finite_noalloc.restype = C.c_int
     lib.fd_destroy.argtypes = [vp]
     lib.fd_destroy.restype = C.c_int
     lib.fd_last_error.argtypes = [vp]
@@ -122,6 +133,8 @@ class Config:
     drag: float = 0.1
     deriv_order: int = 4
     poisson_symbol: int = 0
+    learned: bool = False
+    k_c: int = 0
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -147,7 +160,7 @@ class Solver:
         g = FdGrid(cfg.n, cfg.n, cfg.lx, cfg.ly, cfg.batch, FD_F64 if cfg.dtype == "f64" else FD_F32,
                    FD_BURGERS if cfg.flow == "burgers" else FD_NAVIER_STOKES)
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
-        o = FdOptions(cfg.deriv_order, 2, 0, 0, cfg.poisson_symbol, 8, 1 << 26)
+        o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26)
         h = C.c_void_p()
         st = self.lib.fd_init(C.byref(g), cfg.nu, cfg.dt, C.byref(f), C.byref(o), C.byref(h))
         if st != FD_OK:
@@ -188,6 +201,19 @@ class Solver:
             return False
         self._check(st)
         return True
+
+    def param_count(self) -> int:
+        return int(self.lib.fd_param_count(self.h))
+
+    def set_params(self, params, stream=None):
+        """Upload the learnable parameters (host float32 array, layout of include/fd.h)."""
+        import numpy as np
+
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        self._check(self.lib.fd_set_params(self.h, p.ctypes.data, int(p.size), _stream_handle(stream)))
+
+    def network_forward(self, u, coef_out, stream=None):
+        self._check(self.lib.fd_network_forward(self.h, _ptr(u), _ptr(coef_out), _stream_handle(stream)))
 
     def last_launch_count(self) -> int:
         return int(self.lib.fd_last_launch_count(self.h))

@@ -165,3 +165,15 @@ def random_wl(seed: int, std: float = 1e-3) -> np.ndarray:
     """Learnable-conv kernels W_L[kind, axis, 5, 4] ~ N(0, std), float32-representable."""
     rng = np.random.default_rng(seed)
     return np.asarray(rng.standard_normal((2, 2, 5, 4)) * std, dtype=np.float32).astype(np.float64)
+
+
+def pack_params(W_L: np.ndarray, stencil, tc=None) -> np.ndarray:
+    """Flat float32 parameter array in the layout fd_set_params documents:
+    W_L[2][2][5][4], then every stencil layer's W[Cout][Cin][3][3] and b[Cout],
+    then (optionally) every temporal-correction layer's weights and biases."""
+    parts = [np.asarray(W_L, dtype=np.float64).ravel()]
+    for W, b in stencil:
+        parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
+    for W, b in (tc or []):
+        parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
+    return np.concatenate(parts).astype(np.float32)

@@ -18,10 +18,10 @@
 // accumulators P_dx over the *unshifted* pixels, and the epilogue forms
 // out[x] = P_-1[x-1] + P_0[x] + P_+1[x+1] with the periodic wrap.
 //
-// Roles (12 warps): warp 0 lane 0 issues the bulk copies of the input tiles
+// Roles (20 warps): warp 0 lane 0 issues the bulk copies of the input tiles
 // (double buffered, mbarrier transaction counts), warp 1 allocates TMEM and
-// its lane 0 issues the MMAs, warps 4..11 run the epilogue (two warps per TMEM
-// lane quarter, each taking half the output channels). Accumulators are
+// its lane 0 issues the MMAs, warps 4..19 run the epilogue (four warps per
+// TMEM lane quarter, each taking a quarter of the output channels). Accumulators are
 // double buffered so the epilogue of one tile overlaps the MMAs of the next.
 // Every mbarrier wait is bounded; on time-out the CTA records an error and
 // stops issuing work.
@@ -110,7 +110,47 @@ __device__ __forceinline__ void tmem_ld8f(uint32_t taddr, float (&v)[8]) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// 16 or 32 consecutive FP32 columns of this thread's TMEM lane; the caller
+// issues tmem_wait_ld() before using the values
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float (&v)[16]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+template <int NC>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[NC]) {
+  static_assert(NC % 8 == 0, "8-column loads");
+  if constexpr (NC % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < NC / 16; ++k) tmem_ld16_nowait(taddr + 16 * k, *reinterpret_cast<float(*)[16]>(v + 16 * k));
+  } else {
+#pragma unroll
+    for (int k = 0; k < NC / 8; ++k) tmem_ld8_nowait(taddr + 8 * k, v + 8 * k);
+  }
+}
+
+// GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)) with erf from the rational
+// approximation 7.1.26 of Abramowitz & Stegun (|error| <= 1.5e-7, far below
+// the BF16 rounding of the activations).
+__device__ __forceinline__ float gelu_f(float x) {
+  const float z = fabsf(x) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, 1.0f + 0.3275911f * z);
+  const float poly = t * (0.254829592f + t * (-0.284496736f + t * (1.421413741f + t * (-1.453152027f + t * 1.061405429f))));
+  const float erf_abs = 1.0f - poly * __expf(-z * z);
+  const float erf_x = x < 0.0f ? -erf_abs : erf_abs;
+  return 0.5f * x * (1.0f + erf_x);
+}
 
 template <int LOGN, int CIN, int COUT_TILE>
 struct ConvCfg {
@@ -119,7 +159,9 @@ struct ConvCfg {
   static constexpr int TROWS = TM / N;       // image rows per tile
   static constexpr int IROWS = TROWS + 2;    // input rows with the dy halo
   static constexpr int KC = CIN / 8;         // 8-channel chunks
-  static constexpr int NT = 384;
+  static constexpr int NT = 640;
+  static constexpr int NEPI = 16;           // epilogue warps
+  static constexpr int CG = COUT_TILE / 4;  // output channels per epilogue warp
   static constexpr uint32_t PLANE_BYTES = IROWS * N * 16;         // one chunk plane of the tile
   static constexpr uint32_t ATILE_BYTES = KC * PLANE_BYTES;       // one input tile
   static constexpr uint32_t TAP_BYTES = KC * (COUT_TILE / 8) * 128;
@@ -127,8 +169,9 @@ struct ConvCfg {
   static constexpr uint32_t OFF_A = 0;                            // two input tiles
   static constexpr uint32_t OFF_W = 2 * ATILE_BYTES;
   static constexpr uint32_t OFF_BND = OFF_W + W_BYTES;            // epilogue boundary exchange
-  static constexpr uint32_t BND_BYTES = 2 * 4 * 2 * (COUT_TILE / 2) * 4;
-  static constexpr uint32_t OFF_BAR = OFF_BND + BND_BYTES;
+  static constexpr uint32_t BND_BYTES = 2 * 4 * 4 * 2 * CG * 4;  // [parity][group][quarter][2][CG]
+  static constexpr uint32_t OFF_BIASV = OFF_BND + BND_BYTES;      // bias of the whole output tensor
+  static constexpr uint32_t OFF_BAR = OFF_BIASV + 256 * 4;
   static constexpr uint32_t SMEM = OFF_BAR + 128;
   static constexpr int ACC_COLS = 3 * COUT_TILE;                  // P_-1, P_0, P_+1
   static constexpr int TMEM_COLS = 2 * ACC_COLS <= 256 ? 256 : 512;
@@ -141,14 +184,15 @@ struct ConvCfg {
 };
 
 template <int LOGN, int CIN, int COUT_TILE>
-__global__ void __launch_bounds__(384, 1) conv3x3_tc_kernel(const ConvArgs a) {
+__global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
   using Cfg = ConvCfg<LOGN, CIN, COUT_TILE>;
   constexpr int N = Cfg::N, TROWS = Cfg::TROWS, IROWS = Cfg::IROWS, KC = Cfg::KC;
-  constexpr int HALF_CO = COUT_TILE / 2;
+  constexpr int CG = Cfg::CG;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* const sA = smem + Cfg::OFF_A;
   unsigned char* const sW = smem + Cfg::OFF_W;
   float* const bnd = reinterpret_cast<float*>(smem + Cfg::OFF_BND);
+  float* const sbias = reinterpret_cast<float*>(smem + Cfg::OFF_BIASV);
   uint64_t* const bars = reinterpret_cast<uint64_t*>(smem + Cfg::OFF_BAR);
   uint64_t* const a_full = bars + 0;   // [2]
   uint64_t* const a_empty = bars + 2;  // [2]
@@ -170,7 +214,7 @@ __global__ void __launch_bounds__(384, 1) conv3x3_tc_kernel(const ConvArgs a) {
       mbar_init(a_full + s, 1);
       mbar_init(a_empty + s, 1);
       mbar_init(c_full + s, 1);
-      mbar_init(c_empty + s, 8 * 32);
+      mbar_init(c_empty + s, Cfg::NEPI * 32);
     }
     mbar_init(w_full, 1);
     *abort_flag = 0;
@@ -178,6 +222,7 @@ __global__ void __launch_bounds__(384, 1) conv3x3_tc_kernel(const ConvArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tslot, Cfg::TMEM_COLS);
+  for (int k = tid; k < a.cout_total; k += Cfg::NT) sbias[k] = a.bias[k];
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
@@ -287,12 +332,15 @@ __global__ void __launch_bounds__(384, 1) conv3x3_tc_kernel(const ConvArgs a) {
     }
   } else if (warp >= 4) {
     // ---------------- epilogue ---------------------------------------------------------
-    const int ew = warp - 4;          // 0..7
+    // out[x] = b + P_-1[x-1] + P_0[x] + P_+1[x+1]: neighbours within a warp come
+    // by shuffles; the lane-0 / lane-31 edges of each 32-pixel quarter go
+    // through shared memory (double buffered by tile parity, one named barrier
+    // per tile for the epilogue warps).
+    const int ew = warp - 4;          // 0..15
     const int quarter = warp & 3;     // TMEM lane quarter = pixels 32q .. 32q+31
-    const int half = ew >> 2;         // output-channel half
+    const int grp = ew >> 2;          // output-channel group of CG channels
     const int m = quarter * 32 + lane;
     const int x = m & (N - 1);
-    // neighbour quarters for the periodic x wrap at the lane-0 / lane-31 edges
     const int m0 = quarter * 32;
     const int qleft = ((m0 & (N - 1)) == 0 ? m0 - 1 + N : m0 - 1) >> 5;
     const int qright = (((m0 & (N - 1)) + 32) == N ? m0 + 32 - N : m0 + 32) >> 5;
@@ -302,46 +350,50 @@ __global__ void __launch_bounds__(384, 1) conv3x3_tc_kernel(const ConvArgs a) {
       const int pix = t % npix;
       const int b = pix / tiles_per_img, y0 = (pix % tiles_per_img) * TROWS;
       const int s = i & 1;
-      if (!mbar_wait(c_full + s, (i >> 1) & 1, lim)) {
+      const bool ok = mbar_wait(c_full + s, (i >> 1) & 1, lim);
+      if (!ok) {
         *ep_abort = 1;
         atomicOr(a.err, 16u);
       }
-      // decide together: only epilogue warps write ep_abort, before this barrier
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (*ep_abort) break;
       tmem_fence_after_sync();
-      const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Cfg::ACC_COLS);
-      const int co0 = a.co_base + part * COUT_TILE + half * HALF_CO;
-      const int gy = y0 + m / N;
-#pragma unroll 1
-      for (int cc = 0; cc < HALF_CO; cc += 8) {
-        const int col = half * HALF_CO + cc;
-        float pm[8], p0[8], pp[8];
-        tmem_ld8f(trow + 0 * COUT_TILE + col, pm);
-        tmem_ld8f(trow + 1 * COUT_TILE + col, p0);
-        tmem_ld8f(trow + 2 * COUT_TILE + col, pp);
-        // lane-edge values go to the neighbour quarter through shared memory
-        float* mybnd = bnd + ((half * 4 + quarter) * 2) * 8;
+      const uint32_t tcol = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Cfg::ACC_COLS) + grp * CG;
+      float pm[CG], pp[CG], p0[CG];
+      float* const eb = bnd + (size_t)s * (4 * 4 * 2 * CG);
+      if (ok) {
+        tmem_ld_cols<CG>(tcol + 0 * COUT_TILE, pm);
+        tmem_ld_cols<CG>(tcol + 2 * COUT_TILE, pp);
+        tmem_ld_cols<CG>(tcol + 1 * COUT_TILE, p0);
+        tmem_wait_ld();
+        float* mine = eb + ((grp * 4 + quarter) * 2) * CG;
         if (lane == 31) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) mybnd[j] = pm[j];  // P_-1 at the last pixel
+          for (int j = 0; j < CG; ++j) mine[j] = pm[j];
         }
         if (lane == 0) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) mybnd[8 + j] = pp[j];  // P_+1 at the first pixel
+          for (int j = 0; j < CG; ++j) mine[CG + j] = pp[j];
         }
-        asm volatile("bar.sync 1, 256;" ::: "memory");
+      }
+      // every epilogue warp arrives here once per tile; the abort decision is
+      // taken together after it
+      asm volatile("bar.sync 1, %0;" ::"r"(Cfg::NEPI * 32) : "memory");
+      if (*ep_abort) break;
+      const int co0 = a.co_base + part * COUT_TILE + grp * CG;
+      const int gy = y0 + m / N;
+      const float* eleft = eb + ((grp * 4 + qleft) * 2) * CG;
+      const float* eright = eb + ((grp * 4 + qright) * 2) * CG + CG;
+#pragma unroll
+      for (int cc = 0; cc < CG; cc += 8) {
         float outv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          float left = __shfl_up_sync(0xffffffffu, pm[j], 1);
-          float right = __shfl_down_sync(0xffffffffu, pp[j], 1);
-          if (lane == 0) left = bnd[((half * 4 + qleft) * 2) * 8 + j];
-          if (lane == 31) right = bnd[((half * 4 + qright) * 2) * 8 + 8 + j];
-          float v = p0[j] + left + right + a.bias[co0 + cc + j];
+          float left = __shfl_up_sync(0xffffffffu, pm[cc + j], 1);
+          float right = __shfl_down_sync(0xffffffffu, pp[cc + j], 1);
+          if (lane == 0) left = eleft[cc + j];
+          if (lane == 31) right = eright[cc + j];
+          const float v = p0[cc + j] + left + right + sbias[co0 + cc + j];
           outv[j] = a.gelu ? gelu_f(v) : v;
         }
-        asm volatile("bar.sync 1, 256;" ::: "memory");
         uint4 pk;
         __nv_bfloat162 h0 = __floats2bfloat162_rn(outv[0], outv[1]);
         __nv_bfloat162 h1 = __floats2bfloat162_rn(outv[2], outv[3]);
@@ -423,6 +475,44 @@ __global__ void __launch_bounds__(256) conv_in_kernel(const ConvInArgs a) {
       pk.z = *reinterpret_cast<uint32_t*>(&h2);
       pk.w = *reinterpret_cast<uint32_t*>(&h3);
       *reinterpret_cast<uint4*>(a.out + ((((size_t)b * 8 + c8) * N + y) * N + x) * 8) = pk;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// First-layer input for the tensor cores: cin/2 FP32 states -> 16 BF16
+// channels per pixel (channels cin .. 15 are zero), chunk planes
+// [batch][2][N][N][8].
+// ---------------------------------------------------------------------------
+struct PackArgs {
+  const float* const* hist;  // cin/2 pointers to [batch][2][N][N] states
+  __nv_bfloat16* out;        // [batch][2][N][N][8]
+  int batch, cin;
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(256) pack_input_kernel(const PackArgs a) {
+  constexpr int N = 1 << LOGN;
+  const size_t total = (size_t)a.batch * N * N;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / (N * N));
+    const size_t pix = p % (N * N);
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = 0.f;
+    for (int c = 0; c < a.cin; ++c) v[c] = a.hist[c >> 1][((size_t)b * 2 + (c & 1)) * N * N + pix];
+#pragma unroll
+    for (int c8 = 0; c8 < 2; ++c8) {
+      uint4 pk;
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(v[c8 * 8 + 0], v[c8 * 8 + 1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(v[c8 * 8 + 2], v[c8 * 8 + 3]);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[c8 * 8 + 4], v[c8 * 8 + 5]);
+      __nv_bfloat162 h3 = __floats2bfloat162_rn(v[c8 * 8 + 6], v[c8 * 8 + 7]);
+      pk.x = *reinterpret_cast<uint32_t*>(&h0);
+      pk.y = *reinterpret_cast<uint32_t*>(&h1);
+      pk.z = *reinterpret_cast<uint32_t*>(&h2);
+      pk.w = *reinterpret_cast<uint32_t*>(&h3);
+      *reinterpret_cast<uint4*>(a.out + (((size_t)b * 2 + c8) * N * N + pix) * 8) = pk;
     }
   }
 }

@@ -30,7 +30,9 @@ struct LearnedState {
   size_t raw_off_tw[6] = {}, raw_off_tb[6] = {};  // temporal-correction layers
   size_t pk_stencil[5] = {};   // packed tiles: hidden layers 1..4, last layer (64-wide parts)
   size_t pk_stencil_last32 = 0;
+  size_t pk_stencil_first = 0; // first layer, input channels padded to 16
   size_t pk_tc[4] = {};
+  size_t pk_tc_first = 0;
   __nv_bfloat16* act0 = nullptr;
   __nv_bfloat16* act1 = nullptr;
   __nv_bfloat16* coef = nullptr;

@@ -34,18 +34,20 @@ uint16_t bf16_bits(float f) {
   return (uint16_t)(r >> 16);
 }
 
-// tensor-core tile of one conv layer part: [9 taps][cin/8][cout_tile/8][8 co][8 ci]
-void pack_part(const float* W, int cin, int cout_total, int co0, int cout_tile, uint16_t* dst) {
+// tensor-core tile of one conv layer part: [9 taps][cin_pad/8][cout_tile/8][8 co][8 ci]; input
+// channels cin .. cin_pad - 1 are zero
+void pack_part(const float* W, int cin, int cout_total, int co0, int cout_tile, uint16_t* dst, int cin_pad = 0) {
+  if (cin_pad == 0) cin_pad = cin;
   for (int a = 0; a < 3; ++a)
     for (int e = 0; e < 3; ++e) {
       const int tap = a * 3 + e;
-      for (int c8 = 0; c8 < cin / 8; ++c8)
+      for (int c8 = 0; c8 < cin_pad / 8; ++c8)
         for (int n8 = 0; n8 < cout_tile / 8; ++n8)
           for (int n = 0; n < 8; ++n)
             for (int k = 0; k < 8; ++k) {
               const int co = co0 + n8 * 8 + n, ci = c8 * 8 + k;
-              const float w = W[(((size_t)co * cin + ci) * 3 + a) * 3 + e];
-              const size_t idx = ((((size_t)tap * (cin / 8) + c8) * (cout_tile / 8) + n8) * 8 + n) * 8 + k;
+              const float w = ci < cin ? W[(((size_t)co * cin + ci) * 3 + a) * 3 + e] : 0.0f;
+              const size_t idx = ((((size_t)tap * (cin_pad / 8) + c8) * (cout_tile / 8) + n8) * 8 + n) * 8 + k;
               dst[idx] = bf16_bits(w);
             }
       (void)cout_total;
@@ -54,11 +56,11 @@ void pack_part(const float* W, int cin, int cout_total, int co0, int cout_tile, 
 
 size_t part_elems(int cin, int cout_tile) { return (size_t)9 * cin * cout_tile; }
 
-template <int LOGN, int COUT_TILE>
+template <int LOGN, int COUT_TILE, int CIN = 64>
 cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __nv_bfloat16* wpack,
                         const float* bias, __nv_bfloat16* out, int batch, int parts, int co_base, int cout_total,
                         int gelu, cudaStream_t st) {
-  using Cfg = ConvCfg<LOGN, 64, COUT_TILE>;
+  using Cfg = ConvCfg<LOGN, CIN, COUT_TILE>;
   ConvArgs a;
   a.in = in;
   a.w = wpack;
@@ -73,7 +75,7 @@ cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __
   a.spin_limit = kSpin;
   const int ntiles = batch * (Cfg::N / Cfg::TROWS) * parts;
   const int grid = ntiles < L.sms ? ntiles : L.sms;
-  conv3x3_tc_kernel<LOGN, 64, COUT_TILE><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a);
+  conv3x3_tc_kernel<LOGN, CIN, COUT_TILE><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -85,6 +87,9 @@ cudaError_t prepare_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(conv3x3_tc_kernel<LOGN, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ConvCfg<LOGN, 64, 32>::SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(conv3x3_tc_kernel<LOGN, 16, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ConvCfg<LOGN, 16, 64>::SMEM);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fv_learned_stage_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)LearnedCfg<LOGN>::SMEM);
@@ -99,21 +104,22 @@ cudaError_t prepare_kernels() {
 // network of six conv3x3 layers from first-layer inputs (pointer array `hist`
 // of cin/2 states) to the chunk-plane output of the last hidden layer in act0
 template <int LOGN>
-cudaError_t run_trunk(fd_ctx* c, const float* const* hist, int cin, const float* w0, const float* b0,
+cudaError_t run_trunk(fd_ctx* c, const float* const* hist, int cin, size_t pk_first, const float* b0,
                       const size_t* pk_hidden, const size_t* raw_b, cudaStream_t st) {
   LearnedState& L = *c->lrn;
   const int B = c->grid.batch;
-  ConvInArgs ia;
-  ia.hist = hist;
-  ia.w = w0;
-  ia.bias = b0;
-  ia.out = L.act0;
-  ia.batch = B;
-  ia.cin = cin;
+  // first layer on the tensor cores: inputs packed to 16 BF16 channels
+  PackArgs pa;
+  pa.hist = hist;
+  pa.out = L.act1;
+  pa.batch = B;
+  pa.cin = cin;
   const size_t pix = (size_t)B << (2 * LOGN);
   const int blocks = (int)((pix + 255) / 256 < (size_t)(4 * L.sms) ? (pix + 255) / 256 : (size_t)(4 * L.sms));
-  conv_in_kernel<LOGN><<<blocks, 256, (64 * cin * 9 + 64) * sizeof(float), st>>>(ia);
+  pack_input_kernel<LOGN><<<blocks, 256, 0, st>>>(pa);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = launch_conv<LOGN, 64, 16>(L, L.act1, L.d_wpack + pk_first, b0, L.act0, B, 1, 0, 64, 1, st);
   __nv_bfloat16* bufs[2] = {L.act0, L.act1};
   for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
     e = launch_conv<LOGN, 64>(L, bufs[(l - 1) & 1], L.d_wpack + pk_hidden[l - 1], L.d_raw + raw_b[l], bufs[l & 1], B,
@@ -127,7 +133,7 @@ cudaError_t run_stencil_net(fd_ctx* c, const float* const* hist, cudaStream_t st
   LearnedState& L = *c->lrn;
   const int B = c->grid.batch;
   size_t hidden[4] = {L.pk_stencil[0], L.pk_stencil[1], L.pk_stencil[2], L.pk_stencil[3]};
-  cudaError_t e = run_trunk<LOGN>(c, hist, 2, L.d_raw + L.raw_off_sw[0], L.d_raw + L.raw_off_sb[0], hidden,
+  cudaError_t e = run_trunk<LOGN>(c, hist, 2, L.pk_stencil_first, L.d_raw + L.raw_off_sb[0], hidden,
                                   L.raw_off_sb, st);
   if (e != cudaSuccess) return e;
   // last layer 64 -> 160: two 64-channel parts and one 32-channel part
@@ -142,7 +148,7 @@ template <int LOGN>
 cudaError_t run_tc_net(fd_ctx* c, const float* const* hist, cudaStream_t st) {
   LearnedState& L = *c->lrn;
   const int B = c->grid.batch;
-  cudaError_t e = run_trunk<LOGN>(c, hist, 2 * L.kc, L.d_raw + L.raw_off_tw[0], L.d_raw + L.raw_off_tb[0], L.pk_tc,
+  cudaError_t e = run_trunk<LOGN>(c, hist, 2 * L.kc, L.pk_tc_first, L.d_raw + L.raw_off_tb[0], L.pk_tc,
                                   L.raw_off_tb, st);
   if (e != cudaSuccess) return e;
   ConvOut2Args oa;
@@ -346,6 +352,11 @@ fd_status fd_set_params(fd_ctx* c, const float* params, int64_t count, void* str
     pk.resize(o + elems);
     return o;
   };
+  {
+    const size_t o = add(part_elems(16, 64));
+    pack_part(&raw[L.raw_off_sw[0]], 2, 64, 0, 64, &pk[o], 16);
+    L.pk_stencil_first = o;
+  }
   for (int l = 1; l <= 4; ++l) {
     const size_t o = add(part_elems(64, 64));
     pack_part(&raw[L.raw_off_sw[l]], 64, 64, 0, 64, &pk[o]);
@@ -360,12 +371,16 @@ fd_status fd_set_params(fd_ctx* c, const float* params, int64_t count, void* str
     pack_part(&raw[L.raw_off_sw[5]], 64, kCoef, 128, 32, &pk[o2]);
     L.pk_stencil_last32 = o2;
   }
-  if (L.kc > 0)
+  if (L.kc > 0) {
+    const size_t o = add(part_elems(16, 64));
+    pack_part(&raw[L.raw_off_tw[0]], 2 * L.kc, 64, 0, 64, &pk[o], 16);
+    L.pk_tc_first = o;
     for (int l = 1; l <= 4; ++l) {
-      const size_t o = add(part_elems(64, 64));
-      pack_part(&raw[L.raw_off_tw[l]], 64, 64, 0, 64, &pk[o]);
-      L.pk_tc[l - 1] = o;
+      const size_t o2 = add(part_elems(64, 64));
+      pack_part(&raw[L.raw_off_tw[l]], 64, 64, 0, 64, &pk[o2]);
+      L.pk_tc[l - 1] = o2;
     }
+  }
   cudaError_t e = cudaSuccess;
   if (!L.d_raw) e = cudaMalloc(&L.d_raw, raw.size() * sizeof(float));
   if (e == cudaSuccess && !L.d_wpack) e = cudaMalloc(&L.d_wpack, pk.size() * sizeof(uint16_t));

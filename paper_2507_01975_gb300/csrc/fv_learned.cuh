@@ -279,59 +279,25 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kern
   __syncthreads();
 
   // ---- flux block: the eight instance values at every index -------------------
+  // Instances come in (interp, deriv) pairs that share field, axis and taps:
+  // pair p = 0 u-x, 1 u-y, 2 v-x, 3 v-y (instances 2p and 2p + 1).
+  __shared__ float swl[80];
+  if (tid < 80) swl[tid] = a.wl[tid];
+  __syncthreads();
   const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
+  const uint4* cbase = a.coef ? reinterpret_cast<const uint4*>(a.coef) + (size_t)b * 20 * NN : nullptr;
   for (int c = tid; c < N * N; c += NT) {
     const int j = c / N, i = c % N;
 #pragma unroll 1
-    for (int qi = 0; qi < 8; ++qi) {
-      const int fld = kInstField[qi], axis = kInstAxis[qi], kind = kInstKind[qi], sh = kInstShift[qi];
+    for (int pr_ = 0; pr_ < 4; ++pr_) {
+      const int fld = pr_ >> 1, axis = pr_ & 1;
+      const int sh = (pr_ == 0 || pr_ == 3) ? -1 : -2;
       const float* f = wt + fld * NN;
-      float L[20];
-#pragma unroll
-      for (int t = 0; t < 20; ++t) L[t] = a.wl[(kind * 2 + axis) * 20 + t];
-      if (a.coef) {
-        // channels 20 qi .. 20 qi + 19 of this cell
-#pragma unroll
-        for (int t = 0; t < 20; ++t) {
-          const int ch = 20 * qi + t;
-          const __nv_bfloat16 v = a.coef[((((size_t)b * 20 + (ch >> 3)) * N + j) * N + i) * 8 + (ch & 7)];
-          L[t] += __bfloat162float(v);
-        }
-      }
-      // consistency projection: remove sum, axial and transverse first moments
-      float s1 = 0.f, sc = 0.f, sr = 0.f;
+      float tap[20];
 #pragma unroll
       for (int r = 0; r < 5; ++r)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          const float v = L[r * 4 + cc];
-          s1 += v;
-          sc += v * cval[cc];
-          sr += v * (float)(r - 2);
-        }
-      s1 *= (1.0f / 20.0f);
-      sc *= (1.0f / 25.0f);
-      sr *= (1.0f / 40.0f);
-      const float h = axis == 0 ? 1.0f / a.idx : 1.0f / a.idy;
-      const float scale = kind == 1 ? 1.0f / h : 1.0f;
-      float val = 0.f;
-#pragma unroll
-      for (int r = 0; r < 5; ++r)
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
-          if (r == 2) {
-            // physics kernel W_P on the centre row
-            if (kind == 0) {
-              k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
-            } else if (a.dord == 4) {
-              const float d4[4] = {1.f / 24.f, -27.f / 24.f, 27.f / 24.f, -1.f / 24.f};
-              k += d4[cc] / h;
-            } else {
-              const float d2[4] = {0.f, -1.f, 1.f, 0.f};
-              k += d2[cc] / h;
-            }
-          }
           int jj, ii;
           if (axis == 0) {
             jj = (j + r - 2) & MSK;
@@ -340,9 +306,76 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kern
             jj = (j + cc + sh) & MSK;
             ii = (i + r - 2) & MSK;
           }
-          val += k * f[jj * N + ii];
+          tap[r * 4 + cc] = f[jj * N + ii];
         }
-      inst[qi * NN + c] = val;
+      const float h = axis == 0 ? 1.0f / a.idx : 1.0f / a.idy;
+#pragma unroll
+      for (int kind = 0; kind < 2; ++kind) {
+        const int qi = 2 * pr_ + kind;
+        float L[20];
+#pragma unroll
+        for (int t = 0; t < 20; ++t) L[t] = swl[(kind * 2 + axis) * 20 + t];
+        if (cbase) {
+          // channels 20 qi .. 20 qi + 19 lie in the three 8-channel chunks from
+          // (20 qi) / 8, starting at offset 0 (qi even) or 4 (qi odd)
+          const int k0 = (20 * qi) >> 3;
+          float fch[24];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const uint4 v = cbase[(size_t)(k0 + k) * NN + c];
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 f2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[e]));
+              fch[k * 8 + 2 * e] = f2.x;
+              fch[k * 8 + 2 * e + 1] = f2.y;
+            }
+          }
+          if (kind == 0) {
+#pragma unroll
+            for (int t = 0; t < 20; ++t) L[t] += fch[t];
+          } else {
+#pragma unroll
+            for (int t = 0; t < 20; ++t) L[t] += fch[4 + t];
+          }
+        }
+        // consistency projection: remove sum, axial and transverse first moments
+        float s1 = 0.f, sc = 0.f, sr = 0.f;
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const float v = L[r * 4 + cc];
+            s1 += v;
+            sc += v * cval[cc];
+            sr += v * (float)(r - 2);
+          }
+        s1 *= (1.0f / 20.0f);
+        sc *= (1.0f / 25.0f);
+        sr *= (1.0f / 40.0f);
+        const float scale = kind == 1 ? 1.0f / h : 1.0f;
+        float val = 0.f;
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
+            if (r == 2) {
+              // physics kernel W_P on the centre row
+              if (kind == 0) {
+                k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
+              } else if (a.dord == 4) {
+                const float d4[4] = {1.f / 24.f, -27.f / 24.f, 27.f / 24.f, -1.f / 24.f};
+                k += d4[cc] / h;
+              } else {
+                const float d2[4] = {0.f, -1.f, 1.f, 0.f};
+                k += d2[cc] / h;
+              }
+            }
+            val += k * tap[r * 4 + cc];
+          }
+        inst[qi * NN + c] = val;
+      }
     }
   }
   __syncthreads();

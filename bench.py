@@ -163,6 +163,59 @@ def cpu_baseline(seconds: float = 12.0):
     }
 
 
+def learned_measurement(fd, I, steps: int = 60):
+    """Learned-stencil inference (Kolmogorov 64^2, batch 128, BF16 network on the
+    tensor cores, temporal correction every 4 steps): cell-updates/s and the
+    tensor-core rate of the stencil network, timed with CUDA events."""
+    import torch
+
+    n, b, kc = 64, 128, 4
+    st = I.random_conv_stack(1, 2, 64, 160, last_scale=0.05)
+    tc = I.random_conv_stack(2, 2 * kc, 64, 2, last_scale=0.02)
+    s = fd.Solver(fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=1.75e-3, forcing="kolmogorov",
+                            learned=True, k_c=kc))
+    s.set_params(I.pack_params(I.random_wl(3, 1e-2), st, tc))
+    U0 = np.stack([I.kolmogorov_ic(n, k) for k in range(b)]).astype(np.float32)
+    u = torch.tensor(U0, device="cuda")
+    o = torch.empty_like(u)
+    coef = torch.empty((b, 160, n, n), device="cuda")
+    for _ in range(2):
+        s.rollout(u, o, 8)
+        s.network_forward(u, coef)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.rollout(u, o, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / steps
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        s.network_forward(u, coef)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_net = e0.elapsed_time(e1) / reps
+    flop_net = 481_536 * n * n * b  # one stencil-network evaluation (6 conv3x3 layers)
+    flop_step = (4 * 481_536 + (2 * kc * 64 * 9 * 2 + 4 * 64 * 64 * 9 * 2 + 64 * 2 * 9 * 2) / kc) * n * n * b
+    peaks = _measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained") or 1757.0
+    achieved = flop_net / (ms_net * 1e-3) / 1e12
+    return {
+        "workload": "Kolmogorov 64^2, batch 128, learned stencil network (6 conv3x3, 64 ch, BF16) + temporal correction k_c=4",
+        "value": n * n * b / (ms_step * 1e-3),
+        "unit": "cell-updates/s",
+        "ms_per_time_step": ms_step,
+        "step_tflops": flop_step / (ms_step * 1e-3) / 1e12,
+        "finite": bool(s.check_finite(o)),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "stencil network forward (conv3x3_tc_kernel launches, 7 per evaluation)",
+                     "peak_basis": "measured cuBLAS bf16 sustained (MEASURED_PEAKS.json)"},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,6 +223,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
                     help="time steps per rollout (the workload's 2000 by default; smaller only for ncu captures)")
     args = ap.parse_args()
@@ -279,6 +333,7 @@ def main():
         "hbm_gbs_measured": _measured_peaks().get("hbm_gbs"),
     }
     cpu = None if args.no_cpu_baseline else cpu_baseline()
+    learned = None if args.no_learned else learned_measurement(fd, I)
     line = {
         "metric": METRIC,
         "value": value,
@@ -306,6 +361,7 @@ def main():
                 "d2h_bytes_per_step": int(U0.nbytes)},
         "gpu_launches": launches,
         "clocks": clocks,
+        "learned": learned,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

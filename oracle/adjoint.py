@@ -1,0 +1,233 @@
+"""FP64 oracle of the adjoint (vector-Jacobian product) of one FV step.
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring. Hand-derived reverse
+mode of ``oracle.fv``: given u_n and lam = dL/du_{n+1}, returns dL/du_n and
+dL/dtheta for the learnable parameters (W_L, the stencil network). The
+solver's differentiability is what the paper's training relies on (Sec. 4.1,
+Eq. for the loss; the "differentiable solver backbone" of the introduction);
+the paper gives no derivation, so every rule here is the transpose of the
+corresponding forward line in ``oracle.fv``:
+
+* periodic shift  g = shifted(f, a, b)      ->  f_bar += shifted(g_bar, -a, -b)
+* face operator   v = sum_rc K_rc tap_rc(f) ->  f_bar += sum_rc tap_rc^T(K_rc v_bar),
+                                                K_bar_rc = v_bar tap_rc(f)
+* projection      P symmetric (P^T = P)
+* consistency projection (orthogonal projector) -> L_bar = proj(K_bar) * scale
+* conv3x3 / GELU: transposed convolution, weight correlation, GELU'.
+
+Pinned in ``tests/test_oracle_adjoint.py`` by dot-product tests against a
+fourth-order finite-difference Jacobian-vector product and by central
+differences on the parameters.
+"""
+
+from __future__ import annotations
+
+from typing import Optional
+
+import numpy as np
+
+from .fv import (
+    FLOW_BURGERS,
+    FLOW_NAVIER_STOKES,
+    INSTANCES,
+    LearnedModel,
+    Problem,
+    apply_axial,
+    cnn_forward,
+    consistency_project,
+    face_values,
+    gelu_grad,
+    learned_kernels,
+    physics_kernel,
+    plain_kernels,
+    project,
+    shifted,
+    shifted_c,
+    tendency,
+)
+
+
+def unshift(g: np.ndarray, dj: int, di: int) -> np.ndarray:
+    """Adjoint of ``shifted(f, dj, di)``: ``shifted(g, -dj, -di)``."""
+    return shifted(g, -dj, -di)
+
+
+def tendency_vjp(U: np.ndarray, p: Problem, kernels, Tbar: np.ndarray, want_kbar: bool = False):
+    """Reverse mode of ``oracle.fv.tendency`` for fixed kernels.
+
+    Returns ``(Ubar, Kbar)``: the gradient with respect to the state through
+    the face values and the direct terms, and (when ``want_kbar``) the
+    per-location kernel gradients ``Kbar[q][5, 4, ny, nx]``.
+    """
+    dx, dy = p.dx, p.dy
+    Uc, Gxc, Uk, Gyu, Vk, Gxv, Vc, Gyc = face_values(U, kernels)
+    Tu, Tv = Tbar[0], Tbar[1]
+    vbar = [None] * 8
+    # advection of u: -(Uc^2 - W(Uc^2)) / dx
+    A_bar = -Tu / dx + unshift(Tu, 0, -1) / dx
+    vbar[0] = 2.0 * Uc * A_bar
+    # corner products P = Uk Vk in both equations
+    P_bar = (-unshift(Tu, 1, 0) + Tu) / dy + (-unshift(Tv, 0, 1) + Tv) / dx
+    vbar[2] = P_bar * Vk
+    vbar[4] = P_bar * Uk
+    # advection of v: -(Vc^2 - S(Vc^2)) / dy
+    B_bar = -Tv / dy + unshift(Tv, -1, 0) / dy
+    vbar[6] = 2.0 * Vc * B_bar
+    # diffusion
+    vbar[1] = p.nu * (Tu - unshift(Tu, 0, -1)) / dx
+    vbar[3] = p.nu * (unshift(Tu, 1, 0) - Tu) / dy
+    vbar[5] = p.nu * (unshift(Tv, 0, 1) - Tv) / dx
+    vbar[7] = p.nu * (Tv - unshift(Tv, -1, 0)) / dy
+    Ubar = np.zeros_like(U)
+    if p.flow == FLOW_BURGERS:
+        divc = Gxc + Gyc
+        Ubar[0] += Tu * 0.5 * (shifted(divc, 0, -1) + divc)
+        Ubar[1] += Tv * 0.5 * (shifted(divc, -1, 0) + divc)
+        hu = 0.5 * Tu * U[0]
+        hv = 0.5 * Tv * U[1]
+        divc_bar = unshift(hu, 0, -1) + hu + unshift(hv, -1, 0) + hv
+        vbar[1] = vbar[1] + divc_bar
+        vbar[7] = vbar[7] + divc_bar
+    if p.forcing_kind == 1:
+        Ubar[0] += -p.drag * Tu
+        Ubar[1] += -p.drag * Tv
+    # face operators
+    Kbar = [None] * 8
+    for q, (fld, axis, _kind, shift) in enumerate(INSTANCES):
+        K = kernels[q]
+        if want_kbar:
+            Kbar[q] = np.zeros((5, 4) + U.shape[1:])
+        for r in range(5):
+            for c in range(4):
+                if axis == 0:
+                    a, b = r - 2, c + shift
+                else:
+                    a, b = c + shift, r - 2
+                Ubar[fld] += unshift(K[r, c] * vbar[q], a, b)
+                if want_kbar:
+                    Kbar[q][r, c] = vbar[q] * shifted(U[fld], a, b)
+    return Ubar, Kbar
+
+
+def cnn_vjp(x: np.ndarray, layers, ybar: np.ndarray):
+    """Reverse mode of ``oracle.fv.cnn_forward``: returns (xbar, [(dW, db)])."""
+    _, pre = cnn_forward(x, layers, keep=True)
+    n_layers = len(layers)
+    acts = [x] + [None] * n_layers
+    from .fv import gelu
+
+    for l in range(n_layers - 1):
+        acts[l + 1] = gelu(pre[l])
+    grads = [None] * n_layers
+    zbar = ybar
+    for l in range(n_layers - 1, -1, -1):
+        W, _b = layers[l]
+        h = acts[l]
+        dW = np.zeros_like(W)
+        for a in (-1, 0, 1):
+            for e in (-1, 0, 1):
+                dW[:, :, a + 1, e + 1] = np.einsum("oji,cji->oc", zbar, shifted_c(h, a, e))
+        db = zbar.sum(axis=(1, 2))
+        grads[l] = (dW, db)
+        hbar = np.zeros_like(h)
+        for a in (-1, 0, 1):
+            for e in (-1, 0, 1):
+                hbar += shifted_c(np.einsum("oc,oji->cji", W[:, :, a + 1, e + 1], zbar), -a, -e)
+        if l > 0:
+            zbar = hbar * gelu_grad(pre[l - 1])
+        else:
+            zbar = hbar
+    return zbar, grads
+
+
+def learned_tendency_vjp(U: np.ndarray, p: Problem, model: LearnedModel, Tbar: np.ndarray):
+    """Reverse mode of H(U) = tendency(U, learned_kernels(U)).
+
+    Returns ``(Ubar, W_L_bar, stencil_grads)``.
+    """
+    ks = learned_kernels(U, p, model)
+    Ubar, Kbar = tendency_vjp(U, p, ks, Tbar, want_kbar=True)
+    ny, nx = U.shape[1:]
+    Cbar = np.zeros((160, ny, nx))
+    WLbar = np.zeros_like(model.W_L)
+    for q, (_fld, axis, kind, _shift) in enumerate(INSTANCES):
+        h = p.dx if axis == 0 else p.dy
+        scale = 1.0 / h if kind == 1 else 1.0
+        Lbar = consistency_project(Kbar[q]) * scale
+        Cbar[q * 20:(q + 1) * 20] = Lbar.reshape(20, ny, nx)
+        WLbar[kind, axis] += Lbar.sum(axis=(2, 3))
+    xbar, grads = cnn_vjp(U, model.stencil, Cbar)
+    return Ubar + xbar, WLbar, grads
+
+
+def step_vjp(U: np.ndarray, p: Problem, lam: np.ndarray, model: Optional[LearnedModel] = None):
+    """Reverse mode of one RK4 step (``oracle.fv.rk4_step`` / ``learned_step``).
+
+    u' = P(u + dt/6 (r1 + 2 r2 + 2 r3 + r4)), r_s = H(w_s), w_1 = u,
+    w_2 = P(u + dt/2 r1), w_3 = P(u + dt/2 r2), w_4 = P(u + dt r3).
+    Returns ``(lam_in, grads)`` where ``grads`` is None for the plain step and
+    ``(W_L_bar, stencil_grads)`` for the learned step.
+    """
+    ns = p.flow == FLOW_NAVIER_STOKES
+    P = (lambda W: project(W, p)) if ns else (lambda W: W)
+
+    def H(W):
+        if model is None:
+            return tendency(W, p)
+        return tendency(W, p, learned_kernels(W, p, model))
+
+    def H_vjp(W, Tb):
+        if model is None:
+            Ub, _ = tendency_vjp(W, p, plain_kernels(p), Tb)
+            return Ub, None
+        Ub, wlb, g = learned_tendency_vjp(W, p, model, Tb)
+        return Ub, (wlb, g)
+
+    # forward stage states
+    w1 = U
+    r1 = H(w1)
+    w2 = P(U + 0.5 * p.dt * r1)
+    r2 = H(w2)
+    w3 = P(U + 0.5 * p.dt * r2)
+    r3 = H(w3)
+    w4 = P(U + p.dt * r3)
+    # reverse
+    g = P(lam)
+    lam_in = g.copy()
+    rb4 = p.dt / 6.0 * g
+    rb3 = p.dt / 3.0 * g
+    rb2 = p.dt / 3.0 * g
+    rb1 = p.dt / 6.0 * g
+    acc_wl = np.zeros((2, 2, 5, 4)) if model is not None else None
+    acc_g = None
+
+    def add(grads):
+        nonlocal acc_wl, acc_g
+        if grads is None:
+            return
+        wlb, g_ = grads
+        acc_wl += wlb
+        if acc_g is None:
+            acc_g = [(dW.copy(), db.copy()) for dW, db in g_]
+        else:
+            acc_g = [(a0 + dW, a1 + db) for (a0, a1), (dW, db) in zip(acc_g, g_)]
+
+    wb4, gr = H_vjp(w4, rb4)
+    add(gr)
+    y = P(wb4)
+    lam_in += y
+    rb3 = rb3 + p.dt * y
+    wb3, gr = H_vjp(w3, rb3)
+    add(gr)
+    y = P(wb3)
+    lam_in += y
+    rb2 = rb2 + 0.5 * p.dt * y
+    wb2, gr = H_vjp(w2, rb2)
+    add(gr)
+    y = P(wb2)
+    lam_in += y
+    rb1 = rb1 + 0.5 * p.dt * y
+    wb1, gr = H_vjp(w1, rb1)
+    add(gr)
+    lam_in += wb1
+    return lam_in, (None if model is None else (acc_wl, acc_g))

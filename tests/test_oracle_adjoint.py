@@ -1,0 +1,133 @@
+"""Pins of the adjoint oracle (CPU): dot-product tests against a fourth-order
+finite-difference Jacobian-vector product, and central differences on the
+learnable parameters (epsilon = 1e-3, FP64)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import adjoint as A
+from paper_2507_01975_gb300 import inputs as I
+
+
+def fd4_jvp(f, x, d, eps):
+    """[-f(x+2ed) + 8 f(x+ed) - 8 f(x-ed) + f(x-2ed)] / (12 e): error O(e^4)."""
+    return (-f(x + 2 * eps * d) + 8 * f(x + eps * d) - 8 * f(x - eps * d) + f(x - 2 * eps * d)) / (12 * eps)
+
+
+def small_model(seed, n, last_scale=0.05):
+    st = I.random_conv_stack(seed, 2, 8, O.N_COEF, last_scale=last_scale)  # narrow network keeps FD cheap
+    return O.LearnedModel(W_L=I.random_wl(seed + 1, 1e-2), stencil=st)
+
+
+@pytest.mark.parametrize("flow,forcing", [(O.FLOW_NAVIER_STOKES, 0), (O.FLOW_NAVIER_STOKES, 1), (O.FLOW_BURGERS, 0)])
+def test_plain_step_dot_product(flow, forcing):
+    n = 16
+    p = O.Problem(nx=n, ny=n, nu=0.02, dt=0.02, flow=flow, forcing_kind=forcing)
+    rng = np.random.default_rng(3)
+    U = I.decaying_ic(n, 1) if flow == O.FLOW_NAVIER_STOKES else I.burgers_ic(n, 1)
+    du = rng.standard_normal(U.shape)
+    if flow == O.FLOW_NAVIER_STOKES:
+        du = O.project(du, p)  # tangent directions of the divergence-free manifold
+    lam = rng.standard_normal(U.shape)
+    jv = fd4_jvp(lambda x: O.rk4_step(x, p), U, du, 1e-3)
+    lam_in, _ = A.step_vjp(U, p, lam)
+    lhs = np.sum(jv * lam)
+    rhs = np.sum(du * lam_in)
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+def test_tendency_kernel_gradient_matches_finite_differences():
+    n = 8
+    p = O.Problem(nx=n, ny=n, nu=0.05, dt=0.01)
+    U = I.decaying_ic(n, 2)
+    rng = np.random.default_rng(4)
+    ks = [k[:, :, None, None] + 0.1 * rng.standard_normal((5, 4, n, n)) for k in O.plain_kernels(p)]
+    Tb = rng.standard_normal(U.shape)
+    _, Kbar = A.tendency_vjp(U, p, ks, Tb, want_kbar=True)
+    for q, (r, c, j, i) in [(0, (2, 1, 3, 4)), (3, (0, 3, 7, 1)), (6, (4, 0, 2, 2))]:
+        def L(eps, q=q, r=r, c=c, j=j, i=i):
+            kk = [k.copy() for k in ks]
+            kk[q][r, c, j, i] += eps
+            return np.sum(O.tendency(U, p, kk) * Tb)
+        fd = (L(1e-4) - L(-1e-4)) / 2e-4
+        assert abs(fd - Kbar[q][r, c, j, i]) <= 1e-8 * max(1.0, abs(fd))
+
+
+def test_cnn_vjp_dot_product_and_weight_gradient():
+    n = 8
+    layers = I.random_conv_stack(5, 2, 8, 6, last_scale=1.0)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((2, n, n))
+    dx = rng.standard_normal(x.shape)
+    yb = rng.standard_normal((6, n, n))
+    jv = fd4_jvp(lambda z: O.cnn_forward(z, layers), x, dx, 1e-3)
+    xb, grads = A.cnn_vjp(x, layers, yb)
+    assert abs(np.sum(jv * yb) - np.sum(dx * xb)) <= 1e-9 * np.abs(jv * yb).sum()
+    for l, idx in [(0, (3, 1, 0, 2)), (2, (5, 7, 1, 1)), (5, (4, 2, 2, 0))]:
+        def L(eps, l=l, idx=idx):
+            ll = [(W.copy(), b.copy()) for W, b in layers]
+            ll[l][0][idx] += eps
+            return np.sum(O.cnn_forward(x, ll) * yb)
+        fd = (L(1e-3) - L(-1e-3)) / 2e-3
+        assert abs(fd - grads[l][0][idx]) <= 1e-5 * max(1.0, abs(fd))
+    def Lb(eps):
+        ll = [(W.copy(), b.copy()) for W, b in layers]
+        ll[3][1][2] += eps
+        return np.sum(O.cnn_forward(x, ll) * yb)
+    fd = (Lb(1e-3) - Lb(-1e-3)) / 2e-3
+    assert abs(fd - grads[3][1][2]) <= 1e-5 * max(1.0, abs(fd))
+
+
+def test_learned_step_dot_product():
+    n = 8
+    p = O.Problem(nx=n, ny=n, nu=0.02, dt=0.02, forcing_kind=1)
+    model = small_model(7, n)
+    rng = np.random.default_rng(8)
+    U = I.kolmogorov_ic(n, 3)
+    du = O.project(rng.standard_normal(U.shape), p)
+    lam = rng.standard_normal(U.shape)
+    jv = fd4_jvp(lambda x: O.learned_step(x, p, model), U, du, 1e-3)
+    lam_in, _ = A.step_vjp(U, p, lam, model)
+    lhs, rhs = np.sum(jv * lam), np.sum(du * lam_in)
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+def test_learned_step_parameter_gradients_central_differences():
+    n = 8
+    p = O.Problem(nx=n, ny=n, nu=0.02, dt=0.02)
+    model = small_model(9, n)
+    rng = np.random.default_rng(10)
+    U = I.decaying_ic(n, 4)
+    lam = rng.standard_normal(U.shape)
+    _, (wlb, grads) = A.step_vjp(U, p, lam, model)
+
+    def loss_with(mod):
+        return np.sum(O.learned_step(U, p, mod) * lam)
+
+    eps = 1e-3
+    # W_L entries
+    for idx in [(0, 0, 2, 1), (1, 1, 0, 3), (1, 0, 4, 2)]:
+        def m(s, idx=idx):
+            wl = model.W_L.copy()
+            wl[idx] += s
+            return O.LearnedModel(W_L=wl, stencil=model.stencil)
+        fd = (loss_with(m(eps)) - loss_with(m(-eps))) / (2 * eps)
+        assert abs(fd - wlb[idx]) <= 1e-5 * max(1e-3, abs(fd))
+    # network weights and a bias
+    for l, idx in [(0, (1, 0, 1, 1)), (3, (2, 5, 0, 2)), (5, (17, 3, 1, 1))]:
+        def m(s, l=l, idx=idx):
+            st = [(W.copy(), b.copy()) for W, b in model.stencil]
+            st[l][0][idx] += s
+            return O.LearnedModel(W_L=model.W_L, stencil=st)
+        fd = (loss_with(m(eps)) - loss_with(m(-eps))) / (2 * eps)
+        assert abs(fd - grads[l][0][idx]) <= 1e-5 * max(1e-3, abs(fd))
+
+
+def test_adjoint_of_projection_is_projection():
+    # P is symmetric: the reverse of "project" is "project"
+    n = 16
+    p = O.Problem(nx=n, ny=n)
+    rng = np.random.default_rng(12)
+    a, b = rng.standard_normal((2, 2, n, n))
+    assert abs(np.sum(O.project(a, p) * b) - np.sum(a * O.project(b, p))) < 1e-12 * np.abs(a * b).sum()

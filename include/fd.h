@@ -163,6 +163,33 @@ fd_status fd_set_params(fd_ctx* ctx, const float* params, int64_t count, void* s
  * float32) = C_theta(u) for the device state u. For tests and diagnostics. */
 fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* stream);
 
+/* ---- reverse mode ----------------------------------------------------------
+ *
+ * Vector-Jacobian product of one time step u' = FV(u) (the solver's
+ * differentiability, which the paper's training through unrolled rollouts
+ * relies on: Sec. 4.1 loss, Sec. 3.2 integrated solver). Given the state u_in
+ * and the cotangent lam_out = dL/du', computes lam_in = (du'/du)^T lam_out and,
+ * for a learned context, adds (du'/dtheta)^T lam_out to dparams.
+ *
+ * The step is recomputed from u_in (stage states and every network activation
+ * of the four RK stages are kept in a context-owned workspace, allocated by the
+ * first call), then the stages are run backwards: the projection is symmetric
+ * (its own adjoint), the face operators transpose to scatters, the per-face
+ * kernel cotangent passes through the consistency projection to the network
+ * output, and the network's data and weight gradients run on the tensor cores
+ * (BF16 operands, FP32 accumulation; the weight gradients are reduced
+ * deterministically).
+ *
+ * u_in, lam_out, lam_in: device float32 [batch][2][ny][nx]; lam_in may alias
+ * lam_out. dparams: device float32 array of fd_param_count values in the
+ * fd_set_params layout, ACCUMULATED into (+=); NULL skips the parameter
+ * gradients. Stream-ordered; the first call allocates and synchronises.
+ * Scope: FP32 contexts with N = 32 or 64, plain or learned without the
+ * temporal correction (k_c = 0); FD_EUNSUPPORTED otherwise. FD_EINVAL for null
+ * pointers, dparams on a plain context or parameters not yet set. */
+fd_status fd_step_adjoint(fd_ctx* ctx, const void* u_in, const void* lam_out, void* lam_in, float* dparams,
+                          void* stream);
+
 /* Release the context and its device tables (synchronises the device). */
 fd_status fd_destroy(fd_ctx* ctx);
 

@@ -43,7 +43,10 @@ struct ConvArgs {
   int parts;                 // output-channel parts of COUT_TILE channels each
   int co_base;               // first output channel of part 0
   int cout_total;            // channel count of the output tensor
-  int gelu;                  // apply GELU in the epilogue
+  int gelu;                  // epilogue: 0 none, 1 GELU (pre-activation to aux if set),
+                             // 2 multiply by GELU'(aux) (reverse mode of GELU, no bias)
+  const __nv_bfloat16* aux_in;  // mode 2: pre-activation, same layout as out
+  __nv_bfloat16* aux_out;       // mode 1: pre-activation is stored here when non-null
   unsigned* err;             // set to nonzero on a timed-out wait
   long long spin_limit;
 };
@@ -152,7 +155,18 @@ __device__ __forceinline__ float gelu_f(float x) {
   return 0.5f * x * (1.0f + erf_x);
 }
 
-template <int LOGN, int CIN, int COUT_TILE>
+// GELU'(x) = Phi(x) + x phi(x), with the same erf approximation
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  const float z = fabsf(x) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, 1.0f + 0.3275911f * z);
+  const float poly = t * (0.254829592f + t * (-0.284496736f + t * (1.421413741f + t * (-1.453152027f + t * 1.061405429f))));
+  const float g = __expf(-z * z);
+  const float erf_abs = 1.0f - poly * g;
+  const float erf_x = x < 0.0f ? -erf_abs : erf_abs;
+  return 0.5f * (1.0f + erf_x) + x * 0.39894228040143268f * g;
+}
+
+template <int LOGN, int CIN, int COUT_TILE, int NBUF = 2>
 struct ConvCfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int TM = 128;             // output pixels per tile
@@ -166,8 +180,8 @@ struct ConvCfg {
   static constexpr uint32_t ATILE_BYTES = KC * PLANE_BYTES;       // one input tile
   static constexpr uint32_t TAP_BYTES = KC * (COUT_TILE / 8) * 128;
   static constexpr uint32_t W_BYTES = 9 * TAP_BYTES;
-  static constexpr uint32_t OFF_A = 0;                            // two input tiles
-  static constexpr uint32_t OFF_W = 2 * ATILE_BYTES;
+  static constexpr uint32_t OFF_A = 0;                            // NBUF input tiles
+  static constexpr uint32_t OFF_W = NBUF * ATILE_BYTES;
   static constexpr uint32_t OFF_BND = OFF_W + W_BYTES;            // epilogue boundary exchange
   static constexpr uint32_t BND_BYTES = 2 * 4 * 4 * 2 * CG * 4;  // [parity][group][quarter][2][CG]
   static constexpr uint32_t OFF_BIASV = OFF_BND + BND_BYTES;      // bias of the whole output tensor
@@ -181,11 +195,12 @@ struct ConvCfg {
   static_assert(2 * ACC_COLS <= 512, "double-buffered accumulators fit tensor memory");
   static_assert(SMEM <= 232448, "shared memory");
   static_assert(PLANE_BYTES < (1u << 18), "descriptor offsets");
+  static_assert(NBUF == 1 || NBUF == 2, "input buffering");
 };
 
-template <int LOGN, int CIN, int COUT_TILE>
+template <int LOGN, int CIN, int COUT_TILE, int NBUF = 2>
 __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
-  using Cfg = ConvCfg<LOGN, CIN, COUT_TILE>;
+  using Cfg = ConvCfg<LOGN, CIN, COUT_TILE, NBUF>;
   constexpr int N = Cfg::N, TROWS = Cfg::TROWS, IROWS = Cfg::IROWS, KC = Cfg::KC;
   constexpr int CG = Cfg::CG;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tslot, Cfg::TMEM_COLS);
-  for (int k = tid; k < a.cout_total; k += Cfg::NT) sbias[k] = a.bias[k];
+  for (int k = tid; k < a.cout_total; k += Cfg::NT) sbias[k] = a.bias ? a.bias[k] : 0.0f;
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
@@ -239,8 +254,9 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
         const int part = t / npix;
         const int pix = t % npix;
         const int b = pix / tiles_per_img, y0 = (pix % tiles_per_img) * TROWS;
-        const int s = i & 1;
-        if (!mbar_wait(a_empty + s, ((i >> 1) & 1) ^ 1, lim)) {
+        const int s = NBUF == 2 ? (i & 1) : 0;
+        const uint32_t aph = NBUF == 2 ? ((i >> 1) & 1) : (i & 1);
+        if (!mbar_wait(a_empty + s, aph ^ 1, lim)) {
           *abort_flag = 1;
           atomicOr(a.err, 1u);
           break;
@@ -249,7 +265,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
           // the MMAs of every earlier tile have completed (a_empty of the
           // previous tile in this buffer and of the other buffer), so the
           // weight area can be overwritten
-          if (i > 0 && !mbar_wait(a_empty + (s ^ 1), (((i - 1) >> 1) & 1), lim)) {
+          if (NBUF == 2 && i > 0 && !mbar_wait(a_empty + (s ^ 1), (((i - 1) >> 1) & 1), lim)) {
             *abort_flag = 1;
             atomicOr(a.err, 2u);
             break;
@@ -277,7 +293,8 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
       // never leave with bulk copies in flight: wait (bounded) for the last
       // tiles and the last weight load to land
       for (int j = issued - 2; j < issued; ++j)
-        if (j >= 0) mbar_wait(a_full + (j & 1), (j >> 1) & 1, lim);
+        if (j >= 0 && (NBUF == 2 || j == issued - 1))
+          mbar_wait(a_full + (NBUF == 2 ? (j & 1) : 0), NBUF == 2 ? ((j >> 1) & 1) : (j & 1), lim);
       if (wphase_waits > 0) mbar_wait(w_full, (wphase_waits - 1) & 1, lim);
     }
   } else if (warp == 1) {
@@ -289,7 +306,9 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
       int i = 0;
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
         const int part = t / npix;
-        const int s = i & 1;
+        const int s = i & 1;                              // accumulator buffer
+        const int sa = NBUF == 2 ? s : 0;                 // input buffer
+        const uint32_t aph = NBUF == 2 ? ((i >> 1) & 1) : (i & 1);
         if (*abort_flag) break;
         if (part != cur_part) {
           if (!mbar_wait(w_full, wpar, lim)) {
@@ -300,13 +319,13 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
           wpar ^= 1;
           cur_part = part;
         }
-        if (!mbar_wait(a_full + s, (i >> 1) & 1, lim) || !mbar_wait(c_empty + s, ((i >> 1) & 1) ^ 1, lim)) {
+        if (!mbar_wait(a_full + sa, aph, lim) || !mbar_wait(c_empty + s, ((i >> 1) & 1) ^ 1, lim)) {
           *abort_flag = 1;
           atomicOr(a.err, 8u);
           break;
         }
         tmem_fence_after_sync();
-        const uint32_t abase = smem_u32(sA + s * Cfg::ATILE_BYTES);
+        const uint32_t abase = smem_u32(sA + sa * Cfg::ATILE_BYTES);
         const uint32_t wbase = smem_u32(sW);
         const uint32_t dbase = tmem + (uint32_t)(s * Cfg::ACC_COLS);
 #pragma unroll 1
@@ -326,7 +345,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
             }
           }
         }
-        umma_commit(a_empty + s);
+        umma_commit(a_empty + sa);
         umma_commit(c_full + s);
       }
     }
@@ -391,8 +410,39 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
           float right = __shfl_down_sync(0xffffffffu, pp[cc + j], 1);
           if (lane == 0) left = eleft[cc + j];
           if (lane == 31) right = eright[cc + j];
-          const float v = p0[cc + j] + left + right + sbias[co0 + cc + j];
-          outv[j] = a.gelu ? gelu_f(v) : v;
+          outv[j] = p0[cc + j] + left + right;
+        }
+        const int chunk = (co0 + cc) >> 3;
+        const size_t oidx = ((((size_t)b * (a.cout_total / 8) + chunk) * N + gy) * N + x) * 8;
+        if (a.gelu == 2) {
+          // reverse mode of GELU: multiply by GELU'(pre-activation)
+          const uint4 zk = *reinterpret_cast<const uint4*>(a.aux_in + oidx);
+          const uint32_t z4[4] = {zk.x, zk.y, zk.z, zk.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&z4[e]));
+            outv[2 * e] *= gelu_grad_f(f.x);
+            outv[2 * e + 1] *= gelu_grad_f(f.y);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) outv[j] += sbias[co0 + cc + j];
+          if (a.gelu == 1) {
+            if (a.aux_out) {
+              uint4 zk;
+              __nv_bfloat162 z0 = __floats2bfloat162_rn(outv[0], outv[1]);
+              __nv_bfloat162 z1 = __floats2bfloat162_rn(outv[2], outv[3]);
+              __nv_bfloat162 z2 = __floats2bfloat162_rn(outv[4], outv[5]);
+              __nv_bfloat162 z3 = __floats2bfloat162_rn(outv[6], outv[7]);
+              zk.x = *reinterpret_cast<uint32_t*>(&z0);
+              zk.y = *reinterpret_cast<uint32_t*>(&z1);
+              zk.z = *reinterpret_cast<uint32_t*>(&z2);
+              zk.w = *reinterpret_cast<uint32_t*>(&z3);
+              *reinterpret_cast<uint4*>(a.aux_out + oidx) = zk;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) outv[j] = gelu_f(outv[j]);
+          }
         }
         uint4 pk;
         __nv_bfloat162 h0 = __floats2bfloat162_rn(outv[0], outv[1]);
@@ -403,9 +453,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
         pk.y = *reinterpret_cast<uint32_t*>(&h1);
         pk.z = *reinterpret_cast<uint32_t*>(&h2);
         pk.w = *reinterpret_cast<uint32_t*>(&h3);
-        const int chunk = (co0 + cc) >> 3;
-        __nv_bfloat16* dst = a.out + ((((size_t)b * (a.cout_total / 8) + chunk) * N + gy) * N + x) * 8;
-        *reinterpret_cast<uint4*>(dst) = pk;
+        *reinterpret_cast<uint4*>(a.out + oidx) = pk;
       }
       tmem_fence_before_sync();
       mbar_arrive(c_empty + s);
@@ -486,6 +534,7 @@ __global__ void __launch_bounds__(256) conv_in_kernel(const ConvInArgs a) {
 // ---------------------------------------------------------------------------
 struct PackArgs {
   const float* const* hist;  // cin/2 pointers to [batch][2][N][N] states
+  const float* single;       // or (cin = 2) the one state directly, when non-null
   __nv_bfloat16* out;        // [batch][2][N][N][8]
   int batch, cin;
 };
@@ -500,7 +549,7 @@ __global__ void __launch_bounds__(256) pack_input_kernel(const PackArgs a) {
     float v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = 0.f;
-    for (int c = 0; c < a.cin; ++c) v[c] = a.hist[c >> 1][((size_t)b * 2 + (c & 1)) * N * N + pix];
+    for (int c = 0; c < a.cin; ++c) v[c] = (a.single ? a.single : a.hist[c >> 1])[((size_t)b * 2 + (c & 1)) * N * N + pix];
 #pragma unroll
     for (int c8 = 0; c8 < 2; ++c8) {
       uint4 pk;

@@ -33,6 +33,10 @@ struct LearnedState {
   size_t pk_stencil_first = 0; // first layer, input channels padded to 16
   size_t pk_tc[4] = {};
   size_t pk_tc_first = 0;
+  size_t pk_t[4] = {};         // data-gradient tiles of hidden layers 1..4 (transposed, flipped)
+  size_t pk_t5 = 0;            // data-gradient tiles of the last layer: 160 -> 64 in two parts of 32
+  size_t raw_off_w0t = 0;      // FP32 [2][64][3][3] transposed, flipped first layer
+  size_t raw_off_zero = 0;     // eight zeros
   __nv_bfloat16* act0 = nullptr;
   __nv_bfloat16* act1 = nullptr;
   __nv_bfloat16* coef = nullptr;
@@ -47,6 +51,27 @@ struct LearnedState {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   int sms = 0;
+};
+
+// Workspace of the reverse mode of one step (allocated by the first
+// fd_step_adjoint call): stage states, cotangents, and for the learned path
+// every network activation of the four stages plus weight-gradient partials.
+struct AdjointState {
+  float* wst[3] = {};          // stage states w2, w3, w4
+  float* acc = nullptr;        // RK accumulator of the recomputed forward stages
+  float* g = nullptr;          // P(lam_out)
+  float* rb = nullptr;         // tendency cotangent of the current stage
+  float* wbar = nullptr;       // state cotangent through the FV part
+  float* xbar = nullptr;       // state cotangent through the network input
+  float* zeros = nullptr;      // 80 zeros (W_L of a plain context)
+  __nv_bfloat16* h[4][6] = {}; // layer inputs per stage (h[s][0]: packed state, 16 channels)
+  __nv_bfloat16* z[4][5] = {}; // pre-activations of layers 0..4 per stage
+  __nv_bfloat16* coef[4] = {}; // network outputs per stage
+  __nv_bfloat16* cbar = nullptr;   // network-output cotangent (160 channels)
+  __nv_bfloat16* zbar[2] = {};     // hidden-layer cotangents (64 channels, ping-pong)
+  float* partial = nullptr;        // weight-gradient partial sums
+  float* partial_b = nullptr;
+  bool ready = false;
 };
 
 }  // namespace ldfv
@@ -67,6 +92,7 @@ struct fd_ctx {
   std::string err;
   ldfv::FvArgs base;
   ldfv::LearnedState* lrn = nullptr;
+  ldfv::AdjointState* adj = nullptr;
 };
 
 // shared helpers of the ABI translation units

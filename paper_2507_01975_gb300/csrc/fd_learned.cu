@@ -11,73 +11,12 @@
 #include "../../include/fd.h"
 #include "conv_tc.cuh"
 #include "fd_ctx.h"
+#include "fd_net.cuh"
 #include "fv_learned.cuh"
 
 using namespace ldfv;
 
 namespace {
-
-constexpr int kHidden = 64;
-constexpr int kCoef = 160;
-constexpr long long kSpin = 1ll << 20;
-
-int stencil_cin(int l) { return l == 0 ? 2 : kHidden; }
-int stencil_cout(int l) { return l == 5 ? kCoef : kHidden; }
-int tc_cin(int l, int kc) { return l == 0 ? 2 * kc : kHidden; }
-int tc_cout(int l) { return l == 5 ? 2 : kHidden; }
-
-// round to the nearest BF16 (ties to even), as the weights are rounded on upload
-uint16_t bf16_bits(float f) {
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  const uint32_t r = u + 0x7FFF + ((u >> 16) & 1);
-  return (uint16_t)(r >> 16);
-}
-
-// tensor-core tile of one conv layer part: [9 taps][cin_pad/8][cout_tile/8][8 co][8 ci]; input
-// channels cin .. cin_pad - 1 are zero
-void pack_part(const float* W, int cin, int cout_total, int co0, int cout_tile, uint16_t* dst, int cin_pad = 0) {
-  if (cin_pad == 0) cin_pad = cin;
-  for (int a = 0; a < 3; ++a)
-    for (int e = 0; e < 3; ++e) {
-      const int tap = a * 3 + e;
-      for (int c8 = 0; c8 < cin_pad / 8; ++c8)
-        for (int n8 = 0; n8 < cout_tile / 8; ++n8)
-          for (int n = 0; n < 8; ++n)
-            for (int k = 0; k < 8; ++k) {
-              const int co = co0 + n8 * 8 + n, ci = c8 * 8 + k;
-              const float w = ci < cin ? W[(((size_t)co * cin + ci) * 3 + a) * 3 + e] : 0.0f;
-              const size_t idx = ((((size_t)tap * (cin_pad / 8) + c8) * (cout_tile / 8) + n8) * 8 + n) * 8 + k;
-              dst[idx] = bf16_bits(w);
-            }
-      (void)cout_total;
-    }
-}
-
-size_t part_elems(int cin, int cout_tile) { return (size_t)9 * cin * cout_tile; }
-
-template <int LOGN, int COUT_TILE, int CIN = 64>
-cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __nv_bfloat16* wpack,
-                        const float* bias, __nv_bfloat16* out, int batch, int parts, int co_base, int cout_total,
-                        int gelu, cudaStream_t st) {
-  using Cfg = ConvCfg<LOGN, CIN, COUT_TILE>;
-  ConvArgs a;
-  a.in = in;
-  a.w = wpack;
-  a.bias = bias;
-  a.out = out;
-  a.batch = batch;
-  a.parts = parts;
-  a.co_base = co_base;
-  a.cout_total = cout_total;
-  a.gelu = gelu;
-  a.err = L.d_err;
-  a.spin_limit = kSpin;
-  const int ntiles = batch * (Cfg::N / Cfg::TROWS) * parts;
-  const int grid = ntiles < L.sms ? ntiles : L.sms;
-  conv3x3_tc_kernel<LOGN, CIN, COUT_TILE><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a);
-  return cudaGetLastError();
-}
 
 template <int LOGN>
 cudaError_t prepare_kernels() {
@@ -111,6 +50,7 @@ cudaError_t run_trunk(fd_ctx* c, const float* const* hist, int cin, size_t pk_fi
   // first layer on the tensor cores: inputs packed to 16 BF16 channels
   PackArgs pa;
   pa.hist = hist;
+  pa.single = nullptr;
   pa.out = L.act1;
   pa.batch = B;
   pa.cin = cin;
@@ -161,28 +101,6 @@ cudaError_t run_tc_net(fd_ctx* c, const float* const* hist, cudaStream_t st) {
   const int blocks = (int)((pix + 255) / 256 < (size_t)(4 * L.sms) ? (pix + 255) / 256 : (size_t)(4 * L.sms));
   conv_out2_kernel<LOGN><<<blocks, 256, 0, st>>>(oa);
   return cudaGetLastError();
-}
-
-LStageArgs stage_args(fd_ctx* c) {
-  LStageArgs a;
-  std::memset(&a, 0, sizeof a);
-  const FvArgs& b = c->base;
-  a.flow = c->grid.flow;
-  a.forcing = c->forcing.kind;
-  a.dord = c->opts.deriv_order;
-  a.dt = (float)b.dt;
-  a.nu = (float)b.nu;
-  a.idx = (float)b.idx;
-  a.idy = (float)b.idy;
-  a.drag = (float)b.drag;
-  a.inv_nn = (float)b.inv_nn;
-  a.tw = reinterpret_cast<const float2*>(b.tw);
-  a.symx = reinterpret_cast<const float*>(b.symx);
-  a.symy = reinterpret_cast<const float*>(b.symy);
-  a.frc = reinterpret_cast<const float*>(b.frc);
-  a.wl = c->lrn->d_raw + c->lrn->raw_off_wl;
-  a.acc = c->lrn->acc;
-  return a;
 }
 
 // One learned time step s_in -> s_out. ptr_in / ptr_w: device pointer arrays
@@ -371,6 +289,18 @@ fd_status fd_set_params(fd_ctx* c, const float* params, int64_t count, void* str
     pack_part(&raw[L.raw_off_sw[5]], 64, kCoef, 128, 32, &pk[o2]);
     L.pk_stencil_last32 = o2;
   }
+  // reverse-mode (data-gradient) tiles: transposed, flipped kernels
+  for (int l = 1; l <= 4; ++l) {
+    const size_t o = add(part_elems(64, 64));
+    pack_part_transposed(&raw[L.raw_off_sw[l]], 64, 64, 0, 64, &pk[o]);
+    L.pk_t[l - 1] = o;
+  }
+  {
+    const size_t o = add(2 * part_elems(kCoef, 32));
+    pack_part_transposed(&raw[L.raw_off_sw[5]], 64, kCoef, 0, 32, &pk[o]);
+    pack_part_transposed(&raw[L.raw_off_sw[5]], 64, kCoef, 32, 32, &pk[o + part_elems(kCoef, 32)]);
+    L.pk_t5 = o;
+  }
   if (L.kc > 0) {
     const size_t o = add(part_elems(16, 64));
     pack_part(&raw[L.raw_off_tw[0]], 2 * L.kc, 64, 0, 64, &pk[o], 16);
@@ -381,6 +311,17 @@ fd_status fd_set_params(fd_ctx* c, const float* params, int64_t count, void* str
       L.pk_tc[l - 1] = o2;
     }
   }
+  // after the parameters: the first layer's transposed, flipped kernel in FP32
+  // ([2][64][3][3], for its data gradient on CUDA cores) and a few zeros
+  L.raw_off_w0t = raw.size();
+  raw.resize(raw.size() + 2 * 64 * 9 + 8, 0.0f);
+  L.raw_off_zero = L.raw_off_w0t + 2 * 64 * 9;
+  for (int ci = 0; ci < 2; ++ci)
+    for (int o = 0; o < 64; ++o)
+      for (int a = 0; a < 3; ++a)
+        for (int e2 = 0; e2 < 3; ++e2)
+          raw[L.raw_off_w0t + ((ci * 64 + o) * 3 + a) * 3 + e2] =
+              raw[L.raw_off_sw[0] + ((o * 2 + ci) * 3 + (2 - a)) * 3 + (2 - e2)];
   cudaError_t e = cudaSuccess;
   if (!L.d_raw) e = cudaMalloc(&L.d_raw, raw.size() * sizeof(float));
   if (e == cudaSuccess && !L.d_wpack) e = cudaMalloc(&L.d_wpack, pk.size() * sizeof(uint16_t));

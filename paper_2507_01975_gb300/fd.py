@@ -32,6 +32,7 @@ EXPORTS = [
     "fd_param_count",
     "fd_set_params",
     "fd_network_forward",
+    "fd_step_adjoint",
     "fd_destroy",
     "fd_last_error",
     "fd_version",
@@ -103,6 +104,8 @@ def load(path: str = LIB_PATH):
     lib.fd_set_params.restype = C.c_int
     lib.fd_network_forward.argtypes = [vp, vp, vp, vp]
     lib.fd_network_forward.restype = C.c_int
+    lib.fd_step_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.fd_step_adjoint.restype = C.c_int
     lib.fd_check_finite_noalloc.argtypes = [vp, C.c_int64, i32, C.POINTER(C.c_int64), vp]
     lib.fd_check_finite_noalloc.restype = C.c_int
     lib.fd_destroy.argtypes = [vp]
@@ -214,6 +217,13 @@ class Solver:
 
     def network_forward(self, u, coef_out, stream=None):
         self._check(self.lib.fd_network_forward(self.h, _ptr(u), _ptr(coef_out), _stream_handle(stream)))
+
+    def step_adjoint(self, u_in, lam_out, lam_in, dparams=None, stream=None):
+        """lam_in = (du'/du)^T lam_out for u' = step(u_in); dparams (device
+        float32, fd_param_count values) accumulates (du'/dtheta)^T lam_out."""
+        dp = _ptr(dparams) if dparams is not None else None
+        self._check(self.lib.fd_step_adjoint(self.h, _ptr(u_in), _ptr(lam_out), _ptr(lam_in), dp,
+                                             _stream_handle(stream)))
 
     def last_launch_count(self) -> int:
         return int(self.lib.fd_last_launch_count(self.h))

@@ -216,6 +216,60 @@ def learned_measurement(fd, I, steps: int = 60):
     }
 
 
+def training_measurement(fd, I, iters: int = 5):
+    """Differentiable training (shear layer 64^2, batch 32, 32-step unrolled
+    rollouts through the hand-written adjoint, checkpoints every 8 steps, MSE,
+    Adam): milliseconds per training iteration and the rollout cell-updates per
+    second it sustains, timed with CUDA events."""
+    import torch
+
+    from paper_2507_01975_gb300.train import TrainConfig, Trainer
+
+    n, b, unroll, ckpt = 64, 32, 32, 8
+    nu, dt = 1e-3, 7e-3
+    st = I.random_conv_stack(4, 2, 64, 160, last_scale=0.05)
+    params = I.pack_params(I.random_wl(5, 1e-2), st)
+    s = fd.Solver(fd.Config(n=n, batch=b, dtype="f32", nu=nu, dt=dt, learned=True))
+    plain = fd.Solver(fd.Config(n=n, batch=b, dtype="f32", nu=nu, dt=dt))
+    u0 = torch.tensor(np.stack([I.shear_ic(n)] * b).astype(np.float32), device="cuda")
+    # labels: the plain coarse solver's rollout (stand-in for coarse-grained fine-grid states)
+    tgt = torch.empty((unroll, b, 2, n, n), device="cuda")
+    last = torch.empty_like(u0)
+    plain.rollout(u0, last, unroll, traj=tgt, save_every=1)
+    tr = Trainer(s, params, TrainConfig(unroll=unroll, ckpt_every=ckpt, lr=1e-4))
+    for _ in range(2):
+        tr.step(u0, tgt)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        loss = tr.step(u0, tgt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_iter = e0.elapsed_time(e1) / iters
+    # one step's reverse mode alone
+    lam = torch.ones_like(u0)
+    dp = torch.zeros(s.param_count(), device="cuda")
+    s.step_adjoint(u0, lam, lam, dp)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(iters):
+        s.step_adjoint(u0, lam, lam, dp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1) / iters
+    return {
+        "workload": "shear layer 64^2, batch 32, 32-step unrolled rollouts, checkpoints every 8 steps, MSE, Adam "
+                    "(labels: plain coarse rollout)",
+        "ms_per_iteration": ms_iter,
+        "value": n * n * b * unroll / (ms_iter * 1e-3),
+        "unit": "rollout cell-updates/s (forward + reverse mode + Adam)",
+        "ms_per_step_adjoint": ms_adj,
+        "loss": float(loss.item()),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,6 +278,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
+    ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
                     help="time steps per rollout (the workload's 2000 by default; smaller only for ncu captures)")
     args = ap.parse_args()
@@ -334,6 +389,7 @@ def main():
     }
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     learned = None if args.no_learned else learned_measurement(fd, I)
+    training = None if args.no_training else training_measurement(fd, I)
     line = {
         "metric": METRIC,
         "value": value,
@@ -362,6 +418,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "learned": learned,
+        "training": training,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -159,6 +159,11 @@ int64_t fd_param_count(const fd_ctx* ctx);
  * a context without the learned option. */
 fd_status fd_set_params(fd_ctx* ctx, const float* params, int64_t count, void* stream);
 
+/* Same as fd_set_params from a DEVICE float32 array (for optimisers that keep
+ * the parameters on the GPU): stream-ordered, no synchronisation; the array
+ * may be overwritten once the work queued on `stream` has run. */
+fd_status fd_set_params_device(fd_ctx* ctx, const float* params, int64_t count, void* stream);
+
 /* Stencil-network forward pass alone: coef_out[batch][160][ny][nx] (device,
  * float32) = C_theta(u) for the device state u. For tests and diagnostics. */
 fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* stream);
@@ -189,6 +194,49 @@ fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* 
  * pointers, dparams on a plain context or parameters not yet set. */
 fd_status fd_step_adjoint(fd_ctx* ctx, const void* u_in, const void* lam_out, void* lam_in, float* dparams,
                           void* stream);
+
+/* Reverse mode of an n-step rollout u_0 -> (u_1 .. u_n) with checkpoints:
+ * lam_traj[n][batch][2][ny][nx] holds the cotangents dL/du_k of the states
+ * after steps 1 .. n (device); lam0 receives dL/du_0; dparams (learned
+ * context, may be NULL) accumulates dL/dtheta. The forward pass keeps only the
+ * states u_0, u_k, u_2k, ... (k = ckpt_every) and each segment is recomputed
+ * before its steps are run backwards with fd_step_adjoint, so the memory
+ * is (n/k + k + 1) states plus one step's workspace. Same scope as
+ * fd_step_adjoint; the workspace grows on demand (allocating calls). */
+fd_status fd_rollout_adjoint(fd_ctx* ctx, const void* u0, int32_t n_steps, int32_t ckpt_every,
+                             const void* lam_traj, void* lam0, float* dparams, void* stream);
+
+/* One training step of the paper's objective (Sec. 4, Model Training): the
+ * rollout of n_steps from u0 is compared with targets[n][batch][2][ny][nx]
+ * (device, the coarse-grained labels of u_1 .. u_n) by the mean squared error
+ * over every step, trajectory and element; *loss (device double) receives the
+ * loss, dparams (device, fd_param_count values) accumulates its gradient.
+ * Checkpointing as in fd_rollout_adjoint. */
+fd_status fd_train_step(fd_ctx* ctx, const void* u0, const void* targets, int32_t n_steps, int32_t ckpt_every,
+                        float* dparams, double* loss, void* stream);
+
+/* *loss = mean((pred - target)^2) over `count` float32 device elements (FP64
+ * accumulation, fixed reduction order: deterministic); when grad is non-NULL,
+ * grad = 2 (pred - target) / count. Uses the context's workspace. */
+fd_status fd_mse_loss(fd_ctx* ctx, const float* pred, const float* target, int64_t count, double* loss,
+                      float* grad, void* stream);
+
+/* One Adam update (the optimiser of the paper's training; Kingma & Ba 2015)
+ * of `count` float32 device parameters: m, v are the caller-owned first and
+ * second moment buffers (zero before step t = 1), t >= 1 the step number.
+ * When zero_grads != 0 the gradient buffer is cleared after use.
+ * Context-free; errors are reported through fd_last_error(NULL). */
+fd_status fd_adam_step(float* params, float* grads, float* m, float* v, int64_t count, int32_t t, float lr,
+                       float beta1, float beta2, float eps, int32_t zero_grads, void* stream);
+
+/* Coarse-graining of fine-grid states into training labels (Sec. 4,
+ * Simulation Datasets; App. C.1): fine[batch][2][n_fine][n_fine] ->
+ * coarse[batch][2][n_fine/ratio][n_fine/ratio] by face averages: a coarse
+ * face value is the mean of the `ratio` fine face values that tile the coarse
+ * face, which keeps a divergence-free field divergence-free. dtype: fd_dtype.
+ * Context-free; errors are reported through fd_last_error(NULL). */
+fd_status fd_downsample(const void* fine, void* coarse, int32_t batch, int32_t n_fine, int32_t ratio,
+                        int32_t dtype, void* stream);
 
 /* Release the context and its device tables (synchronises the device). */
 fd_status fd_destroy(fd_ctx* ctx);

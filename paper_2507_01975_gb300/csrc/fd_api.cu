@@ -23,6 +23,7 @@ int64_t fd_learned_param_count(int kc);
 fd_status fd_learned_init(fd_ctx* c);
 void fd_learned_free(fd_ctx* c);
 void fd_adjoint_free(fd_ctx* c);
+void fd_train_free(fd_ctx* c);
 fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                              cudaStream_t st);
 fd_status fd_learned_error_flag(fd_ctx* c);
@@ -371,6 +372,7 @@ fd_status fd_destroy(fd_ctx* c) {
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_state) cudaFree(c->d_state);
   if (c->d_flag) cudaFree(c->d_flag);
+  fd_train_free(c);
   fd_adjoint_free(c);
   fd_learned_free(c);
   delete c;

@@ -37,6 +37,12 @@ struct LearnedState {
   size_t pk_t5 = 0;            // data-gradient tiles of the last layer: 160 -> 64 in two parts of 32
   size_t raw_off_w0t = 0;      // FP32 [2][64][3][3] transposed, flipped first layer
   size_t raw_off_zero = 0;     // eight zeros
+  size_t raw_total = 0;        // raw array length (parameters, w0t, zeros)
+  size_t pk_total = 0;         // packed tile elements
+  float* d_stage = nullptr;    // host-uploaded parameters before rounding / packing
+  void* d_desc = nullptr;      // tile recipe (one descriptor per tile)
+  uint32_t* d_ranges = nullptr;  // (offset, length) of every network weight array in the raw layout
+  int ndesc = 0, nranges = 0;
   __nv_bfloat16* act0 = nullptr;
   __nv_bfloat16* act1 = nullptr;
   __nv_bfloat16* coef = nullptr;
@@ -74,6 +80,17 @@ struct AdjointState {
   bool ready = false;
 };
 
+// Workspace of the rollout reverse mode and the training step: checkpoints
+// every k steps, the recomputed states of one segment, the running state
+// cotangent and the partial sums of the loss reduction.
+struct TrainState {
+  float* ckpt = nullptr;
+  float* seg = nullptr;
+  float* lam = nullptr;
+  double* partial = nullptr;
+  int nckpt = 0, nseg = 0;
+};
+
 }  // namespace ldfv
 
 struct fd_ctx {
@@ -93,6 +110,7 @@ struct fd_ctx {
   ldfv::FvArgs base;
   ldfv::LearnedState* lrn = nullptr;
   ldfv::AdjointState* adj = nullptr;
+  ldfv::TrainState* trn = nullptr;
 };
 
 // shared helpers of the ABI translation units

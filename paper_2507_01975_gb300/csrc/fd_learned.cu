@@ -149,6 +149,126 @@ __global__ void coef_unpack_kernel(const __nv_bfloat16* in, float* out, int batc
   }
 }
 
+// ---------------------------------------------------------------------------
+// parameter upload on the device: BF16 rounding of the network weights, the
+// first layer's transposed kernel in FP32, and every tensor-core weight tile
+// (forward tiles and the transposed, flipped tiles of the data gradients)
+// ---------------------------------------------------------------------------
+struct PackDesc {
+  uint32_t src_off;     // layer weights W[cout][cin][3][3] in the raw array
+  uint32_t dst_off;     // first element of the tile in the packed array
+  uint32_t count;       // 9 x cin_pad x cout_tile
+  uint32_t cin_tile;    // input channels of the tile that carry data
+  uint32_t cin_pad;     // input channels of the tile (multiple of 16)
+  uint32_t cout_tile;   // output channels of the tile
+  uint32_t co0;         // first output channel of the tile
+  uint32_t layer_cin;   // Cin of the layer
+  uint32_t transposed;  // 1: tile of the data gradient (transposed, flipped kernel)
+};
+
+__device__ __forceinline__ float round_bf16_dev(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void prep_raw_kernel(const float* params, float* raw, size_t nparams, const uint32_t* ranges, int nranges,
+                                size_t off_w0, size_t off_w0t, size_t off_zero) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nparams; k += (size_t)gridDim.x * blockDim.x) {
+    float v = params[k];
+    for (int r = 0; r < nranges; ++r)
+      if (k >= ranges[2 * r] && k < (size_t)ranges[2 * r] + ranges[2 * r + 1]) v = round_bf16_dev(v);
+    raw[k] = v;
+  }
+  // first layer, transposed and flipped: w0t[ci][o][t] = W0[o][ci][8 - t]
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * 64 * 9; k += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(k / 576), o = (int)((k / 9) % 64), t = (int)(k % 9);
+    raw[off_w0t + k] = round_bf16_dev(params[off_w0 + (o * 2 + ci) * 9 + 8 - t]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 8) raw[off_zero + threadIdx.x] = 0.f;
+}
+
+// tile element (tap, c8, n8, n, k): input channel ci = 8 c8 + k, output channel co = co0 + 8 n8 + n
+__global__ void pack_tiles_kernel(const float* raw, __nv_bfloat16* pk, const PackDesc* descs) {
+  const PackDesc d = descs[blockIdx.y];
+  const float* W = raw + d.src_off;
+  const uint32_t n8s = d.cout_tile / 8, c8s = d.cin_pad / 8;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < d.count; idx += gridDim.x * blockDim.x) {
+    const uint32_t k = idx & 7, n = (idx >> 3) & 7;
+    const uint32_t n8 = (idx >> 6) % n8s;
+    const uint32_t c8 = (idx / (64 * n8s)) % c8s;
+    const uint32_t tap = idx / (64 * n8s * c8s);
+    const uint32_t ci = c8 * 8 + k, co = d.co0 + n8 * 8 + n;
+    float v = 0.f;
+    if (ci < d.cin_tile)
+      v = d.transposed ? W[((size_t)ci * d.layer_cin + co) * 9 + (8 - tap)] : W[((size_t)co * d.layer_cin + ci) * 9 + tap];
+    pk[d.dst_off + idx] = __float2bfloat16_rn(v);
+  }
+}
+
+// raw offsets, tile offsets and the tile recipe of a context (fixed by k_c)
+void plan_layout(LearnedState& L, std::vector<PackDesc>& descs, std::vector<uint32_t>& ranges) {
+  size_t off = 0;
+  L.raw_off_wl = off;
+  off += 80;
+  for (int l = 0; l < 6; ++l) {
+    L.raw_off_sw[l] = off;
+    ranges.push_back((uint32_t)off);
+    ranges.push_back((uint32_t)(stencil_cout(l) * stencil_cin(l) * 9));
+    off += (size_t)stencil_cout(l) * stencil_cin(l) * 9;
+    L.raw_off_sb[l] = off;
+    off += stencil_cout(l);
+  }
+  if (L.kc > 0)
+    for (int l = 0; l < 6; ++l) {
+      L.raw_off_tw[l] = off;
+      ranges.push_back((uint32_t)off);
+      ranges.push_back((uint32_t)(tc_cout(l) * tc_cin(l, L.kc) * 9));
+      off += (size_t)tc_cout(l) * tc_cin(l, L.kc) * 9;
+      L.raw_off_tb[l] = off;
+      off += tc_cout(l);
+    }
+  L.raw_off_w0t = off;
+  off += 2 * 64 * 9;
+  L.raw_off_zero = off;
+  off += 8;
+  L.raw_total = off;
+  size_t pk = 0;
+  auto add = [&](size_t src, int cin_tile, int cin_pad, int cout_tile, int co0, int layer_cin, int tr) {
+    PackDesc d;
+    d.src_off = (uint32_t)src;
+    d.dst_off = (uint32_t)pk;
+    d.count = (uint32_t)(9 * cin_pad * cout_tile);
+    d.cin_tile = (uint32_t)cin_tile;
+    d.cin_pad = (uint32_t)cin_pad;
+    d.cout_tile = (uint32_t)cout_tile;
+    d.co0 = (uint32_t)co0;
+    d.layer_cin = (uint32_t)layer_cin;
+    d.transposed = (uint32_t)tr;
+    descs.push_back(d);
+    pk += d.count;
+    return (size_t)d.dst_off;
+  };
+  L.pk_stencil_first = add(L.raw_off_sw[0], 2, 16, 64, 0, 2, 0);
+  for (int l = 1; l <= 4; ++l) L.pk_stencil[l - 1] = add(L.raw_off_sw[l], 64, 64, 64, 0, 64, 0);
+  L.pk_stencil[4] = add(L.raw_off_sw[5], 64, 64, 64, 0, 64, 0);
+  add(L.raw_off_sw[5], 64, 64, 64, 64, 64, 0);
+  L.pk_stencil_last32 = add(L.raw_off_sw[5], 64, 64, 32, 128, 64, 0);
+  for (int l = 1; l <= 4; ++l) L.pk_t[l - 1] = add(L.raw_off_sw[l], 64, 64, 64, 0, 64, 1);
+  L.pk_t5 = add(L.raw_off_sw[5], kCoef, kCoef, 32, 0, 64, 1);
+  add(L.raw_off_sw[5], kCoef, kCoef, 32, 32, 64, 1);
+  if (L.kc > 0) {
+    L.pk_tc_first = add(L.raw_off_tw[0], 2 * L.kc, 16, 64, 0, 2 * L.kc, 0);
+    for (int l = 1; l <= 4; ++l) L.pk_tc[l - 1] = add(L.raw_off_tw[l], 64, 64, 64, 0, 64, 0);
+  }
+  L.pk_total = pk;
+}
+
+cudaError_t upload_params(LearnedState& L, const float* params, cudaStream_t st) {
+  prep_raw_kernel<<<2 * L.sms, 256, 0, st>>>(params, L.d_raw, (size_t)L.nparams, L.d_ranges, L.nranges,
+                                             L.raw_off_sw[0], L.raw_off_w0t, L.raw_off_zero);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  pack_tiles_kernel<<<dim3(32, L.ndesc), 256, 0, st>>>(L.d_raw, L.d_wpack, reinterpret_cast<const PackDesc*>(L.d_desc));
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -193,6 +313,19 @@ fd_status fd_learned_init(fd_ctx* c) {
   alloc((void**)&L->ring, state * L->nring);
   alloc((void**)&L->d_err, sizeof(unsigned));
   alloc((void**)&L->d_ptrs, sizeof(float*) * (L->nring + 1 + 8 * L->nring));
+  std::vector<PackDesc> descs;
+  std::vector<uint32_t> ranges;
+  plan_layout(*L, descs, ranges);
+  L->ndesc = (int)descs.size();
+  L->nranges = (int)(ranges.size() / 2);
+  alloc((void**)&L->d_raw, L->raw_total * sizeof(float));
+  alloc((void**)&L->d_wpack, L->pk_total * sizeof(__nv_bfloat16));
+  alloc((void**)&L->d_stage, (size_t)L->nparams * sizeof(float));
+  alloc(&L->d_desc, descs.size() * sizeof(PackDesc));
+  alloc((void**)&L->d_ranges, ranges.size() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(L->d_desc, descs.data(), descs.size() * sizeof(PackDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(L->d_ranges, ranges.data(), ranges.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(L->d_err, 0, sizeof(unsigned));
   if (e == cudaSuccess) {
     // pointer arrays: [0, nring) single ring slots, [nring] wbuf, then k_c-long
@@ -215,8 +348,9 @@ void fd_learned_free(fd_ctx* c) {
   if (!L) return;
   if (L->graph) cudaGraphExecDestroy(L->graph);
   if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
-  void* ps[] = {L->d_raw, L->d_wpack, L->act0, L->act1, L->coef, L->acc, L->wbuf, L->corr, L->ring,
-                (void*)L->d_ptrs, L->d_err};
+  void* ps[] = {L->d_raw,  L->d_wpack, L->d_stage, L->d_desc,         (void*)L->d_ranges, L->act0, L->act1,
+                L->coef,   L->acc,     L->wbuf,    L->corr,           L->ring,            (void*)L->d_ptrs,
+                L->d_err};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete L;
@@ -235,102 +369,26 @@ fd_status fd_set_params(fd_ctx* c, const float* params, int64_t count, void* str
   if (count != L.nparams)
     return fd_set_error(c, FD_EINVAL, "fd_set_params: expected %lld values, got %lld", (long long)L.nparams,
                         (long long)count);
-  // raw offsets
-  size_t off = 0;
-  L.raw_off_wl = off;
-  off += 80;
-  for (int l = 0; l < 6; ++l) {
-    L.raw_off_sw[l] = off;
-    off += (size_t)stencil_cout(l) * stencil_cin(l) * 9;
-    L.raw_off_sb[l] = off;
-    off += stencil_cout(l);
-  }
-  if (L.kc > 0)
-    for (int l = 0; l < 6; ++l) {
-      L.raw_off_tw[l] = off;
-      off += (size_t)tc_cout(l) * tc_cin(l, L.kc) * 9;
-      L.raw_off_tb[l] = off;
-      off += tc_cout(l);
-    }
-  // network weights rounded to BF16 everywhere (also for the CUDA-core layers)
-  std::vector<float> raw(params, params + count);
-  auto round_range = [&](size_t o, size_t n) {
-    for (size_t k = 0; k < n; ++k) {
-      const uint32_t b = (uint32_t)bf16_bits(raw[o + k]) << 16;
-      std::memcpy(&raw[o + k], &b, 4);
-    }
-  };
-  for (int l = 0; l < 6; ++l) round_range(L.raw_off_sw[l], (size_t)stencil_cout(l) * stencil_cin(l) * 9);
-  if (L.kc > 0)
-    for (int l = 0; l < 6; ++l) round_range(L.raw_off_tw[l], (size_t)tc_cout(l) * tc_cin(l, L.kc) * 9);
-  // tensor-core tiles
-  std::vector<uint16_t> pk;
-  auto add = [&](size_t elems) {
-    const size_t o = pk.size();
-    pk.resize(o + elems);
-    return o;
-  };
-  {
-    const size_t o = add(part_elems(16, 64));
-    pack_part(&raw[L.raw_off_sw[0]], 2, 64, 0, 64, &pk[o], 16);
-    L.pk_stencil_first = o;
-  }
-  for (int l = 1; l <= 4; ++l) {
-    const size_t o = add(part_elems(64, 64));
-    pack_part(&raw[L.raw_off_sw[l]], 64, 64, 0, 64, &pk[o]);
-    L.pk_stencil[l - 1] = o;
-  }
-  {
-    const size_t o = add(2 * part_elems(64, 64));
-    pack_part(&raw[L.raw_off_sw[5]], 64, kCoef, 0, 64, &pk[o]);
-    pack_part(&raw[L.raw_off_sw[5]], 64, kCoef, 64, 64, &pk[o + part_elems(64, 64)]);
-    L.pk_stencil[4] = o;
-    const size_t o2 = add(part_elems(64, 32));
-    pack_part(&raw[L.raw_off_sw[5]], 64, kCoef, 128, 32, &pk[o2]);
-    L.pk_stencil_last32 = o2;
-  }
-  // reverse-mode (data-gradient) tiles: transposed, flipped kernels
-  for (int l = 1; l <= 4; ++l) {
-    const size_t o = add(part_elems(64, 64));
-    pack_part_transposed(&raw[L.raw_off_sw[l]], 64, 64, 0, 64, &pk[o]);
-    L.pk_t[l - 1] = o;
-  }
-  {
-    const size_t o = add(2 * part_elems(kCoef, 32));
-    pack_part_transposed(&raw[L.raw_off_sw[5]], 64, kCoef, 0, 32, &pk[o]);
-    pack_part_transposed(&raw[L.raw_off_sw[5]], 64, kCoef, 32, 32, &pk[o + part_elems(kCoef, 32)]);
-    L.pk_t5 = o;
-  }
-  if (L.kc > 0) {
-    const size_t o = add(part_elems(16, 64));
-    pack_part(&raw[L.raw_off_tw[0]], 2 * L.kc, 64, 0, 64, &pk[o], 16);
-    L.pk_tc_first = o;
-    for (int l = 1; l <= 4; ++l) {
-      const size_t o2 = add(part_elems(64, 64));
-      pack_part(&raw[L.raw_off_tw[l]], 64, 64, 0, 64, &pk[o2]);
-      L.pk_tc[l - 1] = o2;
-    }
-  }
-  // after the parameters: the first layer's transposed, flipped kernel in FP32
-  // ([2][64][3][3], for its data gradient on CUDA cores) and a few zeros
-  L.raw_off_w0t = raw.size();
-  raw.resize(raw.size() + 2 * 64 * 9 + 8, 0.0f);
-  L.raw_off_zero = L.raw_off_w0t + 2 * 64 * 9;
-  for (int ci = 0; ci < 2; ++ci)
-    for (int o = 0; o < 64; ++o)
-      for (int a = 0; a < 3; ++a)
-        for (int e2 = 0; e2 < 3; ++e2)
-          raw[L.raw_off_w0t + ((ci * 64 + o) * 3 + a) * 3 + e2] =
-              raw[L.raw_off_sw[0] + ((o * 2 + ci) * 3 + (2 - a)) * 3 + (2 - e2)];
-  cudaError_t e = cudaSuccess;
-  if (!L.d_raw) e = cudaMalloc(&L.d_raw, raw.size() * sizeof(float));
-  if (e == cudaSuccess && !L.d_wpack) e = cudaMalloc(&L.d_wpack, pk.size() * sizeof(uint16_t));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_raw, raw.data(), raw.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(L.d_wpack, pk.data(), pk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(L.d_stage, params, (size_t)count * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = upload_params(L, L.d_stage, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_set_params: %s", cudaGetErrorString(e));
+  L.ready = true;
+  return FD_OK;
+}
+
+fd_status fd_set_params_device(fd_ctx* c, const float* params, int64_t count, void* stream) {
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_set_params_device: null context");
+  if (!c->lrn)
+    return fd_set_error(c, FD_EINVAL, "fd_set_params_device: context was created without the learned option");
+  if (!params) return fd_set_error(c, FD_EINVAL, "fd_set_params_device: null parameter array");
+  LearnedState& L = *c->lrn;
+  if (count != L.nparams)
+    return fd_set_error(c, FD_EINVAL, "fd_set_params_device: expected %lld values, got %lld", (long long)L.nparams,
+                        (long long)count);
+  cudaError_t e = upload_params(L, params, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_set_params_device: %s", cudaGetErrorString(e));
   L.ready = true;
   return FD_OK;
 }

@@ -31,8 +31,14 @@ EXPORTS = [
     "fd_last_launch_count",
     "fd_param_count",
     "fd_set_params",
+    "fd_set_params_device",
     "fd_network_forward",
     "fd_step_adjoint",
+    "fd_rollout_adjoint",
+    "fd_train_step",
+    "fd_mse_loss",
+    "fd_adam_step",
+    "fd_downsample",
     "fd_destroy",
     "fd_last_error",
     "fd_version",
@@ -102,10 +108,22 @@ def load(path: str = LIB_PATH):
     lib.fd_param_count.restype = C.c_int64
     lib.fd_set_params.argtypes = [vp, vp, C.c_int64, vp]
     lib.fd_set_params.restype = C.c_int
+    lib.fd_set_params_device.argtypes = [vp, vp, C.c_int64, vp]
+    lib.fd_set_params_device.restype = C.c_int
     lib.fd_network_forward.argtypes = [vp, vp, vp, vp]
     lib.fd_network_forward.restype = C.c_int
     lib.fd_step_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.fd_step_adjoint.restype = C.c_int
+    lib.fd_rollout_adjoint.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+    lib.fd_rollout_adjoint.restype = C.c_int
+    lib.fd_train_step.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp]
+    lib.fd_train_step.restype = C.c_int
+    lib.fd_mse_loss.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
+    lib.fd_mse_loss.restype = C.c_int
+    lib.fd_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, i32, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]
+    lib.fd_adam_step.restype = C.c_int
+    lib.fd_downsample.argtypes = [vp, vp, i32, i32, i32, i32, vp]
+    lib.fd_downsample.restype = C.c_int
     lib.fd_check_finite_noalloc.argtypes = [vp, C.c_int64, i32, C.POINTER(C.c_int64), vp]
     lib.fd_check_finite_noalloc.restype = C.c_int
     lib.fd_destroy.argtypes = [vp]
@@ -215,6 +233,10 @@ class Solver:
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
         self._check(self.lib.fd_set_params(self.h, p.ctypes.data, int(p.size), _stream_handle(stream)))
 
+    def set_params_device(self, params, stream=None):
+        """Upload the learnable parameters from a device float32 tensor (no synchronisation)."""
+        self._check(self.lib.fd_set_params_device(self.h, _ptr(params), int(params.numel()), _stream_handle(stream)))
+
     def network_forward(self, u, coef_out, stream=None):
         self._check(self.lib.fd_network_forward(self.h, _ptr(u), _ptr(coef_out), _stream_handle(stream)))
 
@@ -224,6 +246,22 @@ class Solver:
         dp = _ptr(dparams) if dparams is not None else None
         self._check(self.lib.fd_step_adjoint(self.h, _ptr(u_in), _ptr(lam_out), _ptr(lam_in), dp,
                                              _stream_handle(stream)))
+
+    def rollout_adjoint(self, u0, n_steps: int, ckpt_every: int, lam_traj, lam0, dparams=None, stream=None):
+        """lam0 = dL/du0 for the cotangents lam_traj of the states after steps 1..n."""
+        dp = _ptr(dparams) if dparams is not None else None
+        self._check(self.lib.fd_rollout_adjoint(self.h, _ptr(u0), int(n_steps), int(ckpt_every), _ptr(lam_traj),
+                                                _ptr(lam0), dp, _stream_handle(stream)))
+
+    def train_step(self, u0, targets, n_steps: int, ckpt_every: int, dparams, loss, stream=None):
+        """MSE of the n-step rollout against targets -> loss (device float64), dparams += gradient."""
+        self._check(self.lib.fd_train_step(self.h, _ptr(u0), _ptr(targets), int(n_steps), int(ckpt_every),
+                                           _ptr(dparams), _ptr(loss), _stream_handle(stream)))
+
+    def mse_loss(self, pred, target, loss, grad=None, stream=None):
+        g = _ptr(grad) if grad is not None else None
+        self._check(self.lib.fd_mse_loss(self.h, _ptr(pred), _ptr(target), int(pred.numel()), _ptr(loss), g,
+                                         _stream_handle(stream)))
 
     def last_launch_count(self) -> int:
         return int(self.lib.fd_last_launch_count(self.h))
@@ -238,6 +276,30 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _check_free(lib, st):
+    if st != FD_OK:
+        raise FdError(st, lib.fd_last_error(None).decode())
+
+
+def adam_step(params, grads, m, v, t: int, lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8, zero_grads: bool = True, stream=None):
+    """One Adam update of device float32 tensors (fd_adam_step)."""
+    lib = load()
+    _check_free(lib, lib.fd_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(params.numel()), int(t),
+                                      float(lr), float(beta1), float(beta2), float(eps), 1 if zero_grads else 0,
+                                      _stream_handle(stream)))
+
+
+def downsample(fine, coarse, ratio: int, stream=None):
+    """Face-average coarse-graining fine[B,2,n,n] -> coarse[B,2,n/ratio,n/ratio] (fd_downsample)."""
+    import torch
+
+    lib = load()
+    dt = FD_F64 if fine.dtype == torch.float64 else FD_F32
+    _check_free(lib, lib.fd_downsample(_ptr(fine), _ptr(coarse), int(fine.shape[0]), int(fine.shape[-1]), int(ratio),
+                                       dt, _stream_handle(stream)))
 
 
 def version() -> str:

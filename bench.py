@@ -270,6 +270,30 @@ def training_measurement(fd, I, iters: int = 5):
     }
 
 
+def adjoint_measurement(fd, I, iters: int = 5):
+    """Reverse mode of one learned step (shear layer 64^2, batch 32) alone."""
+    import torch
+
+    n, b = 64, 32
+    st = I.random_conv_stack(4, 2, 64, 160, last_scale=0.05)
+    s = fd.Solver(fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=7e-3, learned=True))
+    s.set_params(I.pack_params(I.random_wl(5, 1e-2), st))
+    u0 = torch.tensor(np.stack([I.shear_ic(n)] * b).astype(np.float32), device="cuda")
+    lam = torch.ones_like(u0)
+    dp = torch.zeros(s.param_count(), device="cuda")
+    s.step_adjoint(u0, lam, lam, dp)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        s.step_adjoint(u0, lam, lam, dp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return {"workload": "reverse mode of one learned step, shear layer 64^2, batch 32",
+            "ms_per_step_adjoint": e0.elapsed_time(e1) / iters, "launches_per_call": s.last_launch_count()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,6 +303,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--only", choices=["learned", "training", "adjoint"],
+                    help="run one side measurement alone and print its JSON (for profiling)")
+    ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
     ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
                     help="time steps per rollout (the workload's 2000 by default; smaller only for ncu captures)")
     args = ap.parse_args()
@@ -290,6 +317,16 @@ def main():
     from paper_2507_01975_gb300 import build as B
     from paper_2507_01975_gb300 import fd
     from paper_2507_01975_gb300 import inputs as I
+
+    if args.only:
+        torch.cuda.set_device(0)
+        B.build()
+        fd.load()
+        fn = {"learned": lambda: learned_measurement(fd, I, steps=max(args.iters, 4)),
+              "training": lambda: training_measurement(fd, I, iters=args.iters),
+              "adjoint": lambda: adjoint_measurement(fd, I, iters=args.iters)}[args.only]
+        print(json.dumps(fn()), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -55,8 +55,12 @@ typedef enum { FD_F32 = 0, FD_F64 = 1 } fd_dtype;
  * equation with a pressure projection after every RK sub-step. */
 typedef enum { FD_BURGERS = 0, FD_NAVIER_STOKES = 1 } fd_flow;
 
-/* Grid: nx = ny = N with N a power of two in [8, 256] (this build), box
- * [0, lx] x [0, ly], `batch` independent trajectories. */
+/* Grid: nx = ny = N with N a power of two in [8, 2048], box [0, lx] x [0, ly],
+ * `batch` independent trajectories. Two plain paths: the on-chip rollout
+ * kernel (one thread-block cluster per trajectory holds the state in shared
+ * and tensor memory for the whole rollout; FP32 N <= 256, FP64 N <= 128) and
+ * the streaming path for larger grids (FP32, N up to 2048: tiled flux kernels
+ * and a three-pass FFT projection through HBM, one CUDA graph per step). */
 typedef struct {
   int32_t nx, ny;
   double lx, ly;
@@ -83,6 +87,9 @@ typedef struct {
   int32_t poisson_symbol; /* 0 = discrete D2 G2 symbol (default, exact projection) */
   int32_t ckpt_every;     /* reserved for the adjoint: checkpoint interval */
   int64_t spin_limit;     /* reserved: iteration limit of bounded device waits */
+  int32_t path;           /* 0 = automatic (default): on chip where built (FP32 N <= 256,
+                             FP64 N <= 128), streaming through HBM otherwise;
+                             1 = on chip only; 2 = streaming (FP32, N in [32, 2048]) */
 } fd_options;
 
 typedef struct fd_ctx fd_ctx; /* opaque, library-owned */
@@ -105,8 +112,10 @@ fd_status fd_step(fd_ctx* ctx, const void* u_in, void* u_out, void* stream);
 /* n_steps time steps from u0 (device), result in u_final (device; may alias
  * u0). When save_every > 0 and traj != NULL, the state after steps
  * save_every, 2 save_every, ... is written to traj[s][batch][2][ny][nx]
- * (n_steps / save_every snapshots). The whole rollout runs in one kernel
- * launch with the state resident in on-chip memory. */
+ * (n_steps / save_every snapshots). On the on-chip path the whole rollout is
+ * one kernel launch with the state resident on chip; on the streaming path a
+ * step is 17 launches replayed as a CUDA graph (direct launches when
+ * snapshots are taken). */
 fd_status fd_rollout(fd_ctx* ctx, const void* u0, void* traj, void* u_final, int32_t n_steps,
                      int32_t save_every, void* stream);
 

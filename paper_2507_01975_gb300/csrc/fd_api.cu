@@ -27,6 +27,12 @@ void fd_train_free(fd_ctx* c);
 fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                              cudaStream_t st);
 fd_status fd_learned_error_flag(fd_ctx* c);
+// streaming path (fd_large.cu)
+bool fd_large_supported(int dtype, int n);
+fd_status fd_large_init(fd_ctx* c);
+void fd_large_free(fd_ctx* c);
+fd_status fd_large_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
+                           cudaStream_t st);
 
 namespace {
 
@@ -196,7 +202,7 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown flow");
   if (!(dt > 0) || !std::isfinite(dt)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: dt must be positive");
   if (!(nu >= 0) || !std::isfinite(nu)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
-  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26};
+  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0};
   if (opts) o = *opts;
   if (o.deriv_order != 2 && o.deriv_order != 4)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
@@ -209,11 +215,20 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   if (g.nx != g.ny) return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: only square grids are built");
   if (o.learned != 0 && o.learned != 1) return fd_set_error(nullptr, FD_EINVAL, "fd_init: learned must be 0 or 1");
   if (!o.learned && o.k_c) return fd_set_error(nullptr, FD_EINVAL, "fd_init: k_c needs the learned option");
+  if (o.path < 0 || o.path > 2) return fd_set_error(nullptr, FD_EINVAL, "fd_init: path must be 0, 1 or 2");
   int logn = 0;
   while ((1 << logn) < g.nx) ++logn;
   Launcher L;
-  if (!pick_launcher(g.dtype, logn, o.deriv_order, &L))
-    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: no on-chip kernel for N=%d dtype=%d", g.nx, g.dtype);
+  const bool onchip = o.path != 2 && pick_launcher(g.dtype, logn, o.deriv_order, &L);
+  if (!onchip) {
+    if (o.path == 1)
+      return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: no on-chip kernel for N=%d dtype=%d", g.nx, g.dtype);
+    if (!fd_large_supported(g.dtype, g.nx))
+      return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: no kernel for N=%d dtype=%d (the streaming path is FP32, "
+                          "N in [32, 2048])", g.nx, g.dtype);
+    if (o.learned)
+      return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: the learned path runs on chip (N = 32 or 64)");
+  }
 
   fd_ctx* c = new (std::nothrow) fd_ctx();
   if (!c) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: out of host memory");
@@ -236,7 +251,7 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_ENOMEM, "fd_init: cudaMalloc: %s", cudaGetErrorString(e));
   }
   e = cudaMemcpy(c->d_tables, host.data(), host.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = L.prepare(L.smem);
+  if (e == cudaSuccess && onchip) e = L.prepare(L.smem);
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
     delete c;
@@ -260,6 +275,15 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   a.symx = base + c->off_symx;
   a.symy = base + c->off_symy;
   a.frc = base + c->off_frc;
+  if (!onchip) {
+    fd_status ls = fd_large_init(c);
+    if (ls != FD_OK) {
+      fd_large_free(c);
+      cudaFree(c->d_tables);
+      delete c;
+      return ls;
+    }
+  }
   if (o.learned) {
     fd_status ls = fd_learned_init(c);
     if (ls != FD_OK) {
@@ -282,6 +306,7 @@ fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32
   if (save_every < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every must be >= 0");
   if (save_every > 0 && !traj) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every > 0 needs traj");
   if (c->lrn) return fd_learned_rollout(c, u0, traj, u_final, n_steps, save_every, static_cast<cudaStream_t>(stream));
+  if (c->big) return fd_large_rollout(c, u0, traj, u_final, n_steps, save_every, static_cast<cudaStream_t>(stream));
   FvArgs a = c->base;
   a.u_in = u0;
   a.u_out = u_final;
@@ -375,6 +400,7 @@ fd_status fd_destroy(fd_ctx* c) {
   fd_train_free(c);
   fd_adjoint_free(c);
   fd_learned_free(c);
+  fd_large_free(c);
   delete c;
   return FD_OK;
 }

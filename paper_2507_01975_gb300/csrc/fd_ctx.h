@@ -80,6 +80,18 @@ struct AdjointState {
   bool ready = false;
 };
 
+// Buffers of the streaming (HBM) path for large grids.
+struct LargeState {
+  float* un = nullptr;         // state
+  float* acc = nullptr;        // RK accumulator
+  float* wsA = nullptr;        // stage results w* (ping-pong: a stage reads the previous one with halos)
+  float* wsB = nullptr;
+  float* p = nullptr;          // pressure of the latest projection
+  void* spec = nullptr;        // [batch][N/2 + 1][N] complex half spectra, column-major
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;  // one step
+};
+
 // Workspace of the rollout reverse mode and the training step: checkpoints
 // every k steps, the recomputed states of one segment, the running state
 // cotangent and the partial sums of the loss reduction.
@@ -111,6 +123,7 @@ struct fd_ctx {
   ldfv::LearnedState* lrn = nullptr;
   ldfv::AdjointState* adj = nullptr;
   ldfv::TrainState* trn = nullptr;
+  ldfv::LargeState* big = nullptr;   // set when the streaming path runs this context
 };
 
 // shared helpers of the ABI translation units

@@ -70,6 +70,7 @@ class FdOptions(C.Structure):
         ("poisson_symbol", C.c_int32),
         ("ckpt_every", C.c_int32),
         ("spin_limit", C.c_int64),
+        ("path", C.c_int32),
     ]
 
 
@@ -156,6 +157,7 @@ class Config:
     poisson_symbol: int = 0
     learned: bool = False
     k_c: int = 0
+    path: int = 0  # 0 automatic, 1 on chip, 2 streaming through HBM
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -181,7 +183,7 @@ class Solver:
         g = FdGrid(cfg.n, cfg.n, cfg.lx, cfg.ly, cfg.batch, FD_F64 if cfg.dtype == "f64" else FD_F32,
                    FD_BURGERS if cfg.flow == "burgers" else FD_NAVIER_STOKES)
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
-        o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26)
+        o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26, cfg.path)
         h = C.c_void_p()
         st = self.lib.fd_init(C.byref(g), cfg.nu, cfg.dt, C.byref(f), C.byref(o), C.byref(h))
         if st != FD_OK:

@@ -1,0 +1,104 @@
+"""GPU parity of the streaming (HBM) plain-FV path for large grids against the
+FP64 oracle, and against the on-chip path where both exist.
+
+Tolerances: one FP32 step <= 1e-6 relative L2 (the stated per-step bound);
+10 steps <= 1e-5; streaming vs on-chip FP32 after 20 steps <= 1e-5 (two FP32
+evaluations with different summation orders); projected fields keep the
+discrete divergence below 1e-5 max|u| / dx (FP32 round-off of a 2048-point FFT).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2507_01975_gb300 import fd
+from paper_2507_01975_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_01975_gb300 import build
+
+    build.build()
+    fd.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def problem(cfg):
+    return O.Problem(nx=cfg.n, ny=cfg.n, nu=cfg.nu, dt=cfg.dt,
+                     flow=O.FLOW_BURGERS if cfg.flow == "burgers" else O.FLOW_NAVIER_STOKES,
+                     forcing_kind=1 if cfg.forcing == "kolmogorov" else 0, deriv_order=cfg.deriv_order)
+
+
+def run(cfg, U0, steps, **kw):
+    s = fd.Solver(cfg)
+    u = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(u)
+    s.rollout(u, out, steps, **kw)
+    torch.cuda.synchronize()
+    return s, out
+
+
+@pytest.mark.parametrize("flow,forcing,dord", [("ns", None, 4), ("ns", "kolmogorov", 4), ("burgers", None, 2)])
+def test_streaming_step_matches_oracle(flow, forcing, dord):
+    n, b = 64, 2
+    cfg = fd.Config(n=n, batch=b, dtype="f32", flow=flow, forcing=forcing, nu=2e-3, dt=5e-3, deriv_order=dord, path=2)
+    U0 = I.ic_batch("burgers" if flow == "burgers" else "kolmogorov", n, b, seed0=2)
+    _, out = run(cfg, U0, 1)
+    p = problem(cfg)
+    U32 = U0.astype(np.float32).astype(np.float64)
+    ref = np.stack([O.rk4_step(U32[k], p) for k in range(b)])
+    assert rel_l2(out.double().cpu().numpy(), ref) <= 1e-6
+    _, out10 = run(cfg, U0, 10)
+    ref10 = np.stack([O.rollout(U32[k], p, 10)[0] for k in range(b)])
+    assert rel_l2(out10.double().cpu().numpy(), ref10) <= 1e-5
+
+
+def test_streaming_equals_on_chip_at_256():
+    n, b = 256, 2
+    U0 = I.ic_batch("decaying", n, b, seed0=4)
+    a = run(fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=1.75e-3, path=2), U0, 20)[1]
+    c = run(fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=1.75e-3, path=1), U0, 20)[1]
+    assert rel_l2(a.double().cpu().numpy(), c.double().cpu().numpy()) <= 1e-5
+
+
+def test_streaming_step_matches_oracle_at_1024():
+    n = 1024
+    cfg = fd.Config(n=n, batch=1, dtype="f32", nu=1e-3, dt=4.4e-4, forcing="kolmogorov")
+    U0 = I.kolmogorov_ic(n, 7)[None]
+    s, out = run(cfg, U0, 1)
+    assert s.last_launch_count() == 17
+    ref = O.rk4_step(U0[0].astype(np.float32).astype(np.float64), problem(cfg))
+    assert rel_l2(out[0].double().cpu().numpy(), ref) <= 1e-6
+
+
+def test_streaming_2048_properties_and_snapshots():
+    # full size of the fine-grid reference: divergence after projection, mean
+    # momentum, and snapshot rollouts equal to graph-replayed rollouts
+    n = 2048
+    cfg = fd.Config(n=n, batch=1, dtype="f32", nu=1e-3, dt=2.19e-4)
+    U0 = I.decaying_ic(n, 1)[None].astype(np.float32)
+    s = fd.Solver(cfg)
+    u = torch.tensor(U0, device="cuda")
+    a = torch.empty_like(u)
+    s.rollout(u, a, 4)
+    traj = torch.empty((2,) + tuple(u.shape), device="cuda")
+    c = torch.empty_like(u)
+    s.rollout(u, c, 4, traj=traj, save_every=2)
+    torch.cuda.synchronize()
+    assert torch.equal(a, c) and torch.equal(traj[-1], c)
+    g = a[0].double().cpu().numpy()
+    h = 2 * np.pi / n
+    assert np.max(np.abs(O.divergence(g, h, h))) <= 1e-5 * np.max(np.abs(g)) / h
+    for k in range(2):
+        assert abs(g[k].mean() - U0[0, k].astype(np.float64).mean()) <= 1e-6
+    assert s.check_finite(a)

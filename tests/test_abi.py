@@ -91,6 +91,16 @@ def test_calls_on_null_context_are_rejected(lib):
     assert lib.fd_last_launch_count(None) == 0
 
 
-def test_oversized_grid_is_unsupported_not_invalid(lib):
-    st, _ = _init(lib, n=512)
+def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):
+    # FP64 runs on chip only (N <= 128); the streaming path is FP32
+    st, _ = _init(lib, n=512, dtype=fd.FD_F64)
     assert st == fd.FD_EUNSUPPORTED
+    # forcing the on-chip path beyond its sizes
+    st, _ = _init(lib, n=512, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 1))
+    assert st == fd.FD_EUNSUPPORTED
+    # the learned path is on chip only
+    st, _ = _init(lib, n=512, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
+    assert st == fd.FD_EUNSUPPORTED
+    # an unknown path value is invalid
+    st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 3))
+    assert st == fd.FD_EINVAL

@@ -270,6 +270,45 @@ def training_measurement(fd, I, iters: int = 5):
     }
 
 
+# algorithmic HBM bytes per cell and time step of the streaming path (FP32):
+# stage kernels 32 + 44 + 44 + 36, projections 4 x (12 + 8 + 8), final 20
+STREAM_BYTES_PER_CELL_STEP = 288
+
+
+def fine_measurement(fd, I, steps: int = 40):
+    """Plain FV 2048^2 FP32, one trajectory, streaming path (the fine-grid
+    reference): cell-updates/s and the whole step's effective HBM bandwidth
+    against the measured copy bandwidth."""
+    import torch
+
+    n = 2048
+    s = fd.Solver(fd.Config(n=n, batch=1, dtype="f32", nu=1e-3, dt=2.19e-4))
+    u = torch.tensor(I.decaying_ic(n, 0)[None].astype(np.float32), device="cuda")
+    o = torch.empty_like(u)
+    s.rollout(u, o, 4)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.rollout(u, o, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    gbs = STREAM_BYTES_PER_CELL_STEP * n * n / (ms * 1e-3) / 1e9
+    peak = _measured_peaks().get("hbm_gbs") or 6800.0
+    return {
+        "workload": "decaying NS 2048^2, batch 1, FP32, streaming path (17 launches per step, CUDA graph)",
+        "value": n * n / (ms * 1e-3),
+        "unit": "cell-updates/s",
+        "ms_per_time_step": ms,
+        "finite": bool(s.check_finite(o)),
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                     "traffic": None, "kernel": "whole step (stage, FFT and final kernels)",
+                     "algorithmic_bytes_per_cell_step": STREAM_BYTES_PER_CELL_STEP,
+                     "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"},
+    }
+
+
 def adjoint_measurement(fd, I, iters: int = 5):
     """Reverse mode of one learned step (shear layer 64^2, batch 32) alone."""
     import torch
@@ -303,7 +342,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
-    ap.add_argument("--only", choices=["learned", "training", "adjoint"],
+    ap.add_argument("--no-fine", action="store_true", help="skip the 2048^2 streaming-path measurement")
+    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
     ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
@@ -324,7 +364,8 @@ def main():
         fd.load()
         fn = {"learned": lambda: learned_measurement(fd, I, steps=max(args.iters, 4)),
               "training": lambda: training_measurement(fd, I, iters=args.iters),
-              "adjoint": lambda: adjoint_measurement(fd, I, iters=args.iters)}[args.only]
+              "adjoint": lambda: adjoint_measurement(fd, I, iters=args.iters),
+              "fine": lambda: fine_measurement(fd, I, steps=max(args.iters, 2))}[args.only]
         print(json.dumps(fn()), flush=True)
         return
 
@@ -427,6 +468,7 @@ def main():
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     learned = None if args.no_learned else learned_measurement(fd, I)
     training = None if args.no_training else training_measurement(fd, I)
+    fine = None if args.no_fine else fine_measurement(fd, I)
     line = {
         "metric": METRIC,
         "value": value,
@@ -456,6 +498,7 @@ def main():
         "clocks": clocks,
         "learned": learned,
         "training": training,
+        "fine_grid": fine,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -87,7 +87,7 @@ struct LargeState {
   float* wsA = nullptr;        // stage results w* (ping-pong: a stage reads the previous one with halos)
   float* wsB = nullptr;
   float* p = nullptr;          // pressure of the latest projection
-  void* spec = nullptr;        // [batch][N/2 + 1][N] complex half spectra, column-major
+  void* spec = nullptr;        // [batch][N/8][N/2 + 1][8] complex half spectra (8-row groups)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;  // one step
 };

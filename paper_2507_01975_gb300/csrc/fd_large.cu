@@ -13,9 +13,9 @@ using namespace ldfv;
 
 namespace {
 
-size_t rows_smem(int n) { return (size_t)(kLRB / 2) * n * 8 + (size_t)(n / 2) * 8; }
-size_t cols_smem(int n) { return (size_t)kLCB * n * 8 + (size_t)(n / 2) * 8 + (size_t)n * 4; }
-size_t rows_inv_smem(int n) { return rows_smem(n) + (size_t)kLKC * kLRB * 8; }
+size_t rows_smem(int n) { return (size_t)(kLRB / 2) * n * 8 + (size_t)n * 8; }
+size_t cols_smem(int n) { return (size_t)kLCB * n * 8 + (size_t)n * 8 + (size_t)n * 4; }
+size_t rows_inv_smem(int n) { return rows_smem(n); }
 
 LargeArgs base_args(fd_ctx* c) {
   LargeArgs a;
@@ -100,7 +100,7 @@ fd_status fd_large_init(fd_ctx* c) {
   alloc((void**)&S->wsA, state);
   alloc((void**)&S->wsB, state);
   alloc((void**)&S->p, B * n * n * sizeof(float));
-  alloc(&S->spec, B * (n / 2 + 1) * n * 8);
+  alloc(&S->spec, B * (n / kLRB) * (n / 2 + 1) * kLRB * 8);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(large_rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(n));
   if (e == cudaSuccess)

@@ -9,7 +9,8 @@
 //             and the accumulator -> w* and acc;
 //   rows_fwd  divergence D2 w* (two-point, Sec. 3.6) of 8 rows, real-to-complex
 //             row FFTs (two real rows per complex transform), half spectra
-//             written column-major (kx-major, y contiguous);
+//             written as one contiguous block per group of 8 rows:
+//             spec[b][y / 8][kx][y % 8];
 //   cols      column FFTs, multiplication by 1 / symbol(D2 G2) (zero mode 0,
 //             App. B.3-B.4), inverse column FFTs;
 //   rows_inv  complex-to-real inverse row FFTs -> pressure p.
@@ -32,7 +33,7 @@ struct LargeArgs {
   const float* un;    // state at the start of the step
   float* acc;         // RK accumulator
   float* ws;          // stage: w* output; rows_fwd input; final input
-  float2* spec;       // [batch][N/2 + 1][N] complex (column-major half spectra)
+  float2* spec;       // [batch][N/8][N/2 + 1][8] complex half spectra (8-row groups)
   float* pout;        // rows_inv output; final input
   float* uout;        // final output
   int stage, flow, forcing;
@@ -44,9 +45,8 @@ struct LargeArgs {
 };
 
 constexpr int kLTX = 32, kLTY = 16;  // stage tile (cells)
-constexpr int kLRB = 8;              // rows per CTA of the row transforms
-constexpr int kLCB = 2;              // columns per CTA of the column transforms
-constexpr int kLKC = 128;            // spectrum columns staged at a time by rows_inv
+constexpr int kLRB = 8;              // rows per CTA of the row transforms (4 complex transforms)
+constexpr int kLCB = 2;              // columns per CTA of the column transforms (power of two)
 
 __device__ __forceinline__ float2 c2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -58,38 +58,87 @@ __device__ __forceinline__ float2 c2mulc(float2 a, float2 w) {  // a * conj(w)
 }
 __device__ __forceinline__ int brev_n(int k, int logn) { return (int)(__brev((unsigned)k) >> (32 - logn)); }
 
-// F forward transforms of length N = 2^logn stored at x + f * stride:
-// natural-order input, bit-reversed output (radix-2 decimation in frequency)
-__device__ void block_fft_dif(float2* x, int F, int stride, int logn, const float2* tw) {
-  const int N = 1 << logn, H = N >> 1;
-  for (int len = N; len >= 2; len >>= 1) {
-    const int half = len >> 1, tstep = N / len;
+// Stage-major twiddles in shared memory: tws[h + j] = exp(-2 pi i j / (2 h)) for
+// h = 1, 2, 4, .., N/2 and j < h (N - 1 entries, index 0 unused), so that the
+// butterflies of one stage read consecutive entries (no bank conflicts).
+__device__ void load_stage_twiddles(float2* tws, const float2* tw, int logn) {
+  const int N = 1 << logn;
+  for (int e = threadIdx.x + 1; e < N; e += blockDim.x) {
+    const int ls = 31 - __clz(e);  // h = 2^ls <= e < 2h
+    const int j = e - (1 << ls);
+    tws[e] = tw[j << (logn - 1 - ls)];
+  }
+}
+
+// F forward transforms of length N = 2^logn stored at x + f * N: natural-order
+// input, bit-reversed output (decimation in frequency). Two radix-2 stages
+// (halves 2q and q) are fused into one radix-4 pass in registers; an odd
+// logn ends with one radix-2 stage. Index arithmetic is shifts and masks.
+__device__ void block_fft_dif(float2* x, int F, int logn, const float2* tws) {
+  const int Q = 1 << (logn - 2);  // radix-4 groups per transform
+  int ls = logn - 1;              // log2 of the current stage's half
+  for (; ls >= 1; ls -= 2) {
+    const int lq = ls - 1, q = 1 << lq;  // halves 2q (first stage) and q (second)
+    for (int t = threadIdx.x; t < F * Q; t += blockDim.x) {
+      const int f = t >> (logn - 2), r = t & (Q - 1);
+      const int j = r & (q - 1);
+      float2* b = x + (f << logn) + ((r >> lq) << (lq + 2));
+      float2 a0 = b[j], a1 = b[j + q], a2 = b[j + 2 * q], a3 = b[j + 3 * q];
+      const float2 s0 = c2add(a0, a2), s2 = c2mul(c2sub(a0, a2), tws[2 * q + j]);
+      const float2 s1 = c2add(a1, a3), s3 = c2mul(c2sub(a1, a3), tws[3 * q + j]);
+      const float2 w = tws[q + j];
+      b[j] = c2add(s0, s1);
+      b[j + q] = c2mul(c2sub(s0, s1), w);
+      b[j + 2 * q] = c2add(s2, s3);
+      b[j + 3 * q] = c2mul(c2sub(s2, s3), w);
+    }
+    __syncthreads();
+  }
+  if (ls == 0) {  // remaining radix-2 stage, half = 1
+    const int H = 1 << (logn - 1);
     for (int t = threadIdx.x; t < F * H; t += blockDim.x) {
-      const int f = t / H, r = t - f * H;
-      const int blk = r / half, j = r - blk * half;
-      float2* b = x + f * stride + blk * len;
-      const float2 a = b[j], c = b[j + half];
-      b[j] = c2add(a, c);
-      b[j + half] = c2mul(c2sub(a, c), tw[j * tstep]);
+      float2* b = x + 2 * t;
+      const float2 a = b[0], c = b[1];
+      b[0] = c2add(a, c);
+      b[1] = c2sub(a, c);
     }
     __syncthreads();
   }
 }
 
 // F inverse (unnormalised) transforms: bit-reversed input, natural output
-// (radix-2 decimation in time with conjugate twiddles)
-__device__ void block_ifft_dit(float2* x, int F, int stride, int logn, const float2* tw) {
-  const int N = 1 << logn, H = N >> 1;
-  for (int len = 2; len <= N; len <<= 1) {
-    const int half = len >> 1, tstep = N / len;
+// (decimation in time, conjugate twiddles): an odd logn starts with one
+// radix-2 stage, then radix-4 passes fuse halves q and 2q.
+__device__ void block_ifft_dit(float2* x, int F, int logn, const float2* tws) {
+  int ls = 0;
+  if (logn & 1) {
+    const int H = 1 << (logn - 1);
     for (int t = threadIdx.x; t < F * H; t += blockDim.x) {
-      const int f = t / H, r = t - f * H;
-      const int blk = r / half, j = r - blk * half;
-      float2* b = x + f * stride + blk * len;
-      const float2 a = b[j];
-      const float2 c = c2mulc(b[j + half], tw[j * tstep]);
-      b[j] = c2add(a, c);
-      b[j + half] = c2sub(a, c);
+      float2* b = x + 2 * t;
+      const float2 a = b[0], c = b[1];
+      b[0] = c2add(a, c);
+      b[1] = c2sub(a, c);
+    }
+    __syncthreads();
+    ls = 1;
+  }
+  const int Q = 1 << (logn - 2);
+  for (; ls + 1 < logn; ls += 2) {
+    const int lq = ls, q = 1 << lq;  // halves q (first stage) and 2q (second)
+    for (int t = threadIdx.x; t < F * Q; t += blockDim.x) {
+      const int f = t >> (logn - 2), r = t & (Q - 1);
+      const int j = r & (q - 1);
+      float2* b = x + (f << logn) + ((r >> lq) << (lq + 2));
+      const float2 a0 = b[j], a1 = b[j + q], a2 = b[j + 2 * q], a3 = b[j + 3 * q];
+      const float2 w = tws[q + j];
+      const float2 t1 = c2mulc(a1, w), t3 = c2mulc(a3, w);
+      const float2 s0 = c2add(a0, t1), s1 = c2sub(a0, t1);
+      const float2 s2 = c2add(a2, t3), s3 = c2sub(a2, t3);
+      const float2 u2 = c2mulc(s2, tws[2 * q + j]), u3 = c2mulc(s3, tws[3 * q + j]);
+      b[j] = c2add(s0, u2);
+      b[j + 2 * q] = c2sub(s0, u2);
+      b[j + q] = c2add(s1, u3);
+      b[j + 3 * q] = c2sub(s1, u3);
     }
     __syncthreads();
   }
@@ -207,38 +256,33 @@ __global__ void __launch_bounds__(512) large_rows_fwd_kernel(const LargeArgs a, 
   const int N = 1 << logn, MSK = N - 1, H = N / 2;
   constexpr int F = kLRB / 2;
   float2* buf = sm;           // [F][N]
-  float2* tw = sm + F * N;    // [N/2]
-  const int b = blockIdx.y, y0 = blockIdx.x * kLRB;
+  float2* tw = sm + F * N;    // [N] stage-major twiddles
+  const int b = blockIdx.y, g = blockIdx.x, y0 = g * kLRB;
   const size_t NN = (size_t)N * N;
   const float* u = a.ws + (size_t)b * 2 * NN;
   const float* v = u + NN;
-  for (int k = threadIdx.x; k < H; k += blockDim.x) tw[k] = a.tw[k];
+  load_stage_twiddles(tw, a.tw, logn);
   for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
-    const int f = t / N, x = t - f * N;
+    const int f = t >> logn, x = t & MSK;
     const int ra = y0 + 2 * f, rb = ra + 1;
     const int xe = (x + 1) & MSK;
     const float da = (u[(size_t)ra * N + xe] - u[(size_t)ra * N + x]) * a.idx +
                      (v[(size_t)rb * N + x] - v[(size_t)ra * N + x]) * a.idy;
     const float db = (u[(size_t)rb * N + xe] - u[(size_t)rb * N + x]) * a.idx +
                      (v[(size_t)((rb + 1) & MSK) * N + x] - v[(size_t)rb * N + x]) * a.idy;
-    buf[f * N + x] = make_float2(da, db);
+    buf[t] = make_float2(da, db);
   }
   __syncthreads();
-  block_fft_dif(buf, F, N, logn, tw);
-  // unpack the two real rows of each transform: A_k = (Z_k + conj Z_{N-k}) / 2,
-  // B_k = (Z_k - conj Z_{N-k}) / (2i); Z_k sits at bit-reversed position
-  float2* spec = a.spec + (size_t)b * (H + 1) * N;
-  for (int t = threadIdx.x; t < (H + 1) * kLRB; t += blockDim.x) {
-    const int k = t / kLRB, yy = t - k * kLRB;
-    const int f = yy >> 1;
-    const float2 zk = buf[f * N + brev_n(k & MSK, logn)];
-    const float2 zm = buf[f * N + brev_n((N - k) & MSK, logn)];
-    float2 val;
-    if ((yy & 1) == 0)
-      val = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    else
-      val = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-    spec[(size_t)k * N + y0 + yy] = val;
+  block_fft_dif(buf, F, logn, tw);
+  // unpack the two real rows of transform f: A_k = (Z_k + conj Z_{N-k}) / 2,
+  // B_k = (Z_k - conj Z_{N-k}) / (2i); Z_k sits at bit-reversed position. One
+  // float4 (A_k, B_k) per (k, f): the block is written contiguously.
+  float4* blk = reinterpret_cast<float4*>(a.spec + ((size_t)b * (N / kLRB) + g) * (H + 1) * kLRB);
+  for (int t = threadIdx.x; t < (H + 1) * F; t += blockDim.x) {
+    const int k = t >> 2, f = t & 3;
+    const float2 zk = buf[(f << logn) + brev_n(k & MSK, logn)];
+    const float2 zm = buf[(f << logn) + brev_n((N - k) & MSK, logn)];
+    blk[t] = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
 }
 
@@ -247,27 +291,35 @@ __global__ void __launch_bounds__(512) large_rows_fwd_kernel(const LargeArgs a, 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) large_cols_kernel(const LargeArgs a, int logn) {
   extern __shared__ __align__(16) float2 sm[];
-  const int N = 1 << logn, H = N / 2;
+  const int N = 1 << logn, H = N / 2, G = N / kLRB;
   float2* buf = sm;                 // [kLCB][N]
-  float2* tw = sm + kLCB * N;       // [N/2]
-  float* sy = reinterpret_cast<float*>(tw + H);  // [N]
+  float2* tw = sm + kLCB * N;       // [N] stage-major twiddles
+  float* sy = reinterpret_cast<float*>(tw + N);  // [N]
   const int b = blockIdx.y, kx0 = blockIdx.x * kLCB;
   const int F = (H + 1 - kx0) < kLCB ? (H + 1 - kx0) : kLCB;
-  float2* spec = a.spec + (size_t)b * (H + 1) * N;
-  for (int k = threadIdx.x; k < H; k += blockDim.x) tw[k] = a.tw[k];
+  float2* spec = a.spec + (size_t)b * G * (H + 1) * kLRB;
+  load_stage_twiddles(tw, a.tw, logn);
   for (int k = threadIdx.x; k < N; k += blockDim.x) sy[k] = a.symy[k];
-  for (int t = threadIdx.x; t < F * N; t += blockDim.x) buf[t] = spec[(size_t)kx0 * N + t];
+  // column kx0 + c, row y = 8 g + yy sits at spec[(g (H + 1) + kx0 + c) 8 + yy]:
+  // kLCB x 8 consecutive complex values per row group
+  for (int t = threadIdx.x; t < kLCB * N; t += blockDim.x) {
+    const int yy = t & (kLRB - 1), c = (t >> 3) & (kLCB - 1), g = t >> 4;
+    if (c < F) buf[(c << logn) + g * kLRB + yy] = spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy];
+  }
   __syncthreads();
-  block_fft_dif(buf, F, N, logn, tw);
+  block_fft_dif(buf, F, logn, tw);
   for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
-    const int f = t / N, pos = t - f * N;
+    const int f = t >> logn, pos = t & (N - 1);
     const int kx = kx0 + f, ky = brev_n(pos, logn);
     const float m = (kx == 0 && ky == 0) ? 0.0f : __fdividef(a.inv_nn, a.symx[kx] + sy[ky]);
     buf[t] = make_float2(buf[t].x * m, buf[t].y * m);
   }
   __syncthreads();
-  block_ifft_dit(buf, F, N, logn, tw);
-  for (int t = threadIdx.x; t < F * N; t += blockDim.x) spec[(size_t)kx0 * N + t] = buf[t];
+  block_ifft_dit(buf, F, logn, tw);
+  for (int t = threadIdx.x; t < kLCB * N; t += blockDim.x) {
+    const int yy = t & (kLRB - 1), c = (t >> 3) & (kLCB - 1), g = t >> 4;
+    if (c < F) spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy] = buf[(c << logn) + g * kLRB + yy];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -278,33 +330,22 @@ __global__ void __launch_bounds__(512) large_rows_inv_kernel(const LargeArgs a, 
   const int N = 1 << logn, H = N / 2, MSK = N - 1;
   constexpr int F = kLRB / 2;
   float2* buf = sm;                   // [F][N]
-  float2* tw = sm + F * N;            // [N/2]
-  float2* stg = tw + H;               // [kLKC][kLRB]
-  const int b = blockIdx.y, y0 = blockIdx.x * kLRB;
-  const float2* spec = a.spec + (size_t)b * (H + 1) * N;
-  for (int k = threadIdx.x; k < H; k += blockDim.x) tw[k] = a.tw[k];
-  // rebuild the packed transforms Z_k = P_a[k] + i P_b[k] (Hermitian halves for k > N/2)
-  for (int k0 = 0; k0 <= H; k0 += kLKC) {
-    const int kn = (H + 1 - k0) < kLKC ? (H + 1 - k0) : kLKC;
-    __syncthreads();
-    for (int t = threadIdx.x; t < kn * kLRB; t += blockDim.x) {
-      const int kk = t / kLRB, yy = t - kk * kLRB;
-      stg[t] = spec[(size_t)(k0 + kk) * N + y0 + yy];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < F * kn; t += blockDim.x) {
-      const int f = t / kn, kk = t - f * kn;
-      const int k = k0 + kk;
-      const float2 pa = stg[kk * kLRB + 2 * f], pb = stg[kk * kLRB + 2 * f + 1];
-      buf[f * N + brev_n(k & MSK, logn)] = make_float2(pa.x - pb.y, pa.y + pb.x);
-      if (k > 0 && k < H) buf[f * N + brev_n(N - k, logn)] = make_float2(pa.x + pb.y, pb.x - pa.y);
-    }
+  float2* tw = sm + F * N;            // [N] stage-major twiddles
+  const int b = blockIdx.y, g = blockIdx.x, y0 = g * kLRB;
+  const float4* blk = reinterpret_cast<const float4*>(a.spec + ((size_t)b * (N / kLRB) + g) * (H + 1) * kLRB);
+  load_stage_twiddles(tw, a.tw, logn);
+  // packed transforms Z_k = P_a[k] + i P_b[k], Hermitian mirror for k > N/2
+  for (int t = threadIdx.x; t < (H + 1) * F; t += blockDim.x) {
+    const int k = t >> 2, f = t & 3;
+    const float4 v = blk[t];  // (P_a[k], P_b[k])
+    buf[(f << logn) + brev_n(k & MSK, logn)] = make_float2(v.x - v.w, v.y + v.z);
+    if (k > 0 && k < H) buf[(f << logn) + brev_n(N - k, logn)] = make_float2(v.x + v.w, v.z - v.y);
   }
   __syncthreads();
-  block_ifft_dit(buf, F, N, logn, tw);
+  block_ifft_dit(buf, F, logn, tw);
   float* p = a.pout + (size_t)b * N * N;
   for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
-    const int f = t / N, x = t - f * N;
+    const int f = t >> logn, x = t & MSK;
     const float2 z = buf[t];
     p[(size_t)(y0 + 2 * f) * N + x] = z.x;
     p[(size_t)(y0 + 2 * f + 1) * N + x] = z.y;

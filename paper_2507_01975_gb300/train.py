@@ -94,9 +94,13 @@ class TrainConfig:
 class Trainer:
     """Adam on the parameters of a learned solver, one fused training step per iteration."""
 
-    def __init__(self, solver: fd.Solver, params0, cfg: Optional[TrainConfig] = None):
+    def __init__(self, solver: fd.Solver, params0, cfg: Optional[TrainConfig] = None, group=None):
+        """``group``: a torch.distributed process group for data-parallel training
+        (one process per GPU, each with its own batch); the gradients are averaged
+        over the ranks, weighted by batch size, before every Adam step."""
         torch = _torch()
         self.solver = solver
+        self.group = group
         self.cfg = cfg or TrainConfig()
         self.theta = torch.as_tensor(params0, dtype=torch.float32).to("cuda").contiguous()
         self.grad = torch.zeros_like(self.theta)
@@ -111,6 +115,10 @@ class Trainer:
         (device), gradient, Adam update, parameter upload. Returns the loss tensor."""
         c = self.cfg
         self.solver.train_step(u0, targets, c.unroll, c.ckpt_every, self.grad, self.loss)
+        if self.group is not None:
+            from .shard import average_gradients
+
+            average_gradients(self.grad, int(u0.shape[0]), self.group)
         self.t += 1
         fd.adam_step(self.theta, self.grad, self.m, self.v, self.t, c.lr, c.beta1, c.beta2, c.eps, zero_grads=True)
         self.solver.set_params_device(self.theta)

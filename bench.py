@@ -309,6 +309,109 @@ def fine_measurement(fd, I, steps: int = 40):
     }
 
 
+def corr_measurement(fd, I, n_fine: int = 1024, n_train: int = 4, n_test: int = 2, warm: float = 4.0,
+                     horizon: float = 2.0, iters: int = 200, unroll: int = 16, lr: float = 1e-3):
+    """Wall time to a 0.95 vorticity correlation, learned vs plain FV (forced flow, Re = 1000).
+
+    A fine plain-FV reference (n_fine^2, streaming path) is warmed up from random
+    fields, then coarse-grained (face averages to 64^2, every 16 fine steps) into
+    labels. Plain solvers at 64..512 (same CFL number) and the learned 64^2 solver
+    (trained here with Adam on the first n_train trajectories, unrolled MSE through
+    the hand-written adjoint) start from the coarse-grained state of the test
+    trajectories; their vorticity correlation with the labels is tracked to the
+    horizon. Reported per solver: the time until the correlation first drops below
+    0.95 and the wall time of a rollout to the horizon (CUDA events).
+    """
+    import torch
+
+    from paper_2507_01975_gb300.train import TrainConfig, Trainer
+
+    nc, nu = 64, 1e-3
+    dt_f = 2.19e-4 * 2048 / n_fine
+    rt = 16
+    dt_c = rt * dt_f
+    B = n_train + n_test
+    kt = int(round(horizon / dt_c))
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # fine reference and labels
+    fine = fd.Solver(fd.Config(n=n_fine, batch=B, dtype="f32", nu=nu, dt=dt_f, forcing="kolmogorov"))
+    u = torch.tensor(np.stack([I.kolmogorov_ic(n_fine, 200 + k) for k in range(B)]).astype(np.float32), device="cuda")
+    fine.rollout(u, u, int(round(warm / dt_f)))
+    labels = torch.empty((kt + 1, B, 2, nc, nc), device="cuda")
+    fd.downsample(u, labels[0], n_fine // nc)
+    u_fine0 = u.clone()
+    for k in range(kt):
+        fine.rollout(u, u, rt)
+        fd.downsample(u, labels[k + 1], n_fine // nc)
+    torch.cuda.synchronize()
+    lt = labels[:, :n_train].contiguous()
+    lv = labels[:, n_train:].contiguous()
+    test0 = u_fine0[n_train:].contiguous()
+    corr = torch.zeros(n_test, dtype=torch.float64, device="cuda")
+    judge = fd.Solver(fd.Config(n=nc, batch=n_test, dtype="f32"))
+
+    def track(solver, n, steps_per_coarse):
+        """Correlation curve (min over test trajectories) and wall time to the horizon."""
+        u0 = torch.empty((n_test, 2, n, n), device="cuda")
+        fd.downsample(test0, u0, n_fine // n)
+        traj = torch.empty((kt, n_test, 2, n, n), device="cuda")
+        last = torch.empty_like(u0)
+        solver.rollout(u0, last, kt * steps_per_coarse, traj=traj, save_every=steps_per_coarse)
+        coarse = torch.empty((n_test, 2, nc, nc), device="cuda")
+        curve = []
+        for k in range(kt):
+            fd.downsample(traj[k], coarse, n // nc)
+            judge.vorticity_pcc(coarse, lv[k + 1], corr)
+            curve.append(float(corr.min().item()))
+        solver.rollout(u0, last, kt * steps_per_coarse)  # warm graph
+        wall = timed(lambda: solver.rollout(u0, last, kt * steps_per_coarse))
+        t95 = next((k * dt_c for k, c in enumerate(curve) if c < 0.95), kt * dt_c)
+        return {"t_corr_095": t95, "wall_ms_to_horizon": wall, "corr_at_horizon": curve[-1],
+                "corr_curve_every_10": curve[::10]}
+
+    out = {"workload": f"forced NS (Re 1000), fine {n_fine}^2 reference coarse-grained to 64^2, "
+                       f"{n_train} training / {n_test} test trajectories, horizon {horizon} time units",
+           "solvers": {}}
+    for n in (64, 128, 256, 512):
+        s = fd.Solver(fd.Config(n=n, batch=n_test, dtype="f32", nu=nu, dt=dt_f * n_fine / n, forcing="kolmogorov"))
+        out["solvers"][f"plain{n}"] = track(s, n, rt * n // n_fine)
+    # learned 64^2: last layer zero-initialised (starts as the plain solver), W_L = 0
+    st = I.random_conv_stack(11, 2, 64, 160, last_scale=0.0)
+    params = I.pack_params(np.zeros((2, 2, 5, 4)), st)
+    ls = fd.Solver(fd.Config(n=nc, batch=n_train, dtype="f32", nu=nu, dt=dt_c, forcing="kolmogorov", learned=True))
+    tr = Trainer(ls, params, TrainConfig(unroll=unroll, ckpt_every=8, lr=lr))
+    rng = np.random.default_rng(0)
+    losses = []
+    t_train = 0.0
+    for it in range(iters):
+        s0 = int(rng.integers(0, kt - unroll + 1))
+        t_train += timed(lambda: tr.step(lt[s0], lt[s0 + 1:s0 + 1 + unroll]))
+        if it % 20 == 0 or it == iters - 1:
+            losses.append(float(tr.loss.item()))
+    le = fd.Solver(fd.Config(n=nc, batch=n_test, dtype="f32", nu=nu, dt=dt_c, forcing="kolmogorov", learned=True))
+    le.set_params_device(tr.theta)
+    out["solvers"]["learned64"] = track(le, nc, 1)
+    out["training"] = {"iterations": iters, "unroll": unroll, "lr": lr, "loss_every_20": losses,
+                       "seconds": t_train / 1e3}
+    L = out["solvers"]["learned64"]
+    plains = [(k, v) for k, v in out["solvers"].items() if k.startswith("plain") and v["t_corr_095"] >= L["t_corr_095"]]
+    if plains:
+        k, v = min(plains, key=lambda kv: kv[1]["wall_ms_to_horizon"])
+        out["cheapest_plain_matching_learned"] = k
+        out["wall_time_ratio_plain_over_learned"] = v["wall_ms_to_horizon"] / L["wall_ms_to_horizon"]
+    return out
+
+
 def adjoint_measurement(fd, I, iters: int = 5):
     """Reverse mode of one learned step (shear layer 64^2, batch 32) alone."""
     import torch
@@ -343,7 +446,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-fine", action="store_true", help="skip the 2048^2 streaming-path measurement")
-    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine"],
+    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
     ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
@@ -365,7 +468,8 @@ def main():
         fn = {"learned": lambda: learned_measurement(fd, I, steps=max(args.iters, 4)),
               "training": lambda: training_measurement(fd, I, iters=args.iters),
               "adjoint": lambda: adjoint_measurement(fd, I, iters=args.iters),
-              "fine": lambda: fine_measurement(fd, I, steps=max(args.iters, 2))}[args.only]
+              "fine": lambda: fine_measurement(fd, I, steps=max(args.iters, 2)),
+              "corr": lambda: corr_measurement(fd, I, iters=args.iters)}[args.only]
         print(json.dumps(fn()), flush=True)
         return
 

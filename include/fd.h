@@ -230,6 +230,13 @@ fd_status fd_train_step(fd_ctx* ctx, const void* u0, const void* targets, int32_
 fd_status fd_mse_loss(fd_ctx* ctx, const float* pred, const float* target, int64_t count, double* loss,
                       float* grad, void* stream);
 
+/* Vorticity correlation (App. D.1, PCC; the accuracy measure of the paper's
+ * correlation curves): for each trajectory b, the Pearson correlation of the
+ * corner vorticities w = (v - v[i-1]) / dx - (u - u[j-1]) / dy of the device
+ * states a[b] and b[b] (context grid and dtype), accumulated in FP64 in a fixed
+ * order. pcc: device double[batch]. Uses the context's workspace. */
+fd_status fd_vorticity_pcc(fd_ctx* ctx, const void* a, const void* b, double* pcc, void* stream);
+
 /* One Adam update (the optimiser of the paper's training; Kingma & Ba 2015)
  * of `count` float32 device parameters: m, v are the caller-owned first and
  * second moment buffers (zero before step t = 1), t >= 1 the step number.

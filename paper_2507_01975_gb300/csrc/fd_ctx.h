@@ -100,6 +100,8 @@ struct TrainState {
   float* seg = nullptr;
   float* lam = nullptr;
   double* partial = nullptr;
+  double* corr = nullptr;      // partial sums of fd_vorticity_pcc
+  size_t ncorr = 0;
   int nckpt = 0, nseg = 0;
 };
 

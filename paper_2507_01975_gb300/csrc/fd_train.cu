@@ -100,6 +100,54 @@ __global__ void adam_kernel(float* p, float* g, float* m, float* v, size_t n, fl
   }
 }
 
+// Per-trajectory partial sums for the Pearson correlation of corner vorticities
+// w = (v - v[i-1]) / dx - (u - u[j-1]) / dy of two states a, b: (sum wa, sum wb,
+// sum wa^2, sum wb^2, sum wa wb) in FP64, one row of 5 per block.
+template <typename T>
+__global__ void vort_partial_kernel(const T* a, const T* b, int logn, double idx, double idy, double* partial) {
+  __shared__ double red[5][32];
+  const int N = 1 << logn, MSK = N - 1;
+  const size_t NN = (size_t)N * N;
+  const int tr = blockIdx.y;
+  const T* ua = a + (size_t)tr * 2 * NN;
+  const T* ub = b + (size_t)tr * 2 * NN;
+  double s[5] = {0, 0, 0, 0, 0};
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < NN; c += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c >> logn), i = (int)(c & MSK);
+    const size_t cw = (size_t)j * N + ((i - 1) & MSK), cs = (size_t)((j - 1) & MSK) * N + i;
+    const double wa = ((double)ua[NN + c] - (double)ua[NN + cw]) * idx - ((double)ua[c] - (double)ua[cs]) * idy;
+    const double wb = ((double)ub[NN + c] - (double)ub[NN + cw]) * idx - ((double)ub[c] - (double)ub[cs]) * idy;
+    s[0] += wa;
+    s[1] += wb;
+    s[2] += wa * wa;
+    s[3] += wb * wb;
+    s[4] += wa * wb;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+    if (lane == 0) red[k][w] = s[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+    partial[((size_t)tr * gridDim.x + blockIdx.x) * 5 + threadIdx.x] = t;
+  }
+}
+
+__global__ void vort_pcc_kernel(const double* partial, int nblk, double n, double* out) {
+  const int tr = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < nblk; ++k)
+    for (int m = 0; m < 5; ++m) s[m] += partial[((size_t)tr * nblk + k) * 5 + m];
+  const double cov = s[4] - s[0] * s[1] / n;
+  const double va = s[2] - s[0] * s[0] / n, vb = s[3] - s[1] * s[1] / n;
+  out[tr] = cov / sqrt(va * vb);
+}
+
 int grid_for(size_t n) {
   const size_t b = (n + 255) / 256;
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -212,7 +260,7 @@ fd_status rollout_reverse(fd_ctx* c, const float* u0, int n, int k, const float*
 void fd_train_free(fd_ctx* c) {
   TrainState* T = c->trn;
   if (!T) return;
-  void* ps[] = {T->ckpt, T->seg, T->lam, T->partial};
+  void* ps[] = {T->ckpt, T->seg, T->lam, T->partial, T->corr};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete T;
@@ -273,6 +321,37 @@ fd_status fd_train_step(fd_ctx* c, const void* u0, const void* targets, int32_t 
   return rollout_reverse(c, static_cast<const float*>(u0), n_steps, ckpt_every, nullptr,
                          static_cast<const float*>(targets), nullptr, dparams, loss,
                          static_cast<cudaStream_t>(stream), "fd_train_step");
+}
+
+fd_status fd_vorticity_pcc(fd_ctx* c, const void* a, const void* b, double* pcc, void* stream) {
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_vorticity_pcc: null context");
+  if (!a || !b || !pcc) return fd_set_error(c, FD_EINVAL, "fd_vorticity_pcc: null pointer");
+  fd_status s = train_reserve(c, 0, 0);
+  if (s != FD_OK) return s;
+  TrainState& T = *c->trn;
+  constexpr int kBlk = 64;
+  const int B = c->grid.batch;
+  if (T.ncorr < (size_t)B * kBlk * 5) {
+    if (T.corr) cudaFree(T.corr);
+    T.corr = nullptr;
+    T.ncorr = 0;
+    if (cudaMalloc(&T.corr, (size_t)B * kBlk * 5 * sizeof(double)) != cudaSuccess)
+      return fd_set_error(c, FD_ENOMEM, "fd_vorticity_pcc: out of device memory");
+    T.ncorr = (size_t)B * kBlk * 5;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const dim3 grid(kBlk, B);
+  if (c->grid.dtype == FD_F64)
+    vort_partial_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(a), static_cast<const double*>(b),
+                                                     c->logn, c->base.idx, c->base.idy, T.corr);
+  else
+    vort_partial_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(a), static_cast<const float*>(b),
+                                                    c->logn, c->base.idx, c->base.idy, T.corr);
+  vort_pcc_kernel<<<B, 32, 0, st>>>(T.corr, kBlk, (double)c->grid.nx * c->grid.ny, pcc);
+  cudaError_t e = cudaGetLastError();
+  c->launches = 2;
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_vorticity_pcc: %s", cudaGetErrorString(e));
+  return FD_OK;
 }
 
 fd_status fd_adam_step(float* params, float* grads, float* m, float* v, int64_t count, int32_t t, float lr,

@@ -37,6 +37,7 @@ EXPORTS = [
     "fd_rollout_adjoint",
     "fd_train_step",
     "fd_mse_loss",
+    "fd_vorticity_pcc",
     "fd_adam_step",
     "fd_downsample",
     "fd_destroy",
@@ -121,6 +122,8 @@ def load(path: str = LIB_PATH):
     lib.fd_train_step.restype = C.c_int
     lib.fd_mse_loss.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
     lib.fd_mse_loss.restype = C.c_int
+    lib.fd_vorticity_pcc.argtypes = [vp, vp, vp, vp, vp]
+    lib.fd_vorticity_pcc.restype = C.c_int
     lib.fd_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, i32, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]
     lib.fd_adam_step.restype = C.c_int
     lib.fd_downsample.argtypes = [vp, vp, i32, i32, i32, i32, vp]
@@ -264,6 +267,10 @@ class Solver:
         g = _ptr(grad) if grad is not None else None
         self._check(self.lib.fd_mse_loss(self.h, _ptr(pred), _ptr(target), int(pred.numel()), _ptr(loss), g,
                                          _stream_handle(stream)))
+
+    def vorticity_pcc(self, a, b, out, stream=None):
+        """out[batch] (device float64) = vorticity correlation of states a and b per trajectory."""
+        self._check(self.lib.fd_vorticity_pcc(self.h, _ptr(a), _ptr(b), _ptr(out), _stream_handle(stream)))
 
     def last_launch_count(self) -> int:
         return int(self.lib.fd_last_launch_count(self.h))

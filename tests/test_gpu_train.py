@@ -182,3 +182,24 @@ def test_autograd_rollout_gradient_matches_rollout_adjoint():
     torch.cuda.synchronize()
     assert rel_l2(u0.grad.double().cpu().numpy(), lam0.double().cpu().numpy()) <= 1e-5
     assert rel_l2(theta.grad.double().cpu().numpy(), dp.double().cpu().numpy()) <= 1e-3
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_vorticity_correlation_matches_oracle(dtype):
+    n, b = 64, 3
+    s = fd.Solver(fd.Config(n=n, batch=b, dtype=dtype))
+    A_ = I.ic_batch("decaying", n, b, seed0=80)
+    rng = np.random.default_rng(81)
+    B_ = A_ + 0.3 * rng.standard_normal(A_.shape)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    out = torch.zeros(b, dtype=torch.float64, device="cuda")
+    s.vorticity_pcc(dev(A_, tdt), dev(B_, tdt), out)
+    torch.cuda.synchronize()
+    h = 2 * np.pi / n
+    cast = (lambda x: x) if dtype == "f64" else (lambda x: x.astype(np.float32).astype(np.float64))
+    ref = [O.pcc(O.vorticity(cast(A_[k]), h, h), O.vorticity(cast(B_[k]), h, h)) for k in range(b)]
+    assert np.max(np.abs(out.cpu().numpy() - np.array(ref))) <= 1e-12
+    # identical fields correlate perfectly
+    s.vorticity_pcc(dev(A_, tdt), dev(A_, tdt), out)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy() - 1.0)) <= 1e-12

@@ -30,18 +30,18 @@ inline cudaError_t mark(cudaError_t e, const char* where) {
   return e;
 }
 
+constexpr int kAdjBandRows = 8;  // rows per CTA of the flux-block reverse kernel
 constexpr int kWgradMaxCols = 3 * 2 * 80;  // largest per-CTA partial: 3 dx x 2 MMAs x 80 channels
 
 template <int LOGN>
 cudaError_t prepare_adjoint(bool learned) {
-  cudaError_t e = cudaFuncSetAttribute(fv_adjoint_stage_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)AdjCfg<LOGN>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(fv_adjoint_band_kernel<LOGN, kAdjBandRows>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)AdjBandCfg<LOGN, kAdjBandRows>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fv_adjoint_combine_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)LearnedCfg<LOGN>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fv_learned_stage_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LearnedCfg<LOGN>::SMEM);
+  if (e == cudaSuccess) e = prepare_learned_stage<LOGN>();
   if (!learned || e != cudaSuccess) return e;
   // kernel templates are instantiated per translation unit: the forward
   // convolutions launched from here need their attributes set from here too
@@ -298,9 +298,8 @@ cudaError_t step_adjoint(fd_ctx* c, const float* u, const float* lam_out, float*
     fa.w = ws[s];
     fa.wout = A.wst[s];
     fa.coef = learned ? A.coef[s] : nullptr;
-    fv_learned_stage_kernel<LOGN><<<B, LearnedCfg<LOGN>::NT, LearnedCfg<LOGN>::SMEM, st>>>(fa);
-    e = mark(cudaGetLastError(), "forward stage");
-    ++*launches;
+    e = mark(launch_learned_stage<LOGN>(fa, A.xbar, B, st), "forward stage");  // xbar is free until the reverse pass
+    *launches += 2;
   }
   if (e == cudaSuccess && learned) e = net_forward_saved<LOGN>(c, 3, ws[3], st, launches);
   // ---- reverse ------------------------------------------------------------------------
@@ -326,7 +325,11 @@ cudaError_t step_adjoint(fd_ctx* c, const float* u, const float* lam_out, float*
   for (int s = 3; s >= 0 && e == cudaSuccess; --s) {
     sa.w = ws[s];
     sa.coef = learned ? A.coef[s] : nullptr;
-    fv_adjoint_stage_kernel<LOGN><<<B, AdjCfg<LOGN>::NT, AdjCfg<LOGN>::SMEM, st>>>(sa);
+    // banded flux-block reverse: bands add their scatter into the zeroed w_bar
+    e = mark(cudaMemsetAsync(A.wbar, 0, fd_state_bytes(c->grid), st), "stage adjoint");
+    if (e != cudaSuccess) break;
+    fv_adjoint_band_kernel<LOGN, kAdjBandRows>
+        <<<dim3((1 << LOGN) / kAdjBandRows, B), 256, AdjBandCfg<LOGN, kAdjBandRows>::SMEM, st>>>(sa);
     e = mark(cudaGetLastError(), "stage adjoint");
     ++*launches;
     if (e == cudaSuccess && learned) e = net_backward<LOGN>(c, s, dparams, st, launches);

@@ -48,6 +48,7 @@ struct LearnedState {
   __nv_bfloat16* coef = nullptr;
   float* acc = nullptr;
   float* wbuf = nullptr;
+  float* ws = nullptr;         // unprojected stage result of the banded flux kernel
   float* corr = nullptr;
   float* ring = nullptr;       // kc + 1 (or 2) states
   int nring = 0;

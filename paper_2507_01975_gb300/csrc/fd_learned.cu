@@ -18,6 +18,15 @@ using namespace ldfv;
 
 namespace {
 
+// kernel launches of one learned step: per stage the stencil network (input
+// packing, six layers with the last one in two launches) and the flux and
+// projection kernels; the temporal correction adds its network and the
+// corrected projection
+constexpr int kLaunchesPerStep = 4 * (8 + 2);
+constexpr int kLaunchesTc = 7 + 1;
+
+thread_local const char* g_where = "";  // the launch group that failed last
+
 template <int LOGN>
 cudaError_t prepare_kernels() {
   cudaError_t e;
@@ -30,11 +39,10 @@ cudaError_t prepare_kernels() {
   e = cudaFuncSetAttribute(conv3x3_tc_kernel<LOGN, 16, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ConvCfg<LOGN, 16, 64>::SMEM);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(fv_learned_stage_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)LearnedCfg<LOGN>::SMEM);
-  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fv_correct_project_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)LearnedCfg<LOGN>::SMEM);
+  if (e != cudaSuccess) return e;
+  e = prepare_learned_stage<LOGN>();
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(conv_in_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)((64 * 16 * 9 + 64) * sizeof(float)));
@@ -116,12 +124,15 @@ cudaError_t learned_step(fd_ctx* c, const float* s_in, float* s_out, const float
   a.coef = L.coef;
   for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
     e = run_stencil_net<LOGN>(c, s == 0 ? ptr_in : ptr_w, st);
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess) {
+      g_where = "stencil network";
+      break;
+    }
     a.stage = s;
     a.w = s == 0 ? s_in : L.wbuf;
     a.wout = s < 3 ? L.wbuf : s_out;
-    fv_learned_stage_kernel<LOGN><<<B, LearnedCfg<LOGN>::NT, LearnedCfg<LOGN>::SMEM, st>>>(a);
-    e = cudaGetLastError();
+    e = launch_learned_stage<LOGN>(a, L.ws, B, st);
+    if (e != cudaSuccess) g_where = "flux / projection kernels";
   }
   if (e == cudaSuccess && tc_hist) {
     e = run_tc_net<LOGN>(c, tc_hist, st);
@@ -309,6 +320,7 @@ fd_status fd_learned_init(fd_ctx* c) {
   alloc((void**)&L->coef, B * kCoef * NN * 2);
   alloc((void**)&L->acc, state);
   alloc((void**)&L->wbuf, state);
+  alloc((void**)&L->ws, state);
   alloc((void**)&L->corr, state);
   alloc((void**)&L->ring, state * L->nring);
   alloc((void**)&L->d_err, sizeof(unsigned));
@@ -349,7 +361,8 @@ void fd_learned_free(fd_ctx* c) {
   if (L->graph) cudaGraphExecDestroy(L->graph);
   if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
   void* ps[] = {L->d_raw,  L->d_wpack, L->d_stage, L->d_desc,         (void*)L->d_ranges, L->act0, L->act1,
-                L->coef,   L->acc,     L->wbuf,    L->corr,           L->ring,            (void*)L->d_ptrs,
+                L->coef,   L->acc,     L->wbuf,    L->ws,             L->corr,            L->ring,
+                (void*)L->d_ptrs,
                 L->d_err};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -433,7 +446,9 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
     return learned_step<5>(c, L.ring + r * slot, L.ring + (r + 1) * slot, pin, pw, ph, s);
   };
   int launches = 0;
+  g_where = "state copy";
   cudaError_t e = cudaMemcpyAsync(L.ring, u0, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) g_where = "";
   const bool use_graph = save_every == 0;
   if (e == cudaSuccess && use_graph && n_steps >= G && !L.graph) {
     // capture one group on the side stream; the history for the temporal
@@ -453,7 +468,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
   if (e == cudaSuccess && use_graph && L.graph) {
     for (; done + G <= n_steps && e == cudaSuccess; done += G) {
       e = cudaGraphLaunch(L.graph, st);
-      launches += G * (4 * 7);
+      launches += G * kLaunchesPerStep + (L.kc > 0 ? kLaunchesTc : 0);
     }
   }
   // remaining steps (or every step when snapshots are requested): direct launches
@@ -461,7 +476,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
     const int r = done % G;
     const bool tc = L.kc > 0 && ((done + 1) % L.kc == 0);
     e = step_fn(r, tc, st);
-    launches += 4 * 7 + (tc ? 7 : 0);
+    launches += kLaunchesPerStep + (tc ? kLaunchesTc : 0);
     if (e == cudaSuccess && save_every > 0 && traj && ((done + 1) % save_every) == 0) {
       e = cudaMemcpyAsync(static_cast<float*>(traj) + (size_t)snap * slot, L.ring + (r + 1) * slot, bytes,
                           cudaMemcpyDeviceToDevice, st);
@@ -473,7 +488,8 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
   const int rlast = n_steps == 0 ? 0 : (n_steps % G == 0 ? 0 : n_steps % G);
   if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, L.ring + rlast * slot, bytes, cudaMemcpyDeviceToDevice, st);
   c->launches = launches;
-  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout (learned): %s", cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return fd_set_error(c, FD_ECUDA, "fd_rollout (learned): %s: %s", g_where, cudaGetErrorString(e));
   return FD_OK;
 }
 

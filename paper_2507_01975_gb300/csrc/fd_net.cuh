@@ -13,6 +13,10 @@
 #include "fv_learned.cuh"
 
 namespace ldfv {
+// Every helper here that launches or configures kernel templates is static:
+// kernel stubs are private to each translation unit, so the helpers must be
+// too (an inline function merged across units could set an attribute on one
+// unit's kernel and launch the other's).
 
 constexpr int kHidden = 64;
 constexpr int kCoef = 160;
@@ -26,7 +30,7 @@ inline int tc_cout(int l) { return l == 5 ? 2 : kHidden; }
 // One tensor-core convolution over `parts` output-channel parts of COUT_TILE.
 // gelu: 0 none, 1 GELU (pre-activation to aux_out when set), 2 multiply by GELU'(aux_in).
 template <int LOGN, int COUT_TILE, int CIN = 64, int NBUF = 2>
-cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __nv_bfloat16* wpack,
+static cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __nv_bfloat16* wpack,
                         const float* bias, __nv_bfloat16* out, int batch, int parts, int co_base, int cout_total,
                         int gelu, cudaStream_t st, const __nv_bfloat16* aux_in = nullptr,
                         __nv_bfloat16* aux_out = nullptr) {
@@ -50,6 +54,33 @@ cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __
   const int grid = ntiles < L.sms ? ntiles : L.sms;
   conv3x3_tc_kernel<LOGN, CIN, COUT_TILE, NBUF><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a);
   return cudaGetLastError();
+}
+
+// One learned RK stage: the banded flux kernel writes the unprojected stage
+// result to `scratch` (a state-sized buffer distinct from a.w and a.wout), then
+// the projection kernel writes a.wout. 2 launches.
+constexpr int kBandRows = 8;
+
+template <int LOGN>
+static cudaError_t launch_learned_stage(const LStageArgs& a_in, float* scratch, int batch, cudaStream_t st) {
+  LStageArgs a = a_in;
+  a.wout = scratch;
+  fv_learned_flux_kernel<LOGN, kBandRows>
+      <<<dim3((1 << LOGN) / kBandRows, batch), 256, BandCfg<LOGN, kBandRows>::SMEM, st>>>(a);
+  LStageArgs p = a_in;
+  p.w = scratch;
+  fv_project_kernel<LOGN><<<batch, LearnedCfg<LOGN>::NT, LearnedCfg<LOGN>::SMEM, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int LOGN>
+static cudaError_t prepare_learned_stage() {
+  cudaError_t e = cudaFuncSetAttribute(fv_learned_flux_kernel<LOGN, kBandRows>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)BandCfg<LOGN, kBandRows>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fv_project_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)LearnedCfg<LOGN>::SMEM);
 }
 
 inline LStageArgs stage_args(fd_ctx* c) {

@@ -1,6 +1,6 @@
 // fv_adjoint.cuh -- reverse mode of one FV stage (flux block, flux assembly,
-// direct terms) and of the projection / RK4 combination, one CTA per
-// trajectory (N <= 64), FP32.
+// direct terms; banded over rows) and of the projection / RK4 combination (one
+// CTA per trajectory), N <= 64, FP32.
 //
 // The forward tendency H(w) (Sec. 3.4 face operators with per-face kernels
 // K = W_P + proj(W_L + C_theta(w)) / h^(deriv), App. B.2 flux assembly, Eq. 1
@@ -34,18 +34,6 @@ struct AdjStageArgs {
   float* wl_bar;               // out: W_L_bar [80], accumulated with atomics, or null
   int flow, forcing, dord;
   float nu, idx, idy, drag;
-};
-
-template <int LOGN>
-struct AdjCfg {
-  static constexpr int N = 1 << LOGN;
-  static constexpr int NT = N >= 64 ? 512 : 256;
-  static constexpr size_t F_BYTES = (size_t)2 * N * N * 4;
-  static constexpr size_t OFF_TB = F_BYTES;
-  static constexpr size_t OFF_I = 2 * F_BYTES;             // six face-value arrays
-  static constexpr size_t OFF_WB = OFF_I + (size_t)6 * N * N * 4;
-  static constexpr size_t SMEM = OFF_WB + F_BYTES;
-  static_assert(SMEM <= 232448 - 1024, "shared memory");
 };
 
 // Per-face kernel of instance qi (axis, kind) at cell c: K[20] (5 x 4, row-major).
@@ -112,31 +100,53 @@ __device__ __forceinline__ void adj_kernel_at(int qi, int axis, int kind, const 
     }
 }
 
-// flat index of tap (r, c) of an instance along `axis` with axial shift `sh` at cell (j, i)
-template <int N>
-__device__ __forceinline__ int adj_tap(int axis, int sh, int j, int i, int r, int cc) {
-  constexpr int MSK = N - 1;
-  return axis == 0 ? ((j + r - 2) & MSK) * N + ((i + cc + sh) & MSK) : ((j + cc + sh) & MSK) * N + ((i + r - 2) & MSK);
-}
+// ---------------------------------------------------------------------------
+// The faces of RB rows of one trajectory per CTA (grid
+// N/RB x batch, 256 threads). The scatter w_bar[tap] += K v_bar of a band covers
+// rows j0 - 2 .. j0 + RB + 1; it is accumulated in shared memory and added to
+// the zero-initialised global w_bar with atomics. Rows are tile-relative:
+// global row jj sits at tile row (jj - first row) mod N.
+// ---------------------------------------------------------------------------
+template <int LOGN, int RB>
+struct AdjBandCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int NT = 256;
+  static constexpr int WR = RB + 5;  // w rows j0 - 3 .. j0 + RB + 1
+  static constexpr int TRR = RB + 2; // T_bar rows j0 - 1 .. j0 + RB
+  static constexpr int FR = RB + 1;  // face-value rows j0 - 1 .. j0 + RB - 1
+  static constexpr int BR = RB + 4;  // w_bar rows j0 - 2 .. j0 + RB + 1
+  static constexpr size_t SMEM = ((size_t)2 * WR * N + (size_t)2 * TRR * N + (size_t)6 * FR * N + (size_t)2 * BR * N) * 4;
+};
 
-template <int LOGN>
-__global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(const AdjStageArgs a) {
-  using Cfg = AdjCfg<LOGN>;
-  constexpr int N = Cfg::N, NT = Cfg::NT, MSK = N - 1;
+template <int LOGN, int RB>
+__global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs a) {
+  using Cfg = AdjBandCfg<LOGN, RB>;
+  constexpr int N = Cfg::N, NT = Cfg::NT, MSK = N - 1, WR = Cfg::WR, TRR = Cfg::TRR, FR = Cfg::FR, BR = Cfg::BR;
   constexpr size_t NN = (size_t)N * N;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  float* const wt = reinterpret_cast<float*>(smem);
-  float* const tb = reinterpret_cast<float*>(smem + Cfg::OFF_TB);
-  float* const inst = reinterpret_cast<float*>(smem + Cfg::OFF_I);
-  float* const wb = reinterpret_cast<float*>(smem + Cfg::OFF_WB);
+  extern __shared__ __align__(16) float asm_[];
+  float* const wt = asm_;                  // [2][WR][N]
+  float* const tb = wt + 2 * WR * N;       // [2][TRR][N]
+  float* const inst = tb + 2 * TRR * N;    // [6][FR][N]
+  float* const wb = inst + 6 * FR * N;     // [2][BR][N]
   __shared__ float swl[80];
   __shared__ float swlb[80];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int b = blockIdx.x;
-  for (size_t c = tid; c < 2 * NN; c += NT) {
-    wt[c] = a.w[(size_t)b * 2 * NN + c];
-    tb[c] = a.tbar[(size_t)b * 2 * NN + c];
+  const int b = blockIdx.y, j0 = blockIdx.x * RB;
+  const float* w = a.w + (size_t)b * 2 * NN;
+  const float* tg = a.tbar + (size_t)b * 2 * NN;
+  auto W = [&](int fld, int jj, int ii) { return wt[(fld * WR + ((jj - j0 + 3) & MSK)) * N + (ii & MSK)]; };
+  auto T = [&](int fld, int jj, int ii) { return tb[(fld * TRR + ((jj - j0 + 1) & MSK)) * N + (ii & MSK)]; };
+  auto F = [&](int sl, int jj, int ii) { return inst[(sl * FR + ((jj - j0 + 1) & MSK)) * N + (ii & MSK)]; };
+  auto WB = [&](int fld, int jj, int ii) -> float& { return wb[(fld * BR + ((jj - j0 + 2) & MSK)) * N + (ii & MSK)]; };
+  for (int k = tid; k < 2 * WR * N; k += NT) {
+    const int f = k / (WR * N), rem = k - f * WR * N;
+    wt[k] = w[(size_t)f * NN + (size_t)((j0 - 3 + (rem >> LOGN)) & MSK) * N + (rem & MSK)];
   }
+  for (int k = tid; k < 2 * TRR * N; k += NT) {
+    const int f = k / (TRR * N), rem = k - f * TRR * N;
+    tb[k] = tg[(size_t)f * NN + (size_t)((j0 - 1 + (rem >> LOGN)) & MSK) * N + (rem & MSK)];
+  }
+  for (int k = tid; k < 2 * BR * N; k += NT) wb[k] = 0.f;
   if (tid < 80) {
     swl[tid] = a.wl ? a.wl[tid] : 0.f;
     swlb[tid] = 0.f;
@@ -147,11 +157,12 @@ __global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(c
   const float hx = 1.0f / a.idx, hy = 1.0f / a.idy;
   const bool burgers = a.flow == 0;
 
-  // ---- forward face values needed by the reverse pass --------------------------------
+  // forward face values of rows j0 - 1 .. j0 + RB - 1
   // slots: 0 Uc (q0), 1 Uk (q2), 2 Vk (q4), 3 Vc (q6), 4 Gxc (q1), 5 Gyc (q7)
   const int nslot = burgers ? 6 : 4;
-  for (int c = tid; c < (int)NN; c += NT) {
-    const int j = c / N, i = c % N;
+  for (int fc = tid; fc < FR * N; fc += NT) {
+    const int j = (j0 - 1 + (fc >> LOGN)) & MSK, i = fc & MSK;
+    const int c = j * N + i;
 #pragma unroll 1
     for (int sl = 0; sl < nslot; ++sl) {
       const int qi = sl < 4 ? 2 * sl : (sl == 4 ? 1 : 7);
@@ -163,40 +174,35 @@ __global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(c
 #pragma unroll
       for (int r = 0; r < 5; ++r)
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) v += K[r * 4 + cc] * wt[fld * NN + adj_tap<N>(axis, sh, j, i, r, cc)];
-      inst[sl * NN + c] = v;
+        for (int cc = 0; cc < 4; ++cc) {
+          const int jj = axis == 0 ? j + r - 2 : j + cc + sh;
+          const int ii = axis == 0 ? i + cc + sh : i + r - 2;
+          v += K[r * 4 + cc] * W(fld, jj, ii);
+        }
+      inst[(sl * FR + (fc >> LOGN)) * N + i] = v;
     }
   }
   __syncthreads();
-  const float* Uc = inst + 0 * NN;
-  const float* Uk = inst + 1 * NN;
-  const float* Vk = inst + 2 * NN;
-  const float* Vc = inst + 3 * NN;
-  const float* Gxc = inst + 4 * NN;
-  const float* Gyc = inst + 5 * NN;
-  const float* Tu = tb;
-  const float* Tv = tb + NN;
 
-  // ---- direct terms (Burgers advective correction, linear drag) -------------------
-  for (int c = tid; c < (int)NN; c += NT) {
-    const int j = c / N, i = c % N;
+  // direct terms of the owned cells (Burgers advective correction, drag)
+  for (int k = tid; k < RB * N; k += NT) {
+    const int j = j0 + (k >> LOGN), i = k & MSK;
     float du = 0.f, dv = 0.f;
     if (burgers) {
-      const int cw = j * N + ((i - 1) & MSK), cs = ((j - 1) & MSK) * N + i;
-      const float d0 = Gxc[c] + Gyc[c];
-      du += Tu[c] * 0.5f * ((Gxc[cw] + Gyc[cw]) + d0);
-      dv += Tv[c] * 0.5f * ((Gxc[cs] + Gyc[cs]) + d0);
+      const float d0 = F(4, j, i) + F(5, j, i);
+      du += T(0, j, i) * 0.5f * ((F(4, j, i - 1) + F(5, j, i - 1)) + d0);
+      dv += T(1, j, i) * 0.5f * ((F(4, j - 1, i) + F(5, j - 1, i)) + d0);
     }
     if (a.forcing == 1) {
-      du -= a.drag * Tu[c];
-      dv -= a.drag * Tv[c];
+      du -= a.drag * T(0, j, i);
+      dv -= a.drag * T(1, j, i);
     }
-    wb[c] = du;
-    wb[NN + c] = dv;
+    WB(0, j, i) += du;
+    WB(1, j, i) += dv;
   }
   __syncthreads();
 
-  // ---- reverse through the eight face operators ------------------------------------
+  // reverse through the eight face operators of the owned faces
   const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
 #pragma unroll 1
   for (int qi = 0; qi < 8; ++qi) {
@@ -207,24 +213,23 @@ __global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(c
     float lsum[20];
 #pragma unroll
     for (int t = 0; t < 20; ++t) lsum[t] = 0.f;
-    for (int c = tid; c < (int)NN; c += NT) {
-      const int j = c / N, i = c % N;
-      const int ce = j * N + ((i + 1) & MSK), cw = j * N + ((i - 1) & MSK);
-      const int cn = ((j + 1) & MSK) * N + i, cs = ((j - 1) & MSK) * N + i;
-      // cotangent of this face value (product rule of the flux assembly)
+    for (int k = tid; k < RB * N; k += NT) {
+      const int j = j0 + (k >> LOGN), i = k & MSK;
+      const int c = j * N + i;
       float vb;
       switch (qi) {
-        case 0: vb = 2.0f * Uc[c] * (Tu[ce] - Tu[c]) * a.idx; break;
-        case 1: vb = a.nu * (Tu[c] - Tu[ce]) * a.idx; break;
-        case 2: vb = ((Tu[c] - Tu[cs]) * a.idy + (Tv[c] - Tv[cw]) * a.idx) * Vk[c]; break;
-        case 3: vb = a.nu * (Tu[cs] - Tu[c]) * a.idy; break;
-        case 4: vb = ((Tu[c] - Tu[cs]) * a.idy + (Tv[c] - Tv[cw]) * a.idx) * Uk[c]; break;
-        case 5: vb = a.nu * (Tv[cw] - Tv[c]) * a.idx; break;
-        case 6: vb = 2.0f * Vc[c] * (Tv[cn] - Tv[c]) * a.idy; break;
-        default: vb = a.nu * (Tv[c] - Tv[cn]) * a.idy; break;
+        case 0: vb = 2.0f * F(0, j, i) * (T(0, j, i + 1) - T(0, j, i)) * a.idx; break;
+        case 1: vb = a.nu * (T(0, j, i) - T(0, j, i + 1)) * a.idx; break;
+        case 2: vb = ((T(0, j, i) - T(0, j - 1, i)) * a.idy + (T(1, j, i) - T(1, j, i - 1)) * a.idx) * F(2, j, i); break;
+        case 3: vb = a.nu * (T(0, j - 1, i) - T(0, j, i)) * a.idy; break;
+        case 4: vb = ((T(0, j, i) - T(0, j - 1, i)) * a.idy + (T(1, j, i) - T(1, j, i - 1)) * a.idx) * F(1, j, i); break;
+        case 5: vb = a.nu * (T(1, j, i - 1) - T(1, j, i)) * a.idx; break;
+        case 6: vb = 2.0f * F(3, j, i) * (T(1, j + 1, i) - T(1, j, i)) * a.idy; break;
+        default: vb = a.nu * (T(1, j, i) - T(1, j + 1, i)) * a.idy; break;
       }
       if (burgers && (qi == 1 || qi == 7))
-        vb += 0.5f * (Tu[c] * wt[c] + Tu[ce] * wt[ce]) + 0.5f * (Tv[c] * wt[NN + c] + Tv[cn] * wt[NN + cn]);
+        vb += 0.5f * (T(0, j, i) * W(0, j, i) + T(0, j, i + 1) * W(0, j, i + 1)) +
+              0.5f * (T(1, j, i) * W(1, j, i) + T(1, j + 1, i) * W(1, j + 1, i));
       float K[20];
       adj_kernel_at(qi, axis, kind, swlp, cbase, NN, c, a.dord, h, K);
       float Kb[20];
@@ -232,11 +237,11 @@ __global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(c
       for (int r = 0; r < 5; ++r)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          const int t = adj_tap<N>(axis, sh, j, i, r, cc);
-          atomicAdd(&wb[fld * NN + t], K[r * 4 + cc] * vb);
-          Kb[r * 4 + cc] = vb * wt[fld * NN + t];
+          const int jj = axis == 0 ? j + r - 2 : j + cc + sh;
+          const int ii = axis == 0 ? i + cc + sh : i + r - 2;
+          atomicAdd(&WB(fld, jj, ii), K[r * 4 + cc] * vb);
+          Kb[r * 4 + cc] = vb * W(fld, jj, ii);
         }
-      // C_bar = proj(K_bar) * scale (the projector is symmetric)
       float s1 = 0.f, sc = 0.f, sr = 0.f;
 #pragma unroll
       for (int r = 0; r < 5; ++r)
@@ -263,8 +268,6 @@ __global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(c
         for (int t = 0; t < 20; ++t) a.cbar_f32[((size_t)b * 160 + qi * 20 + t) * NN + c] = lb[t];
       }
       if (a.cbar) {
-        // channels 20 qi + t: even qi -> chunks k0, k0+1 and the low half of k0+2;
-        // odd qi -> the high half of k0, then k0+1 and k0+2 (8-byte halves do not overlap)
         uint32_t pk[10];
 #pragma unroll
         for (int e = 0; e < 10; ++e) {
@@ -285,7 +288,6 @@ __global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(c
       }
     }
     if (a.wl_bar) {
-      // W_L_bar[kind][axis] gathers the learned-part cotangent of both fields
 #pragma unroll
       for (int t = 0; t < 20; ++t) {
         float v = lsum[t];
@@ -296,7 +298,12 @@ __global__ void __launch_bounds__(AdjCfg<LOGN>::NT, 1) fv_adjoint_stage_kernel(c
     }
   }
   __syncthreads();
-  for (size_t c = tid; c < 2 * NN; c += NT) a.wbar[(size_t)b * 2 * NN + c] = wb[c];
+  float* gw = a.wbar + (size_t)b * 2 * NN;
+  for (int k = tid; k < 2 * BR * N; k += NT) {
+    const int f = k / (BR * N), rem = k - f * BR * N;
+    const int jj = (j0 - 2 + (rem >> LOGN)) & MSK;
+    atomicAdd(&gw[(size_t)f * NN + (size_t)jj * N + (rem & MSK)], wb[k]);
+  }
   if (a.wl_bar && tid < 80) atomicAdd(&a.wl_bar[tid], swlb[tid]);
 }
 

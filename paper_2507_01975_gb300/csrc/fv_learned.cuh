@@ -1,5 +1,6 @@
-// fv_learned.cuh -- one RK stage of the learned FV step, and the corrected
-// projection of the temporal-correction step (one CTA per trajectory, N <= 64).
+// fv_learned.cuh -- one RK stage of the learned FV step (banded flux kernel +
+// per-trajectory projection), and the corrected projection of the
+// temporal-correction step (N <= 64).
 //
 // Flux block with learned per-face kernels (Sec. 3.4, integrated operator):
 // for each of the eight operator instances q (u/v x x/y x interp/deriv) the
@@ -249,64 +250,68 @@ __device__ void project_tile(float* wt, unsigned char* scr, const float2* tw, co
   __syncthreads();
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kernel(const LStageArgs a) {
-  using Cfg = LearnedCfg<LOGN>;
-  constexpr int N = Cfg::N, NT = Cfg::NT, MSK = N - 1;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  float* const wt = reinterpret_cast<float*>(smem);
-  float* const inst = reinterpret_cast<float*>(smem + Cfg::OFF_I);
-  unsigned char* const scr = smem + Cfg::OFF_SCR;
-  float2* const tw = reinterpret_cast<float2*>(smem + Cfg::OFF_TW);
-  float* const sx = reinterpret_cast<float*>(smem + Cfg::OFF_SX);
-  float* const sy = reinterpret_cast<float*>(smem + Cfg::OFF_SY);
-  float* const frc = reinterpret_cast<float*>(smem + Cfg::OFF_FRC);
+// ---------------------------------------------------------------------------
+// Banded variant of one learned stage: the flux block, flux assembly and RK
+// combination of RB rows of one trajectory per CTA (grid N/RB x batch, 256
+// threads), writing the unprojected stage result w*; fv_project_kernel then
+// projects each trajectory. Splitting the trajectory over N/RB CTAs hides the
+// latency of the network-output loads that bound the one-CTA-per-trajectory
+// kernel at small batch.
+// ---------------------------------------------------------------------------
+template <int LOGN, int RB>
+struct BandCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int NT = 256;
+  static constexpr int TR = RB + 6;  // tile rows j0 - 3 .. j0 + RB + 2
+  static constexpr int FR = RB + 2;  // face rows j0 - 1 .. j0 + RB
+  static constexpr size_t SMEM = (size_t)2 * TR * N * 4 + (size_t)8 * FR * N * 4;
+};
+
+template <int LOGN, int RB>
+__global__ void __launch_bounds__(256) fv_learned_flux_kernel(const LStageArgs a) {
+  using Cfg = BandCfg<LOGN, RB>;
+  constexpr int N = Cfg::N, NT = Cfg::NT, MSK = N - 1, TR = Cfg::TR, FR = Cfg::FR;
+  extern __shared__ __align__(16) float bsm[];
+  float* const wt = bsm;                 // [2][TR][N]
+  float* const inst = bsm + 2 * TR * N;  // [8][FR][N]
+  __shared__ float swl[80];
   const int tid = threadIdx.x;
-  const int b = blockIdx.x;
+  const int b = blockIdx.y, j0 = blockIdx.x * RB;
   const size_t NN = (size_t)N * N;
   const float* w = a.w + (size_t)b * 2 * NN;
-  const float* un = a.un + (size_t)b * 2 * NN;
-  float* acc = a.acc + (size_t)b * 2 * NN;
-  float* wout = a.wout + (size_t)b * 2 * NN;
-
-  for (int k = tid; k < N / 2; k += NT) tw[k] = a.tw[k];
-  for (int k = tid; k <= N / 2; k += NT) sx[k] = a.symx[k];
-  for (int k = tid; k < N; k += NT) {
-    sy[k] = a.symy[k];
-    frc[k] = a.frc[k];
+  for (int k = tid; k < 2 * TR * N; k += NT) {
+    const int f = k / (TR * N), rem = k - f * TR * N;
+    const int tr = rem >> LOGN, i = rem & MSK;
+    wt[k] = w[(size_t)f * NN + (size_t)((j0 - 3 + tr) & MSK) * N + i];
   }
-  for (int c = tid; c < 2 * N * N; c += NT) wt[c] = w[c];
-  __syncthreads();
-
-  // ---- flux block: the eight instance values at every index -------------------
-  // Instances come in (interp, deriv) pairs that share field, axis and taps:
-  // pair p = 0 u-x, 1 u-y, 2 v-x, 3 v-y (instances 2p and 2p + 1).
-  __shared__ float swl[80];
   if (tid < 80) swl[tid] = a.wl[tid];
   __syncthreads();
   const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
   const uint4* cbase = a.coef ? reinterpret_cast<const uint4*>(a.coef) + (size_t)b * 20 * NN : nullptr;
-  for (int c = tid; c < N * N; c += NT) {
-    const int j = c / N, i = c % N;
+  // face values of rows j0 - 1 .. j0 + RB
+  for (int fc = tid; fc < FR * N; fc += NT) {
+    const int fr = fc >> LOGN, i = fc & MSK;
+    const int j = (j0 - 1 + fr) & MSK;
+    const int c = j * N + i;
 #pragma unroll 1
     for (int pr_ = 0; pr_ < 4; ++pr_) {
       const int fld = pr_ >> 1, axis = pr_ & 1;
       const int sh = (pr_ == 0 || pr_ == 3) ? -1 : -2;
-      const float* f = wt + fld * NN;
+      const float* f = wt + fld * TR * N;
       float tap[20];
 #pragma unroll
       for (int r = 0; r < 5; ++r)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          int jj, ii;
+          int tr, ii;
           if (axis == 0) {
-            jj = (j + r - 2) & MSK;
+            tr = fr + r;  // tile row of j + r - 2
             ii = (i + cc + sh) & MSK;
           } else {
-            jj = (j + cc + sh) & MSK;
+            tr = fr + 2 + cc + sh;
             ii = (i + r - 2) & MSK;
           }
-          tap[r * 4 + cc] = f[jj * N + ii];
+          tap[r * 4 + cc] = f[tr * N + ii];
         }
       const float h = axis == 0 ? 1.0f / a.idx : 1.0f / a.idy;
 #pragma unroll
@@ -316,8 +321,6 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kern
 #pragma unroll
         for (int t = 0; t < 20; ++t) L[t] = swl[(kind * 2 + axis) * 20 + t];
         if (cbase) {
-          // channels 20 qi .. 20 qi + 19 lie in the three 8-channel chunks from
-          // (20 qi) / 8, starting at offset 0 (qi even) or 4 (qi odd)
           const int k0 = (20 * qi) >> 3;
           float fch[24];
 #pragma unroll
@@ -339,7 +342,6 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kern
             for (int t = 0; t < 20; ++t) L[t] += fch[4 + t];
           }
         }
-        // consistency projection: remove sum, axial and transverse first moments
         float s1 = 0.f, sc = 0.f, sr = 0.f;
 #pragma unroll
         for (int r = 0; r < 5; ++r)
@@ -361,7 +363,6 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kern
           for (int cc = 0; cc < 4; ++cc) {
             float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
             if (r == 2) {
-              // physics kernel W_P on the centre row
               if (kind == 0) {
                 k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
               } else if (a.dord == 4) {
@@ -374,63 +375,85 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_learned_stage_kern
             }
             val += k * tap[r * 4 + cc];
           }
-        inst[qi * NN + c] = val;
+        inst[(qi * FR + fr) * N + i] = val;
       }
     }
   }
   __syncthreads();
-
-  // ---- flux assembly, RK4 combination ----------------------------------------------
-  const float* Uc = inst + 0 * NN;
-  const float* Gxc = inst + 1 * NN;
-  const float* Uk = inst + 2 * NN;
-  const float* Gyu = inst + 3 * NN;
-  const float* Vk = inst + 4 * NN;
-  const float* Gxv = inst + 5 * NN;
-  const float* Vc = inst + 6 * NN;
-  const float* Gyc = inst + 7 * NN;
-  const int stage = a.stage;
-  const float ca = stage == 2 ? a.dt : 0.5f * a.dt;
+  // flux assembly and RK combination of rows j0 .. j0 + RB - 1 (face row = row - j0 + 1)
+  const float ca = a.stage == 2 ? a.dt : 0.5f * a.dt;
   const float c6 = a.dt / 6.0f;
-  for (int c = tid; c < N * N; c += NT) {
-    const int j = c / N, i = c % N;
-    const int iw = (i - 1) & MSK, ie = (i + 1) & MSK, js = (j - 1) & MSK, jn = (j + 1) & MSK;
-    const int cw = j * N + iw, ce = j * N + ie, cs = js * N + i, cn = jn * N + i;
-    float tu = -(Uc[c] * Uc[c] - Uc[cw] * Uc[cw]) * a.idx - (Uk[cn] * Vk[cn] - Uk[c] * Vk[c]) * a.idy +
-               a.nu * ((Gxc[c] - Gxc[cw]) * a.idx + (Gyu[cn] - Gyu[c]) * a.idy);
-    float tv = -(Uk[ce] * Vk[ce] - Uk[c] * Vk[c]) * a.idx - (Vc[c] * Vc[c] - Vc[cs] * Vc[cs]) * a.idy +
-               a.nu * ((Gxv[ce] - Gxv[c]) * a.idx + (Gyc[c] - Gyc[cs]) * a.idy);
-    const float uc = wt[c], vc = wt[NN + c];
+  auto I_ = [&](int q, int fr, int i) { return inst[(q * FR + fr) * N + (i & MSK)]; };
+  for (int k = tid; k < RB * N; k += NT) {
+    const int rr = k >> LOGN, i = k & MSK;
+    const int fr = rr + 1, j = j0 + rr;
+    const float Uc = I_(0, fr, i), Ucw = I_(0, fr, i - 1);
+    const float Gxc = I_(1, fr, i), Gxcw = I_(1, fr, i - 1);
+    const float Uk = I_(2, fr, i), Ukn = I_(2, fr + 1, i), Uke = I_(2, fr, i + 1);
+    const float Gyu = I_(3, fr, i), Gyun = I_(3, fr + 1, i);
+    const float Vk = I_(4, fr, i), Vkn = I_(4, fr + 1, i), Vke = I_(4, fr, i + 1);
+    const float Gxv = I_(5, fr, i), Gxve = I_(5, fr, i + 1);
+    const float Vc = I_(6, fr, i), Vcs = I_(6, fr - 1, i);
+    const float Gyc = I_(7, fr, i), Gycs = I_(7, fr - 1, i);
+    float tu = -(Uc * Uc - Ucw * Ucw) * a.idx - (Ukn * Vkn - Uk * Vk) * a.idy +
+               a.nu * ((Gxc - Gxcw) * a.idx + (Gyun - Gyu) * a.idy);
+    float tv = -(Uke * Vke - Uk * Vk) * a.idx - (Vc * Vc - Vcs * Vcs) * a.idy +
+               a.nu * ((Gxve - Gxv) * a.idx + (Gyc - Gycs) * a.idy);
+    const float uc = wt[(rr + 3) * N + i], vc = wt[TR * N + (rr + 3) * N + i];
     if (a.flow == 0) {
-      const float d0 = Gxc[c] + Gyc[c];
-      tu += uc * 0.5f * ((Gxc[cw] + Gyc[cw]) + d0);
-      tv += vc * 0.5f * ((Gxc[cs] + Gyc[cs]) + d0);
+      const float d0 = Gxc + Gyc;
+      tu += uc * 0.5f * ((Gxcw + I_(7, fr, i - 1)) + d0);
+      tv += vc * 0.5f * ((I_(1, fr - 1, i) + Gycs) + d0);
     }
     if (a.forcing == 1) {
-      tu += frc[j] - a.drag * uc;
+      tu += a.frc[j] - a.drag * uc;
       tv += -a.drag * vc;
     }
+    const size_t g = (size_t)b * 2 * NN + (size_t)j * N + i;
+    float* acc = a.acc;
     float au, av;
-    if (stage == 0) {
+    if (a.stage == 0) {
       au = tu;
       av = tv;
     } else {
-      au = acc[c] + (stage < 3 ? 2.0f : 1.0f) * tu;
-      av = acc[NN + c] + (stage < 3 ? 2.0f : 1.0f) * tv;
+      au = acc[g] + (a.stage < 3 ? 2.0f : 1.0f) * tu;
+      av = acc[g + NN] + (a.stage < 3 ? 2.0f : 1.0f) * tv;
     }
-    if (stage < 3) {
-      acc[c] = au;
-      acc[NN + c] = av;
-      wt[c] = un[c] + ca * tu;
-      wt[NN + c] = un[NN + c] + ca * tv;
+    if (a.stage < 3) {
+      acc[g] = au;
+      acc[g + NN] = av;
+      a.wout[g] = a.un[g] + ca * tu;
+      a.wout[g + NN] = a.un[g + NN] + ca * tv;
     } else {
-      wt[c] = un[c] + c6 * au;
-      wt[NN + c] = un[NN + c] + c6 * av;
+      a.wout[g] = a.un[g] + c6 * au;
+      a.wout[g + NN] = a.un[g + NN] + c6 * av;
     }
   }
+}
+
+// w <- P(w*) for each trajectory (one CTA per trajectory, projection in shared memory;
+// a plain copy for Burgers)
+template <int LOGN>
+__global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_project_kernel(const LStageArgs a) {
+  using Cfg = LearnedCfg<LOGN>;
+  constexpr int N = Cfg::N, NT = Cfg::NT;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* const wt = reinterpret_cast<float*>(smem);
+  unsigned char* const scr = smem + Cfg::OFF_SCR;
+  float2* const tw = reinterpret_cast<float2*>(smem + Cfg::OFF_TW);
+  float* const sx = reinterpret_cast<float*>(smem + Cfg::OFF_SX);
+  float* const sy = reinterpret_cast<float*>(smem + Cfg::OFF_SY);
+  const int tid = threadIdx.x;
+  const size_t NN = (size_t)N * N;
+  const float* src = a.w + (size_t)blockIdx.x * 2 * NN;
+  float* dst = a.wout + (size_t)blockIdx.x * 2 * NN;
+  for (int k = tid; k < N / 2; k += NT) tw[k] = a.tw[k];
+  for (int k = tid; k <= N / 2; k += NT) sx[k] = a.symx[k];
+  for (int k = tid; k < N; k += NT) sy[k] = a.symy[k];
+  for (int c = tid; c < 2 * N * N; c += NT) wt[c] = src[c];
   __syncthreads();
-  if (a.flow == 1) project_tile<LOGN, NT>(wt, scr, tw, sx, sy, a.idx, a.idy, a.inv_nn);
-  for (int c = tid; c < 2 * N * N; c += NT) wout[c] = wt[c];
+  if (a.flow == 1) project_tile<LOGN, NT>(wt, scr, tw, sx, sy, a.idx, a.idy, a.inv_nn);  // Burgers: a copy
+  for (int c = tid; c < 2 * N * N; c += NT) dst[c] = wt[c];
 }
 
 // Temporal correction (Sec. 3.2, Sec. 3.5): u <- P(u + c - mean(c)) for each

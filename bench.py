@@ -412,6 +412,60 @@ def corr_measurement(fd, I, n_fine: int = 1024, n_train: int = 4, n_test: int = 
     return out
 
 
+def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
+    """Mixed batch (512 trajectories): plain FP32 32^2 Burgers, 64^2 decaying, 128^2
+    Kolmogorov, 256^2 shear (64 each) and learned BF16-network 32^2 Kolmogorov and 64^2
+    decaying (128 each), every group advanced by the same physical time T with the
+    CFL-matched step dt(N) = 1.75e-3 * 256 / N, all in one graph (fd_batch). Reported:
+    cell-updates/s of the graph, and the same rollouts run one after another."""
+    import torch
+
+    st = I.random_conv_stack(12, 2, 64, 160, last_scale=0.05)
+    params = I.pack_params(I.random_wl(13, 1e-2), st)
+    groups = [(32, 64, "burgers", False), (64, 64, "decaying", False), (128, 64, "kolmogorov", False),
+              (256, 64, "shear", False), (32, 128, "kolmogorov", True), (64, 128, "decaying", True)]
+    batch = fd.Batch()
+    runs = []
+    cells = 0
+    for n, b, kind, learned in groups:
+        dt = 1.75e-3 * 256 / n
+        steps = int(round(T / dt))
+        cfg = fd.Config(n=n, batch=b, dtype="f32", nu=1e-2 if kind == "burgers" else 1e-3, dt=dt,
+                        flow="burgers" if kind == "burgers" else "ns",
+                        forcing="kolmogorov" if kind == "kolmogorov" else None, learned=learned)
+        s = fd.Solver(cfg)
+        if learned:
+            s.set_params(params)
+        u0 = torch.tensor(I.ic_batch(kind, n, b, seed0=300).astype(np.float32), device="cuda")
+        out = torch.empty_like(u0)
+        batch.add(s, u0, out, steps)
+        runs.append((s, u0, out, steps))
+        cells += b * n * n * steps
+    batch.run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        batch.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    for s, u0, out, steps in runs:  # warm every solver's own path
+        s.rollout(u0, out, steps)
+    e0.record(stream)
+    for s, u0, out, steps in runs:
+        s.rollout(u0, out, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    return {"workload": "512 trajectories: plain FP32 32^2 Burgers, 64^2 decaying, 128^2 Kolmogorov, 256^2 shear "
+                        "(64 each) + learned 32^2 Kolmogorov, 64^2 decaying (128 each), physical time 0.5 each",
+            "value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_batch": ms,
+            "ms_one_after_another": ms_seq, "graph_kernel_launches": batch.launch_count(),
+            "finite": all(bool(s.check_finite(out)) for s, _, out, _ in runs)}
+
+
 def adjoint_measurement(fd, I, iters: int = 5):
     """Reverse mode of one learned step (shear layer 64^2, batch 32) alone."""
     import torch
@@ -446,7 +500,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-fine", action="store_true", help="skip the 2048^2 streaming-path measurement")
-    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr"],
+    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
     ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
@@ -469,7 +523,8 @@ def main():
               "training": lambda: training_measurement(fd, I, iters=args.iters),
               "adjoint": lambda: adjoint_measurement(fd, I, iters=args.iters),
               "fine": lambda: fine_measurement(fd, I, steps=max(args.iters, 2)),
-              "corr": lambda: corr_measurement(fd, I, iters=args.iters)}[args.only]
+              "corr": lambda: corr_measurement(fd, I, iters=args.iters),
+              "batch": lambda: batch_measurement(fd, I)}[args.only]
         print(json.dumps(fn()), flush=True)
         return
 

@@ -254,6 +254,27 @@ fd_status fd_adam_step(float* params, float* grads, float* m, float* v, int64_t 
 fd_status fd_downsample(const void* fine, void* coarse, int32_t batch, int32_t n_fine, int32_t ratio,
                         int32_t dtype, void* stream);
 
+/* ---- batches of rollouts ----------------------------------------------------
+ *
+ * Many concurrent trajectories of uneven grid sizes and flow types, learned
+ * and plain: one context per (grid, flow, dtype, learned) group, each with its
+ * own device states; a batch runs every member's rollout as one CUDA graph
+ * with a parallel branch per member (captured by the first fd_batch_run after
+ * the last fd_batch_add, replayed by a single graph launch afterwards). The
+ * paper has no counterpart (it advances one trajectory at a time); this is the
+ * serving form of fd_rollout. A context may appear once per batch and must not
+ * be used by other calls while its batch runs; the state pointers are fixed at
+ * fd_batch_add (u_final may alias u0). */
+typedef struct fd_batch fd_batch; /* opaque, library-owned */
+
+fd_status fd_batch_create(fd_batch** out);
+fd_status fd_batch_add(fd_batch* batch, fd_ctx* ctx, const void* u0, void* u_final, int32_t n_steps);
+fd_status fd_batch_run(fd_batch* batch, void* stream);
+/* kernel launches inside one fd_batch_run (the graph's kernel nodes) */
+int32_t fd_batch_launch_count(const fd_batch* batch);
+const char* fd_batch_last_error(const fd_batch* batch);
+fd_status fd_batch_destroy(fd_batch* batch);
+
 /* Release the context and its device tables (synchronises the device). */
 fd_status fd_destroy(fd_ctx* ctx);
 

@@ -25,14 +25,14 @@ void fd_learned_free(fd_ctx* c);
 void fd_adjoint_free(fd_ctx* c);
 void fd_train_free(fd_ctx* c);
 fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
-                             cudaStream_t st);
+                             cudaStream_t st, bool allow_graph);
 fd_status fd_learned_error_flag(fd_ctx* c);
 // streaming path (fd_large.cu)
 bool fd_large_supported(int dtype, int n);
 fd_status fd_large_init(fd_ctx* c);
 void fd_large_free(fd_ctx* c);
 fd_status fd_large_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
-                           cudaStream_t st);
+                           cudaStream_t st, bool allow_graph);
 
 namespace {
 
@@ -297,16 +297,21 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   return FD_OK;
 }
 
-fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32_t n_steps,
-                     int32_t save_every, void* stream) {
+}  // extern "C"
+
+// rollout behind fd_rollout; allow_graph = false issues every launch directly
+// (for callers that capture the work into a graph of their own)
+fd_status fd_rollout_impl(fd_ctx* c, const void* u0, void* traj, void* u_final, int32_t n_steps, int32_t save_every,
+                          void* stream, bool allow_graph) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout: null context");
   c->launches = 0;
   if (!u0 || !u_final) return fd_set_error(c, FD_EINVAL, "fd_rollout: null state pointer");
   if (n_steps < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout: n_steps must be >= 0");
   if (save_every < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every must be >= 0");
   if (save_every > 0 && !traj) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every > 0 needs traj");
-  if (c->lrn) return fd_learned_rollout(c, u0, traj, u_final, n_steps, save_every, static_cast<cudaStream_t>(stream));
-  if (c->big) return fd_large_rollout(c, u0, traj, u_final, n_steps, save_every, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->lrn) return fd_learned_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
+  if (c->big) return fd_large_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
   FvArgs a = c->base;
   a.u_in = u0;
   a.u_out = u_final;
@@ -317,6 +322,13 @@ fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout: launch failed: %s", cudaGetErrorString(e));
   c->launches = 1;
   return FD_OK;
+}
+
+extern "C" {
+
+fd_status fd_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int32_t n_steps,
+                     int32_t save_every, void* stream) {
+  return fd_rollout_impl(c, u0, traj, u_final, n_steps, save_every, stream, true);
 }
 
 fd_status fd_step(fd_ctx* c, const void* u_in, void* u_out, void* stream) {

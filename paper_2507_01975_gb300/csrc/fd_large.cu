@@ -126,12 +126,13 @@ void fd_large_free(fd_ctx* c) {
 }
 
 fd_status fd_large_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool allow_graph) {
   LargeState& S = *c->big;
   const size_t bytes = fd_state_bytes(c->grid);
   cudaError_t e = cudaMemcpyAsync(S.un, u0, bytes, cudaMemcpyDeviceToDevice, st);
   int launches = 0;
-  if (e == cudaSuccess && save_every == 0 && n_steps > 0 && !S.graph) {
+  const bool use_graph = allow_graph && save_every == 0;
+  if (e == cudaSuccess && use_graph && n_steps > 0 && !S.graph) {
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -144,11 +145,11 @@ fd_status fd_large_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final,
   }
   int snap = 0;
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
-    if (save_every == 0) {
+    if (use_graph) {
       e = cudaGraphLaunch(S.graph, st);
     } else {
       e = large_step(c, st);
-      if (e == cudaSuccess && traj && (k + 1) % save_every == 0) {
+      if (e == cudaSuccess && traj && save_every > 0 && (k + 1) % save_every == 0) {
         e = cudaMemcpyAsync(static_cast<char*>(traj) + (size_t)snap * bytes, S.un, bytes, cudaMemcpyDeviceToDevice,
                             st);
         ++snap;

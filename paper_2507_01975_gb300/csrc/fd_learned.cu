@@ -432,7 +432,7 @@ fd_status fd_network_forward(fd_ctx* c, const void* u, float* coef_out, void* st
 // current group; a group of G = max(k_c, 1) steps is captured once as a CUDA
 // graph (with the temporal correction at its last step) and replayed.
 fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool allow_graph) {
   LearnedState& L = *c->lrn;
   if (!L.ready) return fd_set_error(c, FD_EINVAL, "fd_rollout: learned parameters not set (fd_set_params)");
   const size_t bytes = fd_state_bytes(c->grid);
@@ -449,7 +449,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
   g_where = "state copy";
   cudaError_t e = cudaMemcpyAsync(L.ring, u0, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) g_where = "";
-  const bool use_graph = save_every == 0;
+  const bool use_graph = allow_graph && save_every == 0;
   if (e == cudaSuccess && use_graph && n_steps >= G && !L.graph) {
     // capture one group on the side stream; the history for the temporal
     // correction of the group's last step is ring[0 .. k_c - 1]

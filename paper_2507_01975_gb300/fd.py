@@ -40,6 +40,12 @@ EXPORTS = [
     "fd_vorticity_pcc",
     "fd_adam_step",
     "fd_downsample",
+    "fd_batch_create",
+    "fd_batch_add",
+    "fd_batch_run",
+    "fd_batch_launch_count",
+    "fd_batch_last_error",
+    "fd_batch_destroy",
     "fd_destroy",
     "fd_last_error",
     "fd_version",
@@ -128,6 +134,18 @@ def load(path: str = LIB_PATH):
     lib.fd_adam_step.restype = C.c_int
     lib.fd_downsample.argtypes = [vp, vp, i32, i32, i32, i32, vp]
     lib.fd_downsample.restype = C.c_int
+    lib.fd_batch_create.argtypes = [C.POINTER(C.c_void_p)]
+    lib.fd_batch_create.restype = C.c_int
+    lib.fd_batch_add.argtypes = [vp, vp, vp, vp, i32]
+    lib.fd_batch_add.restype = C.c_int
+    lib.fd_batch_run.argtypes = [vp, vp]
+    lib.fd_batch_run.restype = C.c_int
+    lib.fd_batch_launch_count.argtypes = [vp]
+    lib.fd_batch_launch_count.restype = i32
+    lib.fd_batch_last_error.argtypes = [vp]
+    lib.fd_batch_last_error.restype = C.c_char_p
+    lib.fd_batch_destroy.argtypes = [vp]
+    lib.fd_batch_destroy.restype = C.c_int
     lib.fd_check_finite_noalloc.argtypes = [vp, C.c_int64, i32, C.POINTER(C.c_int64), vp]
     lib.fd_check_finite_noalloc.restype = C.c_int
     lib.fd_destroy.argtypes = [vp]
@@ -278,6 +296,43 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.fd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """fd_batch: rollouts of several solvers (mixed sizes, flows, learned and
+    plain) replayed as one CUDA graph with a parallel branch per solver."""
+
+    def __init__(self):
+        self.lib = load()
+        h = C.c_void_p()
+        _check_free(self.lib, self.lib.fd_batch_create(C.byref(h)))
+        self.h = h
+        self._keep = []
+
+    def add(self, solver: "Solver", u0, u_final, n_steps: int):
+        st = self.lib.fd_batch_add(self.h, solver.h, _ptr(u0), _ptr(u_final), int(n_steps))
+        if st != FD_OK:
+            raise FdError(st, self.lib.fd_batch_last_error(self.h).decode())
+        self._keep.append((solver, u0, u_final))
+
+    def run(self, stream=None):
+        st = self.lib.fd_batch_run(self.h, _stream_handle(stream))
+        if st != FD_OK:
+            raise FdError(st, self.lib.fd_batch_last_error(self.h).decode())
+
+    def launch_count(self) -> int:
+        return int(self.lib.fd_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fd_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

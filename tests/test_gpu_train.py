@@ -203,3 +203,32 @@ def test_vorticity_correlation_matches_oracle(dtype):
     s.vorticity_pcc(dev(A_, tdt), dev(A_, tdt), out)
     torch.cuda.synchronize()
     assert np.max(np.abs(out.cpu().numpy() - 1.0)) <= 1e-12
+
+
+def test_batch_of_mixed_rollouts_equals_individual_rollouts():
+    # one graph with a branch per context: plain on-chip (Burgers 32^2, NS 64^2),
+    # learned 32^2, and the streaming path at 64^2
+    specs = [
+        (fd.Config(n=32, batch=2, dtype="f32", flow="burgers", nu=1e-2, dt=2e-3, deriv_order=2), "burgers", 10, None),
+        (fd.Config(n=64, batch=2, dtype="f32", nu=1e-3, dt=5e-3), "decaying", 5, None),
+        (fd.Config(n=32, batch=2, dtype="f32", nu=1e-3, dt=1e-2, learned=True), "kolmogorov", 4, make_model(90)),
+        (fd.Config(n=64, batch=1, dtype="f32", nu=1e-3, dt=5e-3, path=2), "decaying", 3, None),
+    ]
+    batch = fd.Batch()
+    runs = []
+    for cfg, kind, steps, model in specs:
+        s = fd.Solver(cfg)
+        if model is not None:
+            s.set_params(I.pack_params(model.W_L, model.stencil))
+        u0 = dev(I.ic_batch(kind, cfg.n, cfg.batch, seed0=91))
+        out = torch.empty_like(u0)
+        ref = torch.empty_like(u0)
+        s.rollout(u0, ref, steps)
+        batch.add(s, u0, out, steps)
+        runs.append((out, ref))
+    batch.run()
+    batch.run()  # replay
+    torch.cuda.synchronize()
+    assert batch.launch_count() > 0
+    for out, ref in runs:
+        assert torch.equal(out, ref)

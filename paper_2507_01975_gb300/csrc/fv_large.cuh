@@ -58,6 +58,13 @@ __device__ __forceinline__ float2 c2mulc(float2 a, float2 w) {  // a * conj(w)
 }
 __device__ __forceinline__ int brev_n(int k, int logn) { return (int)(__brev((unsigned)k) >> (32 - logn)); }
 
+// Shared-memory position of element p of the transform buffers: bits 0-4 are
+// XOR-ed with bits 6-10. Runs of 64 consecutive elements stay a permutation of
+// one another (conflict-free passes), while the bit-reversed gathers and
+// scatters of the packing steps (elements 64 m apart) spread over 16 banks
+// instead of one. Its own inverse.
+__device__ __forceinline__ int swz(int p) { return p ^ ((p >> 6) & 31); }
+
 // Stage-major twiddles in shared memory: tws[h + j] = exp(-2 pi i j / (2 h)) for
 // h = 1, 2, 4, .., N/2 and j < h (N - 1 entries, index 0 unused), so that the
 // butterflies of one stage read consecutive entries (no bank conflicts).
@@ -82,25 +89,26 @@ __device__ void block_fft_dif(float2* x, int F, int logn, const float2* tws) {
     for (int t = threadIdx.x; t < F * Q; t += blockDim.x) {
       const int f = t >> (logn - 2), r = t & (Q - 1);
       const int j = r & (q - 1);
-      float2* b = x + (f << logn) + ((r >> lq) << (lq + 2));
-      float2 a0 = b[j], a1 = b[j + q], a2 = b[j + 2 * q], a3 = b[j + 3 * q];
+      const int o = (f << logn) + ((r >> lq) << (lq + 2)) + j;
+      const int i0 = swz(o), i1 = swz(o + q), i2 = swz(o + 2 * q), i3 = swz(o + 3 * q);
+      const float2 a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
       const float2 s0 = c2add(a0, a2), s2 = c2mul(c2sub(a0, a2), tws[2 * q + j]);
       const float2 s1 = c2add(a1, a3), s3 = c2mul(c2sub(a1, a3), tws[3 * q + j]);
       const float2 w = tws[q + j];
-      b[j] = c2add(s0, s1);
-      b[j + q] = c2mul(c2sub(s0, s1), w);
-      b[j + 2 * q] = c2add(s2, s3);
-      b[j + 3 * q] = c2mul(c2sub(s2, s3), w);
+      x[i0] = c2add(s0, s1);
+      x[i1] = c2mul(c2sub(s0, s1), w);
+      x[i2] = c2add(s2, s3);
+      x[i3] = c2mul(c2sub(s2, s3), w);
     }
     __syncthreads();
   }
   if (ls == 0) {  // remaining radix-2 stage, half = 1
     const int H = 1 << (logn - 1);
     for (int t = threadIdx.x; t < F * H; t += blockDim.x) {
-      float2* b = x + 2 * t;
-      const float2 a = b[0], c = b[1];
-      b[0] = c2add(a, c);
-      b[1] = c2sub(a, c);
+      const int i0 = swz(2 * t), i1 = swz(2 * t + 1);
+      const float2 a = x[i0], c = x[i1];
+      x[i0] = c2add(a, c);
+      x[i1] = c2sub(a, c);
     }
     __syncthreads();
   }
@@ -114,10 +122,10 @@ __device__ void block_ifft_dit(float2* x, int F, int logn, const float2* tws) {
   if (logn & 1) {
     const int H = 1 << (logn - 1);
     for (int t = threadIdx.x; t < F * H; t += blockDim.x) {
-      float2* b = x + 2 * t;
-      const float2 a = b[0], c = b[1];
-      b[0] = c2add(a, c);
-      b[1] = c2sub(a, c);
+      const int i0 = swz(2 * t), i1 = swz(2 * t + 1);
+      const float2 a = x[i0], c = x[i1];
+      x[i0] = c2add(a, c);
+      x[i1] = c2sub(a, c);
     }
     __syncthreads();
     ls = 1;
@@ -128,17 +136,18 @@ __device__ void block_ifft_dit(float2* x, int F, int logn, const float2* tws) {
     for (int t = threadIdx.x; t < F * Q; t += blockDim.x) {
       const int f = t >> (logn - 2), r = t & (Q - 1);
       const int j = r & (q - 1);
-      float2* b = x + (f << logn) + ((r >> lq) << (lq + 2));
-      const float2 a0 = b[j], a1 = b[j + q], a2 = b[j + 2 * q], a3 = b[j + 3 * q];
+      const int o = (f << logn) + ((r >> lq) << (lq + 2)) + j;
+      const int i0 = swz(o), i1 = swz(o + q), i2 = swz(o + 2 * q), i3 = swz(o + 3 * q);
+      const float2 a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
       const float2 w = tws[q + j];
       const float2 t1 = c2mulc(a1, w), t3 = c2mulc(a3, w);
       const float2 s0 = c2add(a0, t1), s1 = c2sub(a0, t1);
       const float2 s2 = c2add(a2, t3), s3 = c2sub(a2, t3);
       const float2 u2 = c2mulc(s2, tws[2 * q + j]), u3 = c2mulc(s3, tws[3 * q + j]);
-      b[j] = c2add(s0, u2);
-      b[j + 2 * q] = c2sub(s0, u2);
-      b[j + q] = c2add(s1, u3);
-      b[j + 3 * q] = c2sub(s1, u3);
+      x[i0] = c2add(s0, u2);
+      x[i2] = c2sub(s0, u2);
+      x[i1] = c2add(s1, u3);
+      x[i3] = c2sub(s1, u3);
     }
     __syncthreads();
   }
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(512) large_rows_fwd_kernel(const LargeArgs a, 
                      (v[(size_t)rb * N + x] - v[(size_t)ra * N + x]) * a.idy;
     const float db = (u[(size_t)rb * N + xe] - u[(size_t)rb * N + x]) * a.idx +
                      (v[(size_t)((rb + 1) & MSK) * N + x] - v[(size_t)rb * N + x]) * a.idy;
-    buf[t] = make_float2(da, db);
+    buf[swz(t)] = make_float2(da, db);
   }
   __syncthreads();
   block_fft_dif(buf, F, logn, tw);
@@ -280,8 +289,8 @@ __global__ void __launch_bounds__(512) large_rows_fwd_kernel(const LargeArgs a, 
   float4* blk = reinterpret_cast<float4*>(a.spec + ((size_t)b * (N / kLRB) + g) * (H + 1) * kLRB);
   for (int t = threadIdx.x; t < (H + 1) * F; t += blockDim.x) {
     const int k = t >> 2, f = t & 3;
-    const float2 zk = buf[(f << logn) + brev_n(k & MSK, logn)];
-    const float2 zm = buf[(f << logn) + brev_n((N - k) & MSK, logn)];
+    const float2 zk = buf[swz((f << logn) + brev_n(k & MSK, logn))];
+    const float2 zm = buf[swz((f << logn) + brev_n((N - k) & MSK, logn))];
     blk[t] = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
 }
@@ -294,31 +303,32 @@ __global__ void __launch_bounds__(512) large_cols_kernel(const LargeArgs a, int 
   const int N = 1 << logn, H = N / 2, G = N / kLRB;
   float2* buf = sm;                 // [kLCB][N]
   float2* tw = sm + kLCB * N;       // [N] stage-major twiddles
-  float* sy = reinterpret_cast<float*>(tw + N);  // [N]
+  float* sy = reinterpret_cast<float*>(tw + N);  // [N] symbol in bit-reversed order: sy[pos] = symy[brev(pos)]
   const int b = blockIdx.y, kx0 = blockIdx.x * kLCB;
   const int F = (H + 1 - kx0) < kLCB ? (H + 1 - kx0) : kLCB;
   float2* spec = a.spec + (size_t)b * G * (H + 1) * kLRB;
   load_stage_twiddles(tw, a.tw, logn);
-  for (int k = threadIdx.x; k < N; k += blockDim.x) sy[k] = a.symy[k];
+  for (int k = threadIdx.x; k < N; k += blockDim.x) sy[k] = a.symy[brev_n(k, logn)];
   // column kx0 + c, row y = 8 g + yy sits at spec[(g (H + 1) + kx0 + c) 8 + yy]:
   // kLCB x 8 consecutive complex values per row group
   for (int t = threadIdx.x; t < kLCB * N; t += blockDim.x) {
     const int yy = t & (kLRB - 1), c = (t >> 3) & (kLCB - 1), g = t >> 4;
-    if (c < F) buf[(c << logn) + g * kLRB + yy] = spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy];
+    if (c < F) buf[swz((c << logn) + g * kLRB + yy)] = spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy];
   }
   __syncthreads();
   block_fft_dif(buf, F, logn, tw);
   for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
     const int f = t >> logn, pos = t & (N - 1);
-    const int kx = kx0 + f, ky = brev_n(pos, logn);
-    const float m = (kx == 0 && ky == 0) ? 0.0f : __fdividef(a.inv_nn, a.symx[kx] + sy[ky]);
-    buf[t] = make_float2(buf[t].x * m, buf[t].y * m);
+    const int kx = kx0 + f;
+    const float m = (kx == 0 && pos == 0) ? 0.0f : __fdividef(a.inv_nn, a.symx[kx] + sy[pos]);  // pos 0 is ky 0
+    const float2 z = buf[swz(t)];
+    buf[swz(t)] = make_float2(z.x * m, z.y * m);
   }
   __syncthreads();
   block_ifft_dit(buf, F, logn, tw);
   for (int t = threadIdx.x; t < kLCB * N; t += blockDim.x) {
     const int yy = t & (kLRB - 1), c = (t >> 3) & (kLCB - 1), g = t >> 4;
-    if (c < F) spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy] = buf[(c << logn) + g * kLRB + yy];
+    if (c < F) spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy] = buf[swz((c << logn) + g * kLRB + yy)];
   }
 }
 
@@ -338,15 +348,15 @@ __global__ void __launch_bounds__(512) large_rows_inv_kernel(const LargeArgs a, 
   for (int t = threadIdx.x; t < (H + 1) * F; t += blockDim.x) {
     const int k = t >> 2, f = t & 3;
     const float4 v = blk[t];  // (P_a[k], P_b[k])
-    buf[(f << logn) + brev_n(k & MSK, logn)] = make_float2(v.x - v.w, v.y + v.z);
-    if (k > 0 && k < H) buf[(f << logn) + brev_n(N - k, logn)] = make_float2(v.x + v.w, v.z - v.y);
+    buf[swz((f << logn) + brev_n(k & MSK, logn))] = make_float2(v.x - v.w, v.y + v.z);
+    if (k > 0 && k < H) buf[swz((f << logn) + brev_n(N - k, logn))] = make_float2(v.x + v.w, v.z - v.y);
   }
   __syncthreads();
   block_ifft_dit(buf, F, logn, tw);
   float* p = a.pout + (size_t)b * N * N;
   for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
     const int f = t >> logn, x = t & MSK;
-    const float2 z = buf[t];
+    const float2 z = buf[swz(t)];
     p[(size_t)(y0 + 2 * f) * N + x] = z.x;
     p[(size_t)(y0 + 2 * f + 1) * N + x] = z.y;
   }

@@ -174,7 +174,8 @@ fd_status fd_set_params(fd_ctx* ctx, const float* params, int64_t count, void* s
 fd_status fd_set_params_device(fd_ctx* ctx, const float* params, int64_t count, void* stream);
 
 /* Stencil-network forward pass alone: coef_out[batch][160][ny][nx] (device,
- * float32) = C_theta(u) for the device state u. For tests and diagnostics. */
+ * float32) = C_theta(u) for the device state u. For tests and diagnostics;
+ * coef_out = NULL runs the network only (its BF16 output stays internal). */
 fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* stream);
 
 /* ---- reverse mode ----------------------------------------------------------

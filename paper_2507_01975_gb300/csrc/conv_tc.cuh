@@ -13,9 +13,10 @@
 // which is exactly the no-swizzle K-major operand layout of tcgen05.mma
 // (8-pixel x 16-byte core matrices, M-stride 128 B, K-stride one plane). A
 // shift by dy is a start-address offset of one image row. Shifts by dx would
-// wrap around the row ends (periodic padding), so instead the MMAs of the
-// three dx columns of the kernel accumulate into three separate TMEM
-// accumulators P_dx over the *unshifted* pixels, and the epilogue forms
+// wrap around the row ends (periodic padding), so instead the three dx
+// columns of the kernel accumulate into three TMEM accumulators P_dx over the
+// *unshifted* pixels -- one MMA with N = 3 x COUT_TILE (the weights of the
+// three dx taps side by side) produces all three -- and the epilogue forms
 // out[x] = P_-1[x-1] + P_0[x] + P_+1[x+1] with the periodic wrap.
 //
 // Roles (20 warps): warp 0 lane 0 issues the bulk copies of the input tiles
@@ -166,7 +167,7 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
   return 0.5f * (1.0f + erf_x) + x * 0.39894228040143268f * g;
 }
 
-template <int LOGN, int CIN, int COUT_TILE, int NBUF = 2>
+template <int LOGN, int CIN, int COUT_TILE, int NBUF = 4>
 struct ConvCfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int TM = 128;             // output pixels per tile
@@ -178,8 +179,10 @@ struct ConvCfg {
   static constexpr int CG = COUT_TILE / 4;  // output channels per epilogue warp
   static constexpr uint32_t PLANE_BYTES = IROWS * N * 16;         // one chunk plane of the tile
   static constexpr uint32_t ATILE_BYTES = KC * PLANE_BYTES;       // one input tile
-  static constexpr uint32_t TAP_BYTES = KC * (COUT_TILE / 8) * 128;
-  static constexpr uint32_t W_BYTES = 9 * TAP_BYTES;
+  // weights [dy][c8][dx][co8][8 co][8 ci]: the three dx blocks of one (dy, c8)
+  // are adjacent along N, so one MMA with N = 3 COUT_TILE produces P_-1, P_0, P_+1
+  static constexpr uint32_t KSTEP_BYTES = 3 * (COUT_TILE / 8) * 128;  // one c8 of one dy
+  static constexpr uint32_t W_BYTES = 3 * KC * KSTEP_BYTES;
   static constexpr uint32_t OFF_A = 0;                            // NBUF input tiles
   static constexpr uint32_t OFF_W = NBUF * ATILE_BYTES;
   static constexpr uint32_t OFF_BND = OFF_W + W_BYTES;            // epilogue boundary exchange
@@ -191,14 +194,14 @@ struct ConvCfg {
   static constexpr int TMEM_COLS = 2 * ACC_COLS <= 256 ? 256 : 512;
   static_assert(N >= 32 && N <= 128, "a tile covers whole image rows");
   static_assert(CIN % 16 == 0, "K steps of 16");
-  static_assert(COUT_TILE % 32 == 0 && COUT_TILE >= 32 && COUT_TILE <= 128, "accumulator width");
+  static_assert(COUT_TILE % 32 == 0 && COUT_TILE >= 32 && 3 * COUT_TILE <= 256, "accumulator width (MMA N)");
   static_assert(2 * ACC_COLS <= 512, "double-buffered accumulators fit tensor memory");
   static_assert(SMEM <= 232448, "shared memory");
   static_assert(PLANE_BYTES < (1u << 18), "descriptor offsets");
-  static_assert(NBUF == 1 || NBUF == 2, "input buffering");
+  static_assert(NBUF >= 1 && NBUF <= 4, "input buffering");
 };
 
-template <int LOGN, int CIN, int COUT_TILE, int NBUF = 2>
+template <int LOGN, int CIN, int COUT_TILE, int NBUF = 4>
 __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
   using Cfg = ConvCfg<LOGN, CIN, COUT_TILE, NBUF>;
   constexpr int N = Cfg::N, TROWS = Cfg::TROWS, IROWS = Cfg::IROWS, KC = Cfg::KC;
@@ -209,14 +212,14 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
   float* const bnd = reinterpret_cast<float*>(smem + Cfg::OFF_BND);
   float* const sbias = reinterpret_cast<float*>(smem + Cfg::OFF_BIASV);
   uint64_t* const bars = reinterpret_cast<uint64_t*>(smem + Cfg::OFF_BAR);
-  uint64_t* const a_full = bars + 0;   // [2]
-  uint64_t* const a_empty = bars + 2;  // [2]
-  uint64_t* const c_full = bars + 4;   // [2]
-  uint64_t* const c_empty = bars + 6;  // [2]
-  uint64_t* const w_full = bars + 8;
-  uint32_t* const tslot = reinterpret_cast<uint32_t*>(bars + 9);
-  volatile uint32_t* const abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 10);
-  volatile uint32_t* const ep_abort = reinterpret_cast<volatile uint32_t*>(bars + 11);
+  uint64_t* const a_full = bars + 0;    // [NBUF] input tile landed
+  uint64_t* const a_empty = bars + 4;   // [NBUF] MMAs of the input tile done
+  uint64_t* const c_full = bars + 8;    // [2] accumulator ready
+  uint64_t* const c_empty = bars + 10;  // [2] accumulator read out
+  uint64_t* const w_full = bars + 12;
+  uint32_t* const tslot = reinterpret_cast<uint32_t*>(bars + 13);
+  volatile uint32_t* const abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 14);
+  volatile uint32_t* const ep_abort = reinterpret_cast<volatile uint32_t*>(bars + 15);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tiles_per_img = N / TROWS;
@@ -225,9 +228,11 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
   const long long lim = a.spin_limit;
 
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NBUF; ++s) {
       mbar_init(a_full + s, 1);
       mbar_init(a_empty + s, 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       mbar_init(c_full + s, 1);
       mbar_init(c_empty + s, Cfg::NEPI * 32);
     }
@@ -245,70 +250,86 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
 
   if (warp == 0) {
     // ---------------- producer: weights once per part change, input tiles ----------
-    if (lane == 0) {
-      int cur_part = -1;
-      uint32_t wphase_waits = 0;
-      int i = 0;
-      int issued = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        const int part = t / npix;
-        const int pix = t % npix;
-        const int b = pix / tiles_per_img, y0 = (pix % tiles_per_img) * TROWS;
-        const int s = NBUF == 2 ? (i & 1) : 0;
-        const uint32_t aph = NBUF == 2 ? ((i >> 1) & 1) : (i & 1);
+    // lane 0 waits and arms the barriers; all 32 lanes issue the tile's copies
+    int cur_part = -1;
+    uint32_t wphase_waits = 0;
+    int i = 0;
+    int issued = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int part = t / npix;
+      const int pix = t % npix;
+      const int b = pix / tiles_per_img, y0 = (pix % tiles_per_img) * TROWS;
+      const int s = i % NBUF;
+      const uint32_t aph = (uint32_t)((i / NBUF) & 1);
+      int ok = 1;
+      if (lane == 0) {
         if (!mbar_wait(a_empty + s, aph ^ 1, lim)) {
-          *abort_flag = 1;
+          ok = 0;
           atomicOr(a.err, 1u);
-          break;
-        }
-        if (part != cur_part) {
-          // the MMAs of every earlier tile have completed (a_empty of the
-          // previous tile in this buffer and of the other buffer), so the
+        } else if (part != cur_part) {
+          // the MMAs of every earlier tile have completed once the previous
+          // tile's commit has arrived (commits track all prior MMAs), so the
           // weight area can be overwritten
-          if (NBUF == 2 && i > 0 && !mbar_wait(a_empty + (s ^ 1), (((i - 1) >> 1) & 1), lim)) {
-            *abort_flag = 1;
+          if (i > 0 && !mbar_wait(a_empty + (i - 1) % NBUF, (uint32_t)(((i - 1) / NBUF) & 1), lim)) {
+            ok = 0;
             atomicOr(a.err, 2u);
-            break;
-          }
-          mbar_expect_tx(w_full, Cfg::W_BYTES);
-          const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(a.w) + (size_t)part * Cfg::W_BYTES;
-          for (uint32_t off = 0; off < Cfg::W_BYTES; off += 16384) {
-            const uint32_t sz = (Cfg::W_BYTES - off) < 16384 ? (Cfg::W_BYTES - off) : 16384;
-            bulk_g2s(sW + off, wsrc + off, sz, w_full);
-          }
-          cur_part = part;
-          ++wphase_waits;
-        }
-        mbar_expect_tx(a_full + s, Cfg::ATILE_BYTES);
-        unsigned char* dst = sA + s * Cfg::ATILE_BYTES;
-        for (int c = 0; c < KC; ++c) {
-          for (int r = 0; r < IROWS; ++r) {
-            const int gy = (y0 - 1 + r + N) & (N - 1);
-            const __nv_bfloat16* src = a.in + (((size_t)b * KC + c) * N + gy) * N * 8;
-            bulk_g2s(dst + c * Cfg::PLANE_BYTES + r * N * 16, src, N * 16, a_full + s);
+          } else {
+            mbar_expect_tx(w_full, Cfg::W_BYTES);
+            const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(a.w) + (size_t)part * Cfg::W_BYTES;
+            for (uint32_t off = 0; off < Cfg::W_BYTES; off += 16384) {
+              const uint32_t sz = (Cfg::W_BYTES - off) < 16384 ? (Cfg::W_BYTES - off) : 16384;
+              bulk_g2s(sW + off, wsrc + off, sz, w_full);
+            }
           }
         }
-        issued = i + 1;
+        if (ok) mbar_expect_tx(a_full + s, Cfg::ATILE_BYTES);
+        if (!ok) *abort_flag = 1;
       }
-      // never leave with bulk copies in flight: wait (bounded) for the last
-      // tiles and the last weight load to land
-      for (int j = issued - 2; j < issued; ++j)
-        if (j >= 0 && (NBUF == 2 || j == issued - 1))
-          mbar_wait(a_full + (NBUF == 2 ? (j & 1) : 0), NBUF == 2 ? ((j >> 1) & 1) : (j & 1), lim);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (part != cur_part) {
+        cur_part = part;
+        ++wphase_waits;
+      }
+      __syncwarp();
+      // rows y0 - 1 .. y0 + TROWS of each plane are contiguous in global memory
+      // except across the periodic wrap: one copy per plane, two at the wrap
+      unsigned char* dst = sA + s * Cfg::ATILE_BYTES;
+      for (int c = lane; c < KC; c += 32) {
+        const unsigned char* plane = reinterpret_cast<const unsigned char*>(a.in + ((size_t)b * KC + c) * N * N * 8);
+        unsigned char* d = dst + c * Cfg::PLANE_BYTES;
+        constexpr uint32_t ROWB = N * 16;
+        if (y0 == 0) {  // row -1 is row N - 1
+          bulk_g2s(d, plane + (size_t)(N - 1) * ROWB, ROWB, a_full + s);
+          bulk_g2s(d + ROWB, plane, (IROWS - 1) * ROWB, a_full + s);
+        } else if (y0 + TROWS == N) {  // row N is row 0
+          bulk_g2s(d, plane + (size_t)(y0 - 1) * ROWB, (IROWS - 1) * ROWB, a_full + s);
+          bulk_g2s(d + (IROWS - 1) * ROWB, plane, ROWB, a_full + s);
+        } else {
+          bulk_g2s(d, plane + (size_t)(y0 - 1) * ROWB, IROWS * ROWB, a_full + s);
+        }
+      }
+      issued = i + 1;
+    }
+    // never leave with bulk copies in flight: wait (bounded) for the last
+    // NBUF tiles and the last weight load to land
+    if (lane == 0) {
+      for (int j = issued - NBUF; j < issued; ++j)
+        if (j >= 0) mbar_wait(a_full + j % NBUF, (uint32_t)((j / NBUF) & 1), lim);
       if (wphase_waits > 0) mbar_wait(w_full, (wphase_waits - 1) & 1, lim);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer -------------------------------------------------
     if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc_bf16<128, COUT_TILE>();
+      constexpr uint32_t idesc = umma_idesc_bf16<128, 3 * COUT_TILE>();
       int cur_part = -1;
       uint32_t wpar = 0;
       int i = 0;
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
         const int part = t / npix;
         const int s = i & 1;                              // accumulator buffer
-        const int sa = NBUF == 2 ? s : 0;                 // input buffer
-        const uint32_t aph = NBUF == 2 ? ((i >> 1) & 1) : (i & 1);
+        const int sa = i % NBUF;                          // input buffer
+        const uint32_t aph = (uint32_t)((i / NBUF) & 1);
         if (*abort_flag) break;
         if (part != cur_part) {
           if (!mbar_wait(w_full, wpar, lim)) {
@@ -328,21 +349,20 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
         const uint32_t abase = smem_u32(sA + sa * Cfg::ATILE_BYTES);
         const uint32_t wbase = smem_u32(sW);
         const uint32_t dbase = tmem + (uint32_t)(s * Cfg::ACC_COLS);
-#pragma unroll 1
-        for (int dxi = 0; dxi < 3; ++dxi) {
-          bool first = true;
-#pragma unroll 1
-          for (int dyi = 0; dyi < 3; ++dyi) {
-            const int tap = dyi * 3 + dxi;  // (dy, dx) = (dyi - 1, dxi - 1)
+        // descriptors of the tile's first A and B core matrices; the start
+        // address field is linear (16-byte units, no carry out of it inside
+        // shared memory), so every MMA's operands are these plus a constant.
+        // One MMA per (dy, 16 input channels) with N = 3 COUT_TILE writes the
+        // three dx accumulators at once (columns dx * COUT_TILE + co).
+        const uint64_t ad0 = umma_desc(abase, Cfg::PLANE_BYTES, 128);
+        const uint64_t bd0 = umma_desc(wbase, Cfg::KSTEP_BYTES, 128);
 #pragma unroll
-            for (int kk = 0; kk < KC / 2; ++kk) {
-              const uint32_t aaddr = abase + (uint32_t)(2 * kk) * Cfg::PLANE_BYTES + (uint32_t)dyi * N * 16;
-              const uint32_t baddr = wbase + (uint32_t)tap * Cfg::TAP_BYTES + (uint32_t)(2 * kk) * (COUT_TILE / 8) * 128;
-              const uint64_t ad = umma_desc(aaddr, Cfg::PLANE_BYTES, 128);
-              const uint64_t bd = umma_desc(baddr, (COUT_TILE / 8) * 128, 128);
-              umma_bf16(dbase + (uint32_t)(dxi * COUT_TILE), ad, bd, idesc, first ? 0u : 1u);
-              first = false;
-            }
+        for (int dyi = 0; dyi < 3; ++dyi) {  // dy = dyi - 1: a start offset of one image row
+#pragma unroll
+          for (int kk = 0; kk < KC / 2; ++kk) {
+            const uint64_t ad = ad0 + (uint64_t)(((2 * kk) * Cfg::PLANE_BYTES + dyi * N * 16) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)(((dyi * KC + 2 * kk) * Cfg::KSTEP_BYTES) >> 4);
+            umma_bf16(dbase, ad, bd, idesc, (dyi | kk) ? 1u : 0u);
           }
         }
         umma_commit(a_empty + sa);
@@ -406,11 +426,19 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
         float outv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          float left = __shfl_up_sync(0xffffffffu, pm[cc + j], 1);
-          float right = __shfl_down_sync(0xffffffffu, pp[cc + j], 1);
-          if (lane == 0) left = eleft[cc + j];
-          if (lane == 31) right = eright[cc + j];
+          const float left = __shfl_up_sync(0xffffffffu, pm[cc + j], 1);
+          const float right = __shfl_down_sync(0xffffffffu, pp[cc + j], 1);
           outv[j] = p0[cc + j] + left + right;
+        }
+        // lanes 0 and 31 got their own value back from the shuffle; swap in the
+        // neighbouring quarter's edge value, one branch per 8 values
+        if (lane == 0) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) outv[j] += eleft[cc + j] - pm[cc + j];
+        }
+        if (lane == 31) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) outv[j] += eright[cc + j] - pp[cc + j];
         }
         const int chunk = (co0 + cc) >> 3;
         const size_t oidx = ((((size_t)b * (a.cout_total / 8) + chunk) * N + gy) * N + x) * 8;

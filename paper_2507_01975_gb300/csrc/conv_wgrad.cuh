@@ -171,9 +171,12 @@ __global__ void __launch_bounds__(256, 1) conv_wgrad_kernel(const WgradArgs a) {
         tmem_fence_after_sync();
         const uint32_t hb = smem_u32(smem + s * Cfg::STAGE_BYTES);
         const uint32_t zb = hb + Cfg::H_BYTES;
+        // base descriptors; each MMA adds a constant to the start address field
+        const uint64_t ad0 = umma_desc(hb, 128, P * 16);
+        const uint64_t bd0 = umma_desc(zb, 128, N * 16);
 #pragma unroll 1
         for (int t = 0; t < R; ++t) {
-#pragma unroll 1
+#pragma unroll
           for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
             for (int mm = 0; mm < NMMA; ++mm) {
@@ -181,10 +184,9 @@ __global__ void __launch_bounds__(256, 1) conv_wgrad_kernel(const WgradArgs a) {
 #pragma unroll
               for (int kc = 0; kc < N / 16; ++kc) {
                 // h rows (y - 1 + mm RPM) .., pixels 16 kc + dx - 1 (+1 for the halo)
-                const uint32_t aaddr = hb + (uint32_t)((t + mm * RPM) * Cfg::HROW_BYTES) + (uint32_t)((16 * kc + dx) * 16);
-                const uint32_t baddr = zb + (uint32_t)(t * Cfg::ZROW_BYTES) + (uint32_t)(16 * kc * 16);
-                const uint64_t ad = umma_desc(aaddr, 128, P * 16);
-                const uint64_t bd = umma_desc(baddr, 128, N * 16);
+                const uint64_t ad =
+                    ad0 + (uint64_t)((((t + mm * RPM) * Cfg::HROW_BYTES) + (16 * kc + dx) * 16) >> 4);
+                const uint64_t bd = bd0 + (uint64_t)((t * Cfg::ZROW_BYTES + 16 * kc * 16) >> 4);
                 umma_bf16(d, ad, bd, idesc, (first && t == 0 && kc == 0) ? 0u : 1u);
               }
             }

@@ -195,7 +195,9 @@ __global__ void prep_raw_kernel(const float* params, float* raw, size_t nparams,
   if (blockIdx.x == 0 && threadIdx.x < 8) raw[off_zero + threadIdx.x] = 0.f;
 }
 
-// tile element (tap, c8, n8, n, k): input channel ci = 8 c8 + k, output channel co = co0 + 8 n8 + n
+// tile element (dy, c8, dx, n8, n, k): input channel ci = 8 c8 + k, output
+// channel co = co0 + 8 n8 + n, tap = 3 dy + dx. The three dx blocks of one
+// (dy, c8) are adjacent, so one MMA with N = 3 x cout_tile covers all three.
 __global__ void pack_tiles_kernel(const float* raw, __nv_bfloat16* pk, const PackDesc* descs) {
   const PackDesc d = descs[blockIdx.y];
   const float* W = raw + d.src_off;
@@ -203,8 +205,10 @@ __global__ void pack_tiles_kernel(const float* raw, __nv_bfloat16* pk, const Pac
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < d.count; idx += gridDim.x * blockDim.x) {
     const uint32_t k = idx & 7, n = (idx >> 3) & 7;
     const uint32_t n8 = (idx >> 6) % n8s;
-    const uint32_t c8 = (idx / (64 * n8s)) % c8s;
-    const uint32_t tap = idx / (64 * n8s * c8s);
+    const uint32_t dx = (idx / (64 * n8s)) % 3;
+    const uint32_t c8 = (idx / (64 * n8s * 3)) % c8s;
+    const uint32_t dy = idx / (64 * n8s * 3 * c8s);
+    const uint32_t tap = dy * 3 + dx;
     const uint32_t ci = c8 * 8 + k, co = d.co0 + n8 * 8 + n;
     float v = 0.f;
     if (ci < d.cin_tile)
@@ -409,7 +413,7 @@ fd_status fd_set_params_device(fd_ctx* c, const float* params, int64_t count, vo
 fd_status fd_network_forward(fd_ctx* c, const void* u, float* coef_out, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_network_forward: null context");
   if (!c->lrn || !c->lrn->ready) return fd_set_error(c, FD_EINVAL, "fd_network_forward: parameters not set");
-  if (!u || !coef_out) return fd_set_error(c, FD_EINVAL, "fd_network_forward: null pointer");
+  if (!u) return fd_set_error(c, FD_EINVAL, "fd_network_forward: null state pointer");
   LearnedState& L = *c->lrn;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = fd_state_bytes(c->grid);
@@ -417,11 +421,12 @@ fd_status fd_network_forward(fd_ctx* c, const void* u, float* coef_out, void* st
   cudaError_t e = cudaMemcpyAsync(L.wbuf, u, bytes, cudaMemcpyDeviceToDevice, st);
   const float* const* pw = L.d_ptrs + L.nring;
   if (e == cudaSuccess) e = (c->grid.nx == 64) ? run_stencil_net<6>(c, pw, st) : run_stencil_net<5>(c, pw, st);
-  if (e == cudaSuccess) {
+  c->launches = 8;
+  if (e == cudaSuccess && coef_out) {
     coef_unpack_kernel<<<4 * L.sms, 256, 0, st>>>(L.coef, coef_out, c->grid.batch, c->logn);
     e = cudaGetLastError();
+    ++c->launches;
   }
-  c->launches = 8;
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_network_forward: %s", cudaGetErrorString(e));
   return FD_OK;
 }

@@ -29,7 +29,7 @@ inline int tc_cout(int l) { return l == 5 ? 2 : kHidden; }
 
 // One tensor-core convolution over `parts` output-channel parts of COUT_TILE.
 // gelu: 0 none, 1 GELU (pre-activation to aux_out when set), 2 multiply by GELU'(aux_in).
-template <int LOGN, int COUT_TILE, int CIN = 64, int NBUF = 2>
+template <int LOGN, int COUT_TILE, int CIN = 64, int NBUF = 4>
 static cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __nv_bfloat16* wpack,
                         const float* bias, __nv_bfloat16* out, int batch, int parts, int co_base, int cout_total,
                         int gelu, cudaStream_t st, const __nv_bfloat16* aux_in = nullptr,

@@ -260,8 +260,10 @@ class Solver:
         """Upload the learnable parameters from a device float32 tensor (no synchronisation)."""
         self._check(self.lib.fd_set_params_device(self.h, _ptr(params), int(params.numel()), _stream_handle(stream)))
 
-    def network_forward(self, u, coef_out, stream=None):
-        self._check(self.lib.fd_network_forward(self.h, _ptr(u), _ptr(coef_out), _stream_handle(stream)))
+    def network_forward(self, u, coef_out=None, stream=None):
+        """coef_out[batch, 160, n, n] float32 = C_theta(u); None runs the network only."""
+        cp = _ptr(coef_out) if coef_out is not None else None
+        self._check(self.lib.fd_network_forward(self.h, _ptr(u), cp, _stream_handle(stream)))
 
     def step_adjoint(self, u_in, lam_out, lam_in, dparams=None, stream=None):
         """lam_in = (du'/du)^T lam_out for u' = step(u_in); dparams (device

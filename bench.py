@@ -425,7 +425,7 @@ def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
     params = I.pack_params(I.random_wl(13, 1e-2), st)
     groups = [(32, 64, "burgers", False), (64, 64, "decaying", False), (128, 64, "kolmogorov", False),
               (256, 64, "shear", False), (32, 128, "kolmogorov", True), (64, 128, "decaying", True)]
-    batch = fd.Batch()
+    batch, tuned = fd.Batch(), fd.Batch()
     runs = []
     cells = 0
     for n, b, kind, learned in groups:
@@ -442,16 +442,30 @@ def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
         batch.add(s, u0, out, steps)
         runs.append((s, u0, out, steps))
         cells += b * n * n * steps
-    batch.run()
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        batch.run()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+
+    def timed_batch(bt):
+        bt.run()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            bt.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed_batch(batch)
+    batch.close()
+    # the same batch after each context's autotuner picked its plan (timed alone)
+    plans = []
+    for s, u0, out, steps in runs:
+        s.autotune(probe_steps=16)
+        plans.append(s.plan())
+        tuned.add(s, u0, out, steps)
+    ms_tuned = timed_batch(tuned)
+    tuned_launches = tuned.launch_count()
+    tuned.close()
     for s, u0, out, steps in runs:  # warm every solver's own path
         s.rollout(u0, out, steps)
     e0.record(stream)
@@ -462,8 +476,10 @@ def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
     ms_seq = e0.elapsed_time(e1)
     return {"workload": "512 trajectories: plain FP32 32^2 Burgers, 64^2 decaying, 128^2 Kolmogorov, 256^2 shear "
                         "(64 each) + learned 32^2 Kolmogorov, 64^2 decaying (128 each), physical time 0.5 each",
-            "value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_batch": ms,
-            "ms_one_after_another": ms_seq, "graph_kernel_launches": batch.launch_count(),
+            "value": cells / (min(ms, ms_tuned) * 1e-3), "unit": "cell-updates/s",
+            "ms_per_batch_default_plans": ms, "ms_per_batch_autotuned_plans": ms_tuned,
+            "autotuned_plans": [{k: p[k] for k in ("path", "cluster", "n_onchip", "n_stream")} for p in plans],
+            "ms_one_after_another": ms_seq, "graph_kernel_launches_autotuned": tuned_launches,
             "finite": all(bool(s.check_finite(out)) for s, _, out, _ in runs)}
 
 
@@ -549,6 +565,10 @@ def main():
 
     cfg = fd.Config(n=N, batch=BATCH, dtype="f32", nu=NU, dt=DT)
     solver = fd.Solver(cfg)
+    # launch plan: the library's autotuner times the cluster shapes and the
+    # on-chip / streaming splits of this batch and keeps the fastest
+    candidates = solver.autotune(probe_steps=32)
+    plan = solver.plan()
     seed0 = rank * BATCH
     U0 = np.stack([I.decaying_ic(N, seed0 + b) for b in range(BATCH)]).astype(np.float32)
     u0 = torch.tensor(U0, device="cuda")
@@ -610,7 +630,10 @@ def main():
         return
 
     avg_launch_s = statistics.mean(ms) * 1e-3
-    flops = FLOP_PER_CELL_STEP * units
+    # the dominant kernel is the on-chip rollout kernel; it processes the plan's
+    # n_onchip trajectories, and the call (which also waits for the concurrent
+    # streaming part) bounds its duration from above
+    flops = FLOP_PER_CELL_STEP * N * N * plan["n_onchip"] * args.time_steps
     achieved = flops / avg_launch_s / 1e12
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
@@ -621,8 +644,10 @@ def main():
         "unit": "TFLOP/s",
         "frac": achieved / peak,
         "traffic": None,
-        "kernel": "fv_rollout_kernel<float, 8, 8, 512, 4>",
+        "kernel": f"fv_rollout_kernel<float, 8, {plan['cluster']}, 512, 4> ({plan['n_onchip']} of {BATCH} "
+                  f"trajectories; {plan['n_stream']} on the streaming kernels concurrently)",
         "peak_basis": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x median sampled SM clock",
+        "achieved_all_trajectories": FLOP_PER_CELL_STEP * units / avg_launch_s / 1e12,
         "hbm_gbs_measured": _measured_peaks().get("hbm_gbs"),
     }
     cpu = None if args.no_cpu_baseline else cpu_baseline()
@@ -649,6 +674,9 @@ def main():
             "time_steps_per_bench_step": args.time_steps,
             "l2": "flushed (256 MB write) between timed bench steps; state resident on chip within a rollout",
             "parallelism": f"replicas x{world}",
+            "plan": plan,
+            "autotune_candidates": [{k: c[k] for k in ("cluster", "n_onchip", "n_stream", "resident", "us_per_step")}
+                                    for c in candidates],
         },
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -255,6 +255,55 @@ fd_status fd_adam_step(float* params, float* grads, float* m, float* v, int64_t 
 fd_status fd_downsample(const void* fine, void* coarse, int32_t batch, int32_t n_fine, int32_t ratio,
                         int32_t dtype, void* stream);
 
+/* ---- launch plans and the autotuner ------------------------------------------
+ *
+ * How a plain context's batch is laid out on the GPU. The paper has no
+ * counterpart (it runs one trajectory at a time on its own hardware); every
+ * plan computes the same step, and plans differ only in rounding order.
+ *   path 1 (plain, on chip): trajectories [0, n_onchip) run on the on-chip
+ *     rollout kernel with `cluster` CTAs per trajectory (each CTA owns
+ *     N / cluster rows); `resident` of them fit on the device at once, the
+ *     rest run in further waves. Trajectories [n_onchip, batch) run on the
+ *     streaming kernels (FP32, N >= 32) on a second, library-owned stream,
+ *     concurrently, on the SMs the resident clusters leave free; the call's
+ *     stream waits for both parts (graph capture of the call's stream
+ *     captures both).
+ *   path 2 (plain, streaming only) and path 3 (learned) have one plan each.
+ * A new context starts on its default plan: the first cluster shape of its
+ * grid, the whole batch on chip. */
+typedef struct {
+  int32_t path;       /* 1 plain on chip (+ streaming part), 2 streaming only, 3 learned (output) */
+  int32_t cluster;    /* CTAs per on-chip trajectory; 0 when n_onchip == 0 */
+  int32_t n_onchip;   /* trajectories [0, n_onchip) on the on-chip kernel */
+  int32_t n_stream;   /* trajectories [n_onchip, batch) on the streaming kernels */
+  int32_t resident;   /* on-chip trajectories resident at once on this device (output) */
+  double us_per_step; /* per-step time measured by fd_autotune (output; 0 = not measured) */
+} fd_plan;
+
+/* The context's current plan. Errors: FD_EINVAL for null pointers. */
+fd_status fd_get_plan(const fd_ctx* ctx, fd_plan* plan);
+
+/* Select a plan: cluster, n_onchip and n_stream are read (n_onchip +
+ * n_stream = batch). Synchronises the device. Errors: FD_EINVAL for a split
+ * that does not add up to the batch; FD_EUNSUPPORTED for a cluster size this
+ * build has no kernel for at this N, a streaming part the grid cannot take
+ * (FP64, N < 32), or any change to a learned or streaming-only context. */
+fd_status fd_set_plan(fd_ctx* ctx, const fd_plan* plan);
+
+/* Time every candidate plan of the context for `probe_steps` time steps
+ * (<= 0: 32) on a zero state of the context's shape (a library-owned scratch
+ * buffer of two states, freed before return), keep the fastest, and
+ * describe the candidates in report[0 .. min(max_report, *n_report) - 1]
+ * with their measured us_per_step. Candidates: every cluster shape with the
+ * whole batch on chip; for each shape whose resident count does not divide
+ * the batch, the same shape on the full waves with the remainder on the
+ * streaming kernels; the whole batch on the streaming kernels. Learned and
+ * streaming-only contexts have one candidate, which is timed. Runs on
+ * `stream` and synchronises it; report may be NULL when max_report is 0.
+ * Errors: FD_EINVAL, FD_ENOMEM, FD_ECUDA (the previous plan is kept). */
+fd_status fd_autotune(fd_ctx* ctx, int32_t probe_steps, fd_plan* report, int32_t max_report, int32_t* n_report,
+                      void* stream);
+
 /* ---- batches of rollouts ----------------------------------------------------
  *
  * Many concurrent trajectories of uneven grid sizes and flow types, learned

@@ -14,6 +14,7 @@
 
 #include "../../include/fd.h"
 #include "fd_ctx.h"
+#include "fd_launch.cuh"
 #include "fv_fused.cuh"
 
 using namespace ldfv;
@@ -33,57 +34,16 @@ fd_status fd_large_init(fd_ctx* c);
 void fd_large_free(fd_ctx* c);
 fd_status fd_large_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                            cudaStream_t st, bool allow_graph);
+// launch plans (fd_variants.cu, fd_plan.cu)
+void fd_extra_launchers(int dtype, int logn, int dord, std::vector<Launcher>& out);
+fd_status fd_plain_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
+                           cudaStream_t st, bool allow_graph);
 
 namespace {
 
 thread_local std::string g_init_error;
 
 
-
-template <typename T, int LOGN, int CS, int NT, int DORD>
-cudaError_t launch_fused(const FvArgs& a, int batch, size_t smem, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CS, batch, 1);
-  cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = CS > 1 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, fv_rollout_kernel<T, LOGN, CS, NT, DORD>, a);
-}
-
-template <typename T, int LOGN, int CS, int NT, int DORD>
-cudaError_t prepare_fused(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT, DORD>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (CS > 8) {
-    e = cudaFuncSetAttribute(fv_rollout_kernel<T, LOGN, CS, NT, DORD>,
-                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  }
-  return e;
-}
-
-template <typename T, int LOGN, int CS, int NT>
-Launcher make_launcher(int dord) {
-  Launcher l;
-  l.cs = CS;
-  l.nt = NT;
-  l.smem = FusedCfg<T, LOGN, CS, NT>::SMEM;
-  if (dord == 4) {
-    l.launch = &launch_fused<T, LOGN, CS, NT, 4>;
-    l.prepare = &prepare_fused<T, LOGN, CS, NT, 4>;
-  } else {
-    l.launch = &launch_fused<T, LOGN, CS, NT, 2>;
-    l.prepare = &prepare_fused<T, LOGN, CS, NT, 2>;
-  }
-  return l;
-}
 
 // Cluster size and block size per (type, N): CTAs own R = N / CS rows, each
 // thread one column of R * N / NT of those rows. Every configuration with
@@ -252,6 +212,24 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   }
   e = cudaMemcpy(c->d_tables, host.data(), host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && onchip) e = L.prepare(L.smem);
+  if (e == cudaSuccess && onchip) {
+    // launch plan: the default configuration first, then the other cluster
+    // shapes this build has for the grid (a shape that cannot be prepared on
+    // this device is left out)
+    std::vector<Launcher> extra;
+    if (!o.learned) fd_extra_launchers(g.dtype, logn, o.deriv_order, extra);
+    c->variants.push_back(L);
+    for (const Launcher& x : extra)
+      if (x.prepare(x.smem) == cudaSuccess) c->variants.push_back(x);
+    cudaGetLastError();
+    for (const Launcher& x : c->variants) {
+      int cap = 0;
+      if (x.occupancy(x.smem, &cap) != cudaSuccess) cap = 0;
+      c->capacity.push_back(cap);
+    }
+    cudaGetLastError();
+    c->n_onchip = g.batch;
+  }
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
     delete c;
@@ -312,16 +290,7 @@ fd_status fd_rollout_impl(fd_ctx* c, const void* u0, void* traj, void* u_final, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (c->lrn) return fd_learned_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
   if (c->big) return fd_large_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
-  FvArgs a = c->base;
-  a.u_in = u0;
-  a.u_out = u_final;
-  a.traj = save_every > 0 ? traj : nullptr;
-  a.n_steps = n_steps;
-  a.save_every = save_every;
-  cudaError_t e = c->L.launch(a, c->grid.batch, c->L.smem, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout: launch failed: %s", cudaGetErrorString(e));
-  c->launches = 1;
-  return FD_OK;
+  return fd_plain_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
 }
 
 extern "C" {
@@ -409,6 +378,10 @@ fd_status fd_destroy(fd_ctx* c) {
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_state) cudaFree(c->d_state);
   if (c->d_flag) cudaFree(c->d_flag);
+  if (c->side) fd_destroy(c->side);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   fd_train_free(c);
   fd_adjoint_free(c);
   fd_learned_free(c);

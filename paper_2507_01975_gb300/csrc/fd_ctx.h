@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fd.h"
 #include "fv_fused.cuh"
@@ -16,6 +17,8 @@ struct Launcher {
   size_t smem = 0;
   cudaError_t (*launch)(const FvArgs&, int batch, size_t smem, cudaStream_t) = nullptr;
   cudaError_t (*prepare)(size_t smem) = nullptr;
+  // trajectories resident at once (after prepare)
+  cudaError_t (*occupancy)(size_t smem, int* trajectories) = nullptr;
 };
 
 // Device buffers and launch state of the learnable module.
@@ -91,6 +94,7 @@ struct LargeState {
   void* spec = nullptr;        // [batch][N/8][N/2 + 1][8] complex half spectra (8-row groups)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;  // one step
+  size_t snap_stride = 0;      // bytes between snapshots in traj (0: one state)
 };
 
 // Workspace of the rollout reverse mode and the training step: checkpoints
@@ -127,6 +131,18 @@ struct fd_ctx {
   ldfv::AdjointState* adj = nullptr;
   ldfv::TrainState* trn = nullptr;
   ldfv::LargeState* big = nullptr;   // set when the streaming path runs this context
+  // launch plan of a plain on-chip context: on-chip configurations valid for
+  // this grid ([0] = default), the one in use, and how the batch is split
+  // between it and a streaming context that runs the trajectories
+  // [n_onchip, batch) concurrently on side_stream
+  std::vector<ldfv::Launcher> variants;
+  std::vector<int> capacity;          // trajectories resident at once, per variant
+  int variant = 0;
+  int n_onchip = 0, n_stream = 0;
+  double plan_us = 0;                 // per-step time measured by fd_autotune
+  fd_ctx* side = nullptr;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // shared helpers of the ABI translation units

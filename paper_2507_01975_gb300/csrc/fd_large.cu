@@ -150,7 +150,8 @@ fd_status fd_large_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final,
     } else {
       e = large_step(c, st);
       if (e == cudaSuccess && traj && save_every > 0 && (k + 1) % save_every == 0) {
-        e = cudaMemcpyAsync(static_cast<char*>(traj) + (size_t)snap * bytes, S.un, bytes, cudaMemcpyDeviceToDevice,
+        const size_t stride = S.snap_stride ? S.snap_stride : bytes;
+        e = cudaMemcpyAsync(static_cast<char*>(traj) + (size_t)snap * stride, S.un, bytes, cudaMemcpyDeviceToDevice,
                             st);
         ++snap;
       }

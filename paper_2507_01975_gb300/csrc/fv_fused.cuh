@@ -41,6 +41,7 @@ struct FvArgs {
   void* traj;
   int n_steps;
   int save_every;
+  int traj_batch;  // trajectories per snapshot in traj (0: the launch's batch)
   int flow;     // 0 Burgers, 1 Navier-Stokes
   int forcing;  // 0 none, 1 Kolmogorov
   double dt, nu, idx, idy, drag, inv_nn;
@@ -110,6 +111,16 @@ __device__ __forceinline__ void csync() {
   } else {
     __syncthreads();
   }
+}
+
+// split cluster barrier: every thread arrives once and then waits once
+template <int CS>
+__device__ __forceinline__ void cluster_arrive() {
+  if constexpr (CS > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+template <int CS>
+__device__ __forceinline__ void cluster_wait() {
+  if constexpr (CS > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 template <int CS, typename P>
@@ -277,6 +288,10 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
           }
         }
       }
+      // the neighbours read this CTA's rows above; phase C overwrites them in
+      // place, so its first write waits until every CTA of the cluster has
+      // arrived here (split barrier: the wait falls after two bands of work)
+      cluster_arrive<CS>();
       __syncthreads();
 
       // ---- C: tendency and RK4 combination -------------------------------------
@@ -325,6 +340,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             wv_extra = stage < 3 ? unv0 + ca * ev : unv0 + c6 * (nrow[N + ci] + ev);
           }
           __syncthreads();
+          if (r == 1) cluster_wait<CS>();
           if (r > 0) {
             const int hp = (r - 1) * Cfg::G + grp + 2;
             wt[hp * N + ci] = pu;
@@ -334,6 +350,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
           pv = nv_;
         }
         tmem_wait_st();
+        if constexpr (RT == 1) cluster_wait<CS>();
         __syncthreads();
         const int hl = (RT - 1) * Cfg::G + grp + 2;
         wt[hl * N + ci] = pu;
@@ -547,7 +564,8 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
     if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
     tmem_wait_st();
     if (a.save_every > 0 && a.traj != nullptr && (step % a.save_every) == 0) {
-      T* out = reinterpret_cast<T*>(a.traj) + ((size_t)snap * gridDim.y + traj) * 2 * NN;
+      const size_t tb = a.traj_batch > 0 ? (size_t)a.traj_batch : (size_t)gridDim.y;
+      T* out = reinterpret_cast<T*>(a.traj) + ((size_t)snap * tb + traj) * 2 * NN;
 #pragma unroll
       for (int r = 0; r < RT; ++r) {
         const int jj = r * Cfg::G + grp, hr = jj + 2;

@@ -40,6 +40,9 @@ EXPORTS = [
     "fd_vorticity_pcc",
     "fd_adam_step",
     "fd_downsample",
+    "fd_get_plan",
+    "fd_set_plan",
+    "fd_autotune",
     "fd_batch_create",
     "fd_batch_add",
     "fd_batch_run",
@@ -79,6 +82,20 @@ class FdOptions(C.Structure):
         ("spin_limit", C.c_int64),
         ("path", C.c_int32),
     ]
+
+
+class FdPlan(C.Structure):
+    _fields_ = [
+        ("path", C.c_int32),
+        ("cluster", C.c_int32),
+        ("n_onchip", C.c_int32),
+        ("n_stream", C.c_int32),
+        ("resident", C.c_int32),
+        ("us_per_step", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class FdError(RuntimeError):
@@ -134,6 +151,12 @@ def load(path: str = LIB_PATH):
     lib.fd_adam_step.restype = C.c_int
     lib.fd_downsample.argtypes = [vp, vp, i32, i32, i32, i32, vp]
     lib.fd_downsample.restype = C.c_int
+    lib.fd_get_plan.argtypes = [vp, C.POINTER(FdPlan)]
+    lib.fd_get_plan.restype = C.c_int
+    lib.fd_set_plan.argtypes = [vp, C.POINTER(FdPlan)]
+    lib.fd_set_plan.restype = C.c_int
+    lib.fd_autotune.argtypes = [vp, i32, C.POINTER(FdPlan), i32, C.POINTER(i32), vp]
+    lib.fd_autotune.restype = C.c_int
     lib.fd_batch_create.argtypes = [C.POINTER(C.c_void_p)]
     lib.fd_batch_create.restype = C.c_int
     lib.fd_batch_add.argtypes = [vp, vp, vp, vp, i32]
@@ -238,6 +261,23 @@ class Solver:
     def rollout_host(self, u0_host, u_final_host, n_steps: int, stream=None):
         self._check(self.lib.fd_rollout_host(self.h, _ptr(u0_host), _ptr(u_final_host), int(n_steps),
                                              _stream_handle(stream)))
+
+    def plan(self) -> dict:
+        """The context's launch plan (path, cluster, n_onchip, n_stream, resident, us_per_step)."""
+        p = FdPlan()
+        self._check(self.lib.fd_get_plan(self.h, C.byref(p)))
+        return p.as_dict()
+
+    def set_plan(self, cluster: int, n_onchip: int, n_stream: int = 0):
+        p = FdPlan(0, int(cluster), int(n_onchip), int(n_stream), 0, 0.0)
+        self._check(self.lib.fd_set_plan(self.h, C.byref(p)))
+
+    def autotune(self, probe_steps: int = 32, stream=None) -> list:
+        """Time every candidate launch plan, keep the fastest; returns the candidates."""
+        rep = (FdPlan * 32)()
+        n = C.c_int32(0)
+        self._check(self.lib.fd_autotune(self.h, int(probe_steps), rep, 32, C.byref(n), _stream_handle(stream)))
+        return [rep[i].as_dict() for i in range(min(n.value, 32))]
 
     def check_finite(self, u, stream=None) -> bool:
         st = self.lib.fd_check_finite(self.h, _ptr(u), _stream_handle(stream))

@@ -520,6 +520,9 @@ def main():
     ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
+    ap.add_argument("--plan", default=None,
+                    help="cluster,n_onchip,n_stream: fix the launch plan instead of autotuning it (profiling "
+                         "under ncu, which serialises kernels and so changes the autotuner's ranking)")
     ap.add_argument("--time-steps", type=int, default=STEPS_PER_ROLLOUT,
                     help="time steps per rollout (the workload's 2000 by default; smaller only for ncu captures)")
     args = ap.parse_args()
@@ -567,7 +570,12 @@ def main():
     solver = fd.Solver(cfg)
     # launch plan: the library's autotuner times the cluster shapes and the
     # on-chip / streaming splits of this batch and keeps the fastest
-    candidates = solver.autotune(probe_steps=32)
+    if args.plan:
+        cl, on, stv = (int(x) for x in args.plan.split(","))
+        solver.set_plan(cl, on, stv)
+        candidates = []
+    else:
+        candidates = solver.autotune(probe_steps=32)
     plan = solver.plan()
     seed0 = rank * BATCH
     U0 = np.stack([I.decaying_ic(N, seed0 + b) for b in range(BATCH)]).astype(np.float32)

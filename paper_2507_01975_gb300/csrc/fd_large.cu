@@ -13,9 +13,49 @@ using namespace ldfv;
 
 namespace {
 
-size_t rows_smem(int n) { return (size_t)(kLRB / 2) * n * 8 + (size_t)n * 8; }
-size_t cols_smem(int n) { return (size_t)kLCB * n * 8 + (size_t)n * 8 + (size_t)n * 4; }
-size_t rows_inv_smem(int n) { return rows_smem(n); }
+// the three projection kernels of one stage, instantiated per grid size
+template <int LOGN>
+cudaError_t projection(const LargeArgs& a, int B, cudaStream_t st) {
+  using R = RowCfg<LOGN>;
+  using C = ColCfg<LOGN>;
+  const dim3 grow(R::N / R::RG, B);
+  const dim3 gcol((R::N / 2 + 1 + C::C - 1) / C::C, B);
+  large_rows_fwd_kernel<LOGN><<<grow, R::NT, R::SMEM, st>>>(a);
+  large_cols_kernel<LOGN><<<gcol, C::NT, C::SMEM, st>>>(a);
+  large_rows_inv_kernel<LOGN><<<grow, R::NT, R::SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t prepare_projection() {
+  cudaError_t e = cudaFuncSetAttribute(large_rows_fwd_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)RowCfg<LOGN>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(large_cols_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ColCfg<LOGN>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(large_rows_inv_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RowCfg<LOGN>::SMEM);
+  return e;
+}
+
+cudaError_t dispatch_projection(int logn, const LargeArgs* a, int B, cudaStream_t st) {
+  switch (logn) {
+#define LDFV_PROJ(L) \
+  case L:            \
+    return a ? projection<L>(*a, B, st) : prepare_projection<L>();
+    LDFV_PROJ(5)
+    LDFV_PROJ(6)
+    LDFV_PROJ(7)
+    LDFV_PROJ(8)
+    LDFV_PROJ(9)
+    LDFV_PROJ(10)
+    LDFV_PROJ(11)
+#undef LDFV_PROJ
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
 
 LargeArgs base_args(fd_ctx* c) {
   LargeArgs a;
@@ -48,8 +88,6 @@ cudaError_t large_step(fd_ctx* c, cudaStream_t st) {
   LargeArgs a = base_args(c);
   float* wsb[2] = {S.wsA, S.wsB};
   const dim3 gst(n / kLTX, n / kLTY, B);
-  const dim3 grow(n / kLRB, B);
-  const dim3 gcol((n / 2 + 1 + kLCB - 1) / kLCB, B);
   cudaError_t e = cudaSuccess;
   // Burgers has no pressure: the stages chain without projections
   const bool ns = c->grid.flow == FD_NAVIER_STOKES;
@@ -62,12 +100,8 @@ cudaError_t large_step(fd_ctx* c, cudaStream_t st) {
       large_stage_kernel<4><<<gst, 256, 0, st>>>(a, logn);
     else
       large_stage_kernel<2><<<gst, 256, 0, st>>>(a, logn);
-    if (ns) {
-      large_rows_fwd_kernel<<<grow, 512, rows_smem(n), st>>>(a, logn);
-      large_cols_kernel<<<gcol, 512, cols_smem(n), st>>>(a, logn);
-      large_rows_inv_kernel<<<grow, 512, rows_inv_smem(n), st>>>(a, logn);
-    }
     e = cudaGetLastError();
+    if (ns && e == cudaSuccess) e = dispatch_projection(logn, &a, B, st);
   }
   if (e == cudaSuccess) {
     a.ws = wsb[1];
@@ -101,13 +135,7 @@ fd_status fd_large_init(fd_ctx* c) {
   alloc((void**)&S->wsB, state);
   alloc((void**)&S->p, B * n * n * sizeof(float));
   alloc(&S->spec, B * (n / kLRB) * (n / 2 + 1) * kLRB * 8);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(large_rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(n));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(large_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem(n));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(large_rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)rows_inv_smem(n));
+  if (e == cudaSuccess) e = dispatch_projection(c->logn, nullptr, 0, nullptr);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: streaming workspace: %s", cudaGetErrorString(e));
   return FD_OK;

@@ -14,10 +14,11 @@
 //   cols      column FFTs, multiplication by 1 / symbol(D2 G2) (zero mode 0,
 //             App. B.3-B.4), inverse column FFTs;
 //   rows_inv  complex-to-real inverse row FFTs -> pressure p.
-// A final kernel forms u_{n+1} = w*_4 - G2 p_4. The FFTs are radix-2
-// transforms in shared memory (decimation in frequency forward, natural in /
-// bit-reversed out; decimation in time inverse, bit-reversed in / natural out),
-// so no reordering pass is needed between them.
+// A final kernel forms u_{n+1} = w*_4 - G2 p_4. The FFTs are register-resident
+// Stockham transforms: N/16 threads per transform hold 16 points each, a pass
+// is one radix-16 (or the remaining radix-2/4/8) butterfly per thread in
+// registers, and the points go through shared memory only between passes
+// (two exchanges for N = 2048); input and output are in natural order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,113 +46,233 @@ struct LargeArgs {
 };
 
 constexpr int kLTX = 32, kLTY = 16;  // stage tile (cells)
-constexpr int kLRB = 8;              // rows per CTA of the row transforms (4 complex transforms)
-constexpr int kLCB = 2;              // columns per CTA of the column transforms (power of two)
+constexpr int kLRB = 8;              // rows per block of the half-spectrum layout
 
 __device__ __forceinline__ float2 c2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c2mul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 c2mulc(float2 a, float2 w) {  // a * conj(w)
-  return make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
-}
-__device__ __forceinline__ int brev_n(int k, int logn) { return (int)(__brev((unsigned)k) >> (32 - logn)); }
+__device__ __forceinline__ float2 c2negi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
+__device__ __forceinline__ float2 c2conj(float2 a) { return make_float2(a.x, -a.y); }
 
-// Shared-memory position of element p of the transform buffers: bits 0-4 are
-// XOR-ed with bits 6-10. Runs of 64 consecutive elements stay a permutation of
-// one another (conflict-free passes), while the bit-reversed gathers and
-// scatters of the packing steps (elements 64 m apart) spread over 16 banks
-// instead of one. Its own inverse.
-__device__ __forceinline__ int swz(int p) { return p ^ ((p >> 6) & 31); }
+// ---- register-resident Stockham FFT -------------------------------------------
+// A transform of N = 2^LOGN points is done by T = N / 16 threads holding 16
+// points each. Pass p has radix R_p (16, 16, ..., then 2^(LOGN mod 4)) and
+// stride NS_p = R_0 ... R_{p-1}. Butterfly q of the pass takes the points
+// q + r N / R (r < R), which thread t = q mod T holds in registers s + (16/R) r
+// (s = q / T) when every thread holds the points t + m T (m < 16); it
+// multiplies point r by exp(-2 pi i (q mod NS) r / (NS R)), transforms the R
+// points and sends output r to position (q / NS) NS R + (q mod NS) + r NS
+// (Stockham autosort: after the last pass the order is natural). Between
+// passes the points go through a padded shared-memory buffer and come back
+// in the "points t + m T" pattern.
+template <int LOGN>
+struct SPlan {
+  static constexpr int N = 1 << LOGN, T = N / 16;
+  static constexpr int NP = (LOGN + 3) / 4;  // passes
+  static constexpr int radix(int p) { return p < LOGN / 4 ? 16 : (1 << (LOGN % 4)); }
+  static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
+  // per-pass twiddle tables [R][NS] for passes 1 .. NP-1, stored one after another
+  static constexpr int tw_off(int p) { return p <= 1 ? 0 : tw_off(p - 1) + ns(p - 1) * radix(p - 1); }
+  static constexpr int TW = NP > 1 ? tw_off(NP) : 0;
+  // after the last pass register s + SL r of thread t holds X[t + s T + r NSL]
+  static constexpr int RL = radix(NP - 1), SL = 16 / RL, NSL = ns(NP - 1);
+  static constexpr int BUF = N + N / 16 + 4;  // padded buffer of one transform (float2)
+};
 
-// Stage-major twiddles in shared memory: tws[h + j] = exp(-2 pi i j / (2 h)) for
-// h = 1, 2, 4, .., N/2 and j < h (N - 1 entries, index 0 unused), so that the
-// butterflies of one stage read consecutive entries (no bank conflicts).
-__device__ void load_stage_twiddles(float2* tws, const float2* tw, int logn) {
-  const int N = 1 << logn;
-  for (int e = threadIdx.x + 1; e < N; e += blockDim.x) {
-    const int ls = 31 - __clz(e);  // h = 2^ls <= e < 2h
-    const int j = e - (1 << ls);
-    tws[e] = tw[j << (logn - 1 - ls)];
-  }
-}
+__device__ __forceinline__ int fpad(int p) { return p + (p >> 4); }
 
-// F forward transforms of length N = 2^logn stored at x + f * N: natural-order
-// input, bit-reversed output (decimation in frequency). Two radix-2 stages
-// (halves 2q and q) are fused into one radix-4 pass in registers; an odd
-// logn ends with one radix-2 stage. Index arithmetic is shifts and masks.
-__device__ void block_fft_dif(float2* x, int F, int logn, const float2* tws) {
-  const int Q = 1 << (logn - 2);  // radix-4 groups per transform
-  int ls = logn - 1;              // log2 of the current stage's half
-  for (; ls >= 1; ls -= 2) {
-    const int lq = ls - 1, q = 1 << lq;  // halves 2q (first stage) and q (second)
-    for (int t = threadIdx.x; t < F * Q; t += blockDim.x) {
-      const int f = t >> (logn - 2), r = t & (Q - 1);
-      const int j = r & (q - 1);
-      const int o = (f << logn) + ((r >> lq) << (lq + 2)) + j;
-      const int i0 = swz(o), i1 = swz(o + q), i2 = swz(o + 2 * q), i3 = swz(o + 3 * q);
-      const float2 a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
-      const float2 s0 = c2add(a0, a2), s2 = c2mul(c2sub(a0, a2), tws[2 * q + j]);
-      const float2 s1 = c2add(a1, a3), s3 = c2mul(c2sub(a1, a3), tws[3 * q + j]);
-      const float2 w = tws[q + j];
-      x[i0] = c2add(s0, s1);
-      x[i1] = c2mul(c2sub(s0, s1), w);
-      x[i2] = c2add(s2, s3);
-      x[i3] = c2mul(c2sub(s2, s3), w);
+// twiddles of passes 1 .. NP-1 from the table tw[m] = exp(-2 pi i m / N), m < N/2
+template <int LOGN>
+__device__ void build_pass_twiddles(float2* tws, const float2* tw) {
+  using SP = SPlan<LOGN>;
+  constexpr int N = SP::N;
+#pragma unroll
+  for (int p = 1; p < SP::NP; ++p) {
+    const int R = SP::radix(p), NS = SP::ns(p), off = SP::tw_off(p);
+    for (int e = threadIdx.x; e < R * NS; e += blockDim.x) {
+      const int r = e / NS, j = e % NS;
+      const int m = j * r * (N / (NS * R));
+      tws[off + e] = m < N / 2 ? tw[m] : make_float2(-tw[m - N / 2].x, -tw[m - N / 2].y);
     }
-    __syncthreads();
-  }
-  if (ls == 0) {  // remaining radix-2 stage, half = 1
-    const int H = 1 << (logn - 1);
-    for (int t = threadIdx.x; t < F * H; t += blockDim.x) {
-      const int i0 = swz(2 * t), i1 = swz(2 * t + 1);
-      const float2 a = x[i0], c = x[i1];
-      x[i0] = c2add(a, c);
-      x[i1] = c2sub(a, c);
-    }
-    __syncthreads();
   }
 }
 
-// F inverse (unnormalised) transforms: bit-reversed input, natural output
-// (decimation in time, conjugate twiddles): an odd logn starts with one
-// radix-2 stage, then radix-4 passes fuse halves q and 2q.
-__device__ void block_ifft_dit(float2* x, int F, int logn, const float2* tws) {
-  int ls = 0;
-  if (logn & 1) {
-    const int H = 1 << (logn - 1);
-    for (int t = threadIdx.x; t < F * H; t += blockDim.x) {
-      const int i0 = swz(2 * t), i1 = swz(2 * t + 1);
-      const float2 a = x[i0], c = x[i1];
-      x[i0] = c2add(a, c);
-      x[i1] = c2sub(a, c);
-    }
-    __syncthreads();
-    ls = 1;
-  }
-  const int Q = 1 << (logn - 2);
-  for (; ls + 1 < logn; ls += 2) {
-    const int lq = ls, q = 1 << lq;  // halves q (first stage) and 2q (second)
-    for (int t = threadIdx.x; t < F * Q; t += blockDim.x) {
-      const int f = t >> (logn - 2), r = t & (Q - 1);
-      const int j = r & (q - 1);
-      const int o = (f << logn) + ((r >> lq) << (lq + 2)) + j;
-      const int i0 = swz(o), i1 = swz(o + q), i2 = swz(o + 2 * q), i3 = swz(o + 3 * q);
-      const float2 a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
-      const float2 w = tws[q + j];
-      const float2 t1 = c2mulc(a1, w), t3 = c2mulc(a3, w);
-      const float2 s0 = c2add(a0, t1), s1 = c2sub(a0, t1);
-      const float2 s2 = c2add(a2, t3), s3 = c2sub(a2, t3);
-      const float2 u2 = c2mulc(s2, tws[2 * q + j]), u3 = c2mulc(s3, tws[3 * q + j]);
-      x[i0] = c2add(s0, u2);
-      x[i2] = c2sub(s0, u2);
-      x[i1] = c2add(s1, u3);
-      x[i3] = c2sub(s1, u3);
-    }
-    __syncthreads();
+// forward DFT of R points in registers, natural order in and out
+template <int R>
+__device__ __forceinline__ void dft(float2* v);
+template <>
+__device__ __forceinline__ void dft<1>(float2*) {}
+template <>
+__device__ __forceinline__ void dft<2>(float2* v) {
+  const float2 a = v[0], b = v[1];
+  v[0] = c2add(a, b);
+  v[1] = c2sub(a, b);
+}
+template <>
+__device__ __forceinline__ void dft<4>(float2* v) {
+  const float2 t0 = c2add(v[0], v[2]), t1 = c2sub(v[0], v[2]);
+  const float2 t2 = c2add(v[1], v[3]), t3 = c2negi(c2sub(v[1], v[3]));
+  v[0] = c2add(t0, t2);
+  v[2] = c2sub(t0, t2);
+  v[1] = c2add(t1, t3);
+  v[3] = c2sub(t1, t3);
+}
+// radix 2 x 4: X_k = E_k + W8^k O_k, X_{k+4} = E_k - W8^k O_k
+template <>
+__device__ __forceinline__ void dft<8>(float2* v) {
+  float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+  dft<4>(e);
+  dft<4>(o);
+  const float h = 0.70710678118654752f;  // cos(pi / 4)
+  o[1] = make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));   // (1 - i) h
+  o[2] = c2negi(o[2]);                                                 // -i
+  o[3] = make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));  // -(1 + i) h
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = c2add(e[k], o[k]);
+    v[k + 4] = c2sub(e[k], o[k]);
   }
 }
+// radix 2 x 8: X_k = E_k + W16^k O_k, X_{k+8} = E_k - W16^k O_k
+template <>
+__device__ __forceinline__ void dft<16>(float2* v) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    e[k] = v[2 * k];
+    o[k] = v[2 * k + 1];
+  }
+  dft<8>(e);
+  dft<8>(o);
+  const float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  o[1] = c2mul(o[1], make_float2(c1, -s1));
+  o[2] = make_float2(h * (o[2].x + o[2].y), h * (o[2].y - o[2].x));
+  o[3] = c2mul(o[3], make_float2(s1, -c1));
+  o[4] = c2negi(o[4]);
+  o[5] = c2mul(o[5], make_float2(-s1, -c1));
+  o[6] = make_float2(h * (o[6].y - o[6].x), -h * (o[6].x + o[6].y));
+  o[7] = c2mul(o[7], make_float2(-c1, -s1));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = c2add(e[k], o[k]);
+    v[k + 8] = c2sub(e[k], o[k]);
+  }
+}
+
+template <int LOGN, int P>
+__device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2* tws, int t) {
+  using SP = SPlan<LOGN>;
+  constexpr int R = SP::radix(P), NS = SP::ns(P), S = 16 / R, T = SP::T;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    float2 w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = v[s + S * r];
+    if constexpr (NS > 1) {
+      const int j = (t + s * T) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) w[r] = c2mul(w[r], tws[SP::tw_off(P) + r * NS + j]);
+    }
+    dft<R>(w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[s + S * r] = w[r];
+  }
+}
+
+// outputs of pass P to their Stockham positions
+template <int LOGN, int P>
+__device__ __forceinline__ void fft_store(float2* buf, const float2 (&v)[16], int t) {
+  using SP = SPlan<LOGN>;
+  constexpr int R = SP::radix(P), NS = SP::ns(P), S = 16 / R, T = SP::T;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int q = t + s * T;
+    const int base = (q / NS) * NS * R + (q & (NS - 1));
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[fpad(base + r * NS)] = v[s + S * r];
+  }
+}
+
+template <int LOGN>
+__device__ __forceinline__ void fft_load(float2 (&v)[16], const float2* buf, int t) {
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = buf[fpad(t + m * SPlan<LOGN>::T)];
+}
+
+// the final registers (natural order X[t + s T + r NSL]) to the buffer
+template <int LOGN>
+__device__ __forceinline__ void fft_store_natural(float2* buf, const float2 (&v)[16], int t) {
+  using SP = SPlan<LOGN>;
+#pragma unroll
+  for (int s = 0; s < SP::SL; ++s)
+#pragma unroll
+    for (int r = 0; r < SP::RL; ++r) buf[fpad(t + s * SP::T + r * SP::NSL)] = v[s + SP::SL * r];
+}
+
+// synchronisation of the T threads of one transform: a named barrier per
+// transform when it spans whole warps of its own (T >= 64), else the warp
+struct TransformSync {
+  int id, n;
+  __device__ __forceinline__ void operator()() const {
+    if (n >= 64)
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    else
+      __syncwarp();
+  }
+};
+
+// forward transform of the points t + m T in v; on return v[s + SL r] = X[t + s T + r NSL].
+// buf is the transform's shared buffer (free on entry and on return)
+template <int LOGN>
+__device__ __forceinline__ void fft_forward(float2 (&v)[16], float2* buf, const float2* tws, int t, TransformSync sync) {
+  using SP = SPlan<LOGN>;
+  fft_pass<LOGN, 0>(v, tws, t);
+  if constexpr (SP::NP > 1) {
+    fft_store<LOGN, 0>(buf, v, t);
+    sync();
+    fft_load<LOGN>(v, buf, t);
+    sync();
+    fft_pass<LOGN, 1>(v, tws, t);
+  }
+  if constexpr (SP::NP > 2) {
+    fft_store<LOGN, 1>(buf, v, t);
+    sync();
+    fft_load<LOGN>(v, buf, t);
+    sync();
+    fft_pass<LOGN, 2>(v, tws, t);
+  }
+  static_assert(SP::NP <= 3, "N <= 4096");
+}
+
+// unnormalised inverse: conj(forward(conj(x)))
+template <int LOGN>
+__device__ __forceinline__ void fft_inverse(float2 (&v)[16], float2* buf, const float2* tws, int t, TransformSync sync) {
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = c2conj(v[m]);
+  fft_forward<LOGN>(v, buf, tws, t, sync);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = c2conj(v[m]);
+}
+
+// transforms per CTA of the row and column kernels: 512 threads at most
+template <int LOGN>
+struct RowCfg {
+  static constexpr int N = 1 << LOGN, T = N / 16;
+  static constexpr int F = (512 / T) < (N / 2) ? (512 / T) : (N / 2);  // row transforms (2 real rows each)
+  static constexpr int NT = F * T;
+  static constexpr int RG = 2 * F;  // rows per CTA, a multiple of kLRB
+  static constexpr size_t SMEM = ((size_t)F * SPlan<LOGN>::BUF + SPlan<LOGN>::TW) * sizeof(float2);
+  static_assert(RG % kLRB == 0, "whole row groups");
+};
+template <int LOGN>
+struct ColCfg {
+  static constexpr int N = 1 << LOGN, T = N / 16;
+  static constexpr int C = (512 / T) < N ? (512 / T) : N;  // spectrum columns per CTA
+  static constexpr int NT = C * T;
+  static constexpr size_t SMEM = ((size_t)C * SPlan<LOGN>::BUF + SPlan<LOGN>::TW) * sizeof(float2);
+};
 
 // ---------------------------------------------------------------------------
 // stage kernel: tile of kLTX x kLTY cells, 256 threads (two cells each)
@@ -258,108 +379,143 @@ __global__ void __launch_bounds__(256) large_stage_kernel(const LargeArgs a, int
 }
 
 // ---------------------------------------------------------------------------
-// rows_fwd: kLRB rows per CTA -> kLRB / 2 complex row transforms
+// rows_fwd: RG rows per CTA -> RG / 2 complex row transforms
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) large_rows_fwd_kernel(const LargeArgs a, int logn) {
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_fwd_kernel(const LargeArgs a) {
+  using Cfg = RowCfg<LOGN>;
+  using SP = SPlan<LOGN>;
+  constexpr int N = Cfg::N, T = Cfg::T, H = N / 2, MSK = N - 1;
   extern __shared__ __align__(16) float2 sm[];
-  const int N = 1 << logn, MSK = N - 1, H = N / 2;
-  constexpr int F = kLRB / 2;
-  float2* buf = sm;           // [F][N]
-  float2* tw = sm + F * N;    // [N] stage-major twiddles
-  const int b = blockIdx.y, g = blockIdx.x, y0 = g * kLRB;
+  float2* tws = sm + Cfg::F * SP::BUF;
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = sm + f * SP::BUF;
+  const int b = blockIdx.y, y0 = blockIdx.x * Cfg::RG;
   const size_t NN = (size_t)N * N;
   const float* u = a.ws + (size_t)b * 2 * NN;
   const float* v = u + NN;
-  load_stage_twiddles(tw, a.tw, logn);
-  for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
-    const int f = t >> logn, x = t & MSK;
-    const int ra = y0 + 2 * f, rb = ra + 1;
-    const int xe = (x + 1) & MSK;
+  build_pass_twiddles<LOGN>(tws, a.tw);
+  // divergence D2 w* of rows ra and rb as the real and imaginary parts
+  const int ra = y0 + 2 * f, rb = ra + 1, rc = (rb + 1) & MSK;
+  float2 z[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int x = t + m * T, xe = (x + 1) & MSK;
     const float da = (u[(size_t)ra * N + xe] - u[(size_t)ra * N + x]) * a.idx +
                      (v[(size_t)rb * N + x] - v[(size_t)ra * N + x]) * a.idy;
     const float db = (u[(size_t)rb * N + xe] - u[(size_t)rb * N + x]) * a.idx +
-                     (v[(size_t)((rb + 1) & MSK) * N + x] - v[(size_t)rb * N + x]) * a.idy;
-    buf[swz(t)] = make_float2(da, db);
+                     (v[(size_t)rc * N + x] - v[(size_t)rb * N + x]) * a.idy;
+    z[m] = make_float2(da, db);
   }
+  __syncthreads();  // twiddles
+  fft_forward<LOGN>(z, buf, tws, t, TransformSync{1 + f, T});
+  fft_store_natural<LOGN>(buf, z, t);
   __syncthreads();
-  block_fft_dif(buf, F, logn, tw);
-  // unpack the two real rows of transform f: A_k = (Z_k + conj Z_{N-k}) / 2,
-  // B_k = (Z_k - conj Z_{N-k}) / (2i); Z_k sits at bit-reversed position. One
-  // float4 (A_k, B_k) per (k, f): the block is written contiguously.
-  float4* blk = reinterpret_cast<float4*>(a.spec + ((size_t)b * (N / kLRB) + g) * (H + 1) * kLRB);
-  for (int t = threadIdx.x; t < (H + 1) * F; t += blockDim.x) {
-    const int k = t >> 2, f = t & 3;
-    const float2 zk = buf[swz((f << logn) + brev_n(k & MSK, logn))];
-    const float2 zm = buf[swz((f << logn) + brev_n((N - k) & MSK, logn))];
-    blk[t] = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  // unpack the two real rows of each transform: A_k = (Z_k + conj Z_{N-k}) / 2,
+  // B_k = (Z_k - conj Z_{N-k}) / (2i); one float4 (A_k, B_k) per (k, transform),
+  // each row group's block written contiguously
+  for (int e = threadIdx.x; e < (H + 1) * Cfg::F; e += Cfg::NT) {
+    const int gi = e / ((H + 1) * 4), rem = e - gi * ((H + 1) * 4);
+    const int k = rem >> 2, ff = gi * 4 + (rem & 3);
+    const float2* bf = sm + ff * SP::BUF;
+    const float2 zk = bf[fpad(k & MSK)], zm = bf[fpad((N - k) & MSK)];
+    float4* blk = reinterpret_cast<float4*>(a.spec + ((size_t)b * (N / kLRB) + y0 / kLRB + gi) * (H + 1) * kLRB);
+    blk[rem] = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
 }
 
 // ---------------------------------------------------------------------------
-// cols: kLCB spectrum columns per CTA: forward FFT along y, 1 / symbol, inverse
+// cols: C spectrum columns per CTA: forward FFT along y, 1 / symbol, inverse
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) large_cols_kernel(const LargeArgs a, int logn) {
+template <int LOGN>
+__global__ void __launch_bounds__(ColCfg<LOGN>::NT, 2) large_cols_kernel(const LargeArgs a) {
+  using Cfg = ColCfg<LOGN>;
+  using SP = SPlan<LOGN>;
+  constexpr int N = Cfg::N, T = Cfg::T, H = N / 2, G = N / kLRB;
   extern __shared__ __align__(16) float2 sm[];
-  const int N = 1 << logn, H = N / 2, G = N / kLRB;
-  float2* buf = sm;                 // [kLCB][N]
-  float2* tw = sm + kLCB * N;       // [N] stage-major twiddles
-  float* sy = reinterpret_cast<float*>(tw + N);  // [N] symbol in bit-reversed order: sy[pos] = symy[brev(pos)]
-  const int b = blockIdx.y, kx0 = blockIdx.x * kLCB;
-  const int F = (H + 1 - kx0) < kLCB ? (H + 1 - kx0) : kLCB;
+  float2* tws = sm + Cfg::C * SP::BUF;
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = sm + f * SP::BUF;
+  const int b = blockIdx.y, kx = blockIdx.x * Cfg::C + f;
+  const bool valid = kx <= H;  // idle transforms still take part in the warp-level syncs
   float2* spec = a.spec + (size_t)b * G * (H + 1) * kLRB;
-  load_stage_twiddles(tw, a.tw, logn);
-  for (int k = threadIdx.x; k < N; k += blockDim.x) sy[k] = a.symy[brev_n(k, logn)];
-  // column kx0 + c, row y = 8 g + yy sits at spec[(g (H + 1) + kx0 + c) 8 + yy]:
-  // kLCB x 8 consecutive complex values per row group
-  for (int t = threadIdx.x; t < kLCB * N; t += blockDim.x) {
-    const int yy = t & (kLRB - 1), c = (t >> 3) & (kLCB - 1), g = t >> 4;
-    if (c < F) buf[swz((c << logn) + g * kLRB + yy)] = spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy];
+  build_pass_twiddles<LOGN>(tws, a.tw);
+  // column kx, row y = 8 g + yy sits at spec[(g (H + 1) + kx) 8 + yy]
+  float2 z[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int y = t + m * T;
+    z[m] = valid ? spec[((size_t)(y >> 3) * (H + 1) + kx) * kLRB + (y & 7)] : make_float2(0.0f, 0.0f);
   }
-  __syncthreads();
-  block_fft_dif(buf, F, logn, tw);
-  for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
-    const int f = t >> logn, pos = t & (N - 1);
-    const int kx = kx0 + f;
-    const float m = (kx == 0 && pos == 0) ? 0.0f : __fdividef(a.inv_nn, a.symx[kx] + sy[pos]);  // pos 0 is ky 0
-    const float2 z = buf[swz(t)];
-    buf[swz(t)] = make_float2(z.x * m, z.y * m);
-  }
-  __syncthreads();
-  block_ifft_dit(buf, F, logn, tw);
-  for (int t = threadIdx.x; t < kLCB * N; t += blockDim.x) {
-    const int yy = t & (kLRB - 1), c = (t >> 3) & (kLCB - 1), g = t >> 4;
-    if (c < F) spec[((size_t)g * (H + 1) + kx0 + c) * kLRB + yy] = buf[swz((c << logn) + g * kLRB + yy)];
+  __syncthreads();  // twiddles
+  const TransformSync sync{1 + f, T};
+  fft_forward<LOGN>(z, buf, tws, t, sync);
+  // multiply by 1 / (N^2 symbol(kx, ky)); the zero mode is removed
+  const float sx = valid ? a.symx[kx] : 1.0f;
+#pragma unroll
+  for (int s = 0; s < SP::SL; ++s)
+#pragma unroll
+    for (int r = 0; r < SP::RL; ++r) {
+      const int ky = t + s * T + r * SP::NSL;
+      const float mlt = (kx == 0 && ky == 0) ? 0.0f : __fdividef(a.inv_nn, sx + __ldg(a.symy + ky));
+      float2& zz = z[s + SP::SL * r];
+      zz = make_float2(zz.x * mlt, zz.y * mlt);
+    }
+  fft_store_natural<LOGN>(buf, z, t);
+  sync();
+  fft_load<LOGN>(z, buf, t);
+  sync();
+  fft_inverse<LOGN>(z, buf, tws, t, sync);
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < SP::SL; ++s)
+#pragma unroll
+      for (int r = 0; r < SP::RL; ++r) {
+        const int y = t + s * T + r * SP::NSL;
+        spec[((size_t)(y >> 3) * (H + 1) + kx) * kLRB + (y & 7)] = z[s + SP::SL * r];
+      }
   }
 }
 
 // ---------------------------------------------------------------------------
-// rows_inv: kLRB rows per CTA from the column-major spectrum -> pressure rows
+// rows_inv: RG rows per CTA from the half spectra -> pressure rows
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) large_rows_inv_kernel(const LargeArgs a, int logn) {
+template <int LOGN>
+__global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_inv_kernel(const LargeArgs a) {
+  using Cfg = RowCfg<LOGN>;
+  using SP = SPlan<LOGN>;
+  constexpr int N = Cfg::N, T = Cfg::T, H = N / 2;
   extern __shared__ __align__(16) float2 sm[];
-  const int N = 1 << logn, H = N / 2, MSK = N - 1;
-  constexpr int F = kLRB / 2;
-  float2* buf = sm;                   // [F][N]
-  float2* tw = sm + F * N;            // [N] stage-major twiddles
-  const int b = blockIdx.y, g = blockIdx.x, y0 = g * kLRB;
-  const float4* blk = reinterpret_cast<const float4*>(a.spec + ((size_t)b * (N / kLRB) + g) * (H + 1) * kLRB);
-  load_stage_twiddles(tw, a.tw, logn);
-  // packed transforms Z_k = P_a[k] + i P_b[k], Hermitian mirror for k > N/2
-  for (int t = threadIdx.x; t < (H + 1) * F; t += blockDim.x) {
-    const int k = t >> 2, f = t & 3;
-    const float4 v = blk[t];  // (P_a[k], P_b[k])
-    buf[swz((f << logn) + brev_n(k & MSK, logn))] = make_float2(v.x - v.w, v.y + v.z);
-    if (k > 0 && k < H) buf[swz((f << logn) + brev_n(N - k, logn))] = make_float2(v.x + v.w, v.z - v.y);
+  float2* tws = sm + Cfg::F * SP::BUF;
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = sm + f * SP::BUF;
+  const int b = blockIdx.y, y0 = blockIdx.x * Cfg::RG;
+  const int ra = y0 + 2 * f;
+  build_pass_twiddles<LOGN>(tws, a.tw);
+  // packed transform Z_k = A_k + i B_k of rows ra, ra + 1; the half spectra
+  // hold k <= N/2, and Z_k = conj(A_{N-k}) + i conj(B_{N-k}) above
+  const float4* blk = reinterpret_cast<const float4*>(a.spec + ((size_t)b * (N / kLRB) + ra / kLRB) * (H + 1) * kLRB) +
+                      ((ra % kLRB) >> 1);
+  float2 z[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int k = t + m * T;
+    const bool lo = k <= H;
+    const float4 q = blk[(size_t)(lo ? k : N - k) * 4];
+    z[m] = lo ? make_float2(q.x - q.w, q.y + q.z) : make_float2(q.x + q.w, q.z - q.y);
   }
-  __syncthreads();
-  block_ifft_dit(buf, F, logn, tw);
+  __syncthreads();  // twiddles
+  fft_inverse<LOGN>(z, buf, tws, t, TransformSync{1 + f, T});
   float* p = a.pout + (size_t)b * N * N;
-  for (int t = threadIdx.x; t < F * N; t += blockDim.x) {
-    const int f = t >> logn, x = t & MSK;
-    const float2 z = buf[swz(t)];
-    p[(size_t)(y0 + 2 * f) * N + x] = z.x;
-    p[(size_t)(y0 + 2 * f + 1) * N + x] = z.y;
-  }
+#pragma unroll
+  for (int s = 0; s < SP::SL; ++s)
+#pragma unroll
+    for (int r = 0; r < SP::RL; ++r) {
+      const int x = t + s * T + r * SP::NSL;
+      const float2 zz = z[s + SP::SL * r];
+      p[(size_t)ra * N + x] = zz.x;
+      p[(size_t)(ra + 1) * N + x] = zz.y;
+    }
 }
 
 // u_{n+1} = w* - G2 p (or w* itself without a projection)

@@ -63,6 +63,23 @@ def test_streaming_step_matches_oracle(flow, forcing, dord):
     assert rel_l2(out10.double().cpu().numpy(), ref10) <= 1e-5
 
 
+@pytest.mark.parametrize("n", [32, 128, 256, 512])
+def test_streaming_step_matches_oracle_every_fft_size(n):
+    # each grid size has its own register-FFT instantiation (radices 16 x 2 at
+    # 32 up to 16 x 16 x 2 at 512; 1024 and 2048 below)
+    b = 2
+    cfg = fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=1e-3, path=2)
+    U0 = I.ic_batch("decaying", n, b, seed0=5)
+    _, out = run(cfg, U0, 1)
+    U32 = U0.astype(np.float32).astype(np.float64)
+    ref = np.stack([O.rk4_step(U32[k], problem(cfg)) for k in range(b)])
+    g = out.double().cpu().numpy()
+    assert rel_l2(g, ref) <= 1e-6
+    h = 2 * np.pi / n
+    for k in range(b):
+        assert np.max(np.abs(O.divergence(g[k], h, h))) <= 1e-5 * np.max(np.abs(g[k])) / h
+
+
 def test_streaming_equals_on_chip_at_256():
     n, b = 256, 2
     U0 = I.ic_batch("decaying", n, b, seed0=4)

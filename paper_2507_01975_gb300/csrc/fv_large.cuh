@@ -47,6 +47,9 @@ struct LargeArgs {
 
 constexpr int kLTX = 32, kLTY = 16;  // stage tile (cells)
 constexpr int kLRB = 8;              // rows per block of the half-spectrum layout
+constexpr int kFP = 16;              // FFT points per thread (a power of two, 4 .. 16)
+constexpr int kFPL = kFP == 16 ? 4 : kFP == 8 ? 3 : 2;  // log2 kFP
+constexpr int kFMB = kFP == 16 ? 2 : 3;                  // CTAs per SM the FFT kernels are built for
 
 __device__ __forceinline__ float2 c2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -57,11 +60,11 @@ __device__ __forceinline__ float2 c2negi(float2 a) { return make_float2(a.y, -a.
 __device__ __forceinline__ float2 c2conj(float2 a) { return make_float2(a.x, -a.y); }
 
 // ---- register-resident Stockham FFT -------------------------------------------
-// A transform of N = 2^LOGN points is done by T = N / 16 threads holding 16
-// points each. Pass p has radix R_p (16, 16, ..., then 2^(LOGN mod 4)) and
-// stride NS_p = R_0 ... R_{p-1}. Butterfly q of the pass takes the points
-// q + r N / R (r < R), which thread t = q mod T holds in registers s + (16/R) r
-// (s = q / T) when every thread holds the points t + m T (m < 16); it
+// A transform of N = 2^LOGN points is done by T = N / P threads holding P =
+// kFP points each. Pass p has radix R_p (P, P, ..., then the remaining power
+// of two) and stride NS_p = R_0 ... R_{p-1}. Butterfly q of the pass takes the
+// points q + r N / R (r < R), which thread t = q mod T holds in registers
+// s + (P/R) r (s = q / T) when every thread holds the points t + m T (m < P); it
 // multiplies point r by exp(-2 pi i (q mod NS) r / (NS R)), transforms the R
 // points and sends output r to position (q / NS) NS R + (q mod NS) + r NS
 // (Stockham autosort: after the last pass the order is natural). Between
@@ -69,15 +72,15 @@ __device__ __forceinline__ float2 c2conj(float2 a) { return make_float2(a.x, -a.
 // in the "points t + m T" pattern.
 template <int LOGN>
 struct SPlan {
-  static constexpr int N = 1 << LOGN, T = N / 16;
-  static constexpr int NP = (LOGN + 3) / 4;  // passes
-  static constexpr int radix(int p) { return p < LOGN / 4 ? 16 : (1 << (LOGN % 4)); }
+  static constexpr int N = 1 << LOGN, T = N / kFP;
+  static constexpr int NP = (LOGN + kFPL - 1) / kFPL;  // passes
+  static constexpr int radix(int p) { return p < LOGN / kFPL ? kFP : (1 << (LOGN % kFPL)); }
   static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
   // per-pass twiddle tables [R][NS] for passes 1 .. NP-1, stored one after another
   static constexpr int tw_off(int p) { return p <= 1 ? 0 : tw_off(p - 1) + ns(p - 1) * radix(p - 1); }
   static constexpr int TW = NP > 1 ? tw_off(NP) : 0;
   // after the last pass register s + SL r of thread t holds X[t + s T + r NSL]
-  static constexpr int RL = radix(NP - 1), SL = 16 / RL, NSL = ns(NP - 1);
+  static constexpr int RL = radix(NP - 1), SL = kFP / RL, NSL = ns(NP - 1);
   static constexpr int BUF = N + N / 16 + 4;  // padded buffer of one transform (float2)
 };
 
@@ -162,9 +165,9 @@ __device__ __forceinline__ void dft<16>(float2* v) {
 }
 
 template <int LOGN, int P>
-__device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2* tws, int t) {
+__device__ __forceinline__ void fft_pass(float2 (&v)[kFP], const float2* tws, int t) {
   using SP = SPlan<LOGN>;
-  constexpr int R = SP::radix(P), NS = SP::ns(P), S = 16 / R, T = SP::T;
+  constexpr int R = SP::radix(P), NS = SP::ns(P), S = kFP / R, T = SP::T;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     float2 w[R];
@@ -183,9 +186,9 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2* tws, int
 
 // outputs of pass P to their Stockham positions
 template <int LOGN, int P>
-__device__ __forceinline__ void fft_store(float2* buf, const float2 (&v)[16], int t) {
+__device__ __forceinline__ void fft_store(float2* buf, const float2 (&v)[kFP], int t) {
   using SP = SPlan<LOGN>;
-  constexpr int R = SP::radix(P), NS = SP::ns(P), S = 16 / R, T = SP::T;
+  constexpr int R = SP::radix(P), NS = SP::ns(P), S = kFP / R, T = SP::T;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int q = t + s * T;
@@ -196,14 +199,14 @@ __device__ __forceinline__ void fft_store(float2* buf, const float2 (&v)[16], in
 }
 
 template <int LOGN>
-__device__ __forceinline__ void fft_load(float2 (&v)[16], const float2* buf, int t) {
+__device__ __forceinline__ void fft_load(float2 (&v)[kFP], const float2* buf, int t) {
 #pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = buf[fpad(t + m * SPlan<LOGN>::T)];
+  for (int m = 0; m < kFP; ++m) v[m] = buf[fpad(t + m * SPlan<LOGN>::T)];
 }
 
 // the final registers (natural order X[t + s T + r NSL]) to the buffer
 template <int LOGN>
-__device__ __forceinline__ void fft_store_natural(float2* buf, const float2 (&v)[16], int t) {
+__device__ __forceinline__ void fft_store_natural(float2* buf, const float2 (&v)[kFP], int t) {
   using SP = SPlan<LOGN>;
 #pragma unroll
   for (int s = 0; s < SP::SL; ++s)
@@ -223,52 +226,51 @@ struct TransformSync {
   }
 };
 
+// passes P .. NP-1, each after an exchange of the previous pass's outputs
+template <int LOGN, int P>
+__device__ __forceinline__ void fft_passes_from(float2 (&v)[kFP], float2* buf, const float2* tws, int t,
+                                                TransformSync sync) {
+  if constexpr (P < SPlan<LOGN>::NP) {
+    fft_store<LOGN, P - 1>(buf, v, t);
+    sync();
+    fft_load<LOGN>(v, buf, t);
+    sync();
+    fft_pass<LOGN, P>(v, tws, t);
+    fft_passes_from<LOGN, P + 1>(v, buf, tws, t, sync);
+  }
+}
+
 // forward transform of the points t + m T in v; on return v[s + SL r] = X[t + s T + r NSL].
 // buf is the transform's shared buffer (free on entry and on return)
 template <int LOGN>
-__device__ __forceinline__ void fft_forward(float2 (&v)[16], float2* buf, const float2* tws, int t, TransformSync sync) {
-  using SP = SPlan<LOGN>;
+__device__ __forceinline__ void fft_forward(float2 (&v)[kFP], float2* buf, const float2* tws, int t, TransformSync sync) {
   fft_pass<LOGN, 0>(v, tws, t);
-  if constexpr (SP::NP > 1) {
-    fft_store<LOGN, 0>(buf, v, t);
-    sync();
-    fft_load<LOGN>(v, buf, t);
-    sync();
-    fft_pass<LOGN, 1>(v, tws, t);
-  }
-  if constexpr (SP::NP > 2) {
-    fft_store<LOGN, 1>(buf, v, t);
-    sync();
-    fft_load<LOGN>(v, buf, t);
-    sync();
-    fft_pass<LOGN, 2>(v, tws, t);
-  }
-  static_assert(SP::NP <= 3, "N <= 4096");
+  fft_passes_from<LOGN, 1>(v, buf, tws, t, sync);
 }
 
 // unnormalised inverse: conj(forward(conj(x)))
 template <int LOGN>
-__device__ __forceinline__ void fft_inverse(float2 (&v)[16], float2* buf, const float2* tws, int t, TransformSync sync) {
+__device__ __forceinline__ void fft_inverse(float2 (&v)[kFP], float2* buf, const float2* tws, int t, TransformSync sync) {
 #pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = c2conj(v[m]);
+  for (int m = 0; m < kFP; ++m) v[m] = c2conj(v[m]);
   fft_forward<LOGN>(v, buf, tws, t, sync);
 #pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = c2conj(v[m]);
+  for (int m = 0; m < kFP; ++m) v[m] = c2conj(v[m]);
 }
 
 // transforms per CTA of the row and column kernels: 512 threads at most
 template <int LOGN>
 struct RowCfg {
-  static constexpr int N = 1 << LOGN, T = N / 16;
+  static constexpr int N = 1 << LOGN, T = N / kFP;
   static constexpr int F = (512 / T) < (N / 2) ? (512 / T) : (N / 2);  // row transforms (2 real rows each)
   static constexpr int NT = F * T;
-  static constexpr int RG = 2 * F;  // rows per CTA, a multiple of kLRB
+  static constexpr int RG = 2 * F;  // rows per CTA
   static constexpr size_t SMEM = ((size_t)F * SPlan<LOGN>::BUF + SPlan<LOGN>::TW) * sizeof(float2);
-  static_assert(RG % kLRB == 0, "whole row groups");
+  static_assert(RG % kLRB == 0 || kLRB % RG == 0, "row groups split evenly over CTAs");
 };
 template <int LOGN>
 struct ColCfg {
-  static constexpr int N = 1 << LOGN, T = N / 16;
+  static constexpr int N = 1 << LOGN, T = N / kFP;
   static constexpr int C = (512 / T) < N ? (512 / T) : N;  // spectrum columns per CTA
   static constexpr int NT = C * T;
   static constexpr size_t SMEM = ((size_t)C * SPlan<LOGN>::BUF + SPlan<LOGN>::TW) * sizeof(float2);
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(256) large_stage_kernel(const LargeArgs a, int
 // rows_fwd: RG rows per CTA -> RG / 2 complex row transforms
 // ---------------------------------------------------------------------------
 template <int LOGN>
-__global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_fwd_kernel(const LargeArgs a) {
+__global__ void __launch_bounds__(RowCfg<LOGN>::NT, kFMB) large_rows_fwd_kernel(const LargeArgs a) {
   using Cfg = RowCfg<LOGN>;
   using SP = SPlan<LOGN>;
   constexpr int N = Cfg::N, T = Cfg::T, H = N / 2, MSK = N - 1;
@@ -397,9 +399,9 @@ __global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_fwd_kernel(con
   build_pass_twiddles<LOGN>(tws, a.tw);
   // divergence D2 w* of rows ra and rb as the real and imaginary parts
   const int ra = y0 + 2 * f, rb = ra + 1, rc = (rb + 1) & MSK;
-  float2 z[16];
+  float2 z[kFP];
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  for (int m = 0; m < kFP; ++m) {
     const int x = t + m * T, xe = (x + 1) & MSK;
     const float da = (u[(size_t)ra * N + xe] - u[(size_t)ra * N + x]) * a.idx +
                      (v[(size_t)rb * N + x] - v[(size_t)ra * N + x]) * a.idy;
@@ -412,15 +414,16 @@ __global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_fwd_kernel(con
   fft_store_natural<LOGN>(buf, z, t);
   __syncthreads();
   // unpack the two real rows of each transform: A_k = (Z_k + conj Z_{N-k}) / 2,
-  // B_k = (Z_k - conj Z_{N-k}) / (2i); one float4 (A_k, B_k) per (k, transform),
-  // each row group's block written contiguously
+  // B_k = (Z_k - conj Z_{N-k}) / (2i); one float4 (A_k, B_k) per (k, transform)
+  // at float4 index 4 k + (row % 8) / 2 of the row group's block
   for (int e = threadIdx.x; e < (H + 1) * Cfg::F; e += Cfg::NT) {
-    const int gi = e / ((H + 1) * 4), rem = e - gi * ((H + 1) * 4);
-    const int k = rem >> 2, ff = gi * 4 + (rem & 3);
+    const int k = e / Cfg::F, ff = e - k * Cfg::F;
+    const int row = y0 + 2 * ff;
     const float2* bf = sm + ff * SP::BUF;
     const float2 zk = bf[fpad(k & MSK)], zm = bf[fpad((N - k) & MSK)];
-    float4* blk = reinterpret_cast<float4*>(a.spec + ((size_t)b * (N / kLRB) + y0 / kLRB + gi) * (H + 1) * kLRB);
-    blk[rem] = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    float4* blk = reinterpret_cast<float4*>(a.spec + ((size_t)b * (N / kLRB) + row / kLRB) * (H + 1) * kLRB);
+    blk[4 * k + ((row % kLRB) >> 1)] =
+        make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
 }
 
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_fwd_kernel(con
 // cols: C spectrum columns per CTA: forward FFT along y, 1 / symbol, inverse
 // ---------------------------------------------------------------------------
 template <int LOGN>
-__global__ void __launch_bounds__(ColCfg<LOGN>::NT, 2) large_cols_kernel(const LargeArgs a) {
+__global__ void __launch_bounds__(ColCfg<LOGN>::NT, kFMB) large_cols_kernel(const LargeArgs a) {
   using Cfg = ColCfg<LOGN>;
   using SP = SPlan<LOGN>;
   constexpr int N = Cfg::N, T = Cfg::T, H = N / 2, G = N / kLRB;
@@ -441,9 +444,9 @@ __global__ void __launch_bounds__(ColCfg<LOGN>::NT, 2) large_cols_kernel(const L
   float2* spec = a.spec + (size_t)b * G * (H + 1) * kLRB;
   build_pass_twiddles<LOGN>(tws, a.tw);
   // column kx, row y = 8 g + yy sits at spec[(g (H + 1) + kx) 8 + yy]
-  float2 z[16];
+  float2 z[kFP];
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  for (int m = 0; m < kFP; ++m) {
     const int y = t + m * T;
     z[m] = valid ? spec[((size_t)(y >> 3) * (H + 1) + kx) * kLRB + (y & 7)] : make_float2(0.0f, 0.0f);
   }
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(ColCfg<LOGN>::NT, 2) large_cols_kernel(const L
 // rows_inv: RG rows per CTA from the half spectra -> pressure rows
 // ---------------------------------------------------------------------------
 template <int LOGN>
-__global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_inv_kernel(const LargeArgs a) {
+__global__ void __launch_bounds__(RowCfg<LOGN>::NT, kFMB) large_rows_inv_kernel(const LargeArgs a) {
   using Cfg = RowCfg<LOGN>;
   using SP = SPlan<LOGN>;
   constexpr int N = Cfg::N, T = Cfg::T, H = N / 2;
@@ -496,9 +499,9 @@ __global__ void __launch_bounds__(RowCfg<LOGN>::NT, 2) large_rows_inv_kernel(con
   // hold k <= N/2, and Z_k = conj(A_{N-k}) + i conj(B_{N-k}) above
   const float4* blk = reinterpret_cast<const float4*>(a.spec + ((size_t)b * (N / kLRB) + ra / kLRB) * (H + 1) * kLRB) +
                       ((ra % kLRB) >> 1);
-  float2 z[16];
+  float2 z[kFP];
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  for (int m = 0; m < kFP; ++m) {
     const int k = t + m * T;
     const bool lo = k <= H;
     const float4 q = blk[(size_t)(lo ? k : N - k) * 4];

@@ -87,7 +87,8 @@ cudaError_t large_step(fd_ctx* c, cudaStream_t st) {
   const int n = c->grid.nx, logn = c->logn, B = c->grid.batch;
   LargeArgs a = base_args(c);
   float* wsb[2] = {S.wsA, S.wsB};
-  const dim3 gst(n / kLTX, n / kLTY, B);
+  const int tx = n >= 64 ? 64 : 32;  // stage tile width
+  const dim3 gst(n / tx, n / kLTY, B);
   cudaError_t e = cudaSuccess;
   // Burgers has no pressure: the stages chain without projections
   const bool ns = c->grid.flow == FD_NAVIER_STOKES;
@@ -96,10 +97,17 @@ cudaError_t large_step(fd_ctx* c, cudaStream_t st) {
     a.x = s == 0 ? S.un : wsb[(s - 1) & 1];
     a.p = (s == 0 || !ns) ? nullptr : S.p;
     a.ws = wsb[s & 1];
-    if (c->opts.deriv_order == 4)
-      large_stage_kernel<4><<<gst, 256, 0, st>>>(a, logn);
-    else
-      large_stage_kernel<2><<<gst, 256, 0, st>>>(a, logn);
+    if (tx == 64) {
+      if (c->opts.deriv_order == 4)
+        large_stage_kernel<4, 64><<<gst, 256, 0, st>>>(a, logn);
+      else
+        large_stage_kernel<2, 64><<<gst, 256, 0, st>>>(a, logn);
+    } else {
+      if (c->opts.deriv_order == 4)
+        large_stage_kernel<4, 32><<<gst, 128, 0, st>>>(a, logn);
+      else
+        large_stage_kernel<2, 32><<<gst, 128, 0, st>>>(a, logn);
+    }
     e = cudaGetLastError();
     if (ns && e == cudaSuccess) e = dispatch_projection(logn, &a, B, st);
   }
@@ -107,8 +115,8 @@ cudaError_t large_step(fd_ctx* c, cudaStream_t st) {
     a.ws = wsb[1];
     a.uout = S.un;
     if (!ns) a.pout = nullptr;
-    const size_t cells = (size_t)B * n * n;
-    const int blocks = (int)((cells + 255) / 256 < 8192 ? (cells + 255) / 256 : 8192);
+    const size_t quads = (size_t)B * n * n / 4;
+    const int blocks = (int)((quads + 255) / 256 < 8192 ? (quads + 255) / 256 : 8192);
     large_final_kernel<<<blocks, 256, 0, st>>>(a, logn, B);
     e = cudaGetLastError();
   }

@@ -2,7 +2,7 @@
 // not fit on chip: the state streams through HBM once per kernel.
 //
 // One RK4 stage (App. B.5) is four kernels:
-//   stage     tiles of 32 x 16 cells with a 2-cell halo in shared memory:
+//   stage     tiles of 64 x 16 cells with a 2-cell halo in shared memory:
 //             w = x - G2 p (the projection of the previous stage, applied on
 //             the fly), the eight physics face operators (Sec. 3.4, App. B.2),
 //             the flux assembly and source terms, the RK combination with u_n
@@ -45,7 +45,7 @@ struct LargeArgs {
   const float* frc;   // [N]
 };
 
-constexpr int kLTX = 32, kLTY = 16;  // stage tile (cells)
+constexpr int kLTY = 16;             // stage tile rows (cells)
 constexpr int kLRB = 8;              // rows per block of the half-spectrum layout
 constexpr int kFP = 16;              // FFT points per thread (a power of two, 4 .. 16)
 constexpr int kFPL = kFP == 16 ? 4 : kFP == 8 ? 3 : 2;  // log2 kFP
@@ -277,106 +277,176 @@ struct ColCfg {
 };
 
 // ---------------------------------------------------------------------------
-// stage kernel: tile of kLTX x kLTY cells, 256 threads (two cells each)
+// stage kernel: tile of TX x kLTY cells, (TX / 4) x kLTY threads; each thread
+// owns a strip of 4 consecutive cells of one row and holds the 5 x 8 window
+// of u and v around it in registers, so every face value of the strip is
+// formed once from registers (16-byte shared loads, float4 global traffic)
 // ---------------------------------------------------------------------------
-template <int DORD>
-__global__ void __launch_bounds__(256) large_stage_kernel(const LargeArgs a, int logn) {
-  constexpr int WX = kLTX + 4, WY = kLTY + 4, PX = kLTX + 5, PY = kLTY + 5;
-  __shared__ float U[WY][WX];
-  __shared__ float V[WY][WX];
+template <int DORD, int TX>
+__global__ void __launch_bounds__(TX / 4 * kLTY, 4) large_stage_kernel(const LargeArgs a, int logn) {
+  constexpr int NT = TX / 4 * kLTY;
+  constexpr int WX = TX + 4, WY = kLTY + 4, PX = TX + 5, PY = kLTY + 5;
+  __shared__ __align__(16) float U[WY][WX];
+  __shared__ __align__(16) float V[WY][WX];
   __shared__ float P[PY][PX];
   const int N = 1 << logn, MSK = N - 1;
   const size_t NN = (size_t)N * N;
   const int b = blockIdx.z;
-  const int x0 = blockIdx.x * kLTX, y0 = blockIdx.y * kLTY;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * kLTY;
   const int tid = threadIdx.x;
   const float* xu = a.x + (size_t)b * 2 * NN;
   const float* xv = xu + NN;
+  // every global load of the tile is issued before the first use (registers),
+  // so the DRAM latency is paid once per CTA, not once per loop trip
+  constexpr int NW = (WX * WY + NT - 1) / NT, NPW = (PX * PY + NT - 1) / NT;
+  float ru[NW], rv[NW], rp[NPW];
+#pragma unroll
+  for (int q = 0; q < NW; ++q) {
+    const int k = tid + q * NT;
+    if (k < WX * WY) {
+      const int wy = k / WX, wx = k - wy * WX;
+      const size_t g = (size_t)((y0 - 2 + wy) & MSK) * N + ((x0 - 2 + wx) & MSK);
+      ru[q] = xu[g];
+      rv[q] = xv[g];
+    }
+  }
   if (a.p) {
     const float* pp = a.p + (size_t)b * NN;
-    for (int k = tid; k < PX * PY; k += 256) {
-      const int py = k / PX, px = k - py * PX;
-      P[py][px] = pp[(size_t)((y0 - 3 + py) & MSK) * N + ((x0 - 3 + px) & MSK)];
+#pragma unroll
+    for (int q = 0; q < NPW; ++q) {
+      const int k = tid + q * NT;
+      if (k < PX * PY) {
+        const int py = k / PX, px = k - py * PX;
+        rp[q] = pp[(size_t)((y0 - 3 + py) & MSK) * N + ((x0 - 3 + px) & MSK)];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NPW; ++q) {
+      const int k = tid + q * NT;
+      if (k < PX * PY) P[k / PX][k % PX] = rp[q];
     }
     __syncthreads();
   }
-  for (int k = tid; k < WX * WY; k += 256) {
-    const int wy = k / WX, wx = k - wy * WX;
-    const size_t g = (size_t)((y0 - 2 + wy) & MSK) * N + ((x0 - 2 + wx) & MSK);
-    float u = xu[g], v = xv[g];
-    if (a.p) {
-      // w = x - G2 p: u-face gradient p(i) - p(i - 1), v-face p(j) - p(j - 1)
-      u -= (P[wy + 1][wx + 1] - P[wy + 1][wx]) * a.idx;
-      v -= (P[wy + 1][wx + 1] - P[wy][wx + 1]) * a.idy;
+#pragma unroll
+  for (int q = 0; q < NW; ++q) {
+    const int k = tid + q * NT;
+    if (k < WX * WY) {
+      const int wy = k / WX, wx = k - wy * WX;
+      float u = ru[q], v = rv[q];
+      if (a.p) {
+        // w = x - G2 p: u-face gradient p(i) - p(i - 1), v-face p(j) - p(j - 1)
+        u -= (P[wy + 1][wx + 1] - P[wy + 1][wx]) * a.idx;
+        v -= (P[wy + 1][wx + 1] - P[wy][wx + 1]) * a.idy;
+      }
+      U[wy][wx] = u;
+      V[wy][wx] = v;
     }
-    U[wy][wx] = u;
-    V[wy][wx] = v;
   }
   __syncthreads();
+
+  // window: u[r][c] = U[ly - 2 + r][lx - 2 + c] around the strip's first cell
+  // (tile coordinates ly = ty + 2, lx = 4 sx + 2); the strip's cells are c = 2 .. 5
+  const int sx = tid % (TX / 4), ty = tid / (TX / 4);
+  float u[5][8], v[5][8];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&U[ty + r][4 * sx]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&U[ty + r][4 * sx + 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&V[ty + r][4 * sx]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&V[ty + r][4 * sx + 4]);
+    u[r][0] = a0.x; u[r][1] = a0.y; u[r][2] = a0.z; u[r][3] = a0.w;
+    u[r][4] = a1.x; u[r][5] = a1.y; u[r][6] = a1.z; u[r][7] = a1.w;
+    v[r][0] = b0.x; v[r][1] = b0.y; v[r][2] = b0.z; v[r][3] = b0.w;
+    v[r][4] = b1.x; v[r][5] = b1.y; v[r][6] = b1.z; v[r][7] = b1.w;
+  }
 
   constexpr float d0 = DORD == 4 ? 1.0f / 24.0f : 0.0f;
   constexpr float d1 = DORD == 4 ? -27.0f / 24.0f : -1.0f;
   constexpr float d2 = DORD == 4 ? 27.0f / 24.0f : 1.0f;
   constexpr float d3 = DORD == 4 ? -1.0f / 24.0f : 0.0f;
-  const float idx = a.idx, idy = a.idy;
-  // face values at tile-local coordinates (ly, lx) = (j - y0 + 2, i - x0 + 2)
-  auto Uc = [&](int ly, int lx) { return 0.5f * (U[ly][lx] + U[ly][lx + 1]); };
-  auto Gxc = [&](int ly, int lx) {
-    return (d0 * U[ly][lx - 1] + d1 * U[ly][lx] + d2 * U[ly][lx + 1] + d3 * U[ly][lx + 2]) * idx;
-  };
-  auto Uk = [&](int ly, int lx) { return 0.5f * (U[ly - 1][lx] + U[ly][lx]); };
-  auto Gyu = [&](int ly, int lx) {
-    return (d0 * U[ly - 2][lx] + d1 * U[ly - 1][lx] + d2 * U[ly][lx] + d3 * U[ly + 1][lx]) * idy;
-  };
-  auto Vk = [&](int ly, int lx) { return 0.5f * (V[ly][lx - 1] + V[ly][lx]); };
-  auto Gxv = [&](int ly, int lx) {
-    return (d0 * V[ly][lx - 2] + d1 * V[ly][lx - 1] + d2 * V[ly][lx] + d3 * V[ly][lx + 1]) * idx;
-  };
-  auto Vc = [&](int ly, int lx) { return 0.5f * (V[ly][lx] + V[ly + 1][lx]); };
-  auto Gyc = [&](int ly, int lx) {
-    return (d0 * V[ly - 1][lx] + d1 * V[ly][lx] + d2 * V[ly + 1][lx] + d3 * V[ly + 2][lx]) * idy;
-  };
-
-  const float ca = a.stage == 2 ? a.dt : 0.5f * a.dt;
-  const float c6 = a.dt / 6.0f;
+  const float idx = a.idx, idy = a.idy, nu = a.nu;
+  auto der = [&](float f0, float f1, float f2, float f3, float ih) { return (d0 * f0 + d1 * f1 + d2 * f2 + d3 * f3) * ih; };
+  // face values of the window row r = 2 (cell centres and corners of row j),
+  // c = column of the window: centres (j, c) carry u along x and v along y,
+  // corners (j, c) sit between rows j - 1 and j at u-face column c
+  float Uc2[6], Gxc[6];      // centres c = 1 .. 5 (index c)
+  float Gxcs[4];             // centres of row j - 1, c = 2 .. 5 (Burgers)
+  float UV0[7], Gxv[7];      // corners of row j, c = 2 .. 6
+  float UV1[6], Gyu0[6], Gyu1[6];  // corners of row j + 1 (UV1, Gyu1) and row j (Gyu0), c = 2 .. 5
+  float Vc0[6], Vc1[6], Gyc0[6], Gyc1[6];  // centres of rows j (0) and j - 1 (1), c = 1 .. 5
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int tx = tid & 31, ty = (tid >> 5) + 8 * h;
-    const int lx = tx + 2, ly = ty + 2;
-    const int i = x0 + tx, j = y0 + ty;
-    const float ukc = Uk(ly, lx) * Vk(ly, lx);
-    float tu = -(Uc(ly, lx) * Uc(ly, lx) - Uc(ly, lx - 1) * Uc(ly, lx - 1)) * idx -
-               (Uk(ly + 1, lx) * Vk(ly + 1, lx) - ukc) * idy +
-               a.nu * ((Gxc(ly, lx) - Gxc(ly, lx - 1)) * idx + (Gyu(ly + 1, lx) - Gyu(ly, lx)) * idy);
-    float tv = -(Uk(ly, lx + 1) * Vk(ly, lx + 1) - ukc) * idx -
-               (Vc(ly, lx) * Vc(ly, lx) - Vc(ly - 1, lx) * Vc(ly - 1, lx)) * idy +
-               a.nu * ((Gxv(ly, lx + 1) - Gxv(ly, lx)) * idx + (Gyc(ly, lx) - Gyc(ly - 1, lx)) * idy);
-    const float uc = U[ly][lx], vc = V[ly][lx];
+  for (int c = 1; c <= 5; ++c) {
+    const float uc = 0.5f * (u[2][c] + u[2][c + 1]);
+    Uc2[c] = uc * uc;
+    Gxc[c] = der(u[2][c - 1], u[2][c], u[2][c + 1], u[2][c + 2], idx);
+    const float vc0 = 0.5f * (v[2][c] + v[3][c]), vc1 = 0.5f * (v[1][c] + v[2][c]);
+    Vc0[c] = vc0 * vc0;
+    Vc1[c] = vc1 * vc1;
+    Gyc0[c] = der(v[1][c], v[2][c], v[3][c], v[4][c], idy);
+    Gyc1[c] = der(v[0][c], v[1][c], v[2][c], v[3][c], idy);
+  }
+#pragma unroll
+  for (int c = 2; c <= 6; ++c) {
+    UV0[c] = 0.5f * (u[1][c] + u[2][c]) * (0.5f * (v[2][c - 1] + v[2][c]));
+    Gxv[c] = der(v[2][c - 2], v[2][c - 1], v[2][c], v[2][c + 1], idx);
+  }
+#pragma unroll
+  for (int c = 2; c <= 5; ++c) {
+    UV1[c] = 0.5f * (u[2][c] + u[3][c]) * (0.5f * (v[3][c - 1] + v[3][c]));
+    Gyu0[c] = der(u[0][c], u[1][c], u[2][c], u[3][c], idy);
+    Gyu1[c] = der(u[1][c], u[2][c], u[3][c], u[4][c], idy);
+    Gxcs[c - 2] = der(u[1][c - 1], u[1][c], u[1][c + 1], u[1][c + 2], idx);
+  }
+
+  const int j = y0 + ty, i0 = x0 + 4 * sx;
+  const size_t g = (size_t)b * 2 * NN + (size_t)j * N + i0;
+  const float fx = a.forcing == 1 ? a.frc[j] : 0.0f;
+  float tu[4], tv[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = q + 2;
+    float du = -(Uc2[c] - Uc2[c - 1]) * idx - (UV1[c] - UV0[c]) * idy +
+               nu * ((Gxc[c] - Gxc[c - 1]) * idx + (Gyu1[c] - Gyu0[c]) * idy);
+    float dv = -(UV0[c + 1] - UV0[c]) * idx - (Vc0[c] - Vc1[c]) * idy +
+               nu * ((Gxv[c + 1] - Gxv[c]) * idx + (Gyc0[c] - Gyc1[c]) * idy);
+    const float uc = u[2][c], vc = v[2][c];
     if (a.flow == 0) {
-      const float dc = Gxc(ly, lx) + Gyc(ly, lx);
-      tu += uc * 0.5f * ((Gxc(ly, lx - 1) + Gyc(ly, lx - 1)) + dc);
-      tv += vc * 0.5f * ((Gxc(ly - 1, lx) + Gyc(ly - 1, lx)) + dc);
+      const float dc = Gxc[c] + Gyc0[c];
+      du += uc * 0.5f * ((Gxc[c - 1] + Gyc0[c - 1]) + dc);
+      dv += vc * 0.5f * ((Gxcs[q] + Gyc1[c]) + dc);
     }
     if (a.forcing == 1) {
-      tu += a.frc[j] - a.drag * uc;
-      tv -= a.drag * vc;
+      du += fx - a.drag * uc;
+      dv -= a.drag * vc;
     }
-    const size_t g = (size_t)b * 2 * NN + (size_t)j * N + i;
-    const float un_u = a.un[g], un_v = a.un[g + NN];
-    if (a.stage < 3) {
-      float au = tu, av = tv;
-      if (a.stage > 0) {
-        au = a.acc[g] + 2.0f * tu;
-        av = a.acc[g + NN] + 2.0f * tv;
-      }
-      a.acc[g] = au;
-      a.acc[g + NN] = av;
-      a.ws[g] = un_u + ca * tu;
-      a.ws[g + NN] = un_v + ca * tv;
-    } else {
-      a.ws[g] = un_u + c6 * (a.acc[g] + tu);
-      a.ws[g + NN] = un_v + c6 * (a.acc[g + NN] + tv);
+    tu[q] = du;
+    tv[q] = dv;
+  }
+  const float ca = a.stage == 2 ? a.dt : 0.5f * a.dt;
+  const float c6 = a.dt / 6.0f;
+  const float4 unu = *reinterpret_cast<const float4*>(a.un + g);
+  const float4 unv = *reinterpret_cast<const float4*>(a.un + g + NN);
+  float4* wsu = reinterpret_cast<float4*>(a.ws + g);
+  float4* wsv = reinterpret_cast<float4*>(a.ws + g + NN);
+  float4* acu = reinterpret_cast<float4*>(a.acc + g);
+  float4* acv = reinterpret_cast<float4*>(a.acc + g + NN);
+  if (a.stage < 3) {
+    float4 au = make_float4(tu[0], tu[1], tu[2], tu[3]), av = make_float4(tv[0], tv[1], tv[2], tv[3]);
+    if (a.stage > 0) {
+      const float4 pu = *acu, pv = *acv;
+      au = make_float4(pu.x + 2.0f * tu[0], pu.y + 2.0f * tu[1], pu.z + 2.0f * tu[2], pu.w + 2.0f * tu[3]);
+      av = make_float4(pv.x + 2.0f * tv[0], pv.y + 2.0f * tv[1], pv.z + 2.0f * tv[2], pv.w + 2.0f * tv[3]);
     }
+    *acu = au;
+    *acv = av;
+    *wsu = make_float4(unu.x + ca * tu[0], unu.y + ca * tu[1], unu.z + ca * tu[2], unu.w + ca * tu[3]);
+    *wsv = make_float4(unv.x + ca * tv[0], unv.y + ca * tv[1], unv.z + ca * tv[2], unv.w + ca * tv[3]);
+  } else {
+    const float4 pu = *acu, pv = *acv;
+    *wsu = make_float4(unu.x + c6 * (pu.x + tu[0]), unu.y + c6 * (pu.y + tu[1]), unu.z + c6 * (pu.z + tu[2]),
+                       unu.w + c6 * (pu.w + tu[3]));
+    *wsv = make_float4(unv.x + c6 * (pv.x + tv[0]), unv.y + c6 * (pv.y + tv[1]), unv.z + c6 * (pv.z + tv[2]),
+                       unv.w + c6 * (pv.w + tv[3]));
   }
 }
 
@@ -521,26 +591,34 @@ __global__ void __launch_bounds__(RowCfg<LOGN>::NT, kFMB) large_rows_inv_kernel(
     }
 }
 
-// u_{n+1} = w* - G2 p (or w* itself without a projection)
+// u_{n+1} = w* - G2 p (or w* itself without a projection); four consecutive
+// cells of a row per thread (float4 traffic)
 __global__ void __launch_bounds__(256) large_final_kernel(const LargeArgs a, int logn, int batch) {
   const int N = 1 << logn, MSK = N - 1;
-  const size_t NN = (size_t)N * N;
-  const size_t total = (size_t)batch * NN;
+  const size_t NN = (size_t)N * N, Q = NN / 4;
+  const size_t total = (size_t)batch * Q;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = e / NN, c = e - b * NN;
+    const size_t b = e / Q, c = (e - b * Q) * 4;
     const size_t g = b * 2 * NN + c;
+    const float4 wu = *reinterpret_cast<const float4*>(a.ws + g);
+    const float4 wv = *reinterpret_cast<const float4*>(a.ws + g + NN);
+    float4* ou = reinterpret_cast<float4*>(a.uout + g);
+    float4* ov = reinterpret_cast<float4*>(a.uout + g + NN);
     if (!a.pout) {  // no projection (Burgers)
-      a.uout[g] = a.ws[g];
-      a.uout[g + NN] = a.ws[g + NN];
+      *ou = wu;
+      *ov = wv;
       continue;
     }
     const int j = (int)(c >> logn), i = (int)(c & MSK);
     const float* p = a.pout + b * NN;
-    const float pc = p[c];
+    const float4 pc = *reinterpret_cast<const float4*>(p + c);
     const float pw = p[(size_t)j * N + ((i - 1) & MSK)];
-    const float ps = p[(size_t)((j - 1) & MSK) * N + i];
-    a.uout[g] = a.ws[g] - (pc - pw) * a.idx;
-    a.uout[g + NN] = a.ws[g + NN] - (pc - ps) * a.idy;
+    const float4 ps = *reinterpret_cast<const float4*>(p + (size_t)((j - 1) & MSK) * N + i);
+    const float ix = a.idx, iy = a.idy;
+    *ou = make_float4(wu.x - (pc.x - pw) * ix, wu.y - (pc.y - pc.x) * ix, wu.z - (pc.z - pc.y) * ix,
+                      wu.w - (pc.w - pc.z) * ix);
+    *ov = make_float4(wv.x - (pc.x - ps.x) * iy, wv.y - (pc.y - ps.y) * iy, wv.z - (pc.z - ps.z) * iy,
+                      wv.w - (pc.w - ps.w) * iy);
   }
 }
 

@@ -13,6 +13,24 @@ using namespace ldfv;
 
 namespace {
 
+// launch with programmatic stream serialisation (the kernel overlaps its
+// launch and prologue with the tail of the previous kernel in the stream)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // the three projection kernels of one stage, instantiated per grid size
 template <int LOGN>
 cudaError_t projection(const LargeArgs& a, int B, cudaStream_t st) {
@@ -20,10 +38,10 @@ cudaError_t projection(const LargeArgs& a, int B, cudaStream_t st) {
   using C = ColCfg<LOGN>;
   const dim3 grow(R::N / R::RG, B);
   const dim3 gcol((R::N / 2 + 1 + C::C - 1) / C::C, B);
-  large_rows_fwd_kernel<LOGN><<<grow, R::NT, R::SMEM, st>>>(a);
-  large_cols_kernel<LOGN><<<gcol, C::NT, C::SMEM, st>>>(a);
-  large_rows_inv_kernel<LOGN><<<grow, R::NT, R::SMEM, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(large_rows_fwd_kernel<LOGN>, grow, dim3(R::NT), R::SMEM, st, a);
+  if (e == cudaSuccess) e = launch_pdl(large_cols_kernel<LOGN>, gcol, dim3(C::NT), C::SMEM, st, a);
+  if (e == cudaSuccess) e = launch_pdl(large_rows_inv_kernel<LOGN>, grow, dim3(R::NT), R::SMEM, st, a);
+  return e;
 }
 
 template <int LOGN>
@@ -98,17 +116,12 @@ cudaError_t large_step(fd_ctx* c, cudaStream_t st) {
     a.p = (s == 0 || !ns) ? nullptr : S.p;
     a.ws = wsb[s & 1];
     if (tx == 64) {
-      if (c->opts.deriv_order == 4)
-        large_stage_kernel<4, 64><<<gst, 256, 0, st>>>(a, logn);
-      else
-        large_stage_kernel<2, 64><<<gst, 256, 0, st>>>(a, logn);
+      e = c->opts.deriv_order == 4 ? launch_pdl(large_stage_kernel<4, 64>, gst, dim3(256), 0, st, a, logn)
+                                   : launch_pdl(large_stage_kernel<2, 64>, gst, dim3(256), 0, st, a, logn);
     } else {
-      if (c->opts.deriv_order == 4)
-        large_stage_kernel<4, 32><<<gst, 128, 0, st>>>(a, logn);
-      else
-        large_stage_kernel<2, 32><<<gst, 128, 0, st>>>(a, logn);
+      e = c->opts.deriv_order == 4 ? launch_pdl(large_stage_kernel<4, 32>, gst, dim3(128), 0, st, a, logn)
+                                   : launch_pdl(large_stage_kernel<2, 32>, gst, dim3(128), 0, st, a, logn);
     }
-    e = cudaGetLastError();
     if (ns && e == cudaSuccess) e = dispatch_projection(logn, &a, B, st);
   }
   if (e == cudaSuccess) {
@@ -117,8 +130,7 @@ cudaError_t large_step(fd_ctx* c, cudaStream_t st) {
     if (!ns) a.pout = nullptr;
     const size_t quads = (size_t)B * n * n / 4;
     const int blocks = (int)((quads + 255) / 256 < 8192 ? (quads + 255) / 256 : 8192);
-    large_final_kernel<<<blocks, 256, 0, st>>>(a, logn, B);
-    e = cudaGetLastError();
+    e = launch_pdl(large_final_kernel, dim3(blocks), dim3(256), 0, st, a, logn, B);
   }
   return e;
 }

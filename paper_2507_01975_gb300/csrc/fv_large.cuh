@@ -51,6 +51,13 @@ constexpr int kFP = 16;              // FFT points per thread (a power of two, 4
 constexpr int kFPL = kFP == 16 ? 4 : kFP == 8 ? 3 : 2;  // log2 kFP
 constexpr int kFMB = kFP == 16 ? 2 : 3;                  // CTAs per SM the FFT kernels are built for
 
+// Programmatic dependent launch between the kernels of a step: a kernel lets
+// the next one in the stream start launching at once (its CTAs fill the SMs
+// this one's last wave frees and run their prologue), and the next one waits
+// for this one to complete, with its writes visible, before it touches them.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float2 c2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c2mul(float2 a, float2 b) {
@@ -296,6 +303,8 @@ __global__ void __launch_bounds__(TX / 4 * kLTY, 4) large_stage_kernel(const Lar
   const int tid = threadIdx.x;
   const float* xu = a.x + (size_t)b * 2 * NN;
   const float* xv = xu + NN;
+  pdl_trigger();
+  pdl_wait();
   // every global load of the tile is issued before the first use (registers),
   // so the DRAM latency is paid once per CTA, not once per loop trip
   constexpr int NW = (WX * WY + NT - 1) / NT, NPW = (PX * PY + NT - 1) / NT;
@@ -466,7 +475,9 @@ __global__ void __launch_bounds__(RowCfg<LOGN>::NT, kFMB) large_rows_fwd_kernel(
   const size_t NN = (size_t)N * N;
   const float* u = a.ws + (size_t)b * 2 * NN;
   const float* v = u + NN;
+  pdl_trigger();
   build_pass_twiddles<LOGN>(tws, a.tw);
+  pdl_wait();
   // divergence D2 w* of rows ra and rb as the real and imaginary parts
   const int ra = y0 + 2 * f, rb = ra + 1, rc = (rb + 1) & MSK;
   float2 z[kFP];
@@ -512,7 +523,9 @@ __global__ void __launch_bounds__(ColCfg<LOGN>::NT, kFMB) large_cols_kernel(cons
   const int b = blockIdx.y, kx = blockIdx.x * Cfg::C + f;
   const bool valid = kx <= H;  // idle transforms still take part in the warp-level syncs
   float2* spec = a.spec + (size_t)b * G * (H + 1) * kLRB;
+  pdl_trigger();
   build_pass_twiddles<LOGN>(tws, a.tw);
+  pdl_wait();
   // column kx, row y = 8 g + yy sits at spec[(g (H + 1) + kx) 8 + yy]
   float2 z[kFP];
 #pragma unroll
@@ -564,7 +577,9 @@ __global__ void __launch_bounds__(RowCfg<LOGN>::NT, kFMB) large_rows_inv_kernel(
   float2* buf = sm + f * SP::BUF;
   const int b = blockIdx.y, y0 = blockIdx.x * Cfg::RG;
   const int ra = y0 + 2 * f;
+  pdl_trigger();
   build_pass_twiddles<LOGN>(tws, a.tw);
+  pdl_wait();
   // packed transform Z_k = A_k + i B_k of rows ra, ra + 1; the half spectra
   // hold k <= N/2, and Z_k = conj(A_{N-k}) + i conj(B_{N-k}) above
   const float4* blk = reinterpret_cast<const float4*>(a.spec + ((size_t)b * (N / kLRB) + ra / kLRB) * (H + 1) * kLRB) +
@@ -597,6 +612,8 @@ __global__ void __launch_bounds__(256) large_final_kernel(const LargeArgs a, int
   const int N = 1 << logn, MSK = N - 1;
   const size_t NN = (size_t)N * N, Q = NN / 4;
   const size_t total = (size_t)batch * Q;
+  pdl_trigger();
+  pdl_wait();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t b = e / Q, c = (e - b * Q) * 4;
     const size_t g = b * 2 * NN + c;

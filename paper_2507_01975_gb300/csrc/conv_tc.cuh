@@ -247,6 +247,10 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tmem = *tslot;
+  // the prologue above overlaps the previous kernel's tail; the inputs and
+  // the outputs' previous readers belong to the previous kernel
+  pdl_wait();
+  pdl_trigger();
 
   if (warp == 0) {
     // ---------------- producer: weights once per part change, input tiles ----------
@@ -570,6 +574,8 @@ struct PackArgs {
 template <int LOGN>
 __global__ void __launch_bounds__(256) pack_input_kernel(const PackArgs a) {
   constexpr int N = 1 << LOGN;
+  pdl_wait();
+  pdl_trigger();
   const size_t total = (size_t)a.batch * N * N;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(p / (N * N));
@@ -613,6 +619,8 @@ __global__ void __launch_bounds__(256) conv_out2_kernel(const ConvOut2Args a) {
   for (int k = threadIdx.x; k < 2 * 64 * 9; k += blockDim.x) sw[k] = a.w[k];
   if (threadIdx.x < 2) sw[2 * 64 * 9 + threadIdx.x] = a.bias[threadIdx.x];
   __syncthreads();
+  pdl_wait();
+  pdl_trigger();
   const size_t total = (size_t)a.batch * N * N;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(p / (N * N));

@@ -145,6 +145,25 @@ struct fd_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel of the stream finishes (see pdl_wait / pdl_trigger).
+// Translation-unit local, like the kernel stubs it takes.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // shared helpers of the ABI translation units
 fd_status fd_set_error(fd_ctx* c, fd_status s, const char* fmt, ...);
 size_t fd_state_bytes(const fd_grid& g);

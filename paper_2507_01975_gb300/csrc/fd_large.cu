@@ -13,24 +13,6 @@ using namespace ldfv;
 
 namespace {
 
-// launch with programmatic stream serialisation (the kernel overlaps its
-// launch and prologue with the tail of the previous kernel in the stream)
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                       Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 // the three projection kernels of one stage, instantiated per grid size
 template <int LOGN>
 cudaError_t projection(const LargeArgs& a, int B, cudaStream_t st) {

@@ -64,8 +64,7 @@ cudaError_t run_trunk(fd_ctx* c, const float* const* hist, int cin, size_t pk_fi
   pa.cin = cin;
   const size_t pix = (size_t)B << (2 * LOGN);
   const int blocks = (int)((pix + 255) / 256 < (size_t)(4 * L.sms) ? (pix + 255) / 256 : (size_t)(4 * L.sms));
-  pack_input_kernel<LOGN><<<blocks, 256, 0, st>>>(pa);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(pack_input_kernel<LOGN>, dim3(blocks), dim3(256), 0, st, pa);
   if (e == cudaSuccess)
     e = launch_conv<LOGN, 64, 16>(L, L.act1, L.d_wpack + pk_first, b0, L.act0, B, 1, 0, 64, 1, st);
   __nv_bfloat16* bufs[2] = {L.act0, L.act1};
@@ -107,8 +106,7 @@ cudaError_t run_tc_net(fd_ctx* c, const float* const* hist, cudaStream_t st) {
   oa.batch = B;
   const size_t pix = (size_t)B << (2 * LOGN);
   const int blocks = (int)((pix + 255) / 256 < (size_t)(4 * L.sms) ? (pix + 255) / 256 : (size_t)(4 * L.sms));
-  conv_out2_kernel<LOGN><<<blocks, 256, 0, st>>>(oa);
-  return cudaGetLastError();
+  return launch_pdl(conv_out2_kernel<LOGN>, dim3(blocks), dim3(256), 0, st, oa);
 }
 
 // One learned time step s_in -> s_out. ptr_in / ptr_w: device pointer arrays
@@ -139,8 +137,8 @@ cudaError_t learned_step(fd_ctx* c, const float* s_in, float* s_out, const float
     if (e == cudaSuccess) {
       a.corr = L.corr;
       a.wout = s_out;
-      fv_correct_project_kernel<LOGN><<<B, LearnedCfg<LOGN>::NT, LearnedCfg<LOGN>::SMEM, st>>>(a);
-      e = cudaGetLastError();
+      e = launch_pdl(fv_correct_project_kernel<LOGN>, dim3(B), dim3(LearnedCfg<LOGN>::NT), LearnedCfg<LOGN>::SMEM,
+                     st, a);
     }
   }
   return e;

@@ -52,8 +52,7 @@ static cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, c
   a.spin_limit = kSpin;
   const int ntiles = batch * (Cfg::N / Cfg::TROWS) * parts;
   const int grid = ntiles < L.sms ? ntiles : L.sms;
-  conv3x3_tc_kernel<LOGN, CIN, COUT_TILE, NBUF><<<grid, Cfg::NT, Cfg::SMEM, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(conv3x3_tc_kernel<LOGN, CIN, COUT_TILE, NBUF>, dim3(grid), dim3(Cfg::NT), Cfg::SMEM, st, a);
 }
 
 // One learned RK stage: the banded flux kernel writes the unprojected stage
@@ -65,12 +64,13 @@ template <int LOGN>
 static cudaError_t launch_learned_stage(const LStageArgs& a_in, float* scratch, int batch, cudaStream_t st) {
   LStageArgs a = a_in;
   a.wout = scratch;
-  fv_learned_flux_kernel<LOGN, kBandRows>
-      <<<dim3((1 << LOGN) / kBandRows, batch), 256, BandCfg<LOGN, kBandRows>::SMEM, st>>>(a);
+  cudaError_t e = launch_pdl(fv_learned_flux_kernel<LOGN, kBandRows>, dim3((1 << LOGN) / kBandRows, batch), dim3(256),
+                             BandCfg<LOGN, kBandRows>::SMEM, st, a);
   LStageArgs p = a_in;
   p.w = scratch;
-  fv_project_kernel<LOGN><<<batch, LearnedCfg<LOGN>::NT, LearnedCfg<LOGN>::SMEM, st>>>(p);
-  return cudaGetLastError();
+  if (e == cudaSuccess)
+    e = launch_pdl(fv_project_kernel<LOGN>, dim3(batch), dim3(LearnedCfg<LOGN>::NT), LearnedCfg<LOGN>::SMEM, st, p);
+  return e;
 }
 
 template <int LOGN>

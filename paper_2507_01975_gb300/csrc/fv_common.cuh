@@ -19,6 +19,17 @@
 
 namespace ldfv {
 
+// Programmatic dependent launch. pdl_trigger lets the next kernel of the
+// stream (launched with programmatic stream serialisation) start launching:
+// its CTAs take the SMs this kernel's last wave frees and run their prologue.
+// pdl_wait blocks until the previous kernel has completed and its writes are
+// visible. Both are no-ops for kernels launched without that attribute.
+// A kernel whose prologue reads data written two or more launches back calls
+// pdl_wait before pdl_trigger, so that its successor's prologue runs only
+// after every earlier kernel has completed.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T>
 struct Cplx;
 template <>

@@ -51,13 +51,6 @@ constexpr int kFP = 16;              // FFT points per thread (a power of two, 4
 constexpr int kFPL = kFP == 16 ? 4 : kFP == 8 ? 3 : 2;  // log2 kFP
 constexpr int kFMB = kFP == 16 ? 2 : 3;                  // CTAs per SM the FFT kernels are built for
 
-// Programmatic dependent launch between the kernels of a step: a kernel lets
-// the next one in the stream start launching at once (its CTAs fill the SMs
-// this one's last wave frees and run their prologue), and the next one waits
-// for this one to complete, with its writes visible, before it touches them.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 __device__ __forceinline__ float2 c2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c2mul(float2 a, float2 b) {

@@ -279,6 +279,8 @@ __global__ void __launch_bounds__(256) fv_learned_flux_kernel(const LStageArgs a
   const int b = blockIdx.y, j0 = blockIdx.x * RB;
   const size_t NN = (size_t)N * N;
   const float* w = a.w + (size_t)b * 2 * NN;
+  pdl_wait();
+  pdl_trigger();
   for (int k = tid; k < 2 * TR * N; k += NT) {
     const int f = k / (TR * N), rem = k - f * TR * N;
     const int tr = rem >> LOGN, i = rem & MSK;
@@ -450,6 +452,8 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_project_kernel(con
   for (int k = tid; k < N / 2; k += NT) tw[k] = a.tw[k];
   for (int k = tid; k <= N / 2; k += NT) sx[k] = a.symx[k];
   for (int k = tid; k < N; k += NT) sy[k] = a.symy[k];
+  pdl_wait();
+  pdl_trigger();
   for (int c = tid; c < 2 * N * N; c += NT) wt[c] = src[c];
   __syncthreads();
   if (a.flow == 1) project_tile<LOGN, NT>(wt, scr, tw, sx, sy, a.idx, a.idy, a.inv_nn);  // Burgers: a copy
@@ -477,6 +481,8 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_correct_project_ke
   for (int k = tid; k < N / 2; k += NT) tw[k] = a.tw[k];
   for (int k = tid; k <= N / 2; k += NT) sx[k] = a.symx[k];
   for (int k = tid; k < N; k += NT) sy[k] = a.symy[k];
+  pdl_wait();
+  pdl_trigger();
   // per-component mean of the correction
   float s0 = 0.f, s1 = 0.f;
   for (int c = tid; c < N * N; c += NT) {

@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(256, 1) conv_wgrad_kernel(const WgradArgs a) {
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tmem = *tslot;
+  pdl_wait();
+  pdl_trigger();
 
   if (warp == 0) {
     // ---------------- producer: h rows with periodic halo, z rows -------------------
@@ -293,6 +295,8 @@ __global__ void __launch_bounds__(256) conv_wgrad_reduce_kernel(const WgradReduc
   constexpr int RPM = 128 / CIN, NMMA = (3 + RPM - 1) / RPM;
   const int nw = a.parts * O_TILE * a.cin * 9;
   const size_t cta_stride = (size_t)3 * NMMA * O_TILE * 128;
+  pdl_wait();
+  pdl_trigger();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nw + a.parts * O_TILE; e += gridDim.x * blockDim.x) {
     if (e < nw) {
       // e enumerates (part, o, a, dx, c) with c fastest: coalesced partial reads

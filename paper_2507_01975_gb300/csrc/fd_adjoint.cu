@@ -149,8 +149,8 @@ cudaError_t wgrad(fd_ctx* c, const __nv_bfloat16* h, const __nv_bfloat16* z, int
   a.cout_total = cout_total;
   a.err = L.d_err;
   a.spin_limit = kSpin;
-  conv_wgrad_kernel<LOGN, CIN, O_TILE><<<dim3(gx, parts), Cfg::NT, Cfg::SMEM, st>>>(a);
-  cudaError_t e = mark(cudaGetLastError(), "weight-gradient kernel");
+  cudaError_t e = mark(launch_pdl(conv_wgrad_kernel<LOGN, CIN, O_TILE>, dim3(gx, parts), dim3(Cfg::NT), Cfg::SMEM, st, a),
+                       "weight-gradient kernel");
   if (e != cudaSuccess) return e;
   WgradReduceArgs r;
   r.partial = A.partial;
@@ -162,9 +162,9 @@ cudaError_t wgrad(fd_ctx* c, const __nv_bfloat16* h, const __nv_bfloat16* z, int
   r.cin = cin_real;
   r.co_base = 0;
   const int total = parts * O_TILE * cin_real * 9 + parts * O_TILE;
-  conv_wgrad_reduce_kernel<CIN, O_TILE><<<(total + 255) / 256, 256, 0, st>>>(r);
   *launches += 2;
-  return mark(cudaGetLastError(), "weight-gradient reduction");
+  return mark(launch_pdl(conv_wgrad_reduce_kernel<CIN, O_TILE>, dim3((total + 255) / 256), dim3(256), 0, st, r),
+              "weight-gradient reduction");
 }
 
 // stencil network at stage state w, keeping every layer input and pre-activation
@@ -181,8 +181,7 @@ cudaError_t net_forward_saved(fd_ctx* c, int s, const float* w, cudaStream_t st,
   pa.cin = 2;
   const size_t pix = (size_t)B << (2 * LOGN);
   const int blocks = (int)((pix + 255) / 256 < (size_t)(4 * L.sms) ? (pix + 255) / 256 : (size_t)(4 * L.sms));
-  pack_input_kernel<LOGN><<<blocks, 256, 0, st>>>(pa);
-  cudaError_t e = mark(cudaGetLastError(), "input packing");
+  cudaError_t e = mark(launch_pdl(pack_input_kernel<LOGN>, dim3(blocks), dim3(256), 0, st, pa), "input packing");
   if (e == cudaSuccess)
     e = launch_conv<LOGN, 64, 16>(L, A.h[s][0], L.d_wpack + L.pk_stencil_first, L.d_raw + L.raw_off_sb[0], A.h[s][1],
                                   B, 1, 0, 64, 1, st, nullptr, A.z[s][0]);
@@ -242,8 +241,7 @@ cudaError_t net_backward(fd_ctx* c, int s, float* dparams, cudaStream_t st, int*
     oa.batch = B;
     const size_t pix = (size_t)B << (2 * LOGN);
     const int blocks = (int)((pix + 255) / 256 < (size_t)(4 * L.sms) ? (pix + 255) / 256 : (size_t)(4 * L.sms));
-    conv_out2_kernel<LOGN><<<blocks, 256, 0, st>>>(oa);
-    e = mark(cudaGetLastError(), "first-layer data gradient");
+    e = mark(launch_pdl(conv_out2_kernel<LOGN>, dim3(blocks), dim3(256), 0, st, oa), "first-layer data gradient");
     ++*launches;
   }
   return e;
@@ -270,8 +268,9 @@ cudaError_t combine(fd_ctx* c, const float* in0, const float* in1, float* lam, f
   a.tw = reinterpret_cast<const float2*>(b.tw);
   a.symx = reinterpret_cast<const float*>(b.symx);
   a.symy = reinterpret_cast<const float*>(b.symy);
-  fv_adjoint_combine_kernel<LOGN><<<c->grid.batch, LearnedCfg<LOGN>::NT, LearnedCfg<LOGN>::SMEM, st>>>(a);
-  return mark(cudaGetLastError(), "stage combination");
+  return mark(launch_pdl(fv_adjoint_combine_kernel<LOGN>, dim3(c->grid.batch), dim3(LearnedCfg<LOGN>::NT),
+                         LearnedCfg<LOGN>::SMEM, st, a),
+              "stage combination");
 }
 
 // u' = P(u + dt/6 (r1 + 2 r2 + 2 r3 + r4)), r_s = H(w_s), w_1 = u,
@@ -328,9 +327,9 @@ cudaError_t step_adjoint(fd_ctx* c, const float* u, const float* lam_out, float*
     // banded flux-block reverse: bands add their scatter into the zeroed w_bar
     e = mark(cudaMemsetAsync(A.wbar, 0, fd_state_bytes(c->grid), st), "stage adjoint");
     if (e != cudaSuccess) break;
-    fv_adjoint_band_kernel<LOGN, kAdjBandRows>
-        <<<dim3((1 << LOGN) / kAdjBandRows, B), 256, AdjBandCfg<LOGN, kAdjBandRows>::SMEM, st>>>(sa);
-    e = mark(cudaGetLastError(), "stage adjoint");
+    e = mark(launch_pdl(fv_adjoint_band_kernel<LOGN, kAdjBandRows>, dim3((1 << LOGN) / kAdjBandRows, B), dim3(256),
+                        AdjBandCfg<LOGN, kAdjBandRows>::SMEM, st, sa),
+             "stage adjoint");
     ++*launches;
     if (e == cudaSuccess && learned) e = net_backward<LOGN>(c, s, dparams, st, launches);
     if (e != cudaSuccess) break;

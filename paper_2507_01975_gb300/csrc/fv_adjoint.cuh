@@ -134,6 +134,8 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
   const int b = blockIdx.y, j0 = blockIdx.x * RB;
   const float* w = a.w + (size_t)b * 2 * NN;
   const float* tg = a.tbar + (size_t)b * 2 * NN;
+  pdl_wait();
+  pdl_trigger();
   auto W = [&](int fld, int jj, int ii) { return wt[(fld * WR + ((jj - j0 + 3) & MSK)) * N + (ii & MSK)]; };
   auto T = [&](int fld, int jj, int ii) { return tb[(fld * TRR + ((jj - j0 + 1) & MSK)) * N + (ii & MSK)]; };
   auto F = [&](int sl, int jj, int ii) { return inst[(sl * FR + ((jj - j0 + 1) & MSK)) * N + (ii & MSK)]; };
@@ -342,6 +344,8 @@ __global__ void __launch_bounds__(LearnedCfg<LOGN>::NT, 1) fv_adjoint_combine_ke
   for (int k = tid; k < N / 2; k += NT) tw[k] = a.tw[k];
   for (int k = tid; k <= N / 2; k += NT) sx[k] = a.symx[k];
   for (int k = tid; k < N; k += NT) sy[k] = a.symy[k];
+  pdl_wait();
+  pdl_trigger();
   for (size_t c = tid; c < 2 * NN; c += NT) wt[c] = a.in0[off + c] + (a.in1 ? a.in1[off + c] : 0.f);
   __syncthreads();
   if (a.project) project_tile<LOGN, NT>(wt, scr, tw, sx, sy, a.idx, a.idy, a.inv_nn);

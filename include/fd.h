@@ -295,9 +295,10 @@ fd_status fd_set_plan(fd_ctx* ctx, const fd_plan* plan);
  * buffer of two states, freed before return), keep the fastest, and
  * describe the candidates in report[0 .. min(max_report, *n_report) - 1]
  * with their measured us_per_step. Candidates: every cluster shape with the
- * whole batch on chip; for each shape whose resident count does not divide
- * the batch, the same shape on the full waves with the remainder on the
- * streaming kernels; the whole batch on the streaming kernels. Learned and
+ * whole batch on chip; for each shape, splits that keep on chip the full
+ * waves (when the resident count does not divide the batch) or 3/4, 1/2 or
+ * 1/4 of one wave, with the rest on the streaming kernels; the whole batch on
+ * the streaming kernels. Learned and
  * streaming-only contexts have one candidate, which is timed. Runs on
  * `stream` and synchronises it; report may be NULL when max_report is 0.
  * Errors: FD_EINVAL, FD_ENOMEM, FD_ECUDA (the previous plan is kept). */

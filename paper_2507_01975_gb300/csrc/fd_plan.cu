@@ -190,7 +190,19 @@ fd_status fd_autotune(fd_ctx* c, int32_t probe_steps, fd_plan* report, int32_t m
     for (size_t v = 0; v < c->variants.size(); ++v) {
       cands.push_back({(int)v, B, 0, 0});
       const int cap = c->capacity[v];
-      if (stream_ok(c) && cap > 0 && B > cap && B % cap != 0) cands.push_back({(int)v, B - B % cap, B % cap, 0});
+      if (!stream_ok(c) || cap <= 0) continue;
+      // on-chip shares: the full waves (remainder streaming), and 3/4, 1/2, 1/4
+      // of one wave (the streaming kernels take the SMs the clusters leave free)
+      std::vector<int> shares;
+      if (B > cap && B % cap != 0) shares.push_back(B - B % cap);
+      const int wave = B < cap ? B : cap;
+      for (int f = 3; f >= 1; --f) shares.push_back((wave * f + 2) / 4);
+      for (int on : shares) {
+        if (on <= 0 || on >= B) continue;
+        bool dup = false;
+        for (const Cand& x : cands) dup |= x.variant == (int)v && x.n_onchip == on;
+        if (!dup) cands.push_back({(int)v, on, B - on, 0});
+      }
     }
     if (stream_ok(c)) cands.push_back({0, 0, B, 0});
   } else {

@@ -75,7 +75,12 @@ struct FusedCfg {
   static constexpr size_t OFF_FRC = OFF_SY + align16(N * sizeof(T));
   static constexpr size_t OFF_ROW0 = OFF_FRC + align16(R * sizeof(T));  // u_n.v and acc.v of row 0
   static constexpr size_t OFF_TMEM = OFF_ROW0 + align16(2 * N * sizeof(T));
-  static constexpr size_t SMEM = OFF_TMEM + 16;
+  // N = 256: the FFTs are warp-level Stockham transforms with an exchange
+  // buffer per warp (WarpFFT256); smaller N keep the shuffle transforms
+  static constexpr bool STOCK = LOGN == 8;
+  static constexpr size_t OFF_XB = OFF_TMEM + 16;
+  static constexpr size_t XB_BYTES = STOCK ? (size_t)NW * WarpFFT256<T>::XB * sizeof(CT) : 0;
+  static constexpr size_t SMEM = OFF_XB + XB_BYTES;
   // forward-transpose and backward-transpose register staging per thread
   static constexpr int NFWD = (NC * N + NT - 1) / NT;
   static constexpr int NBWD = (R * (N / 2) + NT - 1) / NT;
@@ -215,6 +220,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   T* const unrow0 = reinterpret_cast<T*>(smem + Cfg::OFF_ROW0);  // u_n.v on local row 0
   T* const accrow0 = unrow0 + N;                                // acc.v on local row 0 (stage 2)
   uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::OFF_TMEM);
+  CT* const xbuf = reinterpret_cast<CT*>(smem + Cfg::OFF_XB);  // [NW][288] (N = 256 only)
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -361,7 +367,48 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
 
       if (ns) {
         // ---- D1: divergence, forward row FFTs, half spectra ---------------------
-        {
+        // half-spectrum rows hold kx in natural order for N = 256 (Stockham)
+        // and bit-reversed order otherwise; column 0 packs kx = 0 and N/2
+        if constexpr (Cfg::STOCK) {
+          using F2 = WarpFFT256<T>;
+          const T* fu = wt;
+          const T* fv = wt + HR * N;
+          CT* xb = xbuf + warp * F2::XB;
+          for (int pp = warp; pp < R / 2; pp += NW) {
+            const int ja = 2 * pp, hra = ja + 2, hrb = ja + 3;
+            CT z[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              const int x = lane + 32 * m;
+              const T da = (fu[hra * N + ((x + 1) & MSK)] - fu[hra * N + x]) * idx +
+                           (fv[(hra + 1) * N + x] - fv[hra * N + x]) * idy;
+              const T db = (fu[hrb * N + ((x + 1) & MSK)] - fu[hrb * N + x]) * idx +
+                           (fv[(hrb + 1) * N + x] - fv[hrb * N + x]) * idy;
+              z[m] = CT{da, db};
+            }
+            F2::forward(z, xb, tw, lane);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) xb[F2::pad(F2::out_index(lane, i))] = z[i];
+            __syncwarp();
+            // two real rows from one complex transform: A_k = (Z_k + conj Z_{N-k}) / 2,
+            // B_k = (Z_k - conj Z_{N-k}) / (2i); k = 0 packs the DC and Nyquist values
+            for (int k = lane; k < HALF; k += 32) {
+              const CT zk = xb[F2::pad(k)];
+              const CT zm = xb[F2::pad(k == 0 ? HALF : N - k)];
+              CT A, B;
+              if (k == 0) {
+                A = CT{zk.x, zm.x};
+                B = CT{zk.y, zm.y};
+              } else {
+                A = CT{(T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y)};
+                B = CT{(T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x)};
+              }
+              hs[ja * HSTR + k] = A;
+              hs[(ja + 1) * HSTR + k] = B;
+            }
+            __syncwarp();
+          }
+        } else {
           const T* fu = wt;
           const T* fv = wt + HR * N;
           for (int t0 = warp * TPW; t0 < R / 2; t0 += NW * TPW) {
@@ -430,6 +477,42 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
         }
         __syncthreads();
         // ---- D3: column FFTs, spectral multiply, inverse column FFTs -----------
+        if constexpr (Cfg::STOCK) {
+          using F2 = WarpFFT256<T>;
+          CT* xb = xbuf + warp * F2::XB;
+          for (int sl = warp; sl < NC; sl += NW) {
+            const int kx = rank * NC + sl;  // natural order; column 0 packs kx = 0 and N/2
+            CT z[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) z[m] = col[sl * Cfg::COLLEN + lane + 32 * m];
+            F2::forward(z, xb, tw, lane);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) xb[F2::pad(F2::out_index(lane, i))] = z[i];
+            __syncwarp();
+            // multiply by 1 / (N^2 L(kx, ky)) while gathering the inverse's input
+            // pattern; column 0: Z'[ky] = hp Z[ky] + hm conj(Z[-ky]) (kx = 0 in the
+            // real part, kx = N/2 in the imaginary part, both real and even in ky)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              const int ky = lane + 32 * m;
+              const CT za = xb[F2::pad(ky)];
+              if (kx != 0) {
+                const T ma = sdiv(inv_nn, sx[kx] + sy[ky]);
+                z[m] = CT{za.x * ma, za.y * ma};
+              } else {
+                const CT pa = xb[F2::pad((N - ky) & MSK)];
+                const T m0 = ky == 0 ? (T)0 : sdiv(inv_nn, sx[0] + sy[ky]);
+                const T mn = sdiv(inv_nn, sx[HALF] + sy[ky]);
+                const T hp = (T)0.5 * (m0 + mn), hm = (T)0.5 * (m0 - mn);
+                z[m] = CT{hp * za.x + hm * pa.x, hp * za.y - hm * pa.y};
+              }
+            }
+            __syncwarp();
+            F2::inverse(z, xb, tw, lane);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) col[sl * Cfg::COLLEN + F2::out_index(lane, i)] = z[i];
+          }
+        } else {
         for (int t0 = warp * TPW; t0 < NC; t0 += NW * TPW) {
           const int sl = t0 + lane / W;
           const bool act = sl < NC;
@@ -480,6 +563,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             for (int m = 0; m < E; ++m) col[slc * Cfg::COLLEN + q + W * m] = z[m];
           }
         }
+        }
         csync<CS>();
         // ---- D4: transpose columns -> rows (in place) ---------------------------
         {
@@ -505,6 +589,38 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
         }
         __syncthreads();
         // ---- D5: inverse row FFTs -> pressure rows -------------------------------
+        if constexpr (Cfg::STOCK) {
+          using F2 = WarpFFT256<T>;
+          CT* xb = xbuf + warp * F2::XB;
+          for (int pp = warp; pp < R / 2; pp += NW) {
+            const int ra = 2 * pp;
+            // packed transform Z_k = A_k + i B_k of rows ra, ra + 1 from the
+            // half spectra (natural order, column 0 packing DC and Nyquist)
+            CT z[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              const int k = lane + 32 * m;
+              if (k < HALF) {
+                const CT A = hs[ra * HSTR + k];
+                const CT B = hs[(ra + 1) * HSTR + k];
+                z[m] = (k == 0) ? CT{A.x, B.x} : CT{A.x - B.y, A.y + B.x};
+              } else {
+                const int kp = N - k;  // in (0, N/2]
+                const CT A = hs[ra * HSTR + (kp == HALF ? 0 : kp)];
+                const CT B = hs[(ra + 1) * HSTR + (kp == HALF ? 0 : kp)];
+                z[m] = (kp == HALF) ? CT{A.y, B.y} : CT{A.x + B.y, B.x - A.y};
+              }
+            }
+            __syncwarp();  // the pressure rows overwrite these half-spectrum rows
+            F2::inverse(z, xb, tw, lane);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int x = F2::out_index(lane, i);
+              pr[ra * (2 * HSTR) + x] = z[i].x;
+              pr[(ra + 1) * (2 * HSTR) + x] = z[i].y;
+            }
+          }
+        } else {
         for (int t0 = warp * TPW; t0 < R / 2; t0 += NW * TPW) {
           const int jp = t0 + lane / W;
           const bool act = jp < R / 2;
@@ -536,6 +652,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
               pr[(ra + 1) * (2 * HSTR) + x] = z[m].y;
             }
           }
+        }
         }
         // pressure of the row below the first owned row lives in the previous CTA
         csync<CS>();

@@ -258,11 +258,14 @@ __device__ __forceinline__ void fft_inverse(float2 (&v)[kFP], float2* buf, const
   for (int m = 0; m < kFP; ++m) v[m] = c2conj(v[m]);
 }
 
-// transforms per CTA of the row and column kernels: 512 threads at most
+// transforms per CTA of the row and column kernels: four (one row group of the
+// spectrum layout; 512 threads at N = 2048), so that small grids still spread
+// over many CTAs; at least one whole warp (the transform syncs are warp-wide
+// below 64 threads per transform)
 template <int LOGN>
 struct RowCfg {
   static constexpr int N = 1 << LOGN, T = N / kFP;
-  static constexpr int F = (512 / T) < (N / 2) ? (512 / T) : (N / 2);  // row transforms (2 real rows each)
+  static constexpr int F = T >= 8 ? 4 : 32 / T;  // row transforms (2 real rows each); whole warps
   static constexpr int NT = F * T;
   static constexpr int RG = 2 * F;  // rows per CTA
   static constexpr size_t SMEM = ((size_t)F * SPlan<LOGN>::BUF + SPlan<LOGN>::TW) * sizeof(float2);
@@ -271,7 +274,7 @@ struct RowCfg {
 template <int LOGN>
 struct ColCfg {
   static constexpr int N = 1 << LOGN, T = N / kFP;
-  static constexpr int C = (512 / T) < N ? (512 / T) : N;  // spectrum columns per CTA
+  static constexpr int C = T >= 8 ? 4 : 32 / T;  // spectrum columns per CTA; whole warps
   static constexpr int NT = C * T;
   static constexpr size_t SMEM = ((size_t)C * SPlan<LOGN>::BUF + SPlan<LOGN>::TW) * sizeof(float2);
 };

@@ -174,6 +174,72 @@ struct WarpFFT {
 };
 
 
+// Tendency H(w) of the flux block (App. B.2: advection, dissipation, forcing,
+// and the Burgers correction) for a strip of 4 consecutive cells of one row,
+// from the 5 x 8 window u[r][c] = w_u(row - 2 + r, col - 2 + c) (same for v)
+// around the strip's first cell (row, col); the strip's cells are c = 2 .. 5.
+// Every face value of the strip is formed once: linear interpolation
+// [0, 1/2, 1/2, 0] and the derivative [1, -27, 27, -1] / 24h (DORD = 4) or
+// [0, -1, 1, 0] / h (DORD = 2).
+template <typename T, int DORD>
+__device__ __forceinline__ void strip_tendency(const T (&u)[5][8], const T (&v)[5][8], T idx, T idy, T nu,
+                                               bool burgers, bool forced, T fx, T drag, T (&tu)[4], T (&tv)[4]) {
+  constexpr T d0 = DORD == 4 ? (T)(1.0 / 24.0) : (T)0;
+  constexpr T d1 = DORD == 4 ? (T)(-27.0 / 24.0) : (T)-1;
+  constexpr T d2 = DORD == 4 ? (T)(27.0 / 24.0) : (T)1;
+  constexpr T d3 = DORD == 4 ? (T)(-1.0 / 24.0) : (T)0;
+  auto der = [&](T f0, T f1, T f2, T f3, T ih) { return (d0 * f0 + d1 * f1 + d2 * f2 + d3 * f3) * ih; };
+  const T h = (T)0.5;
+  // cell centres (row, c) carry u along x and v along y; corners (row, c) sit
+  // between rows row - 1 and row at u-face column c
+  T Uc2[6], Gxc[6], Vc0[6], Vc1[6], Gyc0[6], Gyc1[6];  // centres c = 1 .. 5 (rows j, j - 1 for v)
+  T UV0[7], Gxv[7];                                    // corners of row j, c = 2 .. 6
+  T UV1[6], Gyu0[6], Gyu1[6], Gxcs[4];                 // corners of rows j + 1, j; centres of row j - 1
+#pragma unroll
+  for (int c = 1; c <= 5; ++c) {
+    const T uc = h * (u[2][c] + u[2][c + 1]);
+    Uc2[c] = uc * uc;
+    Gxc[c] = der(u[2][c - 1], u[2][c], u[2][c + 1], u[2][c + 2], idx);
+    const T vc0 = h * (v[2][c] + v[3][c]), vc1 = h * (v[1][c] + v[2][c]);
+    Vc0[c] = vc0 * vc0;
+    Vc1[c] = vc1 * vc1;
+    Gyc0[c] = der(v[1][c], v[2][c], v[3][c], v[4][c], idy);
+    Gyc1[c] = der(v[0][c], v[1][c], v[2][c], v[3][c], idy);
+  }
+#pragma unroll
+  for (int c = 2; c <= 6; ++c) {
+    UV0[c] = h * (u[1][c] + u[2][c]) * (h * (v[2][c - 1] + v[2][c]));
+    Gxv[c] = der(v[2][c - 2], v[2][c - 1], v[2][c], v[2][c + 1], idx);
+  }
+#pragma unroll
+  for (int c = 2; c <= 5; ++c) {
+    UV1[c] = h * (u[2][c] + u[3][c]) * (h * (v[3][c - 1] + v[3][c]));
+    Gyu0[c] = der(u[0][c], u[1][c], u[2][c], u[3][c], idy);
+    Gyu1[c] = der(u[1][c], u[2][c], u[3][c], u[4][c], idy);
+    Gxcs[c - 2] = der(u[1][c - 1], u[1][c], u[1][c + 1], u[1][c + 2], idx);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = q + 2;
+    T du = -(Uc2[c] - Uc2[c - 1]) * idx - (UV1[c] - UV0[c]) * idy +
+           nu * ((Gxc[c] - Gxc[c - 1]) * idx + (Gyu1[c] - Gyu0[c]) * idy);
+    T dv = -(UV0[c + 1] - UV0[c]) * idx - (Vc0[c] - Vc1[c]) * idy +
+           nu * ((Gxv[c + 1] - Gxv[c]) * idx + (Gyc0[c] - Gyc1[c]) * idy);
+    const T uc = u[2][c], vc = v[2][c];
+    if (burgers) {
+      const T dc = Gxc[c] + Gyc0[c];
+      du += uc * h * ((Gxc[c - 1] + Gyc0[c - 1]) + dc);
+      dv += vc * h * ((Gxcs[q] + Gyc1[c]) + dc);
+    }
+    if (forced) {
+      du += fx - drag * uc;
+      dv -= drag * vc;
+    }
+    tu[q] = du;
+    tv[q] = dv;
+  }
+}
+
 // 256-point transforms, one per warp, 8 points per lane: Stockham autosort
 // with radices 8, 8, 4. On entry lane t holds the points t + 32 m (m < 8); on
 // return register i holds X[t + 32 (i & 1) + 64 (i >> 1)] (natural order).

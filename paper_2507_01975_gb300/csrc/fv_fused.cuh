@@ -77,7 +77,10 @@ struct FusedCfg {
   static constexpr size_t OFF_TMEM = OFF_ROW0 + align16(2 * N * sizeof(T));
   // N = 256: the FFTs are warp-level Stockham transforms with an exchange
   // buffer per warp (WarpFFT256); smaller N keep the shuffle transforms
-  static constexpr bool STOCK = LOGN == 8;
+  static constexpr bool STOCK = LOGN == 8 && sizeof(T) == 4;
+  // N = 256: the tendency phase works on strips of 4 cells (register window,
+  // strip_tendency); GC row groups of N/4 strips, RTC bands per CTA
+  static constexpr int GC = NT / (N / 4), RTC = R / GC;
   static constexpr size_t OFF_XB = OFF_TMEM + 16;
   static constexpr size_t XB_BYTES = STOCK ? (size_t)NW * WarpFFT256<T>::XB * sizeof(CT) : 0;
   static constexpr size_t SMEM = OFF_XB + XB_BYTES;
@@ -266,12 +269,28 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   const T dt = (T)a.dt, idx = (T)a.idx, idy = (T)a.idy, inv_nn = (T)a.inv_nn;
   const bool extra = ns && (grp == Cfg::G - 1);  // recompute v' on the next CTA's first row
 
-  // u_n of the owned cells into TMEM
+  // u_n of the owned cells into TMEM (N = 256: the cells of the thread's strips)
+  const int sx4 = 4 * (tid % (N / 4)), gc = tid / (N / 4);
+  auto store_un = [&]() {
+    if constexpr (Cfg::STOCK) {
+      // the strips' cells were last written by other threads (gradient phase)
+      __syncthreads();
 #pragma unroll
-  for (int r = 0; r < RT; ++r) {
-    const int hr = r * Cfg::G + grp + 2;
-    Slot::store(tbase + r * Cfg::SLOT, wt[hr * N + ci], wt[(HR + hr) * N + ci], (T)0, (T)0);
-  }
+      for (int r = 0; r < Cfg::RTC; ++r) {
+        const int hr = r * Cfg::GC + gc + 2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          Slot::store(tbase + (4 * r + q) * Cfg::SLOT, wt[hr * N + sx4 + q], wt[(HR + hr) * N + sx4 + q], (T)0, (T)0);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RT; ++r) {
+        const int hr = r * Cfg::G + grp + 2;
+        Slot::store(tbase + r * Cfg::SLOT, wt[hr * N + ci], wt[(HR + hr) * N + ci], (T)0, (T)0);
+      }
+    }
+  };
+  store_un();
   if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
   tmem_wait_st();
 
@@ -305,6 +324,103 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
       // one per row group) by all threads in lockstep. Band r reads rows
       // r G - 2 .. r G + G + 1, so once every thread has finished band r, band
       // r - 1 is never read again and its new values are written in place.
+      if constexpr (Cfg::STOCK) {
+        // strips: thread (gc, strip) owns rows r GC + gc at columns sx4 .. sx4 + 3;
+        // bands of GC rows in lockstep, band r - 1 written after band r (as below)
+        constexpr int GC = Cfg::GC, RTC = Cfg::RTC;
+        const T ca = stage == 2 ? dt : (T)0.5 * dt;
+        const T c6 = dt / (T)6;
+        const bool xtra = ns && (gc == GC - 1);  // v' on the next CTA's first row
+        auto window = [&](int hr, T (&u)[5][8], T (&v)[5][8]) {
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr) {
+            const T* ru = wt + (hr - 2 + rr) * N;
+            const T* rv = wt + (HR + hr - 2 + rr) * N;
+            const float2 lu = *reinterpret_cast<const float2*>(ru + ((sx4 - 2) & MSK));
+            const float4 mu = *reinterpret_cast<const float4*>(ru + sx4);
+            const float2 gu = *reinterpret_cast<const float2*>(ru + ((sx4 + 4) & MSK));
+            const float2 lv = *reinterpret_cast<const float2*>(rv + ((sx4 - 2) & MSK));
+            const float4 mv = *reinterpret_cast<const float4*>(rv + sx4);
+            const float2 gv = *reinterpret_cast<const float2*>(rv + ((sx4 + 4) & MSK));
+            u[rr][0] = lu.x; u[rr][1] = lu.y; u[rr][2] = mu.x; u[rr][3] = mu.y;
+            u[rr][4] = mu.z; u[rr][5] = mu.w; u[rr][6] = gu.x; u[rr][7] = gu.y;
+            v[rr][0] = lv.x; v[rr][1] = lv.y; v[rr][2] = mv.x; v[rr][3] = mv.y;
+            v[rr][4] = mv.z; v[rr][5] = mv.w; v[rr][6] = gv.x; v[rr][7] = gv.y;
+          }
+        };
+        T pu[4], pv[4], wve[4];
+#pragma unroll
+        for (int r = 0; r < RTC; ++r) {
+          const int jj = r * GC + gc, hr = jj + 2;
+          uint32_t tr[4][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) tmem_ld4(tbase + (4 * r + q) * Cfg::SLOT, tr[q]);
+          T u[5][8], v[5][8];
+          window(hr, u, v);
+          T tu[4], tv[4];
+          strip_tendency<T, DORD>(u, v, idx, idy, tend.nu, tend.burgers, tend.forced, frc[jj], tend.drag, tu, tv);
+          tmem_wait_ld();
+          T nu4[4], nv4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const T unu = __uint_as_float(tr[q][0]), unv = __uint_as_float(tr[q][1]);
+            T au = __uint_as_float(tr[q][2]), av = __uint_as_float(tr[q][3]);
+            if (stage == 0) {
+              au = tu[q];
+              av = tv[q];
+            } else if (stage < 3) {
+              au += (T)2 * tu[q];
+              av += (T)2 * tv[q];
+            } else {
+              au += tu[q];
+              av += tv[q];
+            }
+            if (stage < 3) {
+              Slot::store(tbase + (4 * r + q) * Cfg::SLOT, unu, unv, au, av);
+              nu4[q] = unu + ca * tu[q];
+              nv4[q] = unv + ca * tv[q];
+              if (stage == 2 && jj == 0) accrow0[sx4 + q] = av;
+            } else {
+              nu4[q] = unu + c6 * au;
+              nv4[q] = unv + c6 * av;
+            }
+          }
+          if (r == RTC - 1 && xtra) {
+            // v' on the next CTA's first row, from rows R-2 .. R+2
+            const T* nrow = remote<CS>(unrow0, next);
+            T ue[5][8], ve[5][8];
+            window(R + 2, ue, ve);
+            T eu[4], ev[4];
+            strip_tendency<T, DORD>(ue, ve, idx, idy, tend.nu, tend.burgers, tend.forced, (T)0, tend.drag, eu, ev);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const T unv0 = nrow[sx4 + q];
+              wve[q] = stage < 3 ? unv0 + ca * ev[q] : unv0 + c6 * (nrow[N + sx4 + q] + ev[q]);
+            }
+          }
+          __syncthreads();
+          if (r == 1) cluster_wait<CS>();
+          if (r > 0) {
+            const int hp = (r - 1) * GC + gc + 2;
+            *reinterpret_cast<float4*>(wt + hp * N + sx4) = make_float4(pu[0], pu[1], pu[2], pu[3]);
+            *reinterpret_cast<float4*>(wt + (HR + hp) * N + sx4) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            pu[q] = nu4[q];
+            pv[q] = nv4[q];
+          }
+        }
+        tmem_wait_st();
+        if constexpr (RTC == 1) cluster_wait<CS>();
+        __syncthreads();
+        const int hl = (RTC - 1) * GC + gc + 2;
+        *reinterpret_cast<float4*>(wt + hl * N + sx4) = make_float4(pu[0], pu[1], pu[2], pu[3]);
+        *reinterpret_cast<float4*>(wt + (HR + hl) * N + sx4) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        if (xtra)
+          *reinterpret_cast<float4*>(wt + (HR + R + 2) * N + sx4) = make_float4(wve[0], wve[1], wve[2], wve[3]);
+        __syncthreads();
+      } else
       {
         const T ca = stage == 2 ? dt : (T)0.5 * dt;
         const T c6 = dt / (T)6;
@@ -673,11 +789,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
     }
 
     // ---- end of the time step: u_{n+1} becomes u_n -------------------------------
-#pragma unroll
-    for (int r = 0; r < RT; ++r) {
-      const int hr = r * Cfg::G + grp + 2;
-      Slot::store(tbase + r * Cfg::SLOT, wt[hr * N + ci], wt[(HR + hr) * N + ci], (T)0, (T)0);
-    }
+    store_un();
     if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
     tmem_wait_st();
     if (a.save_every > 0 && a.traj != nullptr && (step % a.save_every) == 0) {

@@ -365,68 +365,11 @@ __global__ void __launch_bounds__(TX / 4 * kLTY, 4) large_stage_kernel(const Lar
     v[r][4] = b1.x; v[r][5] = b1.y; v[r][6] = b1.z; v[r][7] = b1.w;
   }
 
-  constexpr float d0 = DORD == 4 ? 1.0f / 24.0f : 0.0f;
-  constexpr float d1 = DORD == 4 ? -27.0f / 24.0f : -1.0f;
-  constexpr float d2 = DORD == 4 ? 27.0f / 24.0f : 1.0f;
-  constexpr float d3 = DORD == 4 ? -1.0f / 24.0f : 0.0f;
-  const float idx = a.idx, idy = a.idy, nu = a.nu;
-  auto der = [&](float f0, float f1, float f2, float f3, float ih) { return (d0 * f0 + d1 * f1 + d2 * f2 + d3 * f3) * ih; };
-  // face values of the window row r = 2 (cell centres and corners of row j),
-  // c = column of the window: centres (j, c) carry u along x and v along y,
-  // corners (j, c) sit between rows j - 1 and j at u-face column c
-  float Uc2[6], Gxc[6];      // centres c = 1 .. 5 (index c)
-  float Gxcs[4];             // centres of row j - 1, c = 2 .. 5 (Burgers)
-  float UV0[7], Gxv[7];      // corners of row j, c = 2 .. 6
-  float UV1[6], Gyu0[6], Gyu1[6];  // corners of row j + 1 (UV1, Gyu1) and row j (Gyu0), c = 2 .. 5
-  float Vc0[6], Vc1[6], Gyc0[6], Gyc1[6];  // centres of rows j (0) and j - 1 (1), c = 1 .. 5
-#pragma unroll
-  for (int c = 1; c <= 5; ++c) {
-    const float uc = 0.5f * (u[2][c] + u[2][c + 1]);
-    Uc2[c] = uc * uc;
-    Gxc[c] = der(u[2][c - 1], u[2][c], u[2][c + 1], u[2][c + 2], idx);
-    const float vc0 = 0.5f * (v[2][c] + v[3][c]), vc1 = 0.5f * (v[1][c] + v[2][c]);
-    Vc0[c] = vc0 * vc0;
-    Vc1[c] = vc1 * vc1;
-    Gyc0[c] = der(v[1][c], v[2][c], v[3][c], v[4][c], idy);
-    Gyc1[c] = der(v[0][c], v[1][c], v[2][c], v[3][c], idy);
-  }
-#pragma unroll
-  for (int c = 2; c <= 6; ++c) {
-    UV0[c] = 0.5f * (u[1][c] + u[2][c]) * (0.5f * (v[2][c - 1] + v[2][c]));
-    Gxv[c] = der(v[2][c - 2], v[2][c - 1], v[2][c], v[2][c + 1], idx);
-  }
-#pragma unroll
-  for (int c = 2; c <= 5; ++c) {
-    UV1[c] = 0.5f * (u[2][c] + u[3][c]) * (0.5f * (v[3][c - 1] + v[3][c]));
-    Gyu0[c] = der(u[0][c], u[1][c], u[2][c], u[3][c], idy);
-    Gyu1[c] = der(u[1][c], u[2][c], u[3][c], u[4][c], idy);
-    Gxcs[c - 2] = der(u[1][c - 1], u[1][c], u[1][c + 1], u[1][c + 2], idx);
-  }
-
   const int j = y0 + ty, i0 = x0 + 4 * sx;
   const size_t g = (size_t)b * 2 * NN + (size_t)j * N + i0;
   const float fx = a.forcing == 1 ? a.frc[j] : 0.0f;
   float tu[4], tv[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int c = q + 2;
-    float du = -(Uc2[c] - Uc2[c - 1]) * idx - (UV1[c] - UV0[c]) * idy +
-               nu * ((Gxc[c] - Gxc[c - 1]) * idx + (Gyu1[c] - Gyu0[c]) * idy);
-    float dv = -(UV0[c + 1] - UV0[c]) * idx - (Vc0[c] - Vc1[c]) * idy +
-               nu * ((Gxv[c + 1] - Gxv[c]) * idx + (Gyc0[c] - Gyc1[c]) * idy);
-    const float uc = u[2][c], vc = v[2][c];
-    if (a.flow == 0) {
-      const float dc = Gxc[c] + Gyc0[c];
-      du += uc * 0.5f * ((Gxc[c - 1] + Gyc0[c - 1]) + dc);
-      dv += vc * 0.5f * ((Gxcs[q] + Gyc1[c]) + dc);
-    }
-    if (a.forcing == 1) {
-      du += fx - a.drag * uc;
-      dv -= a.drag * vc;
-    }
-    tu[q] = du;
-    tv[q] = dv;
-  }
+  strip_tendency<float, DORD>(u, v, a.idx, a.idy, a.nu, a.flow == 0, a.forcing == 1, fx, a.drag, tu, tv);
   const float ca = a.stage == 2 ? a.dt : 0.5f * a.dt;
   const float c6 = a.dt / 6.0f;
   const float4 unu = *reinterpret_cast<const float4*>(a.un + g);

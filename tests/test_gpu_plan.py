@@ -64,7 +64,7 @@ def clusters_of(n, dtype):
             ("f64", 32): [1, 2, 4]}[(dtype, n)]
 
 
-@pytest.mark.parametrize("n", [32, 64, 128])
+@pytest.mark.parametrize("n", [32, 64, 128, 256])
 @pytest.mark.parametrize("flow", ["ns", "burgers"])
 def test_cluster_shapes_match_oracle_one_step(n, flow):
     cfg = fd.Config(n=n, batch=2, dtype="f32", flow=flow, nu=1e-3 if flow != "burgers" else 0.01,

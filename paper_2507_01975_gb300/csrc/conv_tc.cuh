@@ -247,16 +247,29 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tmem = *tslot;
-  // the prologue above overlaps the previous kernel's tail; the inputs and
-  // the outputs' previous readers belong to the previous kernel
+  // the first part's weights were written two or more launches back (every
+  // kernel here waits for its predecessor before it lets its successor
+  // launch), so their copy starts before the wait, overlapping the previous
+  // kernel's tail
+  const int first_part = (int)blockIdx.x < ntiles ? (int)blockIdx.x / npix : -1;
+  if (warp == 0 && lane == 0 && first_part >= 0) {
+    mbar_expect_tx(w_full, Cfg::W_BYTES);
+    const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(a.w) + (size_t)first_part * Cfg::W_BYTES;
+    for (uint32_t off = 0; off < Cfg::W_BYTES; off += 16384) {
+      const uint32_t sz = (Cfg::W_BYTES - off) < 16384 ? (Cfg::W_BYTES - off) : 16384;
+      bulk_g2s(sW + off, wsrc + off, sz, w_full);
+    }
+  }
+  // the rest of the prologue overlaps the previous kernel's tail; the inputs
+  // and the outputs' previous readers belong to the previous kernel
   pdl_wait();
   pdl_trigger();
 
   if (warp == 0) {
     // ---------------- producer: weights once per part change, input tiles ----------
     // lane 0 waits and arms the barriers; all 32 lanes issue the tile's copies
-    int cur_part = -1;
-    uint32_t wphase_waits = 0;
+    int cur_part = first_part;
+    uint32_t wphase_waits = first_part >= 0 ? 1u : 0u;
     int i = 0;
     int issued = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {

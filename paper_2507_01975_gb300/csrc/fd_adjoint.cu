@@ -87,6 +87,9 @@ void adjoint_free(AdjointState* A) {
 fd_status adjoint_alloc(fd_ctx* c) {
   AdjointState* A = new (std::nothrow) AdjointState();
   if (!A) return fd_set_error(c, FD_ENOMEM, "fd_step_adjoint: out of host memory");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&A->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    A->sms = 1;
   const size_t NN = (size_t)c->grid.nx * c->grid.ny;
   const size_t B = c->grid.batch;
   const size_t state = fd_state_bytes(c->grid);
@@ -297,7 +300,7 @@ cudaError_t step_adjoint(fd_ctx* c, const float* u, const float* lam_out, float*
     fa.w = ws[s];
     fa.wout = A.wst[s];
     fa.coef = learned ? A.coef[s] : nullptr;
-    e = mark(launch_learned_stage<LOGN>(fa, A.xbar, B, st), "forward stage");  // xbar is free until the reverse pass
+    e = mark(launch_learned_stage<LOGN>(fa, A.xbar, B, A.sms, st), "forward stage");  // xbar is free until the reverse pass
     *launches += 2;
   }
   if (e == cudaSuccess && learned) e = net_forward_saved<LOGN>(c, 3, ws[3], st, launches);

@@ -81,6 +81,7 @@ struct AdjointState {
   __nv_bfloat16* zbar[2] = {};     // hidden-layer cotangents (64 channels, ping-pong)
   float* partial = nullptr;        // weight-gradient partial sums
   float* partial_b = nullptr;
+  int sms = 0;                     // SM count of the device (plain contexts have no learned state)
   bool ready = false;
 };
 

@@ -129,7 +129,7 @@ cudaError_t learned_step(fd_ctx* c, const float* s_in, float* s_out, const float
     a.stage = s;
     a.w = s == 0 ? s_in : L.wbuf;
     a.wout = s < 3 ? L.wbuf : s_out;
-    e = launch_learned_stage<LOGN>(a, L.ws, B, st);
+    e = launch_learned_stage<LOGN>(a, L.ws, B, L.sms, st);
     if (e != cudaSuccess) g_where = "flux / projection kernels";
   }
   if (e == cudaSuccess && tc_hist) {

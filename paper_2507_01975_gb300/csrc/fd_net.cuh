@@ -57,15 +57,23 @@ static cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, c
 
 // One learned RK stage: the banded flux kernel writes the unprojected stage
 // result to `scratch` (a state-sized buffer distinct from a.w and a.wout), then
-// the projection kernel writes a.wout. 2 launches.
+// the projection kernel writes a.wout. 2 launches. Bands of kBandRows rows;
+// when those would leave SMs idle (small batches) bands of kBandRowsSmall
+// rows, which recompute more face rows per cell row but spread the stage over
+// four times as many CTAs.
 constexpr int kBandRows = 8;
+constexpr int kBandRowsSmall = 2;
 
 template <int LOGN>
-static cudaError_t launch_learned_stage(const LStageArgs& a_in, float* scratch, int batch, cudaStream_t st) {
+static cudaError_t launch_learned_stage(const LStageArgs& a_in, float* scratch, int batch, int sms, cudaStream_t st) {
   LStageArgs a = a_in;
   a.wout = scratch;
-  cudaError_t e = launch_pdl(fv_learned_flux_kernel<LOGN, kBandRows>, dim3((1 << LOGN) / kBandRows, batch), dim3(256),
-                             BandCfg<LOGN, kBandRows>::SMEM, st, a);
+  const bool small = batch * ((1 << LOGN) / kBandRows) < sms;
+  cudaError_t e =
+      small ? launch_pdl(fv_learned_flux_kernel<LOGN, kBandRowsSmall>, dim3((1 << LOGN) / kBandRowsSmall, batch),
+                         dim3(256), BandCfg<LOGN, kBandRowsSmall>::SMEM, st, a)
+            : launch_pdl(fv_learned_flux_kernel<LOGN, kBandRows>, dim3((1 << LOGN) / kBandRows, batch), dim3(256),
+                         BandCfg<LOGN, kBandRows>::SMEM, st, a);
   LStageArgs p = a_in;
   p.w = scratch;
   if (e == cudaSuccess)
@@ -78,6 +86,9 @@ static cudaError_t prepare_learned_stage() {
   cudaError_t e = cudaFuncSetAttribute(fv_learned_flux_kernel<LOGN, kBandRows>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BandCfg<LOGN, kBandRows>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fv_learned_flux_kernel<LOGN, kBandRowsSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BandCfg<LOGN, kBandRowsSmall>::SMEM);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(fv_project_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)LearnedCfg<LOGN>::SMEM);

@@ -268,7 +268,7 @@ struct BandCfg {
 };
 
 template <int LOGN, int RB>
-__global__ void __launch_bounds__(256) fv_learned_flux_kernel(const LStageArgs a) {
+__global__ void __launch_bounds__(256, 4) fv_learned_flux_kernel(const LStageArgs a) {
   using Cfg = BandCfg<LOGN, RB>;
   constexpr int N = Cfg::N, NT = Cfg::NT, MSK = N - 1, TR = Cfg::TR, FR = Cfg::FR;
   extern __shared__ __align__(16) float bsm[];

@@ -468,6 +468,36 @@ def temporal_correction(U: np.ndarray, hist: Sequence[np.ndarray], p: Problem,
 # ----------------------------------------------------------------------------
 # diagnostics and metrics (App. D.1)
 # ----------------------------------------------------------------------------
+def shell_index(q: np.ndarray) -> np.ndarray:
+    """Nearest integer to sqrt(q) for integer q >= 0, in exact integer arithmetic:
+    the k with (k - 1/2)^2 <= q < (k + 1/2)^2, i.e. k^2 - k < q <= k^2 + k."""
+    q = np.asarray(q, dtype=np.int64)
+    k = np.floor(np.sqrt(q.astype(np.float64))).astype(np.int64)
+    k = np.where(k * k > q, k - 1, k)
+    k = np.where((k + 1) * (k + 1) <= q, k + 1, k)
+    return np.where(q > k * k + k, k + 1, k)
+
+
+def energy_spectrum(U: np.ndarray, kmax: int) -> np.ndarray:
+    """Shell-summed kinetic-energy spectrum (the energy spectra the paper compares for
+    the forced flow, Sec. 4 "Forced Flow" / Fig. 5). With the discrete Fourier
+    coefficients u^(k) = N^-2 sum_x u(x) exp(-2 pi i k.x / N) over integer wavevectors
+    k in [-N/2, N/2)^2, E(k) = 1/2 sum over |k| rounded to k of (|u^|^2 + |v^|^2), for
+    k = 0 .. kmax. The half-cell offsets of the MAC faces change phases only. Summed
+    over every shell, E equals 1/2 mean(u^2 + v^2) (Parseval)."""
+    ny, nx = U.shape[1:]
+    uh = np.fft.fft2(U[0]) / (nx * ny)
+    vh = np.fft.fft2(U[1]) / (nx * ny)
+    e = 0.5 * (np.abs(uh) ** 2 + np.abs(vh) ** 2)
+    ky = np.rint(np.fft.fftfreq(ny) * ny).astype(np.int64)
+    kx = np.rint(np.fft.fftfreq(nx) * nx).astype(np.int64)
+    kk = shell_index(ky[:, None] ** 2 + kx[None, :] ** 2)
+    E = np.zeros(kmax + 1)
+    m = kk <= kmax
+    np.add.at(E, kk[m], e[m])
+    return E
+
+
 def vorticity(U: np.ndarray, dx: float, dy: float) -> np.ndarray:
     """Corner vorticity w = dv/dx - du/dy by differences of adjacent faces."""
     return (U[1] - shifted(U[1], 0, -1)) / dx - (U[0] - shifted(U[0], -1, 0)) / dy

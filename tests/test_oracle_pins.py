@@ -448,3 +448,36 @@ def test_vorticity_of_taylor_green_and_pcc():
     assert np.max(np.abs(w - 2 * np.sin(x) * np.sin(y))) < 2e-2
     assert abs(O.pcc(w, 3 * w + 1) - 1.0) < 1e-14
     assert abs(O.pcc(w, -w) + 1.0) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# energy spectrum (Sec. 4, forced flow / Fig. 5): closed forms and Parseval
+# ----------------------------------------------------------------------------
+def test_shell_index_is_the_nearest_integer_root():
+    q = np.arange(0, 200000)
+    k = O.shell_index(q)
+    # (k - 1/2)^2 <= q < (k + 1/2)^2 checked in exact integer arithmetic (x4)
+    lo = np.maximum(2 * k - 1, 0)
+    assert np.all(lo ** 2 <= 4 * q) and np.all(4 * q < (2 * k + 1) ** 2)
+
+
+def test_energy_spectrum_single_modes_and_parseval():
+    n = 32
+    x = np.arange(n) * (2 * np.pi / n)
+    X, Y = np.meshgrid(x, x)
+    A = 0.7
+    U = np.stack([A * np.cos(3 * X), np.zeros_like(X)])
+    E = O.energy_spectrum(U, n)
+    assert abs(E[3] - A * A / 4) < 1e-14 and np.abs(np.delete(E, 3)).max() < 1e-14
+    # |k| = 5 from (kx, ky) = (3, 4), in v this time, shifted by half a cell
+    U = np.stack([np.zeros_like(X), np.sin(3 * X + 4 * (Y + np.pi / n))])
+    E = O.energy_spectrum(U, n)
+    assert abs(E[5] - 0.25) < 1e-14 and np.abs(np.delete(E, 5)).max() < 1e-14
+    # Parseval on a random field, and invariance under a periodic translation
+    U = np.random.default_rng(5).standard_normal((2, n, n))
+    E = O.energy_spectrum(U, n)
+    assert abs(E.sum() - 0.5 * np.mean(U[0] ** 2 + U[1] ** 2)) < 1e-13
+    Es = O.energy_spectrum(np.roll(U, (3, -5), axis=(1, 2)), n)
+    assert np.abs(Es - E).max() < 1e-14
+    # shells beyond kmax are dropped, the rest unchanged
+    assert np.abs(O.energy_spectrum(U, 7) - E[:8]).max() == 0.0

@@ -297,6 +297,18 @@ def fine_measurement(fd, I, steps: int = 40):
     ms = e0.elapsed_time(e1) / steps
     gbs = STREAM_BYTES_PER_CELL_STEP * n * n / (ms * 1e-3) / 1e9
     peak = _measured_peaks().get("hbm_gbs") or 6800.0
+    # energy spectrum of the final state (analysis kernels: row and column FFTs of
+    # u + iv, shell sums); algorithmic traffic 24 B per cell (state in, complex
+    # scratch out and back in)
+    spec = torch.empty((1, n // 2 + 1), dtype=torch.float64, device="cuda")
+    s.energy_spectrum(o, spec)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        s.energy_spectrum(o, spec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_spec = e0.elapsed_time(e1) / reps
     return {
         "workload": "decaying NS 2048^2, batch 1, FP32, streaming path (17 launches per step, CUDA graph)",
         "value": n * n / (ms * 1e-3),
@@ -306,7 +318,11 @@ def fine_measurement(fd, I, steps: int = 40):
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                      "traffic": None, "kernel": "whole step (stage, FFT and final kernels)",
                      "algorithmic_bytes_per_cell_step": STREAM_BYTES_PER_CELL_STEP,
+                     "frac_at_384_bytes_per_cell_step": 384 * n * n / (ms * 1e-3) / 1e9 / peak,
                      "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"},
+        "energy_spectrum": {"ms": ms_spec, "kmax": n // 2,
+                            "gbs_at_24_bytes_per_cell": 24 * n * n / (ms_spec * 1e-3) / 1e9,
+                            "energy": float(spec.sum().item())},
     }
 
 

@@ -231,6 +231,17 @@ fd_status fd_train_step(fd_ctx* ctx, const void* u0, const void* targets, int32_
 fd_status fd_mse_loss(fd_ctx* ctx, const float* pred, const float* target, int64_t count, double* loss,
                       float* grad, void* stream);
 
+/* Kinetic-energy spectrum (the energy spectra of the forced-flow comparison,
+ * Sec. 4 / Fig. 5): for each trajectory b of the device state u (FP32
+ * [batch][2][N][N], N >= 32), spectrum[b][k] = 1/2 sum over the integer
+ * wavevectors whose length rounds to k of |u^|^2 + |v^|^2, where u^ is the DFT
+ * normalised by 1/N^2 (so that sum_k spectrum[b][k] over k <= N/sqrt(2) is
+ * 1/2 mean(u^2 + v^2)), for k = 0 .. kmax (kmax <= N). spectrum: device
+ * double[batch][kmax + 1], overwritten. A complex scratch of the state's size
+ * is allocated on the first call and kept by the context. Errors: FD_EINVAL,
+ * FD_EUNSUPPORTED (FP64 or N < 32), FD_ENOMEM, FD_ECUDA. */
+fd_status fd_energy_spectrum(fd_ctx* ctx, const void* u, double* spectrum, int32_t kmax, void* stream);
+
 /* Vorticity correlation (App. D.1, PCC; the accuracy measure of the paper's
  * correlation curves): for each trajectory b, the Pearson correlation of the
  * corner vorticities w = (v - v[i-1]) / dx - (u - u[j-1]) / dy of the device

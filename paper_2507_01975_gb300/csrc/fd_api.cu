@@ -378,6 +378,7 @@ fd_status fd_destroy(fd_ctx* c) {
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_state) cudaFree(c->d_state);
   if (c->d_flag) cudaFree(c->d_flag);
+  if (c->d_spec) cudaFree(c->d_spec);
   if (c->side) fd_destroy(c->side);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);

@@ -124,6 +124,8 @@ struct fd_ctx {
   void* d_tables = nullptr;  // tw | symx | symy | frc
   size_t off_symx = 0, off_symy = 0, off_frc = 0;
   void* d_state = nullptr;   // device state for fd_rollout_host
+  void* d_spec = nullptr;    // complex scratch of fd_energy_spectrum
+  size_t spec_bytes = 0;
   unsigned* d_flag = nullptr;
   int launches = 0;
   std::string err;

@@ -38,6 +38,7 @@ EXPORTS = [
     "fd_train_step",
     "fd_mse_loss",
     "fd_vorticity_pcc",
+    "fd_energy_spectrum",
     "fd_adam_step",
     "fd_downsample",
     "fd_get_plan",
@@ -145,6 +146,8 @@ def load(path: str = LIB_PATH):
     lib.fd_train_step.restype = C.c_int
     lib.fd_mse_loss.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
     lib.fd_mse_loss.restype = C.c_int
+    lib.fd_energy_spectrum.argtypes = [vp, vp, vp, i32, vp]
+    lib.fd_energy_spectrum.restype = C.c_int
     lib.fd_vorticity_pcc.argtypes = [vp, vp, vp, vp, vp]
     lib.fd_vorticity_pcc.restype = C.c_int
     lib.fd_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, i32, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]
@@ -327,6 +330,11 @@ class Solver:
         g = _ptr(grad) if grad is not None else None
         self._check(self.lib.fd_mse_loss(self.h, _ptr(pred), _ptr(target), int(pred.numel()), _ptr(loss), g,
                                          _stream_handle(stream)))
+
+    def energy_spectrum(self, u, out, stream=None):
+        """Shell-summed kinetic-energy spectrum into out (device float64 [batch, kmax + 1])."""
+        self._check(self.lib.fd_energy_spectrum(self.h, _ptr(u), _ptr(out), int(out.shape[-1]) - 1,
+                                                _stream_handle(stream)))
 
     def vorticity_pcc(self, a, b, out, stream=None):
         """out[batch] (device float64) = vorticity correlation of states a and b per trajectory."""

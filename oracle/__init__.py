@@ -18,3 +18,4 @@ this package.
 """
 
 from .fv import *  # noqa: F401,F403
+from .fno import FNOParams, fno_forward, spectral_conv  # noqa: F401

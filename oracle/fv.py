@@ -174,7 +174,8 @@ def forcing(U: np.ndarray, p: Problem) -> np.ndarray:
     return f
 
 
-def tendency(U: np.ndarray, p: Problem, kernels: Optional[Sequence] = None) -> np.ndarray:
+def tendency(U: np.ndarray, p: Problem, kernels: Optional[Sequence] = None,
+             extra: Optional[np.ndarray] = None) -> np.ndarray:
     """Right-hand side H(u) of the momentum equation without the pressure flux.
 
     Finite-volume form of Eq. 4 (App. B.2): for the u control volume centred on
@@ -192,11 +193,17 @@ def tendency(U: np.ndarray, p: Problem, kernels: Optional[Sequence] = None) -> n
     u_t = nu lap u - u . grad u): the conservative flux divergence above minus
     u times the cell divergence (Gxc + Gyc) averaged to the face, which equals
     u . grad u for the continuum operators.
+
+    ``extra[q]`` (optional, [8, ny, nx]) is added to instance q's face values:
+    the frequency-domain operator O_F of the integrated operator (Sec. 3.4).
     """
     if kernels is None:
         kernels = plain_kernels(p)
     dx, dy = p.dx, p.dy
-    Uc, Gxc, Uk, Gyu, Vk, Gxv, Vc, Gyc = face_values(U, kernels)
+    fv = face_values(U, kernels)
+    if extra is not None:
+        fv = [f + extra[q] for q, f in enumerate(fv)]
+    Uc, Gxc, Uk, Gyu, Vk, Gxv, Vc, Gyc = fv
     P = Uk * Vk  # (u v) at corners, shared by both momentum equations
     Tu = (
         -(Uc**2 - shifted(Uc**2, 0, -1)) / dx
@@ -285,18 +292,24 @@ def rk4_step(U: np.ndarray, p: Problem, kernels_fn=None) -> np.ndarray:
     u' = u + dt/6 (r1 + 2 r2 + 2 r3 + r4). For Navier-Stokes every sub-step's
     intermediate field and the final combination are projected (Sec. 3.2:
     the projection completes each RK4 sub-step). ``kernels_fn(W)`` returns the
-    eight face kernels for stage state W (plain kernels when None).
+    eight face kernels for stage state W (plain kernels when None), or a pair
+    (kernels, extra face values) when the operator has a frequency-domain part.
     """
     ns = p.flow == FLOW_NAVIER_STOKES
     P = (lambda W: project(W, p)) if ns else (lambda W: W)
     K = (lambda W: None) if kernels_fn is None else kernels_fn
-    r1 = tendency(U, p, K(U))
+
+    def H(W):
+        k = K(W)
+        return tendency(W, p, *k) if isinstance(k, tuple) else tendency(W, p, k)
+
+    r1 = H(U)
     w = P(U + 0.5 * p.dt * r1)
-    r2 = tendency(w, p, K(w))
+    r2 = H(w)
     w = P(U + 0.5 * p.dt * r2)
-    r3 = tendency(w, p, K(w))
+    r3 = H(w)
     w = P(U + p.dt * r3)
-    r4 = tendency(w, p, K(w))
+    r4 = H(w)
     return P(U + (p.dt / 6.0) * (r1 + 2.0 * r2 + 2.0 * r3 + r4))
 
 
@@ -420,6 +433,8 @@ class LearnedModel:
     ``q * 20 + r * 4 + c``).
     ``tc``: list of six ``(W, b)`` layers, 2 k_c -> 64 x5 -> 2, the temporal
     correction network (Sec. 3.5); empty or k_c == 0 disables it.
+    ``fno``: the frequency-domain operator O_F (``oracle.fno``), whose eight
+    output channels add to the eight instances' face values; None disables it.
     Learned derivative parts are dimensionless and divided by the spacing
     along the instance's axis.
     """
@@ -428,6 +443,8 @@ class LearnedModel:
     stencil: list
     tc: list = field(default_factory=list)
     k_c: int = 0
+    #: frequency-domain operator O_F (oracle.fno.FNOParams) or None
+    fno: object = None
 
 
 def learned_kernels(U: np.ndarray, p: Problem, model: LearnedModel) -> list:
@@ -446,8 +463,13 @@ def learned_kernels(U: np.ndarray, p: Problem, model: LearnedModel) -> list:
 
 
 def learned_step(U: np.ndarray, p: Problem, model: LearnedModel) -> np.ndarray:
-    """FV-module step with the learned flux block evaluated at every RK stage."""
-    return rk4_step(U, p, kernels_fn=lambda W: learned_kernels(W, p, model))
+    """FV-module step with the learned flux block evaluated at every RK stage
+    (O = O_P + O_L + O_F when the model has a frequency-domain operator)."""
+    if model.fno is None:
+        return rk4_step(U, p, kernels_fn=lambda W: learned_kernels(W, p, model))
+    from .fno import fno_forward
+
+    return rk4_step(U, p, kernels_fn=lambda W: (learned_kernels(W, p, model), fno_forward(W, model.fno)))
 
 
 def temporal_correction(U: np.ndarray, hist: Sequence[np.ndarray], p: Problem,

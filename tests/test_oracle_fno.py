@@ -1,0 +1,108 @@
+"""Pins of the oracle's frequency-domain operator O_F (Sec. 3.4; Table S3).
+
+* a single Fourier mode through the spectral convolution has a closed form
+  (a cos - b sin for the complex weight a + ib), in both row blocks;
+* modes outside the kept set are removed;
+* with zero spectral weights the operator is a chain of pointwise maps and
+  GELUs, checked against explicit loops;
+* the whole operator commutes with periodic translations;
+* inside the flux block: zero output changes nothing, any output keeps the
+  mean momentum (the flux form telescopes for any face values).
+"""
+
+import numpy as np
+
+import oracle as O
+from oracle.fno import FNOParams, fno_forward, spectral_conv
+
+
+def random_fno(rng, width=4, modes=4, layers=2, scale=0.3):
+    R = [(rng.standard_normal((2 * modes, modes, width, width)) + 1j * rng.standard_normal((2 * modes, modes, width, width)))
+         * scale / width for _ in range(layers)]
+    return FNOParams(P_w=rng.standard_normal((width, 2)) * scale, P_b=rng.standard_normal(width) * 0.1,
+                     R=R, W=[rng.standard_normal((width, width)) * scale for _ in range(layers)],
+                     Wb=[rng.standard_normal(width) * 0.1 for _ in range(layers)],
+                     Q_w=rng.standard_normal((8, width)) * scale, Q_b=rng.standard_normal(8) * 0.01)
+
+
+def mode(n, ky, kx):
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    return 2 * np.pi * (ky * j + kx * i) / n
+
+
+def test_single_mode_closed_form_both_blocks():
+    n, m = 16, 4
+    for ky, row in ((2, 2), (-2, 2 * m - 2)):  # ky = -2 lives in the second block
+        th = mode(n, ky, 3)
+        v = np.stack([np.zeros((n, n)), np.cos(th)])
+        R = np.zeros((2 * m, m, 2, 3), dtype=complex)
+        w = np.array([0.5 - 0.25j, -1.0 + 2.0j, 0.3j])
+        R[row, 3, 1, :] = w
+        out = spectral_conv(v, R)
+        for o in range(3):
+            ref = w[o].real * np.cos(th) - w[o].imag * np.sin(th)
+            assert np.abs(out[o] - ref).max() < 1e-13
+
+
+def test_modes_outside_the_kept_set_are_removed():
+    n, m = 16, 4
+    R = np.ones((2 * m, m, 1, 1), dtype=complex)
+    for ky, kx in ((0, m), (m, 1), (-m - 1, 2), (n // 2, 0)):
+        v = np.cos(mode(n, ky, kx))[None]
+        assert np.abs(spectral_conv(v, R)).max() < 1e-13
+    # a kept mode with unit weights passes unchanged
+    v = np.cos(mode(n, -3, 2))[None]
+    assert np.abs(spectral_conv(v, R) - v).max() < 1e-13
+
+
+def test_zero_spectral_weights_reduce_to_pointwise_loops():
+    rng = np.random.default_rng(7)
+    n, width = 8, 3
+    prm = random_fno(rng, width=width, modes=2, layers=2)
+    prm.R = [np.zeros_like(r) for r in prm.R]
+    U = rng.standard_normal((2, n, n))
+    out = fno_forward(U, prm)
+    ref = np.zeros((8, n, n))
+    for y in range(n):
+        for x in range(n):
+            v = [sum(prm.P_w[o, i] * U[i, y, x] for i in range(2)) + prm.P_b[o] for o in range(width)]
+            for l in range(2):
+                v = [sum(prm.W[l][o, i] * v[i] for i in range(width)) + prm.Wb[l][o] for o in range(width)]
+                if l == 0:
+                    v = [float(O.gelu(np.array(t))) for t in v]
+            for q in range(8):
+                ref[q, y, x] = sum(prm.Q_w[q, i] * v[i] for i in range(width)) + prm.Q_b[q]
+    assert np.abs(out - ref).max() < 1e-12
+
+
+def test_translation_equivariance():
+    rng = np.random.default_rng(8)
+    n = 16
+    prm = random_fno(rng, width=4, modes=4, layers=3)
+    U = rng.standard_normal((2, n, n))
+    a = fno_forward(np.roll(U, (3, -5), axis=(1, 2)), prm)
+    b = np.roll(fno_forward(U, prm), (3, -5), axis=(1, 2))
+    assert np.abs(a - b).max() < 1e-12
+
+
+def _model(rng, fno):
+    st = [(rng.standard_normal((64, 2, 3, 3)) * 0.05, np.zeros(64))]
+    for _ in range(4):
+        st.append((rng.standard_normal((64, 64, 3, 3)) * 0.02, np.zeros(64)))
+    st.append((np.zeros((160, 64, 3, 3)), np.zeros(160)))
+    return O.LearnedModel(W_L=rng.standard_normal((2, 2, 5, 4)) * 1e-3, stencil=st, fno=fno)
+
+
+def test_operator_in_the_flux_block():
+    rng = np.random.default_rng(9)
+    n = 16
+    p = O.Problem(nx=n, ny=n, nu=1e-3, dt=2e-3)
+    U = O.project(rng.standard_normal((2, n, n)) * 0.3, p)
+    prm = random_fno(rng, width=4, modes=4, layers=2)
+    base = O.learned_step(U, p, _model(np.random.default_rng(1), None))
+    zero = FNOParams(**{**prm.__dict__, "Q_w": np.zeros_like(prm.Q_w), "Q_b": np.zeros_like(prm.Q_b)})
+    assert np.array_equal(O.learned_step(U, p, _model(np.random.default_rng(1), zero)), base)
+    with_f = O.learned_step(U, p, _model(np.random.default_rng(1), prm))
+    assert np.abs(with_f - base).max() > 1e-6
+    for c in range(2):
+        assert abs(with_f[c].sum() - U[c].sum()) < 1e-12 * np.abs(U[c]).sum()

@@ -90,6 +90,11 @@ typedef struct {
   int32_t path;           /* 0 = automatic (default): on chip where built (FP32 N <= 256,
                              FP64 N <= 128), streaming through HBM otherwise;
                              1 = on chip only; 2 = streaming (FP32, N in [32, 2048]) */
+  int32_t fno_layers;     /* frequency-domain operator O_F of the learnable module (Sec. 3.4):
+                             Fourier layers, 0 = off (default); needs learned = 1; forward only
+                             (the reverse-mode calls refuse a context that has it) */
+  int32_t fno_modes;      /* kept Fourier modes M per axis, 1 <= M <= N/2 (Table S3: 16 or 32) */
+  int32_t fno_width;      /* channels of the Fourier layers: 8 or 16 (the widths of Table S3) */
 } fd_options;
 
 typedef struct fd_ctx fd_ctx; /* opaque, library-owned */
@@ -157,8 +162,18 @@ int32_t fd_last_launch_count(const fd_ctx* ctx);
  *   temporal correction (only when k_c > 0): layers as above with
  *                   (Cin, Cout) = (2 k_c, 64) (64,64) x4 (64, 2); input channel
  *                   2 s + c is component c of u_{k-k_c+s}.
+ *   frequency-domain operator O_F (only when fno_layers = L > 0; width C,
+ *                   modes M): P_w[C][2], P_b[C]; per layer R[2M][M][C][C][2]
+ *                   (complex channel matrices [in][out] of the kept modes, real
+ *                   and imaginary parts; rows 0 .. M-1 are ky = 0 .. M-1, rows
+ *                   M .. 2M-1 are ky = N-M .. N-1; kx = 0 .. M-1), W[C][C]
+ *                   ([out][in]), b[C]; then Q_w[8][C], Q_b[8]. O_F(u) = Q(v_L),
+ *                   v_0 = P(u), v_l = sigma(W_l v_{l-1} + b_l + irfft2(R_l .
+ *                   rfft2(v_{l-1}))) with sigma = GELU except after the last
+ *                   layer; channel q of O_F(u) is added to instance q's face
+ *                   values. All in FP32 on the CUDA cores.
  * Network weights are rounded to BF16 (round to nearest even) on upload;
- * biases and W_L stay FP32. */
+ * biases, W_L and the O_F parameters stay FP32. */
 
 /* Number of float32 parameters fd_set_params expects (0 when not learned). */
 int64_t fd_param_count(const fd_ctx* ctx);

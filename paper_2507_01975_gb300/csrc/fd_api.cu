@@ -20,7 +20,6 @@
 using namespace ldfv;
 
 // learned path (fd_learned.cu)
-int64_t fd_learned_param_count(int kc);
 fd_status fd_learned_init(fd_ctx* c);
 void fd_learned_free(fd_ctx* c);
 void fd_adjoint_free(fd_ctx* c);
@@ -162,7 +161,7 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown flow");
   if (!(dt > 0) || !std::isfinite(dt)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: dt must be positive");
   if (!(nu >= 0) || !std::isfinite(nu)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
-  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0};
+  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (o.deriv_order != 2 && o.deriv_order != 4)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
@@ -176,6 +175,17 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   if (o.learned != 0 && o.learned != 1) return fd_set_error(nullptr, FD_EINVAL, "fd_init: learned must be 0 or 1");
   if (!o.learned && o.k_c) return fd_set_error(nullptr, FD_EINVAL, "fd_init: k_c needs the learned option");
   if (o.path < 0 || o.path > 2) return fd_set_error(nullptr, FD_EINVAL, "fd_init: path must be 0, 1 or 2");
+  if (o.fno_layers < 0 || o.fno_layers > 8)
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: fno_layers must be in [0, 8]");
+  if (o.fno_layers > 0) {
+    if (!o.learned) return fd_set_error(nullptr, FD_EINVAL, "fd_init: the frequency-domain operator needs learned = 1");
+    if (o.fno_width != 8 && o.fno_width != 16)
+      return fd_set_error(nullptr, FD_EINVAL, "fd_init: fno_width must be 8 or 16 (the widths of Table S3)");
+    if (o.fno_modes < 1 || 2 * o.fno_modes > g.nx)
+      return fd_set_error(nullptr, FD_EINVAL, "fd_init: fno_modes must be in [1, N/2]");
+  } else {
+    o.fno_modes = o.fno_width = 0;
+  }
   int logn = 0;
   while ((1 << logn) < g.nx) ++logn;
   Launcher L;

@@ -61,6 +61,14 @@ struct LearnedState {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   int sms = 0;
+  // frequency-domain operator O_F (fno_layers > 0)
+  int fno_layers = 0, fno_modes = 0, fno_width = 0;
+  size_t raw_off_fno = 0;      // P_w, P_b, layers (R, W, b), Q_w, Q_b in the raw array
+  float* fno_v[2] = {};        // channel fields [batch][width][N][N] (ping-pong)
+  float* fno_y = nullptr;      // inverse spectral convolution [batch][width][N][N]
+  float2* fno_s = nullptr;     // kept modes [batch][width][2M][M]
+  float2* fno_s2 = nullptr;    // mixed modes
+  float* fno_out = nullptr;    // O_F(u) [batch][8][N][N]
 };
 
 // Workspace of the reverse mode of one step (allocated by the first

@@ -16,6 +16,12 @@
 
 using namespace ldfv;
 
+// frequency-domain operator O_F of one stage state (fd_fno.cu): writes L.fno_out
+cudaError_t fd_fno_forward(fd_ctx* c, const float* u, cudaStream_t st);
+int fd_fno_launches(int layers);
+int64_t fd_fno_param_count(int layers, int modes, int width);
+cudaError_t fd_fno_prepare();
+
 namespace {
 
 // kernel launches of one learned step: per stage the stencil network (input
@@ -125,6 +131,14 @@ cudaError_t learned_step(fd_ctx* c, const float* s_in, float* s_out, const float
     if (e != cudaSuccess) {
       g_where = "stencil network";
       break;
+    }
+    if (L.fno_layers > 0) {
+      e = fd_fno_forward(c, s == 0 ? s_in : L.wbuf, st);
+      if (e != cudaSuccess) {
+        g_where = "frequency-domain operator";
+        break;
+      }
+      a.fno = L.fno_out;
     }
     a.stage = s;
     a.w = s == 0 ? s_in : L.wbuf;
@@ -237,6 +251,8 @@ void plan_layout(LearnedState& L, std::vector<PackDesc>& descs, std::vector<uint
       L.raw_off_tb[l] = off;
       off += tc_cout(l);
     }
+  L.raw_off_fno = off;  // O_F parameters stay FP32 (no rounding range)
+  off += (size_t)fd_fno_param_count(L.fno_layers, L.fno_modes, L.fno_width);
   L.raw_off_w0t = off;
   off += 2 * 64 * 9;
   L.raw_off_zero = off;
@@ -287,12 +303,19 @@ cudaError_t upload_params(LearnedState& L, const float* params, cudaStream_t st)
 // ---------------------------------------------------------------------------
 // entry points used by fd_api.cu
 // ---------------------------------------------------------------------------
-int64_t fd_learned_param_count(int kc) {
+// parameters of the frequency-domain operator O_F (layout in include/fd.h)
+int64_t fd_fno_param_count(int layers, int modes, int width) {
+  if (layers <= 0) return 0;
+  const int64_t c = width;
+  return c * 2 + c + (int64_t)layers * (2 * (int64_t)modes * modes * c * c * 2 + c * c + c) + 8 * c + 8;
+}
+
+int64_t fd_learned_param_count(int kc, int fno_layers, int fno_modes, int fno_width) {
   int64_t n = 80;
   for (int l = 0; l < 6; ++l) n += (int64_t)stencil_cout(l) * stencil_cin(l) * 9 + stencil_cout(l);
   if (kc > 0)
     for (int l = 0; l < 6; ++l) n += (int64_t)tc_cout(l) * tc_cin(l, kc) * 9 + tc_cout(l);
-  return n;
+  return n + fd_fno_param_count(fno_layers, fno_modes, fno_width);
 }
 
 fd_status fd_learned_init(fd_ctx* c) {
@@ -305,7 +328,10 @@ fd_status fd_learned_init(fd_ctx* c) {
   if (!L) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: out of host memory");
   c->lrn = L;
   L->kc = c->opts.k_c;
-  L->nparams = fd_learned_param_count(L->kc);
+  L->fno_layers = c->opts.fno_layers;
+  L->fno_modes = c->opts.fno_modes;
+  L->fno_width = c->opts.fno_width;
+  L->nparams = fd_learned_param_count(L->kc, L->fno_layers, L->fno_modes, L->fno_width);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&L->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -327,6 +353,15 @@ fd_status fd_learned_init(fd_ctx* c) {
   alloc((void**)&L->ring, state * L->nring);
   alloc((void**)&L->d_err, sizeof(unsigned));
   alloc((void**)&L->d_ptrs, sizeof(float*) * (L->nring + 1 + 8 * L->nring));
+  if (L->fno_layers > 0) {
+    const size_t C = L->fno_width, M = L->fno_modes;
+    alloc((void**)&L->fno_v[0], B * C * NN * sizeof(float));
+    alloc((void**)&L->fno_v[1], B * C * NN * sizeof(float));
+    alloc((void**)&L->fno_y, B * C * NN * sizeof(float));
+    alloc((void**)&L->fno_s, B * C * 2 * M * M * sizeof(float2));
+    alloc((void**)&L->fno_s2, B * C * 2 * M * M * sizeof(float2));
+    alloc((void**)&L->fno_out, B * 8 * NN * sizeof(float));
+  }
   std::vector<PackDesc> descs;
   std::vector<uint32_t> ranges;
   plan_layout(*L, descs, ranges);
@@ -352,6 +387,7 @@ fd_status fd_learned_init(fd_ctx* c) {
     e = cudaMemcpy(L->d_ptrs, h.data(), sizeof(float*) * h.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = (g.nx == 64) ? prepare_kernels<6>() : prepare_kernels<5>();
+  if (e == cudaSuccess && L->fno_layers > 0) e = fd_fno_prepare();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: learned workspace: %s", cudaGetErrorString(e));
   return FD_OK;
@@ -365,7 +401,8 @@ void fd_learned_free(fd_ctx* c) {
   void* ps[] = {L->d_raw,  L->d_wpack, L->d_stage, L->d_desc,         (void*)L->d_ranges, L->act0, L->act1,
                 L->coef,   L->acc,     L->wbuf,    L->ws,             L->corr,            L->ring,
                 (void*)L->d_ptrs,
-                L->d_err};
+                L->d_err,  L->fno_v[0], L->fno_v[1], L->fno_y,        L->fno_s,           L->fno_s2,
+                L->fno_out};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete L;
@@ -471,7 +508,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
   if (e == cudaSuccess && use_graph && L.graph) {
     for (; done + G <= n_steps && e == cudaSuccess; done += G) {
       e = cudaGraphLaunch(L.graph, st);
-      launches += G * kLaunchesPerStep + (L.kc > 0 ? kLaunchesTc : 0);
+      launches += G * (kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers)) + (L.kc > 0 ? kLaunchesTc : 0);
     }
   }
   // remaining steps (or every step when snapshots are requested): direct launches
@@ -479,7 +516,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
     const int r = done % G;
     const bool tc = L.kc > 0 && ((done + 1) % L.kc == 0);
     e = step_fn(r, tc, st);
-    launches += kLaunchesPerStep + (tc ? kLaunchesTc : 0);
+    launches += kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers) + (tc ? kLaunchesTc : 0);
     if (e == cudaSuccess && save_every > 0 && traj && ((done + 1) % save_every) == 0) {
       e = cudaMemcpyAsync(static_cast<float*>(traj) + (size_t)snap * slot, L.ring + (r + 1) * slot, bytes,
                           cudaMemcpyDeviceToDevice, st);

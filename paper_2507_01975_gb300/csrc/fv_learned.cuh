@@ -32,6 +32,7 @@ struct LStageArgs {
   const __nv_bfloat16* coef;  // [batch][20][N][N][8] network output, or null (C = 0)
   const float* wl;   // W_L [kind 2][axis 2][5][4]
   const float* corr; // correct_project only: correction [batch][2][N][N]
+  const float* fno;  // O_F(u) [batch][8][N][N] added to the face values, or null
   int stage;
   int flow;          // 0 Burgers, 1 Navier-Stokes
   int forcing;
@@ -377,6 +378,7 @@ __global__ void __launch_bounds__(256, 4) fv_learned_flux_kernel(const LStageArg
             }
             val += k * tap[r * 4 + cc];
           }
+        if (a.fno) val += a.fno[((size_t)b * 8 + qi) * NN + c];
         inst[(qi * FR + fr) * N + i] = val;
       }
     }

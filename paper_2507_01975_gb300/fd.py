@@ -82,6 +82,9 @@ class FdOptions(C.Structure):
         ("ckpt_every", C.c_int32),
         ("spin_limit", C.c_int64),
         ("path", C.c_int32),
+        ("fno_layers", C.c_int32),
+        ("fno_modes", C.c_int32),
+        ("fno_width", C.c_int32),
     ]
 
 
@@ -205,6 +208,9 @@ class Config:
     learned: bool = False
     k_c: int = 0
     path: int = 0  # 0 automatic, 1 on chip, 2 streaming through HBM
+    fno_layers: int = 0  # frequency-domain operator O_F: Fourier layers (0 = off)
+    fno_modes: int = 0
+    fno_width: int = 0
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -230,7 +236,8 @@ class Solver:
         g = FdGrid(cfg.n, cfg.n, cfg.lx, cfg.ly, cfg.batch, FD_F64 if cfg.dtype == "f64" else FD_F32,
                    FD_BURGERS if cfg.flow == "burgers" else FD_NAVIER_STOKES)
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
-        o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26, cfg.path)
+        o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26, cfg.path,
+                      cfg.fno_layers, cfg.fno_modes, cfg.fno_width)
         h = C.c_void_p()
         st = self.lib.fd_init(C.byref(g), cfg.nu, cfg.dt, C.byref(f), C.byref(o), C.byref(h))
         if st != FD_OK:

@@ -167,13 +167,46 @@ def random_wl(seed: int, std: float = 1e-3) -> np.ndarray:
     return np.asarray(rng.standard_normal((2, 2, 5, 4)) * std, dtype=np.float32).astype(np.float64)
 
 
-def pack_params(W_L: np.ndarray, stencil, tc=None) -> np.ndarray:
+def random_fno(seed: int, width: int, modes: int, layers: int, scale: float = 1.0,
+               out_scale: float = 0.01) -> dict:
+    """Seeded parameters of a frequency-domain operator (float32-representable
+    float64 arrays): P_w[width, 2], P_b[width]; per layer R[2M, M, width, width]
+    (complex), W[width, width], Wb[width]; Q_w[8, width], Q_b[8]. Weights are
+    N(0, scale / sqrt(fan-in)) (the spectral ones also divided by the number of
+    kept modes), biases N(0, 0.02); Q is scaled by ``out_scale``."""
+    rng = np.random.default_rng(seed)
+
+    def f32(a):
+        return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+    m = modes
+    R = [f32(rng.standard_normal((2 * m, m, width, width)) * scale / (width * m))
+         + 1j * f32(rng.standard_normal((2 * m, m, width, width)) * scale / (width * m)) for _ in range(layers)]
+    return {
+        "P_w": f32(rng.standard_normal((width, 2)) * scale / np.sqrt(2)),
+        "P_b": f32(rng.standard_normal(width) * 0.02),
+        "R": R,
+        "W": [f32(rng.standard_normal((width, width)) * scale / np.sqrt(width)) for _ in range(layers)],
+        "Wb": [f32(rng.standard_normal(width) * 0.02) for _ in range(layers)],
+        "Q_w": f32(rng.standard_normal((8, width)) * out_scale / np.sqrt(width)),
+        "Q_b": f32(rng.standard_normal(8) * out_scale * 0.1),
+    }
+
+
+def pack_params(W_L: np.ndarray, stencil, tc=None, fno=None) -> np.ndarray:
     """Flat float32 parameter array in the layout fd_set_params documents:
     W_L[2][2][5][4], then every stencil layer's W[Cout][Cin][3][3] and b[Cout],
-    then (optionally) every temporal-correction layer's weights and biases."""
+    then (optionally) every temporal-correction layer's weights and biases, then
+    (optionally) the frequency-domain operator: P_w, P_b, per layer R as
+    [2M][M][Cin][Cout][re, im], W[Cout][Cin], b, and Q_w, Q_b."""
     parts = [np.asarray(W_L, dtype=np.float64).ravel()]
     for W, b in stencil:
         parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
     for W, b in (tc or []):
         parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
+    if fno is not None:
+        parts += [fno["P_w"].ravel(), fno["P_b"].ravel()]
+        for R, W, b in zip(fno["R"], fno["W"], fno["Wb"]):
+            parts += [np.stack([R.real, R.imag], axis=-1).ravel(), W.ravel(), b.ravel()]
+        parts += [fno["Q_w"].ravel(), fno["Q_b"].ravel()]
     return np.concatenate(parts).astype(np.float32)

@@ -66,6 +66,15 @@ def _init(lib, n=32, batch=1, dtype=fd.FD_F32, flow=fd.FD_NAVIER_STOKES, nu=1e-3
         dict(lx=0.0),
         dict(opts=fd.FdOptions(3, 2, 0, 0, 0, 8, 1)),
         dict(opts=fd.FdOptions(4, 4, 0, 0, 0, 8, 1)),
+        # frequency-domain operator: too many layers, without the learned module,
+        # width and modes out of range (modes <= N/2)
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 9, 16, 8)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 0, 2, 16, 8)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 2, 16, 0)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 2, 16, 33)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 2, 16, 12)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 2, 33, 8)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 2, 0, 8)),
     ],
 )
 def test_init_rejects_invalid_arguments(lib, kw):

@@ -1,0 +1,96 @@
+"""Frequency-domain operator O_F inside the learned step, sm_103a vs the FP64 oracle.
+
+The operator runs in FP32 (no BF16 rounding), so the learned step with O_F is held
+to the learned step's tolerance (relative L2 <= 1e-4 per step, the BF16 network's
+share dominating) and is checked to differ from the step without O_F by far more
+than that.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2507_01975_gb300 import fd
+from paper_2507_01975_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_01975_gb300 import build
+
+    build.build()
+    fd.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def model(seed, fno):
+    st = I.random_conv_stack(seed, 2, O.CNN_HIDDEN, O.N_COEF, last_scale=0.5)
+    return O.LearnedModel(W_L=I.random_wl(seed + 2, 1e-3), stencil=st,
+                          fno=None if fno is None else O.FNOParams(**fno))
+
+
+def run(n, b, m, fno, steps, forcing=None, dt=2e-3):
+    layers, modes, width = (0, 0, 0) if fno is None else (len(fno["R"]), fno["R"][0].shape[1], fno["P_w"].shape[0])
+    cfg = fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=dt, learned=True, forcing=forcing,
+                    fno_layers=layers, fno_modes=modes, fno_width=width)
+    s = fd.Solver(cfg)
+    s.set_params(I.pack_params(m.W_L, m.stencil, None, fno))
+    kind = "kolmogorov" if forcing else "decaying"
+    U0 = I.ic_batch(kind, n, b, seed0=3).astype(np.float32)
+    u = torch.tensor(U0, device="cuda")
+    out = torch.empty_like(u)
+    s.rollout(u, out, steps)
+    torch.cuda.synchronize()
+    return s, U0.astype(np.float64), out.double().cpu().numpy()
+
+
+def oracle(n, U0, m, steps, forcing=None, dt=2e-3):
+    p = O.Problem(nx=n, ny=n, nu=1e-3, dt=dt, forcing_kind=1 if forcing else 0)
+    return np.stack([O.rollout(U0[k], p, steps, model=m)[0] for k in range(U0.shape[0])])
+
+
+@pytest.mark.parametrize("n,modes,width,layers", [(64, 32, 16, 6), (64, 16, 8, 4), (32, 16, 8, 2)])
+def test_learned_step_with_frequency_operator_matches_oracle(n, modes, width, layers):
+    fno = I.random_fno(21, width, modes, layers, out_scale=0.5)
+    m = model(5, fno)
+    s, U0, g = run(n, 2, m, fno, 1, forcing="kolmogorov")
+    counts = 80 + 241_248
+    C = width
+    assert s.param_count() == counts + 3 * C + layers * (2 * modes * modes * C * C * 2 + C * C + C) + 8 * C + 8
+    ref = oracle(n, U0, m, 1, forcing="kolmogorov")
+    assert rel_l2(g, ref) <= 1e-4, rel_l2(g, ref)
+    # O_F is live: without it the step differs by far more than the tolerance
+    without = oracle(n, U0, model(5, None), 1, forcing="kolmogorov")
+    assert rel_l2(without, ref) > 20 * rel_l2(g, ref)
+    s.close()
+
+
+def test_frequency_operator_rollout_and_zero_output():
+    n = 64
+    fno = I.random_fno(22, 16, 32, 6, out_scale=0.05)
+    m = model(6, fno)
+    s, U0, g = run(n, 2, m, fno, 10)
+    ref = oracle(n, U0, m, 10)
+    assert rel_l2(g, ref) <= 1e-3, rel_l2(g, ref)
+    s.close()
+    # Q = 0: the operator adds exact zeros, so the step equals the step without it
+    zero = dict(fno, Q_w=np.zeros_like(fno["Q_w"]), Q_b=np.zeros_like(fno["Q_b"]))
+    s1, _, a = run(n, 2, model(6, zero), zero, 3)
+    s2, _, b = run(n, 2, model(6, None), None, 3)
+    assert np.array_equal(a, b)
+    # no reverse mode for the operator in this build
+    u = torch.zeros((2, 2, n, n), device="cuda")
+    with pytest.raises(fd.FdError) as e:
+        s1.step_adjoint(u, u, torch.empty_like(u))
+    assert e.value.status == fd.FD_EUNSUPPORTED
+    s1.close()
+    s2.close()

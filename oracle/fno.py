@@ -19,6 +19,10 @@ rows ky in [0, M) and [N - M, N), each row block with its own weights (M <= N/2)
 Q maps to one channel per face-operator instance (the eight of the flux block,
 in the order of fv.INSTANCES), whose value at index (j, i) is added to that
 instance's face value at (j, i).
+
+The same operator with 2 k_c input channels (the last k_c states, component c
+of state s as channel 2 s + c) and 2 output channels is the paper's temporal
+correction (Sec. 3.5; Table S3: 4 layers, 32 modes, width 8).
 """
 
 from __future__ import annotations
@@ -32,9 +36,10 @@ from .fv import gelu
 
 @dataclass
 class FNOParams:
-    """``P_w[width, 2]``, ``P_b[width]``; per layer ``R[l][2M, M, width_in, width_out]``
+    """``P_w[width, c_in]``, ``P_b[width]``; per layer ``R[l][2M, M, width_in, width_out]``
     (complex; rows 0 .. M-1 for ky = 0 .. M-1, rows M .. 2M-1 for ky = N-M .. N-1),
-    ``W[l][width_out, width_in]``, ``Wb[l][width]``; ``Q_w[8, width]``, ``Q_b[8]``."""
+    ``W[l][width_out, width_in]``, ``Wb[l][width]``; ``Q_w[c_out, width]``, ``Q_b[c_out]``
+    (c_in = 2, c_out = 8 for O_F; c_in = 2 k_c, c_out = 2 for the temporal correction)."""
 
     P_w: np.ndarray
     P_b: np.ndarray
@@ -76,7 +81,9 @@ def spectral_conv(v: np.ndarray, R: np.ndarray) -> np.ndarray:
 
 
 def fno_forward(U: np.ndarray, prm: FNOParams) -> np.ndarray:
-    """O_F(u): the eight face-value corrections [8, N, N] for the state U[2, N, N]."""
+    """The operator on U[c_in, N, N]: for O_F the eight face-value corrections
+    [8, N, N] of the state U[2, N, N]; for the temporal correction the correction
+    [2, N, N] of the stacked history U[2 k_c, N, N]."""
     v = pointwise(prm.P_w, prm.P_b, U)
     for l in range(prm.layers):
         v = spectral_conv(v, prm.R[l]) + pointwise(prm.W[l], prm.Wb[l], v)

@@ -433,6 +433,9 @@ class LearnedModel:
     ``q * 20 + r * 4 + c``).
     ``tc``: list of six ``(W, b)`` layers, 2 k_c -> 64 x5 -> 2, the temporal
     correction network (Sec. 3.5); empty or k_c == 0 disables it.
+    ``tc_fno``: the temporal correction as a Fourier neural operator instead
+    (the paper's form, Sec. 3.5 and Table S3): ``oracle.fno.FNOParams`` with
+    2 k_c input and 2 output channels; when set it replaces ``tc``.
     ``fno``: the frequency-domain operator O_F (``oracle.fno``), whose eight
     output channels add to the eight instances' face values; None disables it.
     Learned derivative parts are dimensionless and divided by the spacing
@@ -445,6 +448,8 @@ class LearnedModel:
     k_c: int = 0
     #: frequency-domain operator O_F (oracle.fno.FNOParams) or None
     fno: object = None
+    #: FNO temporal correction (oracle.fno.FNOParams, 2 k_c -> 2 channels) or None
+    tc_fno: object = None
 
 
 def learned_kernels(U: np.ndarray, p: Problem, model: LearnedModel) -> list:
@@ -481,7 +486,12 @@ def temporal_correction(U: np.ndarray, hist: Sequence[np.ndarray], p: Problem,
     Navier-Stokes, the corrected field is projected.
     """
     x = np.concatenate([h for h in hist], axis=0)
-    c = cnn_forward(x, model.tc)
+    if model.tc_fno is not None:
+        from .fno import fno_forward
+
+        c = fno_forward(x, model.tc_fno)
+    else:
+        c = cnn_forward(x, model.tc)
     c = c - c.mean(axis=(1, 2), keepdims=True)
     out = U + c
     return project(out, p) if p.flow == FLOW_NAVIER_STOKES else out

@@ -106,3 +106,39 @@ def test_operator_in_the_flux_block():
     assert np.abs(with_f - base).max() > 1e-6
     for c in range(2):
         assert abs(with_f[c].sum() - U[c].sum()) < 1e-12 * np.abs(U[c]).sum()
+
+
+def test_temporal_correction_operator():
+    """The FNO temporal correction (Sec. 3.5): 2 k_c -> 2 channels. With zero
+    spectral weights it is a chain of pointwise maps (brute force over the
+    history channels); the corrected state keeps the mean momentum and is
+    divergence-free; Q = 0 leaves a divergence-free state unchanged."""
+    rng = np.random.default_rng(10)
+    n, kc, width = 8, 3, 3
+    prm = random_fno(rng, width=width, modes=2, layers=2)
+    prm.P_w = rng.standard_normal((width, 2 * kc)) * 0.3
+    prm.Q_w = rng.standard_normal((2, width)) * 0.3
+    prm.Q_b = rng.standard_normal(2) * 0.01
+    hist = [rng.standard_normal((2, n, n)) for _ in range(kc)]
+    zero_r = FNOParams(**{**prm.__dict__, "R": [np.zeros_like(r) for r in prm.R]})
+    out = fno_forward(np.concatenate(hist), zero_r)
+    for y, x in ((0, 0), (3, 5), (7, 2)):
+        v = [sum(prm.P_w[o, 2 * s + c] * hist[s][c, y, x] for s in range(kc) for c in range(2)) + prm.P_b[o]
+             for o in range(width)]
+        for l in range(2):
+            v = [sum(prm.W[l][o, i] * v[i] for i in range(width)) + prm.Wb[l][o] for o in range(width)]
+            if l == 0:
+                v = [float(O.gelu(np.array(t))) for t in v]
+        for q in range(2):
+            ref = sum(prm.Q_w[q, i] * v[i] for i in range(width)) + prm.Q_b[q]
+            assert abs(out[q, y, x] - ref) < 1e-12
+    p = O.Problem(nx=n, ny=n, nu=1e-3, dt=2e-3)
+    U = O.project(rng.standard_normal((2, n, n)), p)
+    m = _model(np.random.default_rng(2), None)
+    m.k_c, m.tc_fno = kc, prm
+    V = O.temporal_correction(U, hist, p, m)
+    assert np.abs(V.mean(axis=(1, 2)) - U.mean(axis=(1, 2))).max() < 1e-13
+    assert np.abs(O.divergence(V, p.dx, p.dy)).max() < 1e-11
+    assert np.abs(V - U).max() > 1e-3
+    m.tc_fno = FNOParams(**{**prm.__dict__, "Q_w": np.zeros_like(prm.Q_w), "Q_b": np.zeros_like(prm.Q_b)})
+    assert np.abs(O.temporal_correction(U, hist, p, m) - U).max() < 1e-13

@@ -95,6 +95,11 @@ typedef struct {
                              (the reverse-mode calls refuse a context that has it) */
   int32_t fno_modes;      /* kept Fourier modes M per axis, 1 <= M <= N/2 (Table S3: 16 or 32) */
   int32_t fno_width;      /* channels of the Fourier layers: 8 or 16 (the widths of Table S3) */
+  int32_t tc_fno_layers;  /* temporal correction as a Fourier neural operator (Sec. 3.5; Table S3:
+                             4 layers, 32 modes, width 8) instead of the CNN head: Fourier layers,
+                             0 = CNN head (default); needs k_c > 0 */
+  int32_t tc_fno_modes;   /* its kept modes per axis, 1 <= M <= N/2 */
+  int32_t tc_fno_width;   /* its channels: 8 or 16 */
 } fd_options;
 
 typedef struct fd_ctx fd_ctx; /* opaque, library-owned */
@@ -161,7 +166,10 @@ int32_t fd_last_launch_count(const fd_ctx* ctx);
  *                    4 v-x-interp, 5 v-x-deriv, 6 v-y-interp, 7 v-y-deriv)
  *   temporal correction (only when k_c > 0): layers as above with
  *                   (Cin, Cout) = (2 k_c, 64) (64,64) x4 (64, 2); input channel
- *                   2 s + c is component c of u_{k-k_c+s}.
+ *                   2 s + c is component c of u_{k-k_c+s}. With tc_fno_layers > 0
+ *                   instead a Fourier neural operator in the layout of O_F below
+ *                   with P_w[C][2 k_c] (same input channels) and Q_w[2][C],
+ *                   Q_b[2] (width, modes and layers from the tc_fno_* options).
  *   frequency-domain operator O_F (only when fno_layers = L > 0; width C,
  *                   modes M): P_w[C][2], P_b[C]; per layer R[2M][M][C][C][2]
  *                   (complex channel matrices [in][out] of the kept modes, real

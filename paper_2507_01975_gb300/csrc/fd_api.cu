@@ -161,7 +161,7 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown flow");
   if (!(dt > 0) || !std::isfinite(dt)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: dt must be positive");
   if (!(nu >= 0) || !std::isfinite(nu)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
-  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0};
+  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (o.deriv_order != 2 && o.deriv_order != 4)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
@@ -185,6 +185,17 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
       return fd_set_error(nullptr, FD_EINVAL, "fd_init: fno_modes must be in [1, N/2]");
   } else {
     o.fno_modes = o.fno_width = 0;
+  }
+  if (o.tc_fno_layers < 0 || o.tc_fno_layers > 8)
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: tc_fno_layers must be in [0, 8]");
+  if (o.tc_fno_layers > 0) {
+    if (o.k_c <= 0) return fd_set_error(nullptr, FD_EINVAL, "fd_init: the FNO temporal correction needs k_c > 0");
+    if (o.tc_fno_width != 8 && o.tc_fno_width != 16)
+      return fd_set_error(nullptr, FD_EINVAL, "fd_init: tc_fno_width must be 8 or 16");
+    if (o.tc_fno_modes < 1 || 2 * o.tc_fno_modes > g.nx)
+      return fd_set_error(nullptr, FD_EINVAL, "fd_init: tc_fno_modes must be in [1, N/2]");
+  } else {
+    o.tc_fno_modes = o.tc_fno_width = 0;
   }
   int logn = 0;
   while ((1 << logn) < g.nx) ++logn;

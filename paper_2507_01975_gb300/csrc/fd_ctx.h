@@ -69,6 +69,10 @@ struct LearnedState {
   float2* fno_s = nullptr;     // kept modes [batch][width][2M][M]
   float2* fno_s2 = nullptr;    // mixed modes
   float* fno_out = nullptr;    // O_F(u) [batch][8][N][N]
+  // temporal correction as a Fourier neural operator (tcf_layers > 0, k_c > 0):
+  // 2 k_c -> 2 channels into corr; shares the O_F scratch above
+  int tcf_layers = 0, tcf_modes = 0, tcf_width = 0;
+  size_t raw_off_tcf = 0;
 };
 
 // Workspace of the reverse mode of one step (allocated by the first

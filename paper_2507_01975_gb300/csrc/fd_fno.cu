@@ -6,6 +6,8 @@
 // are pointwise channel maps, R_l a complex channel matrix per kept Fourier mode
 // (kx < M, ky in [0, M) or [N - M, N)). Its eight output channels are added to
 // the eight face-operator instances' face values by the learned flux kernel.
+// The same operator with the last k_c states as 2 k_c input channels and two
+// output channels is the temporal correction (Sec. 3.5; Table S3).
 // Per evaluation: lift, per layer {real 2D FFT of every (trajectory, channel)
 // field keeping the M-mode blocks, per-mode channel mixing, inverse real 2D
 // FFT with numpy's irfft2 semantics, pointwise map + bias + GELU}, projection:
@@ -23,19 +25,36 @@ namespace {
 
 __device__ __forceinline__ float gelu_exact(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
-// v[b][o][p] = sum_i P_w[o][i] u[b][i][p] + P_b[o]  (two input components)
+// v[b][o][p] = sum_i P_w[o][i] x[b][i][p] + P_b[o], x = the state (single, two
+// channels) or the ns states of hist stacked (channel 2 s + c = component c of
+// hist[s])
+constexpr int kFnoMaxIn = 16;
+
 template <int C>
-__global__ void __launch_bounds__(256) fno_lift_kernel(const float* __restrict__ u, const float* __restrict__ pw,
-                                                      const float* __restrict__ pb, float* __restrict__ v,
+__global__ void __launch_bounds__(256) fno_lift_kernel(const float* __restrict__ single,
+                                                      const float* const* __restrict__ hist, int ns,
+                                                      const float* __restrict__ pw, float* __restrict__ v,
                                                       int batch, int nn) {
+  __shared__ float sw[C * kFnoMaxIn + C];
+  const int cin = 2 * ns;
+  for (int k = threadIdx.x; k < C * cin + C; k += blockDim.x) sw[k] = pw[k];  // P_w[C][cin], then P_b[C]
   pdl_wait();
   pdl_trigger();
+  __syncthreads();
   const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (e >= (size_t)batch * nn) return;
   const size_t b = e / nn, p = e - b * nn;
-  const float u0 = u[b * 2 * nn + p], u1 = u[b * 2 * nn + nn + p];
+  float acc[C];
 #pragma unroll
-  for (int o = 0; o < C; ++o) v[(b * C + o) * nn + p] = pw[2 * o] * u0 + pw[2 * o + 1] * u1 + pb[o];
+  for (int o = 0; o < C; ++o) acc[o] = sw[C * cin + o];
+  for (int st = 0; st < ns; ++st) {
+    const float* src = single ? single : hist[st];
+    const float u0 = src[b * 2 * nn + p], u1 = src[b * 2 * nn + nn + p];
+#pragma unroll
+    for (int o = 0; o < C; ++o) acc[o] += sw[o * cin + 2 * st] * u0 + sw[o * cin + 2 * st + 1] * u1;
+  }
+#pragma unroll
+  for (int o = 0; o < C; ++o) v[(b * C + o) * nn + p] = acc[o];
 }
 
 // out[b][o][p] = act(add[b][o][p] + sum_i W[o][i] v[b][i][p] + bias[o]), one pixel
@@ -265,23 +284,34 @@ __global__ void __launch_bounds__(FnoFftCfg<LOGN>::NT) fno_irfft_kernel(const fl
     }
 }
 
-template <int LOGN, int C>
-cudaError_t fno_run(LearnedState& L, const float* u, const float2* tw, int batch, cudaStream_t st) {
+// one Fourier neural operator: width C, `layers` layers of `modes` kept modes,
+// parameters at raw_off (P_w[C][cin], P_b[C], layers, Q_w[cout][C], Q_b[cout]),
+// output [batch][cout][N][N]
+struct FnoNet {
+  int layers, modes, cout;
+  size_t raw_off;
+  float* out;
+};
+
+template <int LOGN, int C, int CO>
+cudaError_t fno_run(LearnedState& L, const FnoNet& net, const float* single, const float* const* hist, int ns,
+                    const float2* tw, int batch, cudaStream_t st) {
   using Cfg = FnoFftCfg<LOGN>;
   constexpr int N = Cfg::N;
-  const int M = L.fno_modes, nl = L.fno_layers;
+  const int M = net.modes, nl = net.layers, cin = 2 * ns;
   const int nn = N * N, nm = 2 * M * M;
   // fsm <= 35 KB (M <= N/2 <= 32): within the default dynamic shared-memory limit
   const size_t fsm = Cfg::smem(M);
-  const float* P = L.d_raw + L.raw_off_fno;
+  const float* P = L.d_raw + net.raw_off;
   const size_t layer_size = (size_t)nm * C * C * 2 + (size_t)C * C + C;
-  const float* Q = P + 3 * C + (size_t)nl * layer_size;
+  const float* R0 = P + (size_t)C * cin + C;
+  const float* Q = R0 + (size_t)nl * layer_size;
   const dim3 pix((unsigned)(((size_t)batch * nn + 255) / 256));
   const dim3 mix((nm + kMixModes - 1) / kMixModes, (batch + kMixBatch - 1) / kMixBatch);
-  cudaError_t e = launch_pdl(fno_lift_kernel<C>, pix, dim3(256), 0, st, u, P, P + 2 * C, L.fno_v[0], batch, nn);
+  cudaError_t e = launch_pdl(fno_lift_kernel<C>, pix, dim3(256), 0, st, single, hist, ns, P, L.fno_v[0], batch, nn);
   int cur = 0;
   for (int l = 0; l < nl && e == cudaSuccess; ++l) {
-    const float* R = P + 3 * C + (size_t)l * layer_size;
+    const float* R = R0 + (size_t)l * layer_size;
     const float* W = R + (size_t)nm * C * C * 2;
     const float* Wb = W + (size_t)C * C;
     e = launch_pdl(fno_rfft_kernel<LOGN>, dim3(C, batch), dim3(Cfg::NT), fsm, st, (const float*)L.fno_v[cur], L.fno_s,
@@ -298,9 +328,22 @@ cudaError_t fno_run(LearnedState& L, const float* u, const float2* tw, int batch
     cur ^= 1;
   }
   if (e == cudaSuccess)
-    e = launch_pdl(fno_pointwise_kernel<C, 8>, pix, dim3(256), 0, st, (const float*)nullptr,
-                   (const float*)L.fno_v[cur], Q, Q + 8 * C, L.fno_out, batch, nn, 0);
+    e = launch_pdl(fno_pointwise_kernel<C, CO>, pix, dim3(256), 0, st, (const float*)nullptr,
+                   (const float*)L.fno_v[cur], Q, Q + (size_t)CO * C, net.out, batch, nn, 0);
   return e;
+}
+
+template <int CO>
+cudaError_t fno_dispatch(fd_ctx* c, const FnoNet& net, int width, const float* single, const float* const* hist,
+                         int ns, cudaStream_t st) {
+  LearnedState& L = *c->lrn;
+  const float2* tw = reinterpret_cast<const float2*>(c->base.tw);
+  const int B = c->grid.batch;
+  if (c->logn == 6)
+    return width == 16 ? fno_run<6, 16, CO>(L, net, single, hist, ns, tw, B, st)
+                       : fno_run<6, 8, CO>(L, net, single, hist, ns, tw, B, st);
+  return width == 16 ? fno_run<5, 16, CO>(L, net, single, hist, ns, tw, B, st)
+                     : fno_run<5, 8, CO>(L, net, single, hist, ns, tw, B, st);
 }
 
 }  // namespace
@@ -310,11 +353,16 @@ int fd_fno_launches(int layers) { return layers > 0 ? 2 + 4 * layers : 0; }
 // O_F of the stage state u [batch][2][N][N] into c->lrn->fno_out [batch][8][N][N]
 cudaError_t fd_fno_forward(fd_ctx* c, const float* u, cudaStream_t st) {
   LearnedState& L = *c->lrn;
-  const float2* tw = reinterpret_cast<const float2*>(c->base.tw);
-  const int B = c->grid.batch;
-  if (c->logn == 6)
-    return L.fno_width == 16 ? fno_run<6, 16>(L, u, tw, B, st) : fno_run<6, 8>(L, u, tw, B, st);
-  return L.fno_width == 16 ? fno_run<5, 16>(L, u, tw, B, st) : fno_run<5, 8>(L, u, tw, B, st);
+  const FnoNet net{L.fno_layers, L.fno_modes, 8, L.raw_off_fno, L.fno_out};
+  return fno_dispatch<8>(c, net, L.fno_width, u, nullptr, 1, st);
+}
+
+// FNO temporal correction of the k_c states hist[0 .. k_c-1] (device pointer
+// array, oldest first) into c->lrn->corr [batch][2][N][N]
+cudaError_t fd_fno_tc(fd_ctx* c, const float* const* hist, cudaStream_t st) {
+  LearnedState& L = *c->lrn;
+  const FnoNet net{L.tcf_layers, L.tcf_modes, 2, L.raw_off_tcf, L.corr};
+  return fno_dispatch<2>(c, net, L.tcf_width, nullptr, hist, L.kc, st);
 }
 
 // kernel attributes (outside any stream capture): the mixing kernels' shared memory

@@ -19,8 +19,9 @@ using namespace ldfv;
 // frequency-domain operator O_F of one stage state (fd_fno.cu): writes L.fno_out
 cudaError_t fd_fno_forward(fd_ctx* c, const float* u, cudaStream_t st);
 int fd_fno_launches(int layers);
-int64_t fd_fno_param_count(int layers, int modes, int width);
+int64_t fd_fno_param_count(int layers, int modes, int width, int cin, int cout);
 cudaError_t fd_fno_prepare();
+cudaError_t fd_fno_tc(fd_ctx* c, const float* const* hist, cudaStream_t st);
 
 namespace {
 
@@ -30,6 +31,9 @@ namespace {
 // corrected projection
 constexpr int kLaunchesPerStep = 4 * (8 + 2);
 constexpr int kLaunchesTc = 7 + 1;
+
+// launches of one temporal correction (CNN head or FNO, plus the corrected projection)
+int tc_launches(const LearnedState& L) { return L.tcf_layers > 0 ? fd_fno_launches(L.tcf_layers) + 1 : kLaunchesTc; }
 
 thread_local const char* g_where = "";  // the launch group that failed last
 
@@ -147,7 +151,7 @@ cudaError_t learned_step(fd_ctx* c, const float* s_in, float* s_out, const float
     if (e != cudaSuccess) g_where = "flux / projection kernels";
   }
   if (e == cudaSuccess && tc_hist) {
-    e = run_tc_net<LOGN>(c, tc_hist, st);
+    e = L.tcf_layers > 0 ? fd_fno_tc(c, tc_hist, st) : run_tc_net<LOGN>(c, tc_hist, st);
     if (e == cudaSuccess) {
       a.corr = L.corr;
       a.wout = s_out;
@@ -242,7 +246,10 @@ void plan_layout(LearnedState& L, std::vector<PackDesc>& descs, std::vector<uint
     L.raw_off_sb[l] = off;
     off += stencil_cout(l);
   }
-  if (L.kc > 0)
+  if (L.kc > 0 && L.tcf_layers > 0) {  // FNO temporal correction: FP32, no rounding range
+    L.raw_off_tcf = off;
+    off += (size_t)fd_fno_param_count(L.tcf_layers, L.tcf_modes, L.tcf_width, 2 * L.kc, 2);
+  } else if (L.kc > 0)
     for (int l = 0; l < 6; ++l) {
       L.raw_off_tw[l] = off;
       ranges.push_back((uint32_t)off);
@@ -252,7 +259,7 @@ void plan_layout(LearnedState& L, std::vector<PackDesc>& descs, std::vector<uint
       off += tc_cout(l);
     }
   L.raw_off_fno = off;  // O_F parameters stay FP32 (no rounding range)
-  off += (size_t)fd_fno_param_count(L.fno_layers, L.fno_modes, L.fno_width);
+  off += (size_t)fd_fno_param_count(L.fno_layers, L.fno_modes, L.fno_width, 2, 8);
   L.raw_off_w0t = off;
   off += 2 * 64 * 9;
   L.raw_off_zero = off;
@@ -282,7 +289,7 @@ void plan_layout(LearnedState& L, std::vector<PackDesc>& descs, std::vector<uint
   for (int l = 1; l <= 4; ++l) L.pk_t[l - 1] = add(L.raw_off_sw[l], 64, 64, 64, 0, 64, 1);
   L.pk_t5 = add(L.raw_off_sw[5], kCoef, kCoef, 32, 0, 64, 1);
   add(L.raw_off_sw[5], kCoef, kCoef, 32, 32, 64, 1);
-  if (L.kc > 0) {
+  if (L.kc > 0 && L.tcf_layers == 0) {
     L.pk_tc_first = add(L.raw_off_tw[0], 2 * L.kc, 16, 64, 0, 2 * L.kc, 0);
     for (int l = 1; l <= 4; ++l) L.pk_tc[l - 1] = add(L.raw_off_tw[l], 64, 64, 64, 0, 64, 0);
   }
@@ -303,19 +310,22 @@ cudaError_t upload_params(LearnedState& L, const float* params, cudaStream_t st)
 // ---------------------------------------------------------------------------
 // entry points used by fd_api.cu
 // ---------------------------------------------------------------------------
-// parameters of the frequency-domain operator O_F (layout in include/fd.h)
-int64_t fd_fno_param_count(int layers, int modes, int width) {
+// parameters of a Fourier neural operator with cin inputs and cout outputs
+// (O_F: 2 -> 8; the FNO temporal correction: 2 k_c -> 2; layout in include/fd.h)
+int64_t fd_fno_param_count(int layers, int modes, int width, int cin, int cout) {
   if (layers <= 0) return 0;
   const int64_t c = width;
-  return c * 2 + c + (int64_t)layers * (2 * (int64_t)modes * modes * c * c * 2 + c * c + c) + 8 * c + 8;
+  return c * cin + c + (int64_t)layers * (2 * (int64_t)modes * modes * c * c * 2 + c * c + c) + cout * c + cout;
 }
 
-int64_t fd_learned_param_count(int kc, int fno_layers, int fno_modes, int fno_width) {
+int64_t fd_learned_param_count(const fd_options& o) {
   int64_t n = 80;
   for (int l = 0; l < 6; ++l) n += (int64_t)stencil_cout(l) * stencil_cin(l) * 9 + stencil_cout(l);
-  if (kc > 0)
-    for (int l = 0; l < 6; ++l) n += (int64_t)tc_cout(l) * tc_cin(l, kc) * 9 + tc_cout(l);
-  return n + fd_fno_param_count(fno_layers, fno_modes, fno_width);
+  if (o.k_c > 0 && o.tc_fno_layers > 0)
+    n += fd_fno_param_count(o.tc_fno_layers, o.tc_fno_modes, o.tc_fno_width, 2 * o.k_c, 2);
+  else if (o.k_c > 0)
+    for (int l = 0; l < 6; ++l) n += (int64_t)tc_cout(l) * tc_cin(l, o.k_c) * 9 + tc_cout(l);
+  return n + fd_fno_param_count(o.fno_layers, o.fno_modes, o.fno_width, 2, 8);
 }
 
 fd_status fd_learned_init(fd_ctx* c) {
@@ -331,7 +341,10 @@ fd_status fd_learned_init(fd_ctx* c) {
   L->fno_layers = c->opts.fno_layers;
   L->fno_modes = c->opts.fno_modes;
   L->fno_width = c->opts.fno_width;
-  L->nparams = fd_learned_param_count(L->kc, L->fno_layers, L->fno_modes, L->fno_width);
+  L->tcf_layers = c->opts.tc_fno_layers;
+  L->tcf_modes = c->opts.tc_fno_modes;
+  L->tcf_width = c->opts.tc_fno_width;
+  L->nparams = fd_learned_param_count(c->opts);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&L->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -353,15 +366,16 @@ fd_status fd_learned_init(fd_ctx* c) {
   alloc((void**)&L->ring, state * L->nring);
   alloc((void**)&L->d_err, sizeof(unsigned));
   alloc((void**)&L->d_ptrs, sizeof(float*) * (L->nring + 1 + 8 * L->nring));
-  if (L->fno_layers > 0) {
-    const size_t C = L->fno_width, M = L->fno_modes;
+  if (L->fno_layers > 0 || L->tcf_layers > 0) {  // scratch shared by O_F and the FNO temporal correction
+    const size_t C = L->fno_width > L->tcf_width ? L->fno_width : L->tcf_width;
+    const size_t M = L->fno_modes > L->tcf_modes ? L->fno_modes : L->tcf_modes;
     alloc((void**)&L->fno_v[0], B * C * NN * sizeof(float));
     alloc((void**)&L->fno_v[1], B * C * NN * sizeof(float));
     alloc((void**)&L->fno_y, B * C * NN * sizeof(float));
     alloc((void**)&L->fno_s, B * C * 2 * M * M * sizeof(float2));
     alloc((void**)&L->fno_s2, B * C * 2 * M * M * sizeof(float2));
-    alloc((void**)&L->fno_out, B * 8 * NN * sizeof(float));
   }
+  if (L->fno_layers > 0) alloc((void**)&L->fno_out, B * 8 * NN * sizeof(float));
   std::vector<PackDesc> descs;
   std::vector<uint32_t> ranges;
   plan_layout(*L, descs, ranges);
@@ -387,7 +401,7 @@ fd_status fd_learned_init(fd_ctx* c) {
     e = cudaMemcpy(L->d_ptrs, h.data(), sizeof(float*) * h.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = (g.nx == 64) ? prepare_kernels<6>() : prepare_kernels<5>();
-  if (e == cudaSuccess && L->fno_layers > 0) e = fd_fno_prepare();
+  if (e == cudaSuccess && (L->fno_layers > 0 || L->tcf_layers > 0)) e = fd_fno_prepare();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: learned workspace: %s", cudaGetErrorString(e));
   return FD_OK;
@@ -508,7 +522,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
   if (e == cudaSuccess && use_graph && L.graph) {
     for (; done + G <= n_steps && e == cudaSuccess; done += G) {
       e = cudaGraphLaunch(L.graph, st);
-      launches += G * (kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers)) + (L.kc > 0 ? kLaunchesTc : 0);
+      launches += G * (kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers)) + (L.kc > 0 ? tc_launches(L) : 0);
     }
   }
   // remaining steps (or every step when snapshots are requested): direct launches
@@ -516,7 +530,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
     const int r = done % G;
     const bool tc = L.kc > 0 && ((done + 1) % L.kc == 0);
     e = step_fn(r, tc, st);
-    launches += kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers) + (tc ? kLaunchesTc : 0);
+    launches += kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers) + (tc ? tc_launches(L) : 0);
     if (e == cudaSuccess && save_every > 0 && traj && ((done + 1) % save_every) == 0) {
       e = cudaMemcpyAsync(static_cast<float*>(traj) + (size_t)snap * slot, L.ring + (r + 1) * slot, bytes,
                           cudaMemcpyDeviceToDevice, st);

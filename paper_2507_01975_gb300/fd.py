@@ -85,6 +85,9 @@ class FdOptions(C.Structure):
         ("fno_layers", C.c_int32),
         ("fno_modes", C.c_int32),
         ("fno_width", C.c_int32),
+        ("tc_fno_layers", C.c_int32),
+        ("tc_fno_modes", C.c_int32),
+        ("tc_fno_width", C.c_int32),
     ]
 
 
@@ -211,6 +214,9 @@ class Config:
     fno_layers: int = 0  # frequency-domain operator O_F: Fourier layers (0 = off)
     fno_modes: int = 0
     fno_width: int = 0
+    tc_fno_layers: int = 0  # temporal correction as an FNO (0 = CNN head); needs k_c > 0
+    tc_fno_modes: int = 0
+    tc_fno_width: int = 0
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -237,7 +243,8 @@ class Solver:
                    FD_BURGERS if cfg.flow == "burgers" else FD_NAVIER_STOKES)
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
         o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26, cfg.path,
-                      cfg.fno_layers, cfg.fno_modes, cfg.fno_width)
+                      cfg.fno_layers, cfg.fno_modes, cfg.fno_width, cfg.tc_fno_layers, cfg.tc_fno_modes,
+                      cfg.tc_fno_width)
         h = C.c_void_p()
         st = self.lib.fd_init(C.byref(g), cfg.nu, cfg.dt, C.byref(f), C.byref(o), C.byref(h))
         if st != FD_OK:

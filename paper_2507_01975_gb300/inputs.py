@@ -168,12 +168,14 @@ def random_wl(seed: int, std: float = 1e-3) -> np.ndarray:
 
 
 def random_fno(seed: int, width: int, modes: int, layers: int, scale: float = 1.0,
-               out_scale: float = 0.01) -> dict:
-    """Seeded parameters of a frequency-domain operator (float32-representable
-    float64 arrays): P_w[width, 2], P_b[width]; per layer R[2M, M, width, width]
-    (complex), W[width, width], Wb[width]; Q_w[8, width], Q_b[8]. Weights are
+               out_scale: float = 0.01, cin: int = 2, cout: int = 8) -> dict:
+    """Seeded parameters of a Fourier neural operator (float32-representable
+    float64 arrays): P_w[width, cin], P_b[width]; per layer R[2M, M, width, width]
+    (complex), W[width, width], Wb[width]; Q_w[cout, width], Q_b[cout]. Weights are
     N(0, scale / sqrt(fan-in)) (the spectral ones also divided by the number of
-    kept modes), biases N(0, 0.02); Q is scaled by ``out_scale``."""
+    kept modes), biases N(0, 0.02); Q is scaled by ``out_scale``. The defaults
+    (cin 2, cout 8) are the frequency-domain operator O_F; (2 k_c, 2) is the
+    FNO temporal correction."""
     rng = np.random.default_rng(seed)
 
     def f32(a):
@@ -183,30 +185,38 @@ def random_fno(seed: int, width: int, modes: int, layers: int, scale: float = 1.
     R = [f32(rng.standard_normal((2 * m, m, width, width)) * scale / (width * m))
          + 1j * f32(rng.standard_normal((2 * m, m, width, width)) * scale / (width * m)) for _ in range(layers)]
     return {
-        "P_w": f32(rng.standard_normal((width, 2)) * scale / np.sqrt(2)),
+        "P_w": f32(rng.standard_normal((width, cin)) * scale / np.sqrt(cin)),
         "P_b": f32(rng.standard_normal(width) * 0.02),
         "R": R,
         "W": [f32(rng.standard_normal((width, width)) * scale / np.sqrt(width)) for _ in range(layers)],
         "Wb": [f32(rng.standard_normal(width) * 0.02) for _ in range(layers)],
-        "Q_w": f32(rng.standard_normal((8, width)) * out_scale / np.sqrt(width)),
-        "Q_b": f32(rng.standard_normal(8) * out_scale * 0.1),
+        "Q_w": f32(rng.standard_normal((cout, width)) * out_scale / np.sqrt(width)),
+        "Q_b": f32(rng.standard_normal(cout) * out_scale * 0.1),
     }
 
 
 def pack_params(W_L: np.ndarray, stencil, tc=None, fno=None) -> np.ndarray:
     """Flat float32 parameter array in the layout fd_set_params documents:
     W_L[2][2][5][4], then every stencil layer's W[Cout][Cin][3][3] and b[Cout],
-    then (optionally) every temporal-correction layer's weights and biases, then
-    (optionally) the frequency-domain operator: P_w, P_b, per layer R as
-    [2M][M][Cin][Cout][re, im], W[Cout][Cin], b, and Q_w, Q_b."""
+    then (optionally) the temporal correction: every CNN layer's weights and
+    biases (``tc`` a list of (W, b)) or a Fourier neural operator (``tc`` a dict
+    from random_fno), then (optionally) the frequency-domain operator. An operator
+    is P_w, P_b, per layer R as [2M][M][Cin][Cout][re, im], W[Cout][Cin], b, and
+    Q_w, Q_b."""
+    def operator(f):
+        out = [f["P_w"].ravel(), f["P_b"].ravel()]
+        for R, W, b in zip(f["R"], f["W"], f["Wb"]):
+            out += [np.stack([R.real, R.imag], axis=-1).ravel(), W.ravel(), b.ravel()]
+        return out + [f["Q_w"].ravel(), f["Q_b"].ravel()]
+
     parts = [np.asarray(W_L, dtype=np.float64).ravel()]
     for W, b in stencil:
         parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
-    for W, b in (tc or []):
-        parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
+    if isinstance(tc, dict):
+        parts += operator(tc)
+    else:
+        for W, b in (tc or []):
+            parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
     if fno is not None:
-        parts += [fno["P_w"].ravel(), fno["P_b"].ravel()]
-        for R, W, b in zip(fno["R"], fno["W"], fno["Wb"]):
-            parts += [np.stack([R.real, R.imag], axis=-1).ravel(), W.ravel(), b.ravel()]
-        parts += [fno["Q_w"].ravel(), fno["Q_b"].ravel()]
+        parts += operator(fno)
     return np.concatenate(parts).astype(np.float32)

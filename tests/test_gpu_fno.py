@@ -94,3 +94,47 @@ def test_frequency_operator_rollout_and_zero_output():
     assert e.value.status == fd.FD_EUNSUPPORTED
     s1.close()
     s2.close()
+
+
+def run_tc(n, b, m, tcf, fno, k_c, steps):
+    cfg = fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=2e-3, learned=True, forcing="kolmogorov", k_c=k_c,
+                    tc_fno_layers=len(tcf["R"]), tc_fno_modes=tcf["R"][0].shape[1], tc_fno_width=tcf["P_w"].shape[0],
+                    fno_layers=0 if fno is None else len(fno["R"]),
+                    fno_modes=0 if fno is None else fno["R"][0].shape[1],
+                    fno_width=0 if fno is None else fno["P_w"].shape[0])
+    s = fd.Solver(cfg)
+    s.set_params(I.pack_params(m.W_L, m.stencil, tcf, fno))
+    U0 = I.ic_batch("kolmogorov", n, b, seed0=4).astype(np.float32)
+    u = torch.tensor(U0, device="cuda")
+    out = torch.empty_like(u)
+    s.rollout(u, out, steps)
+    torch.cuda.synchronize()
+    return s, U0.astype(np.float64), out.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("n,k_c,tc_modes,tc_width,with_fno", [(64, 4, 32, 8, False), (64, 3, 32, 8, True),
+                                                             (32, 2, 16, 16, False)])
+def test_fno_temporal_correction_rollout_matches_oracle(n, k_c, tc_modes, tc_width, with_fno):
+    """The FNO temporal correction (Table S3: 4 layers, 32 modes, width 8) applied
+    after every k_c-th step; with O_F as well the two share scratch buffers."""
+    tcf = I.random_fno(23, tc_width, tc_modes, 4, out_scale=0.5, cin=2 * k_c, cout=2)
+    fno = I.random_fno(24, 16, 16, 2, out_scale=0.05) if with_fno else None
+    st = I.random_conv_stack(7, 2, O.CNN_HIDDEN, O.N_COEF, last_scale=0.5)
+    wl = I.random_wl(9, 1e-3)
+
+    def model(tc):
+        return O.LearnedModel(W_L=wl, stencil=st, k_c=k_c if tc else 0, tc_fno=O.FNOParams(**tcf) if tc else None,
+                              fno=None if fno is None else O.FNOParams(**fno))
+
+    steps = 2 * k_c
+    s, U0, g = run_tc(n, 2, model(True), tcf, fno, k_c, steps)
+    C = tc_width
+    base = 80 + 241_248 + (0 if fno is None else 3 * 16 + 2 * (2 * 16 * 16 * 16 * 16 * 2 + 16 * 16 + 16) + 8 * 16 + 8)
+    assert s.param_count() == base + C * 2 * k_c + C + 4 * (2 * tc_modes ** 2 * C * C * 2 + C * C + C) + 2 * C + 2
+    p = O.Problem(nx=n, ny=n, nu=1e-3, dt=2e-3, forcing_kind=1)
+    ref = np.stack([O.rollout(U0[k], p, steps, model=model(True))[0] for k in range(2)])
+    err = rel_l2(g, ref)
+    assert err <= 1e-3, err
+    without = np.stack([O.rollout(U0[k], p, steps, model=model(False))[0] for k in range(2)])
+    assert rel_l2(without, ref) > 20 * err
+    s.close()

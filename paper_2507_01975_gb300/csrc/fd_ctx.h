@@ -73,6 +73,10 @@ struct LearnedState {
   // 2 k_c -> 2 channels into corr; shares the O_F scratch above
   int tcf_layers = 0, tcf_modes = 0, tcf_width = 0;
   size_t raw_off_tcf = 0;
+  // channel matrices of both operators in the mixing kernel's mode-blocked layout
+  // (rebuilt from the raw parameters on every upload)
+  float2* fno_rp = nullptr;
+  float2* tcf_rp = nullptr;
 };
 
 // Workspace of the reverse mode of one step (allocated by the first

@@ -88,65 +88,106 @@ __global__ void __launch_bounds__(256) fno_pointwise_kernel(const float* __restr
   }
 }
 
-// S2[b][o][m] = sum_i R[m][i][o] S[b][i][m] (complex); R: [nm][C][C][2] floats.
-// A CTA takes 32 modes x 32 trajectories: the modes' channel matrices go to
-// shared memory once ([i][o][mode], padded), the spectra in slices of 8
-// trajectories ([b][i][mode]); lane = mode, so loads and stores run along the
-// contiguous mode index.
-constexpr int kMixModes = 32, kMixBatch = 32, kMixSlice = 8, kMixPad = 33;
+// S2[b][o][m] = sum_i R[m][i][o] S[b][i][m] (complex). The channel matrices come
+// in the mode-blocked layout Rp[m / 32][i][o][m % 32] (float2, built once per
+// parameter upload by fno_pack_r_kernel), so a warp loads a matrix entry of 32
+// consecutive modes in one coalesced access straight into registers. A CTA
+// takes 32 modes x 16 trajectories; the spectra follow in slices of 4
+// trajectories ([b][i][mode]), double-buffered with cp.async so the next slice
+// is in flight while the current one is mixed; lane = mode, so loads and stores
+// run along the contiguous mode index.
+constexpr int kMixModes = 32, kMixBatch = 16, kMixSlice = 4;
 
 template <int C>
 struct MixCfg {
-  static constexpr size_t SMEM = ((size_t)C * C * kMixPad + (size_t)kMixSlice * C * kMixModes) * sizeof(float2);
+  static constexpr int SLICE = kMixSlice * C * kMixModes;  // float2 per slice buffer
+  static constexpr size_t SMEM = 2 * (size_t)SLICE * sizeof(float2);
 };
 
+// R[m][i][o][re, im] (m < nm) -> Rp[m / 32][i][o][m % 32], zero for the modes past nm
+__global__ void fno_pack_r_kernel(const float* __restrict__ R, float2* __restrict__ Rp, int nm, int C) {
+  const int nb = (nm + kMixModes - 1) / kMixModes;
+  const size_t total = (size_t)nb * C * C * kMixModes;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int mm = (int)(q % kMixModes);
+    const size_t r = q / kMixModes;
+    const int io = (int)(r % ((size_t)C * C));
+    const int m = (int)(r / ((size_t)C * C)) * kMixModes + mm;
+    Rp[q] = m < nm ? make_float2(R[((size_t)m * C * C + io) * 2], R[((size_t)m * C * C + io) * 2 + 1])
+                   : make_float2(0.0f, 0.0f);
+  }
+}
+
+// 8-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <int C>
-__global__ void __launch_bounds__(256) fno_mix_kernel(const float2* __restrict__ S, const float* __restrict__ R,
+__global__ void __launch_bounds__(256) fno_mix_kernel(const float2* __restrict__ S, const float2* __restrict__ Rp,
                                                      float2* __restrict__ S2, int nm, int batch) {
-  extern __shared__ __align__(16) float2 smx[];
-  float2* Rs = smx;                          // [C * C][kMixPad]
-  float2* Ss = smx + C * C * kMixPad;        // [kMixSlice][C][kMixModes]
+  extern __shared__ __align__(16) float2 smx[];  // two slices [kMixSlice][C][kMixModes]
   const int m0 = blockIdx.x * kMixModes, b0 = blockIdx.y * kMixBatch;
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  // R[m0 + mm][i][o] -> Rs[(i C + o) kMixPad + mm]; consecutive threads read consecutive (i, o)
-  for (int e = threadIdx.x; e < C * C * kMixModes; e += blockDim.x) {
-    const int io = e % (C * C), mm = e / (C * C), m = m0 + mm;
-    const float* r = R + ((size_t)m * C * C + io) * 2;
-    Rs[io * kMixPad + mm] = m < nm ? make_float2(r[0], r[1]) : make_float2(0.0f, 0.0f);
-  }
-  pdl_wait();
-  pdl_trigger();
-  __syncthreads();
   // this thread's outputs o = grp + 8 j: their matrix columns in registers
   constexpr int NO = C / 8;
   float2 r[NO][C];
+  const float2* rb = Rp + (size_t)blockIdx.x * C * C * kMixModes;
 #pragma unroll
   for (int j = 0; j < NO; ++j)
 #pragma unroll
-    for (int i = 0; i < C; ++i) r[j][i] = Rs[(i * C + grp + 8 * j) * kMixPad + lane];
-  const int m = m0 + lane;
-  for (int bt = 0; bt < kMixBatch; bt += kMixSlice) {
-    if (bt > 0) __syncthreads();  // the previous slice is consumed
-    for (int e = threadIdx.x; e < kMixSlice * C * kMixModes; e += blockDim.x) {
+    for (int i = 0; i < C; ++i) r[j][i] = rb[(i * C + grp + 8 * j) * kMixModes + lane];
+  pdl_wait();
+  pdl_trigger();
+  auto issue = [&](int sl) {
+    float2* dst = smx + (sl & 1) * MixCfg<C>::SLICE;
+    for (int e = threadIdx.x; e < MixCfg<C>::SLICE; e += blockDim.x) {
       const int mm = e % kMixModes, bi = e / kMixModes, bb = bi / C, i = bi % C;
-      const int b = b0 + bt + bb;
-      Ss[e] = (b < batch && m0 + mm < nm) ? S[((size_t)b * C + i) * nm + m0 + mm] : make_float2(0.0f, 0.0f);
+      const int b = b0 + sl * kMixSlice + bb;
+      const bool ok = b < batch && m0 + mm < nm;
+      cp_async8(dst + e, ok ? (const void*)(S + ((size_t)b * C + i) * nm + m0 + mm) : (const void*)S, ok ? 8 : 0);
     }
-    __syncthreads();
-#pragma unroll 2
+    cp_async_commit();
+  };
+  constexpr int NSL = kMixBatch / kMixSlice;
+  issue(0);
+  const int m = m0 + lane;
+  for (int sl = 0; sl < NSL; ++sl) {
+    if (b0 + sl * kMixSlice >= batch) break;  // uniform over the CTA; nothing left in flight
+    if (sl + 1 < NSL && b0 + (sl + 1) * kMixSlice < batch) {
+      issue(sl + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // slice sl visible to every thread
+    const float2* cur = smx + (sl & 1) * MixCfg<C>::SLICE;
+#pragma unroll
     for (int bb = 0; bb < kMixSlice; ++bb) {
       float2 sv[C];
 #pragma unroll
-      for (int i = 0; i < C; ++i) sv[i] = Ss[(bb * C + i) * kMixModes + lane];
-      const int b = b0 + bt + bb;
+      for (int i = 0; i < C; ++i) sv[i] = cur[(bb * C + i) * kMixModes + lane];
+      const int b = b0 + sl * kMixSlice + bb;
 #pragma unroll
       for (int j = 0; j < NO; ++j) {
-        float2 acc = make_float2(0.0f, 0.0f);
+        float re = 0.0f, im = 0.0f;
 #pragma unroll
-        for (int i = 0; i < C; ++i) acc = c2add(acc, c2mul(sv[i], r[j][i]));
-        if (b < batch && m < nm) S2[((size_t)b * C + grp + 8 * j) * nm + m] = acc;
+        for (int i = 0; i < C; ++i) {
+          re = fmaf(sv[i].x, r[j][i].x, re);
+          re = fmaf(-sv[i].y, r[j][i].y, re);
+          im = fmaf(sv[i].x, r[j][i].y, im);
+          im = fmaf(sv[i].y, r[j][i].x, im);
+        }
+        if (b < batch && m < nm) S2[((size_t)b * C + grp + 8 * j) * nm + m] = make_float2(re, im);
       }
     }
+    __syncthreads();  // slice sl consumed before its buffer is refilled
   }
 }
 
@@ -156,9 +197,18 @@ struct FnoFftCfg {
   static constexpr int NTR = N / 2;  // row transforms (pairs of real rows); also >= the kept columns
   static constexpr int NT = NTR * T;
   static_assert(T < 64, "transform syncs are warp-level here");
-  static size_t smem(int M) {
-    return ((size_t)NTR * SPlan<LOGN>::BUF + SPlan<LOGN>::TW + (size_t)N * M) * sizeof(float2);
-  }
+  // per-transform buffer stride (float2): >= fpad(N - 1) + 1 and = T mod 16, so the
+  // 16 / T transforms of a half-warp start on different banks
+  static constexpr int FBUF = ((N + N / 16 + 15 - T) / 16) * 16 + T;
+  static_assert(FBUF >= N + N / 16 && FBUF % 16 == T, "transform buffer stride");
+  // row stride of the [N][M] mode staging: >= M and = 2 mod 8 (the rows written
+  // by a half-warp's transforms fall on different banks)
+  static __host__ __device__ int rs(int M) { return ((M + 5) & ~7) + 2; }
+  static size_t smem(int M) { return ((size_t)NTR * FBUF + SPlan<LOGN>::TW + (size_t)N * rs(M)) * sizeof(float2); }
+  // the real field passes through the transform buffers as [N][FS] floats: rows
+  // 2f, 2f + 1 of the 16 / T transforms of a half-warp fall on different banks
+  static constexpr int FS = N + 2;
+  static_assert((size_t)N * FS <= (size_t)NTR * FBUF * 2, "field staging fits the transform buffers");
 };
 
 // row index of ky among the kept rows (-1 when not kept)
@@ -176,35 +226,51 @@ __global__ void __launch_bounds__(FnoFftCfg<LOGN>::NT) fno_rfft_kernel(const flo
   using SP = SPlan<LOGN>;
   constexpr int N = Cfg::N, T = Cfg::T, MSK = N - 1;
   extern __shared__ __align__(16) float2 sm[];
-  float2* tws = sm + Cfg::NTR * SP::BUF;
-  float2* Rs = tws + SP::TW;  // [N][M] row spectra
+  float2* tws = sm + Cfg::NTR * Cfg::FBUF;
+  float2* Rs = tws + SP::TW;  // [N][rs] row spectra
+  const int RS = Cfg::rs(M);
   const int f = threadIdx.x / T, t = threadIdx.x % T;
   const int C = gridDim.x, b = blockIdx.y, c = blockIdx.x;
   const size_t NN = (size_t)N * N;
   const float* field = v + ((size_t)b * C + c) * NN;
-  float2* buf = sm + f * SP::BUF;
+  float2* buf = sm + f * Cfg::FBUF;
   const TransformSync sync{1 + f, T};
   build_pass_twiddles<LOGN>(tws, tw);
   pdl_wait();
   pdl_trigger();
-  // rows 2f and 2f + 1 as one complex transform
+  // the field through shared memory ([N][FS] floats over the transform buffers):
+  // coalesced 16-byte global loads, then rows 2f and 2f + 1 as one complex transform
+  float* fs = reinterpret_cast<float*>(sm);
+  constexpr int NQ = N * N / 4 / Cfg::NT;  // 16-byte loads per thread, all in flight before the first store
+  static_assert(NQ * Cfg::NT * 4 == N * N, "the field splits evenly over the threads");
+  float4 w[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) w[k] = reinterpret_cast<const float4*>(field)[threadIdx.x + k * Cfg::NT];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const int q = threadIdx.x + k * Cfg::NT, row = q / (N / 4), col = 4 * (q % (N / 4));
+    *reinterpret_cast<float2*>(fs + row * Cfg::FS + col) = make_float2(w[k].x, w[k].y);
+    *reinterpret_cast<float2*>(fs + row * Cfg::FS + col + 2) = make_float2(w[k].z, w[k].w);
+  }
+  __syncthreads();
   float2 z[kFP];
 #pragma unroll
-  for (int m = 0; m < kFP; ++m) z[m] = make_float2(field[(2 * f) * N + t + m * T], field[(2 * f + 1) * N + t + m * T]);
+  for (int m = 0; m < kFP; ++m)
+    z[m] = make_float2(fs[(2 * f) * Cfg::FS + t + m * T], fs[(2 * f + 1) * Cfg::FS + t + m * T]);
   __syncthreads();
   fft_forward<LOGN>(z, buf, tws, t, sync);
   fft_store_natural<LOGN>(buf, z, t);
   sync();
   for (int k = t; k < M; k += T) {
     const float2 zk = buf[fpad(k)], zm = buf[fpad((N - k) & MSK)];
-    Rs[(2 * f) * M + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    Rs[(2 * f + 1) * M + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    Rs[(2 * f) * RS + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    Rs[(2 * f + 1) * RS + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
   __syncthreads();
   // column kx = f (kept when f < M; the others run on column 0 and discard)
   const int kx = f < M ? f : 0;
 #pragma unroll
-  for (int m = 0; m < kFP; ++m) z[m] = Rs[(t + m * T) * M + kx];
+  for (int m = 0; m < kFP; ++m) z[m] = Rs[(t + m * T) * RS + kx];
   fft_forward<LOGN>(z, buf, tws, t, sync);
   if (f < M) {
     float2* out = S + ((size_t)b * C + c) * 2 * M * M;
@@ -228,13 +294,14 @@ __global__ void __launch_bounds__(FnoFftCfg<LOGN>::NT) fno_irfft_kernel(const fl
   using SP = SPlan<LOGN>;
   constexpr int N = Cfg::N, T = Cfg::T, H = N / 2;
   extern __shared__ __align__(16) float2 sm[];
-  float2* tws = sm + Cfg::NTR * SP::BUF;
-  float2* Rs = tws + SP::TW;  // [N][M] rows after the inverse column transforms
+  float2* tws = sm + Cfg::NTR * Cfg::FBUF;
+  float2* Rs = tws + SP::TW;  // [N][rs] rows after the inverse column transforms
+  const int RS = Cfg::rs(M);
   const int f = threadIdx.x / T, t = threadIdx.x % T;
   const int C = gridDim.x, b = blockIdx.y, c = blockIdx.x;
   const size_t NN = (size_t)N * N;
   const float2* in = S2 + ((size_t)b * C + c) * 2 * M * M;
-  float2* buf = sm + f * SP::BUF;
+  float2* buf = sm + f * Cfg::FBUF;
   const TransformSync sync{1 + f, T};
   build_pass_twiddles<LOGN>(tws, tw);
   pdl_wait();
@@ -252,12 +319,12 @@ __global__ void __launch_bounds__(FnoFftCfg<LOGN>::NT) fno_irfft_kernel(const fl
 #pragma unroll
     for (int s = 0; s < SP::SL; ++s)
 #pragma unroll
-      for (int r = 0; r < SP::RL; ++r) Rs[(t + s * T + r * SP::NSL) * M + kx] = z[s + SP::SL * r];
+      for (int r = 0; r < SP::RL; ++r) Rs[(t + s * T + r * SP::NSL) * RS + kx] = z[s + SP::SL * r];
   }
   __syncthreads();
   // rows 2f, 2f + 1: Z_k = A_k + i B_k on the Hermitian extension of each row
-  const float2* A = Rs + (2 * f) * M;
-  const float2* Bv = Rs + (2 * f + 1) * M;
+  const float2* A = Rs + (2 * f) * RS;
+  const float2* Bv = Rs + (2 * f + 1) * RS;
 #pragma unroll
   for (int m = 0; m < kFP; ++m) {
     const int k = t + m * T;
@@ -273,15 +340,26 @@ __global__ void __launch_bounds__(FnoFftCfg<LOGN>::NT) fno_irfft_kernel(const fl
     z[m] = zz;
   }
   fft_inverse<LOGN>(z, buf, tws, t, sync);
-  float* out = y + ((size_t)b * C + c) * NN;
+  // rows 2f, 2f + 1 through shared memory ([N][FS] floats over the transform
+  // buffers, free once every transform is done), then coalesced 16-byte stores
+  float* fs = reinterpret_cast<float*>(sm);
+  __syncthreads();
 #pragma unroll
   for (int s = 0; s < SP::SL; ++s)
 #pragma unroll
     for (int r = 0; r < SP::RL; ++r) {
       const int x = t + s * T + r * SP::NSL;
-      out[(2 * f) * N + x] = z[s + SP::SL * r].x * scale;
-      out[(2 * f + 1) * N + x] = z[s + SP::SL * r].y * scale;
+      fs[(2 * f) * Cfg::FS + x] = z[s + SP::SL * r].x * scale;
+      fs[(2 * f + 1) * Cfg::FS + x] = z[s + SP::SL * r].y * scale;
     }
+  __syncthreads();
+  float* out = y + ((size_t)b * C + c) * NN;
+  for (int q = threadIdx.x; q < N * N / 4; q += Cfg::NT) {
+    const int row = q / (N / 4), col = 4 * (q % (N / 4));
+    const float2 lo = *reinterpret_cast<const float2*>(fs + row * Cfg::FS + col);
+    const float2 hi = *reinterpret_cast<const float2*>(fs + row * Cfg::FS + col + 2);
+    reinterpret_cast<float4*>(out)[q] = make_float4(lo.x, lo.y, hi.x, hi.y);
+  }
 }
 
 // one Fourier neural operator: width C, `layers` layers of `modes` kept modes,
@@ -291,6 +369,7 @@ struct FnoNet {
   int layers, modes, cout;
   size_t raw_off;
   float* out;
+  const float2* rp;  // mode-blocked channel matrices of every layer
 };
 
 template <int LOGN, int C, int CO>
@@ -307,7 +386,8 @@ cudaError_t fno_run(LearnedState& L, const FnoNet& net, const float* single, con
   const float* R0 = P + (size_t)C * cin + C;
   const float* Q = R0 + (size_t)nl * layer_size;
   const dim3 pix((unsigned)(((size_t)batch * nn + 255) / 256));
-  const dim3 mix((nm + kMixModes - 1) / kMixModes, (batch + kMixBatch - 1) / kMixBatch);
+  const int nb = (nm + kMixModes - 1) / kMixModes;
+  const dim3 mix(nb, (batch + kMixBatch - 1) / kMixBatch);
   cudaError_t e = launch_pdl(fno_lift_kernel<C>, pix, dim3(256), 0, st, single, hist, ns, P, L.fno_v[0], batch, nn);
   int cur = 0;
   for (int l = 0; l < nl && e == cudaSuccess; ++l) {
@@ -317,8 +397,8 @@ cudaError_t fno_run(LearnedState& L, const FnoNet& net, const float* single, con
     e = launch_pdl(fno_rfft_kernel<LOGN>, dim3(C, batch), dim3(Cfg::NT), fsm, st, (const float*)L.fno_v[cur], L.fno_s,
                    tw, M);
     if (e == cudaSuccess)
-      e = launch_pdl(fno_mix_kernel<C>, mix, dim3(256), MixCfg<C>::SMEM, st, (const float2*)L.fno_s, R, L.fno_s2, nm,
-                     batch);
+      e = launch_pdl(fno_mix_kernel<C>, mix, dim3(256), MixCfg<C>::SMEM, st, (const float2*)L.fno_s,
+                     (const float2*)(net.rp + (size_t)l * nb * C * C * kMixModes), L.fno_s2, nm, batch);
     if (e == cudaSuccess)
       e = launch_pdl(fno_irfft_kernel<LOGN>, dim3(C, batch), dim3(Cfg::NT), fsm, st, (const float2*)L.fno_s2, L.fno_y,
                      tw, M, 1.0f / (float)nn);
@@ -353,7 +433,7 @@ int fd_fno_launches(int layers) { return layers > 0 ? 2 + 4 * layers : 0; }
 // O_F of the stage state u [batch][2][N][N] into c->lrn->fno_out [batch][8][N][N]
 cudaError_t fd_fno_forward(fd_ctx* c, const float* u, cudaStream_t st) {
   LearnedState& L = *c->lrn;
-  const FnoNet net{L.fno_layers, L.fno_modes, 8, L.raw_off_fno, L.fno_out};
+  const FnoNet net{L.fno_layers, L.fno_modes, 8, L.raw_off_fno, L.fno_out, L.fno_rp};
   return fno_dispatch<8>(c, net, L.fno_width, u, nullptr, 1, st);
 }
 
@@ -361,8 +441,39 @@ cudaError_t fd_fno_forward(fd_ctx* c, const float* u, cudaStream_t st) {
 // array, oldest first) into c->lrn->corr [batch][2][N][N]
 cudaError_t fd_fno_tc(fd_ctx* c, const float* const* hist, cudaStream_t st) {
   LearnedState& L = *c->lrn;
-  const FnoNet net{L.tcf_layers, L.tcf_modes, 2, L.raw_off_tcf, L.corr};
+  const FnoNet net{L.tcf_layers, L.tcf_modes, 2, L.raw_off_tcf, L.corr, L.tcf_rp};
   return fno_dispatch<2>(c, net, L.tcf_width, nullptr, hist, L.kc, st);
+}
+
+// elements of the mode-blocked channel matrices of one operator (all layers)
+size_t fd_fno_rp_count(int layers, int modes, int width) {
+  const size_t nb = ((size_t)2 * modes * modes + kMixModes - 1) / kMixModes;
+  return (size_t)layers * nb * width * width * kMixModes;
+}
+
+// after a parameter upload: the channel matrices of O_F and of the FNO temporal
+// correction in the mode-blocked layout of the mixing kernel
+cudaError_t fd_fno_pack(LearnedState& L, cudaStream_t st) {
+  struct Op {
+    int layers, modes, width, cin;
+    size_t raw_off;
+    float2* rp;
+  };
+  const Op ops[2] = {{L.fno_layers, L.fno_modes, L.fno_width, 2, L.raw_off_fno, L.fno_rp},
+                     {L.tcf_layers, L.tcf_modes, L.tcf_width, 2 * L.kc, L.raw_off_tcf, L.tcf_rp}};
+  for (const Op& op : ops) {
+    if (op.layers <= 0) continue;
+    const int C = op.width, nm = 2 * op.modes * op.modes;
+    const size_t layer_size = (size_t)nm * C * C * 2 + (size_t)C * C + C;
+    const size_t per = fd_fno_rp_count(1, op.modes, C);
+    for (int l = 0; l < op.layers; ++l) {
+      const float* R = L.d_raw + op.raw_off + (size_t)C * op.cin + C + l * layer_size;
+      fno_pack_r_kernel<<<2 * L.sms, 256, 0, st>>>(R, op.rp + l * per, nm, C);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 // kernel attributes (outside any stream capture): the mixing kernels' shared memory

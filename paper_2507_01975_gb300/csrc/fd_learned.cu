@@ -22,6 +22,8 @@ int fd_fno_launches(int layers);
 int64_t fd_fno_param_count(int layers, int modes, int width, int cin, int cout);
 cudaError_t fd_fno_prepare();
 cudaError_t fd_fno_tc(fd_ctx* c, const float* const* hist, cudaStream_t st);
+size_t fd_fno_rp_count(int layers, int modes, int width);
+cudaError_t fd_fno_pack(LearnedState& L, cudaStream_t st);
 
 namespace {
 
@@ -302,7 +304,9 @@ cudaError_t upload_params(LearnedState& L, const float* params, cudaStream_t st)
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   pack_tiles_kernel<<<dim3(32, L.ndesc), 256, 0, st>>>(L.d_raw, L.d_wpack, reinterpret_cast<const PackDesc*>(L.d_desc));
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess && (L.fno_layers > 0 || L.tcf_layers > 0)) e = fd_fno_pack(L, st);
+  return e;
 }
 
 }  // namespace
@@ -375,7 +379,12 @@ fd_status fd_learned_init(fd_ctx* c) {
     alloc((void**)&L->fno_s, B * C * 2 * M * M * sizeof(float2));
     alloc((void**)&L->fno_s2, B * C * 2 * M * M * sizeof(float2));
   }
-  if (L->fno_layers > 0) alloc((void**)&L->fno_out, B * 8 * NN * sizeof(float));
+  if (L->fno_layers > 0) {
+    alloc((void**)&L->fno_out, B * 8 * NN * sizeof(float));
+    alloc((void**)&L->fno_rp, fd_fno_rp_count(L->fno_layers, L->fno_modes, L->fno_width) * sizeof(float2));
+  }
+  if (L->tcf_layers > 0)
+    alloc((void**)&L->tcf_rp, fd_fno_rp_count(L->tcf_layers, L->tcf_modes, L->tcf_width) * sizeof(float2));
   std::vector<PackDesc> descs;
   std::vector<uint32_t> ranges;
   plan_layout(*L, descs, ranges);
@@ -416,7 +425,7 @@ void fd_learned_free(fd_ctx* c) {
                 L->coef,   L->acc,     L->wbuf,    L->ws,             L->corr,            L->ring,
                 (void*)L->d_ptrs,
                 L->d_err,  L->fno_v[0], L->fno_v[1], L->fno_y,        L->fno_s,           L->fno_s2,
-                L->fno_out};
+                L->fno_out, L->fno_rp, L->tcf_rp};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete L;

@@ -450,20 +450,32 @@ class LearnedModel:
     fno: object = None
     #: FNO temporal correction (oracle.fno.FNOParams, 2 k_c -> 2 channels) or None
     tc_fno: object = None
+    #: ablation variant of the flux block (Sec. 4 ablation study, Table 4):
+    #: 0 the full operator, 1 without the physics-based convolution
+    #: (K = (W_L + C_theta) / h^deriv, no W_P and hence no consistency projection),
+    #: 2 the frequency-domain operator only (face values = O_F(u))
+    ablation: int = 0
 
 
 def learned_kernels(U: np.ndarray, p: Problem, model: LearnedModel) -> list:
-    """Per-face kernels K_f = W_P + proj(W_L + C_theta(u)_f) (Sec. 3.4, integrated operator)."""
-    C = cnn_forward(U, model.stencil)
+    """Per-face kernels K_f = W_P + proj(W_L + C_theta(u)_f) (Sec. 3.4, integrated operator).
+
+    Ablation 1 (without the physics-based convolution) drops W_P and with it the
+    consistency projection, whose job is to keep W_P's consistency: K_f = W_L +
+    C_theta(u)_f. Ablation 2 (frequency-domain operator only) has zero kernels."""
     ny, nx = U.shape[1:]
+    if model.ablation == 2:
+        return [np.zeros((5, 4, ny, nx)) for _ in INSTANCES]
+    C = cnn_forward(U, model.stencil)
     ks = []
     for q, (_fld, axis, kind, _shift) in enumerate(INSTANCES):
         h = p.dx if axis == 0 else p.dy
         L = model.W_L[kind, axis][:, :, None, None] + C[q * 20:(q + 1) * 20].reshape(5, 4, ny, nx)
-        L = consistency_project(L)
+        if model.ablation == 0:
+            L = consistency_project(L)
         if kind == 1:
             L = L / h
-        ks.append(physics_kernel(kind, p.deriv_order, h)[:, :, None, None] + L)
+        ks.append(L if model.ablation == 1 else physics_kernel(kind, p.deriv_order, h)[:, :, None, None] + L)
     return ks
 
 

@@ -142,3 +142,41 @@ def test_temporal_correction_operator():
     assert np.abs(V - U).max() > 1e-3
     m.tc_fno = FNOParams(**{**prm.__dict__, "Q_w": np.zeros_like(prm.Q_w), "Q_b": np.zeros_like(prm.Q_b)})
     assert np.abs(O.temporal_correction(U, hist, p, m) - U).max() < 1e-13
+
+
+def test_ablation_variants():
+    """The ablation variants of the flux block (Sec. 4, Table 4). Without the
+    physics-based convolution and with zero learned kernels the face values
+    vanish, so the step is pure forcing (plus projection); with only the
+    frequency-domain operator the face values are O_F(u) itself, checked
+    against face values assembled by hand; both keep the mean momentum."""
+    rng = np.random.default_rng(11)
+    n = 16
+    p = O.Problem(nx=n, ny=n, nu=1e-3, dt=2e-3, forcing_kind=0)
+    U = O.project(rng.standard_normal((2, n, n)) * 0.3, p)
+    zero = _model(np.random.default_rng(3), None)
+    zero.W_L = np.zeros_like(zero.W_L)
+    zero.ablation = 1  # the last network layer is zero: K = W_L + C = 0
+    for k in O.learned_kernels(U, p, zero):
+        assert np.abs(k).max() == 0.0
+    assert np.array_equal(O.learned_step(U, p, zero), O.project(U, p))
+    # without the physics conv the learned kernel is used as is (no projection)
+    m1 = _model(np.random.default_rng(3), None)
+    m1.ablation = 1
+    ks = O.learned_kernels(U, p, m1)
+    q = 1  # u-x derivative: W_L / h, no physics part, not projected
+    ref = m1.W_L[1, 0] / p.dx
+    assert np.abs(ks[q] - ref[:, :, None, None]).max() < 1e-14
+    # frequency operator only: tendency from the O_F face values alone
+    prm = random_fno(rng, width=4, modes=4, layers=2)
+    m2 = _model(np.random.default_rng(3), prm)
+    m2.ablation = 2
+    H = O.tendency(U, p, O.learned_kernels(U, p, m2), O.fno_forward(U, prm))
+    Uc, Gxc, Uk, Gyu, Vk, Gxv, Vc, Gyc = O.fno_forward(U, prm)
+    sh = O.shifted
+    Tu = (-(Uc**2 - sh(Uc**2, 0, -1)) / p.dx - (sh(Uk * Vk, 1, 0) - Uk * Vk) / p.dy
+          + p.nu * ((Gxc - sh(Gxc, 0, -1)) / p.dx + (sh(Gyu, 1, 0) - Gyu) / p.dy))
+    assert np.abs(H[0] - Tu).max() < 1e-12 * max(1.0, np.abs(Tu).max())
+    for m in (m1, m2):
+        V = O.learned_step(U, p, m)
+        assert np.abs(V.mean(axis=(1, 2)) - U.mean(axis=(1, 2))).max() < 1e-13

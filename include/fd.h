@@ -100,6 +100,12 @@ typedef struct {
                              0 = CNN head (default); needs k_c > 0 */
   int32_t tc_fno_modes;   /* its kept modes per axis, 1 <= M <= N/2 */
   int32_t tc_fno_width;   /* its channels: 8 or 16 */
+  int32_t ablation;       /* flux-block variant of the ablation study (Sec. 4, Table 4): 0 = the full
+                             operator (default); 1 = without the physics-based convolution: per-face
+                             kernels W_L + C_theta (derivative parts / h), no W_P and no consistency
+                             projection; 2 = the frequency-domain operator only: face values O_F(u)
+                             (needs fno_layers > 0; the stencil network does not run). Needs
+                             learned = 1; forward only (the reverse-mode calls refuse 1 and 2) */
 } fd_options;
 
 typedef struct fd_ctx fd_ctx; /* opaque, library-owned */

@@ -358,8 +358,10 @@ extern "C" {
 fd_status fd_step_adjoint(fd_ctx* c, const void* u_in, const void* lam_out, void* lam_in, float* dparams,
                           void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_step_adjoint: null context");
-  if (c->lrn && c->lrn->fno_layers > 0)
-    return fd_set_error(c, FD_EUNSUPPORTED, "fd_step_adjoint: the frequency-domain operator has no reverse mode in this build");
+  if (c->lrn && (c->lrn->fno_layers > 0 || c->lrn->ablation != 0))
+    return fd_set_error(c, FD_EUNSUPPORTED,
+                        "fd_step_adjoint: the frequency-domain operator and the ablation variants have no reverse mode "
+                        "in this build");
   c->launches = 0;
   if (!u_in || !lam_out || !lam_in) return fd_set_error(c, FD_EINVAL, "fd_step_adjoint: null state pointer");
   if (c->grid.dtype != FD_F32 || (c->grid.nx != 32 && c->grid.nx != 64))

@@ -161,7 +161,7 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown flow");
   if (!(dt > 0) || !std::isfinite(dt)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: dt must be positive");
   if (!(nu >= 0) || !std::isfinite(nu)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
-  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0};
+  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (o.deriv_order != 2 && o.deriv_order != 4)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
@@ -186,6 +186,10 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   } else {
     o.fno_modes = o.fno_width = 0;
   }
+  if (o.ablation < 0 || o.ablation > 2) return fd_set_error(nullptr, FD_EINVAL, "fd_init: ablation must be 0, 1 or 2");
+  if (o.ablation && !o.learned) return fd_set_error(nullptr, FD_EINVAL, "fd_init: ablation variants need learned = 1");
+  if (o.ablation == 2 && o.fno_layers <= 0)
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: the frequency-operator-only variant needs fno_layers > 0");
   if (o.tc_fno_layers < 0 || o.tc_fno_layers > 8)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: tc_fno_layers must be in [0, 8]");
   if (o.tc_fno_layers > 0) {

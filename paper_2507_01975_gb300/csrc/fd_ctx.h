@@ -72,6 +72,7 @@ struct LearnedState {
   // temporal correction as a Fourier neural operator (tcf_layers > 0, k_c > 0):
   // 2 k_c -> 2 channels into corr; shares the O_F scratch above
   int tcf_layers = 0, tcf_modes = 0, tcf_width = 0;
+  int ablation = 0;  // 0 full flux block, 1 without the physics conv, 2 frequency operator only
   size_t raw_off_tcf = 0;
   // channel matrices of both operators in the mixing kernel's mode-blocked layout
   // (rebuilt from the raw parameters on every upload)

@@ -32,7 +32,11 @@ namespace {
 // projection kernels; the temporal correction adds its network and the
 // corrected projection
 constexpr int kLaunchesPerStep = 4 * (8 + 2);
+constexpr int kLaunchesPerStepFreqOnly = 4 * 2;  // ablation 2: no stencil network
 constexpr int kLaunchesTc = 7 + 1;
+
+// launches of the four stages of one step without O_F and the temporal correction
+int step_launches(const LearnedState& L) { return L.ablation == 2 ? kLaunchesPerStepFreqOnly : kLaunchesPerStep; }
 
 // launches of one temporal correction (CNN head or FNO, plus the corrected projection)
 int tc_launches(const LearnedState& L) { return L.tcf_layers > 0 ? fd_fno_launches(L.tcf_layers) + 1 : kLaunchesTc; }
@@ -132,8 +136,9 @@ cudaError_t learned_step(fd_ctx* c, const float* s_in, float* s_out, const float
   LStageArgs a = stage_args(c);
   a.un = s_in;
   a.coef = L.coef;
+  if (L.ablation == 2) a.coef = nullptr;  // frequency-domain operator only: no stencil network
   for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
-    e = run_stencil_net<LOGN>(c, s == 0 ? ptr_in : ptr_w, st);
+    if (L.ablation != 2) e = run_stencil_net<LOGN>(c, s == 0 ? ptr_in : ptr_w, st);
     if (e != cudaSuccess) {
       g_where = "stencil network";
       break;
@@ -348,6 +353,7 @@ fd_status fd_learned_init(fd_ctx* c) {
   L->tcf_layers = c->opts.tc_fno_layers;
   L->tcf_modes = c->opts.tc_fno_modes;
   L->tcf_width = c->opts.tc_fno_width;
+  L->ablation = c->opts.ablation;
   L->nparams = fd_learned_param_count(c->opts);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -531,7 +537,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
   if (e == cudaSuccess && use_graph && L.graph) {
     for (; done + G <= n_steps && e == cudaSuccess; done += G) {
       e = cudaGraphLaunch(L.graph, st);
-      launches += G * (kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers)) + (L.kc > 0 ? tc_launches(L) : 0);
+      launches += G * (step_launches(L) + 4 * fd_fno_launches(L.fno_layers)) + (L.kc > 0 ? tc_launches(L) : 0);
     }
   }
   // remaining steps (or every step when snapshots are requested): direct launches
@@ -539,7 +545,7 @@ fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
     const int r = done % G;
     const bool tc = L.kc > 0 && ((done + 1) % L.kc == 0);
     e = step_fn(r, tc, st);
-    launches += kLaunchesPerStep + 4 * fd_fno_launches(L.fno_layers) + (tc ? tc_launches(L) : 0);
+    launches += step_launches(L) + 4 * fd_fno_launches(L.fno_layers) + (tc ? tc_launches(L) : 0);
     if (e == cudaSuccess && save_every > 0 && traj && ((done + 1) % save_every) == 0) {
       e = cudaMemcpyAsync(static_cast<float*>(traj) + (size_t)snap * slot, L.ring + (r + 1) * slot, bytes,
                           cudaMemcpyDeviceToDevice, st);

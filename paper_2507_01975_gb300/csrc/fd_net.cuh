@@ -114,6 +114,7 @@ inline LStageArgs stage_args(fd_ctx* c) {
   if (c->lrn) {
     a.wl = c->lrn->d_raw + c->lrn->raw_off_wl;
     a.acc = c->lrn->acc;
+    a.ablation = c->lrn->ablation;
   }
   return a;
 }

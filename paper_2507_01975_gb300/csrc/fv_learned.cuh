@@ -33,6 +33,7 @@ struct LStageArgs {
   const float* wl;   // W_L [kind 2][axis 2][5][4]
   const float* corr; // correct_project only: correction [batch][2][N][N]
   const float* fno;  // O_F(u) [batch][8][N][N] added to the face values, or null
+  int ablation;      // 0 full operator; 1 K = (W_L + C) / h^deriv (no W_P, no projection); 2 face values = O_F only
   int stage;
   int flow;          // 0 Burgers, 1 Navier-Stokes
   int forcing;
@@ -320,6 +321,10 @@ __global__ void __launch_bounds__(256, 4) fv_learned_flux_kernel(const LStageArg
 #pragma unroll
       for (int kind = 0; kind < 2; ++kind) {
         const int qi = 2 * pr_ + kind;
+        if (a.ablation == 2) {  // frequency-domain operator only
+          inst[(qi * FR + fr) * N + i] = a.fno[((size_t)b * 8 + qi) * NN + c];
+          continue;
+        }
         float L[20];
 #pragma unroll
         for (int t = 0; t < 20; ++t) L[t] = swl[(kind * 2 + axis) * 20 + t];
@@ -355,9 +360,11 @@ __global__ void __launch_bounds__(256, 4) fv_learned_flux_kernel(const LStageArg
             sc += v * cval[cc];
             sr += v * (float)(r - 2);
           }
-        s1 *= (1.0f / 20.0f);
-        sc *= (1.0f / 25.0f);
-        sr *= (1.0f / 40.0f);
+        // the projection keeps W_P's consistency: without W_P (ablation 1) neither is applied
+        const float pk = a.ablation == 0 ? 1.0f : 0.0f;
+        s1 *= pk * (1.0f / 20.0f);
+        sc *= pk * (1.0f / 25.0f);
+        sr *= pk * (1.0f / 40.0f);
         const float scale = kind == 1 ? 1.0f / h : 1.0f;
         float val = 0.f;
 #pragma unroll
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(256, 4) fv_learned_flux_kernel(const LStageArg
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
-            if (r == 2) {
+            if (r == 2 && a.ablation == 0) {
               if (kind == 0) {
                 k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
               } else if (a.dord == 4) {

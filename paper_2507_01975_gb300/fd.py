@@ -88,6 +88,7 @@ class FdOptions(C.Structure):
         ("tc_fno_layers", C.c_int32),
         ("tc_fno_modes", C.c_int32),
         ("tc_fno_width", C.c_int32),
+        ("ablation", C.c_int32),
     ]
 
 
@@ -217,6 +218,7 @@ class Config:
     tc_fno_layers: int = 0  # temporal correction as an FNO (0 = CNN head); needs k_c > 0
     tc_fno_modes: int = 0
     tc_fno_width: int = 0
+    ablation: int = 0  # 0 full flux block, 1 without the physics conv, 2 frequency operator only (Table 4)
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -244,7 +246,7 @@ class Solver:
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
         o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26, cfg.path,
                       cfg.fno_layers, cfg.fno_modes, cfg.fno_width, cfg.tc_fno_layers, cfg.tc_fno_modes,
-                      cfg.tc_fno_width)
+                      cfg.tc_fno_width, cfg.ablation)
         h = C.c_void_p()
         st = self.lib.fd_init(C.byref(g), cfg.nu, cfg.dt, C.byref(f), C.byref(o), C.byref(h))
         if st != FD_OK:

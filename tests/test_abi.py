@@ -81,6 +81,10 @@ def _init(lib, n=32, batch=1, dtype=fd.FD_F32, flow=fd.FD_NAVIER_STOKES, nu=1e-3
         dict(n=64, opts=fd.FdOptions(4, 2, 1, 4, 0, 8, 1 << 26, 0, 0, 0, 0, 4, 32, 12)),
         dict(n=64, opts=fd.FdOptions(4, 2, 1, 4, 0, 8, 1 << 26, 0, 0, 0, 0, 4, 33, 8)),
         dict(n=32, opts=fd.FdOptions(4, 2, 1, 4, 0, 8, 1 << 26, 0, 0, 0, 0, 4, 17, 8)),
+        # ablation variants: out of range, without the learned module, O_F only without O_F
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 3)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 1)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 2)),
     ],
 )
 def test_init_rejects_invalid_arguments(lib, kw):

@@ -138,3 +138,40 @@ def test_fno_temporal_correction_rollout_matches_oracle(n, k_c, tc_modes, tc_wid
     without = np.stack([O.rollout(U0[k], p, steps, model=model(False))[0] for k in range(2)])
     assert rel_l2(without, ref) > 20 * err
     s.close()
+
+
+@pytest.mark.parametrize("ablation,with_fno", [(1, False), (1, True), (2, True)])
+def test_ablation_variants_match_oracle(ablation, with_fno):
+    """The ablation variants of Table 4: without the physics-based convolution
+    (K = W_L + C_theta, unprojected), and the frequency-domain operator alone."""
+    n, b = 64, 2
+    fno = I.random_fno(25, 16, 32, 4, out_scale=0.5) if with_fno else None
+    st = I.random_conv_stack(8, 2, O.CNN_HIDDEN, O.N_COEF, last_scale=0.5)
+    wl = I.random_wl(10, 1e-2)
+
+    def model(abl):
+        return O.LearnedModel(W_L=wl, stencil=st, fno=None if fno is None else O.FNOParams(**fno), ablation=abl)
+
+    cfg = fd.Config(n=n, batch=b, dtype="f32", nu=1e-3, dt=2e-3, learned=True, forcing="kolmogorov",
+                    ablation=ablation, fno_layers=4 if with_fno else 0, fno_modes=32 if with_fno else 0,
+                    fno_width=16 if with_fno else 0)
+    s = fd.Solver(cfg)
+    s.set_params(I.pack_params(wl, st, None, fno))
+    U0 = I.ic_batch("kolmogorov", n, b, seed0=5).astype(np.float32)
+    p = O.Problem(nx=n, ny=n, nu=1e-3, dt=2e-3, forcing_kind=1)
+    for steps, tol in ((1, 1e-4), (5, 1e-3)):
+        u = torch.tensor(U0, device="cuda")
+        out = torch.empty_like(u)
+        s.rollout(u, out, steps)
+        torch.cuda.synchronize()
+        g = out.double().cpu().numpy()
+        ref = np.stack([O.rollout(U0[k].astype(np.float64), p, steps, model=model(ablation))[0] for k in range(b)])
+        err = rel_l2(g, ref)
+        assert err <= tol, (steps, err)
+        full = np.stack([O.rollout(U0[k].astype(np.float64), p, steps, model=model(0))[0] for k in range(b)])
+        assert rel_l2(full, ref) > 20 * err
+    u = torch.zeros((b, 2, n, n), device="cuda")
+    with pytest.raises(fd.FdError) as e:
+        s.step_adjoint(u, u, torch.empty_like(u))
+    assert e.value.status == fd.FD_EUNSUPPORTED
+    s.close()

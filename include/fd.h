@@ -60,7 +60,12 @@ typedef enum { FD_BURGERS = 0, FD_NAVIER_STOKES = 1 } fd_flow;
  * kernel (one thread-block cluster per trajectory holds the state in shared
  * and tensor memory for the whole rollout; FP32 N <= 256, FP64 N <= 128) and
  * the streaming path for larger grids (FP32, N up to 2048: tiled flux kernels
- * and a three-pass FFT projection through HBM, one CUDA graph per step). */
+ * and a three-pass FFT projection through HBM, one CUDA graph per step).
+ * Burgers (no projection, hence no FFT) also runs on any grid, including
+ * non-power-of-two and rectangular ones (nx, ny in [4, 8192]; the paper's
+ * Burgers case is [0, 1]^2 at 100^2 and 25^2, App. C.1): the generic-grid
+ * path, four stage kernels per step through HBM, FP32 or FP64, state layout
+ * [batch][2][ny][nx]. */
 typedef struct {
   int32_t nx, ny;
   double lx, ly;
@@ -88,8 +93,11 @@ typedef struct {
   int32_t ckpt_every;     /* reserved for the adjoint: checkpoint interval */
   int64_t spin_limit;     /* reserved: iteration limit of bounded device waits */
   int32_t path;           /* 0 = automatic (default): on chip where built (FP32 N <= 256,
-                             FP64 N <= 128), streaming through HBM otherwise;
-                             1 = on chip only; 2 = streaming (FP32, N in [32, 2048]) */
+                             FP64 N <= 128), streaming through HBM otherwise, and the
+                             generic-grid kernels for Burgers on a non-power-of-two or
+                             rectangular grid; 1 = on chip only; 2 = streaming (FP32, N in
+                             [32, 2048]); 3 = generic grid (Burgers only, any nx x ny in
+                             [4, 8192]^2, FP32 or FP64, no learned module) */
   int32_t fno_layers;     /* frequency-domain operator O_F of the learnable module (Sec. 3.4):
                              Fourier layers, 0 = off (default); needs learned = 1; forward only
                              (the reverse-mode calls refuse a context that has it) */
@@ -312,7 +320,8 @@ fd_status fd_downsample(const void* fine, void* coarse, int32_t batch, int32_t n
  * A new context starts on its default plan: the first cluster shape of its
  * grid, the whole batch on chip. */
 typedef struct {
-  int32_t path;       /* 1 plain on chip (+ streaming part), 2 streaming only, 3 learned (output) */
+  int32_t path;       /* 1 plain on chip (+ streaming part), 2 streaming only, 3 learned,
+                         4 generic grid (output) */
   int32_t cluster;    /* CTAs per on-chip trajectory; 0 when n_onchip == 0 */
   int32_t n_onchip;   /* trajectories [0, n_onchip) on the on-chip kernel */
   int32_t n_stream;   /* trajectories [n_onchip, batch) on the streaming kernels */

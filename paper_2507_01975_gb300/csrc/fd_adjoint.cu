@@ -358,6 +358,7 @@ extern "C" {
 fd_status fd_step_adjoint(fd_ctx* c, const void* u_in, const void* lam_out, void* lam_in, float* dparams,
                           void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_step_adjoint: null context");
+  if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_step_adjoint: not built for the generic-grid path");
   if (c->lrn && (c->lrn->fno_layers > 0 || c->lrn->ablation != 0))
     return fd_set_error(c, FD_EUNSUPPORTED,
                         "fd_step_adjoint: the frequency-domain operator and the ablation variants have no reverse mode "

@@ -27,6 +27,13 @@ void fd_train_free(fd_ctx* c);
 fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                              cudaStream_t st, bool allow_graph);
 fd_status fd_learned_error_flag(fd_ctx* c);
+// Burgers on any grid (fd_generic.cu)
+bool fd_generic_wanted(const fd_grid& g, int path);
+fd_status fd_generic_init(fd_ctx* c);
+void fd_generic_free(fd_ctx* c);
+fd_status fd_generic_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
+                             cudaStream_t st, bool allow_graph);
+
 // streaming path (fd_large.cu)
 bool fd_large_supported(int dtype, int n);
 fd_status fd_large_init(fd_ctx* c);
@@ -151,9 +158,15 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   *out = nullptr;
   const fd_grid g = *grid;
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-  if (!pow2(g.nx) || !pow2(g.ny) || g.nx < 8 || g.ny < 8 || g.nx > 2048 || g.ny > 2048)
-    return fd_set_error(nullptr, FD_EINVAL, "fd_init: nx, ny must be powers of two in [8, 2048] (got %d x %d)",
-                   g.nx, g.ny);
+  // Burgers on a non-power-of-two or rectangular grid (or path 3) runs on the
+  // generic-grid kernels; every other grid must be a power of two
+  const bool generic = fd_generic_wanted(g, opts ? opts->path : 0);
+  if (generic && (g.nx < 4 || g.ny < 4 || g.nx > 8192 || g.ny > 8192))
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: nx, ny must be in [4, 8192] (got %d x %d)", g.nx, g.ny);
+  if (!generic && (!pow2(g.nx) || !pow2(g.ny) || g.nx < 8 || g.ny < 8 || g.nx > 2048 || g.ny > 2048))
+    return fd_set_error(nullptr, FD_EINVAL,
+                        "fd_init: nx, ny must be powers of two in [8, 2048] (got %d x %d; other grids are built for "
+                        "Burgers only)", g.nx, g.ny);
   if (g.batch < 1 || g.batch > 65535) return fd_set_error(nullptr, FD_EINVAL, "fd_init: batch must be in [1, 65535]");
   if (!(g.lx > 0) || !(g.ly > 0)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: box lengths must be positive");
   if (g.dtype != FD_F32 && g.dtype != FD_F64) return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown dtype");
@@ -162,6 +175,7 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   if (!(dt > 0) || !std::isfinite(dt)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: dt must be positive");
   if (!(nu >= 0) || !std::isfinite(nu)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
   fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 0};
+  static_assert(sizeof(fd_options) == 64, "fd_options layout");
   if (opts) o = *opts;
   if (o.deriv_order != 2 && o.deriv_order != 4)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
@@ -171,10 +185,36 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   fd_forcing f = {0, 1.0, 4, 0.1};
   if (forcing) f = *forcing;
   if (f.kind != 0 && f.kind != 1) return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown forcing kind");
-  if (g.nx != g.ny) return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: only square grids are built");
+  if (!generic && g.nx != g.ny)
+    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: rectangular grids are built for Burgers only");
   if (o.learned != 0 && o.learned != 1) return fd_set_error(nullptr, FD_EINVAL, "fd_init: learned must be 0 or 1");
   if (!o.learned && o.k_c) return fd_set_error(nullptr, FD_EINVAL, "fd_init: k_c needs the learned option");
-  if (o.path < 0 || o.path > 2) return fd_set_error(nullptr, FD_EINVAL, "fd_init: path must be 0, 1 or 2");
+  if (o.path < 0 || o.path > 3) return fd_set_error(nullptr, FD_EINVAL, "fd_init: path must be 0, 1, 2 or 3");
+  if (o.path == 3 && !generic)
+    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: the generic-grid path (3) is built for Burgers");
+  if (generic && o.learned)
+    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: the learned path runs on square power-of-two grids");
+  if (generic && o.path != 0 && o.path != 3)
+    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: this grid runs on the generic-grid path (path 3) only");
+  if (generic) {
+    fd_ctx* c = new (std::nothrow) fd_ctx();
+    if (!c) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: out of host memory");
+    c->grid = g;
+    c->forcing = f;
+    c->opts = o;
+    c->opts.path = 3;
+    c->nu = nu;
+    c->dt = dt;
+    std::memset(&c->base, 0, sizeof c->base);
+    const fd_status gs = fd_generic_init(c);
+    if (gs != FD_OK) {
+      fd_generic_free(c);
+      delete c;
+      return gs;
+    }
+    *out = c;
+    return FD_OK;
+  }
   if (o.fno_layers < 0 || o.fno_layers > 8)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: fno_layers must be in [0, 8]");
   if (o.fno_layers > 0) {
@@ -313,6 +353,7 @@ fd_status fd_rollout_impl(fd_ctx* c, const void* u0, void* traj, void* u_final, 
   if (save_every < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every must be >= 0");
   if (save_every > 0 && !traj) return fd_set_error(c, FD_EINVAL, "fd_rollout: save_every > 0 needs traj");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->gen) return fd_generic_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
   if (c->lrn) return fd_learned_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
   if (c->big) return fd_large_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
   return fd_plain_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
@@ -412,6 +453,7 @@ fd_status fd_destroy(fd_ctx* c) {
   fd_adjoint_free(c);
   fd_learned_free(c);
   fd_large_free(c);
+  fd_generic_free(c);
   delete c;
   return FD_OK;
 }

@@ -130,6 +130,20 @@ struct TrainState {
 
 }  // namespace ldfv
 
+namespace ldfv {
+// Burgers on any grid (fd_generic.cu): state, two stage buffers, accumulator,
+// the forcing table of the ny u-face rows, and the captured step
+struct GenericState {
+  void* un = nullptr;
+  void* wa = nullptr;
+  void* wb = nullptr;
+  void* acc = nullptr;
+  void* frc = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+};
+}  // namespace ldfv
+
 struct fd_ctx {
   fd_grid grid;
   fd_forcing forcing;
@@ -151,6 +165,7 @@ struct fd_ctx {
   ldfv::AdjointState* adj = nullptr;
   ldfv::TrainState* trn = nullptr;
   ldfv::LargeState* big = nullptr;   // set when the streaming path runs this context
+  ldfv::GenericState* gen = nullptr; // set for Burgers on a non-power-of-two or rectangular grid
   // launch plan of a plain on-chip context: on-chip configurations valid for
   // this grid ([0] = default), the one in use, and how the batch is split
   // between it and a streaming context that runs the trajectories

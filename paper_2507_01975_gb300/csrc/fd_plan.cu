@@ -65,7 +65,7 @@ fd_status apply_plan(fd_ctx* c, int variant, int n_onchip, int n_stream) {
   return FD_OK;
 }
 
-int plan_path(const fd_ctx* c) { return c->lrn ? 3 : c->big ? 2 : 1; }
+int plan_path(const fd_ctx* c) { return c->gen ? 4 : c->lrn ? 3 : c->big ? 2 : 1; }
 
 void describe(const fd_ctx* c, fd_plan* p) {
   p->path = plan_path(c);
@@ -76,7 +76,7 @@ void describe(const fd_ctx* c, fd_plan* p) {
   p->us_per_step = c->plan_us;
   if (c->lrn) {
     p->n_onchip = c->grid.batch;
-  } else if (c->big) {
+  } else if (c->big || c->gen) {
     p->n_stream = c->grid.batch;
   } else {
     p->n_onchip = c->n_onchip;
@@ -151,8 +151,9 @@ fd_status fd_set_plan(fd_ctx* c, const fd_plan* p) {
   if (p->n_onchip < 0 || p->n_stream < 0 || p->n_onchip + p->n_stream != B)
     return fd_set_error(c, FD_EINVAL, "fd_set_plan: n_onchip + n_stream must equal the batch (%d)", B);
   if (c->lrn) return fd_set_error(c, FD_EUNSUPPORTED, "fd_set_plan: a learned context has a fixed launch plan");
-  if (c->big) {
-    if (p->n_stream != B) return fd_set_error(c, FD_EUNSUPPORTED, "fd_set_plan: this grid runs on the streaming path only");
+  if (c->big || c->gen) {
+    if (p->n_stream != B)
+      return fd_set_error(c, FD_EUNSUPPORTED, "fd_set_plan: this grid runs through HBM only (streaming or generic-grid path)");
     return FD_OK;
   }
   int variant = c->variant;
@@ -185,7 +186,7 @@ fd_status fd_autotune(fd_ctx* c, int32_t probe_steps, fd_plan* report, int32_t m
     double us;
   };
   std::vector<Cand> cands;
-  const bool plain_onchip = !c->lrn && !c->big;
+  const bool plain_onchip = !c->lrn && !c->big && !c->gen;
   if (plain_onchip) {
     for (size_t v = 0; v < c->variants.size(); ++v) {
       cands.push_back({(int)v, B, 0, 0});
@@ -206,7 +207,7 @@ fd_status fd_autotune(fd_ctx* c, int32_t probe_steps, fd_plan* report, int32_t m
     }
     if (stream_ok(c)) cands.push_back({0, 0, B, 0});
   } else {
-    cands.push_back({0, 0, 0, 0});  // the fixed plan of a learned or streaming-only context
+    cands.push_back({0, 0, 0, 0});  // the fixed plan of a learned, streaming-only or generic-grid context
   }
   const int old_variant = c->variant, old_on = c->n_onchip, old_st = c->n_stream;
 

@@ -116,6 +116,7 @@ extern "C" {
 
 fd_status fd_energy_spectrum(fd_ctx* c, const void* u, double* spectrum, int32_t kmax, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_energy_spectrum: null context");
+  if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_energy_spectrum: not built for the generic-grid path");
   if (!u || !spectrum) return fd_set_error(c, FD_EINVAL, "fd_energy_spectrum: null pointer");
   const int n = c->grid.nx;
   if (kmax < 0 || kmax > n) return fd_set_error(c, FD_EINVAL, "fd_energy_spectrum: kmax must be in [0, N]");

@@ -306,6 +306,7 @@ fd_status fd_mse_loss(fd_ctx* c, const float* pred, const float* target, int64_t
 fd_status fd_rollout_adjoint(fd_ctx* c, const void* u0, int32_t n_steps, int32_t ckpt_every, const void* lam_traj,
                              void* lam0, float* dparams, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout_adjoint: null context");
+  if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_adjoint: not built for the generic-grid path");
   if (c->lrn && (c->lrn->fno_layers > 0 || c->lrn->ablation != 0))
     return fd_set_error(c, FD_EUNSUPPORTED,
                         "fd_rollout_adjoint: the frequency-domain operator and the ablation variants have no reverse "
@@ -320,6 +321,7 @@ fd_status fd_rollout_adjoint(fd_ctx* c, const void* u0, int32_t n_steps, int32_t
 fd_status fd_train_step(fd_ctx* c, const void* u0, const void* targets, int32_t n_steps, int32_t ckpt_every,
                         float* dparams, double* loss, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_train_step: null context");
+  if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_train_step: not built for the generic-grid path");
   if (c->lrn && (c->lrn->fno_layers > 0 || c->lrn->ablation != 0))
     return fd_set_error(c, FD_EUNSUPPORTED,
                         "fd_train_step: the frequency-domain operator and the ablation variants have no reverse mode in "

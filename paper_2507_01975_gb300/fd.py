@@ -211,7 +211,7 @@ class Config:
     poisson_symbol: int = 0
     learned: bool = False
     k_c: int = 0
-    path: int = 0  # 0 automatic, 1 on chip, 2 streaming through HBM
+    path: int = 0  # 0 automatic, 1 on chip, 2 streaming through HBM, 3 generic grid (Burgers)
     fno_layers: int = 0  # frequency-domain operator O_F: Fourier layers (0 = off)
     fno_modes: int = 0
     fno_width: int = 0
@@ -219,6 +219,7 @@ class Config:
     tc_fno_modes: int = 0
     tc_fno_width: int = 0
     ablation: int = 0  # 0 full flux block, 1 without the physics conv, 2 frequency operator only (Table 4)
+    ny: Optional[int] = None  # rows when the grid is rectangular (Burgers on the generic-grid path); n = columns
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -241,7 +242,7 @@ class Solver:
     def __init__(self, cfg: Config):
         self.lib = load()
         self.cfg = cfg
-        g = FdGrid(cfg.n, cfg.n, cfg.lx, cfg.ly, cfg.batch, FD_F64 if cfg.dtype == "f64" else FD_F32,
+        g = FdGrid(cfg.n, cfg.ny or cfg.n, cfg.lx, cfg.ly, cfg.batch, FD_F64 if cfg.dtype == "f64" else FD_F32,
                    FD_BURGERS if cfg.flow == "burgers" else FD_NAVIER_STOKES)
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
         o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26, cfg.path,
@@ -260,7 +261,7 @@ class Solver:
 
     @property
     def state_shape(self):
-        return (self.cfg.batch, 2, self.cfg.n, self.cfg.n)
+        return (self.cfg.batch, 2, self.cfg.ny or self.cfg.n, self.cfg.n)
 
     @property
     def torch_dtype(self):

@@ -27,8 +27,11 @@ def face_coords(nx: int, ny: int, lx: float = TWO_PI, ly: float = TWO_PI):
     return (xu, yu), (xv, yv)
 
 
-def burgers_ic(n: int, seed: int = 0, lx: float = TWO_PI, kmax: int = 4) -> np.ndarray:
-    """Random smooth Burgers initial condition.
+def burgers_ic(n: int, seed: int = 0, lx: float = TWO_PI, kmax: int = 4, ny: int = None,
+               ly: float = None) -> np.ndarray:
+    """Random smooth Burgers initial condition on n x n cells of [0, lx]^2 (or, with
+    ny / ly, on n columns x ny rows of [0, lx] x [0, ly]; wavevector k has phase
+    2 pi (kx x / lx + ky y / ly)).
 
     Each component is a sum over integer wavevectors k != 0 with |k| <= kmax of
     ``a_k cos(k.x) + b_k sin(k.x)``, one (a_k, b_k) per half-plane wavevector,
@@ -44,13 +47,15 @@ def burgers_ic(n: int, seed: int = 0, lx: float = TWO_PI, kmax: int = 4) -> np.n
                 continue
             if kx > 0 or (kx == 0 and ky > 0):
                 ks.append((kx, ky))
-    (xu, yu), (xv, yv) = face_coords(n, n, lx, lx)
-    s = TWO_PI / lx
-    out = np.zeros((2, n, n))
+    ny = n if ny is None else ny
+    ly = lx if ly is None else ly
+    (xu, yu), (xv, yv) = face_coords(n, ny, lx, ly)
+    sx, sy = TWO_PI / lx, TWO_PI / ly
+    out = np.zeros((2, ny, n))
     for comp, (x, y) in enumerate(((xu, yu), (xv, yv))):
         for kx, ky in ks:
             a, b = rng.standard_normal(2)
-            ph = s * (kx * x + ky * y)
+            ph = sx * kx * x + sy * ky * y
             out[comp] += a * np.cos(ph) + b * np.sin(ph)
     return out / np.abs(out).max()
 

@@ -57,6 +57,10 @@ def _init(lib, n=32, batch=1, dtype=fd.FD_F32, flow=fd.FD_NAVIER_STOKES, nu=1e-3
         dict(n=12),
         dict(n=4),
         dict(n=4096),
+        # Burgers runs on any grid in [4, 8192]^2 (generic-grid path), but not beyond
+        dict(n=3, flow=fd.FD_BURGERS),
+        dict(n=9000, flow=fd.FD_BURGERS),
+        dict(n=25, flow=fd.FD_BURGERS, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 4)),
         dict(batch=0),
         dict(dt=0.0),
         dict(dt=-1e-3),
@@ -120,6 +124,10 @@ def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):
     # the learned path is on chip only
     st, _ = _init(lib, n=512, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
     assert st == fd.FD_EUNSUPPORTED
-    # an unknown path value is invalid
+    # the generic-grid path is built for Burgers; an unknown path value is invalid
     st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 3))
+    assert st == fd.FD_EUNSUPPORTED
+    st, _ = _init(lib, n=25, flow=fd.FD_BURGERS, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
+    assert st == fd.FD_EUNSUPPORTED
+    st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 4))
     assert st == fd.FD_EINVAL

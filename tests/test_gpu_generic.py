@@ -1,0 +1,131 @@
+"""Burgers on the generic-grid path (non-power-of-two and rectangular grids) on
+sm_103a vs the FP64 oracle, through the C ABI: the paper's Burgers case
+(App. C.1: [0, 1]^2, nu = 0.002, dt = 1e-3, 100^2 data grid, 25^2 model grid),
+rectangular grids with ragged strips, forcing, both derivative orders, the
+on-chip path on a power-of-two grid, snapshots, coarse-graining 100^2 -> 25^2.
+Tolerances as for the other plain paths: FP64 <= 1e-12 and FP32 <= 1e-6 per step
+(relative L2), FP32 <= 1e-4 after 100 steps."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.train import face_average
+from paper_2507_01975_gb300 import fd
+from paper_2507_01975_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_01975_gb300 import build
+
+    build.build()
+    fd.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def gpu_rollout(cfg, U0, steps, save_every=0):
+    s = fd.Solver(cfg)
+    dt = torch.float64 if cfg.dtype == "f64" else torch.float32
+    u = torch.tensor(U0, dtype=dt, device="cuda")
+    out = torch.empty_like(u)
+    traj = None
+    if save_every:
+        traj = torch.empty((steps // save_every,) + tuple(u.shape), dtype=dt, device="cuda")
+        s.rollout(u, out, steps, traj=traj, save_every=save_every)
+    else:
+        s.rollout(u, out, steps)
+    torch.cuda.synchronize()
+    res = (out.double().cpu().numpy(), None if traj is None else traj.double().cpu().numpy(),
+           s.lib.fd_last_launch_count(s.h))
+    s.close()
+    return res
+
+
+def oracle_rollout(p, U0, steps):
+    return np.stack([O.rollout(U0[b], p, steps)[0] for b in range(U0.shape[0])])
+
+
+@pytest.mark.parametrize("dtype,tol1,tol100", [("f64", 1e-12, 1e-11), ("f32", 1e-6, 1e-4)])
+def test_paper_burgers_case_25(dtype, tol1, tol100):
+    """The paper's Burgers setting on its 25^2 model grid."""
+    n, b = 25, 3
+    U0 = np.stack([I.burgers_ic(n, 40 + k, lx=1.0) for k in range(b)])
+    if dtype == "f32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    cfg = fd.Config(n=n, batch=b, dtype=dtype, flow="burgers", nu=0.002, dt=1e-3, lx=1.0, ly=1.0)
+    p = O.Problem(nx=n, ny=n, lx=1.0, ly=1.0, nu=0.002, dt=1e-3, flow=O.FLOW_BURGERS)
+    for steps, tol in ((1, tol1), (100, tol100)):
+        g, _, launches = gpu_rollout(cfg, U0, steps)
+        err = rel_l2(g, oracle_rollout(p, U0, steps))
+        assert err <= tol, (steps, err)
+        assert launches == 4 * steps
+
+
+@pytest.mark.parametrize("nx,ny,dord,forced", [(48, 40, 4, False), (30, 17, 2, True), (7, 5, 4, False)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rectangular_grids(nx, ny, dord, forced, dtype):
+    """Rectangular grids with a ragged last strip (4 does not divide 30 or 7),
+    unequal spacings, Kolmogorov forcing on ny rows, both derivative orders."""
+    b, lx, ly = 2, 3.0, 2.0
+    U0 = np.stack([I.burgers_ic(nx, 50 + k, lx=lx, ny=ny, ly=ly) for k in range(b)]) * 0.5
+    if dtype == "f32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    cfg = fd.Config(n=nx, ny=ny, batch=b, dtype=dtype, flow="burgers", nu=0.01, dt=2e-3, lx=lx, ly=ly,
+                    deriv_order=dord, forcing="kolmogorov" if forced else None)
+    p = O.Problem(nx=nx, ny=ny, lx=lx, ly=ly, nu=0.01, dt=2e-3, flow=O.FLOW_BURGERS, deriv_order=dord,
+                  forcing_kind=1 if forced else 0)
+    g, _, _ = gpu_rollout(cfg, U0, 5)
+    err = rel_l2(g, oracle_rollout(p, U0, 5))
+    assert err <= (1e-12 if dtype == "f64" else 1e-6), err
+
+
+def test_generic_path_matches_on_chip_path_and_snapshots():
+    """On a power-of-two square grid path 3 computes the on-chip path's step;
+    snapshots hold every save_every-th state."""
+    n, b = 64, 2
+    U0 = np.stack([I.burgers_ic(n, 60 + k) for k in range(b)]).astype(np.float32)
+    base = dict(n=n, batch=b, dtype="f32", flow="burgers", nu=0.01, dt=2e-3)
+    on_chip, _, _ = gpu_rollout(fd.Config(**base), U0, 20)
+    gen, traj, _ = gpu_rollout(fd.Config(**base, path=3), U0, 20, save_every=5)
+    assert rel_l2(gen, on_chip) <= 1e-6
+    assert traj.shape[0] == 4 and np.array_equal(traj[-1], gen)
+    mid, _, _ = gpu_rollout(fd.Config(**base, path=3), U0, 10)
+    assert np.array_equal(traj[1], mid)
+
+
+def test_paper_burgers_data_pipeline_100_to_25():
+    """The paper's data recipe for Burgers: a 100^2 run (dt = 1e-3) coarse-grained by
+    face averages to 25^2, against the oracle's run and face average."""
+    n, b, steps = 100, 2, 20
+    U0 = np.stack([I.burgers_ic(n, 70 + k, lx=1.0) for k in range(b)]).astype(np.float32).astype(np.float64)
+    cfg = fd.Config(n=n, batch=b, dtype="f32", flow="burgers", nu=0.002, dt=1e-3, lx=1.0, ly=1.0)
+    g, _, _ = gpu_rollout(cfg, U0, steps)
+    p = O.Problem(nx=n, ny=n, lx=1.0, ly=1.0, nu=0.002, dt=1e-3, flow=O.FLOW_BURGERS)
+    ref = oracle_rollout(p, U0, steps)
+    assert rel_l2(g, ref) <= 1e-5
+    fine = torch.tensor(g, dtype=torch.float32, device="cuda")
+    coarse = torch.empty((b, 2, 25, 25), dtype=torch.float32, device="cuda")
+    fd.downsample(fine, coarse, 4)
+    torch.cuda.synchronize()
+    want = np.stack([face_average(ref[k], 4) for k in range(b)])
+    assert rel_l2(coarse.double().cpu().numpy(), want) <= 1e-5
+
+
+def test_generic_path_refusals():
+    s = fd.Solver(fd.Config(n=25, batch=1, dtype="f32", flow="burgers", nu=0.002, dt=1e-3, lx=1.0, ly=1.0))
+    u = torch.zeros((1, 2, 25, 25), device="cuda")
+    with pytest.raises(fd.FdError) as e:
+        s.energy_spectrum(u, torch.empty((1, 5), dtype=torch.float64, device="cuda"))
+    assert e.value.status == fd.FD_EUNSUPPORTED
+    assert s.plan()["path"] == 4 and s.plan()["n_stream"] == 1
+    s.close()

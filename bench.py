@@ -546,6 +546,64 @@ def adjoint_measurement(fd, I, iters: int = 5):
             "ms_per_step_adjoint": e0.elapsed_time(e1) / iters, "launches_per_call": s.last_launch_count()}
 
 
+def speed_measurement(fd, I, reps: int = 3):
+    """GPU seconds per simulated physical second, batch 1: the only speed figure the
+    paper reports (Table 4, on an A100), on its grids. DNS rows run the plain solver:
+    Burgers 100^2 on [0, 1]^2 with dt = 1e-3 (Table S2) on the generic-grid path;
+    decaying and forced Navier-Stokes 1024^2 with dt = 2.19e-4 (the fine step of
+    Table S2; the paper does not give the 1024^2 one) on the streaming path. Model
+    rows: the learned 64^2 solver with the paper's forced-flow learnable module
+    (stencil network, O_F of 6 layers / 32 modes / width 16, FNO temporal correction
+    of 4 layers / 32 modes / width 8, k_c = 4; random weights) at dt = 32 x 2.19e-4;
+    for Burgers the plain 25^2 solver at dt = 1e-2 (the learned module is built for
+    32^2 and 64^2 grids only). Shear flow is not built (rectangular Navier-Stokes)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def per_physical_second(s, U0, dt):
+        u = torch.tensor(U0, device="cuda")
+        o = torch.empty_like(u)
+        steps = int(round(1.0 / dt))
+        s.rollout(u, o, steps)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0.record(stream)
+            s.rollout(u, o, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        finite = bool(s.check_finite(o))
+        s.close()
+        return {"seconds": best, "steps": steps, "finite": finite}
+
+    paper = {"burgers": (2.3067, 0.9800), "decaying": (29.2402, 2.3773), "forced": (32.8061, 3.8036)}
+    rows = {}
+    dns = fd.Solver(fd.Config(n=100, batch=1, dtype="f32", flow="burgers", nu=0.002, dt=1e-3, lx=1.0, ly=1.0))
+    coarse = fd.Solver(fd.Config(n=25, batch=1, dtype="f32", flow="burgers", nu=0.002, dt=1e-2, lx=1.0, ly=1.0))
+    rows["burgers"] = {"dns_100x100": per_physical_second(dns, I.burgers_ic(100, 1, lx=1.0)[None].astype(np.float32),
+                                                          1e-3),
+                       "plain_25x25": per_physical_second(coarse, I.burgers_ic(25, 1, lx=1.0)[None]
+                                                          .astype(np.float32), 1e-2)}
+    dt_f, kc = 2.19e-4, 4
+    st = I.random_conv_stack(1, 2, 64, 160, last_scale=0.05)
+    fno = I.random_fno(4, 16, 32, 6, out_scale=0.01)
+    tcf = I.random_fno(5, 8, 32, 4, out_scale=0.01, cin=2 * kc, cout=2)
+    for flow, forcing, ic in (("decaying", None, I.decaying_ic), ("forced", "kolmogorov", I.kolmogorov_ic)):
+        dns = fd.Solver(fd.Config(n=1024, batch=1, dtype="f32", nu=1e-3, dt=dt_f, forcing=forcing))
+        lrn = fd.Solver(fd.Config(n=64, batch=1, dtype="f32", nu=1e-3, dt=32 * dt_f, forcing=forcing, learned=True,
+                                  k_c=kc, fno_layers=6, fno_modes=32, fno_width=16, tc_fno_layers=4,
+                                  tc_fno_modes=32, tc_fno_width=8))
+        lrn.set_params(I.pack_params(I.random_wl(3, 1e-2), st, tcf, fno))
+        rows[flow] = {"dns_1024x1024": per_physical_second(dns, ic(1024, 0)[None].astype(np.float32), dt_f),
+                      "learned_64x64": per_physical_second(lrn, ic(64, 0)[None].astype(np.float32), 32 * dt_f)}
+    for k, (p_dns, p_model) in paper.items():
+        rows[k]["paper_a100"] = {"dns": p_dns, "ldsolver": p_model}
+    return {"unit": "GPU seconds per simulated physical second, batch 1 (min of %d runs)" % reps, **rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -556,7 +614,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-fine", action="store_true", help="skip the 2048^2 streaming-path measurement")
-    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch"],
+    ap.add_argument("--no-speed", action="store_true",
+                    help="skip the GPU-seconds-per-physical-second measurement on the paper's grids")
+    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch", "speed"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
     ap.add_argument("--plan", default=None,
@@ -583,7 +643,8 @@ def main():
               "adjoint": lambda: adjoint_measurement(fd, I, iters=args.iters),
               "fine": lambda: fine_measurement(fd, I, steps=max(args.iters, 2)),
               "corr": lambda: corr_measurement(fd, I, iters=args.iters),
-              "batch": lambda: batch_measurement(fd, I)}[args.only]
+              "batch": lambda: batch_measurement(fd, I),
+              "speed": lambda: speed_measurement(fd, I)}[args.only]
         print(json.dumps(fn()), flush=True)
         return
 
@@ -701,6 +762,7 @@ def main():
     learned = None if args.no_learned else learned_measurement(fd, I)
     training = None if args.no_training else training_measurement(fd, I)
     fine = None if args.no_fine else fine_measurement(fd, I)
+    speed = None if args.no_speed else speed_measurement(fd, I)
     line = {
         "metric": METRIC,
         "value": value,
@@ -734,6 +796,7 @@ def main():
         "learned": learned,
         "training": training,
         "fine_grid": fine,
+        "paper_speed_table": speed,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -92,6 +92,38 @@ def test_projection_divergence_free_idempotent_symmetric():
     assert abs(lhs - rhs) < 1e-12 * np.sum(np.abs(a) * np.abs(b))
 
 
+def test_projection_rectangular_grid_against_dense_solve():
+    """On a rectangular 12 x 8 grid with unequal spacings the spectral projection
+    equals the projection with the Poisson system solved densely: D2 and G2
+    assembled entry by entry, the zero-mean constraint appended, least squares."""
+    nx, ny, lx, ly = 12, 8, 3.0, 4.0
+    p = O.Problem(nx=nx, ny=ny, lx=lx, ly=ly)
+    dx, dy = lx / nx, ly / ny
+    rng = np.random.default_rng(13)
+    U = rng.standard_normal((2, ny, nx))
+    N = nx * ny
+    c = lambda j, i: (j % ny) * nx + (i % nx)
+    D = np.zeros((N, 2 * N))
+    G = np.zeros((2 * N, N))
+    for j in range(ny):
+        for i in range(nx):
+            D[c(j, i), c(j, i + 1)] += 1 / dx
+            D[c(j, i), c(j, i)] -= 1 / dx
+            D[c(j, i), N + c(j + 1, i)] += 1 / dy
+            D[c(j, i), N + c(j, i)] -= 1 / dy
+            G[c(j, i), c(j, i)] += 1 / dx
+            G[c(j, i), c(j, i - 1)] -= 1 / dx
+            G[N + c(j, i), c(j, i)] += 1 / dy
+            G[N + c(j, i), c(j - 1, i)] -= 1 / dy
+    A = np.vstack([D @ G, np.ones((1, N))])
+    rhs = np.concatenate([D @ U.reshape(-1), [0.0]])
+    pc = np.linalg.lstsq(A, rhs, rcond=None)[0]
+    want = U.reshape(-1) - G @ pc
+    got = O.project(U, p).reshape(-1)
+    assert np.abs(got - want).max() < 1e-11
+    assert np.abs(D @ got).max() < 1e-11
+
+
 def _dense_ops(n, h):
     """D2 and G2 written out as dense matrices by index arithmetic."""
     N = n * n

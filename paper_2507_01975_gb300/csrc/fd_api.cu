@@ -27,7 +27,8 @@ void fd_train_free(fd_ctx* c);
 fd_status fd_learned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                              cudaStream_t st, bool allow_graph);
 fd_status fd_learned_error_flag(fd_ctx* c);
-// Burgers on any grid (fd_generic.cu)
+// generic-grid path (fd_generic.cu): Burgers on any grid, Navier-Stokes on
+// rectangular power-of-two grids
 bool fd_generic_wanted(const fd_grid& g, int path);
 fd_status fd_generic_init(fd_ctx* c);
 void fd_generic_free(fd_ctx* c);
@@ -158,11 +159,16 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   *out = nullptr;
   const fd_grid g = *grid;
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-  // Burgers on a non-power-of-two or rectangular grid (or path 3) runs on the
-  // generic-grid kernels; every other grid must be a power of two
+  // Burgers on a non-power-of-two or rectangular grid, Navier-Stokes on a
+  // rectangular power-of-two grid (or either with path 3) run on the
+  // generic-grid kernels; every other grid must be a square power of two
   const bool generic = fd_generic_wanted(g, opts ? opts->path : 0);
   if (generic && (g.nx < 4 || g.ny < 4 || g.nx > 8192 || g.ny > 8192))
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: nx, ny must be in [4, 8192] (got %d x %d)", g.nx, g.ny);
+  if (generic && g.flow == FD_NAVIER_STOKES &&
+      (g.dtype != FD_F32 || g.nx < 32 || g.ny < 32 || g.nx > 2048 || g.ny > 2048))
+    return fd_set_error(nullptr, FD_EUNSUPPORTED,
+                        "fd_init: Navier-Stokes on the generic-grid path is built for FP32, nx, ny in [32, 2048]");
   if (!generic && (!pow2(g.nx) || !pow2(g.ny) || g.nx < 8 || g.ny < 8 || g.nx > 2048 || g.ny > 2048))
     return fd_set_error(nullptr, FD_EINVAL,
                         "fd_init: nx, ny must be powers of two in [8, 2048] (got %d x %d; other grids are built for "
@@ -191,7 +197,9 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   if (!o.learned && o.k_c) return fd_set_error(nullptr, FD_EINVAL, "fd_init: k_c needs the learned option");
   if (o.path < 0 || o.path > 3) return fd_set_error(nullptr, FD_EINVAL, "fd_init: path must be 0, 1, 2 or 3");
   if (o.path == 3 && !generic)
-    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: the generic-grid path (3) is built for Burgers");
+    return fd_set_error(nullptr, FD_EUNSUPPORTED,
+                        "fd_init: the generic-grid path (3) takes Burgers on any grid and Navier-Stokes on "
+                        "power-of-two grids");
   if (generic && o.learned)
     return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: the learned path runs on square power-of-two grids");
   if (generic && o.path != 0 && o.path != 3)

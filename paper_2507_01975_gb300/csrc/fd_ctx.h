@@ -131,14 +131,23 @@ struct TrainState {
 }  // namespace ldfv
 
 namespace ldfv {
-// Burgers on any grid (fd_generic.cu): state, two stage buffers, accumulator,
-// the forcing table of the ny u-face rows, and the captured step
+// generic-grid path (fd_generic.cu): state, two stage buffers, accumulator,
+// the forcing table of the ny u-face rows, the projection workspace, and the
+// captured step
 struct GenericState {
   void* un = nullptr;
   void* wa = nullptr;
   void* wb = nullptr;
   void* acc = nullptr;
   void* frc = nullptr;
+  // Navier-Stokes only: complex spectrum [batch][ny][nx], pressure, twiddles and
+  // Poisson symbols of both axes
+  void* z = nullptr;
+  void* p = nullptr;
+  void* twx = nullptr;
+  void* twy = nullptr;
+  void* symx = nullptr;
+  void* symy = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 };
@@ -165,7 +174,7 @@ struct fd_ctx {
   ldfv::AdjointState* adj = nullptr;
   ldfv::TrainState* trn = nullptr;
   ldfv::LargeState* big = nullptr;   // set when the streaming path runs this context
-  ldfv::GenericState* gen = nullptr; // set for Burgers on a non-power-of-two or rectangular grid
+  ldfv::GenericState* gen = nullptr; // set for the generic-grid path (non-power-of-two / rectangular grids)
   // launch plan of a plain on-chip context: on-chip configurations valid for
   // this grid ([0] = default), the one in use, and how the batch is split
   // between it and a streaming context that runs the trajectories

@@ -1,15 +1,22 @@
-// fd_generic.cu -- plain FV for Burgers' equation on any grid: non-power-of-two
-// and rectangular nx x ny (App. C.1 Burgers on [0, 1]^2 at 100^2 and 25^2,
-// Table S2), FP32 or FP64.
+// fd_generic.cu -- plain FV on grids the other paths do not take: Burgers on
+// any nx x ny (non-power-of-two and rectangular; App. C.1 Burgers on [0, 1]^2
+// at 100^2 and 25^2, Table S2), FP32 or FP64, and Navier-Stokes on rectangular
+// power-of-two grids (the shear-flow grids of Table 4, 128 x 64 and larger), FP32.
 //
-// Burgers has no pressure projection, so a step needs no FFT: four launches of
-// generic_stage_kernel per RK4 step (App. B.5), each thread forming the
-// tendency of a strip of 4 cells of one row with the same flux-block
-// arithmetic as the other paths (strip_tendency: face values of the eight
-// operator instances, flux assembly and divergence, the Burgers correction,
-// forcing) from a 5 x 8 window gathered with periodic wrap, then the RK
-// combination. The last strip of a row is ragged when 4 does not divide nx.
-// A step is captured once as a CUDA graph and replayed.
+// A step is four launches of generic_stage_kernel (App. B.5), each thread
+// forming the tendency of a strip of 4 cells of one row with the same
+// flux-block arithmetic as the other paths (strip_tendency: face values of the
+// eight operator instances, flux assembly and divergence, the Burgers
+// correction, forcing) from a 5 x 8 window gathered with periodic wrap, then
+// the RK combination; the last strip of a row is ragged when 4 does not divide
+// nx. For Navier-Stokes every stage result is projected (Sec. 3.6, App. B.3-B.4):
+// the divergence D2 w* and forward complex FFTs along x (one kernel), forward
+// FFTs along y, division by the symbol of D2 G2 (or the continuous one),
+// inverse FFTs along y (one kernel), inverse FFTs along x giving p, and
+// w = w* - G2 p; the FFTs are the register-resident Stockham transforms of
+// fv_fft.cuh (complex transforms of the real divergence; the rectangular
+// grid rules out the square real-FFT layouts of the streaming path). A step
+// is captured once as a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,6 +26,7 @@
 #include "../../include/fd.h"
 #include "fd_ctx.h"
 #include "fv_common.cuh"
+#include "fv_fft.cuh"
 
 using namespace ldfv;
 
@@ -31,7 +39,7 @@ struct GenArgs {
   T* acc;        // RK4 accumulator
   T* wout;       // next stage state (stage 3: the new state)
   const T* frc;  // [ny] forcing amplitude at the u-face rows
-  int nx, ny, stage, forced;
+  int nx, ny, stage, forced, burgers;
   T dt, nu, idx, idy, drag;
 };
 
@@ -56,7 +64,7 @@ __global__ void __launch_bounds__(256) generic_stage_kernel(const GenArgs<T> a) 
     }
   }
   T tu[4], tv[4];
-  strip_tendency<T, DORD>(u, v, a.idx, a.idy, a.nu, true, a.forced != 0, a.frc[row], a.drag, tu, tv);
+  strip_tendency<T, DORD>(u, v, a.idx, a.idy, a.nu, a.burgers != 0, a.forced != 0, a.frc[row], a.drag, tu, tv);
   const T h6 = a.dt / (T)6, h3 = a.dt / (T)3, h2 = a.dt * (T)0.5;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -89,6 +97,233 @@ __global__ void __launch_bounds__(256) generic_stage_kernel(const GenArgs<T> a) 
   }
 }
 
+// ---- projection of a rectangular power-of-two grid (FP32) -----------------
+// F transforms of L = 2^LOGL points per CTA, L / 16 threads each; every
+// exchange is a CTA-wide barrier (all transforms of a CTA move in lockstep)
+template <int LOGL>
+struct AxCfg {
+  static constexpr int L = 1 << LOGL, T = L / kFP;
+  static constexpr int F = 4096 / L < 1 ? 1 : (4096 / L > 16 ? 16 : 4096 / L);
+  static constexpr int NT = F * T;
+  static constexpr size_t SMEM = ((size_t)F * SPlan<LOGL>::BUF + SPlan<LOGL>::TW) * sizeof(float2);
+  static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+};
+
+// rows: z = D2 w (real), forward FFT along x; Z[b][j][kx]
+template <int LOGL>
+__global__ void __launch_bounds__(AxCfg<LOGL>::NT) gproj_rows_fwd_kernel(const float* w, float2* Z, int ny,
+                                                                        int ntr, const float2* twx, float idx,
+                                                                        float idy) {
+  using C = AxCfg<LOGL>;
+  using SP = SPlan<LOGL>;
+  constexpr int L = C::L, T = C::T;
+  extern __shared__ __align__(16) float2 gsm[];
+  float2* tws = gsm + C::F * SP::BUF;
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  const int tr = blockIdx.x * C::F + f;
+  build_pass_twiddles<LOGL>(tws, twx);
+  float2 z[kFP];
+  const bool live = tr < ntr;
+  const int b = live ? tr / ny : 0, j = live ? tr % ny : 0;
+  const size_t NN = (size_t)L * ny;
+  const float* u = w + (size_t)b * 2 * NN;
+  const float* v = u + NN;
+  const int jn = j + 1 == ny ? 0 : j + 1;
+#pragma unroll
+  for (int m = 0; m < kFP; ++m) {
+    const int i = t + m * T, in = (i + 1) & (L - 1);
+    const float d = live ? (u[(size_t)j * L + in] - u[(size_t)j * L + i]) * idx +
+                               (v[(size_t)jn * L + i] - v[(size_t)j * L + i]) * idy
+                         : 0.0f;
+    z[m] = make_float2(d, 0.0f);
+  }
+  __syncthreads();
+  const TransformSync sync{0, C::NT};
+  fft_forward<LOGL>(z, gsm + f * SP::BUF, tws, t, sync);
+  if (live) {
+#pragma unroll
+    for (int s = 0; s < SP::SL; ++s)
+#pragma unroll
+      for (int r = 0; r < SP::RL; ++r) Z[(size_t)tr * L + t + s * T + r * SP::NSL] = z[s + SP::SL * r];
+  }
+}
+
+// columns: forward FFT along y, divide by the symbol (zero mode dropped),
+// inverse FFT along y; consecutive transforms are consecutive columns, so the
+// F transforms of a CTA read F adjacent complex values per row
+template <int LOGL>
+__global__ void __launch_bounds__(AxCfg<LOGL>::NT) gproj_cols_kernel(float2* Z, int nx, int ncols,
+                                                                    const float2* twy, const float* symx,
+                                                                    const float* symy) {
+  using C = AxCfg<LOGL>;
+  using SP = SPlan<LOGL>;
+  constexpr int L = C::L, T = C::T;
+  extern __shared__ __align__(16) float2 gsm[];
+  float2* tws = gsm + C::F * SP::BUF;
+  const int f = threadIdx.x % C::F, t = threadIdx.x / C::F;
+  const int col = blockIdx.x * C::F + f;
+  build_pass_twiddles<LOGL>(tws, twy);
+  const bool live = col < ncols;
+  const int b = live ? col / nx : 0, i = live ? col % nx : 0;
+  float2* base = Z + (size_t)b * L * nx + i;
+  float2 z[kFP];
+#pragma unroll
+  for (int m = 0; m < kFP; ++m) z[m] = live ? base[(size_t)(t + m * T) * nx] : make_float2(0.0f, 0.0f);
+  __syncthreads();
+  const TransformSync sync{0, C::NT};
+  float2* buf = gsm + f * SP::BUF;
+  fft_forward<LOGL>(z, buf, tws, t, sync);
+  fft_store_natural<LOGL>(buf, z, t);
+  sync();
+  fft_load<LOGL>(z, buf, t);
+  sync();
+  const float sx = live ? symx[i] : 1.0f;
+#pragma unroll
+  for (int m = 0; m < kFP; ++m) {
+    const float sy = sx + symy[t + m * T];
+    const float inv = sy != 0.0f ? 1.0f / sy : 0.0f;
+    z[m] = make_float2(z[m].x * inv, z[m].y * inv);
+  }
+  fft_inverse<LOGL>(z, buf, tws, t, sync);
+  if (live) {
+#pragma unroll
+    for (int s = 0; s < SP::SL; ++s)
+#pragma unroll
+      for (int r = 0; r < SP::RL; ++r) base[(size_t)(t + s * T + r * SP::NSL) * nx] = z[s + SP::SL * r];
+  }
+}
+
+// rows: inverse FFT along x, p = Re / (nx ny)
+template <int LOGL>
+__global__ void __launch_bounds__(AxCfg<LOGL>::NT) gproj_rows_inv_kernel(const float2* Z, float* p, int ntr,
+                                                                        const float2* twx, float scale) {
+  using C = AxCfg<LOGL>;
+  using SP = SPlan<LOGL>;
+  constexpr int L = C::L, T = C::T;
+  extern __shared__ __align__(16) float2 gsm[];
+  float2* tws = gsm + C::F * SP::BUF;
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  const int tr = blockIdx.x * C::F + f;
+  build_pass_twiddles<LOGL>(tws, twx);
+  const bool live = tr < ntr;
+  float2 z[kFP];
+#pragma unroll
+  for (int m = 0; m < kFP; ++m) z[m] = live ? Z[(size_t)tr * L + t + m * T] : make_float2(0.0f, 0.0f);
+  __syncthreads();
+  const TransformSync sync{0, C::NT};
+  fft_inverse<LOGL>(z, gsm + f * SP::BUF, tws, t, sync);
+  if (live) {
+#pragma unroll
+    for (int s = 0; s < SP::SL; ++s)
+#pragma unroll
+      for (int r = 0; r < SP::RL; ++r) p[(size_t)tr * L + t + s * T + r * SP::NSL] = z[s + SP::SL * r].x * scale;
+  }
+}
+
+// w = w* - G2 p (differences of adjacent pressures)
+__global__ void __launch_bounds__(256) gproj_grad_kernel(float* w, const float* p, int nx, int ny, int batch,
+                                                         float idx, float idy) {
+  const size_t NN = (size_t)nx * ny;
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= (size_t)batch * NN) return;
+  const size_t b = e / NN, c = e - b * NN;
+  const int j = (int)(c / nx), i = (int)(c - (size_t)j * nx);
+  const float* pb = p + b * NN;
+  const float pc = pb[c];
+  w[b * 2 * NN + c] -= (pc - pb[(size_t)j * nx + (i == 0 ? nx - 1 : i - 1)]) * idx;
+  w[b * 2 * NN + NN + c] -= (pc - pb[(size_t)(j == 0 ? ny - 1 : j - 1) * nx + i]) * idy;
+}
+
+template <int LOGL>
+cudaError_t launch_rows_fwd(const float* w, float2* Z, int ny, int ntr, const float2* tw, float idx, float idy,
+                            cudaStream_t st) {
+  using C = AxCfg<LOGL>;
+  gproj_rows_fwd_kernel<LOGL><<<(ntr + C::F - 1) / C::F, C::NT, C::SMEM, st>>>(w, Z, ny, ntr, tw, idx, idy);
+  return cudaGetLastError();
+}
+template <int LOGL>
+cudaError_t launch_cols(float2* Z, int nx, int ncols, const float2* tw, const float* sx, const float* sy,
+                        cudaStream_t st) {
+  using C = AxCfg<LOGL>;
+  gproj_cols_kernel<LOGL><<<(ncols + C::F - 1) / C::F, C::NT, C::SMEM, st>>>(Z, nx, ncols, tw, sx, sy);
+  return cudaGetLastError();
+}
+template <int LOGL>
+cudaError_t launch_rows_inv(const float2* Z, float* p, int ntr, const float2* tw, float scale, cudaStream_t st) {
+  using C = AxCfg<LOGL>;
+  gproj_rows_inv_kernel<LOGL><<<(ntr + C::F - 1) / C::F, C::NT, C::SMEM, st>>>(Z, p, ntr, tw, scale);
+  return cudaGetLastError();
+}
+
+// kernel attributes (outside any stream capture): the 2048-point transforms
+// need more than the default 48 KB of dynamic shared memory
+template <int LOGL>
+cudaError_t prepare_axis() {
+  using C = AxCfg<LOGL>;
+  cudaError_t e = cudaFuncSetAttribute(gproj_rows_fwd_kernel<LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gproj_cols_kernel<LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gproj_rows_inv_kernel<LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  return e;
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// projection of the FP32 state w [batch][2][ny][nx] in place
+cudaError_t generic_project(fd_ctx* c, float* w, cudaStream_t st) {
+  GenericState& S = *c->gen;
+  const fd_grid& g = c->grid;
+  const int ntr = g.batch * g.ny, ncols = g.batch * g.nx;
+  const float idx = (float)(g.nx / g.lx), idy = (float)(g.ny / g.ly);
+  float2* Z = static_cast<float2*>(S.z);
+  float* p = static_cast<float*>(S.p);
+  const float2* twx = static_cast<const float2*>(S.twx);
+  const float2* twy = static_cast<const float2*>(S.twy);
+  const float* sx = static_cast<const float*>(S.symx);
+  const float* sy = static_cast<const float*>(S.symy);
+  cudaError_t e;
+  switch (ilog2(g.nx)) {
+    case 5: e = launch_rows_fwd<5>(w, Z, g.ny, ntr, twx, idx, idy, st); break;
+    case 6: e = launch_rows_fwd<6>(w, Z, g.ny, ntr, twx, idx, idy, st); break;
+    case 7: e = launch_rows_fwd<7>(w, Z, g.ny, ntr, twx, idx, idy, st); break;
+    case 8: e = launch_rows_fwd<8>(w, Z, g.ny, ntr, twx, idx, idy, st); break;
+    case 9: e = launch_rows_fwd<9>(w, Z, g.ny, ntr, twx, idx, idy, st); break;
+    case 10: e = launch_rows_fwd<10>(w, Z, g.ny, ntr, twx, idx, idy, st); break;
+    default: e = launch_rows_fwd<11>(w, Z, g.ny, ntr, twx, idx, idy, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  switch (ilog2(g.ny)) {
+    case 5: e = launch_cols<5>(Z, g.nx, ncols, twy, sx, sy, st); break;
+    case 6: e = launch_cols<6>(Z, g.nx, ncols, twy, sx, sy, st); break;
+    case 7: e = launch_cols<7>(Z, g.nx, ncols, twy, sx, sy, st); break;
+    case 8: e = launch_cols<8>(Z, g.nx, ncols, twy, sx, sy, st); break;
+    case 9: e = launch_cols<9>(Z, g.nx, ncols, twy, sx, sy, st); break;
+    case 10: e = launch_cols<10>(Z, g.nx, ncols, twy, sx, sy, st); break;
+    default: e = launch_cols<11>(Z, g.nx, ncols, twy, sx, sy, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  const float scale = 1.0f / ((float)g.nx * (float)g.ny);
+  switch (ilog2(g.nx)) {
+    case 5: e = launch_rows_inv<5>(Z, p, ntr, twx, scale, st); break;
+    case 6: e = launch_rows_inv<6>(Z, p, ntr, twx, scale, st); break;
+    case 7: e = launch_rows_inv<7>(Z, p, ntr, twx, scale, st); break;
+    case 8: e = launch_rows_inv<8>(Z, p, ntr, twx, scale, st); break;
+    case 9: e = launch_rows_inv<9>(Z, p, ntr, twx, scale, st); break;
+    case 10: e = launch_rows_inv<10>(Z, p, ntr, twx, scale, st); break;
+    default: e = launch_rows_inv<11>(Z, p, ntr, twx, scale, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  const size_t cells = (size_t)g.batch * g.nx * g.ny;
+  gproj_grad_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(w, p, g.nx, g.ny, g.batch, idx, idy);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t generic_step(fd_ctx* c, cudaStream_t st) {
   GenericState& S = *c->gen;
@@ -100,6 +335,7 @@ cudaError_t generic_step(fd_ctx* c, cudaStream_t st) {
   a.nx = g.nx;
   a.ny = g.ny;
   a.forced = c->forcing.kind;
+  a.burgers = g.flow == FD_BURGERS;
   a.dt = (T)c->dt;
   a.nu = (T)c->nu;
   a.idx = (T)(g.nx / g.lx);
@@ -118,7 +354,10 @@ cudaError_t generic_step(fd_ctx* c, cudaStream_t st) {
       generic_stage_kernel<T, 4><<<grid, 256, 0, st>>>(a);
     else
       generic_stage_kernel<T, 2><<<grid, 256, 0, st>>>(a);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && g.flow == FD_NAVIER_STOKES) {
+      if constexpr (sizeof(T) == 4) e = generic_project(c, reinterpret_cast<float*>(stage_out[s]), st);
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -130,9 +369,12 @@ cudaError_t generic_step_any(fd_ctx* c, cudaStream_t st) {
 
 }  // namespace
 
+// Burgers on a non-power-of-two or rectangular grid, Navier-Stokes on a
+// rectangular power-of-two grid, or either flow with path 3
 bool fd_generic_wanted(const fd_grid& g, int path) {
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-  return g.flow == FD_BURGERS && (path == 3 || !pow2(g.nx) || !pow2(g.ny) || g.nx != g.ny);
+  if (g.flow == FD_BURGERS) return path == 3 || !pow2(g.nx) || !pow2(g.ny) || g.nx != g.ny;
+  return pow2(g.nx) && pow2(g.ny) && (path == 3 || g.nx != g.ny);
 }
 
 fd_status fd_generic_init(fd_ctx* c) {
@@ -162,6 +404,36 @@ fd_status fd_generic_init(fd_ctx* c) {
       e = cudaMemcpy(S->frc, f.data(), g.ny * es, cudaMemcpyHostToDevice);
     }
   }
+  if (e == cudaSuccess && g.flow == FD_NAVIER_STOKES) {
+    // projection workspace and tables: complex spectrum, pressure, twiddles
+    // exp(-2 pi i m / L) (m < L/2) of both axes, the Poisson symbol per axis
+    const size_t cells = (size_t)g.batch * g.nx * g.ny;
+    e = cudaMalloc(&S->z, cells * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&S->p, cells * sizeof(float));
+    const double pi = 3.14159265358979323846;
+    auto twiddles = [&](void** dst, int L) {
+      std::vector<float2> tw(L / 2);
+      for (int m = 0; m < L / 2; ++m) tw[m] = make_float2((float)std::cos(2 * pi * m / L), (float)-std::sin(2 * pi * m / L));
+      if (e == cudaSuccess) e = cudaMalloc(dst, tw.size() * sizeof(float2));
+      if (e == cudaSuccess) e = cudaMemcpy(*dst, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    };
+    auto symbol = [&](void** dst, int L, double len) {
+      const double h = len / L;
+      std::vector<float> sy(L);
+      for (int k = 0; k < L; ++k) {
+        const int ks = k <= L / 2 ? k : k - L;  // signed frequency
+        const double sn = std::sin(pi * k / L), eta = 2 * pi * ks / len;
+        sy[k] = (float)(c->opts.poisson_symbol == 0 ? -(4.0 / (h * h)) * sn * sn : -eta * eta);
+      }
+      if (e == cudaSuccess) e = cudaMalloc(dst, L * sizeof(float));
+      if (e == cudaSuccess) e = cudaMemcpy(*dst, sy.data(), L * sizeof(float), cudaMemcpyHostToDevice);
+    };
+    if (e == cudaSuccess && (g.nx == 2048 || g.ny == 2048)) e = prepare_axis<11>();
+    twiddles(&S->twx, g.nx);
+    twiddles(&S->twy, g.ny);
+    symbol(&S->symx, g.nx, g.lx);
+    symbol(&S->symy, g.ny, g.ly);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fd_set_error(nullptr, FD_ENOMEM, "fd_init: generic-grid workspace: %s", cudaGetErrorString(e));
   return FD_OK;
@@ -172,7 +444,7 @@ void fd_generic_free(fd_ctx* c) {
   if (!S) return;
   if (S->graph) cudaGraphExecDestroy(S->graph);
   if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
-  void* ps[] = {S->un, S->wa, S->wb, S->acc, S->frc};
+  void* ps[] = {S->un, S->wa, S->wb, S->acc, S->frc, S->z, S->p, S->twx, S->twy, S->symx, S->symy};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete S;
@@ -205,7 +477,7 @@ fd_status fd_generic_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
     }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, S.un, bytes, cudaMemcpyDeviceToDevice, st);
-  c->launches = 4 * n_steps;
+  c->launches = (c->grid.flow == FD_NAVIER_STOKES ? 4 * 5 : 4) * n_steps;
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout (generic grid): %s", cudaGetErrorString(e));
   return FD_OK;
 }

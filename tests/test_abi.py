@@ -124,8 +124,11 @@ def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):
     # the learned path is on chip only
     st, _ = _init(lib, n=512, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
     assert st == fd.FD_EUNSUPPORTED
-    # the generic-grid path is built for Burgers; an unknown path value is invalid
-    st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 3))
+    # Navier-Stokes on the generic-grid path is FP32 with nx, ny in [32, 2048]; an
+    # unknown path value is invalid
+    st, _ = _init(lib, n=64, dtype=fd.FD_F64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 3))
+    assert st == fd.FD_EUNSUPPORTED
+    st, _ = _init(lib, n=16, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 3))
     assert st == fd.FD_EUNSUPPORTED
     st, _ = _init(lib, n=25, flow=fd.FD_BURGERS, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
     assert st == fd.FD_EUNSUPPORTED

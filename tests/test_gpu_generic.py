@@ -129,3 +129,58 @@ def test_generic_path_refusals():
     assert e.value.status == fd.FD_EUNSUPPORTED
     assert s.plan()["path"] == 4 and s.plan()["n_stream"] == 1
     s.close()
+
+
+def ns_ic(nx, ny, lx, ly, seed, b):
+    """Divergence-free smooth fields on a rectangular grid: random Fourier sums
+    projected by the oracle."""
+    p = O.Problem(nx=nx, ny=ny, lx=lx, ly=ly)
+    return np.stack([O.project(I.burgers_ic(nx, seed + k, lx=lx, ny=ny, ly=ly), p) for k in range(b)])
+
+
+@pytest.mark.parametrize("nx,ny,lx,ly,forced,dord,sym", [
+    (128, 64, 8.0, 4.0, False, 4, 0),   # the shear-flow model grid of Table 4
+    (64, 32, 6.283185307179586, 3.141592653589793, True, 2, 0),
+    (32, 64, 3.0, 5.0, False, 4, 1),
+])
+def test_navier_stokes_rectangular(nx, ny, lx, ly, forced, dord, sym):
+    """Navier-Stokes on rectangular power-of-two grids (generic-grid path with its
+    own FFT projection), FP32, against the oracle; the result is divergence-free."""
+    b = 2
+    U0 = ns_ic(nx, ny, lx, ly, 80, b).astype(np.float32).astype(np.float64)
+    kw = dict(nu=1e-3, dt=2e-3, lx=lx, ly=ly)
+    cfg = fd.Config(n=nx, ny=ny, batch=b, dtype="f32", deriv_order=dord, poisson_symbol=sym,
+                    forcing="kolmogorov" if forced else None, **kw)
+    p = O.Problem(nx=nx, ny=ny, flow=O.FLOW_NAVIER_STOKES, deriv_order=dord, poisson_symbol=sym,
+                  forcing_kind=1 if forced else 0, **kw)
+    for steps, tol in ((1, 1e-6), (20, 1e-4)):
+        g, _, launches = gpu_rollout(cfg, U0, steps)
+        ref = oracle_rollout(p, U0, steps)
+        err = rel_l2(g, ref)
+        assert err <= tol, (steps, err)
+        assert launches == 20 * steps
+    if sym == 0:  # the discrete symbol makes the projection exact (not the continuous one)
+        div = np.stack([O.divergence(g[k], p.dx, p.dy) for k in range(b)])
+        grad_scale = np.abs(g).max() / min(p.dx, p.dy)
+        assert np.abs(div).max() <= 1e-5 * grad_scale
+
+
+@pytest.mark.parametrize("nx,ny", [(1024, 512), (2048, 1024)])
+def test_navier_stokes_shear_dns_grids(nx, ny):
+    """The shear-flow DNS grids (1024 x 512 in Table 4, 2048 x 1024 in Table S2):
+    one step against the oracle (2048-point transforms use the opt-in shared memory)."""
+    lx, ly = 8.0, 4.0
+    U0 = ns_ic(nx, ny, lx, ly, 90, 1).astype(np.float32).astype(np.float64)
+    cfg = fd.Config(n=nx, ny=ny, batch=1, dtype="f32", nu=1e-3, dt=3.125e-4, lx=lx, ly=ly)
+    p = O.Problem(nx=nx, ny=ny, lx=lx, ly=ly, nu=1e-3, dt=3.125e-4)
+    g, _, _ = gpu_rollout(cfg, U0, 1)
+    assert rel_l2(g, oracle_rollout(p, U0, 1)) <= 1e-6
+
+
+def test_navier_stokes_generic_path_matches_on_chip_path():
+    n, b = 64, 2
+    U0 = np.stack([I.decaying_ic(n, 100 + k) for k in range(b)]).astype(np.float32)
+    base = dict(n=n, batch=b, dtype="f32", nu=1e-3, dt=5e-3)
+    on_chip, _, _ = gpu_rollout(fd.Config(**base), U0, 20)
+    gen, _, _ = gpu_rollout(fd.Config(**base, path=3), U0, 20)
+    assert rel_l2(gen, on_chip) <= 1e-5

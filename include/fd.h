@@ -61,11 +61,13 @@ typedef enum { FD_BURGERS = 0, FD_NAVIER_STOKES = 1 } fd_flow;
  * and tensor memory for the whole rollout; FP32 N <= 256, FP64 N <= 128) and
  * the streaming path for larger grids (FP32, N up to 2048: tiled flux kernels
  * and a three-pass FFT projection through HBM, one CUDA graph per step).
- * Burgers (no projection, hence no FFT) also runs on any grid, including
- * non-power-of-two and rectangular ones (nx, ny in [4, 8192]; the paper's
- * Burgers case is [0, 1]^2 at 100^2 and 25^2, App. C.1): the generic-grid
- * path, four stage kernels per step through HBM, FP32 or FP64, state layout
- * [batch][2][ny][nx]. */
+ * The generic-grid path (path 3) takes the other grids, state layout
+ * [batch][2][ny][nx]: Burgers (no projection, hence no FFT) on any grid,
+ * including non-power-of-two and rectangular ones (nx, ny in [4, 8192], FP32
+ * or FP64; the paper's Burgers case is [0, 1]^2 at 100^2 and 25^2, App. C.1),
+ * and Navier-Stokes on rectangular power-of-two grids (nx, ny in [32, 2048],
+ * FP32; the shear-flow grids 128 x 64 ... 2048 x 1024), four stage kernels per
+ * step through HBM, each followed for Navier-Stokes by an FFT projection. */
 typedef struct {
   int32_t nx, ny;
   double lx, ly;
@@ -95,9 +97,11 @@ typedef struct {
   int32_t path;           /* 0 = automatic (default): on chip where built (FP32 N <= 256,
                              FP64 N <= 128), streaming through HBM otherwise, and the
                              generic-grid kernels for Burgers on a non-power-of-two or
-                             rectangular grid; 1 = on chip only; 2 = streaming (FP32, N in
-                             [32, 2048]); 3 = generic grid (Burgers only, any nx x ny in
-                             [4, 8192]^2, FP32 or FP64, no learned module) */
+                             rectangular grid and Navier-Stokes on a rectangular power-of-two
+                             grid; 1 = on chip only; 2 = streaming (FP32, N in [32, 2048]);
+                             3 = generic grid (Burgers on any nx x ny in [4, 8192]^2, FP32 or
+                             FP64; Navier-Stokes on power-of-two nx, ny in [32, 2048], FP32;
+                             no learned module) */
   int32_t fno_layers;     /* frequency-domain operator O_F of the learnable module (Sec. 3.4):
                              Fourier layers, 0 = off (default); needs learned = 1; forward only
                              (the reverse-mode calls refuse a context that has it) */

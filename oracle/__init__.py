@@ -19,3 +19,4 @@ this package.
 
 from .fv import *  # noqa: F401,F403
 from .fno import FNOParams, fno_forward, spectral_conv  # noqa: F401
+from .scalar import rk4_step_scalar, rollout_scalar, scalar_tendency  # noqa: F401

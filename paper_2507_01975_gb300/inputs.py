@@ -108,6 +108,29 @@ def shear_ic(n: int, delta: float = math.pi / 15, eps: float = 0.05) -> np.ndarr
     return np.stack([u, v])
 
 
+def shear_scalar_ic(nx: int = 128, ny: int = 64, lx: float = 8.0, ly: float = 4.0, seed: int = 0,
+                    eps: float = 0.05, n_blobs: int = 2, w: float = 0.5):
+    """Shear-flow initial state with its passive scalar on [0, lx] x [0, ly]
+    (the shear-flow case's recipe: two tanh shear layers of width w, vortices
+    sin(n_blobs pi x) exp(-25 w^2 (y - y_k)^2) in v, seeded noise of amplitude eps,
+    the scalar aligned with the layers). The layers sit at y_1 = ly / 4 and
+    y_2 = 3 ly / 4 with opposite signs, u = tanh(5 (y - y_1) / w) - tanh(5 (y -
+    y_2) / w) - 1, so the profile is periodic in y; s = (1 + u_profile) / 2 at the
+    cell centres. Returns (U [2, ny, nx], S [ny, nx]); U is not projected."""
+    rng = np.random.default_rng(seed)
+    (xu, yu), (xv, yv) = face_coords(nx, ny, lx, ly)
+    yc = (np.arange(ny)[:, None] + 0.5) * (ly / ny) * np.ones((1, nx))
+    ys = (0.25 * ly, 0.75 * ly)
+
+    def prof(y):
+        return np.tanh(5 * (y - ys[0]) / w) - np.tanh(5 * (y - ys[1]) / w) - 1.0
+
+    u = prof(yu) + eps * rng.standard_normal(yu.shape)
+    v = sum(np.sin(n_blobs * np.pi * xv) * np.exp(-25 * w * w * (yv - yk) ** 2) for yk in ys)
+    v = v + eps * rng.standard_normal(yv.shape)
+    return np.stack([u, v]), 0.5 * (1.0 + prof(yc))
+
+
 def taylor_green(n: int, t: float = 0.0, nu: float = 0.0) -> np.ndarray:
     """Taylor-Green vortex u = sin x cos y, v = -cos x sin y, times exp(-2 nu t)."""
     (xu, yu), (xv, yv) = face_coords(n, n)

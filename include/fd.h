@@ -154,6 +154,21 @@ fd_status fd_rollout(fd_ctx* ctx, const void* u0, void* traj, void* u_final, int
 fd_status fd_rollout_host(fd_ctx* ctx, const void* u0_host, void* u_final_host, int32_t n_steps,
                           void* stream);
 
+/* Rollout of the velocity together with a passive scalar s (shear flow,
+ * App. C.1: s_t - D lap s = -u . grad s), on a context of the generic-grid
+ * path (path 3; e.g. the shear flow's 128 x 64 grid on [0, 8] x [0, 4]).
+ * s lives at the cell centres, layout [batch][ny][nx] in the grid's dtype,
+ * and is advanced in flux form, -div(u s_f - D grad_f s), with its face values
+ * and face derivatives from the physics kernels (four more operator
+ * instances) and RK4 stages taken from the same (projected) stage velocities;
+ * it is not projected and does not act on the velocity. u0 / s0 are read,
+ * u_final / s_final written (they may alias u0 / s0). The first call
+ * allocates the scalar's device buffers. FD_EUNSUPPORTED on other paths;
+ * FD_EINVAL for null pointers, n_steps < 0 or a negative or non-finite
+ * diffusivity. */
+fd_status fd_rollout_scalar(fd_ctx* ctx, double diffusivity, const void* u0, const void* s0, void* u_final,
+                            void* s_final, int32_t n_steps, void* stream);
+
 /* Scan a device state [batch][2][ny][nx] for NaN/Inf. Synchronises `stream`.
  * Returns FD_OK or FD_ENONFINITE. */
 fd_status fd_check_finite(fd_ctx* ctx, const void* u, void* stream);

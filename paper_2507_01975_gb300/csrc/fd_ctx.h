@@ -148,6 +148,12 @@ struct GenericState {
   void* twy = nullptr;
   void* symx = nullptr;
   void* symy = nullptr;
+  // passive scalar (fd_rollout_scalar, allocated by its first call): state,
+  // two stage buffers, accumulator [batch][ny][nx]
+  void* sn = nullptr;
+  void* sa = nullptr;
+  void* sb = nullptr;
+  void* sacc = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 };

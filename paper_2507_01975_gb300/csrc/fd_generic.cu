@@ -41,14 +41,72 @@ struct GenArgs {
   const T* frc;  // [ny] forcing amplitude at the u-face rows
   int nx, ny, stage, forced, burgers;
   T dt, nu, idx, idy, drag;
+  // passive scalar (fd_rollout_scalar): stage scalar, scalar at the step start,
+  // accumulator, next stage scalar [batch][ny][nx]; sw == null: no scalar
+  const T* sw;
+  const T* sn;
+  T* sacc;
+  T* sout;
+  T diff;
 };
+
+// RK4 combination of one value (App. B.5): stage 0 starts the accumulator,
+// stages 1 and 2 add to it, stage 3 finishes the step
+template <typename T>
+__device__ __forceinline__ void rk_combine(int stage, T r, T dt, const T* un, T* acc, T* out, size_t e) {
+  const T h6 = dt / (T)6, h3 = dt / (T)3, h2 = dt * (T)0.5;
+  switch (stage) {
+    case 0: {
+      const T u0 = un[e];
+      acc[e] = u0 + h6 * r;
+      out[e] = u0 + h2 * r;
+      break;
+    }
+    case 1:
+      acc[e] += h3 * r;
+      out[e] = un[e] + h2 * r;
+      break;
+    case 2:
+      acc[e] += h3 * r;
+      out[e] = un[e] + dt * r;
+      break;
+    default:
+      out[e] = acc[e] + h6 * r;
+  }
+}
+
+// tendency of the passive scalar (shear flow, App. C.1) for the strip's 4
+// cells: -div(u s_f - D grad_f s) with the face value and face derivative of s
+// from the physics kernels along x at the u-faces and along y at the v-faces;
+// s[r][c] = s(row - 2 + r, col - 2 + c), u / v the velocity windows of the strip
+template <typename T, int DORD>
+__device__ __forceinline__ void strip_scalar(const T (&s)[5][8], const T (&u)[5][8], const T (&v)[5][8], T idx,
+                                             T idy, T D, T (&q)[4]) {
+  constexpr T d0 = DORD == 4 ? (T)(1.0 / 24.0) : (T)0;
+  constexpr T d1 = DORD == 4 ? (T)(-27.0 / 24.0) : (T)-1;
+  constexpr T d2 = DORD == 4 ? (T)(27.0 / 24.0) : (T)1;
+  constexpr T d3 = DORD == 4 ? (T)(-1.0 / 24.0) : (T)0;
+  auto der = [&](T f0, T f1, T f2, T f3, T ih) { return (d0 * f0 + d1 * f1 + d2 * f2 + d3 * f3) * ih; };
+  const T h = (T)0.5;
+  T Fx[5];  // x-fluxes through the u-faces c = 2 .. 6 of row 2
+#pragma unroll
+  for (int c = 2; c <= 6; ++c)
+    Fx[c - 2] = u[2][c] * h * (s[2][c - 1] + s[2][c]) - D * der(s[2][c - 2], s[2][c - 1], s[2][c], s[2][c + 1], idx);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = k + 2;
+    const T Fs = v[2][c] * h * (s[1][c] + s[2][c]) - D * der(s[0][c], s[1][c], s[2][c], s[3][c], idy);
+    const T Fn = v[3][c] * h * (s[2][c] + s[3][c]) - D * der(s[1][c], s[2][c], s[3][c], s[4][c], idy);
+    q[k] = -(Fx[k + 1] - Fx[k]) * idx - (Fn - Fs) * idy;
+  }
+}
 
 template <typename T, int DORD>
 __global__ void __launch_bounds__(256) generic_stage_kernel(const GenArgs<T> a) {
   const int strips = (a.nx + 3) >> 2;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= strips * a.ny) return;
-  const int row = q / strips, col0 = (q - row * strips) * 4;
+  const int sid = blockIdx.x * blockDim.x + threadIdx.x;  // strip index
+  if (sid >= strips * a.ny) return;
+  const int row = sid / strips, col0 = (sid - row * strips) * 4;
   const size_t NN = (size_t)a.nx * a.ny;
   const T* wu = a.w + (size_t)blockIdx.y * 2 * NN;
   const T* wv = wu + NN;
@@ -65,35 +123,26 @@ __global__ void __launch_bounds__(256) generic_stage_kernel(const GenArgs<T> a) 
   }
   T tu[4], tv[4];
   strip_tendency<T, DORD>(u, v, a.idx, a.idy, a.nu, a.burgers != 0, a.forced != 0, a.frc[row], a.drag, tu, tv);
-  const T h6 = a.dt / (T)6, h3 = a.dt / (T)3, h2 = a.dt * (T)0.5;
+  T sq[4] = {};
+  if (a.sw) {
+    const T* sb = a.sw + (size_t)blockIdx.y * NN;
+    T s[5][8];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const int j = (row - 2 + r + a.ny) % a.ny;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) s[r][c] = sb[(size_t)j * a.nx + (col0 - 2 + c + a.nx) % a.nx];
+    }
+    strip_scalar<T, DORD>(s, u, v, a.idx, a.idy, a.diff, sq);
+  }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int i = col0 + k;
     if (i >= a.nx) break;
     const size_t e = (size_t)blockIdx.y * 2 * NN + (size_t)row * a.nx + i;
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      const size_t ef = e + f * NN;
-      const T r = f == 0 ? tu[k] : tv[k];
-      switch (a.stage) {
-        case 0: {
-          const T un = a.un[ef];
-          a.acc[ef] = un + h6 * r;
-          a.wout[ef] = un + h2 * r;
-          break;
-        }
-        case 1:
-          a.acc[ef] += h3 * r;
-          a.wout[ef] = a.un[ef] + h2 * r;
-          break;
-        case 2:
-          a.acc[ef] += h3 * r;
-          a.wout[ef] = a.un[ef] + a.dt * r;
-          break;
-        default:
-          a.wout[ef] = a.acc[ef] + h6 * r;
-      }
-    }
+    rk_combine<T>(a.stage, tu[k], a.dt, a.un, a.acc, a.wout, e);
+    rk_combine<T>(a.stage, tv[k], a.dt, a.un, a.acc, a.wout, e + NN);
+    if (a.sw) rk_combine<T>(a.stage, sq[k], a.dt, a.sn, a.sacc, a.sout, (size_t)blockIdx.y * NN + (size_t)row * a.nx + i);
   }
 }
 
@@ -324,11 +373,20 @@ cudaError_t generic_project(fd_ctx* c, float* w, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// one step; with_scalar: the passive scalar with diffusivity diff advances
+// alongside (buffers S.sn, S.sa, S.sb, S.sacc)
 template <typename T>
-cudaError_t generic_step(fd_ctx* c, cudaStream_t st) {
+cudaError_t generic_step(fd_ctx* c, cudaStream_t st, bool with_scalar = false, double diff = 0.0) {
   GenericState& S = *c->gen;
   const fd_grid& g = c->grid;
   GenArgs<T> a;
+  a.sw = nullptr;
+  a.sn = static_cast<const T*>(S.sn);
+  a.sacc = static_cast<T*>(S.sacc);
+  a.diff = (T)diff;
+  T* const s_out[4] = {static_cast<T*>(S.sa), static_cast<T*>(S.sb), static_cast<T*>(S.sa), static_cast<T*>(S.sn)};
+  const T* const s_in[4] = {static_cast<const T*>(S.sn), static_cast<const T*>(S.sa), static_cast<const T*>(S.sb),
+                            static_cast<const T*>(S.sa)};
   a.un = static_cast<const T*>(S.un);
   a.acc = static_cast<T*>(S.acc);
   a.frc = static_cast<const T*>(S.frc);
@@ -350,6 +408,10 @@ cudaError_t generic_step(fd_ctx* c, cudaStream_t st) {
     a.stage = s;
     a.w = stage_in[s];
     a.wout = stage_out[s];
+    if (with_scalar) {
+      a.sw = s_in[s];
+      a.sout = s_out[s];
+    }
     if (c->opts.deriv_order == 4)
       generic_stage_kernel<T, 4><<<grid, 256, 0, st>>>(a);
     else
@@ -363,8 +425,9 @@ cudaError_t generic_step(fd_ctx* c, cudaStream_t st) {
   return cudaSuccess;
 }
 
-cudaError_t generic_step_any(fd_ctx* c, cudaStream_t st) {
-  return c->grid.dtype == FD_F64 ? generic_step<double>(c, st) : generic_step<float>(c, st);
+cudaError_t generic_step_any(fd_ctx* c, cudaStream_t st, bool with_scalar = false, double diff = 0.0) {
+  return c->grid.dtype == FD_F64 ? generic_step<double>(c, st, with_scalar, diff)
+                                 : generic_step<float>(c, st, with_scalar, diff);
 }
 
 }  // namespace
@@ -444,7 +507,8 @@ void fd_generic_free(fd_ctx* c) {
   if (!S) return;
   if (S->graph) cudaGraphExecDestroy(S->graph);
   if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
-  void* ps[] = {S->un, S->wa, S->wb, S->acc, S->frc, S->z, S->p, S->twx, S->twy, S->symx, S->symy};
+  void* ps[] = {S->un, S->wa, S->wb, S->acc, S->frc, S->z, S->p, S->twx, S->twy, S->symx, S->symy,
+                S->sn, S->sa, S->sb, S->sacc};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete S;
@@ -481,3 +545,39 @@ fd_status fd_generic_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fina
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout (generic grid): %s", cudaGetErrorString(e));
   return FD_OK;
 }
+
+extern "C" {
+
+fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const void* s0, void* u_final,
+                            void* s_final, int32_t n_steps, void* stream) {
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout_scalar: null context");
+  c->launches = 0;
+  if (!c->gen)
+    return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_scalar: the passive scalar runs on the generic-grid path (path 3)");
+  if (!u0 || !s0 || !u_final || !s_final) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: null pointer");
+  if (n_steps < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: n_steps must be >= 0");
+  if (!(diffusivity >= 0) || !std::isfinite(diffusivity))
+    return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: the diffusivity must be >= 0");
+  GenericState& S = *c->gen;
+  const fd_grid& g = c->grid;
+  const size_t sbytes = (size_t)g.batch * g.nx * g.ny * (g.dtype == FD_F64 ? sizeof(double) : sizeof(float));
+  cudaError_t e = cudaSuccess;
+  if (!S.sn) {  // scalar buffers, allocated by the first call
+    void** bufs[4] = {&S.sn, &S.sa, &S.sb, &S.sacc};
+    for (void** p : bufs)
+      if (e == cudaSuccess) e = cudaMalloc(p, sbytes);
+    if (e != cudaSuccess) return fd_set_error(c, FD_ENOMEM, "fd_rollout_scalar: cudaMalloc: %s", cudaGetErrorString(e));
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = fd_state_bytes(g);
+  e = cudaMemcpyAsync(S.un, u0, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S.sn, s0, sbytes, cudaMemcpyDeviceToDevice, st);
+  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) e = generic_step_any(c, st, true, diffusivity);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, S.un, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s_final, S.sn, sbytes, cudaMemcpyDeviceToDevice, st);
+  c->launches = (g.flow == FD_NAVIER_STOKES ? 4 * 5 : 4) * n_steps;
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout_scalar: %s", cudaGetErrorString(e));
+  return FD_OK;
+}
+
+}  // extern "C"

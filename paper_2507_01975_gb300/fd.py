@@ -26,6 +26,7 @@ EXPORTS = [
     "fd_step",
     "fd_rollout",
     "fd_rollout_host",
+    "fd_rollout_scalar",
     "fd_check_finite",
     "fd_check_finite_noalloc",
     "fd_last_launch_count",
@@ -133,6 +134,8 @@ def load(path: str = LIB_PATH):
     lib.fd_rollout.restype = C.c_int
     lib.fd_rollout_host.argtypes = [vp, vp, vp, i32, vp]
     lib.fd_rollout_host.restype = C.c_int
+    lib.fd_rollout_scalar.argtypes = [vp, C.c_double, vp, vp, vp, vp, i32, vp]
+    lib.fd_rollout_scalar.restype = C.c_int
     lib.fd_check_finite.argtypes = [vp, vp, vp]
     lib.fd_check_finite.restype = C.c_int
     lib.fd_last_launch_count.argtypes = [vp]
@@ -277,6 +280,11 @@ class Solver:
         tp = _ptr(traj) if traj is not None else None
         self._check(self.lib.fd_rollout(self.h, _ptr(u0), tp, _ptr(u_final), int(n_steps), int(save_every),
                                         _stream_handle(stream)))
+
+    def rollout_scalar(self, u0, s0, u_final, s_final, n_steps: int, diffusivity: float, stream=None):
+        """Velocity and passive scalar s [B, ny, nx] together (generic-grid path)."""
+        self._check(self.lib.fd_rollout_scalar(self.h, float(diffusivity), _ptr(u0), _ptr(s0), _ptr(u_final),
+                                               _ptr(s_final), int(n_steps), _stream_handle(stream)))
 
     def rollout_host(self, u0_host, u_final_host, n_steps: int, stream=None):
         self._check(self.lib.fd_rollout_host(self.h, _ptr(u0_host), _ptr(u_final_host), int(n_steps),

@@ -184,3 +184,76 @@ def test_navier_stokes_generic_path_matches_on_chip_path():
     on_chip, _, _ = gpu_rollout(fd.Config(**base), U0, 20)
     gen, _, _ = gpu_rollout(fd.Config(**base, path=3), U0, 20)
     assert rel_l2(gen, on_chip) <= 1e-5
+
+
+def gpu_scalar_rollout(cfg, U0, S0, steps, D):
+    s = fd.Solver(cfg)
+    dt = torch.float64 if cfg.dtype == "f64" else torch.float32
+    u = torch.tensor(U0, dtype=dt, device="cuda")
+    sc = torch.tensor(S0, dtype=dt, device="cuda")
+    uo, so = torch.empty_like(u), torch.empty_like(sc)
+    s.rollout_scalar(u, sc, uo, so, steps, D)
+    torch.cuda.synchronize()
+    res = uo.double().cpu().numpy(), so.double().cpu().numpy(), s.lib.fd_last_launch_count(s.h)
+    s.close()
+    return res
+
+
+@pytest.mark.parametrize("D", [1e-3, 2e-3])
+def test_shear_flow_with_passive_scalar(D):
+    """The shear flow (App. C.1: [0, 8] x [0, 4], Re = 1000, D in {1e-3, 2e-3}) on its
+    128 x 64 model grid at the coarse step 1e-2, FP32: velocity and scalar against
+    the oracle after 1 and 20 steps."""
+    from oracle.scalar import rollout_scalar
+
+    nx, ny, lx, ly, b = 128, 64, 8.0, 4.0, 2
+    p = O.Problem(nx=nx, ny=ny, lx=lx, ly=ly, nu=1e-3, dt=1e-2)
+    ics = [I.shear_scalar_ic(nx, ny, lx, ly, seed=k) for k in range(b)]
+    U0 = np.stack([O.project(u, p) for u, _ in ics]).astype(np.float32).astype(np.float64)
+    S0 = np.stack([s for _, s in ics]).astype(np.float32).astype(np.float64)
+    cfg = fd.Config(n=nx, ny=ny, batch=b, dtype="f32", nu=1e-3, dt=1e-2, lx=lx, ly=ly)
+    for steps, tol in ((1, 1e-6), (20, 1e-4)):
+        gu, gs, launches = gpu_scalar_rollout(cfg, U0, S0, steps, D)
+        ref = [rollout_scalar(U0[k], S0[k], p, D, steps) for k in range(b)]
+        assert rel_l2(gu, np.stack([r[0] for r in ref])) <= tol
+        assert rel_l2(gs, np.stack([r[1] for r in ref])) <= tol, (steps, rel_l2(gs, np.stack([r[1] for r in ref])))
+        assert launches == 20 * steps
+    # the velocity is not affected by the scalar
+    gu_only, _, _ = gpu_rollout(cfg, U0, 20)
+    assert np.array_equal(gu_only, gu)
+
+
+def test_passive_scalar_fp64_burgers_conservation():
+    """FP64, Burgers velocity on a ragged 25 x 18 grid: scalar against the oracle to
+    1e-12, total scalar conserved to round-off; zero velocity and zero diffusivity
+    leave the scalar unchanged."""
+    from oracle.scalar import rollout_scalar
+
+    nx, ny, lx, ly, D = 25, 18, 1.0, 0.8, 2e-3
+    p = O.Problem(nx=nx, ny=ny, lx=lx, ly=ly, nu=0.002, dt=1e-3, flow=O.FLOW_BURGERS)
+    U0 = I.burgers_ic(nx, 3, lx=lx, ny=ny, ly=ly)[None]
+    S0 = I.burgers_ic(nx, 4, lx=lx, ny=ny, ly=ly)[0][None] + 2.0
+    cfg = fd.Config(n=nx, ny=ny, batch=1, dtype="f64", flow="burgers", nu=0.002, dt=1e-3, lx=lx, ly=ly)
+    gu, gs, _ = gpu_scalar_rollout(cfg, U0, S0, 10, D)
+    ru, rs = rollout_scalar(U0[0], S0[0], p, D, 10)
+    assert rel_l2(gs[0], rs) <= 1e-12 and rel_l2(gu[0], ru) <= 1e-12
+    assert abs(gs.sum() - S0.sum()) <= 1e-12 * np.abs(S0).sum()
+    _, gs0, _ = gpu_scalar_rollout(cfg, np.zeros_like(U0), S0, 5, 0.0)
+    assert np.array_equal(gs0, S0)
+
+
+def test_passive_scalar_refusals():
+    s = fd.Solver(fd.Config(n=64, batch=1, dtype="f32", nu=1e-3, dt=1e-3))  # on-chip path
+    u = torch.zeros((1, 2, 64, 64), device="cuda")
+    sc = torch.zeros((1, 64, 64), device="cuda")
+    with pytest.raises(fd.FdError) as e:
+        s.rollout_scalar(u, sc, torch.empty_like(u), torch.empty_like(sc), 1, 1e-3)
+    assert e.value.status == fd.FD_EUNSUPPORTED
+    s.close()
+    s = fd.Solver(fd.Config(n=64, ny=32, batch=1, dtype="f32", nu=1e-3, dt=1e-3))
+    u = torch.zeros((1, 2, 32, 64), device="cuda")
+    sc = torch.zeros((1, 32, 64), device="cuda")
+    with pytest.raises(fd.FdError) as e:
+        s.rollout_scalar(u, sc, torch.empty_like(u), torch.empty_like(sc), 1, -1.0)
+    assert e.value.status == fd.FD_EINVAL
+    s.close()

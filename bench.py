@@ -556,7 +556,7 @@ def speed_measurement(fd, I, reps: int = 3):
     (stencil network, O_F of 6 layers / 32 modes / width 16, FNO temporal correction
     of 4 layers / 32 modes / width 8, k_c = 4; random weights) at dt = 32 x 2.19e-4;
     for Burgers the plain 25^2 solver at dt = 1e-2 (the learned module is built for
-    32^2 and 64^2 grids only). Shear flow is left out: its passive scalar is not built."""
+    32^2 and 64^2 grids only). Shear flow is left out: no learned module for its 128 x 64 grid."""
     import torch
 
     stream = torch.cuda.current_stream()

@@ -398,7 +398,7 @@ def corr_measurement(fd, I, n_fine: int = 1024, n_train: int = 4, n_test: int = 
     lv = labels[:, n_train:].contiguous()
     test0 = u_fine0[n_train:].contiguous()
     corr = torch.zeros(n_test, dtype=torch.float64, device="cuda")
-    judge = fd.Solver(fd.Config(n=nc, batch=n_test, dtype="f32"))
+    scorer = fd.Solver(fd.Config(n=nc, batch=n_test, dtype="f32"))
 
     def track(solver, n, steps_per_coarse):
         """Correlation curve (min over test trajectories) and wall time to the horizon."""
@@ -411,7 +411,7 @@ def corr_measurement(fd, I, n_fine: int = 1024, n_train: int = 4, n_test: int = 
         curve = []
         for k in range(kt):
             fd.downsample(traj[k], coarse, n // nc)
-            judge.vorticity_pcc(coarse, lv[k + 1], corr)
+            scorer.vorticity_pcc(coarse, lv[k + 1], corr)
             curve.append(float(corr.min().item()))
         solver.rollout(u0, last, kt * steps_per_coarse)  # warm graph
         wall = timed(lambda: solver.rollout(u0, last, kt * steps_per_coarse))

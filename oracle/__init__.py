@@ -18,5 +18,5 @@ this package.
 """
 
 from .fv import *  # noqa: F401,F403
-from .fno import FNOParams, fno_forward, spectral_conv  # noqa: F401
+from .fno import FNOParams, fno_forward, fno_vjp, spectral_conv, spectral_conv_vjp  # noqa: F401
 from .scalar import rk4_step_scalar, rollout_scalar, scalar_tendency  # noqa: F401

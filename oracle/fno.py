@@ -31,7 +31,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .fv import gelu
+from .fv import gelu, gelu_grad
 
 
 @dataclass
@@ -90,3 +90,63 @@ def fno_forward(U: np.ndarray, prm: FNOParams) -> np.ndarray:
         if l < prm.layers - 1:
             v = gelu(v)
     return pointwise(prm.Q_w, prm.Q_b, v)
+
+
+# ----------------------------------------------------------------------------
+# reverse mode (vector-Jacobian products), for training the operators
+# ----------------------------------------------------------------------------
+def _kept(a: np.ndarray, m: int) -> np.ndarray:
+    """The kept modes [C, 2M, M] of a spectrum [C, N, >= M] (rows 0 .. M-1 and N-M .. N-1)."""
+    n = a.shape[1]
+    return np.concatenate([a[:, :m, :m], a[:, n - m:, :m]], axis=1)
+
+
+def spectral_conv_vjp(v: np.ndarray, R: np.ndarray, ybar: np.ndarray):
+    """Adjoint of y = spectral_conv(v, R) for a cotangent ybar [C_out, N, N]:
+    (vbar [C_in, N, N], Rbar [2M, M, C_in, C_out]).
+
+    y is real-linear in v: y(x) = N^-2 sum_k c_k Re(Z_k e^{2 pi i k.x / N}) with Z
+    the mixed kept modes, c = 1 for kx = 0 and 2 otherwise (irfft2 counts each
+    kept half-plane mode with its mirror and drops the imaginary part of the kx = 0
+    column after the inverse along y). Hence Zbar = c N^-2 fft2(ybar) on the kept
+    modes, Sbar = conj(R)^T Zbar per mode, vbar = Re(sum_k Sbar_k e^{2 pi i k.x / N})
+    (the adjoint of the kept part of rfft2), and for the complex weights, with the
+    gradient written d/dRe + i d/dIm, Rbar = Zbar conj(S)."""
+    n = v.shape[1]
+    m = R.shape[1]
+    S = _kept(np.fft.rfft2(v), m)
+    c = np.where(np.arange(m) == 0, 1.0, 2.0)
+    Zbar = _kept(np.fft.fft2(ybar), m) * c[None, None, :] / n**2
+    Rbar = np.einsum("oyx,iyx->yxio", Zbar, np.conj(S))
+    Sbar = np.einsum("yxio,oyx->iyx", np.conj(R), Zbar)
+    E = np.zeros((v.shape[0], n, n), dtype=np.complex128)
+    E[:, :m, :m] = Sbar[:, :m]
+    E[:, n - m:, :m] = Sbar[:, m:]
+    return n**2 * np.real(np.fft.ifft2(E)), Rbar
+
+
+def fno_vjp(U: np.ndarray, prm: FNOParams, gbar: np.ndarray):
+    """Reverse mode of fno_forward: for the cotangent gbar of the output [c_out, N, N],
+    (Ubar [c_in, N, N], FNOParams of gradients; the R entries complex, d/dRe + i d/dIm).
+    Every rule is the transpose of a forward line: pointwise maps, GELU (its
+    derivative at the saved pre-activation), spectral_conv_vjp."""
+    v = [pointwise(prm.P_w, prm.P_b, U)]
+    pre = []
+    for l in range(prm.layers):
+        a = spectral_conv(v[-1], prm.R[l]) + pointwise(prm.W[l], prm.Wb[l], v[-1])
+        pre.append(a)
+        v.append(gelu(a) if l < prm.layers - 1 else a)
+    Q_w = np.einsum("qyx,iyx->qi", gbar, v[-1])
+    Q_b = gbar.sum(axis=(1, 2))
+    vbar = np.einsum("qi,qyx->iyx", prm.Q_w, gbar)
+    R, W, Wb = [None] * prm.layers, [None] * prm.layers, [None] * prm.layers
+    for l in reversed(range(prm.layers)):
+        abar = vbar * gelu_grad(pre[l]) if l < prm.layers - 1 else vbar
+        Wb[l] = abar.sum(axis=(1, 2))
+        W[l] = np.einsum("oyx,iyx->oi", abar, v[l])
+        vs, R[l] = spectral_conv_vjp(v[l], prm.R[l], abar)
+        vbar = np.einsum("oi,oyx->iyx", prm.W[l], abar) + vs
+    P_w = np.einsum("oyx,iyx->oi", vbar, U)
+    P_b = vbar.sum(axis=(1, 2))
+    Ubar = np.einsum("oi,oyx->iyx", prm.P_w, vbar)
+    return Ubar, FNOParams(P_w=P_w, P_b=P_b, R=R, W=W, Wb=Wb, Q_w=Q_w, Q_b=Q_b)

@@ -180,3 +180,66 @@ def test_ablation_variants():
     for m in (m1, m2):
         V = O.learned_step(U, p, m)
         assert np.abs(V.mean(axis=(1, 2)) - U.mean(axis=(1, 2))).max() < 1e-13
+
+
+def test_spectral_conv_vjp_dot_products():
+    """spectral_conv is real-linear in v and in R: <ybar, S(v)> = <vbar, v> and
+    <ybar, S_v(dR)> = Re sum conj(Rbar) dR, for M < N/2 and M = N/2."""
+    from oracle.fno import spectral_conv_vjp
+
+    rng = np.random.default_rng(14)
+    for n, m in ((16, 4), (16, 8), (12, 3)):
+        ci, co = 3, 2
+        v = rng.standard_normal((ci, n, n))
+        R = rng.standard_normal((2 * m, m, ci, co)) + 1j * rng.standard_normal((2 * m, m, ci, co))
+        ybar = rng.standard_normal((co, n, n))
+        vbar, Rbar = spectral_conv_vjp(v, R, ybar)
+        assert abs(np.sum(ybar * spectral_conv(v, R)) - np.sum(vbar * v)) < 1e-11 * np.abs(ybar).sum()
+        dR = rng.standard_normal(R.shape) + 1j * rng.standard_normal(R.shape)
+        assert abs(np.sum(ybar * spectral_conv(v, dR)) - np.real(np.sum(np.conj(Rbar) * dR))) < 1e-11 * np.abs(ybar).sum()
+
+
+def test_fno_vjp_against_finite_differences():
+    """Every gradient of fno_vjp against central differences of fno_forward (FP64):
+    the input, P, every layer's R (real and imaginary parts), W and b, and Q; a
+    random direction for the input."""
+    from oracle.fno import fno_vjp
+
+    rng = np.random.default_rng(15)
+    n, cin = 8, 4
+    prm = random_fno(rng, width=3, modes=3, layers=3, scale=0.5)
+    prm.P_w = rng.standard_normal((3, cin)) * 0.5
+    prm.Q_w = rng.standard_normal((2, 3)) * 0.5
+    prm.Q_b = rng.standard_normal(2) * 0.1
+    U = rng.standard_normal((cin, n, n))
+    gbar = rng.standard_normal((2, n, n))
+    Ubar, g = fno_vjp(U, prm, gbar)
+    L = lambda P, X=U: float(np.sum(gbar * fno_forward(X, P)))
+    eps = 1e-6
+
+    def fd(get, set_, idx, imag=False):
+        def shifted_params(delta):
+            P = FNOParams(P_w=prm.P_w.copy(), P_b=prm.P_b.copy(), R=[r.copy() for r in prm.R],
+                          W=[w.copy() for w in prm.W], Wb=[b.copy() for b in prm.Wb], Q_w=prm.Q_w.copy(),
+                          Q_b=prm.Q_b.copy())
+            a = get(P)
+            a[idx] += delta * (1j if imag else 1.0)
+            return P
+        return (L(shifted_params(eps)) - L(shifted_params(-eps))) / (2 * eps)
+
+    checks = [
+        (lambda P: P.P_w, (1, 2), g.P_w[1, 2]), (lambda P: P.P_b, (0,), g.P_b[0]),
+        (lambda P: P.W[1], (2, 0), g.W[1][2, 0]), (lambda P: P.Wb[2], (1,), g.Wb[2][1]),
+        (lambda P: P.Q_w, (1, 1), g.Q_w[1, 1]), (lambda P: P.Q_b, (0,), g.Q_b[0]),
+    ]
+    for get, idx, want in checks:
+        got = fd(get, None, idx)
+        assert abs(got - want) < 1e-6 * max(1.0, abs(want)), (idx, got, want)
+    for l, idx in ((0, (0, 1, 2, 1)), (2, (5, 0, 1, 0)), (1, (2, 2, 0, 2))):
+        want = g.R[l][idx]
+        re = fd(lambda P, l=l: P.R[l], None, idx)
+        im = fd(lambda P, l=l: P.R[l], None, idx, imag=True)
+        assert abs(re - want.real) < 1e-6 * max(1.0, abs(want)) and abs(im - want.imag) < 1e-6 * max(1.0, abs(want))
+    dU = rng.standard_normal(U.shape)
+    jvp = (L(prm, U + eps * dU) - L(prm, U - eps * dU)) / (2 * eps)
+    assert abs(jvp - np.sum(Ubar * dU)) < 1e-6 * max(1.0, abs(jvp))

@@ -231,3 +231,21 @@ def step_vjp(U: np.ndarray, p: Problem, lam: np.ndarray, model: Optional[Learned
     add(gr)
     lam_in += wb1
     return lam_in, (None if model is None else (acc_wl, acc_g))
+
+
+def temporal_correction_vjp(U: np.ndarray, hist, p: Problem, model: LearnedModel, gbar: np.ndarray):
+    """Reverse mode of ``oracle.fv.temporal_correction`` (Sec. 3.2, 3.5):
+    out = P(U + c - mean(c)), c = TC(concat(hist)), TC the CNN head or the FNO.
+    Returns (Ubar, [hist_bar per state], grads) with grads the CNN's [(dW, db)] or
+    the FNO's gradient FNOParams. The mean removal (identity minus the per-component
+    average) and the projection are symmetric, so each is its own transpose."""
+    g = project(gbar, p) if p.flow == FLOW_NAVIER_STOKES else gbar
+    cbar = g - g.mean(axis=(1, 2), keepdims=True)
+    x = np.concatenate([h for h in hist], axis=0)
+    if model.tc_fno is not None:
+        from .fno import fno_vjp
+
+        xbar, grads = fno_vjp(x, model.tc_fno, cbar)
+    else:
+        xbar, grads = cnn_vjp(x, model.tc, cbar)
+    return g.copy(), [xbar[2 * s:2 * s + 2] for s in range(len(hist))], grads

@@ -131,3 +131,60 @@ def test_adjoint_of_projection_is_projection():
     rng = np.random.default_rng(12)
     a, b = rng.standard_normal((2, 2, n, n))
     assert abs(np.sum(O.project(a, p) * b) - np.sum(a * O.project(b, p))) < 1e-12 * np.abs(a * b).sum()
+
+
+@pytest.mark.parametrize("flow", [O.FLOW_NAVIER_STOKES, O.FLOW_BURGERS])
+@pytest.mark.parametrize("head", ["cnn", "fno"])
+def test_temporal_correction_vjp(flow, head):
+    """Reverse mode of the temporal correction (CNN head and FNO): the dot product
+    with a central-difference JVP in the state and every history state, and central
+    differences on parameter entries."""
+    from oracle.adjoint import temporal_correction_vjp
+    from oracle.fno import FNOParams
+
+    rng = np.random.default_rng(16)
+    n, kc = 8, 3
+    p = O.Problem(nx=n, ny=n, nu=1e-2, dt=1e-2, flow=flow)
+    U = rng.standard_normal((2, n, n))
+    hist = [rng.standard_normal((2, n, n)) for _ in range(kc)]
+    m = O.LearnedModel(W_L=np.zeros((2, 2, 5, 4)), stencil=[], k_c=kc)
+    if head == "cnn":
+        m.tc = [(rng.standard_normal((4, 2 * kc, 3, 3)) * 0.3, rng.standard_normal(4) * 0.1),
+                (rng.standard_normal((2, 4, 3, 3)) * 0.3, rng.standard_normal(2) * 0.1)]
+    else:
+        w = 3
+        m.tc_fno = FNOParams(P_w=rng.standard_normal((w, 2 * kc)) * 0.4, P_b=rng.standard_normal(w) * 0.1,
+                             R=[(rng.standard_normal((6, 3, w, w)) + 1j * rng.standard_normal((6, 3, w, w))) * 0.2
+                                for _ in range(2)],
+                             W=[rng.standard_normal((w, w)) * 0.4 for _ in range(2)],
+                             Wb=[rng.standard_normal(w) * 0.1 for _ in range(2)],
+                             Q_w=rng.standard_normal((2, w)) * 0.4, Q_b=rng.standard_normal(2) * 0.1)
+    gbar = rng.standard_normal((2, n, n))
+    Ubar, hbar, grads = temporal_correction_vjp(U, hist, p, m, gbar)
+    L = lambda U_, h_: float(np.sum(gbar * O.temporal_correction(U_, h_, p, m)))
+    eps = 1e-6
+    dU = rng.standard_normal(U.shape)
+    dh = [rng.standard_normal(h.shape) for h in hist]
+    jvp = (L(U + eps * dU, [h + eps * d for h, d in zip(hist, dh)])
+           - L(U - eps * dU, [h - eps * d for h, d in zip(hist, dh)])) / (2 * eps)
+    vjp = np.sum(Ubar * dU) + sum(np.sum(b * d) for b, d in zip(hbar, dh))
+    assert abs(jvp - vjp) < 1e-6 * max(1.0, abs(jvp))
+    # parameter entries
+    if head == "cnn":
+        for l, idx in ((0, (1, 2, 0, 1)), (1, (0, 3, 2, 2))):
+            W = m.tc[l][0]
+            W[idx] += eps
+            lp = L(U, hist)
+            W[idx] -= 2 * eps
+            lm = L(U, hist)
+            W[idx] += eps
+            assert abs((lp - lm) / (2 * eps) - grads[l][0][idx]) < 1e-6 * max(1.0, abs(grads[l][0][idx]))
+    else:
+        for arr, garr, idx in ((m.tc_fno.P_w, grads.P_w, (1, 4)), (m.tc_fno.Q_w, grads.Q_w, (0, 2)),
+                               (m.tc_fno.W[1], grads.W[1], (2, 1))):
+            arr[idx] += eps
+            lp = L(U, hist)
+            arr[idx] -= 2 * eps
+            lm = L(U, hist)
+            arr[idx] += eps
+            assert abs((lp - lm) / (2 * eps) - garr[idx]) < 1e-6 * max(1.0, abs(garr[idx]))

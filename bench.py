@@ -90,6 +90,13 @@ def _clock_summary(lines, dev: int):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons)}
 
 
+# DRAM bytes (read + write) of one launch of the on-chip rollout kernel on the
+# 256^2 workload with 15 trajectories on chip, from an ncu capture
+# (profiles/fv_rollout_256x256_b16.md): the 7.86 MB state read plus a little;
+# the launch's final 7.86 MB write drains after the kernel ends and is not counted
+ONCHIP_DRAM_BYTES_PER_LAUNCH = 7.95e6
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -751,7 +758,12 @@ def main():
         "peak": peak,
         "unit": "TFLOP/s",
         "frac": achieved / peak,
-        "traffic": None,
+        # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel
+        # (15 on-chip trajectories; ncu capture of the unchanged kernel): the state
+        # is read once and written once per launch, whatever its number of steps
+        "traffic": ONCHIP_DRAM_BYTES_PER_LAUNCH if plan["n_onchip"] == 15 else None,
+        "traffic_unit": "bytes per launch",
+        "traffic_note": "ncu dram read+write of one launch; the final state write drains after the kernel",
         "kernel": f"fv_rollout_kernel<float, 8, {plan['cluster']}, 512, 4> ({plan['n_onchip']} of {BATCH} "
                   f"trajectories; {plan['n_stream']} on the streaming kernels concurrently)",
         "peak_basis": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x median sampled SM clock",

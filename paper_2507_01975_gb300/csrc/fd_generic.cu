@@ -562,11 +562,17 @@ fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const
   const fd_grid& g = c->grid;
   const size_t sbytes = (size_t)g.batch * g.nx * g.ny * (g.dtype == FD_F64 ? sizeof(double) : sizeof(float));
   cudaError_t e = cudaSuccess;
-  if (!S.sn) {  // scalar buffers, allocated by the first call
+  if (!S.sn) {  // scalar buffers, allocated by the first call (all four or none)
     void** bufs[4] = {&S.sn, &S.sa, &S.sb, &S.sacc};
     for (void** p : bufs)
       if (e == cudaSuccess) e = cudaMalloc(p, sbytes);
-    if (e != cudaSuccess) return fd_set_error(c, FD_ENOMEM, "fd_rollout_scalar: cudaMalloc: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      for (void** p : bufs) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+      }
+      return fd_set_error(c, FD_ENOMEM, "fd_rollout_scalar: cudaMalloc: %s", cudaGetErrorString(e));
+    }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = fd_state_bytes(g);

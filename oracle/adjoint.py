@@ -52,15 +52,21 @@ def unshift(g: np.ndarray, dj: int, di: int) -> np.ndarray:
     return shifted(g, -dj, -di)
 
 
-def tendency_vjp(U: np.ndarray, p: Problem, kernels, Tbar: np.ndarray, want_kbar: bool = False):
-    """Reverse mode of ``oracle.fv.tendency`` for fixed kernels.
+def tendency_vjp(U: np.ndarray, p: Problem, kernels, Tbar: np.ndarray, want_kbar: bool = False,
+                 extra: Optional[np.ndarray] = None, want_vbar: bool = False):
+    """Reverse mode of ``oracle.fv.tendency`` for fixed kernels (and fixed extra
+    face values, the frequency-domain operator's output, when given).
 
     Returns ``(Ubar, Kbar)``: the gradient with respect to the state through
-    the face values and the direct terms, and (when ``want_kbar``) the
-    per-location kernel gradients ``Kbar[q][5, 4, ny, nx]``.
+    the face-operator taps and the direct terms, and (when ``want_kbar``) the
+    per-location kernel gradients ``Kbar[q][5, 4, ny, nx]``; with ``want_vbar``
+    also the face-value cotangents ``vbar[q]`` (what flows into ``extra``).
     """
     dx, dy = p.dx, p.dy
-    Uc, Gxc, Uk, Gyu, Vk, Gxv, Vc, Gyc = face_values(U, kernels)
+    fv = face_values(U, kernels)
+    if extra is not None:
+        fv = [f + extra[q] for q, f in enumerate(fv)]
+    Uc, Gxc, Uk, Gyu, Vk, Gxv, Vc, Gyc = fv
     Tu, Tv = Tbar[0], Tbar[1]
     vbar = [None] * 8
     # advection of u: -(Uc^2 - W(Uc^2)) / dx
@@ -106,7 +112,7 @@ def tendency_vjp(U: np.ndarray, p: Problem, kernels, Tbar: np.ndarray, want_kbar
                 Ubar[fld] += unshift(K[r, c] * vbar[q], a, b)
                 if want_kbar:
                     Kbar[q][r, c] = vbar[q] * shifted(U[fld], a, b)
-    return Ubar, Kbar
+    return (Ubar, Kbar, vbar) if want_vbar else (Ubar, Kbar)
 
 
 def cnn_vjp(x: np.ndarray, layers, ybar: np.ndarray):
@@ -141,23 +147,42 @@ def cnn_vjp(x: np.ndarray, layers, ybar: np.ndarray):
 
 
 def learned_tendency_vjp(U: np.ndarray, p: Problem, model: LearnedModel, Tbar: np.ndarray):
-    """Reverse mode of H(U) = tendency(U, learned_kernels(U)).
+    """Reverse mode of H(U) = tendency(U, learned_kernels(U), O_F(U)).
 
-    Returns ``(Ubar, W_L_bar, stencil_grads)``.
+    Returns ``(Ubar, W_L_bar, stencil_grads, fno_grads)``; fno_grads is None without
+    a frequency-domain operator. The ablation variants follow the forward: without
+    the physics convolution the learned kernel is not projected, so neither is its
+    gradient; with the frequency operator only, the kernels are zero and the stencil
+    network's gradients are zero.
     """
+    extra = None
+    if model.fno is not None:
+        from .fno import fno_forward
+
+        extra = fno_forward(U, model.fno)
     ks = learned_kernels(U, p, model)
-    Ubar, Kbar = tendency_vjp(U, p, ks, Tbar, want_kbar=True)
+    Ubar, Kbar, vbar = tendency_vjp(U, p, ks, Tbar, want_kbar=model.ablation != 2, extra=extra, want_vbar=True)
     ny, nx = U.shape[1:]
-    Cbar = np.zeros((160, ny, nx))
     WLbar = np.zeros_like(model.W_L)
-    for q, (_fld, axis, kind, _shift) in enumerate(INSTANCES):
-        h = p.dx if axis == 0 else p.dy
-        scale = 1.0 / h if kind == 1 else 1.0
-        Lbar = consistency_project(Kbar[q]) * scale
-        Cbar[q * 20:(q + 1) * 20] = Lbar.reshape(20, ny, nx)
-        WLbar[kind, axis] += Lbar.sum(axis=(2, 3))
-    xbar, grads = cnn_vjp(U, model.stencil, Cbar)
-    return Ubar + xbar, WLbar, grads
+    if model.ablation == 2:
+        grads = [(np.zeros_like(W), np.zeros_like(b)) for W, b in model.stencil]
+    else:
+        Cbar = np.zeros((160, ny, nx))
+        for q, (_fld, axis, kind, _shift) in enumerate(INSTANCES):
+            h = p.dx if axis == 0 else p.dy
+            scale = 1.0 / h if kind == 1 else 1.0
+            Lbar = (consistency_project(Kbar[q]) if model.ablation == 0 else Kbar[q]) * scale
+            Cbar[q * 20:(q + 1) * 20] = Lbar.reshape(20, ny, nx)
+            WLbar[kind, axis] += Lbar.sum(axis=(2, 3))
+        xbar, grads = cnn_vjp(U, model.stencil, Cbar)
+        Ubar = Ubar + xbar
+    fno_grads = None
+    if model.fno is not None:
+        from .fno import fno_vjp
+
+        Ub_f, fno_grads = fno_vjp(U, model.fno, np.stack(vbar))
+        Ubar = Ubar + Ub_f
+    return Ubar, WLbar, grads, fno_grads
 
 
 def step_vjp(U: np.ndarray, p: Problem, lam: np.ndarray, model: Optional[LearnedModel] = None):
@@ -165,8 +190,9 @@ def step_vjp(U: np.ndarray, p: Problem, lam: np.ndarray, model: Optional[Learned
 
     u' = P(u + dt/6 (r1 + 2 r2 + 2 r3 + r4)), r_s = H(w_s), w_1 = u,
     w_2 = P(u + dt/2 r1), w_3 = P(u + dt/2 r2), w_4 = P(u + dt r3).
-    Returns ``(lam_in, grads)`` where ``grads`` is None for the plain step and
-    ``(W_L_bar, stencil_grads)`` for the learned step.
+    Returns ``(lam_in, grads)`` where ``grads`` is None for the plain step,
+    ``(W_L_bar, stencil_grads)`` for the learned step, and ``(W_L_bar,
+    stencil_grads, fno_grads)`` when the model has a frequency-domain operator.
     """
     ns = p.flow == FLOW_NAVIER_STOKES
     P = (lambda W: project(W, p)) if ns else (lambda W: W)
@@ -174,14 +200,18 @@ def step_vjp(U: np.ndarray, p: Problem, lam: np.ndarray, model: Optional[Learned
     def H(W):
         if model is None:
             return tendency(W, p)
+        if model.fno is not None:
+            from .fno import fno_forward
+
+            return tendency(W, p, learned_kernels(W, p, model), fno_forward(W, model.fno))
         return tendency(W, p, learned_kernels(W, p, model))
 
     def H_vjp(W, Tb):
         if model is None:
             Ub, _ = tendency_vjp(W, p, plain_kernels(p), Tb)
             return Ub, None
-        Ub, wlb, g = learned_tendency_vjp(W, p, model, Tb)
-        return Ub, (wlb, g)
+        Ub, wlb, g, fg = learned_tendency_vjp(W, p, model, Tb)
+        return Ub, (wlb, g, fg)
 
     # forward stage states
     w1 = U
@@ -200,17 +230,20 @@ def step_vjp(U: np.ndarray, p: Problem, lam: np.ndarray, model: Optional[Learned
     rb1 = p.dt / 6.0 * g
     acc_wl = np.zeros((2, 2, 5, 4)) if model is not None else None
     acc_g = None
+    acc_f = None
 
     def add(grads):
-        nonlocal acc_wl, acc_g
+        nonlocal acc_wl, acc_g, acc_f
         if grads is None:
             return
-        wlb, g_ = grads
+        wlb, g_, fg = grads
         acc_wl += wlb
         if acc_g is None:
             acc_g = [(dW.copy(), db.copy()) for dW, db in g_]
         else:
             acc_g = [(a0 + dW, a1 + db) for (a0, a1), (dW, db) in zip(acc_g, g_)]
+        if fg is not None:
+            acc_f = fg if acc_f is None else _fno_sum(acc_f, fg)
 
     wb4, gr = H_vjp(w4, rb4)
     add(gr)
@@ -230,7 +263,18 @@ def step_vjp(U: np.ndarray, p: Problem, lam: np.ndarray, model: Optional[Learned
     wb1, gr = H_vjp(w1, rb1)
     add(gr)
     lam_in += wb1
-    return lam_in, (None if model is None else (acc_wl, acc_g))
+    if model is None:
+        return lam_in, None
+    return lam_in, ((acc_wl, acc_g) if model.fno is None else (acc_wl, acc_g, acc_f))
+
+
+def _fno_sum(a, b):
+    """Sum of two FNOParams-shaped gradients."""
+    from .fno import FNOParams
+
+    return FNOParams(P_w=a.P_w + b.P_w, P_b=a.P_b + b.P_b, R=[x + y for x, y in zip(a.R, b.R)],
+                     W=[x + y for x, y in zip(a.W, b.W)], Wb=[x + y for x, y in zip(a.Wb, b.Wb)],
+                     Q_w=a.Q_w + b.Q_w, Q_b=a.Q_b + b.Q_b)
 
 
 def temporal_correction_vjp(U: np.ndarray, hist, p: Problem, model: LearnedModel, gbar: np.ndarray):

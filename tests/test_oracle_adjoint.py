@@ -188,3 +188,68 @@ def test_temporal_correction_vjp(flow, head):
             lm = L(U, hist)
             arr[idx] += eps
             assert abs((lp - lm) / (2 * eps) - garr[idx]) < 1e-6 * max(1.0, abs(garr[idx]))
+
+
+def _fno_small(seed, width=3, modes=2, layers=2):
+    rng = np.random.default_rng(seed)
+    return O.FNOParams(P_w=rng.standard_normal((width, 2)) * 0.4, P_b=rng.standard_normal(width) * 0.1,
+                       R=[(rng.standard_normal((2 * modes, modes, width, width))
+                           + 1j * rng.standard_normal((2 * modes, modes, width, width))) * 0.2 for _ in range(layers)],
+                       W=[rng.standard_normal((width, width)) * 0.4 for _ in range(layers)],
+                       Wb=[rng.standard_normal(width) * 0.1 for _ in range(layers)],
+                       Q_w=rng.standard_normal((8, width)) * 0.05, Q_b=rng.standard_normal(8) * 0.01)
+
+
+@pytest.mark.parametrize("ablation,with_fno,flow", [(0, True, O.FLOW_NAVIER_STOKES), (1, False, O.FLOW_NAVIER_STOKES),
+                                                    (1, True, O.FLOW_BURGERS), (2, True, O.FLOW_NAVIER_STOKES)])
+def test_learned_step_vjp_with_fno_and_ablations(ablation, with_fno, flow):
+    """Reverse mode of the learned step with the frequency-domain operator and the
+    ablation variants: dot product with a fourth-order finite-difference JVP, and
+    central differences on a W_L entry and on O_F parameters."""
+    n = 8
+    p = O.Problem(nx=n, ny=n, nu=0.02, dt=0.02, flow=flow, forcing_kind=1 if flow == O.FLOW_NAVIER_STOKES else 0)
+    model = small_model(11, n)
+    model.ablation = ablation
+    model.fno = _fno_small(12) if with_fno else None
+    rng = np.random.default_rng(13)
+    U = I.kolmogorov_ic(n, 5) if flow == O.FLOW_NAVIER_STOKES else I.burgers_ic(n, 5)
+    du = rng.standard_normal(U.shape)
+    if flow == O.FLOW_NAVIER_STOKES:
+        du = O.project(du, p)
+    lam = rng.standard_normal(U.shape)
+    jv = fd4_jvp(lambda x: O.learned_step(x, p, model), U, du, 1e-3)
+    lam_in, grads = A.step_vjp(U, p, lam, model)
+    lhs, rhs = np.sum(jv * lam), np.sum(du * lam_in)
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+    def loss_with(mod):
+        return np.sum(O.learned_step(U, p, mod) * lam)
+
+    eps = 1e-4
+    if ablation != 2:
+        idx = (1, 0, 2, 1)
+        def m(s):
+            import copy
+            mm = copy.copy(model)
+            mm.W_L = model.W_L.copy()
+            mm.W_L[idx] += s
+            return mm
+        fd = (loss_with(m(eps)) - loss_with(m(-eps))) / (2 * eps)
+        assert abs(fd - grads[0][idx]) <= 1e-6 * max(1e-3, abs(fd))
+    else:
+        assert np.all(grads[0] == 0)
+    if with_fno:
+        fg = grads[2]
+        for name, get, idx in (("Q_w", lambda f: f.Q_w, (3, 1)), ("W1", lambda f: f.W[1], (0, 2)),
+                               ("P_w", lambda f: f.P_w, (2, 0)), ("R0", lambda f: f.R[0], (1, 1, 0, 2))):
+            def m(s, get=get, idx=idx):
+                import copy
+                mm = copy.copy(model)
+                f = copy.deepcopy(model.fno)
+                get(f)[idx] += s
+                mm.fno = f
+                return mm
+            fd = (loss_with(m(eps)) - loss_with(m(-eps))) / (2 * eps)
+            want = get(fg)[idx]
+            want = want.real if np.iscomplexobj(want) else want
+            assert abs(fd - want) <= 1e-6 * max(1e-3, abs(fd)), name

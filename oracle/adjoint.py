@@ -293,3 +293,65 @@ def temporal_correction_vjp(U: np.ndarray, hist, p: Problem, model: LearnedModel
     else:
         xbar, grads = cnn_vjp(x, model.tc, cbar)
     return g.copy(), [xbar[2 * s:2 * s + 2] for s in range(len(hist))], grads
+
+
+def scalar_tendency_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, qbar: np.ndarray):
+    """Reverse mode of ``oracle.scalar.scalar_tendency``: (Ubar, Sbar) for the
+    cotangent qbar of -div(u s_f - D grad_f s); every rule is the transpose of a
+    forward line (flux difference, product with the face velocity, face operators)."""
+    from .scalar import SCALAR_INSTANCES, SCALAR_SHIFT, scalar_face_values
+
+    sx, _gx, sy, _gy = scalar_face_values(S, p)
+    Fx_bar = (qbar - shifted(qbar, 0, -1)) / p.dx
+    Fy_bar = (qbar - shifted(qbar, -1, 0)) / p.dy
+    Ubar = np.stack([Fx_bar * sx, Fy_bar * sy])
+    face_bar = [Fx_bar * U[0], -D * Fx_bar, Fy_bar * U[1], -D * Fy_bar]
+    Sbar = np.zeros_like(S)
+    for (axis, kind), vb in zip(SCALAR_INSTANCES, face_bar):
+        K = physics_kernel(kind, p.deriv_order, p.dx if axis == 0 else p.dy)
+        for r in range(5):
+            for c in range(4):
+                if K[r, c] == 0.0:
+                    continue
+                a, b = (r - 2, c + SCALAR_SHIFT) if axis == 0 else (c + SCALAR_SHIFT, r - 2)
+                Sbar += unshift(K[r, c] * vb, a, b)
+    return Ubar, Sbar
+
+
+def rk4_step_scalar_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, lamU: np.ndarray, lamS: np.ndarray):
+    """Reverse mode of ``oracle.scalar.rk4_step_scalar``: (Ubar, Sbar) for the
+    cotangents of (u_{k+1}, s_{k+1}). The scalar's stages depend on the stage
+    velocities, so every stage's velocity cotangent collects the scalar term too."""
+    from .scalar import scalar_tendency
+
+    ns = p.flow == FLOW_NAVIER_STOKES
+    P = (lambda W: project(W, p)) if ns else (lambda W: W)
+    dt = p.dt
+    H = lambda W: tendency(W, p)
+    H_vjp = lambda W, Tb: tendency_vjp(W, p, plain_kernels(p), Tb)[0]
+    w1, z1 = U, S
+    r1, q1 = H(w1), scalar_tendency(w1, z1, p, D)
+    w2, z2 = P(U + 0.5 * dt * r1), S + 0.5 * dt * q1
+    r2, q2 = H(w2), scalar_tendency(w2, z2, p, D)
+    w3, z3 = P(U + 0.5 * dt * r2), S + 0.5 * dt * q2
+    r3, q3 = H(w3), scalar_tendency(w3, z3, p, D)
+    w4, z4 = P(U + dt * r3), S + dt * q3
+    g = P(lamU)
+    Ubar, Sbar = g.copy(), lamS.copy()
+    rb = [dt / 6.0 * g, dt / 3.0 * g, dt / 3.0 * g, dt / 6.0 * g]
+    qb = [dt / 6.0 * lamS, dt / 3.0 * lamS, dt / 3.0 * lamS, dt / 6.0 * lamS]
+    ws, zs = [w1, w2, w3, w4], [z1, z2, z3, z4]
+    coef = [None, 0.5 * dt, 0.5 * dt, dt]  # w_s = P(U + coef_s r_{s-1}), z_s = S + coef_s q_{s-1}
+    for s in (3, 2, 1, 0):
+        wq, zb = scalar_tendency_vjp(ws[s], zs[s], p, D, qb[s])
+        wb = H_vjp(ws[s], rb[s]) + wq
+        if s == 0:
+            Ubar += wb
+            Sbar += zb
+        else:
+            Sbar += zb
+            qb[s - 1] = qb[s - 1] + coef[s] * zb
+            y = P(wb)
+            Ubar += y
+            rb[s - 1] = rb[s - 1] + coef[s] * y
+    return Ubar, Sbar

@@ -113,3 +113,37 @@ def test_shear_flow_initial_state():
         U, S = rk4_step_scalar(U, S, p, 0.001)
     assert abs(S.sum() - total) < 1e-10 * abs(total)
     assert np.abs(S).max() < 1.5
+
+
+@pytest.mark.parametrize("flow", [O.FLOW_NAVIER_STOKES, O.FLOW_BURGERS])
+def test_joint_step_vjp_dot_product(flow):
+    """Reverse mode of the joint velocity-scalar step against a fourth-order
+    finite-difference JVP of (u, s) -> (u', s')."""
+    from oracle.adjoint import rk4_step_scalar_vjp, scalar_tendency_vjp
+
+    p = grid(nx=10, ny=8, lx=2.5, ly=2.0, nu=0.02, dt=0.02, flow=flow)
+    rng = np.random.default_rng(17)
+    U = rng.standard_normal((2, p.ny, p.nx)) * 0.5
+    if flow == O.FLOW_NAVIER_STOKES:
+        U = O.project(U, p)
+    S = rng.standard_normal((p.ny, p.nx))
+    dU = rng.standard_normal(U.shape)
+    if flow == O.FLOW_NAVIER_STOKES:
+        dU = O.project(dU, p)
+    dS = rng.standard_normal(S.shape)
+    lamU, lamS = rng.standard_normal(U.shape), rng.standard_normal(S.shape)
+    D, e = 0.01, 1e-3
+
+    def f(t):
+        u1, s1 = rk4_step_scalar(U + t * dU, S + t * dS, p, D)
+        return np.sum(u1 * lamU) + np.sum(s1 * lamS)
+
+    jvp = (-f(2 * e) + 8 * f(e) - 8 * f(-e) + f(-2 * e)) / (12 * e)
+    Ub, Sb = rk4_step_scalar_vjp(U, S, p, D, lamU, lamS)
+    assert abs(jvp - (np.sum(Ub * dU) + np.sum(Sb * dS))) <= 1e-10 * abs(jvp)
+    # the tendency's reverse mode alone: a dot product in both arguments
+    qb = rng.standard_normal(S.shape)
+    g = lambda t: np.sum(scalar_tendency(U + t * dU, S + t * dS, p, D) * qb)
+    jv = (-g(2 * e) + 8 * g(e) - 8 * g(-e) + g(-2 * e)) / (12 * e)
+    tu, ts = scalar_tendency_vjp(U, S, p, D, qb)
+    assert abs(jv - (np.sum(tu * dU) + np.sum(ts * dS))) <= 1e-10 * abs(jv)

@@ -12,8 +12,10 @@ TEST INFRASTRUCTURE ONLY -- see the package docstring.
 * ``mse_loss``: the objective of Sec. 4 (Model Training), the mean over
   samples of the per-sample MSE, i.e. the mean over every rollout step,
   trajectory and element for samples of equal length.
-* ``rollout_vjp``: composition of ``adjoint.step_vjp`` over the steps of a
-  rollout (no checkpointing: the oracle keeps every state).
+* ``rollout_vjp`` / ``rollout_vjp_full``: composition of ``adjoint.step_vjp``
+  and ``adjoint.temporal_correction_vjp`` over the steps of a rollout (no
+  checkpointing: the oracle keeps every state); ``flat_grads`` lays the
+  parameter gradients out like the parameter array.
 * ``adam_step``: Adam (Kingma & Ba, 2015, Algorithm 1), the optimiser of the
   paper's training details.
 """
@@ -25,7 +27,7 @@ from typing import Optional
 import numpy as np
 
 from . import adjoint as A
-from .fv import LearnedModel, Problem, learned_step, rk4_step
+from .fv import LearnedModel, Problem, learned_step, rk4_step, temporal_correction
 
 
 def face_average(U: np.ndarray, r: int) -> np.ndarray:
@@ -53,25 +55,113 @@ def step(U: np.ndarray, p: Problem, model: Optional[LearnedModel]) -> np.ndarray
 
 
 def rollout_vjp(U0: np.ndarray, p: Problem, n: int, lam_traj: np.ndarray, model: Optional[LearnedModel] = None):
-    """Reverse mode of U0 -> (U_1 .. U_n) for the cotangents lam_traj[k] of U_{k+1}.
+    """Reverse mode of U0 -> (U_1 .. U_n) for the cotangents lam_traj[k] of U_{k+1},
+    for a model without a temporal correction (see ``rollout_vjp_full``).
 
     Returns ``(lam0, grads)``; grads is None for the plain step and
     ``(W_L_bar, stencil_grads)`` summed over the steps for the learned one.
     """
-    states = [U0]
-    for _ in range(n):
-        states.append(step(states[-1], p, model))
-    lam = np.zeros_like(U0)
-    acc = None
-    for k in range(n - 1, -1, -1):
-        lam = lam + lam_traj[k]
-        lam, g = A.step_vjp(states[k], p, lam, model)
-        if g is not None:
-            if acc is None:
-                acc = (g[0].copy(), [(dW.copy(), db.copy()) for dW, db in g[1]])
-            else:
-                acc = (acc[0] + g[0], [(a + dW, b + db) for (a, b), (dW, db) in zip(acc[1], g[1])])
-    return lam, acc
+    lam, g = rollout_vjp_full(U0, p, n, lam_traj, model)
+    return lam, (None if g is None else (g["W_L"], g["stencil"]))
+
+
+def _has_tc(model: Optional[LearnedModel]) -> bool:
+    return model is not None and model.k_c > 0 and (model.tc_fno is not None or len(model.tc) > 0)
+
+
+def rollout_states(U0: np.ndarray, p: Problem, n: int, model: Optional[LearnedModel] = None):
+    """States u_0 .. u_n of a rollout (``oracle.fv.rollout``) and, for each k, the FV
+    output before the temporal correction (Sec. 3.2: at k = M k_c,
+    u_k = P(FV(u_{k-1}) + TC(u_{k-k_c} .. u_{k-1}) - mean))."""
+    states, fv_out = [np.array(U0, dtype=np.float64)], [None]
+    for k in range(1, n + 1):
+        V = step(states[-1], p, model)
+        fv_out.append(V)
+        if _has_tc(model) and k % model.k_c == 0:
+            V = temporal_correction(V, states[k - model.k_c:k], p, model)
+        states.append(V)
+    return states, fv_out
+
+
+def _add(a, b):
+    """Sum of two gradients of the same kind (arrays, lists of (dW, db), FNOParams)."""
+    if a is None:
+        return b
+    if isinstance(a, np.ndarray):
+        return a + b
+    if isinstance(a, list):
+        return [(x0 + y0, x1 + y1) for (x0, x1), (y0, y1) in zip(a, b)]
+    return A._fno_sum(a, b)
+
+
+def rollout_vjp_full(U0: np.ndarray, p: Problem, n: int, lam_traj: np.ndarray, model: Optional[LearnedModel] = None):
+    """Reverse mode of U0 -> (U_1 .. U_n), the temporal correction included.
+
+    lam_traj[k] is the cotangent of U_{k+1}. A corrected state u_k (k = M k_c) sends
+    P(lam_k) into the FV step that produced it (``adjoint.step_vjp``; P is
+    idempotent and that step already ends with P) and, through
+    ``adjoint.temporal_correction_vjp``, cotangents to each of u_{k-k_c} .. u_{k-1};
+    every state's cotangent is the sum of what reaches it.
+
+    Returns ``(lam0, grads)``; grads is None for the plain step, else a dict with
+    'W_L', 'stencil' (list of (dW, db)), 'fno' (FNOParams or None) and 'tc' (list
+    of (dW, db) for the CNN head, FNOParams for the FNO correction, None without a
+    correction), each summed over the steps.
+    """
+    states, fv_out = rollout_states(U0, p, n, model)
+    pending = [np.zeros_like(states[0]) for _ in range(n + 1)]
+    g = None if model is None else {"W_L": None, "stencil": None, "fno": None, "tc": None}
+    for k in range(n, 0, -1):
+        lam = pending[k] + lam_traj[k - 1]
+        if _has_tc(model) and k % model.k_c == 0:
+            lam, hbars, tg = A.temporal_correction_vjp(fv_out[k], states[k - model.k_c:k], p, model, lam)
+            for s, hb in enumerate(hbars):
+                pending[k - model.k_c + s] = pending[k - model.k_c + s] + hb
+            g["tc"] = _add(g["tc"], tg)
+        lam_in, sg = A.step_vjp(states[k - 1], p, lam, model)
+        pending[k - 1] = pending[k - 1] + lam_in
+        if sg is not None:
+            g["W_L"] = _add(g["W_L"], sg[0])
+            g["stencil"] = _add(g["stencil"], sg[1])
+            if len(sg) > 2:
+                g["fno"] = _add(g["fno"], sg[2])
+    return pending[0], g
+
+
+def flat_grads(g: dict, model: LearnedModel) -> np.ndarray:
+    """A gradient dict of ``rollout_vjp_full`` as one flat array in the parameter
+    layout of the library's parameter upload: W_L, the stencil layers (W then b),
+    the temporal correction (CNN layers, or the FNO operator), then O_F. An
+    operator is P_w, P_b, per layer R as [2M][M][Cin][Cout][re, im] (the real and
+    imaginary partial derivatives), W, b, then Q_w, Q_b. Absent gradients of
+    present parameters are zero."""
+    def operator(f, like):
+        if f is None:
+            f = like
+            zero = True
+        else:
+            zero = False
+        out = [f.P_w.ravel(), f.P_b.ravel()]
+        for R, W, b in zip(f.R, f.W, f.Wb):
+            out += [np.stack([R.real, R.imag], axis=-1).ravel(), W.ravel(), b.ravel()]
+        out += [f.Q_w.ravel(), f.Q_b.ravel()]
+        v = np.concatenate(out)
+        return np.zeros_like(v) if zero else v
+
+    parts = [np.asarray(g["W_L"] if g["W_L"] is not None else np.zeros_like(model.W_L)).ravel()]
+    st = g["stencil"] if g["stencil"] is not None else [(np.zeros_like(W), np.zeros_like(b)) for W, b in model.stencil]
+    for dW, db in st:
+        parts += [dW.ravel(), db.ravel()]
+    if _has_tc(model):
+        if model.tc_fno is not None:
+            parts.append(operator(g["tc"], model.tc_fno))
+        else:
+            tc = g["tc"] if g["tc"] is not None else [(np.zeros_like(W), np.zeros_like(b)) for W, b in model.tc]
+            for dW, db in tc:
+                parts += [dW.ravel(), db.ravel()]
+    if model.fno is not None:
+        parts.append(operator(g["fno"], model.fno))
+    return np.concatenate(parts)
 
 
 def adam_step(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int, lr: float = 1e-4,

@@ -91,9 +91,10 @@ def _clock_summary(lines, dev: int):
 
 
 # DRAM bytes (read + write) of one launch of the on-chip rollout kernel on the
-# 256^2 workload with 15 trajectories on chip, from an ncu capture
-# (profiles/fv_rollout_256x256_b16.md): the 7.86 MB state read plus a little;
-# the launch's final 7.86 MB write drains after the kernel ends and is not counted
+# 256^2 workload with 15 trajectories on chip, from an ncu capture of the
+# current kernel: the 7.86 MB state read plus a little; the launch's final
+# 7.86 MB write drains after the kernel ends and is not counted. None until a
+# capture of the current kernel exists.
 ONCHIP_DRAM_BYTES_PER_LAUNCH = 7.95e6
 
 
@@ -101,32 +102,102 @@ def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
-    except OSError:
+    except (OSError, ValueError):
         return {}
 
 
-def run_reference(args):
-    """FP64 oracle on the host cores, bounded sample of the same workload."""
+# the profiling recipe's fallback denominators, used only when no measured
+# peaks file is present on the box
+_FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def _peak(key: str):
+    """(value, basis) of a roofline denominator: measured on this machine when the
+    driver's peaks file exists, else the recipe's fallback."""
+    v = _measured_peaks().get(key)
+    if isinstance(v, (int, float)) and v > 0:
+        return float(v), "of measured"
+    return _FALLBACK_PEAKS[key], "of fallback"
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def _oracle_job(args):
+    """One oracle trajectory on one core (runs in a spawn-started worker):
+    ('c2', seed, steps) decaying 256^2; ('c1', seed, steps) Burgers 32^2 FP64
+    with 2nd-order operators; ('c3', seed, steps) learned 64^2 Kolmogorov.
+    Returns (cell-updates, seconds)."""
     import oracle as O
     from paper_2507_01975_gb300 import inputs as I
 
+    kind, seed, steps = args
+    if kind == "c2":
+        p = O.Problem(nx=N, ny=N, nu=NU, dt=DT)
+        U = I.decaying_ic(N, seed)
+        step = lambda U: O.rk4_step(U, p)  # noqa: E731
+    elif kind == "c1":
+        p = O.Problem(nx=32, ny=32, nu=0.01, dt=1e-3, flow=O.FLOW_BURGERS, deriv_order=2)
+        U = I.burgers_ic(32, seed)
+        step = lambda U: O.rk4_step(U, p)  # noqa: E731
+    else:
+        p = O.Problem(nx=64, ny=64, nu=1e-3, dt=1.75e-3, forcing_kind=1)
+        st = I.random_conv_stack(1, 2, 64, 160, last_scale=0.05)
+        model = O.LearnedModel(W_L=I.random_wl(3, 1e-2), stencil=st)
+        U = I.kolmogorov_ic(64, seed)
+        step = lambda U: O.learned_step(U, p, model)  # noqa: E731
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = step(U)
+    el = time.perf_counter() - t0
+    return U.shape[1] * U.shape[2] * steps, el
+
+
+def _pool(procs):
+    import multiprocessing as mp
+
+    pool = mp.get_context("spawn").Pool(procs)
+    pool.map(_oracle_job, [("c1", k, 1) for k in range(procs)])  # start and import in every worker
+    return pool
+
+
+def _rate_all_cores(pool, procs, kind, steps):
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_job, [(kind, k, steps) for k in range(procs)], chunksize=1)
+    wall = time.perf_counter() - t0
+    return sum(r[0] for r in res) / wall, wall
+
+
+def run_reference(args):
+    """FP64 oracle on all host cores (one trajectory per core), bounded sample of
+    the same workload: each bench step advances nproc trajectories of the 256^2
+    decaying flow by one time step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p = O.Problem(nx=N, ny=N, nu=NU, dt=DT)
-    U = I.decaying_ic(N, 0)
-    steps_per_sample = 3
+    procs = os.cpu_count() or 1
+    pool = _pool(procs)
     for _ in range(args.warmup):
-        U = O.rk4_step(U, p)
+        _rate_all_cores(pool, procs, "c2", 1)
     t = []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        for _ in range(steps_per_sample):
-            U = O.rk4_step(U, p)
-        t.append(time.perf_counter() - t0)
-    cells = N * N * steps_per_sample
+        t.append(_rate_all_cores(pool, procs, "c2", 1)[1])
+    pool.close()
+    pool.join()
+    cells = N * N * procs
     value = cells * args.steps / sum(t)
-    sample = f"1 trajectory x {steps_per_sample} time steps of the 256^2 decaying flow per bench step (FP64 numpy oracle)"
+    sample = (f"{procs} trajectories x 1 time step of the 256^2 decaying flow per bench step, one trajectory per "
+              f"host core (FP64 numpy oracle, {_cpu_model()})")
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -142,31 +213,41 @@ def run_reference(args):
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds: float = 12.0):
-    """Time the oracle as it stands on one host core for about `seconds`."""
-    import oracle as O
-    from paper_2507_01975_gb300 import inputs as I
-
-    p = O.Problem(nx=N, ny=N, nu=NU, dt=DT)
-    U = I.decaying_ic(N, 0)
-    U = O.rk4_step(U, p)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        U = O.rk4_step(U, p)
-        n += 1
-    el = time.perf_counter() - t0
+def cpu_baseline():
+    """Time the oracle as it stands on the host cores (about 20 s of CPU work):
+    one core, and every core with one trajectory each, on the headline workload
+    (decaying 256^2) and on the Burgers 32^2 FP64 and learned 64^2 Kolmogorov
+    workloads. The line's value is the all-core rate on the headline workload."""
+    procs = os.cpu_count() or 1
+    pool = _pool(procs)
+    per = {}
+    for kind, steps_one, steps_all, what in (
+            ("c2", 30, 30, "decaying NS 256^2 (FP64)"),
+            ("c1", 200, 200, "Burgers 32^2, 200 steps (FP64, 2nd-order operators)"),
+            ("c3", 1, 1, "learned 64^2 Kolmogorov step (stencil network in FP64 loops)")):
+        cells, el = _oracle_job((kind, 0, steps_one))
+        all_rate, wall = _rate_all_cores(pool, procs, kind, steps_all)
+        per[kind] = {"workload": what, "one_core": cells / el, "all_cores": all_rate,
+                     "one_core_sample": f"1 trajectory x {steps_one} steps ({el:.1f} s)",
+                     "all_cores_sample": f"{procs} trajectories x {steps_all} steps ({wall:.1f} s)"}
+    pool.close()
+    pool.join()
     return {
-        "value": N * N * n / el,
+        "value": per["c2"]["all_cores"],
         "unit": UNIT,
-        "cores": 1,
+        "cores": procs,
         "kind": "oracle",
-        "sample": f"1 trajectory of the 256^2 decaying flow, {n} time steps ({el:.1f} s, FP64 numpy, 1 thread)",
+        "cpu_model": _cpu_model(),
+        "nproc": procs,
+        "sample": per["c2"]["all_cores_sample"] + " of the 256^2 decaying flow, one trajectory per core "
+                                                  "(FP64 numpy, 1 thread per process)",
+        "per_workload": per,
     }
 
 
@@ -207,8 +288,9 @@ def learned_measurement(fd, I, steps: int = 60):
     ms_net = e0.elapsed_time(e1) / reps
     flop_net = 481_536 * n * n * b  # one stencil-network evaluation (6 conv3x3 layers)
     flop_step = (4 * 481_536 + (2 * kc * 64 * 9 * 2 + 4 * 64 * 64 * 9 * 2 + 64 * 2 * 9 * 2) / kc) * n * n * b
-    peaks = _measured_peaks()
-    peak = peaks.get("bf16_tflops_sustained") or 1757.0
+    # the network is timed on its own (a short burst of launches): burst peak
+    peak, basis = _peak("bf16_tflops")
+    peak_sus, _ = _peak("bf16_tflops_sustained")
     achieved = flop_net / (ms_net * 1e-3) / 1e12
     # the same step with the Fourier operators of the forced-flow configuration
     # (Table S3): O_F (6 layers, 32 modes, width 16) in the flux block and the
@@ -243,7 +325,8 @@ def learned_measurement(fd, I, steps: int = 60):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "stencil network forward (input packing + 7 conv3x3_tc_kernel launches per evaluation)",
-                     "peak_basis": "measured cuBLAS bf16 sustained (MEASURED_PEAKS.json)"},
+                     "peak_basis": f"cuBLAS bf16 burst ({basis}): the network is timed alone",
+                     "frac_of_sustained": achieved / peak_sus},
     }
 
 
@@ -301,7 +384,9 @@ def training_measurement(fd, I, iters: int = 5):
     }
 
 
-# algorithmic HBM bytes per cell and time step of the streaming path (FP32):
+# algorithmic minimum per cell and time step: read and write the FP32 state (u, v)
+ALGO_BYTES_PER_CELL_STEP = 16
+# HBM bytes per cell and time step that the streaming path's kernels move (FP32):
 # stage kernels 32 + 44 + 44 + 36, projections 4 x (12 + 8 + 8), final 20
 STREAM_BYTES_PER_CELL_STEP = 288
 
@@ -325,8 +410,9 @@ def fine_measurement(fd, I, steps: int = 40):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    gbs = STREAM_BYTES_PER_CELL_STEP * n * n / (ms * 1e-3) / 1e9
-    peak = _measured_peaks().get("hbm_gbs") or 6800.0
+    gbs = ALGO_BYTES_PER_CELL_STEP * n * n / (ms * 1e-3) / 1e9
+    gbs_model = STREAM_BYTES_PER_CELL_STEP * n * n / (ms * 1e-3) / 1e9
+    peak, basis = _peak("hbm_gbs")
     # energy spectrum of the final state (analysis kernels: row and column FFTs of
     # u + iv, shell sums); algorithmic traffic 24 B per cell (state in, complex
     # scratch out and back in)
@@ -347,17 +433,22 @@ def fine_measurement(fd, I, steps: int = 40):
         "finite": bool(s.check_finite(o)),
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                      "traffic": None, "kernel": "whole step (stage, FFT and final kernels)",
-                     "algorithmic_bytes_per_cell_step": STREAM_BYTES_PER_CELL_STEP,
-                     "frac_at_384_bytes_per_cell_step": 384 * n * n / (ms * 1e-3) / 1e9 / peak,
-                     "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"},
+                     "algorithmic_bytes_per_cell_step": ALGO_BYTES_PER_CELL_STEP,
+                     "peak_basis": f"copy bandwidth ({basis})",
+                     "implementation_model": {
+                         "bytes_per_cell_step": STREAM_BYTES_PER_CELL_STEP,
+                         "note": "HBM traffic of this implementation's 17 launches per step (each RK stage "
+                                 "reads and writes the state, accumulator and stage result, and every "
+                                 "projection passes its field through three FFT kernels)",
+                         "achieved_gbs": gbs_model, "frac": gbs_model / peak}},
         "energy_spectrum": {"ms": ms_spec, "kmax": n // 2,
                             "gbs_at_24_bytes_per_cell": 24 * n * n / (ms_spec * 1e-3) / 1e9,
                             "energy": float(spec.sum().item())},
     }
 
 
-def corr_measurement(fd, I, n_fine: int = 1024, n_train: int = 4, n_test: int = 2, warm: float = 4.0,
-                     horizon: float = 2.0, iters: int = 200, unroll: int = 16, lr: float = 1e-3):
+def corr_measurement(fd, I, n_fine: int = 2048, n_train: int = 4, n_test: int = 2, warm: float = 2.0,
+                     horizon: float = 2.0, iters: int = 200, unroll: int = 16, lr: float = 1e-3, rt: int = 32):
     """Wall time to a 0.95 vorticity correlation, learned vs plain FV (forced flow, Re = 1000).
 
     A fine plain-FV reference (n_fine^2, streaming path) is warmed up from random
@@ -375,7 +466,7 @@ def corr_measurement(fd, I, n_fine: int = 1024, n_train: int = 4, n_test: int = 
 
     nc, nu = 64, 1e-3
     dt_f = 2.19e-4 * 2048 / n_fine
-    rt = 16
+    rt = rt * n_fine // 2048  # coarse step = 32 x the 2048^2 fine step (Table S2)
     dt_c = rt * dt_f
     B = n_train + n_test
     kt = int(round(horizon / dt_c))
@@ -429,7 +520,7 @@ def corr_measurement(fd, I, n_fine: int = 1024, n_train: int = 4, n_test: int = 
     out = {"workload": f"forced NS (Re 1000), fine {n_fine}^2 reference coarse-grained to 64^2, "
                        f"{n_train} training / {n_test} test trajectories, horizon {horizon} time units",
            "solvers": {}}
-    for n in (64, 128, 256, 512):
+    for n in [m for m in (64, 128, 256, 512, 1024) if m < n_fine]:
         s = fd.Solver(fd.Config(n=n, batch=n_test, dtype="f32", nu=nu, dt=dt_f * n_fine / n, forcing="kolmogorov"))
         out["solvers"][f"plain{n}"] = track(s, n, rt * n // n_fine)
     # learned 64^2: last layer zero-initialised (starts as the plain solver), W_L = 0
@@ -621,6 +712,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-fine", action="store_true", help="skip the 2048^2 streaming-path measurement")
+    ap.add_argument("--no-corr", action="store_true",
+                    help="skip the wall-time-to-0.95-correlation measurement (learned vs plain FV)")
     ap.add_argument("--no-speed", action="store_true",
                     help="skip the GPU-seconds-per-physical-second measurement on the paper's grids")
     ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch", "speed"],
@@ -768,13 +861,15 @@ def main():
                   f"trajectories; {plan['n_stream']} on the streaming kernels concurrently)",
         "peak_basis": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x median sampled SM clock",
         "achieved_all_trajectories": FLOP_PER_CELL_STEP * units / avg_launch_s / 1e12,
-        "hbm_gbs_measured": _measured_peaks().get("hbm_gbs"),
+        "hbm_gbs": _peak("hbm_gbs")[0],
+        "hbm_gbs_basis": _peak("hbm_gbs")[1],
     }
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     learned = None if args.no_learned else learned_measurement(fd, I)
     training = None if args.no_training else training_measurement(fd, I)
     fine = None if args.no_fine else fine_measurement(fd, I)
     speed = None if args.no_speed else speed_measurement(fd, I)
+    corr = None if args.no_corr else corr_measurement(fd, I)
     line = {
         "metric": METRIC,
         "value": value,
@@ -809,6 +904,7 @@ def main():
         "training": training,
         "fine_grid": fine,
         "paper_speed_table": speed,
+        "wall_time_to_corr_095": corr,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -44,7 +44,7 @@ typedef enum {
   FD_ENOMEM = 2,        /* device or host allocation failed */
   FD_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
   FD_ENONFINITE = 4,    /* fd_check_finite found a NaN or Inf */
-  FD_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+  FD_ETIMEOUT = 5,      /* a bounded device wait gave up (reported by fd_check_finite) */
   FD_EUNSUPPORTED = 6   /* valid request that this build does not implement */
 } fd_status;
 
@@ -93,7 +93,14 @@ typedef struct {
   int32_t k_c;            /* temporal-correction interval, 0 = off (default) */
   int32_t poisson_symbol; /* 0 = discrete D2 G2 symbol (default, exact projection) */
   int32_t ckpt_every;     /* reserved for the adjoint: checkpoint interval */
-  int64_t spin_limit;     /* reserved: iteration limit of bounded device waits */
+  int64_t spin_limit;     /* iteration limit of each bounded mbarrier wait in the
+                             tensor-core kernels of the learned path (<= 0: the
+                             default, 2^20 tries); a wait that runs out sets the
+                             context's error word (fd_check_finite then returns
+                             FD_ETIMEOUT), and the kernel drains its own copies and
+                             MMAs in flight with a fixed limit, frees its tensor
+                             memory and returns. The outputs of that call are then
+                             undefined; the context stays usable */
   int32_t path;           /* 0 = automatic (default): on chip where built (FP32 N <= 256,
                              FP64 N <= 128), streaming through HBM otherwise, and the
                              generic-grid kernels for Burgers on a non-power-of-two or
@@ -154,6 +161,30 @@ fd_status fd_rollout(fd_ctx* ctx, const void* u0, void* traj, void* u_final, int
 fd_status fd_rollout_host(fd_ctx* ctx, const void* u0_host, void* u_final_host, int32_t n_steps,
                           void* stream);
 
+/* Learned rollout with the plain FV step as its fallback. The paper's learned
+ * module only adds learnable parts to the FV module; without them the step is
+ * the traditional solver (Sec. 3.4, O = O_P; the DNS solver of the Sec. 4
+ * ablation). The paper itself has no fallback mechanism; this call is the
+ * serving safeguard built on that relation. The batch advances in chunks of
+ * `chunk` time steps (<= 0: k_c, or 8 without a temporal correction; with
+ * k_c > 0 it must be a multiple of k_c, so the corrections fall on the same
+ * steps as in fd_rollout): each chunk runs the learned rollout and the plain
+ * rollout from the same chunk-start state, and a trajectory whose learned
+ * chunk produced a NaN or Inf takes the plain result and stays on the plain
+ * solver for the rest of the call. Trajectories that never fell back are
+ * bit-identical to fd_rollout's. A trajectory whose chunk-start state is
+ * already non-finite cannot be rescued: it falls back and stays non-finite.
+ * ctx: a learned context (FD_EUNSUPPORTED otherwise). u0 / u_final: device
+ * states [batch][2][n][n] FP32 (may alias). fell_back: device int32[batch],
+ * written: -1 for a trajectory that stayed learned, else the time step
+ * (0-based, a multiple of chunk) at which its fallback chunk started. The
+ * first call makes a plain context of the same grid and three state buffers
+ * (library-owned, freed by fd_destroy). No host synchronisation.
+ * FD_EINVAL for null pointers, n_steps < 0 or a chunk that is not a multiple
+ * of k_c. */
+fd_status fd_rollout_guarded(fd_ctx* ctx, const void* u0, void* u_final, int32_t n_steps, int32_t chunk,
+                             int32_t* fell_back, void* stream);
+
 /* Rollout of the velocity together with a passive scalar s (shear flow,
  * App. C.1: s_t - D lap s = -u . grad s), on a context of the generic-grid
  * path (path 3; e.g. the shear flow's 128 x 64 grid on [0, 8] x [0, 4]).
@@ -170,7 +201,9 @@ fd_status fd_rollout_scalar(fd_ctx* ctx, double diffusivity, const void* u0, con
                             void* s_final, int32_t n_steps, void* stream);
 
 /* Scan a device state [batch][2][ny][nx] for NaN/Inf. Synchronises `stream`.
- * Returns FD_OK or FD_ENONFINITE. */
+ * Returns FD_OK, FD_ENONFINITE, or (learned contexts, state finite) FD_ETIMEOUT
+ * when a bounded wait of a tensor-core kernel gave up since the last check
+ * (see fd_options.spin_limit); the timeout is reported once and then cleared. */
 fd_status fd_check_finite(fd_ctx* ctx, const void* u, void* stream);
 
 /* Number of kernel launches issued by the last fd_step / fd_rollout call. */
@@ -255,11 +288,33 @@ fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* 
  * lam_out. dparams: device float32 array of fd_param_count values in the
  * fd_set_params layout, ACCUMULATED into (+=); NULL skips the parameter
  * gradients. Stream-ordered; the first call allocates and synchronises.
- * Scope: FP32 contexts with N = 32 or 64, plain or learned without the
- * temporal correction (k_c = 0); FD_EUNSUPPORTED otherwise. FD_EINVAL for null
- * pointers, dparams on a plain context or parameters not yet set. */
+ * With a temporal correction (k_c > 0) this is the VJP of the FV step alone,
+ * the step fd_rollout takes before it applies a correction; the correction's
+ * own reverse mode is fd_tc_adjoint, and fd_rollout_adjoint / fd_train_step
+ * combine the two. Scope: FP32 contexts with N = 32 or 64, plain or learned
+ * (the temporal correction as a CNN head); FD_EUNSUPPORTED otherwise (the
+ * frequency-domain operator, the ablation variants, the FNO correction).
+ * FD_EINVAL for null pointers, dparams on a plain context or parameters not
+ * yet set. */
 fd_status fd_step_adjoint(fd_ctx* ctx, const void* u_in, const void* lam_out, void* lam_in, float* dparams,
                           void* stream);
+
+/* Reverse mode of one temporal correction (Sec. 3.2, Sec. 3.5):
+ * u_k = P(V + c - mean(c)), c = TC(u_{k-k_c}, .., u_{k-1}), V = FV(u_{k-1}),
+ * the CNN head of the correction (2 k_c -> 64 x4 -> 2, GELU). Given the
+ * cotangent lam of u_k: vbar = P(lam), the cotangent of V (P is symmetric and
+ * so is the mean removal, c_bar = P(lam) - mean), and hist_bar = the cotangents
+ * of the k_c history states through the network; dparams (may be NULL)
+ * accumulates the network's weight and bias gradients. The network's forward
+ * activations are recomputed; its data and weight gradients run on the tensor
+ * cores (BF16 operands, FP32 accumulation) except the first layer's data
+ * gradient (CUDA cores, FP32).
+ * hist: device [k_c][batch][2][n][n] float32 (u_{k-k_c} first); lam, vbar:
+ * [batch][2][n][n] (vbar may be NULL); hist_bar: [k_c][batch][2][n][n],
+ * written. A learned context with k_c > 0 and the CNN head; FD_EUNSUPPORTED
+ * otherwise, FD_EINVAL for null pointers or parameters not yet set. */
+fd_status fd_tc_adjoint(fd_ctx* ctx, const void* hist, const void* lam, void* vbar, void* hist_bar, float* dparams,
+                        void* stream);
 
 /* Reverse mode of an n-step rollout u_0 -> (u_1 .. u_n) with checkpoints:
  * lam_traj[n][batch][2][ny][nx] holds the cotangents dL/du_k of the states
@@ -267,8 +322,13 @@ fd_status fd_step_adjoint(fd_ctx* ctx, const void* u_in, const void* lam_out, vo
  * context, may be NULL) accumulates dL/dtheta. The forward pass keeps only the
  * states u_0, u_k, u_2k, ... (k = ckpt_every) and each segment is recomputed
  * before its steps are run backwards with fd_step_adjoint, so the memory
- * is (n/k + k + 1) states plus one step's workspace. Same scope as
- * fd_step_adjoint; the workspace grows on demand (allocating calls). */
+ * is (n/k + k + 1) states plus one step's workspace. With a temporal
+ * correction (k_c > 0) the corrected states' cotangents also flow back to
+ * their history windows (fd_tc_adjoint), k must be a multiple of k_c (so a
+ * window never crosses a checkpoint) and k_c more states are kept. Same scope
+ * as fd_step_adjoint; the workspace grows on demand (allocating calls).
+ * FD_EINVAL for null pointers, n_steps or ckpt_every < 1, or ckpt_every not a
+ * multiple of k_c. */
 fd_status fd_rollout_adjoint(fd_ctx* ctx, const void* u0, int32_t n_steps, int32_t ckpt_every,
                              const void* lam_traj, void* lam0, float* dparams, void* stream);
 
@@ -383,7 +443,10 @@ fd_status fd_autotune(fd_ctx* ctx, int32_t probe_steps, fd_plan* report, int32_t
  * paper has no counterpart (it advances one trajectory at a time); this is the
  * serving form of fd_rollout. A context may appear once per batch and must not
  * be used by other calls while its batch runs; the state pointers are fixed at
- * fd_batch_add (u_final may alias u0). */
+ * fd_batch_add (u_final may alias u0). A member whose launch plan changes
+ * between runs (fd_set_plan, fd_autotune) makes the next fd_batch_run capture
+ * the graph again, since a plan change can replace buffers the old graph used.
+ * Destroy the batch before any of its member contexts. */
 typedef struct fd_batch fd_batch; /* opaque, library-owned */
 
 fd_status fd_batch_create(fd_batch** out);
@@ -401,8 +464,8 @@ fd_status fd_destroy(fd_ctx* ctx);
  * The string is owned by the library and valid until the next call. */
 const char* fd_last_error(const fd_ctx* ctx);
 
-/* Largest element count fd_check_finite_noalloc accepts (2^24: a batch of
- * 16 FP32 256^2 states, or two 2048^2 ones). */
+/* Largest element count fd_check_finite_noalloc accepts (2^24 elements: a
+ * batch of 128 256^2 states, or of two 2048^2 states). */
 #define FD_NOALLOC_MAX_ELEMS (1 << 24)
 
 /* Allocation-free NaN/Inf scan for callers that must not allocate device
@@ -417,7 +480,8 @@ const char* fd_last_error(const fd_ctx* ctx);
  * on a device looks up that array's address: make it before any stream
  * capture. Calls that overlap on the GPU share the array and race.
  * Returns FD_OK (no NaN/Inf), FD_ENONFINITE, FD_EINVAL (null pointer, unknown
- * dtype, count < 0 or count > FD_NOALLOC_MAX_ELEMS) or FD_ECUDA. */
+ * dtype, count < 0 or count > FD_NOALLOC_MAX_ELEMS), FD_EUNSUPPORTED (the
+ * current device's index is 64 or more) or FD_ECUDA. */
 fd_status fd_check_finite_noalloc(const void* u, int64_t count, int32_t dtype, int64_t* nonfinite,
                                   void* stream);
 

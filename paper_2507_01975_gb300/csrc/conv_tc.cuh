@@ -50,6 +50,7 @@ struct ConvArgs {
   __nv_bfloat16* aux_out;       // mode 1: pre-activation is stored here when non-null
   unsigned* err;             // set to nonzero on a timed-out wait
   long long spin_limit;
+  float* dbias;              // mode 2: per-channel sums of the FP32 output added here (atomics), or null
 };
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -77,6 +78,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 // bounded wait for completion of the phase with parity `par`; false on time-out
+// Iteration limit of the waits that drain a CTA's own asynchronous work
+// (bulk copies, MMAs) before it exits after an error: independent of the
+// caller's limit, which can be small enough to make the regular waits give up.
+constexpr long long kDrainSpin = 1ll << 20;
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, long long limit) {
   for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
@@ -332,8 +338,8 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
     // NBUF tiles and the last weight load to land
     if (lane == 0) {
       for (int j = issued - NBUF; j < issued; ++j)
-        if (j >= 0) mbar_wait(a_full + j % NBUF, (uint32_t)((j / NBUF) & 1), lim);
-      if (wphase_waits > 0) mbar_wait(w_full, (wphase_waits - 1) & 1, lim);
+        if (j >= 0) mbar_wait(a_full + j % NBUF, (uint32_t)((j / NBUF) & 1), kDrainSpin);
+      if (wphase_waits > 0) mbar_wait(w_full, (wphase_waits - 1) & 1, kDrainSpin);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer -------------------------------------------------
@@ -342,6 +348,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
       int cur_part = -1;
       uint32_t wpar = 0;
       int i = 0;
+      int last = -1;  // last tile whose MMAs were committed
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
         const int part = t / npix;
         const int s = i & 1;                              // accumulator buffer
@@ -384,7 +391,11 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
         }
         umma_commit(a_empty + sa);
         umma_commit(c_full + s);
+        last = i;
       }
+      // the accumulators are freed below: wait (bounded) until the MMAs of the
+      // last committed tile, and with them every earlier one, have completed
+      if (last >= 0) mbar_wait(a_empty + last % NBUF, (uint32_t)((last / NBUF) & 1), kDrainSpin);
     }
   } else if (warp >= 4) {
     // ---------------- epilogue ---------------------------------------------------------
@@ -468,6 +479,17 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
             const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&z4[e]));
             outv[2 * e] *= gelu_grad_f(f.x);
             outv[2 * e + 1] *= gelu_grad_f(f.y);
+          }
+          if (a.dbias) {
+            // the layer's bias gradient is the pixel sum of this cotangent: taken
+            // here in FP32, before the BF16 rounding of the stored values
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float sv = outv[j];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+              if (lane == j) atomicAdd(a.dbias + co0 + cc + j, sv);
+            }
           }
         } else {
 #pragma unroll

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256, 1) conv_wgrad_kernel(const WgradArgs a) {
     // never leave with copies in flight
     if (lane == 0)
       for (int j = issued - 2; j < issued; ++j)
-        if (j >= 0) mbar_wait(full + (j & 1), (j >> 1) & 1, lim);
+        if (j >= 0) mbar_wait(full + (j & 1), (j >> 1) & 1, kDrainSpin);
   } else if (warp == 1) {
     // ---------------- MMA issuer ------------------------------------------------------
     if (lane == 0) {
@@ -198,6 +198,8 @@ __global__ void __launch_bounds__(256, 1) conv_wgrad_kernel(const WgradArgs a) {
         umma_commit(empty + s);
       }
       umma_commit(done);
+      // tensor memory is freed below: wait (bounded) for every MMA issued here
+      mbar_wait(done, 0, kDrainSpin);
     }
   } else if (warp >= 4) {
     // ---------------- bias sums during the loop, accumulator read-out at the end ------
@@ -288,6 +290,7 @@ struct WgradReduceArgs {
   float* dW;
   float* db;
   int gx, parts, cin, co_base;
+  int cout_real;  // output channels of the layer: tile channels at or beyond it carry padding
 };
 
 template <int CIN, int O_TILE>
@@ -310,13 +313,13 @@ __global__ void __launch_bounds__(256) conv_wgrad_reduce_kernel(const WgradReduc
       float s = 0.f;
       for (int x = 0; x < a.gx; ++x) s += src[(size_t)x * cta_stride];
       const int co = a.co_base + part * O_TILE + o;
-      a.dW[(((size_t)co * a.cin + c) * 3 + ay) * 3 + dx] += s;
+      if (co < a.cout_real) a.dW[(((size_t)co * a.cin + c) * 3 + ay) * 3 + dx] += s;
     } else {
       const int k = e - nw;
       const int part = k / O_TILE, o = k % O_TILE;
       float s = 0.f;
       for (int x = 0; x < a.gx; ++x) s += a.partial_b[((size_t)part * a.gx + x) * O_TILE + o];
-      a.db[a.co_base + part * O_TILE + o] += s;
+      if (a.db && a.co_base + part * O_TILE + o < a.cout_real) a.db[a.co_base + part * O_TILE + o] += s;
     }
   }
 }

@@ -454,6 +454,8 @@ fd_status fd_destroy(fd_ctx* c) {
   if (c->d_flag) cudaFree(c->d_flag);
   if (c->d_spec) cudaFree(c->d_spec);
   if (c->side) fd_destroy(c->side);
+  if (c->fallback) fd_destroy(c->fallback);
+  if (c->d_guard) cudaFree(c->d_guard);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);

@@ -21,6 +21,7 @@ struct fd_batch {
     int n_steps;
     cudaStream_t stream;
     cudaEvent_t done;
+    unsigned long long epoch;  // ctx->epoch when the graph was captured
   };
   std::vector<Entry> entries;
   cudaStream_t origin = nullptr;
@@ -66,7 +67,7 @@ fd_status fd_batch_add(fd_batch* b, fd_ctx* ctx, const void* u0, void* u_final, 
   if (n_steps < 1) return batch_error(b, FD_EINVAL, "fd_batch_add: n_steps must be >= 1");
   for (const auto& e : b->entries)
     if (e.ctx == ctx) return batch_error(b, FD_EINVAL, "fd_batch_add: a context may appear once per batch");
-  fd_batch::Entry e{ctx, u0, u_final, n_steps, nullptr, nullptr};
+  fd_batch::Entry e{ctx, u0, u_final, n_steps, nullptr, nullptr, 0};
   if (cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming) != cudaSuccess)
     return batch_error(b, FD_ECUDA, "fd_batch_add: stream or event creation failed");
@@ -78,6 +79,11 @@ fd_status fd_batch_add(fd_batch* b, fd_ctx* ctx, const void* u0, void* u_final, 
 fd_status fd_batch_run(fd_batch* b, void* stream) {
   if (!b) return fd_set_error(nullptr, FD_EINVAL, "fd_batch_run: null batch");
   if (b->entries.empty()) return batch_error(b, FD_EINVAL, "fd_batch_run: empty batch");
+  // a member whose launch plan changed since the capture (fd_set_plan,
+  // fd_autotune) may have replaced the buffers and launch shapes the graph
+  // holds: capture again
+  for (const auto& en : b->entries)
+    if (b->graph && en.ctx->epoch != en.epoch) drop_graph(b);
   if (!b->graph) {
     cudaGraph_t g = nullptr;
     int launches = 0;
@@ -96,6 +102,7 @@ fd_status fd_batch_run(fd_batch* b, void* stream) {
         break;
       }
       launches += fd_last_launch_count(en.ctx);
+      en.epoch = en.ctx->epoch;
       e = cudaEventRecord(en.done, en.stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, en.done, 0);
     }

@@ -22,6 +22,14 @@ struct Launcher {
 };
 
 // Device buffers and launch state of the learnable module.
+// activations of one Fourier-operator evaluation kept for its reverse mode
+struct FnoSavedBufs {
+  float* v = nullptr;    // v_0 .. v_L: [L + 1][batch][width][N][N]
+  float* a = nullptr;    // pre-activations of layers 0 .. L - 2
+  float2* S = nullptr;   // kept input spectra of every layer [L][batch][width][2M][M]
+  float* out = nullptr;  // the operator's output [batch][cout][N][N]
+};
+
 struct LearnedState {
   bool ready = false;          // parameters uploaded
   int kc = 0;
@@ -36,6 +44,9 @@ struct LearnedState {
   size_t pk_stencil_first = 0; // first layer, input channels padded to 16
   size_t pk_tc[4] = {};
   size_t pk_tc_first = 0;
+  size_t pk_tc_t[4] = {};      // data-gradient tiles of the correction network's hidden layers 1..4
+  size_t pk_tc_t5 = 0;         // data-gradient tile of its last layer: 2 (padded to 16) -> 64
+  size_t raw_off_tw0t = 0;     // FP32 [2 k_c][64][3][3] transposed, flipped first layer of the correction
   size_t pk_t[4] = {};         // data-gradient tiles of hidden layers 1..4 (transposed, flipped)
   size_t pk_t5 = 0;            // data-gradient tiles of the last layer: 160 -> 64 in two parts of 32
   size_t raw_off_w0t = 0;      // FP32 [2][64][3][3] transposed, flipped first layer
@@ -57,6 +68,7 @@ struct LearnedState {
   int nring = 0;
   const float** d_ptrs = nullptr;  // device pointer arrays for the first-layer inputs
   unsigned* d_err = nullptr;
+  long long spin = 0;          // iteration limit of the tensor-core kernels' bounded waits
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -78,6 +90,8 @@ struct LearnedState {
   // (rebuilt from the raw parameters on every upload)
   float2* fno_rp = nullptr;
   float2* tcf_rp = nullptr;
+  float2* fno_rph = nullptr;   // conjugate-transposed channel matrices (the reverse mode's mixing)
+  float2* tcf_rph = nullptr;
 };
 
 // Workspace of the reverse mode of one step (allocated by the first
@@ -98,6 +112,18 @@ struct AdjointState {
   __nv_bfloat16* zbar[2] = {};     // hidden-layer cotangents (64 channels, ping-pong)
   float* partial = nullptr;        // weight-gradient partial sums
   float* partial_b = nullptr;
+  // temporal correction (CNN head): packed 2-channel cotangent of its output and
+  // a device array of k_c history-state pointers
+  __nv_bfloat16* tc_cbar = nullptr;
+  const float** d_hist = nullptr;
+  // Fourier operators: O_F's activations per stage, the FNO correction's, the
+  // face-value cotangents (O_F's output cotangent), the correction's output
+  // cotangent in FP32, and the partial sums of their weight gradients
+  FnoSavedBufs fsv[4];
+  FnoSavedBufs tcs;
+  float* fnobar = nullptr;
+  float* tc_cbar_f32 = nullptr;
+  float* fno_partial = nullptr;
   int sms = 0;                     // SM count of the device (plain contexts have no learned state)
   bool ready = false;
 };
@@ -124,6 +150,7 @@ struct TrainState {
   float* lam = nullptr;
   double* partial = nullptr;
   double* corr = nullptr;      // partial sums of fd_vorticity_pcc
+  float* pend = nullptr;       // k_c history cotangents of the temporal correction
   size_t ncorr = 0;
   int nckpt = 0, nseg = 0;
 };
@@ -193,6 +220,14 @@ struct fd_ctx {
   fd_ctx* side = nullptr;
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // bumped whenever a change would make a captured rollout stale (a new launch
+  // plan, which can also replace the streaming sub-context and its buffers);
+  // fd_batch recaptures its graph when a member's epoch moved since capture
+  unsigned long long epoch = 0;
+  // plain-FV fallback of a learned context (fd_rollout_guarded): a plain
+  // context of the same grid and three state buffers, both made by the first call
+  fd_ctx* fallback = nullptr;
+  void* d_guard = nullptr;
 };
 
 // Launch with programmatic stream serialisation: the kernel may start while

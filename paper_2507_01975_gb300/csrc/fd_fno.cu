@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(256) fno_pointwise_kernel(const float* __restr
                                                            const float* __restrict__ v,
                                                            const float* __restrict__ W,
                                                            const float* __restrict__ bias,
-                                                           float* __restrict__ out, int batch, int nn, int gelu) {
+                                                           float* __restrict__ out, int batch, int nn, int gelu,
+                                                           float* __restrict__ pre_out) {
   __shared__ float sw[CO * CI + CO];
   for (int k = threadIdx.x; k < CO * CI; k += blockDim.x) sw[k] = W[k];
   for (int k = threadIdx.x; k < CO; k += blockDim.x) sw[CO * CI + k] = bias[k];
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(256) fno_pointwise_kernel(const float* __restr
     float s = sw[CO * CI + o] + ad[o];
 #pragma unroll
     for (int i = 0; i < CI; ++i) s += sw[o * CI + i] * vi[i];
+    if (pre_out) pre_out[(b * CO + o) * nn + p] = s;
     out[(b * CO + o) * nn + p] = gelu ? gelu_exact(s) : s;
   }
 }
@@ -362,6 +364,180 @@ __global__ void __launch_bounds__(FnoFftCfg<LOGN>::NT) fno_irfft_kernel(const fl
   }
 }
 
+// ---------------------------------------------------------------------------
+// reverse mode (the adjoint of every forward line; oracle.fno.fno_vjp)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float gelu_grad_exact(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// out[b][o][p] = add[b][o][p] + sum_i W[i][o] x[b][i][p] (the transposed channel
+// map, W stored [CI][CO] as the forward's [out][in]), times GELU'(pre[b][o][p])
+// when pre is set. With ost > 0 channel o goes to out + (o / 2) ost + (b * 2 +
+// o % 2) nn + p (the cotangents of the k_c stacked history states), otherwise
+// out + (b CO + o) nn + p. add may alias out.
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) fno_pointwise_t_kernel(const float* add, const float* __restrict__ x,
+                                                             const float* __restrict__ W,
+                                                             const float* __restrict__ pre, float* out, int batch,
+                                                             int nn, size_t ost) {
+  __shared__ float sw[CI * CO];
+  for (int k = threadIdx.x; k < CI * CO; k += blockDim.x) sw[k] = W[k];
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= (size_t)batch * nn) return;
+  const size_t b = e / nn, p = e - b * nn;
+  float xi[CI];
+#pragma unroll
+  for (int i = 0; i < CI; ++i) xi[i] = x[(b * CI + i) * nn + p];
+#pragma unroll
+  for (int o = 0; o < CO; ++o) {
+    const size_t oi = ost ? (size_t)(o >> 1) * ost + (b * 2 + (o & 1)) * nn + p : (b * CO + o) * nn + p;
+    float s = add ? add[oi] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < CI; ++i) s += sw[i * CO + o] * xi[i];
+    if (pre) s *= gelu_grad_exact(pre[(b * CO + o) * nn + p]);
+    out[oi] = s;
+  }
+}
+
+// Pixel sums of outer products: dW[a][c] += sum_{b,p} X[b][a][p] Y[b][c][p] and
+// db[a] += sum X[b][a][p] (the weight and bias gradients of a channel map).
+// Y is a plain [batch][BC][nn] array, or the state / k_c history states (BC =
+// 2 ns; channel 2 s + c = component c of state s) like the lift's input.
+// Per-CTA partials over a fixed pixel split, summed in a fixed order by
+// fno_outer_reduce_kernel: deterministic.
+constexpr int kOuterTile = 256;
+constexpr int kOuterBlocks = 304;
+
+template <int A, int BC>
+__global__ void __launch_bounds__(256) fno_outer_kernel(const float* __restrict__ X, const float* __restrict__ Y,
+                                                       const float* __restrict__ single,
+                                                       const float* const* __restrict__ hist, int batch, int nn,
+                                                       float* __restrict__ partial) {
+  __shared__ float xs[A][kOuterTile + 1];
+  __shared__ float ys[BC][kOuterTile + 1];
+  const int t = threadIdx.x;
+  const int a = t / BC, c = t % BC;
+  const bool pair = t < A * BC;
+  float acc = 0.0f, accb = 0.0f;
+  pdl_wait();
+  pdl_trigger();
+  const size_t total = (size_t)batch * nn;
+  const size_t ntiles = (total + kOuterTile - 1) / kOuterTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t e = tile * kOuterTile + t;
+    const bool ok = e < total;
+    const size_t b = ok ? e / nn : 0, p = ok ? e - b * nn : 0;
+#pragma unroll
+    for (int k = 0; k < A; ++k) xs[k][t] = ok ? X[(b * A + k) * nn + p] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < BC; ++k) {
+      float y = 0.0f;
+      if (ok) {
+        if (Y)
+          y = Y[(b * BC + k) * nn + p];
+        else
+          y = (single ? single : hist[k >> 1])[(b * 2 + (k & 1)) * nn + p];
+      }
+      ys[k][t] = y;
+    }
+    __syncthreads();
+    if (pair) {
+#pragma unroll 8
+      for (int q = 0; q < kOuterTile; ++q) acc = fmaf(xs[a][q], ys[c][q], acc);
+    }
+    if (t < A) {
+#pragma unroll 8
+      for (int q = 0; q < kOuterTile; ++q) accb += xs[t][q];
+    }
+    __syncthreads();
+  }
+  float* pp = partial + (size_t)blockIdx.x * (A * BC + A);
+  if (pair) pp[t] = acc;
+  if (t < A) pp[A * BC + t] = accb;
+}
+
+__global__ void fno_outer_reduce_kernel(const float* __restrict__ partial, int nblk, int nw, int na,
+                                        float* __restrict__ dW, float* __restrict__ db) {
+  pdl_wait();
+  pdl_trigger();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nw + na) return;
+  float s = 0.0f;
+  for (int x = 0; x < nblk; ++x) s += partial[(size_t)x * (nw + na) + k];
+  if (k < nw)
+    dW[k] += s;
+  else
+    db[k - nw] += s;
+}
+
+// Rbar[m][i][o] += (c_kx / N^2) sum_b Abar[b][o][m] conj(S[b][i][m]), c = 1 for
+// kx = 0 and 2 otherwise (irfft2 counts a kept mode with its mirror): the
+// gradient of the complex weights written d/dRe + i d/dIm, stored [m][i][o][re,
+// im] like the parameters. Abar = the kept modes of rfft2 of the layer's output
+// cotangent, S = those of its input. lane = mode; warp w owns the outputs
+// o = w + 8 j; each (m, i, o) has one writer.
+template <int C>
+__global__ void __launch_bounds__(256) fno_rgrad_kernel(const float2* __restrict__ Abar, const float2* __restrict__ S,
+                                                       float* __restrict__ Rbar, int nm, int M, int batch,
+                                                       float inv_nn) {
+  constexpr int NO = C / 8;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = blockIdx.x * 32 + lane;
+  pdl_wait();
+  pdl_trigger();
+  if (m >= nm) return;
+  float2 acc[NO][C];
+#pragma unroll
+  for (int j = 0; j < NO; ++j)
+#pragma unroll
+    for (int i = 0; i < C; ++i) acc[j][i] = make_float2(0.0f, 0.0f);
+  for (int b = 0; b < batch; ++b) {
+    float2 sv[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) sv[i] = S[((size_t)b * C + i) * nm + m];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      const float2 ab = Abar[((size_t)b * C + w + 8 * j) * nm + m];
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        // ab * conj(s)
+        acc[j][i].x = fmaf(ab.x, sv[i].x, fmaf(ab.y, sv[i].y, acc[j][i].x));
+        acc[j][i].y = fmaf(ab.y, sv[i].x, fmaf(-ab.x, sv[i].y, acc[j][i].y));
+      }
+    }
+  }
+  const float f = ((m % M) == 0 ? 1.0f : 2.0f) * inv_nn;
+#pragma unroll
+  for (int j = 0; j < NO; ++j)
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      float* r = Rbar + (((size_t)m * C + i) * C + w + 8 * j) * 2;
+      r[0] += f * acc[j][i].x;
+      r[1] += f * acc[j][i].y;
+    }
+}
+
+// R[m][i][o][re, im] -> Rh[m / 32][o][i][m % 32] = conj(R[m][i][o]): the channel
+// matrices of the spectral convolution's adjoint in v (conjugate transposes), in
+// the mixing kernel's layout
+__global__ void fno_pack_rh_kernel(const float* __restrict__ R, float2* __restrict__ Rh, int nm, int C) {
+  const int nb = (nm + kMixModes - 1) / kMixModes;
+  const size_t total = (size_t)nb * C * C * kMixModes;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int mm = (int)(q % kMixModes);
+    const size_t r = q / kMixModes;
+    const int oi = (int)(r % ((size_t)C * C));
+    const int o = oi / C, i = oi % C;
+    const int m = (int)(r / ((size_t)C * C)) * kMixModes + mm;
+    Rh[q] = m < nm ? make_float2(R[(((size_t)m * C + i) * C + o) * 2], -R[(((size_t)m * C + i) * C + o) * 2 + 1])
+                   : make_float2(0.0f, 0.0f);
+  }
+}
+
 // one Fourier neural operator: width C, `layers` layers of `modes` kept modes,
 // parameters at raw_off (P_w[C][cin], P_b[C], layers, Q_w[cout][C], Q_b[cout]),
 // output [batch][cout][N][N]
@@ -369,7 +545,8 @@ struct FnoNet {
   int layers, modes, cout;
   size_t raw_off;
   float* out;
-  const float2* rp;  // mode-blocked channel matrices of every layer
+  const float2* rp;   // mode-blocked channel matrices of every layer
+  const float2* rph;  // their conjugate transposes (reverse mode), or null
 };
 
 template <int LOGN, int C, int CO>
@@ -404,12 +581,13 @@ cudaError_t fno_run(LearnedState& L, const FnoNet& net, const float* single, con
                      tw, M, 1.0f / (float)nn);
     if (e == cudaSuccess)
       e = launch_pdl(fno_pointwise_kernel<C, C>, pix, dim3(256), 0, st, (const float*)L.fno_y,
-                     (const float*)L.fno_v[cur], W, Wb, L.fno_v[cur ^ 1], batch, nn, l < nl - 1 ? 1 : 0);
+                     (const float*)L.fno_v[cur], W, Wb, L.fno_v[cur ^ 1], batch, nn, l < nl - 1 ? 1 : 0,
+                     (float*)nullptr);
     cur ^= 1;
   }
   if (e == cudaSuccess)
     e = launch_pdl(fno_pointwise_kernel<C, CO>, pix, dim3(256), 0, st, (const float*)nullptr,
-                   (const float*)L.fno_v[cur], Q, Q + (size_t)CO * C, net.out, batch, nn, 0);
+                   (const float*)L.fno_v[cur], Q, Q + (size_t)CO * C, net.out, batch, nn, 0, (float*)nullptr);
   return e;
 }
 
@@ -426,14 +604,231 @@ cudaError_t fno_dispatch(fd_ctx* c, const FnoNet& net, int width, const float* s
                      : fno_run<5, 8, CO>(L, net, single, hist, ns, tw, B, st);
 }
 
+// forward of one operator keeping what its reverse mode needs: v_0 .. v_L
+// (sb.v, L + 1 fields [batch][C][N][N]), the pre-activations of layers 0 ..
+// L - 2 (sb.a), the kept input spectra of every layer (sb.S, [batch][C][2M][M]),
+// and the output (sb.out)
+template <int LOGN, int C, int CO>
+cudaError_t fno_run_saved(LearnedState& L, const FnoNet& net, const float* single, const float* const* hist, int ns,
+                          const FnoSavedBufs& sb, const float2* tw, int batch, cudaStream_t st) {
+  using Cfg = FnoFftCfg<LOGN>;
+  constexpr int N = Cfg::N;
+  const int M = net.modes, nl = net.layers, cin = 2 * ns;
+  const int nn = N * N, nm = 2 * M * M;
+  const size_t fsm = Cfg::smem(M);
+  const size_t fld = (size_t)batch * C * nn, spec = (size_t)batch * C * nm;
+  const float* P = L.d_raw + net.raw_off;
+  const size_t layer_size = (size_t)nm * C * C * 2 + (size_t)C * C + C;
+  const float* R0 = P + (size_t)C * cin + C;
+  const float* Q = R0 + (size_t)nl * layer_size;
+  const dim3 pix((unsigned)(((size_t)batch * nn + 255) / 256));
+  const int nb = (nm + kMixModes - 1) / kMixModes;
+  const dim3 mix(nb, (batch + kMixBatch - 1) / kMixBatch);
+  cudaError_t e = launch_pdl(fno_lift_kernel<C>, pix, dim3(256), 0, st, single, hist, ns, P, sb.v, batch, nn);
+  for (int l = 0; l < nl && e == cudaSuccess; ++l) {
+    const float* R = R0 + (size_t)l * layer_size;
+    const float* W = R + (size_t)nm * C * C * 2;
+    const float* Wb = W + (size_t)C * C;
+    e = launch_pdl(fno_rfft_kernel<LOGN>, dim3(C, batch), dim3(Cfg::NT), fsm, st, (const float*)(sb.v + l * fld),
+                   sb.S + l * spec, tw, M);
+    if (e == cudaSuccess)
+      e = launch_pdl(fno_mix_kernel<C>, mix, dim3(256), MixCfg<C>::SMEM, st, (const float2*)(sb.S + l * spec),
+                     (const float2*)(net.rp + (size_t)l * nb * C * C * kMixModes), L.fno_s2, nm, batch);
+    if (e == cudaSuccess)
+      e = launch_pdl(fno_irfft_kernel<LOGN>, dim3(C, batch), dim3(Cfg::NT), fsm, st, (const float2*)L.fno_s2, L.fno_y,
+                     tw, M, 1.0f / (float)nn);
+    if (e == cudaSuccess)
+      e = launch_pdl(fno_pointwise_kernel<C, C>, pix, dim3(256), 0, st, (const float*)L.fno_y,
+                     (const float*)(sb.v + l * fld), W, Wb, sb.v + (l + 1) * fld, batch, nn, l < nl - 1 ? 1 : 0,
+                     l < nl - 1 ? sb.a + l * fld : (float*)nullptr);
+  }
+  if (e == cudaSuccess)
+    e = launch_pdl(fno_pointwise_kernel<C, CO>, pix, dim3(256), 0, st, (const float*)nullptr,
+                   (const float*)(sb.v + nl * fld), Q, Q + (size_t)CO * C, sb.out, batch, nn, 0, (float*)nullptr);
+  return e;
+}
+
+// dW[A][BC] += sum X (x) Y, db[A] += sum X over every pixel of the batch
+template <int A, int BC>
+cudaError_t outer_grad(const float* X, const float* Y, const float* single, const float* const* hist, int batch,
+                       int nn, float* partial, float* dW, float* db, cudaStream_t st) {
+  cudaError_t e = launch_pdl(fno_outer_kernel<A, BC>, dim3(kOuterBlocks), dim3(256), 0, st, X, Y, single, hist, batch,
+                             nn, partial);
+  if (e == cudaSuccess)
+    e = launch_pdl(fno_outer_reduce_kernel, dim3((A * BC + A + 255) / 256), dim3(256), 0, st, (const float*)partial,
+                   kOuterBlocks, A * BC, A, dW, db);
+  return e;
+}
+
+// The operator's reverse mode for the output cotangent gbar [batch][CO][N][N]:
+// parameter gradients added to dparams (same layout as the parameters), input
+// cotangent added to ubar (accumulate) or written (overwrite); ubar in the
+// state layout, or the history layout (ost > 0: input channel 2 s + c ->
+// ubar + s ost, component c).
+template <int LOGN, int C, int CO, int CIN>
+cudaError_t fno_back(LearnedState& L, const FnoNet& net, const FnoSavedBufs& sb, const float* single,
+                     const float* const* hist, const float* gbar, float* ubar, size_t ost, bool accumulate,
+                     float* dparams, float* partial, const float2* tw, int batch, cudaStream_t st) {
+  using Cfg = FnoFftCfg<LOGN>;
+  constexpr int N = Cfg::N;
+  const int M = net.modes, nl = net.layers;
+  const int nn = N * N, nm = 2 * M * M;
+  const size_t fsm = Cfg::smem(M);
+  const size_t fld = (size_t)batch * C * nn, spec = (size_t)batch * C * nm;
+  const size_t layer_size = (size_t)nm * C * C * 2 + (size_t)C * C + C;
+  const float* P = L.d_raw + net.raw_off;
+  const float* R0 = P + (size_t)C * CIN + C;
+  const float* Q = R0 + (size_t)nl * layer_size;
+  float* dP = dparams + net.raw_off;
+  float* dR0 = dP + (size_t)C * CIN + C;
+  float* dQ = dR0 + (size_t)nl * layer_size;
+  const dim3 pix((unsigned)(((size_t)batch * nn + 255) / 256));
+  const int nb = (nm + kMixModes - 1) / kMixModes;
+  const dim3 mix(nb, (batch + kMixBatch - 1) / kMixBatch);
+  float* abar[2] = {L.fno_v[0], L.fno_v[1]};
+  // Q: gradients, then v_bar_L = Q^T gbar (= a_bar of the last layer: no GELU after it)
+  cudaError_t e = dparams ? outer_grad<CO, C>(gbar, sb.v + nl * fld, nullptr, nullptr, batch, nn, partial, dQ,
+                                              dQ + (size_t)CO * C, st)
+                          : cudaSuccess;
+  if (e == cudaSuccess)
+    e = launch_pdl(fno_pointwise_t_kernel<CO, C>, pix, dim3(256), 0, st, (const float*)nullptr, gbar, Q,
+                   (const float*)nullptr, abar[0], batch, nn, (size_t)0);
+  int cur = 0;
+  for (int l = nl - 1; l >= 0 && e == cudaSuccess; --l) {
+    const float* W = R0 + (size_t)l * layer_size + (size_t)nm * C * C * 2;
+    float* dR = dR0 + (size_t)l * layer_size;
+    float* dW = dR + (size_t)nm * C * C * 2;
+    const float* vl = sb.v + l * fld;
+    if (dparams) e = outer_grad<C, C>(abar[cur], vl, nullptr, nullptr, batch, nn, partial, dW, dW + (size_t)C * C, st);
+    // spectral part: Abar = rfft2(a_bar) on the kept modes
+    if (e == cudaSuccess)
+      e = launch_pdl(fno_rfft_kernel<LOGN>, dim3(C, batch), dim3(Cfg::NT), fsm, st, (const float*)abar[cur], L.fno_s,
+                     tw, M);
+    if (e == cudaSuccess && dparams)
+      e = launch_pdl(fno_rgrad_kernel<C>, dim3(nb), dim3(256), 0, st, (const float2*)L.fno_s,
+                     (const float2*)(sb.S + l * spec), dR, nm, M, batch, 1.0f / (float)nn);
+    // v_bar through the spectral convolution: the same convolution with R^H
+    if (e == cudaSuccess)
+      e = launch_pdl(fno_mix_kernel<C>, mix, dim3(256), MixCfg<C>::SMEM, st, (const float2*)L.fno_s,
+                     (const float2*)(net.rph + (size_t)l * nb * C * C * kMixModes), L.fno_s2, nm, batch);
+    if (e == cudaSuccess)
+      e = launch_pdl(fno_irfft_kernel<LOGN>, dim3(C, batch), dim3(Cfg::NT), fsm, st, (const float2*)L.fno_s2, L.fno_y,
+                     tw, M, 1.0f / (float)nn);
+    // v_bar_l = W^T a_bar + spectral part; a_bar of layer l - 1 = v_bar_l GELU'(a_{l-1})
+    if (e == cudaSuccess)
+      e = launch_pdl(fno_pointwise_t_kernel<C, C>, pix, dim3(256), 0, st, (const float*)L.fno_y,
+                     (const float*)abar[cur], W, l > 0 ? (const float*)(sb.a + (l - 1) * fld) : (const float*)nullptr,
+                     abar[cur ^ 1], batch, nn, (size_t)0);
+    cur ^= 1;
+  }
+  // lift: gradients of P, input cotangent P^T v_bar_0
+  if (e == cudaSuccess && dparams)
+    e = outer_grad<C, CIN>(abar[cur], nullptr, single, hist, batch, nn, partial, dP, dP + (size_t)C * CIN, st);
+  if (e == cudaSuccess)
+    e = launch_pdl(fno_pointwise_t_kernel<C, CIN>, pix, dim3(256), 0, st, accumulate ? (const float*)ubar : nullptr,
+                   (const float*)abar[cur], P, (const float*)nullptr, ubar, batch, nn, ost);
+  return e;
+}
+
 }  // namespace
 
 int fd_fno_launches(int layers) { return layers > 0 ? 2 + 4 * layers : 0; }
 
+// O_F (which = 0) or the FNO temporal correction (which = 1) of the context
+static FnoNet fno_net(const LearnedState& L, int which) {
+  return which == 0 ? FnoNet{L.fno_layers, L.fno_modes, 8, L.raw_off_fno, L.fno_out, L.fno_rp, L.fno_rph}
+                    : FnoNet{L.tcf_layers, L.tcf_modes, 2, L.raw_off_tcf, L.corr, L.tcf_rp, L.tcf_rph};
+}
+
+// floats of the saved activations of one evaluation (v, a) and float2 of its spectra
+void fd_fno_saved_sizes(const LearnedState& L, int which, int batch, int nn, size_t* v_floats, size_t* a_floats,
+                        size_t* s_float2, size_t* out_floats) {
+  const int layers = which == 0 ? L.fno_layers : L.tcf_layers;
+  const int modes = which == 0 ? L.fno_modes : L.tcf_modes;
+  const int width = which == 0 ? L.fno_width : L.tcf_width;
+  const size_t fld = (size_t)batch * width * nn;
+  *v_floats = (size_t)(layers + 1) * fld;
+  *a_floats = (size_t)(layers > 1 ? layers - 1 : 1) * fld;
+  *s_float2 = (size_t)layers * batch * width * 2 * modes * modes;
+  *out_floats = (size_t)batch * (which == 0 ? 8 : 2) * nn;
+}
+
+// forward of O_F (single = the stage state) or of the FNO correction (hist = the
+// k_c history states), keeping the activations in sb
+cudaError_t fd_fno_forward_saved(fd_ctx* c, int which, const float* single, const float* const* hist,
+                                 const FnoSavedBufs& sb, cudaStream_t st) {
+  LearnedState& L = *c->lrn;
+  FnoNet net = fno_net(L, which);
+  const float2* tw = reinterpret_cast<const float2*>(c->base.tw);
+  const int B = c->grid.batch, ns = which == 0 ? 1 : L.kc;
+  const int width = which == 0 ? L.fno_width : L.tcf_width;
+  if (which == 0) {
+    if (c->logn == 6)
+      return width == 16 ? fno_run_saved<6, 16, 8>(L, net, single, hist, ns, sb, tw, B, st)
+                         : fno_run_saved<6, 8, 8>(L, net, single, hist, ns, sb, tw, B, st);
+    return width == 16 ? fno_run_saved<5, 16, 8>(L, net, single, hist, ns, sb, tw, B, st)
+                       : fno_run_saved<5, 8, 8>(L, net, single, hist, ns, sb, tw, B, st);
+  }
+  if (c->logn == 6)
+    return width == 16 ? fno_run_saved<6, 16, 2>(L, net, single, hist, ns, sb, tw, B, st)
+                       : fno_run_saved<6, 8, 2>(L, net, single, hist, ns, sb, tw, B, st);
+  return width == 16 ? fno_run_saved<5, 16, 2>(L, net, single, hist, ns, sb, tw, B, st)
+                     : fno_run_saved<5, 8, 2>(L, net, single, hist, ns, sb, tw, B, st);
+}
+
+template <int LOGN, int C>
+static cudaError_t fno_back_tc(LearnedState& L, const FnoNet& net, const FnoSavedBufs& sb, const float* const* hist,
+                               const float* gbar, float* ubar, size_t ost, float* dparams, float* partial,
+                               const float2* tw, int B, cudaStream_t st) {
+  switch (L.kc) {
+    case 1: return fno_back<LOGN, C, 2, 2>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+    case 2: return fno_back<LOGN, C, 2, 4>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+    case 3: return fno_back<LOGN, C, 2, 6>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+    case 4: return fno_back<LOGN, C, 2, 8>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+    case 5: return fno_back<LOGN, C, 2, 10>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+    case 6: return fno_back<LOGN, C, 2, 12>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+    case 7: return fno_back<LOGN, C, 2, 14>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+    default: return fno_back<LOGN, C, 2, 16>(L, net, sb, nullptr, hist, gbar, ubar, ost, false, dparams, partial, tw, B, st);
+  }
+}
+
+// reverse mode of O_F (which = 0: gbar [batch][8][N][N], the input cotangent
+// added to / written into ubar [batch][2][N][N]) or of the FNO correction
+// (which = 1: gbar [batch][2][N][N], history cotangents written to ubar with
+// state stride ost); dparams (may be null) accumulates the parameter gradients
+cudaError_t fd_fno_backward(fd_ctx* c, int which, const FnoSavedBufs& sb, const float* single,
+                            const float* const* hist, const float* gbar, float* ubar, size_t ost, bool accumulate,
+                            float* dparams, float* partial, cudaStream_t st) {
+  LearnedState& L = *c->lrn;
+  FnoNet net = fno_net(L, which);
+  const float2* tw = reinterpret_cast<const float2*>(c->base.tw);
+  const int B = c->grid.batch;
+  const int width = which == 0 ? L.fno_width : L.tcf_width;
+  if (which == 0) {
+    if (c->logn == 6)
+      return width == 16 ? fno_back<6, 16, 8, 2>(L, net, sb, single, nullptr, gbar, ubar, 0, accumulate, dparams,
+                                                 partial, tw, B, st)
+                         : fno_back<6, 8, 8, 2>(L, net, sb, single, nullptr, gbar, ubar, 0, accumulate, dparams,
+                                                partial, tw, B, st);
+    return width == 16 ? fno_back<5, 16, 8, 2>(L, net, sb, single, nullptr, gbar, ubar, 0, accumulate, dparams, partial,
+                                               tw, B, st)
+                       : fno_back<5, 8, 8, 2>(L, net, sb, single, nullptr, gbar, ubar, 0, accumulate, dparams, partial,
+                                              tw, B, st);
+  }
+  if (c->logn == 6)
+    return width == 16 ? fno_back_tc<6, 16>(L, net, sb, hist, gbar, ubar, ost, dparams, partial, tw, B, st)
+                       : fno_back_tc<6, 8>(L, net, sb, hist, gbar, ubar, ost, dparams, partial, tw, B, st);
+  return width == 16 ? fno_back_tc<5, 16>(L, net, sb, hist, gbar, ubar, ost, dparams, partial, tw, B, st)
+                     : fno_back_tc<5, 8>(L, net, sb, hist, gbar, ubar, ost, dparams, partial, tw, B, st);
+}
+
+// partial-sum floats the reverse mode of either operator needs
+size_t fd_fno_partial_floats() { return (size_t)kOuterBlocks * (16 * 16 + 16); }
+
 // O_F of the stage state u [batch][2][N][N] into c->lrn->fno_out [batch][8][N][N]
 cudaError_t fd_fno_forward(fd_ctx* c, const float* u, cudaStream_t st) {
   LearnedState& L = *c->lrn;
-  const FnoNet net{L.fno_layers, L.fno_modes, 8, L.raw_off_fno, L.fno_out, L.fno_rp};
+  const FnoNet net{L.fno_layers, L.fno_modes, 8, L.raw_off_fno, L.fno_out, L.fno_rp, L.fno_rph};
   return fno_dispatch<8>(c, net, L.fno_width, u, nullptr, 1, st);
 }
 
@@ -441,7 +836,7 @@ cudaError_t fd_fno_forward(fd_ctx* c, const float* u, cudaStream_t st) {
 // array, oldest first) into c->lrn->corr [batch][2][N][N]
 cudaError_t fd_fno_tc(fd_ctx* c, const float* const* hist, cudaStream_t st) {
   LearnedState& L = *c->lrn;
-  const FnoNet net{L.tcf_layers, L.tcf_modes, 2, L.raw_off_tcf, L.corr, L.tcf_rp};
+  const FnoNet net{L.tcf_layers, L.tcf_modes, 2, L.raw_off_tcf, L.corr, L.tcf_rp, L.tcf_rph};
   return fno_dispatch<2>(c, net, L.tcf_width, nullptr, hist, L.kc, st);
 }
 
@@ -458,9 +853,10 @@ cudaError_t fd_fno_pack(LearnedState& L, cudaStream_t st) {
     int layers, modes, width, cin;
     size_t raw_off;
     float2* rp;
+    float2* rph;
   };
-  const Op ops[2] = {{L.fno_layers, L.fno_modes, L.fno_width, 2, L.raw_off_fno, L.fno_rp},
-                     {L.tcf_layers, L.tcf_modes, L.tcf_width, 2 * L.kc, L.raw_off_tcf, L.tcf_rp}};
+  const Op ops[2] = {{L.fno_layers, L.fno_modes, L.fno_width, 2, L.raw_off_fno, L.fno_rp, L.fno_rph},
+                     {L.tcf_layers, L.tcf_modes, L.tcf_width, 2 * L.kc, L.raw_off_tcf, L.tcf_rp, L.tcf_rph}};
   for (const Op& op : ops) {
     if (op.layers <= 0) continue;
     const int C = op.width, nm = 2 * op.modes * op.modes;
@@ -469,6 +865,7 @@ cudaError_t fd_fno_pack(LearnedState& L, cudaStream_t st) {
     for (int l = 0; l < op.layers; ++l) {
       const float* R = L.d_raw + op.raw_off + (size_t)C * op.cin + C + l * layer_size;
       fno_pack_r_kernel<<<2 * L.sms, 256, 0, st>>>(R, op.rp + l * per, nm, C);
+      fno_pack_rh_kernel<<<2 * L.sms, 256, 0, st>>>(R, op.rph + l * per, nm, C);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

@@ -203,7 +203,8 @@ struct PackDesc {
 __device__ __forceinline__ float round_bf16_dev(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __global__ void prep_raw_kernel(const float* params, float* raw, size_t nparams, const uint32_t* ranges, int nranges,
-                                size_t off_w0, size_t off_w0t, size_t off_zero) {
+                                size_t off_w0, size_t off_w0t, size_t off_zero, size_t off_tw0, size_t off_tw0t,
+                                int tc_cin) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nparams; k += (size_t)gridDim.x * blockDim.x) {
     float v = params[k];
     for (int r = 0; r < nranges; ++r)
@@ -214,6 +215,12 @@ __global__ void prep_raw_kernel(const float* params, float* raw, size_t nparams,
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * 64 * 9; k += (size_t)gridDim.x * blockDim.x) {
     const int ci = (int)(k / 576), o = (int)((k / 9) % 64), t = (int)(k % 9);
     raw[off_w0t + k] = round_bf16_dev(params[off_w0 + (o * 2 + ci) * 9 + 8 - t]);
+  }
+  // the same for the temporal-correction network's first layer (tc_cin = 2 k_c inputs)
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < (size_t)tc_cin * 64 * 9;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(k / 576), o = (int)((k / 9) % 64), t = (int)(k % 9);
+    raw[off_tw0t + k] = round_bf16_dev(params[off_tw0 + (o * tc_cin + ci) * 9 + 8 - t]);
   }
   if (blockIdx.x == 0 && threadIdx.x < 8) raw[off_zero + threadIdx.x] = 0.f;
 }
@@ -269,6 +276,8 @@ void plan_layout(LearnedState& L, std::vector<PackDesc>& descs, std::vector<uint
   off += (size_t)fd_fno_param_count(L.fno_layers, L.fno_modes, L.fno_width, 2, 8);
   L.raw_off_w0t = off;
   off += 2 * 64 * 9;
+  L.raw_off_tw0t = off;
+  if (L.kc > 0 && L.tcf_layers == 0) off += (size_t)2 * L.kc * 64 * 9;
   L.raw_off_zero = off;
   off += 8;
   L.raw_total = off;
@@ -299,13 +308,19 @@ void plan_layout(LearnedState& L, std::vector<PackDesc>& descs, std::vector<uint
   if (L.kc > 0 && L.tcf_layers == 0) {
     L.pk_tc_first = add(L.raw_off_tw[0], 2 * L.kc, 16, 64, 0, 2 * L.kc, 0);
     for (int l = 1; l <= 4; ++l) L.pk_tc[l - 1] = add(L.raw_off_tw[l], 64, 64, 64, 0, 64, 0);
+    // reverse mode: transposed, flipped tiles of the hidden layers and of the
+    // last layer (2 cotangent channels, padded to 16, -> 64)
+    for (int l = 1; l <= 4; ++l) L.pk_tc_t[l - 1] = add(L.raw_off_tw[l], 64, 64, 64, 0, 64, 1);
+    L.pk_tc_t5 = add(L.raw_off_tw[5], 2, 16, 64, 0, 64, 1);
   }
   L.pk_total = pk;
 }
 
 cudaError_t upload_params(LearnedState& L, const float* params, cudaStream_t st) {
+  const int tc_cin = (L.kc > 0 && L.tcf_layers == 0) ? 2 * L.kc : 0;
   prep_raw_kernel<<<2 * L.sms, 256, 0, st>>>(params, L.d_raw, (size_t)L.nparams, L.d_ranges, L.nranges,
-                                             L.raw_off_sw[0], L.raw_off_w0t, L.raw_off_zero);
+                                             L.raw_off_sw[0], L.raw_off_w0t, L.raw_off_zero, L.raw_off_tw[0],
+                                             L.raw_off_tw0t, tc_cin);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   pack_tiles_kernel<<<dim3(32, L.ndesc), 256, 0, st>>>(L.d_raw, L.d_wpack, reinterpret_cast<const PackDesc*>(L.d_desc));
@@ -354,6 +369,7 @@ fd_status fd_learned_init(fd_ctx* c) {
   L->tcf_modes = c->opts.tc_fno_modes;
   L->tcf_width = c->opts.tc_fno_width;
   L->ablation = c->opts.ablation;
+  L->spin = c->opts.spin_limit > 0 ? (long long)c->opts.spin_limit : kSpin;
   L->nparams = fd_learned_param_count(c->opts);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -388,9 +404,12 @@ fd_status fd_learned_init(fd_ctx* c) {
   if (L->fno_layers > 0) {
     alloc((void**)&L->fno_out, B * 8 * NN * sizeof(float));
     alloc((void**)&L->fno_rp, fd_fno_rp_count(L->fno_layers, L->fno_modes, L->fno_width) * sizeof(float2));
+    alloc((void**)&L->fno_rph, fd_fno_rp_count(L->fno_layers, L->fno_modes, L->fno_width) * sizeof(float2));
   }
-  if (L->tcf_layers > 0)
+  if (L->tcf_layers > 0) {
     alloc((void**)&L->tcf_rp, fd_fno_rp_count(L->tcf_layers, L->tcf_modes, L->tcf_width) * sizeof(float2));
+    alloc((void**)&L->tcf_rph, fd_fno_rp_count(L->tcf_layers, L->tcf_modes, L->tcf_width) * sizeof(float2));
+  }
   std::vector<PackDesc> descs;
   std::vector<uint32_t> ranges;
   plan_layout(*L, descs, ranges);
@@ -431,7 +450,7 @@ void fd_learned_free(fd_ctx* c) {
                 L->coef,   L->acc,     L->wbuf,    L->ws,             L->corr,            L->ring,
                 (void*)L->d_ptrs,
                 L->d_err,  L->fno_v[0], L->fno_v[1], L->fno_y,        L->fno_s,           L->fno_s2,
-                L->fno_out, L->fno_rp, L->tcf_rp};
+                L->fno_out, L->fno_rp, L->tcf_rp, L->fno_rph, L->tcf_rph};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete L;
@@ -567,6 +586,10 @@ fd_status fd_learned_error_flag(fd_ctx* c) {
   unsigned h = 0;
   if (cudaMemcpy(&h, c->lrn->d_err, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fd_set_error(c, FD_ECUDA, "error flag read failed");
-  if (h) return fd_set_error(c, FD_ETIMEOUT, "a bounded device wait of the tensor-core convolution gave up (0x%x)", h);
+  if (h) {
+    // reported once: the next check sees only waits that give up after this one
+    cudaMemset(c->lrn->d_err, 0, sizeof h);
+    return fd_set_error(c, FD_ETIMEOUT, "a bounded device wait of the tensor-core convolution gave up (0x%x)", h);
+  }
   return FD_OK;
 }

@@ -20,6 +20,7 @@ namespace ldfv {
 
 constexpr int kHidden = 64;
 constexpr int kCoef = 160;
+// default iteration limit of a bounded mbarrier wait (fd_options.spin_limit <= 0)
 constexpr long long kSpin = 1ll << 20;
 
 inline int stencil_cin(int l) { return l == 0 ? 2 : kHidden; }
@@ -28,12 +29,13 @@ inline int tc_cin(int l, int kc) { return l == 0 ? 2 * kc : kHidden; }
 inline int tc_cout(int l) { return l == 5 ? 2 : kHidden; }
 
 // One tensor-core convolution over `parts` output-channel parts of COUT_TILE.
-// gelu: 0 none, 1 GELU (pre-activation to aux_out when set), 2 multiply by GELU'(aux_in).
+// gelu: 0 none, 1 GELU (pre-activation to aux_out when set), 2 multiply by GELU'(aux_in)
+// (with dbias set, the output's per-channel FP32 sums are added there: a bias gradient).
 template <int LOGN, int COUT_TILE, int CIN = 64, int NBUF = 4>
 static cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, const __nv_bfloat16* wpack,
                         const float* bias, __nv_bfloat16* out, int batch, int parts, int co_base, int cout_total,
                         int gelu, cudaStream_t st, const __nv_bfloat16* aux_in = nullptr,
-                        __nv_bfloat16* aux_out = nullptr) {
+                        __nv_bfloat16* aux_out = nullptr, float* dbias = nullptr) {
   using Cfg = ConvCfg<LOGN, CIN, COUT_TILE, NBUF>;
   ConvArgs a;
   std::memset(&a, 0, sizeof a);
@@ -48,8 +50,9 @@ static cudaError_t launch_conv(const LearnedState& L, const __nv_bfloat16* in, c
   a.gelu = gelu;
   a.aux_in = aux_in;
   a.aux_out = aux_out;
+  a.dbias = dbias;
   a.err = L.d_err;
-  a.spin_limit = kSpin;
+  a.spin_limit = L.spin;
   const int ntiles = batch * (Cfg::N / Cfg::TROWS) * parts;
   const int grid = ntiles < L.sms ? ntiles : L.sms;
   return launch_pdl(conv3x3_tc_kernel<LOGN, CIN, COUT_TILE, NBUF>, dim3(grid), dim3(Cfg::NT), Cfg::SMEM, st, a);

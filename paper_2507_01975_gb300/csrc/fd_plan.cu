@@ -62,6 +62,7 @@ fd_status apply_plan(fd_ctx* c, int variant, int n_onchip, int n_stream) {
   c->n_onchip = n_onchip;
   c->n_stream = n_stream;
   c->plan_us = 0;
+  ++c->epoch;
   return FD_OK;
 }
 

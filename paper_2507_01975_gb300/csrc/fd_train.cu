@@ -12,6 +12,9 @@
 
 using namespace ldfv;
 
+fd_status fd_tc_adjoint_ptrs(fd_ctx* c, const float* const* hist_host, const float* lam, float* hist_bar,
+                             size_t state_stride, float* dparams, cudaStream_t st, int* launches);
+
 namespace {
 
 constexpr int kRedBlocks = 512;  // fixed grid of the deterministic reductions
@@ -165,7 +168,8 @@ cudaError_t mse(fd_ctx* c, const float* pred, const float* target, size_t n, flo
   return e;
 }
 
-// workspace of the rollout reverse mode: nseg + 1 checkpoints, one segment, one cotangent
+// workspace of the rollout reverse mode: nseg + 1 checkpoints, one segment, one
+// cotangent (and, with a temporal correction, the k_c history cotangents)
 fd_status train_reserve(fd_ctx* c, int nseg, int seglen) {
   TrainState*& T = c->trn;
   if (!T) {
@@ -174,6 +178,12 @@ fd_status train_reserve(fd_ctx* c, int nseg, int seglen) {
     if (cudaMalloc(&T->partial, kRedBlocks * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&T->lam, fd_state_bytes(c->grid)) != cudaSuccess)
       return fd_set_error(c, FD_ENOMEM, "training workspace: out of device memory");
+  }
+  if (c->lrn && c->lrn->kc > 0 && !T->pend) {
+    if (cudaMalloc(&T->pend, fd_state_bytes(c->grid) * c->lrn->kc) != cudaSuccess) {
+      T->pend = nullptr;
+      return fd_set_error(c, FD_ENOMEM, "training workspace: history cotangents do not fit");
+    }
   }
   const size_t bytes = fd_state_bytes(c->grid);
   if (nseg + 1 > T->nckpt) {
@@ -199,8 +209,20 @@ fd_status train_reserve(fd_ctx* c, int nseg, int seglen) {
 // Either lam_traj (cotangents of u_1 .. u_n) is given, or targets: then the
 // cotangents are those of L = mean((u_k - t_k)^2) over every step and element,
 // and L is written to *loss.
+//
+// With a temporal correction every k_c-th state u_m (m = M k_c) was formed
+// from the k_c states u_{m-k_c} .. u_{m-1} as well (Sec. 3.2); its cotangent
+// also reaches them (fd_tc_adjoint) through T.pend, slot s holding the
+// cotangent of u_{m-k_c+s}, which is added once the sweep arrives there. The
+// checkpoint interval is a multiple of k_c, so a window never crosses a
+// segment. The FV step before a correction is differentiated by
+// fd_step_adjoint with the corrected state's cotangent: its output is already
+// projected and P is idempotent, so P(lam) and lam give the same result.
 fd_status rollout_reverse(fd_ctx* c, const float* u0, int n, int k, const float* lam_traj, const float* targets,
                           float* lam0, float* dparams, double* loss, cudaStream_t st, const char* who) {
+  const int kc = c->lrn ? c->lrn->kc : 0;
+  if (kc > 0 && k % kc != 0)
+    return fd_set_error(c, FD_EINVAL, "%s: ckpt_every must be a multiple of k_c (%d)", who, kc);
   const int nseg = (n + k - 1) / k;
   fd_status s = train_reserve(c, nseg, k);
   if (s != FD_OK) return s;
@@ -229,10 +251,22 @@ fd_status rollout_reverse(fd_ctx* c, const float* u0, int n, int k, const float*
       if (s != FD_OK) return s;
       launches += c->launches;
     }
+    auto state = [&](int m) -> const float* {  // u_m, m in [g k, g k + len]
+      const int jj = m - g * k;
+      return jj == 0 ? T.ckpt + g * slot : (jj == len ? T.ckpt + (g + 1) * slot : T.seg + (size_t)(jj - 1) * slot);
+    };
     for (int j = len - 1; j >= 0 && e == cudaSuccess; --j) {
       const int step = g * k + j;  // u_step -> u_{step + 1}
       const float* out = j == len - 1 ? T.ckpt + (g + 1) * slot : T.seg + (size_t)j * slot;
       const float* in = j == 0 ? T.ckpt + g * slot : T.seg + (size_t)(j - 1) * slot;
+      if (kc > 0 && step + 1 < n && (step + 1) / kc * kc + kc <= n) {
+        // u_{step+1} lies in the history window of the correction at the end of
+        // its k_c block: add what that correction sent back to it
+        axpy_kernel<<<grid_for(slot), 256, 0, st>>>(T.lam, T.pend + (size_t)((step + 1) % kc) * slot, slot);
+        e = cudaGetLastError();
+        ++launches;
+        if (e != cudaSuccess) break;
+      }
       if (targets) {
         e = mse(c, out, targets + (size_t)step * slot, slot, gscale, T.lam, 2, 1.0 / total, loss, first_loss ? 0 : 1,
                 st);
@@ -244,9 +278,25 @@ fd_status rollout_reverse(fd_ctx* c, const float* u0, int n, int k, const float*
         ++launches;
       }
       if (e != cudaSuccess) break;
+      if (kc > 0 && (step + 1) % kc == 0) {
+        // u_{step+1} is a corrected state: its history u_{step+1-k_c} .. u_step
+        const float* hist[8];
+        for (int q = 0; q < kc; ++q) hist[q] = state(step + 1 - kc + q);
+        s = fd_tc_adjoint_ptrs(c, hist, T.lam, T.pend, slot, dparams, st, &launches);
+        if (s != FD_OK) return s;
+      }
       s = fd_step_adjoint(c, in, T.lam, T.lam, dparams, st);
       if (s != FD_OK) return s;
       launches += c->launches;
+    }
+    if (kc > 0 && g == 0 && e == cudaSuccess) {
+      // u_0 is never a step's output above (a later segment's first state is
+      // the previous segment's last): add its history cotangent here
+      if (kc <= n) {
+        axpy_kernel<<<grid_for(slot), 256, 0, st>>>(T.lam, T.pend, slot);
+        e = cudaGetLastError();
+        ++launches;
+      }
     }
   }
   if (e == cudaSuccess && lam0) e = cudaMemcpyAsync(lam0, T.lam, bytes, cudaMemcpyDeviceToDevice, st);
@@ -260,7 +310,7 @@ fd_status rollout_reverse(fd_ctx* c, const float* u0, int n, int k, const float*
 void fd_train_free(fd_ctx* c) {
   TrainState* T = c->trn;
   if (!T) return;
-  void* ps[] = {T->ckpt, T->seg, T->lam, T->partial, T->corr};
+  void* ps[] = {T->ckpt, T->seg, T->lam, T->partial, T->corr, T->pend};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete T;
@@ -307,10 +357,6 @@ fd_status fd_rollout_adjoint(fd_ctx* c, const void* u0, int32_t n_steps, int32_t
                              void* lam0, float* dparams, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout_adjoint: null context");
   if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_adjoint: not built for the generic-grid path");
-  if (c->lrn && (c->lrn->fno_layers > 0 || c->lrn->ablation != 0))
-    return fd_set_error(c, FD_EUNSUPPORTED,
-                        "fd_rollout_adjoint: the frequency-domain operator and the ablation variants have no reverse "
-                        "mode in this build");
   if (!u0 || !lam_traj || !lam0) return fd_set_error(c, FD_EINVAL, "fd_rollout_adjoint: null pointer");
   if (n_steps < 1 || ckpt_every < 1) return fd_set_error(c, FD_EINVAL, "fd_rollout_adjoint: n_steps, ckpt_every >= 1");
   return rollout_reverse(c, static_cast<const float*>(u0), n_steps, ckpt_every, static_cast<const float*>(lam_traj),
@@ -322,10 +368,6 @@ fd_status fd_train_step(fd_ctx* c, const void* u0, const void* targets, int32_t 
                         float* dparams, double* loss, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_train_step: null context");
   if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_train_step: not built for the generic-grid path");
-  if (c->lrn && (c->lrn->fno_layers > 0 || c->lrn->ablation != 0))
-    return fd_set_error(c, FD_EUNSUPPORTED,
-                        "fd_train_step: the frequency-domain operator and the ablation variants have no reverse mode in "
-                        "this build");
   if (!u0 || !targets || !loss) return fd_set_error(c, FD_EINVAL, "fd_train_step: null pointer");
   if (n_steps < 1 || ckpt_every < 1) return fd_set_error(c, FD_EINVAL, "fd_train_step: n_steps, ckpt_every >= 1");
   return rollout_reverse(c, static_cast<const float*>(u0), n_steps, ckpt_every, nullptr,

@@ -32,14 +32,26 @@ struct AdjStageArgs {
   __nv_bfloat16* cbar;         // out: C_bar as chunk planes [batch][20][N][N][8], or null
   float* cbar_f32;             // out: C_bar as [batch][160][N][N] FP32, or null
   float* wl_bar;               // out: W_L_bar [80], accumulated with atomics, or null
+  float* cbias;                // out: per-channel face sums of C_bar [160] (the network's last bias
+                               // gradient, FP32), accumulated with atomics, or null
+  const float* fno;            // O_F(w) [batch][8][N][N] added to the face values, or null
+  float* fnobar;               // out: face-value cotangents [batch][8][N][N] (O_F's output cotangent), or null
+  int ablation;                // 0 full flux block, 1 without the physics convolution, 2 O_F only
   int flow, forcing, dord;
   float nu, idx, idy, drag;
 };
 
 // Per-face kernel of instance qi (axis, kind) at cell c: K[20] (5 x 4, row-major).
+// ablation 1 (without the physics-based convolution): K = (W_L + C) / h^deriv,
+// neither projected nor added to W_P; ablation 2 (O_F only): K = 0.
 __device__ __forceinline__ void adj_kernel_at(int qi, int axis, int kind, const float* swl, const uint4* cbase,
-                                              size_t NN, int c, int dord, float h, float (&K)[20]) {
+                                              size_t NN, int c, int dord, float h, float (&K)[20], int ablation = 0) {
   const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
+  if (ablation == 2) {
+#pragma unroll
+    for (int t = 0; t < 20; ++t) K[t] = 0.f;
+    return;
+  }
   float L[20];
 #pragma unroll
   for (int t = 0; t < 20; ++t) L[t] = swl ? swl[(kind * 2 + axis) * 20 + t] : 0.f;
@@ -79,13 +91,14 @@ __device__ __forceinline__ void adj_kernel_at(int qi, int axis, int kind, const 
   s1 *= (1.0f / 20.0f);
   sc *= (1.0f / 25.0f);
   sr *= (1.0f / 40.0f);
+  if (ablation == 1) s1 = sc = sr = 0.f;
   const float scale = kind == 1 ? 1.0f / h : 1.0f;
 #pragma unroll
   for (int r = 0; r < 5; ++r)
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
-      if (r == 2) {
+      if (r == 2 && ablation == 0) {
         if (kind == 0) {
           k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
         } else if (dord == 4) {
@@ -130,6 +143,7 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
   float* const wb = inst + 6 * FR * N;     // [2][BR][N]
   __shared__ float swl[80];
   __shared__ float swlb[80];
+  __shared__ float scb[160];
   const int tid = threadIdx.x, lane = tid & 31;
   const int b = blockIdx.y, j0 = blockIdx.x * RB;
   const float* w = a.w + (size_t)b * 2 * NN;
@@ -153,6 +167,7 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
     swl[tid] = a.wl ? a.wl[tid] : 0.f;
     swlb[tid] = 0.f;
   }
+  if (tid < 160) scb[tid] = 0.f;
   __syncthreads();
   const float* swlp = a.wl ? swl : nullptr;
   const uint4* cbase = a.coef ? reinterpret_cast<const uint4*>(a.coef) + (size_t)b * 20 * NN : nullptr;
@@ -171,7 +186,7 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
       const int pr_ = qi >> 1, fld = pr_ >> 1, axis = pr_ & 1, kind = qi & 1;
       const int sh = (pr_ == 0 || pr_ == 3) ? -1 : -2;
       float K[20];
-      adj_kernel_at(qi, axis, kind, swlp, cbase, NN, c, a.dord, axis == 0 ? hx : hy, K);
+      adj_kernel_at(qi, axis, kind, swlp, cbase, NN, c, a.dord, axis == 0 ? hx : hy, K, a.ablation);
       float v = 0.f;
 #pragma unroll
       for (int r = 0; r < 5; ++r)
@@ -181,6 +196,7 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
           const int ii = axis == 0 ? i + cc + sh : i + r - 2;
           v += K[r * 4 + cc] * W(fld, jj, ii);
         }
+      if (a.fno) v += a.fno[((size_t)b * 8 + qi) * NN + c];
       inst[(sl * FR + (fc >> LOGN)) * N + i] = v;
     }
   }
@@ -232,8 +248,10 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
       if (burgers && (qi == 1 || qi == 7))
         vb += 0.5f * (T(0, j, i) * W(0, j, i) + T(0, j, i + 1) * W(0, j, i + 1)) +
               0.5f * (T(1, j, i) * W(1, j, i) + T(1, j + 1, i) * W(1, j + 1, i));
+      if (a.fnobar) a.fnobar[((size_t)b * 8 + qi) * NN + c] = vb;
+      if (a.ablation == 2) continue;  // zero kernels: nothing to scatter, no kernel cotangent
       float K[20];
-      adj_kernel_at(qi, axis, kind, swlp, cbase, NN, c, a.dord, h, K);
+      adj_kernel_at(qi, axis, kind, swlp, cbase, NN, c, a.dord, h, K, a.ablation);
       float Kb[20];
 #pragma unroll
       for (int r = 0; r < 5; ++r)
@@ -257,6 +275,7 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
       s1 *= (1.0f / 20.0f);
       sc *= (1.0f / 25.0f);
       sr *= (1.0f / 40.0f);
+      if (a.ablation == 1) s1 = sc = sr = 0.f;  // the unprojected kernel's cotangent
       float lb[20];
 #pragma unroll
       for (int r = 0; r < 5; ++r)
@@ -289,13 +308,16 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
         }
       }
     }
-    if (a.wl_bar) {
+    if (a.wl_bar || a.cbias) {
 #pragma unroll
       for (int t = 0; t < 20; ++t) {
         float v = lsum[t];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) atomicAdd(&swlb[(kind * 2 + axis) * 20 + t], v);
+        if (lane == 0) {
+          atomicAdd(&swlb[(kind * 2 + axis) * 20 + t], v);
+          atomicAdd(&scb[qi * 20 + t], v);
+        }
       }
     }
   }
@@ -307,6 +329,7 @@ __global__ void __launch_bounds__(256) fv_adjoint_band_kernel(const AdjStageArgs
     atomicAdd(&gw[(size_t)f * NN + (size_t)jj * N + (rem & MSK)], wb[k]);
   }
   if (a.wl_bar && tid < 80) atomicAdd(&a.wl_bar[tid], swlb[tid]);
+  if (a.cbias && tid < 160) atomicAdd(&a.cbias[tid], scb[tid]);
 }
 
 // Reverse-mode combination of the RK4 stages (one CTA per trajectory):

@@ -26,6 +26,7 @@ EXPORTS = [
     "fd_step",
     "fd_rollout",
     "fd_rollout_host",
+    "fd_rollout_guarded",
     "fd_rollout_scalar",
     "fd_check_finite",
     "fd_check_finite_noalloc",
@@ -35,6 +36,7 @@ EXPORTS = [
     "fd_set_params_device",
     "fd_network_forward",
     "fd_step_adjoint",
+    "fd_tc_adjoint",
     "fd_rollout_adjoint",
     "fd_train_step",
     "fd_mse_loss",
@@ -134,6 +136,8 @@ def load(path: str = LIB_PATH):
     lib.fd_rollout.restype = C.c_int
     lib.fd_rollout_host.argtypes = [vp, vp, vp, i32, vp]
     lib.fd_rollout_host.restype = C.c_int
+    lib.fd_rollout_guarded.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.fd_rollout_guarded.restype = C.c_int
     lib.fd_rollout_scalar.argtypes = [vp, C.c_double, vp, vp, vp, vp, i32, vp]
     lib.fd_rollout_scalar.restype = C.c_int
     lib.fd_check_finite.argtypes = [vp, vp, vp]
@@ -150,6 +154,8 @@ def load(path: str = LIB_PATH):
     lib.fd_network_forward.restype = C.c_int
     lib.fd_step_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.fd_step_adjoint.restype = C.c_int
+    lib.fd_tc_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.fd_tc_adjoint.restype = C.c_int
     lib.fd_rollout_adjoint.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
     lib.fd_rollout_adjoint.restype = C.c_int
     lib.fd_train_step.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp]
@@ -223,6 +229,7 @@ class Config:
     tc_fno_width: int = 0
     ablation: int = 0  # 0 full flux block, 1 without the physics conv, 2 frequency operator only (Table 4)
     ny: Optional[int] = None  # rows when the grid is rectangular (Burgers on the generic-grid path); n = columns
+    spin_limit: int = 0  # iteration limit of the tensor-core kernels' bounded waits (0 = library default)
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -248,7 +255,7 @@ class Solver:
         g = FdGrid(cfg.n, cfg.ny or cfg.n, cfg.lx, cfg.ly, cfg.batch, FD_F64 if cfg.dtype == "f64" else FD_F32,
                    FD_BURGERS if cfg.flow == "burgers" else FD_NAVIER_STOKES)
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
-        o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, 1 << 26, cfg.path,
+        o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, cfg.spin_limit, cfg.path,
                       cfg.fno_layers, cfg.fno_modes, cfg.fno_width, cfg.tc_fno_layers, cfg.tc_fno_modes,
                       cfg.tc_fno_width, cfg.ablation)
         h = C.c_void_p()
@@ -285,6 +292,12 @@ class Solver:
         """Velocity and passive scalar s [B, ny, nx] together (generic-grid path)."""
         self._check(self.lib.fd_rollout_scalar(self.h, float(diffusivity), _ptr(u0), _ptr(s0), _ptr(u_final),
                                                _ptr(s_final), int(n_steps), _stream_handle(stream)))
+
+    def rollout_guarded(self, u0, u_final, n_steps: int, fell_back, chunk: int = 0, stream=None):
+        """Learned rollout with the plain FV step as fallback; fell_back (device int32[batch])
+        receives -1 or the step at which the trajectory switched to the plain solver."""
+        self._check(self.lib.fd_rollout_guarded(self.h, _ptr(u0), _ptr(u_final), int(n_steps), int(chunk),
+                                                _ptr(fell_back), _stream_handle(stream)))
 
     def rollout_host(self, u0_host, u_final_host, n_steps: int, stream=None):
         self._check(self.lib.fd_rollout_host(self.h, _ptr(u0_host), _ptr(u_final_host), int(n_steps),
@@ -339,6 +352,14 @@ class Solver:
         dp = _ptr(dparams) if dparams is not None else None
         self._check(self.lib.fd_step_adjoint(self.h, _ptr(u_in), _ptr(lam_out), _ptr(lam_in), dp,
                                              _stream_handle(stream)))
+
+    def tc_adjoint(self, hist, lam, hist_bar, vbar=None, dparams=None, stream=None):
+        """Reverse mode of one temporal correction: hist [k_c, batch, 2, n, n] (oldest first),
+        lam the cotangent of the corrected state; writes hist_bar [k_c, batch, 2, n, n] and
+        vbar = P(lam) when given; dparams accumulates the correction network's gradients."""
+        self._check(self.lib.fd_tc_adjoint(self.h, _ptr(hist), _ptr(lam), _ptr(vbar) if vbar is not None else None,
+                                           _ptr(hist_bar), _ptr(dparams) if dparams is not None else None,
+                                           _stream_handle(stream)))
 
     def rollout_adjoint(self, u0, n_steps: int, ckpt_every: int, lam_traj, lam0, dparams=None, stream=None):
         """lam0 = dL/du0 for the cotangents lam_traj of the states after steps 1..n."""

@@ -30,3 +30,19 @@ def run_pool(fn, jobs, max_procs=16):
         return [fn(j) for j in jobs]
     with mp.get_context("spawn").Pool(procs) as pool:
         return pool.map(fn, jobs, chunksize=1)
+
+
+def rollout_vjp_job(args):
+    """(U0, problem, n, lam_traj, model) -> (lam0, flat parameter gradient) of
+    oracle.train.rollout_vjp_full."""
+    from oracle import train as T
+
+    U0, p, n, lam_traj, model = args
+    lam0, g = T.rollout_vjp_full(U0, p, n, lam_traj, model)
+    return lam0, (None if g is None else T.flat_grads(g, model))
+
+
+def tc_vjp_job(args):
+    """(U, hist, problem, model, gbar) -> oracle.adjoint.temporal_correction_vjp(...)."""
+    U, hist, p, model, gbar = args
+    return A.temporal_correction_vjp(U, hist, p, model, gbar)

@@ -109,6 +109,7 @@ def test_calls_on_null_context_are_rejected(lib):
     assert lib.fd_step(None, None, None, None) == fd.FD_EINVAL
     assert lib.fd_rollout(None, None, None, None, 1, 0, None) == fd.FD_EINVAL
     assert lib.fd_rollout_host(None, None, None, 1, None) == fd.FD_EINVAL
+    assert lib.fd_rollout_guarded(None, None, None, 1, 0, None, None) == fd.FD_EINVAL
     assert lib.fd_check_finite(None, None, None) == fd.FD_EINVAL
     assert lib.fd_destroy(None) == fd.FD_OK
     assert lib.fd_last_launch_count(None) == 0

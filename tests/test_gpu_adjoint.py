@@ -6,7 +6,7 @@ Tolerances: plain FP32 step adjoint <= 1e-5 relative L2 (FP32 arithmetic, four
 stages and five projections); learned step: state cotangent <= 1e-4 (the BF16
 network only touches the small learned part), W_L gradient <= 1e-3 (FP32 sums
 over all faces of terms that include the BF16 network output), network weight
-and bias gradients <= 3e-2 per layer (BF16 activations and cotangents, ~2^-9
+and bias gradients <= 2e-2 per layer (BF16 activations and cotangents, ~2^-9
 relative rounding per operand, FP32 accumulation over up to 2 x 64^2 x 64 x 9
 terms).
 """
@@ -130,8 +130,8 @@ def test_learned_step_adjoint_matches_oracle(n, b, forcing):
     for l in range(6):
         dW_ref = sum(r[1][1][l][0] for r in refs)
         db_ref = sum(r[1][1][l][1] for r in refs)
-        assert rel_l2(layers_g[l][0], dW_ref) <= 3e-2, f"layer {l} weights"
-        assert rel_l2(layers_g[l][1], db_ref) <= 3e-2, f"layer {l} biases"
+        assert rel_l2(layers_g[l][0], dW_ref) <= 2e-2, (l, rel_l2(layers_g[l][0], dW_ref))
+        assert rel_l2(layers_g[l][1], db_ref) <= 2e-2, (l, rel_l2(layers_g[l][1], db_ref))
 
 
 def test_parameter_gradients_accumulate():

@@ -87,11 +87,6 @@ def test_frequency_operator_rollout_and_zero_output():
     s1, _, a = run(n, 2, model(6, zero), zero, 3)
     s2, _, b = run(n, 2, model(6, None), None, 3)
     assert np.array_equal(a, b)
-    # no reverse mode for the operator in this build
-    u = torch.zeros((2, 2, n, n), device="cuda")
-    with pytest.raises(fd.FdError) as e:
-        s1.step_adjoint(u, u, torch.empty_like(u))
-    assert e.value.status == fd.FD_EUNSUPPORTED
     s1.close()
     s2.close()
 
@@ -170,8 +165,4 @@ def test_ablation_variants_match_oracle(ablation, with_fno):
         assert err <= tol, (steps, err)
         full = np.stack([O.rollout(U0[k].astype(np.float64), p, steps, model=model(0))[0] for k in range(b)])
         assert rel_l2(full, ref) > 20 * err
-    u = torch.zeros((b, 2, n, n), device="cuda")
-    with pytest.raises(fd.FdError) as e:
-        s.step_adjoint(u, u, torch.empty_like(u))
-    assert e.value.status == fd.FD_EUNSUPPORTED
     s.close()

@@ -222,3 +222,35 @@ def test_plan_errors():
     c = s.autotune(probe_steps=2)
     assert len(c) == 1 and c[0]["n_stream"] == 1 and c[0]["us_per_step"] > 0
     s.close()
+
+
+def test_batch_recaptures_after_a_member_plan_change():
+    # a plan change can replace the member's streaming sub-context; the batch
+    # must not replay a graph that still launches on the old buffers
+    cfg = fd.Config(n=32, batch=4, dtype="f32", nu=1e-3, dt=1e-3)
+    U0 = ic(cfg, 4).astype(np.float32)
+    p = oracle_problem(cfg)
+    ref = np.stack([O.rollout(U0[k].astype(np.float64), p, 5)[0] for k in range(4)])
+    s = fd.Solver(cfg)
+    other = fd.Solver(fd.Config(n=64, batch=1, dtype="f32", nu=1e-3, dt=1e-3))
+    U1 = I.decaying_ic(64, 3)[None].astype(np.float32)
+    o_ref, _ = rollout(other, U1, 5)
+    a0 = torch.tensor(U0, device="cuda")
+    a1 = torch.empty_like(a0)
+    b0 = torch.tensor(U1, device="cuda")
+    b1 = torch.empty_like(b0)
+    bt = fd.Batch()
+    bt.add(s, a0, a1, 5)
+    bt.add(other, b0, b1, 5)
+    for plan in [None, (1, 2, 2), (2, 1, 3), (1, 4, 0), (4, 3, 1)]:
+        if plan is not None:
+            s.set_plan(*plan)
+        a1.fill_(float("nan"))
+        bt.run()
+        torch.cuda.synchronize()
+        assert rel_l2(a1.double().cpu().numpy(), ref) <= 1e-5, plan
+        assert rel_l2(b1.double().cpu().numpy(), o_ref) <= 1e-6
+        assert s.plan()["n_stream"] == (0 if plan is None else plan[2])
+    bt.close()
+    s.close()
+    other.close()

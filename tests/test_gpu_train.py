@@ -8,7 +8,7 @@ Tolerances: coarse-graining FP32 <= 1e-6 (a mean of <= 8 values), FP64
 <= 1e-14; MSE <= 1e-6 (FP64 accumulation of FP32 differences); Adam <= 1e-6
 (FP32 update of FP32 state); rollout reverse mode: plain <= 1e-5 (FP32, a few
 steps of the 1e-5 step tolerance), learned as the one-step adjoint (state
-cotangent <= 1e-4 per step, network gradients <= 3e-2).
+cotangent <= 1e-4 per step, network gradients <= 2e-2).
 """
 
 import numpy as np
@@ -141,9 +141,9 @@ def test_learned_train_step_matches_oracle():
     assert rel_l2(g[:80], wl_ref.ravel()) <= 2e-3
     o = 80
     for (W, bb), (dW, db) in zip(model.stencil, layers_ref):
-        assert rel_l2(g[o:o + W.size], dW.ravel()) <= 3e-2
+        assert rel_l2(g[o:o + W.size], dW.ravel()) <= 2e-2, rel_l2(g[o:o + W.size], dW.ravel())
         o += W.size
-        assert rel_l2(g[o:o + bb.size], db) <= 3e-2
+        assert rel_l2(g[o:o + bb.size], db) <= 2e-2, rel_l2(g[o:o + bb.size], db)
         o += bb.size
 
 

@@ -74,3 +74,23 @@ def test_noalloc_rejects_oversize_and_bad_arguments(lib):
     assert lib.fd_check_finite_noalloc(None, 8, fd.FD_F32, C.byref(cnt), s) == fd.FD_EINVAL
     assert lib.fd_check_finite_noalloc(u.data_ptr(), 0, fd.FD_F32, C.byref(cnt), s) == fd.FD_OK
     assert cnt.value == 0
+
+
+def test_noalloc_at_the_maximum_count_and_allocates_nothing(lib):
+    # FD_NOALLOC_MAX_ELEMS elements: every per-block slot is used and the last
+    # one sits next to the total; the only non-finite value is the last element
+    n = 1 << 24
+    u = torch.zeros(n, dtype=torch.float32, device="cuda")
+    u[-1] = float("nan")
+    st, cnt = _noalloc(lib, u, fd.FD_F32)
+    assert st == fd.FD_ENONFINITE and cnt == 1
+    u[-1] = 0.0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in range(5):
+        u[k * 1000] = float("inf") if k % 2 else 0.0
+        st, cnt = _noalloc(lib, u, fd.FD_F32)
+        assert cnt == (k + 1) // 2 and (st == fd.FD_ENONFINITE) == (cnt > 0)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0

@@ -150,17 +150,26 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[NC]) {
   }
 }
 
-// GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)) with erf from the rational
-// approximation 7.1.26 of Abramowitz & Stegun (|error| <= 1.5e-7, far below
-// the BF16 rounding of the activations).
-__device__ __forceinline__ float gelu_f(float x) {
-  const float z = fabsf(x) * 0.70710678118654752f;
-  const float t = __fdividef(1.0f, 1.0f + 0.3275911f * z);
-  const float poly = t * (0.254829592f + t * (-0.284496736f + t * (1.421413741f + t * (-1.453152027f + t * 1.061405429f))));
-  const float erf_abs = 1.0f - poly * __expf(-z * z);
-  const float erf_x = x < 0.0f ? -erf_abs : erf_abs;
-  return 0.5f * x * (1.0f + erf_x);
+// GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)) of the forward epilogues,
+// with erf(z) ~ tanh(z (a + b z^2)): a = 1.12967583, b = 0.0997927 minimise the
+// largest error over z >= 0 (2.8e-4; fitted here), so
+// GELU(x) ~ 0.5 x (1 + tanh(x (A + B x^2))), A = a / sqrt 2, B = b / (2 sqrt 2),
+// evaluated with the hardware tanh (one special-function op per value; its
+// relative error is 2^-11). The result is within 4e-4 + 2.5e-4 |x| of GELU,
+// below the BF16 rounding of the activations it produces (2^-9 relative).
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
+__device__ __forceinline__ float gelu_f(float x) {
+  const float y = x * fmaf(0.0352820483f, x * x, 0.798801437f);
+  const float h = 0.5f * x;
+  return fmaf(h, tanh_hw(y), h);
+}
+
+// The same GELU with erf from the rational approximation 7.1.26 of Abramowitz &
+// Stegun (|error| <= 1.5e-7): the reference form of the derivative below.
 
 // GELU'(x) = Phi(x) + x phi(x), with the same erf approximation
 __device__ __forceinline__ float gelu_grad_f(float x) {

@@ -458,24 +458,33 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
       const int gy = y0 + m / N;
       const float* eleft = eb + ((grp * 4 + qleft) * 2) * CG;
       const float* eright = eb + ((grp * 4 + qright) * 2) * CG + CG;
+      // neighbours by a rotation within the warp; lanes 0 and 31 take the
+      // neighbouring quarter's edge value instead (a select, no divergent branch;
+      // for N = 32 a quarter is one row and the rotation is already the
+      // periodic wrap)
+      const bool edge_l = N > 32 && lane == 0, edge_r = N > 32 && lane == 31;
 #pragma unroll
       for (int cc = 0; cc < CG; cc += 8) {
+        float el[8], er[8];
+        if (N > 32) {
+#pragma unroll
+          for (int j = 0; j < 8; j += 4) {
+            const float4 l4 = *reinterpret_cast<const float4*>(eleft + cc + j);
+            const float4 r4 = *reinterpret_cast<const float4*>(eright + cc + j);
+            el[j] = l4.x, el[j + 1] = l4.y, el[j + 2] = l4.z, el[j + 3] = l4.w;
+            er[j] = r4.x, er[j + 1] = r4.y, er[j + 2] = r4.z, er[j + 3] = r4.w;
+          }
+        }
         float outv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float left = __shfl_up_sync(0xffffffffu, pm[cc + j], 1);
-          const float right = __shfl_down_sync(0xffffffffu, pp[cc + j], 1);
+          float left = __shfl_sync(0xffffffffu, pm[cc + j], (lane + 31) & 31);
+          float right = __shfl_sync(0xffffffffu, pp[cc + j], (lane + 1) & 31);
+          if (N > 32) {
+            left = edge_l ? el[j] : left;
+            right = edge_r ? er[j] : right;
+          }
           outv[j] = p0[cc + j] + left + right;
-        }
-        // lanes 0 and 31 got their own value back from the shuffle; swap in the
-        // neighbouring quarter's edge value, one branch per 8 values
-        if (lane == 0) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) outv[j] += eleft[cc + j] - pm[cc + j];
-        }
-        if (lane == 31) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) outv[j] += eright[cc + j] - pp[cc + j];
         }
         const int chunk = (co0 + cc) >> 3;
         const size_t oidx = ((((size_t)b * (a.cout_total / 8) + chunk) * N + gy) * N + x) * 8;

@@ -582,6 +582,87 @@ def corr_measurement(fd, I, n_fine: int = 2048, n_train: int = 8, n_test: int = 
     return out
 
 
+def resweep_measurement(fd, I, train_re: float = 1000.0, res=(200.0, 500.0, 1000.0, 1500.0, 2000.0),
+                        n_fine: int = 1024, n_train: int = 8, n_test: int = 4, warm: float = 2.0,
+                        horizon: float = 3.0, iters: int = 300, unroll: int = 16, lr: float = 1e-3, kc: int = 4):
+    """Generalisation over the Reynolds number (the paper's Re sweep, Sec. 4): the
+    learned 64^2 solver (stencil network + temporal-correction head) is trained once,
+    on forced-flow labels at Re = train_re (an n_fine^2 plain-FV reference
+    face-averaged to 64^2), then evaluated, unchanged, at every Re of the sweep (the
+    context's viscosity is 1/Re; the network is the same) against a fresh reference
+    at that Re. Reported per Re: the time the vorticity correlation (min over the
+    test trajectories) stays >= 0.95 for the learned solver and for plain FV at
+    64^2, and the correlation at the horizon."""
+    import torch
+
+    from paper_2507_01975_gb300.train import TrainConfig, Trainer
+
+    nc = 64
+    dt_f = 2.19e-4 * 2048 / n_fine
+    rt = 32 * n_fine // 2048
+    dt_c = rt * dt_f
+    kt = int(round(horizon / dt_c))
+
+    def reference(nu, batch, seed0):
+        fine = fd.Solver(fd.Config(n=n_fine, batch=batch, dtype="f32", nu=nu, dt=dt_f, forcing="kolmogorov"))
+        u = torch.tensor(np.stack([I.kolmogorov_ic(n_fine, seed0 + k) for k in range(batch)]).astype(np.float32),
+                         device="cuda")
+        fine.rollout(u, u, int(round(warm / dt_f)))
+        labels = torch.empty((kt + 1, batch, 2, nc, nc), device="cuda")
+        fd.downsample(u, labels[0], n_fine // nc)
+        for k in range(kt):
+            fine.rollout(u, u, rt)
+            fd.downsample(u, labels[k + 1], n_fine // nc)
+        torch.cuda.synchronize()
+        fine.close()
+        return labels
+
+    t0 = time.perf_counter()
+    lt = reference(1.0 / train_re, n_train, 500)
+    st = I.random_conv_stack(21, 2, 64, 160, last_scale=0.0)
+    tc = I.random_conv_stack(22, 2 * kc, 64, 2, last_scale=0.0)
+    ls = fd.Solver(fd.Config(n=nc, batch=n_train, dtype="f32", nu=1.0 / train_re, dt=dt_c, forcing="kolmogorov",
+                             learned=True, k_c=kc))
+    tr = Trainer(ls, I.pack_params(np.zeros((2, 2, 5, 4)), st, tc), TrainConfig(unroll=unroll, ckpt_every=8, lr=lr))
+    rng = np.random.default_rng(1)
+    for _ in range(iters):
+        s0 = int(rng.integers(0, kt - unroll + 1))
+        tr.step(lt[s0], lt[s0 + 1:s0 + 1 + unroll])
+    torch.cuda.synchronize()
+    final_loss = float(tr.loss.item())
+    corr = torch.zeros(n_test, dtype=torch.float64, device="cuda")
+    scorer = fd.Solver(fd.Config(n=nc, batch=n_test, dtype="f32"))
+
+    def horizon_of(solver, labels):
+        u0 = labels[0].clone()
+        traj = torch.empty((kt, n_test, 2, nc, nc), device="cuda")
+        last = torch.empty_like(u0)
+        solver.rollout(u0, last, kt, traj=traj, save_every=1)
+        curve = []
+        for k in range(kt):
+            scorer.vorticity_pcc(traj[k], labels[k + 1], corr)
+            curve.append(float(corr.min().item()))
+        t95 = next(((k + 1) * dt_c for k, c in enumerate(curve) if c < 0.95), None)
+        return {"t_corr_095": t95, "corr_at_horizon": curve[-1]}
+
+    rows = {}
+    for re_ in res:
+        nu = 1.0 / re_
+        lv = reference(nu, n_test, 900)
+        le = fd.Solver(fd.Config(n=nc, batch=n_test, dtype="f32", nu=nu, dt=dt_c, forcing="kolmogorov", learned=True,
+                                 k_c=kc))
+        le.set_params_device(tr.theta)
+        pl = fd.Solver(fd.Config(n=nc, batch=n_test, dtype="f32", nu=nu, dt=dt_c, forcing="kolmogorov"))
+        rows[f"Re{int(re_)}"] = {"learned64": horizon_of(le, lv), "plain64": horizon_of(pl, lv)}
+        le.close()
+        pl.close()
+    return {"workload": f"forced NS, learned 64^2 (stencil network + temporal correction every {kc} steps, "
+                        f"dt {dt_c:.3g}) trained at Re {int(train_re)} on {n_train} trajectories of a {n_fine}^2 "
+                        f"reference ({iters} Adam iterations), evaluated unchanged at each Re against a fresh "
+                        f"{n_fine}^2 reference ({n_test} test trajectories, horizon {horizon})",
+            "final_training_loss": final_loss, "per_re": rows, "seconds": time.perf_counter() - t0}
+
+
 def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
     """Mixed batch (512 trajectories): plain FP32 32^2 Burgers, 64^2 decaying, 128^2
     Kolmogorov, 256^2 shear (64 each) and learned BF16-network 32^2 Kolmogorov and 64^2
@@ -744,11 +825,13 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-stencil inference measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-fine", action="store_true", help="skip the 2048^2 streaming-path measurement")
+    ap.add_argument("--no-resweep", action="store_true",
+                    help="skip the Reynolds-number generalisation sweep of the learned solver")
     ap.add_argument("--no-corr", action="store_true",
                     help="skip the wall-time-to-0.95-correlation measurement (learned vs plain FV)")
     ap.add_argument("--no-speed", action="store_true",
                     help="skip the GPU-seconds-per-physical-second measurement on the paper's grids")
-    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch", "speed"],
+    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch", "speed", "resweep"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
     ap.add_argument("--plan", default=None,
@@ -776,7 +859,8 @@ def main():
               "fine": lambda: fine_measurement(fd, I, steps=max(args.iters, 2)),
               "corr": lambda: corr_measurement(fd, I, iters=max(args.iters, 300)),
               "batch": lambda: batch_measurement(fd, I),
-              "speed": lambda: speed_measurement(fd, I)}[args.only]
+              "speed": lambda: speed_measurement(fd, I),
+              "resweep": lambda: resweep_measurement(fd, I)}[args.only]
         print(json.dumps(fn()), flush=True)
         return
 
@@ -902,6 +986,7 @@ def main():
     fine = None if args.no_fine else fine_measurement(fd, I)
     speed = None if args.no_speed else speed_measurement(fd, I)
     corr = None if args.no_corr else corr_measurement(fd, I)
+    resweep = None if args.no_resweep else resweep_measurement(fd, I)
     line = {
         "metric": METRIC,
         "value": value,
@@ -937,6 +1022,7 @@ def main():
         "fine_grid": fine,
         "paper_speed_table": speed,
         "wall_time_to_corr_095": corr,
+        "re_generalisation": resweep,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -168,6 +168,43 @@ __device__ __forceinline__ float gelu_f(float x) {
   return fmaf(h, tanh_hw(y), h);
 }
 
+// Packed FP32 pairs: one add / mul / fma instruction for two values (the
+// epilogue's arithmetic is elementwise, so its values go in pairs).
+struct f32x2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 p, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p.v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+// gelu_f on a pair
+__device__ __forceinline__ f32x2 gelu2(f32x2 x) {
+  const f32x2 y = mul2(x, fma2(mul2(x, x), pack2(0.0352820483f, 0.0352820483f), pack2(0.798801437f, 0.798801437f)));
+  const f32x2 h = mul2(x, pack2(0.5f, 0.5f));
+  float y0, y1;
+  unpack2(y, y0, y1);
+  return fma2(h, pack2(tanh_hw(y0), tanh_hw(y1)), h);
+}
+
 // The same GELU with erf from the rational approximation 7.1.26 of Abramowitz &
 // Stegun (|error| <= 1.5e-7): the reference form of the derivative below.
 
@@ -182,16 +219,19 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
   return 0.5f * (1.0f + erf_x) + x * 0.39894228040143268f * g;
 }
 
-template <int LOGN, int CIN, int COUT_TILE, int NBUF = 4>
+template <int LOGN, int CIN, int COUT_TILE, int NBUF = (LOGN >= 7 ? 3 : 4)>
 struct ConvCfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int TM = 128;             // output pixels per tile
   static constexpr int TROWS = TM / N;       // image rows per tile
   static constexpr int IROWS = TROWS + 2;    // input rows with the dy halo
   static constexpr int KC = CIN / 8;         // 8-channel chunks
-  static constexpr int NT = 640;
-  static constexpr int NEPI = 16;           // epilogue warps
-  static constexpr int CG = COUT_TILE / 4;  // output channels per epilogue warp
+  // epilogue warps: 4 per TMEM lane quarter; warps 0 .. 3 are the producer,
+  // the MMA issuer and two idle warps (640 threads; more epilogue warps would
+  // pass the 1024-thread limit of a CTA)
+  static constexpr int NEPI = 16;
+  static constexpr int NT = 128 + NEPI * 32;
+  static constexpr int CG = COUT_TILE * 4 / NEPI;  // output channels per epilogue warp
   static constexpr uint32_t PLANE_BYTES = IROWS * N * 16;         // one chunk plane of the tile
   static constexpr uint32_t ATILE_BYTES = KC * PLANE_BYTES;       // one input tile
   // weights [dy][c8][dx][co8][8 co][8 ci]: the three dx blocks of one (dy, c8)
@@ -201,10 +241,17 @@ struct ConvCfg {
   static constexpr uint32_t OFF_A = 0;                            // NBUF input tiles
   static constexpr uint32_t OFF_W = NBUF * ATILE_BYTES;
   static constexpr uint32_t OFF_BND = OFF_W + W_BYTES;            // epilogue boundary exchange
-  static constexpr uint32_t BND_BYTES = 2 * 4 * 4 * 2 * CG * 4;  // [parity][group][quarter][2][CG]
+  static constexpr uint32_t BND_BYTES = 2 * (NEPI / 4) * 4 * 2 * CG * 4;  // [parity][group][quarter][2][CG]
   static constexpr uint32_t OFF_BIASV = OFF_BND + BND_BYTES;      // bias of the whole output tensor
   static constexpr uint32_t OFF_BAR = OFF_BIASV + 256 * 4;
-  static constexpr uint32_t SMEM = OFF_BAR + 128;
+  static constexpr uint32_t OFF_PAIR = OFF_BAR + 128;             // per exchange-group abort flags
+  static constexpr uint32_t SMEM = OFF_PAIR + 64;
+  // epilogue warps of one channel group that hold the lane quarters of one
+  // image row exchange edge values: QR quarters per row, groups of QR warps
+  // (none for N = 32, where a quarter is a whole row)
+  static constexpr int QR = N / 32;
+  static constexpr int NXG = QR > 1 ? (NEPI / 4) * (4 / QR) : 0;  // exchange groups
+  static_assert(NXG <= 8, "named barriers 2 .. 9; abort flags [tile parity][group]");
   static constexpr int ACC_COLS = 3 * COUT_TILE;                  // P_-1, P_0, P_+1
   static constexpr int TMEM_COLS = 2 * ACC_COLS <= 256 ? 256 : 512;
   static_assert(N >= 32 && N <= 128, "a tile covers whole image rows");
@@ -216,8 +263,8 @@ struct ConvCfg {
   static_assert(NBUF >= 1 && NBUF <= 4, "input buffering");
 };
 
-template <int LOGN, int CIN, int COUT_TILE, int NBUF = 4>
-__global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
+template <int LOGN, int CIN, int COUT_TILE, int NBUF = (LOGN >= 7 ? 3 : 4)>
+__global__ void __launch_bounds__(ConvCfg<LOGN, CIN, COUT_TILE, NBUF>::NT, 1) conv3x3_tc_kernel(const ConvArgs a) {
   using Cfg = ConvCfg<LOGN, CIN, COUT_TILE, NBUF>;
   constexpr int N = Cfg::N, TROWS = Cfg::TROWS, IROWS = Cfg::IROWS, KC = Cfg::KC;
   constexpr int CG = Cfg::CG;
@@ -234,7 +281,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
   uint64_t* const w_full = bars + 12;
   uint32_t* const tslot = reinterpret_cast<uint32_t*>(bars + 13);
   volatile uint32_t* const abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 14);
-  volatile uint32_t* const ep_abort = reinterpret_cast<volatile uint32_t*>(bars + 15);
+  volatile uint32_t* const pair_abort = reinterpret_cast<volatile uint32_t*>(smem + Cfg::OFF_PAIR);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tiles_per_img = N / TROWS;
@@ -253,7 +300,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
     }
     mbar_init(w_full, 1);
     *abort_flag = 0;
-    *ep_abort = 0;
+    for (int g = 0; g < 16; ++g) pair_abort[g] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tslot, Cfg::TMEM_COLS);
@@ -412,7 +459,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
     // by shuffles; the lane-0 / lane-31 edges of each 32-pixel quarter go
     // through shared memory (double buffered by tile parity, one named barrier
     // per tile for the epilogue warps).
-    const int ew = warp - 4;          // 0..15
+    const int ew = warp - 4;          // 0 .. NEPI - 1
     const int quarter = warp & 3;     // TMEM lane quarter = pixels 32q .. 32q+31
     const int grp = ew >> 2;          // output-channel group of CG channels
     const int m = quarter * 32 + lane;
@@ -427,33 +474,41 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
       const int b = pix / tiles_per_img, y0 = (pix % tiles_per_img) * TROWS;
       const int s = i & 1;
       const bool ok = mbar_wait(c_full + s, (i >> 1) & 1, lim);
-      if (!ok) {
-        *ep_abort = 1;
-        atomicOr(a.err, 16u);
-      }
+      if (!ok) atomicOr(a.err, 16u);
       tmem_fence_after_sync();
       const uint32_t tcol = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Cfg::ACC_COLS) + grp * CG;
       float pm[CG], pp[CG], p0[CG];
-      float* const eb = bnd + (size_t)s * (4 * 4 * 2 * CG);
+      float* const eb = bnd + (size_t)s * ((Cfg::NEPI / 4) * 4 * 2 * CG);
       if (ok) {
         tmem_ld_cols<CG>(tcol + 0 * COUT_TILE, pm);
         tmem_ld_cols<CG>(tcol + 2 * COUT_TILE, pp);
         tmem_ld_cols<CG>(tcol + 1 * COUT_TILE, p0);
         tmem_wait_ld();
         float* mine = eb + ((grp * 4 + quarter) * 2) * CG;
-        if (lane == 31) {
+        if (Cfg::QR > 1 && lane == 31) {
 #pragma unroll
           for (int j = 0; j < CG; ++j) mine[j] = pm[j];
         }
-        if (lane == 0) {
+        if (Cfg::QR > 1 && lane == 0) {
 #pragma unroll
           for (int j = 0; j < CG; ++j) mine[CG + j] = pp[j];
         }
       }
-      // every epilogue warp arrives here once per tile; the abort decision is
-      // taken together after it
-      asm volatile("bar.sync 1, %0;" ::"r"(Cfg::NEPI * 32) : "memory");
-      if (*ep_abort) break;
+      // the warps of an exchange group meet once per tile (named barrier 2 + the
+      // group's index). The group's abort flag for this tile is written only by
+      // its own warps before the barrier and read by them after it, so they all
+      // take the same decision; flags alternate with the tile parity, so a warp
+      // that already moved on to the next tile never writes the flag its
+      // partner is about to read.
+      if constexpr (Cfg::QR > 1) {
+        const int xg = grp * (4 / Cfg::QR) + quarter / Cfg::QR;
+        volatile uint32_t* const flag = pair_abort + (i & 1) * 8 + xg;
+        if (!ok) *flag = 1;
+        asm volatile("bar.sync %0, %1;" ::"r"(2 + xg), "r"(Cfg::QR * 32) : "memory");
+        if (*flag) break;
+      } else {
+        if (!ok) break;
+      }
       const int co0 = a.co_base + part * COUT_TILE + grp * CG;
       const int gy = y0 + m / N;
       const float* eleft = eb + ((grp * 4 + qleft) * 2) * CG;
@@ -477,14 +532,19 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
         }
         float outv[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float left = __shfl_sync(0xffffffffu, pm[cc + j], (lane + 31) & 31);
-          float right = __shfl_sync(0xffffffffu, pp[cc + j], (lane + 1) & 31);
+        for (int j = 0; j < 8; j += 2) {
+          float l0 = __shfl_sync(0xffffffffu, pm[cc + j], (lane + 31) & 31);
+          float l1 = __shfl_sync(0xffffffffu, pm[cc + j + 1], (lane + 31) & 31);
+          float r0 = __shfl_sync(0xffffffffu, pp[cc + j], (lane + 1) & 31);
+          float r1 = __shfl_sync(0xffffffffu, pp[cc + j + 1], (lane + 1) & 31);
           if (N > 32) {
-            left = edge_l ? el[j] : left;
-            right = edge_r ? er[j] : right;
+            l0 = edge_l ? el[j] : l0;
+            l1 = edge_l ? el[j + 1] : l1;
+            r0 = edge_r ? er[j] : r0;
+            r1 = edge_r ? er[j + 1] : r1;
           }
-          outv[j] = p0[cc + j] + left + right;
+          const f32x2 sum = add2(add2(pack2(p0[cc + j], p0[cc + j + 1]), pack2(l0, l1)), pack2(r0, r1));
+          unpack2(sum, outv[j], outv[j + 1]);
         }
         const int chunk = (co0 + cc) >> 3;
         const size_t oidx = ((((size_t)b * (a.cout_total / 8) + chunk) * N + gy) * N + x) * 8;
@@ -511,7 +571,10 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) outv[j] += sbias[co0 + cc + j];
+          for (int j = 0; j < 8; j += 2) {
+            const float2 bb = *reinterpret_cast<const float2*>(sbias + co0 + cc + j);
+            unpack2(add2(pack2(outv[j], outv[j + 1]), pack2(bb.x, bb.y)), outv[j], outv[j + 1]);
+          }
           if (a.gelu == 1) {
             if (a.aux_out) {
               uint4 zk;
@@ -526,7 +589,7 @@ __global__ void __launch_bounds__(640, 1) conv3x3_tc_kernel(const ConvArgs a) {
               *reinterpret_cast<uint4*>(a.aux_out + oidx) = zk;
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) outv[j] = gelu_f(outv[j]);
+            for (int j = 0; j < 8; j += 2) unpack2(gelu2(pack2(outv[j], outv[j + 1])), outv[j], outv[j + 1]);
           }
         }
         uint4 pk;

@@ -58,16 +58,14 @@ struct LearnedCfg {
   static constexpr int HSTR = N / 2 + 1;
   static constexpr int COLLEN = N + 1;
   static constexpr size_t W_BYTES = (size_t)2 * N * N * 4;
-  static constexpr size_t I_BYTES = (size_t)8 * N * N * 4;
   static constexpr size_t SCR_BYTES = align16(cmax((size_t)N * HSTR * 8, (size_t)(N / 2) * COLLEN * 8));
-  static constexpr size_t OFF_I = W_BYTES;
-  static constexpr size_t OFF_SCR = OFF_I + I_BYTES;
+  static constexpr size_t OFF_SCR = W_BYTES;
   static constexpr size_t OFF_TW = OFF_SCR + SCR_BYTES;
   static constexpr size_t OFF_SX = OFF_TW + (N / 2) * 8;
   static constexpr size_t OFF_SY = OFF_SX + align16((N / 2 + 2) * 4);
   static constexpr size_t OFF_FRC = OFF_SY + N * 4;
   static constexpr size_t SMEM = OFF_FRC + N * 4;
-  static constexpr size_t SMEM_PROJ = OFF_FRC;  // correct_project needs no instance arrays (unused region)
+  static_assert(SMEM <= 232448, "one trajectory's state and spectrum scratch in shared memory");
 };
 
 // Spectral projection of a trajectory tile wt[2][N][N] in shared memory

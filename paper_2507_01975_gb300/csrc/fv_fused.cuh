@@ -21,11 +21,13 @@
 //      divergence of its last row needs no extra exchange;
 //   D. (Navier-Stokes) projection of w' (Sec. 3.6, App. B.3-B.4): cell
 //      divergence computed in registers -> warp FFTs of two real rows packed
-//      as one complex row, unpacked into half spectra -> in-place DSMEM
-//      transpose -> warp column FFTs, multiply by 1 / symbol of D2 G2 (zero
-//      mode removed), inverse column FFTs -> in-place DSMEM transpose back ->
-//      inverse warp row FFTs -> w' -= G2 p (the row below comes from the
-//      previous CTA through DSMEM).
+//      as one complex row, unpacked into half spectra -> DSMEM transpose ->
+//      warp column FFTs, multiply by 1 / symbol of D2 G2 (zero mode removed),
+//      inverse column FFTs -> DSMEM transpose back -> inverse warp row FFTs ->
+//      w' -= G2 p (the row below comes from the previous CTA through DSMEM).
+//      The transposes are in place through registers (two cluster barriers
+//      each), except at N = 256, where the transforms store their outputs
+//      straight into the owning CTAs' buffers (one barrier each).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -60,6 +62,13 @@ struct FusedCfg {
   static constexpr int RT = R / G;
   static constexpr int NW = NT / 32;
   static constexpr int NC = N / 2 / CS;  // spectral columns owned after the transpose
+  // N = 256: the FFTs are warp-level Stockham transforms with an exchange
+  // buffer per warp (WarpFFT256), and the transposes are fused into them: the
+  // forward row transforms store their half spectra straight into the owning
+  // CTAs' column buffers, the inverse column transforms theirs straight into
+  // the owning CTAs' row buffers (remote stores, one cluster barrier each).
+  // Smaller N keep the shuffle transforms and the in-place transposes.
+  static constexpr bool STOCK = LOGN == 8 && sizeof(T) == 4;
   static constexpr int COLLEN = N + 1;   // padded column length
   static constexpr int HSTR = N / 2 + 1; // padded half-spectrum row length
   using CT = typename Cplx<T>::t;
@@ -67,17 +76,27 @@ struct FusedCfg {
   static constexpr size_t W_BYTES = (size_t)2 * HR * N * sizeof(T);
   static constexpr size_t ROW_BYTES = (size_t)R * HSTR * sizeof(CT);
   static constexpr size_t COL_BYTES = (size_t)NC * COLLEN * sizeof(CT);
-  static constexpr size_t SCR_BYTES = align16(cmax(ROW_BYTES, COL_BYTES));
+  static constexpr size_t PR_BYTES = (size_t)R * 2 * HSTR * sizeof(T);
+  // fused transposes (N = 256): the buffers a warp's remote stores fill are
+  // laid out so that the 32 lanes of one store write contiguous bytes --
+  // half spectra by spectral column, hsT[kx][RSTR] (the two rows of one
+  // inverse row transform are adjacent: one 16-byte load), and columns by
+  // row, colT[ky][NCP]; the pressure rows reuse the column buffer
+  static constexpr int RSTR = R + 2;
+  static constexpr int NCP = NC + 1;
+  static constexpr size_t HST_BYTES = (size_t)(N / 2) * RSTR * sizeof(CT);
+  static constexpr size_t COLT_BYTES = cmax((size_t)N * NCP * sizeof(CT), PR_BYTES);
+  // rows and columns share one buffer for the in-place transposes
+  static constexpr size_t SCR_BYTES =
+      STOCK ? align16(HST_BYTES) + align16(COLT_BYTES) : align16(cmax(ROW_BYTES, COL_BYTES));
   static constexpr size_t OFF_SCR = align16(W_BYTES);
+  static constexpr size_t OFF_COL = STOCK ? OFF_SCR + align16(HST_BYTES) : OFF_SCR;
   static constexpr size_t OFF_TW = OFF_SCR + SCR_BYTES;
   static constexpr size_t OFF_SX = OFF_TW + align16((N / 2) * sizeof(CT));
   static constexpr size_t OFF_SY = OFF_SX + align16((N / 2 + 2) * sizeof(T));
   static constexpr size_t OFF_FRC = OFF_SY + align16(N * sizeof(T));
   static constexpr size_t OFF_ROW0 = OFF_FRC + align16(R * sizeof(T));  // u_n.v and acc.v of row 0
   static constexpr size_t OFF_TMEM = OFF_ROW0 + align16(2 * N * sizeof(T));
-  // N = 256: the FFTs are warp-level Stockham transforms with an exchange
-  // buffer per warp (WarpFFT256); smaller N keep the shuffle transforms
-  static constexpr bool STOCK = LOGN == 8 && sizeof(T) == 4;
   // N = 256: the tendency phase works on strips of 4 cells (register window,
   // strip_tendency); GC row groups of N/4 strips, RTC bands per CTA
   static constexpr int GC = NT / (N / 4), RTC = R / GC;
@@ -213,9 +232,12 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   extern __shared__ __align__(1024) unsigned char smem[];
   T* const wt = reinterpret_cast<T*>(smem);  // [2][HR][N]
   unsigned char* const scr = smem + Cfg::OFF_SCR;
-  CT* const hs = reinterpret_cast<CT*>(scr);   // [R][HSTR] half spectra (rows)
-  CT* const col = reinterpret_cast<CT*>(scr);  // [NC][N+1] columns
-  T* const pr = reinterpret_cast<T*>(scr);     // [R][2 HSTR] pressure rows
+  // half spectra (rows): [R][HSTR], N = 256: hsT [N/2][RSTR]
+  CT* const hs = reinterpret_cast<CT*>(scr);
+  // columns: [NC][COLLEN], N = 256: colT [N][NCP]
+  CT* const col = reinterpret_cast<CT*>(smem + Cfg::OFF_COL);
+  // pressure rows [R][2 HSTR] (over the half spectra, N = 256: over the columns)
+  T* const pr = reinterpret_cast<T*>(Cfg::STOCK ? smem + Cfg::OFF_COL : scr);
   CT* const tw = reinterpret_cast<CT*>(smem + Cfg::OFF_TW);
   T* const sx = reinterpret_cast<T*>(smem + Cfg::OFF_SX);
   T* const sy = reinterpret_cast<T*>(smem + Cfg::OFF_SY);
@@ -519,8 +541,10 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
                 A = CT{(T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y)};
                 B = CT{(T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x)};
               }
-              hs[ja * HSTR + k] = A;
-              hs[(ja + 1) * HSTR + k] = B;
+              // rows ja, ja + 1 of spectral column k, owned by CTA k / NC
+              CT* dst = remote<CS>(col, k / NC) + (row0 + ja) * Cfg::NCP + (k % NC);
+              dst[0] = A;
+              dst[Cfg::NCP] = B;
             }
             __syncwarp();
           }
@@ -570,7 +594,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
         }
         csync<CS>();
         // ---- D2: transpose rows -> columns (in place, through registers) --------
-        {
+        if constexpr (!Cfg::STOCK) {
           CT reg[Cfg::NFWD];
 #pragma unroll
           for (int k = 0; k < Cfg::NFWD; ++k) {
@@ -590,8 +614,8 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
               col[sl * Cfg::COLLEN + ky] = reg[k];
             }
           }
+          __syncthreads();
         }
-        __syncthreads();
         // ---- D3: column FFTs, spectral multiply, inverse column FFTs -----------
         if constexpr (Cfg::STOCK) {
           using F2 = WarpFFT256<T>;
@@ -600,7 +624,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             const int kx = rank * NC + sl;  // natural order; column 0 packs kx = 0 and N/2
             CT z[8];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) z[m] = col[sl * Cfg::COLLEN + lane + 32 * m];
+            for (int m = 0; m < 8; ++m) z[m] = col[(lane + 32 * m) * Cfg::NCP + sl];
             F2::forward(z, xb, tw, lane);
 #pragma unroll
             for (int i = 0; i < 8; ++i) xb[F2::pad(F2::out_index(lane, i))] = z[i];
@@ -626,7 +650,11 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             __syncwarp();
             F2::inverse(z, xb, tw, lane);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) col[sl * Cfg::COLLEN + F2::out_index(lane, i)] = z[i];
+            for (int i = 0; i < 8; ++i) {
+              // row ky of spectral column kx, owned by CTA ky / R
+              const int ky = F2::out_index(lane, i);
+              remote<CS>(hs, ky / R)[kx * Cfg::RSTR + (ky % R)] = z[i];
+            }
           }
         } else {
         for (int t0 = warp * TPW; t0 < NC; t0 += NW * TPW) {
@@ -682,7 +710,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
         }
         csync<CS>();
         // ---- D4: transpose columns -> rows (in place) ---------------------------
-        {
+        if constexpr (!Cfg::STOCK) {
           CT reg[Cfg::NBWD];
 #pragma unroll
           for (int k = 0; k < Cfg::NBWD; ++k) {
@@ -702,8 +730,8 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
               hs[rr * HSTR + s] = reg[k];
             }
           }
+          __syncthreads();
         }
-        __syncthreads();
         // ---- D5: inverse row FFTs -> pressure rows -------------------------------
         if constexpr (Cfg::STOCK) {
           using F2 = WarpFFT256<T>;
@@ -716,18 +744,15 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
               const int k = lane + 32 * m;
-              if (k < HALF) {
-                const CT A = hs[ra * HSTR + k];
-                const CT B = hs[(ra + 1) * HSTR + k];
+              const int kp = N - k;  // in (0, N/2] for k >= N/2
+              const int ks = k < HALF ? k : (kp == HALF ? 0 : kp);
+              const float4 ab = *reinterpret_cast<const float4*>(hs + ks * Cfg::RSTR + ra);
+              const CT A = CT{ab.x, ab.y}, B = CT{ab.z, ab.w};
+              if (k < HALF)
                 z[m] = (k == 0) ? CT{A.x, B.x} : CT{A.x - B.y, A.y + B.x};
-              } else {
-                const int kp = N - k;  // in (0, N/2]
-                const CT A = hs[ra * HSTR + (kp == HALF ? 0 : kp)];
-                const CT B = hs[(ra + 1) * HSTR + (kp == HALF ? 0 : kp)];
+              else
                 z[m] = (kp == HALF) ? CT{A.y, B.y} : CT{A.x + B.y, B.x - A.y};
-              }
             }
-            __syncwarp();  // the pressure rows overwrite these half-spectrum rows
             F2::inverse(z, xb, tw, lane);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {

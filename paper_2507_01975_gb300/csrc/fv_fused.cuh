@@ -316,13 +316,45 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
   tmem_wait_st();
 
+  // Halo exchange by pushes (N = 256, Navier-Stokes): at the end of every
+  // stage each CTA stores its first three rows into the previous CTA's halo
+  // rows above and its last two rows into the next CTA's halo rows below, then
+  // arrives on the cluster barrier; the next stage starts with the matching
+  // wait. No CTA reads another's state rows, so phase C updates its rows in
+  // place without waiting for the neighbours. The pushes land after the
+  // neighbours' last reads of those halo rows (phases C and D1 of the same
+  // stage, behind two cluster barriers since).
+  const bool fused = Cfg::STOCK && ns;
+  auto push_halos = [&]() {
+    T* wp = remote<CS>(wt, prev);
+    T* wn = remote<CS>(wt, next);
+    constexpr int Q = N / 4;  // float4 per row
+    for (int e = tid; e < 10 * Q; e += NT) {
+      const int c = e / (5 * Q), rem = e % (5 * Q);
+      const int h = rem / Q, i = 4 * (rem % Q);
+      if (h < 3) {  // rows 2 + h -> the previous CTA's rows R + 2 + h
+        *reinterpret_cast<float4*>(wp + (c * HR + R + 2 + h) * N + i) =
+            *reinterpret_cast<const float4*>(wt + (c * HR + 2 + h) * N + i);
+      } else {  // rows R + h - 3 -> the next CTA's rows h - 3
+        *reinterpret_cast<float4*>(wn + (c * HR + h - 3) * N + i) =
+            *reinterpret_cast<const float4*>(wt + (c * HR + R + h - 3) * N + i);
+      }
+    }
+  };
+  if (fused) {
+    push_halos();
+    cluster_arrive<CS>();
+  }
+
   int snap = 0;
   for (int step = 1; step <= a.n_steps; ++step) {
 #pragma unroll 1
     for (int stage = 0; stage < 4; ++stage) {
       // ---- A: halo rows -----------------------------------------------------
-      csync<CS>();
-      {
+      if (fused) {
+        cluster_wait<CS>();  // the neighbours' pushes of the previous stage landed
+      } else {
+        csync<CS>();
         const T* wp = remote<CS>(wt, prev);
         const T* wn = remote<CS>(wt, next);
         for (int e = tid; e < 10 * N; e += NT) {
@@ -334,11 +366,11 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             wt[(c * HR + R + h) * N + i] = wn[(c * HR + h) * N + i];
           }
         }
+        // the neighbours read this CTA's rows above; phase C overwrites them in
+        // place, so its first write waits until every CTA of the cluster has
+        // arrived here (split barrier: the wait falls after two bands of work)
+        cluster_arrive<CS>();
       }
-      // the neighbours read this CTA's rows above; phase C overwrites them in
-      // place, so its first write waits until every CTA of the cluster has
-      // arrived here (split barrier: the wait falls after two bands of work)
-      cluster_arrive<CS>();
       __syncthreads();
 
       // ---- C: tendency and RK4 combination -------------------------------------
@@ -421,7 +453,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             }
           }
           __syncthreads();
-          if (r == 1) cluster_wait<CS>();
+          if (r == 1 && !fused) cluster_wait<CS>();
           if (r > 0) {
             const int hp = (r - 1) * GC + gc + 2;
             *reinterpret_cast<float4*>(wt + hp * N + sx4) = make_float4(pu[0], pu[1], pu[2], pu[3]);
@@ -434,7 +466,9 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
           }
         }
         tmem_wait_st();
-        if constexpr (RTC == 1) cluster_wait<CS>();
+        if constexpr (RTC == 1) {
+          if (!fused) cluster_wait<CS>();
+        }
         __syncthreads();
         const int hl = (RTC - 1) * GC + gc + 2;
         *reinterpret_cast<float4*>(wt + hl * N + sx4) = make_float4(pu[0], pu[1], pu[2], pu[3]);
@@ -810,13 +844,27 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
             wt[(HR + hr) * N + ci] -= (pc - ps) * idy;
           }
         }
+        if (fused) {
+          // u_n of the next step (and the row the previous CTA reads remotely)
+          // before the arrive that lets the neighbours into the next stage
+          if (stage == 3) {
+            store_un();
+            if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
+            tmem_wait_st();
+          }
+          __syncthreads();
+          push_halos();
+          cluster_arrive<CS>();
+        }
       }
     }
 
     // ---- end of the time step: u_{n+1} becomes u_n -------------------------------
-    store_un();
-    if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
-    tmem_wait_st();
+    if (!fused) {
+      store_un();
+      if (grp == 0) unrow0[ci] = wt[(HR + 2) * N + ci];
+      tmem_wait_st();
+    }
     if (a.save_every > 0 && a.traj != nullptr && (step % a.save_every) == 0) {
       const size_t tb = a.traj_batch > 0 ? (size_t)a.traj_batch : (size_t)gridDim.y;
       T* out = reinterpret_cast<T*>(a.traj) + ((size_t)snap * tb + traj) * 2 * NN;
@@ -840,6 +888,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   }
   // keep every CTA of the cluster resident until all DSMEM reads are done,
   // then release the tensor memory
+  if (fused) cluster_wait<CS>();  // the last stage's arrive
   tmem_fence_before_sync();
   csync<CS>();
   tmem_fence_after_sync();

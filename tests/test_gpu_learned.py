@@ -63,6 +63,7 @@ def test_network_forward_matches_oracle_bf16(n):
     coef = torch.empty((3, O.N_COEF, n, n), dtype=torch.float32, device="cuda")
     s.network_forward(u, coef)
     torch.cuda.synchronize()
+    assert s.check_finite(u)  # raises on a timed-out device wait (FD_ETIMEOUT)
     g = coef.double().cpu().numpy()
     for b in range(3):
         ref = O.cnn_forward(U0[b].astype(np.float32).astype(np.float64), model.stencil)
@@ -78,6 +79,7 @@ def test_learned_step_matches_oracle():
     out = torch.empty_like(u)
     s.step(u, out)
     torch.cuda.synchronize()
+    assert s.check_finite(out)  # raises on a timed-out device wait (FD_ETIMEOUT)
     g = out.double().cpu().numpy()
     p = oracle_problem(s)
     ref = np.stack([O.learned_step(U0[k], p, model) for k in range(b)])

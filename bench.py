@@ -667,8 +667,10 @@ def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
     """Mixed batch (512 trajectories): plain FP32 32^2 Burgers, 64^2 decaying, 128^2
     Kolmogorov, 256^2 shear (64 each) and learned BF16-network 32^2 Kolmogorov and 64^2
     decaying (128 each), every group advanced by the same physical time T with the
-    CFL-matched step dt(N) = 1.75e-3 * 256 / N, all in one graph (fd_batch). Reported:
-    cell-updates/s of the graph, and the same rollouts run one after another."""
+    CFL-matched step dt(N) = 1.75e-3 * 256 / N, all in one graph (fd_batch: the plain
+    32^2 and 64^2 trajectories in one persistent launch, the other groups as branches).
+    Reported: cell-updates/s of the graph, the graph without the persistent launch, and
+    the same rollouts run one after another."""
     import torch
 
     st = I.random_conv_stack(12, 2, 64, 160, last_scale=0.05)
@@ -706,6 +708,9 @@ def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
         return e0.elapsed_time(e1) / reps
 
     ms = timed_batch(batch)
+    persistent = batch.persistent_count()
+    batch.set_persistent(False)  # every context its own branch of the graph
+    ms_branches = timed_batch(batch)
     batch.close()
     # the same batch after each context's autotuner picked its plan (timed alone)
     plans = []
@@ -728,6 +733,7 @@ def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
                         "(64 each) + learned 32^2 Kolmogorov, 64^2 decaying (128 each), physical time 0.5 each",
             "value": cells / (min(ms, ms_tuned) * 1e-3), "unit": "cell-updates/s",
             "ms_per_batch_default_plans": ms, "ms_per_batch_autotuned_plans": ms_tuned,
+            "persistent_trajectories": persistent, "ms_per_batch_without_persistent_launch": ms_branches,
             "autotuned_plans": [{k: p[k] for k in ("path", "cluster", "n_onchip", "n_stream")} for p in plans],
             "ms_one_after_another": ms_seq, "graph_kernel_launches_autotuned": tuned_launches,
             "finite": all(bool(s.check_finite(out)) for s, _, out, _ in runs)}

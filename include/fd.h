@@ -438,8 +438,14 @@ fd_status fd_autotune(fd_ctx* ctx, int32_t probe_steps, fd_plan* report, int32_t
  * Many concurrent trajectories of uneven grid sizes and flow types, learned
  * and plain: one context per (grid, flow, dtype, learned) group, each with its
  * own device states; a batch runs every member's rollout as one CUDA graph
- * with a parallel branch per member (captured by the first fd_batch_run after
- * the last fd_batch_add, replayed by a single graph launch afterwards). The
+ * (captured by the first fd_batch_run after the last fd_batch_add, replayed by
+ * a single graph launch afterwards). The trajectories of every plain FP32
+ * member with N = 16, 32 or 64 whose plan keeps the whole batch on chip run
+ * in ONE persistent launch: a work list of (context, trajectory) items, larger
+ * grids first, that the launch's CTAs take items from until it is exhausted
+ * (per derivative order one launch); each item's result is bit-identical to
+ * its context's own on-chip rollout. Every other member is a parallel branch
+ * of the graph running its own rollout. The
  * paper has no counterpart (it advances one trajectory at a time); this is the
  * serving form of fd_rollout. A context may appear once per batch and must not
  * be used by other calls while its batch runs; the state pointers are fixed at
@@ -454,6 +460,13 @@ fd_status fd_batch_add(fd_batch* batch, fd_ctx* ctx, const void* u0, void* u_fin
 fd_status fd_batch_run(fd_batch* batch, void* stream);
 /* kernel launches inside one fd_batch_run (the graph's kernel nodes) */
 int32_t fd_batch_launch_count(const fd_batch* batch);
+/* Turn the persistent launch on (default) or off (every member its own
+ * branch); takes effect at the next fd_batch_run (which captures again).
+ * Errors: FD_EINVAL for a null batch. */
+fd_status fd_batch_set_persistent(fd_batch* batch, int32_t enable);
+/* trajectories that the graph of the last fd_batch_run runs in the persistent
+ * launch */
+int32_t fd_batch_persistent_count(const fd_batch* batch);
 const char* fd_batch_last_error(const fd_batch* batch);
 fd_status fd_batch_destroy(fd_batch* batch);
 

@@ -252,3 +252,10 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // shared helpers of the ABI translation units
 fd_status fd_set_error(fd_ctx* c, fd_status s, const char* fmt, ...);
 size_t fd_state_bytes(const fd_grid& g);
+
+// persistent mixed-batch rollout (fd_mixed.cu)
+bool fd_mixed_eligible(const fd_ctx* c);
+void fd_mixed_items(const fd_ctx* c, const void* u0, void* u_final, int n_steps, std::vector<ldfv::MixedItem>& out);
+void fd_mixed_order(std::vector<ldfv::MixedItem>& items);
+cudaError_t fd_mixed_prepare(int dord);
+cudaError_t fd_mixed_launch(const ldfv::MixedItem* d_items, int n, unsigned* d_counter, int dord, cudaStream_t st);

@@ -218,9 +218,13 @@ struct Tendency {
   }
 };
 
+// The rollout of trajectory `traj` of a.u_in by the calling CTA (its cluster's
+// share of the rows), with this CTA's tensor memory at tmem_base (TMEM_COLS
+// columns allocated by the caller). Every thread of the CTA calls it; it starts
+// by overwriting the whole shared-memory layout and ends with a cluster-wide
+// barrier, so consecutive calls need no synchronisation between them.
 template <typename T, int LOGN, int CS, int NT, int DORD>
-__global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
-    fv_rollout_kernel(const FvArgs a) {
+__device__ __forceinline__ void fv_rollout_body(const FvArgs& a, int traj, uint32_t tmem_base) {
   using Cfg = FusedCfg<T, LOGN, CS, NT>;
   using CT = typename Cfg::CT;
   using FFT = typename Cfg::FFT;
@@ -244,7 +248,6 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   T* const frc = reinterpret_cast<T*>(smem + Cfg::OFF_FRC);
   T* const unrow0 = reinterpret_cast<T*>(smem + Cfg::OFF_ROW0);  // u_n.v on local row 0
   T* const accrow0 = unrow0 + N;                                // acc.v on local row 0 (stage 2)
-  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::OFF_TMEM);
   CT* const xbuf = reinterpret_cast<CT*>(smem + Cfg::OFF_XB);  // [NW][288] (N = 256 only)
 
   const int tid = threadIdx.x;
@@ -253,11 +256,9 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   int rank = 0;
   if constexpr (CS > 1) rank = (int)cg::this_cluster().block_rank();
   const int prev = (rank + CS - 1) % CS, next = (rank + 1) % CS;
-  const int traj = blockIdx.y;
   const int row0 = rank * R;
   const size_t NN = (size_t)N * N;
 
-  if (warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
   for (int k = tid; k < HALF; k += NT) tw[k] = reinterpret_cast<const CT*>(a.tw)[k];
   for (int k = tid; k <= HALF; k += NT) sx[k] = reinterpret_cast<const T*>(a.symx)[k];
   for (int k = tid; k < N; k += NT) sy[k] = reinterpret_cast<const T*>(a.symy)[k];
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
   __syncthreads();
   tmem_fence_after_sync();
   // this thread's TMEM slots: lane quarter of the warp, column range of the warp
-  const uint32_t tbase = *tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * Cfg::TCOLS_THREAD);
+  const uint32_t tbase = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * Cfg::TCOLS_THREAD);
 
   const int ci = tid % N;
   const int grp = tid / N;
@@ -886,13 +887,82 @@ __global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
     uout[gi] = wt[hr * N + ci];
     uout[NN + gi] = wt[(HR + hr) * N + ci];
   }
-  // keep every CTA of the cluster resident until all DSMEM reads are done,
-  // then release the tensor memory
+  // keep every CTA of the cluster resident until all DSMEM reads are done
+  // (and, for the caller, every thread done with shared and tensor memory)
   if (fused) cluster_wait<CS>();  // the last stage's arrive
   tmem_fence_before_sync();
   csync<CS>();
   tmem_fence_after_sync();
-  if (warp == 0) tmem_dealloc(*tmem_slot, Cfg::TMEM_COLS);
+}
+
+template <typename T, int LOGN, int CS, int NT, int DORD>
+__global__ void __launch_bounds__(NT, (FusedCfg<T, LOGN, CS, NT>::MIN_BLOCKS))
+    fv_rollout_kernel(const FvArgs a) {
+  using Cfg = FusedCfg<T, LOGN, CS, NT>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::OFF_TMEM);
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem_base = *tmem_slot;
+  fv_rollout_body<T, LOGN, CS, NT, DORD>(a, (int)blockIdx.y, tmem_base);
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent rollout of a mixed batch: trajectories of different grid sizes
+// (N = 16, 32, 64) and flow types, one CTA each, taken from a work list by the
+// CTAs of one launch through an atomic counter until the list is exhausted
+// (larger trajectories first, so the tail is short). Every trajectory runs the
+// single-CTA configuration of the on-chip rollout at 256 threads, so its result
+// is bit-identical to that of its own context's on-chip rollout.
+// ---------------------------------------------------------------------------
+struct MixedItem {
+  FvArgs a;   // the trajectory's context arguments (u_in / u_out: its batch arrays)
+  int traj;   // trajectory index in a.u_in / a.u_out
+  int logn;   // 4, 5 or 6
+};
+
+constexpr int kMixedNT = 256;
+constexpr int kMixedTmemCols = 128;  // the largest per-CTA need of N = 16 .. 64 at 256 threads
+template <typename T>
+constexpr size_t mixed_smem() {
+  return cmax(FusedCfg<T, 4, 1, kMixedNT>::SMEM, cmax(FusedCfg<T, 5, 1, kMixedNT>::SMEM, FusedCfg<T, 6, 1, kMixedNT>::SMEM));
+}
+static_assert(FusedCfg<float, 6, 1, kMixedNT>::TMEM_COLS <= kMixedTmemCols &&
+                  FusedCfg<float, 5, 1, kMixedNT>::TMEM_COLS <= kMixedTmemCols &&
+                  FusedCfg<float, 4, 1, kMixedNT>::TMEM_COLS <= kMixedTmemCols,
+              "tensor memory of the mixed rollout");
+
+template <int DORD>
+__global__ void __launch_bounds__(kMixedNT, 2)
+    fv_mixed_rollout_kernel(const MixedItem* __restrict__ items, int n_items, unsigned* counter) {
+  __shared__ uint32_t tslot;
+  __shared__ int cur;
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&tslot, kMixedTmemCols);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem_base = tslot;
+  for (;;) {
+    if (threadIdx.x == 0) cur = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int i = cur;
+    __syncthreads();  // every thread has read cur before thread 0 takes the next item
+    if (i >= n_items) break;
+    const FvArgs a = items[i].a;
+    const int traj = items[i].traj;
+    switch (items[i].logn) {
+      case 4: fv_rollout_body<float, 4, 1, kMixedNT, DORD>(a, traj, tmem_base); break;
+      case 5: fv_rollout_body<float, 5, 1, kMixedNT, DORD>(a, traj, tmem_base); break;
+      default: fv_rollout_body<float, 6, 1, kMixedNT, DORD>(a, traj, tmem_base); break;
+    }
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem_base, kMixedTmemCols);
 }
 
 }  // namespace ldfv

@@ -51,6 +51,8 @@ EXPORTS = [
     "fd_batch_add",
     "fd_batch_run",
     "fd_batch_launch_count",
+    "fd_batch_set_persistent",
+    "fd_batch_persistent_count",
     "fd_batch_last_error",
     "fd_batch_destroy",
     "fd_destroy",
@@ -184,6 +186,10 @@ def load(path: str = LIB_PATH):
     lib.fd_batch_run.restype = C.c_int
     lib.fd_batch_launch_count.argtypes = [vp]
     lib.fd_batch_launch_count.restype = i32
+    lib.fd_batch_set_persistent.argtypes = [vp, i32]
+    lib.fd_batch_set_persistent.restype = C.c_int
+    lib.fd_batch_persistent_count.argtypes = [vp]
+    lib.fd_batch_persistent_count.restype = i32
     lib.fd_batch_last_error.argtypes = [vp]
     lib.fd_batch_last_error.restype = C.c_char_p
     lib.fd_batch_destroy.argtypes = [vp]
@@ -403,7 +409,8 @@ class Solver:
 
 class Batch:
     """fd_batch: rollouts of several solvers (mixed sizes, flows, learned and
-    plain) replayed as one CUDA graph with a parallel branch per solver."""
+    plain) replayed as one CUDA graph; the plain FP32 trajectories of N <= 64
+    run in one persistent launch, every other solver is a parallel branch."""
 
     def __init__(self):
         self.lib = load()
@@ -425,6 +432,12 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(self.lib.fd_batch_launch_count(self.h))
+
+    def set_persistent(self, enable: bool):
+        _check_free(self.lib, self.lib.fd_batch_set_persistent(self.h, 1 if enable else 0))
+
+    def persistent_count(self) -> int:
+        return int(self.lib.fd_batch_persistent_count(self.h))
 
     def close(self):
         if getattr(self, "h", None):

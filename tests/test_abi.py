@@ -113,6 +113,9 @@ def test_calls_on_null_context_are_rejected(lib):
     assert lib.fd_check_finite(None, None, None) == fd.FD_EINVAL
     assert lib.fd_destroy(None) == fd.FD_OK
     assert lib.fd_last_launch_count(None) == 0
+    assert lib.fd_batch_set_persistent(None, 1) == fd.FD_EINVAL
+    assert lib.fd_batch_persistent_count(None) == 0
+    assert lib.fd_batch_run(None, None) == fd.FD_EINVAL
 
 
 def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):

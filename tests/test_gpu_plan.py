@@ -254,3 +254,42 @@ def test_batch_recaptures_after_a_member_plan_change():
     bt.close()
     s.close()
     other.close()
+
+
+def test_persistent_launch_runs_the_small_plain_trajectories_bit_identically():
+    # the plain FP32 members with N <= 64 (mixed sizes, flows, forcing, derivative
+    # orders) go into one persistent launch per derivative order; the 128^2
+    # member stays a branch of the graph. Every output equals the member's own
+    # rollout bit for bit, with the persistent launch on and off, on replay too.
+    specs = [
+        (fd.Config(n=16, batch=3, dtype="f32", flow="burgers", nu=1e-2, dt=4e-3), "burgers", 9),
+        (fd.Config(n=32, batch=5, dtype="f32", nu=1e-3, dt=4e-3), "decaying", 7),
+        (fd.Config(n=64, batch=2, dtype="f32", nu=1e-3, dt=2e-3, forcing="kolmogorov"), "kolmogorov", 5),
+        (fd.Config(n=64, batch=3, dtype="f32", nu=1e-3, dt=2e-3, deriv_order=2), "decaying", 6),
+        (fd.Config(n=32, batch=2, dtype="f32", flow="burgers", nu=1e-2, dt=2e-3, deriv_order=2), "burgers", 8),
+        (fd.Config(n=128, batch=2, dtype="f32", nu=1e-3, dt=1e-3), "decaying", 3),
+    ]
+    bt = fd.Batch()
+    runs = []
+    for cfg, kind, steps in specs:
+        s = fd.Solver(cfg)
+        u0 = torch.tensor(I.ic_batch(kind, cfg.n, cfg.batch, seed0=77).astype(np.float32), device="cuda")
+        ref = torch.empty_like(u0)
+        s.rollout(u0, ref, steps)
+        out = torch.full_like(u0, float("nan"))
+        bt.add(s, u0, out, steps)
+        runs.append((s, out, ref))
+    torch.cuda.synchronize()
+    for persistent in (True, False, True):
+        bt.set_persistent(persistent)
+        for _ in range(2):
+            for _, out, _ in runs:
+                out.fill_(float("nan"))
+            bt.run()
+            torch.cuda.synchronize()
+            for s, out, ref in runs:
+                assert torch.equal(out, ref), (s.cfg.n, s.cfg.flow, persistent)
+        assert bt.persistent_count() == (3 + 5 + 2 + 3 + 2 if persistent else 0)
+    bt.close()
+    for s, _, _ in runs:
+        s.close()

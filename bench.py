@@ -768,12 +768,15 @@ def speed_measurement(fd, I, reps: int = 3):
     paper reports (Table 4, on an A100), on its grids. DNS rows run the plain solver:
     Burgers 100^2 on [0, 1]^2 with dt = 1e-3 (Table S2) on the generic-grid path;
     decaying and forced Navier-Stokes 1024^2 with dt = 2.19e-4 (the fine step of
-    Table S2; the paper does not give the 1024^2 one) on the streaming path. Model
-    rows: the learned 64^2 solver with the paper's forced-flow learnable module
-    (stencil network, O_F of 6 layers / 32 modes / width 16, FNO temporal correction
-    of 4 layers / 32 modes / width 8, k_c = 4; random weights) at dt = 32 x 2.19e-4;
-    for Burgers the plain 25^2 solver at dt = 1e-2 (the learned module is built for
-    32^2 and 64^2 grids only). Shear flow is left out: no learned module for its 128 x 64 grid."""
+    Table S2; the paper does not give the 1024^2 one) on the streaming path; the
+    shear layer 1024 x 512 on [0, 8] x [0, 4] with dt = 3.125e-4 on the generic-grid
+    path. Model rows (random weights): the learned 64^2 solver with the paper's
+    forced-flow learnable module (stencil network, O_F of 6 layers / 32 modes / width
+    16, FNO temporal correction of 4 layers / 32 modes / width 8, k_c = 4) at
+    dt = 32 x 2.19e-4 on the tensor-core path; Burgers 25^2 at dt = 1e-2 and the
+    shear layer 128 x 64 at dt = 1e-2 with the stencil network and a CNN temporal
+    correction (k_c = 4) on the generic-grid path, whose learned module has no
+    Fourier operators. The plain 25^2 Burgers solver is reported beside its model."""
     import torch
 
     stream = torch.cuda.current_stream()
@@ -796,16 +799,22 @@ def speed_measurement(fd, I, reps: int = 3):
         s.close()
         return {"seconds": best, "steps": steps, "finite": finite}
 
-    paper = {"burgers": (2.3067, 0.9800), "decaying": (29.2402, 2.3773), "forced": (32.8061, 3.8036)}
+    paper = {"burgers": (2.3067, 0.9800), "decaying": (29.2402, 2.3773), "forced": (32.8061, 3.8036),
+             "shear": (29.1428, 2.7857)}
     rows = {}
+    st = I.random_conv_stack(1, 2, 64, 160, last_scale=0.05)
+    dt_f, kc = 2.19e-4, 4
+    tcc = I.random_conv_stack(6, 2 * kc, 64, 2, last_scale=0.02)
     dns = fd.Solver(fd.Config(n=100, batch=1, dtype="f32", flow="burgers", nu=0.002, dt=1e-3, lx=1.0, ly=1.0))
     coarse = fd.Solver(fd.Config(n=25, batch=1, dtype="f32", flow="burgers", nu=0.002, dt=1e-2, lx=1.0, ly=1.0))
+    lrn25 = fd.Solver(fd.Config(n=25, batch=1, dtype="f32", flow="burgers", nu=0.002, dt=1e-2, lx=1.0, ly=1.0,
+                                learned=True, k_c=kc))
+    lrn25.set_params(I.pack_params(I.random_wl(3, 1e-2), st, tcc))
+    b25 = I.burgers_ic(25, 1, lx=1.0)[None].astype(np.float32)
     rows["burgers"] = {"dns_100x100": per_physical_second(dns, I.burgers_ic(100, 1, lx=1.0)[None].astype(np.float32),
                                                           1e-3),
-                       "plain_25x25": per_physical_second(coarse, I.burgers_ic(25, 1, lx=1.0)[None]
-                                                          .astype(np.float32), 1e-2)}
-    dt_f, kc = 2.19e-4, 4
-    st = I.random_conv_stack(1, 2, 64, 160, last_scale=0.05)
+                       "plain_25x25": per_physical_second(coarse, b25, 1e-2),
+                       "learned_25x25": per_physical_second(lrn25, b25, 1e-2)}
     fno = I.random_fno(4, 16, 32, 6, out_scale=0.01)
     tcf = I.random_fno(5, 8, 32, 4, out_scale=0.01, cin=2 * kc, cout=2)
     for flow, forcing, ic in (("decaying", None, I.decaying_ic), ("forced", "kolmogorov", I.kolmogorov_ic)):
@@ -816,6 +825,14 @@ def speed_measurement(fd, I, reps: int = 3):
         lrn.set_params(I.pack_params(I.random_wl(3, 1e-2), st, tcf, fno))
         rows[flow] = {"dns_1024x1024": per_physical_second(dns, ic(1024, 0)[None].astype(np.float32), dt_f),
                       "learned_64x64": per_physical_second(lrn, ic(64, 0)[None].astype(np.float32), 32 * dt_f)}
+    dns = fd.Solver(fd.Config(n=1024, ny=512, batch=1, dtype="f32", nu=1e-3, dt=3.125e-4, lx=8.0, ly=4.0))
+    lrn = fd.Solver(fd.Config(n=128, ny=64, batch=1, dtype="f32", nu=1e-3, dt=1e-2, lx=8.0, ly=4.0, learned=True,
+                              k_c=kc))
+    lrn.set_params(I.pack_params(I.random_wl(3, 1e-2), st, tcc))
+    rows["shear"] = {"dns_1024x512": per_physical_second(dns, I.shear_scalar_ic(1024, 512)[0][None].astype(np.float32),
+                                                         3.125e-4),
+                     "learned_128x64": per_physical_second(lrn, I.shear_scalar_ic(128, 64)[0][None].astype(np.float32),
+                                                           1e-2)}
     for k, (p_dns, p_model) in paper.items():
         rows[k]["paper_a100"] = {"dns": p_dns, "ldsolver": p_model}
     return {"unit": "GPU seconds per simulated physical second, batch 1 (min of %d runs)" % reps, **rows}

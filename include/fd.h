@@ -219,7 +219,18 @@ int32_t fd_last_launch_count(const fd_ctx* ctx);
  * learned part. With k_c > 0 the temporal correction (Sec. 3.2, Eq. for u_k;
  * Sec. 3.5) u_k <- P(u_k + TC(u_{k-k_c} .. u_{k-1}) - mean) is applied after
  * every k_c-th step of a rollout, with TC a network of the same shape
- * (2 k_c -> 64 x5 -> 2). The learned path is built for FP32, N in {32, 64}.
+ * (2 k_c -> 64 x5 -> 2). The learned module is built for FP32 and runs on two
+ * paths. Square 32^2 and 64^2 grids run it on the tensor cores (BF16
+ * activations), with everything below: the frequency-domain operator, the FNO
+ * temporal correction, the ablation variants, the reverse mode and training.
+ * Every other grid runs it on the generic-grid path (path 3, also selectable for
+ * 32^2 and 64^2): Burgers on any nx x ny in [4, 8192]^2 (the 25^2 and 100^2
+ * presets of App. C.1), Navier-Stokes on power-of-two nx x ny in [32, 2048]^2
+ * (rectangular, e.g. the 128 x 64 shear grid, or square beyond 64^2). There the
+ * network runs on the CUDA cores with FP32 activations; the stencil network, W_L,
+ * the CNN temporal correction and ablation 1 are built, the Fourier operators are
+ * not (FD_EUNSUPPORTED at fd_init), and the calls of the reverse mode and
+ * training return FD_EUNSUPPORTED.
  *
  * Parameter layout (float32, fd_param_count values):
  *   W_L[kind 2][axis 2][5][4]                      (kind 0 interp, 1 deriv;

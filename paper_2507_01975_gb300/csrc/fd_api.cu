@@ -162,7 +162,13 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   // Burgers on a non-power-of-two or rectangular grid, Navier-Stokes on a
   // rectangular power-of-two grid (or either with path 3) run on the
   // generic-grid kernels; every other grid must be a square power of two
-  const bool generic = fd_generic_wanted(g, opts ? opts->path : 0);
+  // learned contexts run on the tensor-core path on square 32^2 and 64^2 grids
+  // (unless path 3 asks for the generic-grid path) and on the generic-grid path
+  // everywhere else
+  const bool learned_req = opts && opts->learned == 1;
+  const bool tc_grid = g.nx == g.ny && (g.nx == 32 || g.nx == 64);
+  const bool generic = fd_generic_wanted(g, opts ? opts->path : 0) ||
+                       (learned_req && (!tc_grid || (opts && opts->path == 3)) && g.nx > 0 && g.ny > 0);
   if (generic && (g.nx < 4 || g.ny < 4 || g.nx > 8192 || g.ny > 8192))
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: nx, ny must be in [4, 8192] (got %d x %d)", g.nx, g.ny);
   if (generic && g.flow == FD_NAVIER_STOKES &&
@@ -200,8 +206,10 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_EUNSUPPORTED,
                         "fd_init: the generic-grid path (3) takes Burgers on any grid and Navier-Stokes on "
                         "power-of-two grids");
-  if (generic && o.learned)
-    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: the learned path runs on square power-of-two grids");
+  if (generic && o.learned) {
+    const fd_status ls = fd_glearned_check(g, o);
+    if (ls != FD_OK) return ls;
+  }
   if (generic && o.path != 0 && o.path != 3)
     return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: this grid runs on the generic-grid path (path 3) only");
   if (generic) {
@@ -214,8 +222,10 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     c->nu = nu;
     c->dt = dt;
     std::memset(&c->base, 0, sizeof c->base);
-    const fd_status gs = fd_generic_init(c);
+    fd_status gs = fd_generic_init(c);
+    if (gs == FD_OK && o.learned) gs = fd_glearned_init(c);
     if (gs != FD_OK) {
+      fd_glearned_free(c);
       fd_generic_free(c);
       delete c;
       return gs;
@@ -463,6 +473,7 @@ fd_status fd_destroy(fd_ctx* c) {
   fd_adjoint_free(c);
   fd_learned_free(c);
   fd_large_free(c);
+  fd_glearned_free(c);
   fd_generic_free(c);
   delete c;
   return FD_OK;

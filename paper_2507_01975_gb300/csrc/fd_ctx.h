@@ -184,6 +184,30 @@ struct GenericState {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 };
+
+// learned module on the generic-grid path (fd_glearned.cu): FP32 parameters
+// (network weights rounded to BF16 at upload), FP32 network activations, the
+// per-face coefficients and face values of a stage, the temporal-correction
+// history ring
+struct GenericLearned {
+  int64_t nparams = 0;
+  int kc = 0;
+  int ablation = 0;
+  bool ready = false;
+  float* d_params = nullptr;        // the parameter array (fd_set_params layout)
+  size_t off_wl = 0;                // W_L[2][2][5][4]
+  size_t off_sw[6] = {}, off_sb[6] = {};  // stencil network layers
+  size_t off_tw[6] = {}, off_tb[6] = {};  // temporal-correction network layers
+  float* act0 = nullptr;            // [batch][64][ny][nx]
+  float* act1 = nullptr;
+  float* coef = nullptr;            // [batch][160][ny][nx]
+  float* inst = nullptr;            // [batch][8][ny][nx] face values
+  float* corr = nullptr;            // [batch][2][ny][nx] temporal correction
+  float* ring = nullptr;            // [kc][batch][2][ny][nx] the last kc states
+  const float** d_hist = nullptr;   // [kc] pointers to the ring slots, oldest first
+  const float** d_single = nullptr; // [4] the network's input states: u_n, the two stage buffers, a free slot
+  cudaGraphExec_t graph = nullptr;  // one group of max(k_c, 1) steps, captured by the first rollout
+};
 }  // namespace ldfv
 
 struct fd_ctx {
@@ -208,6 +232,7 @@ struct fd_ctx {
   ldfv::TrainState* trn = nullptr;
   ldfv::LargeState* big = nullptr;   // set when the streaming path runs this context
   ldfv::GenericState* gen = nullptr; // set for the generic-grid path (non-power-of-two / rectangular grids)
+  ldfv::GenericLearned* glrn = nullptr;  // learned module of a generic-grid context
   // launch plan of a plain on-chip context: on-chip configurations valid for
   // this grid ([0] = default), the one in use, and how the batch is split
   // between it and a streaming context that runs the trajectories
@@ -252,6 +277,17 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // shared helpers of the ABI translation units
 fd_status fd_set_error(fd_ctx* c, fd_status s, const char* fmt, ...);
 size_t fd_state_bytes(const fd_grid& g);
+
+// generic-grid path (fd_generic.cu) and its learned module (fd_glearned.cu)
+cudaError_t fd_generic_project(fd_ctx* c, float* w, cudaStream_t st);
+int64_t fd_learned_param_count(const fd_options& o);
+fd_status fd_glearned_check(const fd_grid& g, const fd_options& o);
+fd_status fd_glearned_init(fd_ctx* c);
+void fd_glearned_free(fd_ctx* c);
+fd_status fd_glearned_set_params(fd_ctx* c, const float* params, int64_t count, bool device, cudaStream_t st);
+fd_status fd_glearned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
+                              cudaStream_t st, bool allow_graph);
+fd_status fd_glearned_network(fd_ctx* c, const void* u, float* coef_out, cudaStream_t st);
 
 // persistent mixed-batch rollout (fd_mixed.cu)
 bool fd_mixed_eligible(const fd_ctx* c);

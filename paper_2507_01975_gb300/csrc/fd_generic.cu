@@ -515,8 +515,11 @@ void fd_generic_free(fd_ctx* c) {
   c->gen = nullptr;
 }
 
+cudaError_t fd_generic_project(fd_ctx* c, float* w, cudaStream_t st) { return generic_project(c, w, st); }
+
 fd_status fd_generic_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                              cudaStream_t st, bool allow_graph) {
+  if (c->glrn) return fd_glearned_rollout(c, u0, traj, u_final, n_steps, save_every, st, allow_graph);
   GenericState& S = *c->gen;
   const size_t bytes = fd_state_bytes(c->grid);
   cudaError_t e = cudaMemcpyAsync(S.un, u0, bytes, cudaMemcpyDeviceToDevice, st);
@@ -554,6 +557,7 @@ fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const
   c->launches = 0;
   if (!c->gen)
     return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_scalar: the passive scalar runs on the generic-grid path (path 3)");
+  if (c->glrn) return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_scalar: built for the plain solver");
   if (!u0 || !s0 || !u_final || !s_final) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: null pointer");
   if (n_steps < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: n_steps must be >= 0");
   if (!(diffusivity >= 0) || !std::isfinite(diffusivity))

@@ -50,7 +50,9 @@ fd_status fd_rollout_guarded(fd_ctx* c, const void* u0, void* u_final, int32_t n
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout_guarded: null context");
   c->launches = 0;
   if (!u0 || !u_final || !fell_back) return fd_set_error(c, FD_EINVAL, "fd_rollout_guarded: null pointer");
-  if (!c->lrn) return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_guarded: needs a learned context");
+  if (!c->lrn)
+    return fd_set_error(c, FD_EUNSUPPORTED, c->glrn ? "fd_rollout_guarded: built for the tensor-core learned path (32^2, 64^2)"
+                                                    : "fd_rollout_guarded: needs a learned context");
   if (n_steps < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout_guarded: n_steps must be >= 0");
   const int kc = c->opts.k_c;
   if (chunk <= 0) chunk = kc > 0 ? kc : 8;

@@ -459,12 +459,16 @@ void fd_learned_free(fd_ctx* c) {
 
 extern "C" {
 
-int64_t fd_param_count(const fd_ctx* c) { return (c && c->lrn) ? c->lrn->nparams : 0; }
+int64_t fd_param_count(const fd_ctx* c) {
+  return (c && c->lrn) ? c->lrn->nparams : (c && c->glrn) ? c->glrn->nparams : 0;
+}
 
 fd_status fd_set_params(fd_ctx* c, const float* params, int64_t count, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_set_params: null context");
-  if (!c->lrn) return fd_set_error(c, FD_EINVAL, "fd_set_params: context was created without the learned option");
+  if (!c->lrn && !c->glrn)
+    return fd_set_error(c, FD_EINVAL, "fd_set_params: context was created without the learned option");
   if (!params) return fd_set_error(c, FD_EINVAL, "fd_set_params: null parameter array");
+  if (c->glrn) return fd_glearned_set_params(c, params, count, false, static_cast<cudaStream_t>(stream));
   LearnedState& L = *c->lrn;
   if (count != L.nparams)
     return fd_set_error(c, FD_EINVAL, "fd_set_params: expected %lld values, got %lld", (long long)L.nparams,
@@ -480,9 +484,10 @@ fd_status fd_set_params(fd_ctx* c, const float* params, int64_t count, void* str
 
 fd_status fd_set_params_device(fd_ctx* c, const float* params, int64_t count, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_set_params_device: null context");
-  if (!c->lrn)
+  if (!c->lrn && !c->glrn)
     return fd_set_error(c, FD_EINVAL, "fd_set_params_device: context was created without the learned option");
   if (!params) return fd_set_error(c, FD_EINVAL, "fd_set_params_device: null parameter array");
+  if (c->glrn) return fd_glearned_set_params(c, params, count, true, static_cast<cudaStream_t>(stream));
   LearnedState& L = *c->lrn;
   if (count != L.nparams)
     return fd_set_error(c, FD_EINVAL, "fd_set_params_device: expected %lld values, got %lld", (long long)L.nparams,
@@ -495,6 +500,11 @@ fd_status fd_set_params_device(fd_ctx* c, const float* params, int64_t count, vo
 
 fd_status fd_network_forward(fd_ctx* c, const void* u, float* coef_out, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_network_forward: null context");
+  if (c->glrn) {
+    if (!c->glrn->ready) return fd_set_error(c, FD_EINVAL, "fd_network_forward: parameters not set");
+    if (!u) return fd_set_error(c, FD_EINVAL, "fd_network_forward: null state pointer");
+    return fd_glearned_network(c, u, coef_out, static_cast<cudaStream_t>(stream));
+  }
   if (!c->lrn || !c->lrn->ready) return fd_set_error(c, FD_EINVAL, "fd_network_forward: parameters not set");
   if (!u) return fd_set_error(c, FD_EINVAL, "fd_network_forward: null state pointer");
   LearnedState& L = *c->lrn;

@@ -226,7 +226,7 @@ class Config:
     poisson_symbol: int = 0
     learned: bool = False
     k_c: int = 0
-    path: int = 0  # 0 automatic, 1 on chip, 2 streaming through HBM, 3 generic grid (Burgers)
+    path: int = 0  # 0 automatic, 1 on chip, 2 streaming through HBM, 3 generic grid
     fno_layers: int = 0  # frequency-domain operator O_F: Fourier layers (0 = off)
     fno_modes: int = 0
     fno_width: int = 0
@@ -234,7 +234,7 @@ class Config:
     tc_fno_modes: int = 0
     tc_fno_width: int = 0
     ablation: int = 0  # 0 full flux block, 1 without the physics conv, 2 frequency operator only (Table 4)
-    ny: Optional[int] = None  # rows when the grid is rectangular (Burgers on the generic-grid path); n = columns
+    ny: Optional[int] = None  # rows when the grid is rectangular (generic-grid path); n = columns
     spin_limit: int = 0  # iteration limit of the tensor-core kernels' bounded waits (0 = library default)
 
 

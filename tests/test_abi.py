@@ -125,8 +125,11 @@ def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):
     # forcing the on-chip path beyond its sizes
     st, _ = _init(lib, n=512, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 1))
     assert st == fd.FD_EUNSUPPORTED
-    # the learned path is on chip only
-    st, _ = _init(lib, n=512, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
+    # the learned module is FP32, and its Fourier operators are built for the
+    # tensor-core grids (32^2, 64^2) only
+    st, _ = _init(lib, n=128, dtype=fd.FD_F64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
+    assert st == fd.FD_EUNSUPPORTED
+    st, _ = _init(lib, n=128, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 2, 16, 8))
     assert st == fd.FD_EUNSUPPORTED
     # Navier-Stokes on the generic-grid path is FP32 with nx, ny in [32, 2048]; an
     # unknown path value is invalid
@@ -134,7 +137,10 @@ def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):
     assert st == fd.FD_EUNSUPPORTED
     st, _ = _init(lib, n=16, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 3))
     assert st == fd.FD_EUNSUPPORTED
-    st, _ = _init(lib, n=25, flow=fd.FD_BURGERS, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
+    st, _ = _init(lib, n=25, flow=fd.FD_BURGERS, dtype=fd.FD_F64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
+    assert st == fd.FD_EUNSUPPORTED
+    # learned Navier-Stokes on the generic-grid path needs nx, ny >= 32
+    st, _ = _init(lib, n=16, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0))
     assert st == fd.FD_EUNSUPPORTED
     st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 4))
     assert st == fd.FD_EINVAL

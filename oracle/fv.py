@@ -455,18 +455,27 @@ class LearnedModel:
     #: (K = (W_L + C_theta) / h^deriv, no W_P and hence no consistency projection),
     #: 2 the frequency-domain operator only (face values = O_F(u))
     ablation: int = 0
+    #: learnable conv of the passive scalar's four operator instances
+    #: ``W_Ls[kind, axis, 5, 4]`` (shear flow, oracle.scalar). When set the model
+    #: also learns the scalar's face operators: the stencil network then takes
+    #: (u, v, s) (3 channels) and emits 240 channels, the eight velocity
+    #: instances' 160 followed by the scalar instances' 80.
+    W_Ls: Optional[np.ndarray] = None
 
 
-def learned_kernels(U: np.ndarray, p: Problem, model: LearnedModel) -> list:
+def learned_kernels(U: np.ndarray, p: Problem, model: LearnedModel, C: Optional[np.ndarray] = None) -> list:
     """Per-face kernels K_f = W_P + proj(W_L + C_theta(u)_f) (Sec. 3.4, integrated operator).
 
     Ablation 1 (without the physics-based convolution) drops W_P and with it the
     consistency projection, whose job is to keep W_P's consistency: K_f = W_L +
-    C_theta(u)_f. Ablation 2 (frequency-domain operator only) has zero kernels."""
+    C_theta(u)_f. Ablation 2 (frequency-domain operator only) has zero kernels.
+    ``C`` is the network's output when the caller has it (a model that also
+    learns the scalar runs the network on (u, v, s))."""
     ny, nx = U.shape[1:]
     if model.ablation == 2:
         return [np.zeros((5, 4, ny, nx)) for _ in INSTANCES]
-    C = cnn_forward(U, model.stencil)
+    if C is None:
+        C = cnn_forward(U, model.stencil)
     ks = []
     for q, (_fld, axis, kind, _shift) in enumerate(INSTANCES):
         h = p.dx if axis == 0 else p.dy

@@ -223,9 +223,10 @@ def random_fno(seed: int, width: int, modes: int, layers: int, scale: float = 1.
     }
 
 
-def pack_params(W_L: np.ndarray, stencil, tc=None, fno=None) -> np.ndarray:
+def pack_params(W_L: np.ndarray, stencil, tc=None, fno=None, W_Ls=None) -> np.ndarray:
     """Flat float32 parameter array in the layout fd_set_params documents:
-    W_L[2][2][5][4], then every stencil layer's W[Cout][Cin][3][3] and b[Cout],
+    W_L[2][2][5][4], (for a model that learns the scalar) W_Ls[2][2][5][4], then
+    every stencil layer's W[Cout][Cin][3][3] and b[Cout],
     then (optionally) the temporal correction: every CNN layer's weights and
     biases (``tc`` a list of (W, b)) or a Fourier neural operator (``tc`` a dict
     from random_fno), then (optionally) the frequency-domain operator. An operator
@@ -238,6 +239,8 @@ def pack_params(W_L: np.ndarray, stencil, tc=None, fno=None) -> np.ndarray:
         return out + [f["Q_w"].ravel(), f["Q_b"].ravel()]
 
     parts = [np.asarray(W_L, dtype=np.float64).ravel()]
+    if W_Ls is not None:
+        parts.append(np.asarray(W_Ls, dtype=np.float64).ravel())
     for W, b in stencil:
         parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
     if isinstance(tc, dict):

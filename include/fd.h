@@ -125,6 +125,14 @@ typedef struct {
                              projection; 2 = the frequency-domain operator only: face values O_F(u)
                              (needs fno_layers > 0; the stencil network does not run). Needs
                              learned = 1; forward only (the reverse-mode calls refuse 1 and 2) */
+  int32_t scalar_learned; /* 1 = the learnable module also learns the passive scalar's transport
+                             (shear flow, App. C.1): the scalar's four operator instances take
+                             per-face kernels W_P + proj(W_Ls + C_s) / h^deriv like the
+                             velocity's eight, the stencil network reads (u, v, s) and emits 240
+                             channels (the last 80 are C_s); the temporal correction stays on
+                             the velocity. Needs learned = 1 and ablation = 0; runs on the
+                             generic-grid path (FP32) and only through fd_rollout_scalar
+                             (fd_rollout / fd_step refuse such a context). 0 = off (default) */
 } fd_options;
 
 typedef struct fd_ctx fd_ctx; /* opaque, library-owned */
@@ -194,9 +202,14 @@ fd_status fd_rollout_guarded(fd_ctx* ctx, const void* u0, void* u_final, int32_t
  * instances) and RK4 stages taken from the same (projected) stage velocities;
  * it is not projected and does not act on the velocity. u0 / s0 are read,
  * u_final / s_final written (they may alias u0 / s0). The first call
- * allocates the scalar's device buffers. FD_EUNSUPPORTED on other paths;
- * FD_EINVAL for null pointers, n_steps < 0 or a negative or non-finite
- * diffusivity. */
+ * allocates the scalar's device buffers. On a learned context built with
+ * scalar_learned = 1 every RK stage runs the stencil network on (u, v, s):
+ * the velocity's eight instances and the scalar's four take their learned
+ * per-face kernels, and every k_c steps the temporal correction acts on the
+ * velocity (after the first call with a given diffusivity the k_c-step group
+ * is replayed as a CUDA graph). FD_EUNSUPPORTED on other paths and on a
+ * learned context without scalar_learned; FD_EINVAL for null pointers,
+ * n_steps < 0, a negative or non-finite diffusivity, or parameters not set. */
 fd_status fd_rollout_scalar(fd_ctx* ctx, double diffusivity, const void* u0, const void* s0, void* u_final,
                             void* s_final, int32_t n_steps, void* stream);
 
@@ -236,11 +249,17 @@ int32_t fd_last_launch_count(const fd_ctx* ctx);
  *   W_L[kind 2][axis 2][5][4]                      (kind 0 interp, 1 deriv;
  *                                                   axis 0 x, 1 y; derivative
  *                                                   parts are in units of 1/h)
+ *   W_Ls[kind 2][axis 2][5][4] (only with scalar_learned): the scalar's W_L
  *   stencil layer l = 0..5: W[Cout][Cin][3][3], b[Cout]
  *                   with (Cin, Cout) = (2,64) (64,64) x4 (64,160);
  *                   output channel 20 q + 4 r + c is tap (r, c) of instance q
  *                   (q: 0 u-x-interp, 1 u-x-deriv, 2 u-y-interp, 3 u-y-deriv,
- *                    4 v-x-interp, 5 v-x-deriv, 6 v-y-interp, 7 v-y-deriv)
+ *                    4 v-x-interp, 5 v-x-deriv, 6 v-y-interp, 7 v-y-deriv).
+ *                   With scalar_learned: (3,64) ... (64,240), input channel 2
+ *                   is s, and channels 160 + 20 m + 4 r + c are the scalar's
+ *                   instances m (0 s-x-interp, 1 s-x-deriv, 2 s-y-interp,
+ *                   3 s-y-deriv; their 5 x 4 taps sit at transverse offset
+ *                   r - 2 and axial offset c - 2 from the face's cell)
  *   temporal correction (only when k_c > 0): layers as above with
  *                   (Cin, Cout) = (2 k_c, 64) (64,64) x4 (64, 2); input channel
  *                   2 s + c is component c of u_{k-k_c+s}. With tc_fno_layers > 0
@@ -275,7 +294,9 @@ fd_status fd_set_params_device(fd_ctx* ctx, const float* params, int64_t count, 
 
 /* Stencil-network forward pass alone: coef_out[batch][160][ny][nx] (device,
  * float32) = C_theta(u) for the device state u. For tests and diagnostics;
- * coef_out = NULL runs the network only (its BF16 output stays internal). */
+ * coef_out = NULL runs the network only (its BF16 output stays internal).
+ * On a scalar_learned context u is [batch][3][ny][nx] (u, v, s) and coef_out
+ * [batch][240][ny][nx]. */
 fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* stream);
 
 /* ---- reverse mode ----------------------------------------------------------

@@ -163,12 +163,13 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
   // rectangular power-of-two grid (or either with path 3) run on the
   // generic-grid kernels; every other grid must be a square power of two
   // learned contexts run on the tensor-core path on square 32^2 and 64^2 grids
-  // (unless path 3 asks for the generic-grid path) and on the generic-grid path
-  // everywhere else
+  // (unless path 3 asks for the generic-grid path or the model learns the
+  // passive scalar) and on the generic-grid path everywhere else
   const bool learned_req = opts && opts->learned == 1;
   const bool tc_grid = g.nx == g.ny && (g.nx == 32 || g.nx == 64);
+  const bool scalar_req = learned_req && opts->scalar_learned != 0;
   const bool generic = fd_generic_wanted(g, opts ? opts->path : 0) ||
-                       (learned_req && (!tc_grid || (opts && opts->path == 3)) && g.nx > 0 && g.ny > 0);
+                       (learned_req && (!tc_grid || opts->path == 3 || scalar_req) && g.nx > 0 && g.ny > 0);
   if (generic && (g.nx < 4 || g.ny < 4 || g.nx > 8192 || g.ny > 8192))
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: nx, ny must be in [4, 8192] (got %d x %d)", g.nx, g.ny);
   if (generic && g.flow == FD_NAVIER_STOKES &&
@@ -186,8 +187,8 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: unknown flow");
   if (!(dt > 0) || !std::isfinite(dt)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: dt must be positive");
   if (!(nu >= 0) || !std::isfinite(nu)) return fd_set_error(nullptr, FD_EINVAL, "fd_init: nu must be >= 0");
-  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 0};
-  static_assert(sizeof(fd_options) == 64, "fd_options layout");
+  fd_options o = {4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  static_assert(sizeof(fd_options) == 72, "fd_options layout");
   if (opts) o = *opts;
   if (o.deriv_order != 2 && o.deriv_order != 4)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: deriv_order must be 2 or 4");
@@ -201,6 +202,10 @@ fd_status fd_init(const fd_grid* grid, double nu, double dt, const fd_forcing* f
     return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: rectangular grids are built for Burgers only");
   if (o.learned != 0 && o.learned != 1) return fd_set_error(nullptr, FD_EINVAL, "fd_init: learned must be 0 or 1");
   if (!o.learned && o.k_c) return fd_set_error(nullptr, FD_EINVAL, "fd_init: k_c needs the learned option");
+  if (o.scalar_learned != 0 && o.scalar_learned != 1)
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: scalar_learned must be 0 or 1");
+  if (o.scalar_learned && !o.learned)
+    return fd_set_error(nullptr, FD_EINVAL, "fd_init: scalar_learned needs the learned option");
   if (o.path < 0 || o.path > 3) return fd_set_error(nullptr, FD_EINVAL, "fd_init: path must be 0, 1, 2 or 3");
   if (o.path == 3 && !generic)
     return fd_set_error(nullptr, FD_EUNSUPPORTED,

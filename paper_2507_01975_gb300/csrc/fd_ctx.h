@@ -193,20 +193,26 @@ struct GenericLearned {
   int64_t nparams = 0;
   int kc = 0;
   int ablation = 0;
+  bool scalar = false;              // the model learns the passive scalar (network on (u, v, s))
+  int ncoef = 160;                  // network output channels: 160, 240 with the scalar
   bool ready = false;
   float* d_params = nullptr;        // the parameter array (fd_set_params layout)
   size_t off_wl = 0;                // W_L[2][2][5][4]
+  size_t off_wls = 0;               // W_Ls[2][2][5][4] (scalar models)
   size_t off_sw[6] = {}, off_sb[6] = {};  // stencil network layers
   size_t off_tw[6] = {}, off_tb[6] = {};  // temporal-correction network layers
   float* act0 = nullptr;            // [batch][64][ny][nx]
   float* act1 = nullptr;
-  float* coef = nullptr;            // [batch][160][ny][nx]
+  float* coef = nullptr;            // [batch][ncoef][ny][nx]
   float* inst = nullptr;            // [batch][8][ny][nx] face values
+  float* sinst = nullptr;           // [batch][4][ny][nx] the scalar's face values (scalar models)
   float* corr = nullptr;            // [batch][2][ny][nx] temporal correction
   float* ring = nullptr;            // [kc][batch][2][ny][nx] the last kc states
   const float** d_hist = nullptr;   // [kc] pointers to the ring slots, oldest first
   const float** d_single = nullptr; // [4] the network's input states: u_n, the two stage buffers, a free slot
+  const float** d_ssingle = nullptr; // [4] the same for the scalar (scalar models): s_n, its two stage buffers
   cudaGraphExec_t graph = nullptr;  // one group of max(k_c, 1) steps, captured by the first rollout
+  double graph_diff = -1.0;         // scalar models: the diffusivity the graph was captured with
 };
 }  // namespace ldfv
 
@@ -288,6 +294,8 @@ fd_status fd_glearned_set_params(fd_ctx* c, const float* params, int64_t count, 
 fd_status fd_glearned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                               cudaStream_t st, bool allow_graph);
 fd_status fd_glearned_network(fd_ctx* c, const void* u, float* coef_out, cudaStream_t st);
+fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, const void* s0, void* u_final,
+                                     void* s_final, int n_steps, cudaStream_t st);
 
 // persistent mixed-batch rollout (fd_mixed.cu)
 bool fd_mixed_eligible(const fd_ctx* c);

@@ -557,11 +557,12 @@ fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const
   c->launches = 0;
   if (!c->gen)
     return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_scalar: the passive scalar runs on the generic-grid path (path 3)");
-  if (c->glrn) return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_scalar: built for the plain solver");
   if (!u0 || !s0 || !u_final || !s_final) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: null pointer");
   if (n_steps < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: n_steps must be >= 0");
   if (!(diffusivity >= 0) || !std::isfinite(diffusivity))
     return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: the diffusivity must be >= 0");
+  if (c->glrn)
+    return fd_glearned_rollout_scalar(c, diffusivity, u0, s0, u_final, s_final, n_steps, static_cast<cudaStream_t>(stream));
   GenericState& S = *c->gen;
   const fd_grid& g = c->grid;
   const size_t sbytes = (size_t)g.batch * g.nx * g.ny * (g.dtype == FD_F64 ? sizeof(double) : sizeof(float));

@@ -17,6 +17,14 @@
 // Every k_c steps the temporal-correction network (2 k_c -> 64 x 5 -> 2) on the
 // last k_c states gives c, and u <- P(u + c - mean(c)) (Sec. 3.2, 3.5).
 // A rollout captures one group of max(k_c, 1) steps as a CUDA graph and replays it.
+//
+// A model that learns the passive scalar of the shear flow (App. C.1) extends
+// the flux block to the scalar's four operator instances (face value and face
+// derivative along x at the u-faces and along y at the v-faces) with per-face
+// kernels W_P + proj(W_Ls + C_s) / h^deriv of their own; the network then reads
+// (u, v, s) and emits 240 channels, the last 80 being C_s, and each stage also
+// advances s by -div(u s_f - D grad_f s) (flux form; the temporal correction
+// stays on the velocity).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -32,14 +40,17 @@ using namespace ldfv;
 namespace {
 
 constexpr int kHid = 64;
-constexpr int kNCoef = 160;
+constexpr int kNCoef = 160;        // the velocity's eight instances x 20 taps
+constexpr int kNCoefScalar = 240;  // with the scalar's four instances
 
 // out[b][o][p] = act(bias[o] + sum_{c, dy, dx} W[o][c][dy + 1][dx + 1] in[b][c][p + (dy, dx)])
 // with periodic wrap; the input is either one tensor [batch][cin][ny][nx] or
-// cin / 2 states [batch][2][ny][nx] given by pointers (the network inputs)
+// cin / 2 states [batch][2][ny][nx] given by pointers (the network inputs), the
+// last channel then optionally a scalar [batch][ny][nx] given by pointer
 struct GConvArgs {
   const float* in;
   const float* const* hist;
+  const float* const* sptr;
   const float* w;
   const float* b;
   float* out;
@@ -77,7 +88,9 @@ __global__ void __launch_bounds__(256) gconv3x3_kernel(const GConvArgs a) {
 #pragma unroll
   for (int o = 0; o < kGCO; ++o) acc[o] = o < nco ? a.b[co0 + o] : 0.f;
   for (int c = 0; c < a.cin; ++c) {
-    const float* src = a.hist ? a.hist[c >> 1] + ((size_t)b * 2 + (c & 1)) * hw : a.in + ((size_t)b * a.cin + c) * hw;
+    const float* src = !a.hist ? a.in + ((size_t)b * a.cin + c) * hw
+                       : a.sptr && c == a.cin - 1 ? a.sptr[0] + (size_t)b * hw
+                                                  : a.hist[c >> 1] + ((size_t)b * 2 + (c & 1)) * hw;
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = src[off[k]];
@@ -100,15 +113,63 @@ __global__ void __launch_bounds__(256) gconv3x3_kernel(const GConvArgs a) {
 
 // face values of the eight instances at every output location (instance q =
 // 2 pr + kind, pr = (field, axis)); 20 taps on the 5 x 4 grid: transverse
-// offset r - 2, axial offset c + sh (sh = -1 or -2 by where the output sits)
+// offset r - 2, axial offset c + sh (sh = -1 or -2 by where the output sits).
+// Scalar models add the scalar's four instances m = 2 axis + kind (sh = -2).
 struct GFaceArgs {
   const float* w;     // stage state [batch][2][ny][nx]
-  const float* coef;  // network output [batch][160][ny][nx]
+  const float* coef;  // network output [batch][ncoef][ny][nx]
   const float* wl;    // W_L[kind 2][axis 2][5][4]
   float* inst;        // [batch][8][ny][nx]
-  int nx, ny, dord, ablation;
+  const float* s;     // stage scalar [batch][ny][nx], or null
+  const float* wls;   // W_Ls[kind 2][axis 2][5][4]
+  float* sinst;       // [batch][4][ny][nx]
+  int nx, ny, dord, ablation, ncoef;
   float idx, idy;
 };
+
+// one face value: the learned part L (20 taps) through the consistency
+// projection onto the kernels that leave W_P's order conditions intact, scaled
+// by 1/h for a derivative, plus W_P (Sec. 3.4), applied to the 20 taps;
+// ablation 1 takes L alone, without W_P or the projection
+__device__ __forceinline__ float face_value(const float (&L)[20], const float (&tap)[20], int kind, float h, int dord,
+                                            int ablation) {
+  const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
+  float s1 = 0.f, sc = 0.f, sr = 0.f;
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const float v = L[r * 4 + cc];
+      s1 += v;
+      sc += v * cval[cc];
+      sr += v * (float)(r - 2);
+    }
+  const float pk = ablation == 0 ? 1.0f : 0.0f;
+  s1 *= pk * (1.0f / 20.0f);
+  sc *= pk * (1.0f / 25.0f);
+  sr *= pk * (1.0f / 40.0f);
+  const float scale = kind == 1 ? 1.0f / h : 1.0f;
+  float val = 0.f;
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
+      if (r == 2 && ablation == 0) {
+        if (kind == 0) {
+          k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
+        } else if (dord == 4) {
+          const float d4[4] = {1.f / 24.f, -27.f / 24.f, 27.f / 24.f, -1.f / 24.f};
+          k += d4[cc] / h;
+        } else {
+          const float d2[4] = {0.f, -1.f, 1.f, 0.f};
+          k += d2[cc] / h;
+        }
+      }
+      val += k * tap[r * 4 + cc];
+    }
+  return val;
+}
 
 __global__ void __launch_bounds__(256) gface_kernel(const GFaceArgs a) {
   const int hw = a.nx * a.ny;
@@ -117,7 +178,7 @@ __global__ void __launch_bounds__(256) gface_kernel(const GFaceArgs a) {
   const int b = blockIdx.y;
   const int j = p / a.nx, i = p - j * a.nx;
   const float* fu = a.w + (size_t)b * 2 * hw;
-  const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
+  const float* cf = a.coef + (size_t)b * a.ncoef * hw + p;
 #pragma unroll 1
   for (int pr = 0; pr < 4; ++pr) {
     const int fld = pr >> 1, axis = pr & 1;
@@ -138,50 +199,40 @@ __global__ void __launch_bounds__(256) gface_kernel(const GFaceArgs a) {
       const int q = 2 * pr + kind;
       float L[20];
 #pragma unroll
+      for (int t = 0; t < 20; ++t) L[t] = a.wl[(kind * 2 + axis) * 20 + t] + cf[(size_t)(q * 20 + t) * hw];
+      a.inst[((size_t)b * 8 + q) * hw + p] = face_value(L, tap, kind, h, a.dord, a.ablation);
+    }
+  }
+  if (!a.s) return;
+  const float* fs = a.s + (size_t)b * hw;
+#pragma unroll 1
+  for (int axis = 0; axis < 2; ++axis) {
+    float tap[20];
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int jj = axis == 0 ? j + r - 2 : j + cc - 2;
+        const int ii = axis == 0 ? i + cc - 2 : i + r - 2;
+        tap[r * 4 + cc] = fs[((jj + a.ny) % a.ny) * a.nx + (ii + a.nx) % a.nx];
+      }
+    const float h = axis == 0 ? 1.0f / a.idx : 1.0f / a.idy;
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const int m = 2 * axis + kind;
+      float L[20];
+#pragma unroll
       for (int t = 0; t < 20; ++t)
-        L[t] = a.wl[(kind * 2 + axis) * 20 + t] + a.coef[((size_t)b * kNCoef + q * 20 + t) * hw + p];
-      float s1 = 0.f, sc = 0.f, sr = 0.f;
-#pragma unroll
-      for (int r = 0; r < 5; ++r)
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const float v = L[r * 4 + cc];
-          s1 += v;
-          sc += v * cval[cc];
-          sr += v * (float)(r - 2);
-        }
-      // the projection keeps W_P's consistency: without W_P (ablation 1) neither is applied
-      const float pk = a.ablation == 0 ? 1.0f : 0.0f;
-      s1 *= pk * (1.0f / 20.0f);
-      sc *= pk * (1.0f / 25.0f);
-      sr *= pk * (1.0f / 40.0f);
-      const float scale = kind == 1 ? 1.0f / h : 1.0f;
-      float val = 0.f;
-#pragma unroll
-      for (int r = 0; r < 5; ++r)
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          float k = (L[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
-          if (r == 2 && a.ablation == 0) {
-            if (kind == 0) {
-              k += (cc == 1 || cc == 2) ? 0.5f : 0.f;
-            } else if (a.dord == 4) {
-              const float d4[4] = {1.f / 24.f, -27.f / 24.f, 27.f / 24.f, -1.f / 24.f};
-              k += d4[cc] / h;
-            } else {
-              const float d2[4] = {0.f, -1.f, 1.f, 0.f};
-              k += d2[cc] / h;
-            }
-          }
-          val += k * tap[r * 4 + cc];
-        }
-      a.inst[((size_t)b * 8 + q) * hw + p] = val;
+        L[t] = a.wls[(kind * 2 + axis) * 20 + t] + cf[(size_t)(kNCoef + m * 20 + t) * hw];
+      a.sinst[((size_t)b * 4 + m) * hw + p] = face_value(L, tap, kind, h, a.dord, 0);
     }
   }
 }
 
 // flux assembly + divergence (App. B.2) from the face values, Burgers
-// correction, forcing, and the RK4 combination (App. B.5)
+// correction, forcing, and the RK4 combination (App. B.5); scalar models also
+// the scalar's flux-form tendency -div(u s_f - D grad_f s) from the stage
+// velocity and its RK4 combination
 struct GStageArgs {
   const float* inst;  // [batch][8][ny][nx]
   const float* w;     // stage state
@@ -189,8 +240,12 @@ struct GStageArgs {
   float* acc;         // RK4 accumulator
   float* wout;        // next stage state (stage 3: the new state)
   const float* frc;   // [ny]
+  const float* sinst; // the scalar's face values [batch][4][ny][nx], or null
+  const float* sn;    // scalar at the start of the step [batch][ny][nx]
+  float* sacc;        // its RK4 accumulator
+  float* sout;        // next stage scalar
   int nx, ny, stage, forced, burgers;
-  float dt, nu, idx, idy, drag;
+  float dt, nu, idx, idy, drag, diff;
 };
 
 __device__ __forceinline__ void rk4_combine(int stage, float r, float dt, const float* un, float* acc, float* out,
@@ -251,6 +306,15 @@ __global__ void __launch_bounds__(256) gstage_kernel(const GStageArgs a) {
   }
   rk4_combine(a.stage, tu, a.dt, a.un, a.acc, a.wout, e);
   rk4_combine(a.stage, tv, a.dt, a.un, a.acc, a.wout, e + hw);
+  if (!a.sinst) return;
+  // F_x on the west face of a cell (u there), F_y on its south face (v there)
+  const float* SI = a.sinst + (size_t)b * 4 * hw;
+  const float* wu = a.w + (size_t)b * 2 * hw;
+  const float* wv = wu + hw;
+  auto fx = [&](int q) { return wu[q] * SI[q] - a.diff * SI[hw + q]; };
+  auto fy = [&](int q) { return wv[q] * SI[2 * hw + q] - a.diff * SI[3 * hw + q]; };
+  const float ts = -(fx(j * a.nx + ie) - fx(p)) * a.idx - (fy(jn * a.nx + i) - fy(p)) * a.idy;
+  rk4_combine(a.stage, ts, a.dt, a.sn, a.sacc, a.sout, (size_t)b * hw + p);
 }
 
 // u += c - mean(c), per trajectory and component (one CTA each)
@@ -273,8 +337,8 @@ __global__ void round_bf16_kernel(float* v, size_t n) {
     v[k] = __bfloat162float(__float2bfloat16_rn(v[k]));
 }
 
-int stencil_cin(int l) { return l == 0 ? 2 : kHid; }
-int stencil_cout(int l) { return l == 5 ? kNCoef : kHid; }
+int stencil_cin(int l, bool scalar) { return l == 0 ? (scalar ? 3 : 2) : kHid; }
+int stencil_cout(int l, bool scalar) { return l == 5 ? (scalar ? kNCoefScalar : kNCoef) : kHid; }
 
 template <int GCO>
 cudaError_t launch_gconv(const GConvArgs& a, int batch, cudaStream_t st) {
@@ -284,19 +348,21 @@ cudaError_t launch_gconv(const GConvArgs& a, int batch, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// one network (six layers) from the state(s) behind `in_ptrs` (cin0 channels)
-// into `out` (cout5 channels); hidden activations in act0 / act1
-cudaError_t run_net(fd_ctx* c, const float* const* in_ptrs, int cin0, const size_t* off_w, const size_t* off_b,
-                    int cout5, float* out, cudaStream_t st) {
+// one network (six layers) into `out` (cout5 channels) from cin0 channels: the
+// state(s) behind `in_ptrs` (and, with `s_ptrs`, a scalar as the last channel),
+// or the tensor `in0` [batch][cin0][ny][nx]; hidden activations in act0 / act1
+cudaError_t run_net(fd_ctx* c, const float* const* in_ptrs, const float* const* s_ptrs, const float* in0, int cin0,
+                    const size_t* off_w, const size_t* off_b, int cout5, float* out, cudaStream_t st) {
   GenericLearned& G = *c->glrn;
   const int nx = c->grid.nx, ny = c->grid.ny, B = c->grid.batch;
   const int hw = nx * ny;
-  const float* in = nullptr;
+  const float* in = in0;
   for (int l = 0; l < 6; ++l) {
     GConvArgs a;
     a.cin = l == 0 ? cin0 : kHid;
     a.cout = l == 5 ? cout5 : kHid;
     a.hist = l == 0 ? in_ptrs : nullptr;
+    a.sptr = l == 0 ? s_ptrs : nullptr;
     a.in = in;
     a.w = G.d_params + off_w[l];
     a.b = G.d_params + off_b[l];
@@ -313,8 +379,9 @@ cudaError_t run_net(fd_ctx* c, const float* const* in_ptrs, int cin0, const size
   return cudaSuccess;
 }
 
-// one learned step of the state in the generic-grid buffers (S.un in place)
-cudaError_t learned_step(fd_ctx* c, cudaStream_t st) {
+// one learned step of the state in the generic-grid buffers (S.un in place);
+// scalar models also advance the scalar (S.sn in place) with diffusivity diff
+cudaError_t learned_step(fd_ctx* c, cudaStream_t st, float diff = 0.f) {
   GenericState& S = *c->gen;
   GenericLearned& G = *c->glrn;
   const fd_grid& g = c->grid;
@@ -323,23 +390,33 @@ cudaError_t learned_step(fd_ctx* c, cudaStream_t st) {
   float* const stage_out[4] = {static_cast<float*>(S.wa), static_cast<float*>(S.wb), static_cast<float*>(S.wa), un};
   const float* const stage_in[4] = {un, static_cast<float*>(S.wa), static_cast<float*>(S.wb),
                                     static_cast<float*>(S.wa)};
+  float* const s_out[4] = {static_cast<float*>(S.sa), static_cast<float*>(S.sb), static_cast<float*>(S.sa),
+                           static_cast<float*>(S.sn)};
+  const float* const s_in[4] = {static_cast<float*>(S.sn), static_cast<float*>(S.sa), static_cast<float*>(S.sb),
+                                static_cast<float*>(S.sa)};
   const dim3 cells((unsigned)((hw + 255) / 256), (unsigned)g.batch);
   const float idx = (float)(g.nx / g.lx), idy = (float)(g.ny / g.ly);
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
-    // the network reads its input through a one-entry pointer array: stage 0
-    // reads u_n, stages 1 and 3 the first stage buffer, stage 2 the second
-    e = run_net(c, G.d_single + (s == 0 ? 0 : s == 2 ? 2 : 1), 2, G.off_sw, G.off_sb, kNCoef, G.coef, st);
+    // the network reads its input through one-entry pointer arrays: stage 0
+    // reads u_n (and s_n), stages 1 and 3 the first stage buffers, stage 2 the second
+    const int slot = s == 0 ? 0 : s == 2 ? 2 : 1;
+    e = run_net(c, G.d_single + slot, G.scalar ? G.d_ssingle + slot : nullptr, nullptr, G.scalar ? 3 : 2, G.off_sw,
+                G.off_sb, G.ncoef, G.coef, st);
     if (e != cudaSuccess) break;
     GFaceArgs fa;
     fa.w = stage_in[s];
     fa.coef = G.coef;
     fa.wl = G.d_params + G.off_wl;
     fa.inst = G.inst;
+    fa.s = G.scalar ? s_in[s] : nullptr;
+    fa.wls = G.d_params + G.off_wls;
+    fa.sinst = G.sinst;
     fa.nx = g.nx;
     fa.ny = g.ny;
     fa.dord = c->opts.deriv_order;
     fa.ablation = G.ablation;
+    fa.ncoef = G.ncoef;
     fa.idx = idx;
     fa.idy = idy;
     gface_kernel<<<cells, 256, 0, st>>>(fa);
@@ -350,6 +427,11 @@ cudaError_t learned_step(fd_ctx* c, cudaStream_t st) {
     sa.acc = static_cast<float*>(S.acc);
     sa.wout = stage_out[s];
     sa.frc = static_cast<const float*>(S.frc);
+    sa.sinst = G.scalar ? G.sinst : nullptr;
+    sa.sn = static_cast<const float*>(S.sn);
+    sa.sacc = static_cast<float*>(S.sacc);
+    sa.sout = s_out[s];
+    sa.diff = diff;
     sa.nx = g.nx;
     sa.ny = g.ny;
     sa.stage = s;
@@ -372,7 +454,7 @@ cudaError_t correct(fd_ctx* c, cudaStream_t st) {
   GenericState& S = *c->gen;
   GenericLearned& G = *c->glrn;
   const fd_grid& g = c->grid;
-  cudaError_t e = run_net(c, G.d_hist, 2 * G.kc, G.off_tw, G.off_tb, 2, G.corr, st);
+  cudaError_t e = run_net(c, G.d_hist, nullptr, nullptr, 2 * G.kc, G.off_tw, G.off_tb, 2, G.corr, st);
   if (e != cudaSuccess) return e;
   gtc_apply_kernel<<<(unsigned)(g.batch * 2), 256, 0, st>>>(static_cast<float*>(S.un), G.corr, g.nx * g.ny);
   e = cudaGetLastError();
@@ -393,6 +475,8 @@ fd_status fd_glearned_check(const fd_grid& g, const fd_options& o) {
   if (o.ablation != 0 && o.ablation != 1)
     return fd_set_error(nullptr, FD_EINVAL, "fd_init: ablation must be 0 or 1 (the O_F-only variant needs the Fourier operator)");
   if (o.k_c < 0 || o.k_c > 8) return fd_set_error(nullptr, FD_EINVAL, "fd_init: k_c must be in [0, 8]");
+  if (o.scalar_learned && o.ablation != 0)
+    return fd_set_error(nullptr, FD_EUNSUPPORTED, "fd_init: a model that learns the scalar is built for the full operator");
   return FD_OK;
 }
 
@@ -403,15 +487,21 @@ fd_status fd_glearned_init(fd_ctx* c) {
   const fd_grid& g = c->grid;
   G->kc = c->opts.k_c;
   G->ablation = c->opts.ablation;
+  G->scalar = c->opts.scalar_learned != 0;
+  G->ncoef = G->scalar ? kNCoefScalar : kNCoef;
   G->nparams = fd_learned_param_count(c->opts);
   size_t off = 0;
   G->off_wl = off;
   off += 80;
+  if (G->scalar) {
+    G->off_wls = off;
+    off += 80;
+  }
   for (int l = 0; l < 6; ++l) {
     G->off_sw[l] = off;
-    off += (size_t)stencil_cout(l) * stencil_cin(l) * 9;
+    off += (size_t)stencil_cout(l, G->scalar) * stencil_cin(l, G->scalar) * 9;
     G->off_sb[l] = off;
-    off += stencil_cout(l);
+    off += stencil_cout(l, G->scalar);
   }
   for (int l = 0; l < 6 && G->kc > 0; ++l) {
     const int ci = l == 0 ? 2 * G->kc : kHid, co = l == 5 ? 2 : kHid;
@@ -431,7 +521,7 @@ fd_status fd_glearned_init(fd_ctx* c) {
   alloc((void**)&G->d_params, (size_t)G->nparams * sizeof(float));
   alloc((void**)&G->act0, B * kHid * hw * sizeof(float));
   alloc((void**)&G->act1, B * kHid * hw * sizeof(float));
-  alloc((void**)&G->coef, B * kNCoef * hw * sizeof(float));
+  alloc((void**)&G->coef, B * G->ncoef * hw * sizeof(float));
   alloc((void**)&G->inst, B * 8 * hw * sizeof(float));
   alloc((void**)&G->d_single, 4 * sizeof(const float*));
   if (e == cudaSuccess) {
@@ -439,6 +529,19 @@ fd_status fd_glearned_init(fd_ctx* c) {
     const float* h[4] = {static_cast<const float*>(c->gen->un), static_cast<const float*>(c->gen->wa),
                          static_cast<const float*>(c->gen->wb), nullptr};
     e = cudaMemcpy(G->d_single, h, sizeof h, cudaMemcpyHostToDevice);
+  }
+  if (G->scalar) {
+    // the scalar's state, stage buffers and accumulator (those fd_rollout_scalar
+    // otherwise allocates on its first call), its face values and input pointers
+    GenericState& S = *c->gen;
+    for (void** q : {&S.sn, &S.sa, &S.sb, &S.sacc}) alloc(q, B * hw * sizeof(float));
+    alloc((void**)&G->sinst, B * 4 * hw * sizeof(float));
+    alloc((void**)&G->d_ssingle, 4 * sizeof(const float*));
+    if (e == cudaSuccess) {
+      const float* h[4] = {static_cast<const float*>(S.sn), static_cast<const float*>(S.sa),
+                           static_cast<const float*>(S.sb), nullptr};
+      e = cudaMemcpy(G->d_ssingle, h, sizeof h, cudaMemcpyHostToDevice);
+    }
   }
   if (G->kc > 0) {
     alloc((void**)&G->corr, B * 2 * hw * sizeof(float));
@@ -458,8 +561,8 @@ void fd_glearned_free(fd_ctx* c) {
   GenericLearned* G = c->glrn;
   if (!G) return;
   if (G->graph) cudaGraphExecDestroy(G->graph);
-  void* ps[] = {G->d_params, G->act0, G->act1, G->coef, G->inst, G->corr, G->ring, (void*)G->d_hist,
-                (void*)G->d_single};
+  void* ps[] = {G->d_params, G->act0, G->act1, G->coef, G->inst, G->sinst, G->corr, G->ring, (void*)G->d_hist,
+                (void*)G->d_single, (void*)G->d_ssingle};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete G;
@@ -493,9 +596,14 @@ fd_status fd_glearned_set_params(fd_ctx* c, const float* params, int64_t count, 
 fd_status fd_glearned_network(fd_ctx* c, const void* u, float* coef_out, cudaStream_t st) {
   GenericLearned& G = *c->glrn;
   const float* in = static_cast<const float*>(u);
-  cudaError_t e = cudaMemcpyAsync(G.d_single + 3, &in, sizeof(const float*), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = run_net(c, G.d_single + 3, 2, G.off_sw, G.off_sb, kNCoef, coef_out ? coef_out : G.coef, st);
+  cudaError_t e = cudaSuccess;
+  if (G.scalar) {  // (u, v, s) as one tensor [batch][3][ny][nx]
+    e = run_net(c, nullptr, nullptr, in, 3, G.off_sw, G.off_sb, G.ncoef, coef_out ? coef_out : G.coef, st);
+  } else {
+    e = cudaMemcpyAsync(G.d_single + 3, &in, sizeof(const float*), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = run_net(c, G.d_single + 3, nullptr, nullptr, 2, G.off_sw, G.off_sb, kNCoef, coef_out ? coef_out : G.coef, st);
+  }
   c->launches = 6;
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_network_forward: %s", cudaGetErrorString(e));
   return FD_OK;
@@ -505,6 +613,8 @@ fd_status fd_glearned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fin
                               cudaStream_t st, bool allow_graph) {
   GenericState& S = *c->gen;
   GenericLearned& G = *c->glrn;
+  if (G.scalar)
+    return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout: the model reads the passive scalar (use fd_rollout_scalar)");
   if (!G.ready) return fd_set_error(c, FD_EINVAL, "fd_rollout: learned parameters not set (fd_set_params)");
   const size_t bytes = fd_state_bytes(c->grid);
   const size_t slot = bytes / sizeof(float);
@@ -553,5 +663,66 @@ fd_status fd_glearned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fin
   if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, S.un, bytes, cudaMemcpyDeviceToDevice, st);
   c->launches = launches;
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout (generic-grid learned): %s", cudaGetErrorString(e));
+  return FD_OK;
+}
+
+fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, const void* s0, void* u_final,
+                                     void* s_final, int n_steps, cudaStream_t st) {
+  GenericState& S = *c->gen;
+  GenericLearned& G = *c->glrn;
+  if (!G.scalar)
+    return fd_set_error(c, FD_EUNSUPPORTED,
+                        "fd_rollout_scalar: the learned model does not read the scalar (fd_init with scalar_learned = 1)");
+  if (!G.ready) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: learned parameters not set (fd_set_params)");
+  const size_t bytes = fd_state_bytes(c->grid);
+  const size_t slot = bytes / sizeof(float);
+  const size_t sbytes = (size_t)c->grid.batch * c->grid.nx * c->grid.ny * sizeof(float);
+  const int grp = G.kc > 0 ? G.kc : 1;
+  // the velocity's history ring and temporal correction as in the velocity-only rollout
+  auto step = [&](int k, cudaStream_t s) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (G.kc > 0) e = cudaMemcpyAsync(G.ring + (size_t)((k - 1) % G.kc) * slot, S.un, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = learned_step(c, s, (float)diff);
+    if (e == cudaSuccess && G.kc > 0 && k % G.kc == 0) e = correct(c, s);
+    return e;
+  };
+  const int per_step = launches_per_step(c), per_corr = G.kc > 0 ? 7 + (c->grid.flow == FD_NAVIER_STOKES ? 5 : 0) : 0;
+  cudaError_t e = cudaMemcpyAsync(S.un, u0, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S.sn, s0, sbytes, cudaMemcpyDeviceToDevice, st);
+  // the diffusivity is a kernel argument: a graph captured with another one is replaced
+  if (e == cudaSuccess && n_steps >= grp && (!G.graph || G.graph_diff != diff)) {
+    if (G.graph) {
+      e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess) e = cudaGraphExecDestroy(G.graph);
+      G.graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaSuccess;
+      for (int k = 1; k <= grp && e1 == cudaSuccess; ++k) e1 = step(k, S.cap_stream);
+      const cudaError_t e2 = cudaStreamEndCapture(S.cap_stream, &g);
+      e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    G.graph_diff = e == cudaSuccess ? diff : -1.0;
+  }
+  int done = 0, launches = 0;
+  if (e == cudaSuccess && G.graph && G.graph_diff == diff) {
+    for (; done + grp <= n_steps && e == cudaSuccess; done += grp) {
+      e = cudaGraphLaunch(G.graph, st);
+      launches += grp * per_step + per_corr;
+    }
+  }
+  for (int k = done + 1; k <= n_steps && e == cudaSuccess; ++k) {
+    e = step(k, st);
+    launches += per_step + (G.kc > 0 && k % G.kc == 0 ? per_corr : 0);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, S.un, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s_final, S.sn, sbytes, cudaMemcpyDeviceToDevice, st);
+  c->launches = launches;
+  if (e != cudaSuccess)
+    return fd_set_error(c, FD_ECUDA, "fd_rollout_scalar (generic-grid learned): %s", cudaGetErrorString(e));
   return FD_OK;
 }

@@ -343,8 +343,13 @@ int64_t fd_fno_param_count(int layers, int modes, int width, int cin, int cout) 
 }
 
 int64_t fd_learned_param_count(const fd_options& o) {
-  int64_t n = 80;
-  for (int l = 0; l < 6; ++l) n += (int64_t)stencil_cout(l) * stencil_cin(l) * 9 + stencil_cout(l);
+  // a model that learns the scalar: W_Ls, one more input channel, 80 more outputs
+  const int sl = o.scalar_learned ? 1 : 0;
+  int64_t n = 80 + 80 * sl;
+  for (int l = 0; l < 6; ++l) {
+    const int64_t ci = stencil_cin(l) + (l == 0 ? sl : 0), co = stencil_cout(l) + (l == 5 ? 80 * sl : 0);
+    n += co * ci * 9 + co;
+  }
   if (o.k_c > 0 && o.tc_fno_layers > 0)
     n += fd_fno_param_count(o.tc_fno_layers, o.tc_fno_modes, o.tc_fno_width, 2 * o.k_c, 2);
   else if (o.k_c > 0)

@@ -94,6 +94,7 @@ class FdOptions(C.Structure):
         ("tc_fno_modes", C.c_int32),
         ("tc_fno_width", C.c_int32),
         ("ablation", C.c_int32),
+        ("scalar_learned", C.c_int32),
     ]
 
 
@@ -234,6 +235,7 @@ class Config:
     tc_fno_modes: int = 0
     tc_fno_width: int = 0
     ablation: int = 0  # 0 full flux block, 1 without the physics conv, 2 frequency operator only (Table 4)
+    scalar_learned: bool = False  # the model also learns the passive scalar (network on (u, v, s), 240 channels)
     ny: Optional[int] = None  # rows when the grid is rectangular (generic-grid path); n = columns
     spin_limit: int = 0  # iteration limit of the tensor-core kernels' bounded waits (0 = library default)
 
@@ -263,7 +265,7 @@ class Solver:
         f = FdForcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.kf, cfg.drag)
         o = FdOptions(cfg.deriv_order, 2, 1 if cfg.learned else 0, cfg.k_c, cfg.poisson_symbol, 8, cfg.spin_limit, cfg.path,
                       cfg.fno_layers, cfg.fno_modes, cfg.fno_width, cfg.tc_fno_layers, cfg.tc_fno_modes,
-                      cfg.tc_fno_width, cfg.ablation)
+                      cfg.tc_fno_width, cfg.ablation, 1 if cfg.scalar_learned else 0)
         h = C.c_void_p()
         st = self.lib.fd_init(C.byref(g), cfg.nu, cfg.dt, C.byref(f), C.byref(o), C.byref(h))
         if st != FD_OK:
@@ -348,7 +350,8 @@ class Solver:
         self._check(self.lib.fd_set_params_device(self.h, _ptr(params), int(params.numel()), _stream_handle(stream)))
 
     def network_forward(self, u, coef_out=None, stream=None):
-        """coef_out[batch, 160, n, n] float32 = C_theta(u); None runs the network only."""
+        """coef_out[batch, 160, n, n] float32 = C_theta(u); None runs the network only.
+        With scalar_learned, u is [batch, 3, ny, n] (u, v, s) and coef_out has 240 channels."""
         cp = _ptr(coef_out) if coef_out is not None else None
         self._check(self.lib.fd_network_forward(self.h, _ptr(u), cp, _stream_handle(stream)))
 

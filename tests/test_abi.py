@@ -89,6 +89,9 @@ def _init(lib, n=32, batch=1, dtype=fd.FD_F32, flow=fd.FD_NAVIER_STOKES, nu=1e-3
         dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 3)),
         dict(n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 1)),
         dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 2)),
+        # the learned scalar: without the learned module, out of range
+        dict(n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 0, 1)),
+        dict(n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 0, 2)),
     ],
 )
 def test_init_rejects_invalid_arguments(lib, kw):
@@ -144,3 +147,16 @@ def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):
     assert st == fd.FD_EUNSUPPORTED
     st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 0, 0, 0, 8, 1 << 26, 4))
     assert st == fd.FD_EINVAL
+    # a model that learns the scalar: FP32 generic-grid path, full operator only
+    st, _ = _init(lib, n=64, dtype=fd.FD_F64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 0, 1))
+    assert st == fd.FD_EUNSUPPORTED
+    st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 0, 0, 0, 0, 0, 0, 0, 1, 1))
+    assert st == fd.FD_EUNSUPPORTED
+    st, _ = _init(lib, n=64, opts=fd.FdOptions(4, 2, 1, 0, 0, 8, 1 << 26, 1, 0, 0, 0, 0, 0, 0, 0, 1))
+    assert st == fd.FD_EUNSUPPORTED
+
+
+def test_options_struct_layout():
+    # int32 x 6, int64, int32 x 9, padded to the int64's alignment
+    assert C.sizeof(fd.FdOptions) == 72
+    assert fd.FdOptions.scalar_learned.offset == 64

@@ -381,7 +381,52 @@ def training_measurement(fd, I, iters: int = 5):
         "unit": "rollout cell-updates/s (forward + reverse mode + Adam)",
         "ms_per_step_adjoint": ms_adj,
         "loss": float(loss.item()),
+        "paper_grids": paper_grid_training(fd, I, iters),
     }
+
+
+def paper_grid_training(fd, I, iters: int):
+    """Training iterations of the models on the paper's own coarse grids, which
+    run on the generic-grid path (CUDA-core network, FP32 reverse mode): the
+    Burgers LDSolver on 25^2 over [0, 1]^2 and the shear-flow LDSolver on 128 x 64
+    over [0, 8] x [0, 4], both at dt = 1e-2 with the stencil network and a CNN
+    temporal correction every k_c = 4 steps; labels are the plain coarse rollout."""
+    import torch
+
+    from paper_2507_01975_gb300.train import TrainConfig, Trainer
+
+    out = {}
+    kc = 4
+    cases = (("burgers_25x25", dict(n=25, flow="burgers", nu=0.002, lx=1.0, ly=1.0), 16, 16,
+              lambda: I.burgers_ic(25, 1, lx=1.0)),
+             ("shear_128x64", dict(n=128, ny=64, nu=1e-3, lx=8.0, ly=4.0), 4, 8,
+              lambda: I.shear_scalar_ic(128, 64)[0]))
+    for name, geo, b, unroll, ic in cases:
+        cfg = dict(batch=b, dtype="f32", dt=1e-2, **geo)
+        s = fd.Solver(fd.Config(learned=True, k_c=kc, **cfg))
+        plain = fd.Solver(fd.Config(**cfg))
+        st = I.random_conv_stack(4, 2, 64, 160, last_scale=0.05)
+        tc = I.random_conv_stack(6, 2 * kc, 64, 2, last_scale=0.02)
+        u0 = torch.tensor(np.stack([ic()] * b).astype(np.float32), device="cuda")
+        tgt = torch.empty((unroll,) + tuple(u0.shape), device="cuda")
+        plain.rollout(u0, torch.empty_like(u0), unroll, traj=tgt, save_every=1)
+        tr = Trainer(s, I.pack_params(I.random_wl(5, 1e-2), st, tc), TrainConfig(unroll=unroll, ckpt_every=kc, lr=1e-4))
+        tr.step(u0, tgt)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(iters):
+            loss = tr.step(u0, tgt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        out[name] = {"batch": b, "unroll": unroll, "ckpt_every": kc, "k_c": kc, "ms_per_iteration": ms,
+                     "rollout_cell_updates_per_s": s.state_shape[2] * s.state_shape[3] * b * unroll / (ms * 1e-3),
+                     "loss": float(loss.item())}
+        s.close()
+        plain.close()
+    return out
 
 
 # algorithmic minimum per cell and time step: read and write the FP32 state (u, v)
@@ -776,22 +821,31 @@ def speed_measurement(fd, I, reps: int = 3):
     dt = 32 x 2.19e-4 on the tensor-core path; Burgers 25^2 at dt = 1e-2 and the
     shear layer 128 x 64 at dt = 1e-2 with the stencil network and a CNN temporal
     correction (k_c = 4) on the generic-grid path, whose learned module has no
-    Fourier operators. The plain 25^2 Burgers solver is reported beside its model."""
+    Fourier operators. The plain 25^2 Burgers solver is reported beside its model.
+    Both shear rows advance the passive scalar with the velocity (D = 2e-3): the DNS
+    with the physics kernels, the model with its learned scalar operators (network on
+    (u, v, s), 240 channels)."""
     import torch
 
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def per_physical_second(s, U0, dt):
+    def per_physical_second(s, U0, dt, S0=None, D=2e-3):
         u = torch.tensor(U0, device="cuda")
         o = torch.empty_like(u)
         steps = int(round(1.0 / dt))
-        s.rollout(u, o, steps)
+        if S0 is None:
+            run = lambda: s.rollout(u, o, steps)
+        else:
+            sc = torch.tensor(S0, device="cuda")
+            so = torch.empty_like(sc)
+            run = lambda: s.rollout_scalar(u, sc, o, so, steps, D)
+        run()
         torch.cuda.synchronize()
         best = float("inf")
         for _ in range(reps):
             e0.record(stream)
-            s.rollout(u, o, steps)
+            run()
             e1.record(stream)
             torch.cuda.synchronize()
             best = min(best, e0.elapsed_time(e1) * 1e-3)
@@ -827,12 +881,13 @@ def speed_measurement(fd, I, reps: int = 3):
                       "learned_64x64": per_physical_second(lrn, ic(64, 0)[None].astype(np.float32), 32 * dt_f)}
     dns = fd.Solver(fd.Config(n=1024, ny=512, batch=1, dtype="f32", nu=1e-3, dt=3.125e-4, lx=8.0, ly=4.0))
     lrn = fd.Solver(fd.Config(n=128, ny=64, batch=1, dtype="f32", nu=1e-3, dt=1e-2, lx=8.0, ly=4.0, learned=True,
-                              k_c=kc))
-    lrn.set_params(I.pack_params(I.random_wl(3, 1e-2), st, tcc))
-    rows["shear"] = {"dns_1024x512": per_physical_second(dns, I.shear_scalar_ic(1024, 512)[0][None].astype(np.float32),
-                                                         3.125e-4),
-                     "learned_128x64": per_physical_second(lrn, I.shear_scalar_ic(128, 64)[0][None].astype(np.float32),
-                                                           1e-2)}
+                              k_c=kc, scalar_learned=True))
+    st_s = I.random_conv_stack(1, 3, 64, 240, last_scale=0.05)
+    lrn.set_params(I.pack_params(I.random_wl(3, 1e-2), st_s, tcc, W_Ls=I.random_wl(7, 1e-2)))
+    (uf, sf), (uc, sc) = I.shear_scalar_ic(1024, 512), I.shear_scalar_ic(128, 64)
+    f32 = lambda a: a[None].astype(np.float32)
+    rows["shear"] = {"dns_1024x512_with_scalar": per_physical_second(dns, f32(uf), 3.125e-4, f32(sf)),
+                     "learned_128x64_with_scalar": per_physical_second(lrn, f32(uc), 1e-2, f32(sc))}
     for k, (p_dns, p_model) in paper.items():
         rows[k]["paper_a100"] = {"dns": p_dns, "ldsolver": p_model}
     return {"unit": "GPU seconds per simulated physical second, batch 1 (min of %d runs)" % reps, **rows}

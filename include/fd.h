@@ -108,10 +108,10 @@ typedef struct {
                              grid; 1 = on chip only; 2 = streaming (FP32, N in [32, 2048]);
                              3 = generic grid (Burgers on any nx x ny in [4, 8192]^2, FP32 or
                              FP64; Navier-Stokes on power-of-two nx, ny in [32, 2048], FP32;
-                             no learned module) */
+                             learned contexts FP32, without the Fourier operators) */
   int32_t fno_layers;     /* frequency-domain operator O_F of the learnable module (Sec. 3.4):
-                             Fourier layers, 0 = off (default); needs learned = 1; forward only
-                             (the reverse-mode calls refuse a context that has it) */
+                             Fourier layers, 0 = off (default); needs learned = 1; built on the
+                             32^2 / 64^2 tensor-core path, forward and reverse mode */
   int32_t fno_modes;      /* kept Fourier modes M per axis, 1 <= M <= N/2 (Table S3: 16 or 32) */
   int32_t fno_width;      /* channels of the Fourier layers: 8 or 16 (the widths of Table S3) */
   int32_t tc_fno_layers;  /* temporal correction as a Fourier neural operator (Sec. 3.5; Table S3:
@@ -124,7 +124,8 @@ typedef struct {
                              kernels W_L + C_theta (derivative parts / h), no W_P and no consistency
                              projection; 2 = the frequency-domain operator only: face values O_F(u)
                              (needs fno_layers > 0; the stencil network does not run). Needs
-                             learned = 1; forward only (the reverse-mode calls refuse 1 and 2) */
+                             learned = 1; forward and reverse mode on the tensor-core path,
+                             variant 1 forward on the generic-grid path */
   int32_t scalar_learned; /* 1 = the learnable module also learns the passive scalar's transport
                              (shear flow, App. C.1): the scalar's four operator instances take
                              per-face kernels W_P + proj(W_Ls + C_s) / h^deriv like the
@@ -241,9 +242,9 @@ int32_t fd_last_launch_count(const fd_ctx* ctx);
  * presets of App. C.1), Navier-Stokes on power-of-two nx x ny in [32, 2048]^2
  * (rectangular, e.g. the 128 x 64 shear grid, or square beyond 64^2). There the
  * network runs on the CUDA cores with FP32 activations; the stencil network, W_L,
- * the CNN temporal correction and ablation 1 are built, the Fourier operators are
- * not (FD_EUNSUPPORTED at fd_init), and the calls of the reverse mode and
- * training return FD_EUNSUPPORTED.
+ * the CNN temporal correction and ablation 1 are built, forward and reverse mode
+ * (training included), the Fourier operators are not (FD_EUNSUPPORTED at
+ * fd_init).
  *
  * Parameter layout (float32, fd_param_count values):
  *   W_L[kind 2][axis 2][5][4]                      (kind 0 interp, 1 deriv;
@@ -323,17 +324,24 @@ fd_status fd_network_forward(fd_ctx* ctx, const void* u, float* coef_out, void* 
  * With a temporal correction (k_c > 0) this is the VJP of the FV step alone,
  * the step fd_rollout takes before it applies a correction; the correction's
  * own reverse mode is fd_tc_adjoint, and fd_rollout_adjoint / fd_train_step
- * combine the two. Scope: FP32 contexts with N = 32 or 64, plain or learned
- * (the temporal correction as a CNN head); FD_EUNSUPPORTED otherwise (the
- * frequency-domain operator, the ablation variants, the FNO correction).
- * FD_EINVAL for null pointers, dparams on a plain context or parameters not
- * yet set. */
+ * combine the two. Scope: FP32 contexts with N = 32 or 64 off the generic-grid
+ * path, plain or learned (with or without the frequency-domain operator, any
+ * ablation variant), and FP32 contexts of the generic-grid path, plain or
+ * learned (ablation 0 or 1): there the stage states are recomputed, each
+ * stage's network forward is run again keeping its pre-activations, and every
+ * reverse product runs on the CUDA cores in FP32 (the weight gradients reduced
+ * over pixels in a fixed order); the workspace (about 200 floats per cell, 650
+ * for learned contexts) is allocated by the first call.
+ * FD_EUNSUPPORTED otherwise (FP64 generic-grid contexts, a model that learns the
+ * scalar). FD_EINVAL for null pointers, dparams on a plain context or
+ * parameters not yet set. */
 fd_status fd_step_adjoint(fd_ctx* ctx, const void* u_in, const void* lam_out, void* lam_in, float* dparams,
                           void* stream);
 
 /* Reverse mode of one temporal correction (Sec. 3.2, Sec. 3.5):
  * u_k = P(V + c - mean(c)), c = TC(u_{k-k_c}, .., u_{k-1}), V = FV(u_{k-1}),
- * the CNN head of the correction (2 k_c -> 64 x4 -> 2, GELU). Given the
+ * the CNN head of the correction (2 k_c -> 64 x4 -> 2, GELU) or its Fourier
+ * neural operator (tc_fno_layers > 0). Given the
  * cotangent lam of u_k: vbar = P(lam), the cotangent of V (P is symmetric and
  * so is the mean removal, c_bar = P(lam) - mean), and hist_bar = the cotangents
  * of the k_c history states through the network; dparams (may be NULL)
@@ -343,8 +351,9 @@ fd_status fd_step_adjoint(fd_ctx* ctx, const void* u_in, const void* lam_out, vo
  * gradient (CUDA cores, FP32).
  * hist: device [k_c][batch][2][n][n] float32 (u_{k-k_c} first); lam, vbar:
  * [batch][2][n][n] (vbar may be NULL); hist_bar: [k_c][batch][2][n][n],
- * written. A learned context with k_c > 0 and the CNN head; FD_EUNSUPPORTED
- * otherwise, FD_EINVAL for null pointers or parameters not yet set. */
+ * written. A learned context with k_c > 0 (on the generic-grid path: the CNN
+ * head on the CUDA cores, FP32); FD_EUNSUPPORTED otherwise, FD_EINVAL for null
+ * pointers or parameters not yet set. */
 fd_status fd_tc_adjoint(fd_ctx* ctx, const void* hist, const void* lam, void* vbar, void* hist_bar, float* dparams,
                         void* stream);
 

@@ -672,9 +672,11 @@ extern "C" {
 fd_status fd_step_adjoint(fd_ctx* c, const void* u_in, const void* lam_out, void* lam_in, float* dparams,
                           void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_step_adjoint: null context");
-  if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_step_adjoint: not built for the generic-grid path");
   c->launches = 0;
   if (!u_in || !lam_out || !lam_in) return fd_set_error(c, FD_EINVAL, "fd_step_adjoint: null state pointer");
+  if (c->gen)
+    return fd_gadjoint_step(c, static_cast<const float*>(u_in), static_cast<const float*>(lam_out),
+                            static_cast<float*>(lam_in), dparams, static_cast<cudaStream_t>(stream));
   if (c->grid.dtype != FD_F32 || (c->grid.nx != 32 && c->grid.nx != 64))
     return fd_set_error(c, FD_EUNSUPPORTED, "fd_step_adjoint: built for FP32 grids of 32 or 64 cells per side");
   if (c->lrn && !c->lrn->ready)
@@ -701,6 +703,19 @@ fd_status fd_tc_adjoint(fd_ctx* c, const void* hist, const void* lam, void* vbar
                         void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_tc_adjoint: null context");
   c->launches = 0;
+  if (c->gen) {
+    if (!hist || !lam || !hist_bar) return fd_set_error(c, FD_EINVAL, "fd_tc_adjoint: null pointer");
+    const size_t slot = fd_state_bytes(c->grid) / sizeof(float);
+    const float* h[8] = {};
+    const int kc = c->glrn ? c->glrn->kc : 0;
+    for (int s = 0; s < kc && s < 8; ++s) h[s] = static_cast<const float*>(hist) + (size_t)s * slot;
+    int launches = 0;
+    const fd_status r = fd_gadjoint_tc(c, h, static_cast<const float*>(lam), static_cast<float*>(vbar),
+                                       static_cast<float*>(hist_bar), slot, dparams, static_cast<cudaStream_t>(stream),
+                                       &launches);
+    c->launches = launches;
+    return r;
+  }
   if (!c->lrn || c->lrn->kc == 0)
     return fd_set_error(c, FD_EUNSUPPORTED, "fd_tc_adjoint: needs a learned context with a temporal correction");
   if (!hist || !lam || !hist_bar) return fd_set_error(c, FD_EINVAL, "fd_tc_adjoint: null pointer");
@@ -733,6 +748,7 @@ fd_status fd_tc_adjoint(fd_ctx* c, const void* hist, const void* lam, void* vbar
 // used by the rollout reverse mode: the history is an array of k_c state pointers
 fd_status fd_tc_adjoint_ptrs(fd_ctx* c, const float* const* hist_host, const float* lam, float* hist_bar,
                              size_t state_stride, float* dparams, cudaStream_t st, int* launches) {
+  if (c->gen) return fd_gadjoint_tc(c, hist_host, lam, nullptr, hist_bar, state_stride, dparams, st, launches);
   if (!c->adj) {
     fd_status s = adjoint_alloc(c);
     if (s != FD_OK) return s;

@@ -478,6 +478,7 @@ fd_status fd_destroy(fd_ctx* c) {
   fd_adjoint_free(c);
   fd_learned_free(c);
   fd_large_free(c);
+  fd_gadjoint_free(c);
   fd_glearned_free(c);
   fd_generic_free(c);
   delete c;

@@ -183,6 +183,9 @@ struct GenericState {
   void* sacc = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
+  // one step with the scalar, captured by fd_rollout_scalar for the diffusivity sgraph_diff
+  cudaGraphExec_t sgraph = nullptr;
+  double sgraph_diff = -1.0;
 };
 
 // learned module on the generic-grid path (fd_glearned.cu): FP32 parameters
@@ -213,6 +216,35 @@ struct GenericLearned {
   const float** d_ssingle = nullptr; // [4] the same for the scalar (scalar models): s_n, its two stage buffers
   cudaGraphExec_t graph = nullptr;  // one group of max(k_c, 1) steps, captured by the first rollout
   double graph_diff = -1.0;         // scalar models: the diffusivity the graph was captured with
+  uint64_t version = 0;             // bumped by every parameter upload
+};
+
+// reverse mode on the generic-grid path (fd_gadjoint.cu), allocated by its
+// first call: the recomputed stage states, the per-face kernels (then the
+// network-output cotangent), face values and their cotangents, the RK4
+// cotangent bookkeeping, and for learned contexts the saved pre-activations,
+// the reverse activations, the transposed weights and the weight-gradient
+// partial sums
+struct GenAdjoint {
+  float* w[4] = {};                 // w[1..3]: stage states [batch][2][ny][nx]
+  float* acc = nullptr;             // scratch RK accumulator
+  float* kbuf = nullptr;            // [batch][160][ny][nx]
+  float* inst = nullptr;            // [batch][8][ny][nx] face values
+  float* vbar = nullptr;            // [batch][8][ny][nx] their cotangents
+  float* ubar = nullptr;            // [batch][2][ny][nx] stage-state cotangent
+  float* g = nullptr;               // P(lam)
+  float* y = nullptr;               // P(stage-state cotangent)
+  float* rb = nullptr;              // tendency cotangent
+  float* lam = nullptr;             // accumulated input cotangent
+  float* zsave[5] = {};             // [batch][64][ny][nx] hidden pre-activations
+  float* zb[2] = {};                // [batch][64][ny][nx] reverse activations
+  float* wt = nullptr;              // transposed, flipped weights of both networks
+  size_t off_wt_s[6] = {}, off_wt_t[6] = {};
+  uint64_t wt_version = ~0ull;      // parameter version the transposed weights belong to
+  float* part = nullptr;            // weight-gradient partial sums
+  size_t npart = 0;                 // floats in part
+  double* sums = nullptr;           // [240] channel sums
+  const float** d_hist = nullptr;   // [8] history pointers of the correction network
 };
 }  // namespace ldfv
 
@@ -239,6 +271,7 @@ struct fd_ctx {
   ldfv::LargeState* big = nullptr;   // set when the streaming path runs this context
   ldfv::GenericState* gen = nullptr; // set for the generic-grid path (non-power-of-two / rectangular grids)
   ldfv::GenericLearned* glrn = nullptr;  // learned module of a generic-grid context
+  ldfv::GenAdjoint* gadj = nullptr;      // reverse mode of a generic-grid context
   // launch plan of a plain on-chip context: on-chip configurations valid for
   // this grid ([0] = default), the one in use, and how the batch is split
   // between it and a streaming context that runs the trajectories
@@ -294,6 +327,12 @@ fd_status fd_glearned_set_params(fd_ctx* c, const float* params, int64_t count, 
 fd_status fd_glearned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_final, int n_steps, int save_every,
                               cudaStream_t st, bool allow_graph);
 fd_status fd_glearned_network(fd_ctx* c, const void* u, float* coef_out, cudaStream_t st);
+// reverse mode on the generic-grid path (fd_gadjoint.cu)
+fd_status fd_gadjoint_step(fd_ctx* c, const float* u_in, const float* lam_out, float* lam_in, float* dparams,
+                           cudaStream_t st);
+fd_status fd_gadjoint_tc(fd_ctx* c, const float* const* hist_host, const float* lam, float* vbar, float* hist_bar,
+                         size_t state_stride, float* dparams, cudaStream_t st, int* launches);
+void fd_gadjoint_free(fd_ctx* c);
 fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, const void* s0, void* u_final,
                                      void* s_final, int n_steps, cudaStream_t st);
 

@@ -222,10 +222,7 @@ __global__ void __launch_bounds__(AxCfg<LOGL>::NT) gproj_cols_kernel(float2* Z, 
   const TransformSync sync{0, C::NT};
   float2* buf = gsm + f * SP::BUF;
   fft_forward<LOGL>(z, buf, tws, t, sync);
-  fft_store_natural<LOGL>(buf, z, t);
-  sync();
-  fft_load<LOGL>(z, buf, t);
-  sync();
+  // register m holds point t + m T, the inverse transform's input order
   const float sx = live ? symx[i] : 1.0f;
 #pragma unroll
   for (int m = 0; m < kFP; ++m) {
@@ -506,6 +503,7 @@ void fd_generic_free(fd_ctx* c) {
   GenericState* S = c->gen;
   if (!S) return;
   if (S->graph) cudaGraphExecDestroy(S->graph);
+  if (S->sgraph) cudaGraphExecDestroy(S->sgraph);
   if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
   void* ps[] = {S->un, S->wa, S->wb, S->acc, S->frc, S->z, S->p, S->twx, S->twy, S->symx, S->symy,
                 S->sn, S->sa, S->sb, S->sacc};
@@ -583,7 +581,26 @@ fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const
   const size_t bytes = fd_state_bytes(g);
   e = cudaMemcpyAsync(S.un, u0, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S.sn, s0, sbytes, cudaMemcpyDeviceToDevice, st);
-  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) e = generic_step_any(c, st, true, diffusivity);
+  // one step is captured as a graph and replayed; the diffusivity is a kernel
+  // argument, so a call with another one recaptures it
+  if (e == cudaSuccess && n_steps > 0 && (!S.sgraph || S.sgraph_diff != diffusivity)) {
+    if (S.sgraph) {
+      e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess) e = cudaGraphExecDestroy(S.sgraph);
+      S.sgraph = nullptr;
+    }
+    cudaGraph_t gr = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e1 = generic_step_any(c, S.cap_stream, true, diffusivity);
+      const cudaError_t e2 = cudaStreamEndCapture(S.cap_stream, &gr);
+      e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S.sgraph, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    S.sgraph_diff = e == cudaSuccess ? diffusivity : -1.0;
+  }
+  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(S.sgraph, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, S.un, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s_final, S.sn, sbytes, cudaMemcpyDeviceToDevice, st);
   c->launches = (g.flow == FD_NAVIER_STOKES ? 4 * 5 : 4) * n_steps;

@@ -179,8 +179,9 @@ fd_status train_reserve(fd_ctx* c, int nseg, int seglen) {
         cudaMalloc(&T->lam, fd_state_bytes(c->grid)) != cudaSuccess)
       return fd_set_error(c, FD_ENOMEM, "training workspace: out of device memory");
   }
-  if (c->lrn && c->lrn->kc > 0 && !T->pend) {
-    if (cudaMalloc(&T->pend, fd_state_bytes(c->grid) * c->lrn->kc) != cudaSuccess) {
+  const int kc = c->lrn ? c->lrn->kc : c->glrn ? c->glrn->kc : 0;
+  if (kc > 0 && !T->pend) {
+    if (cudaMalloc(&T->pend, fd_state_bytes(c->grid) * kc) != cudaSuccess) {
       T->pend = nullptr;
       return fd_set_error(c, FD_ENOMEM, "training workspace: history cotangents do not fit");
     }
@@ -220,7 +221,7 @@ fd_status train_reserve(fd_ctx* c, int nseg, int seglen) {
 // projected and P is idempotent, so P(lam) and lam give the same result.
 fd_status rollout_reverse(fd_ctx* c, const float* u0, int n, int k, const float* lam_traj, const float* targets,
                           float* lam0, float* dparams, double* loss, cudaStream_t st, const char* who) {
-  const int kc = c->lrn ? c->lrn->kc : 0;
+  const int kc = c->lrn ? c->lrn->kc : c->glrn ? c->glrn->kc : 0;
   if (kc > 0 && k % kc != 0)
     return fd_set_error(c, FD_EINVAL, "%s: ckpt_every must be a multiple of k_c (%d)", who, kc);
   const int nseg = (n + k - 1) / k;
@@ -356,7 +357,6 @@ fd_status fd_mse_loss(fd_ctx* c, const float* pred, const float* target, int64_t
 fd_status fd_rollout_adjoint(fd_ctx* c, const void* u0, int32_t n_steps, int32_t ckpt_every, const void* lam_traj,
                              void* lam0, float* dparams, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout_adjoint: null context");
-  if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_rollout_adjoint: not built for the generic-grid path");
   if (!u0 || !lam_traj || !lam0) return fd_set_error(c, FD_EINVAL, "fd_rollout_adjoint: null pointer");
   if (n_steps < 1 || ckpt_every < 1) return fd_set_error(c, FD_EINVAL, "fd_rollout_adjoint: n_steps, ckpt_every >= 1");
   return rollout_reverse(c, static_cast<const float*>(u0), n_steps, ckpt_every, static_cast<const float*>(lam_traj),
@@ -367,7 +367,6 @@ fd_status fd_rollout_adjoint(fd_ctx* c, const void* u0, int32_t n_steps, int32_t
 fd_status fd_train_step(fd_ctx* c, const void* u0, const void* targets, int32_t n_steps, int32_t ckpt_every,
                         float* dparams, double* loss, void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_train_step: null context");
-  if (c->gen) return fd_set_error(c, FD_EUNSUPPORTED, "fd_train_step: not built for the generic-grid path");
   if (!u0 || !targets || !loss) return fd_set_error(c, FD_EINVAL, "fd_train_step: null pointer");
   if (n_steps < 1 || ckpt_every < 1) return fd_set_error(c, FD_EINVAL, "fd_train_step: n_steps, ckpt_every >= 1");
   return rollout_reverse(c, static_cast<const float*>(u0), n_steps, ckpt_every, nullptr,

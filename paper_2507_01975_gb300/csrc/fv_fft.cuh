@@ -46,6 +46,9 @@ struct SPlan {
   static constexpr int TW = NP > 1 ? tw_off(NP) : 0;
   // after the last pass register s + SL r of thread t holds X[t + s T + r NSL]
   static constexpr int RL = radix(NP - 1), SL = kFP / RL, NSL = ns(NP - 1);
+  // NSL = SL T, so register m = s + SL r holds X[t + m T]: a forward transform
+  // leaves every point where an inverse transform of the same thread takes it
+  static_assert(NSL == SL * T, "natural output order equals the input order");
   static constexpr int BUF = N + N / 16 + 4;  // padded buffer of one transform (float2)
 };
 

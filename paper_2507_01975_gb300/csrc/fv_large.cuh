@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(ColCfg<LOGN>::NT, kFMB) large_cols_kernel(cons
   __syncthreads();  // twiddles
   const TransformSync sync{1 + f, T};
   fft_forward<LOGN>(z, buf, tws, t, sync);
-  // multiply by 1 / (N^2 symbol(kx, ky)); the zero mode is removed
+  // multiply by 1 / (N^2 symbol(kx, ky)); the zero mode is removed. The
+  // registers already hold the points in the inverse transform's input order
   const float sx = valid ? a.symx[kx] : 1.0f;
 #pragma unroll
   for (int s = 0; s < SP::SL; ++s)
@@ -254,10 +255,6 @@ __global__ void __launch_bounds__(ColCfg<LOGN>::NT, kFMB) large_cols_kernel(cons
       float2& zz = z[s + SP::SL * r];
       zz = make_float2(zz.x * mlt, zz.y * mlt);
     }
-  fft_store_natural<LOGN>(buf, z, t);
-  sync();
-  fft_load<LOGN>(z, buf, t);
-  sync();
   fft_inverse<LOGN>(z, buf, tws, t, sync);
   if (valid) {
 #pragma unroll

@@ -242,6 +242,28 @@ def test_passive_scalar_fp64_burgers_conservation():
     assert np.array_equal(gs0, S0)
 
 
+def test_passive_scalar_graph_follows_the_diffusivity():
+    """One context, rollouts at D = 1e-3, 2e-3, 1e-3 (the captured step is replaced
+    each time): bit-identical to fresh contexts at each diffusivity."""
+    nx, ny, lx, ly = 128, 64, 8.0, 4.0
+    p = O.Problem(nx=nx, ny=ny, lx=lx, ly=ly, nu=1e-3, dt=1e-2)
+    u, sc = I.shear_scalar_ic(nx, ny, lx, ly, seed=3)
+    U0 = O.project(u, p)[None].astype(np.float32)
+    S0 = sc[None].astype(np.float32)
+    cfg = fd.Config(n=nx, ny=ny, batch=1, dtype="f32", nu=1e-3, dt=1e-2, lx=lx, ly=ly)
+    fresh = {D: gpu_scalar_rollout(cfg, U0, S0, 5, D)[1] for D in (1e-3, 2e-3)}
+    s = fd.Solver(cfg)
+    u = torch.tensor(U0, device="cuda")
+    sc = torch.tensor(S0, device="cuda")
+    for D in (1e-3, 2e-3, 1e-3):
+        uo, so = torch.empty_like(u), torch.empty_like(sc)
+        s.rollout_scalar(u, sc, uo, so, 5, D)
+        torch.cuda.synchronize()
+        assert np.array_equal(so.double().cpu().numpy(), fresh[D])
+    assert not np.array_equal(fresh[1e-3], fresh[2e-3])
+    s.close()
+
+
 def test_passive_scalar_refusals():
     s = fd.Solver(fd.Config(n=64, batch=1, dtype="f32", nu=1e-3, dt=1e-3))  # on-chip path
     u = torch.zeros((1, 2, 64, 64), device="cuda")

@@ -107,17 +107,16 @@ __global__ void adam_kernel(float* p, float* g, float* m, float* v, size_t n, fl
 // w = (v - v[i-1]) / dx - (u - u[j-1]) / dy of two states a, b: (sum wa, sum wb,
 // sum wa^2, sum wb^2, sum wa wb) in FP64, one row of 5 per block.
 template <typename T>
-__global__ void vort_partial_kernel(const T* a, const T* b, int logn, double idx, double idy, double* partial) {
+__global__ void vort_partial_kernel(const T* a, const T* b, int nx, int ny, double idx, double idy, double* partial) {
   __shared__ double red[5][32];
-  const int N = 1 << logn, MSK = N - 1;
-  const size_t NN = (size_t)N * N;
+  const size_t NN = (size_t)nx * ny;
   const int tr = blockIdx.y;
   const T* ua = a + (size_t)tr * 2 * NN;
   const T* ub = b + (size_t)tr * 2 * NN;
   double s[5] = {0, 0, 0, 0, 0};
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < NN; c += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(c >> logn), i = (int)(c & MSK);
-    const size_t cw = (size_t)j * N + ((i - 1) & MSK), cs = (size_t)((j - 1) & MSK) * N + i;
+    const int j = (int)(c / nx), i = (int)(c - (size_t)j * nx);
+    const size_t cw = (size_t)j * nx + (i - 1 + nx) % nx, cs = (size_t)((j - 1 + ny) % ny) * nx + i;
     const double wa = ((double)ua[NN + c] - (double)ua[NN + cw]) * idx - ((double)ua[c] - (double)ua[cs]) * idy;
     const double wb = ((double)ub[NN + c] - (double)ub[NN + cw]) * idx - ((double)ub[c] - (double)ub[cs]) * idy;
     s[0] += wa;
@@ -392,12 +391,14 @@ fd_status fd_vorticity_pcc(fd_ctx* c, const void* a, const void* b, double* pcc,
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const dim3 grid(kBlk, B);
-  if (c->grid.dtype == FD_F64)
+  const fd_grid& g = c->grid;
+  const double idx = g.nx / g.lx, idy = g.ny / g.ly;
+  if (g.dtype == FD_F64)
     vort_partial_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(a), static_cast<const double*>(b),
-                                                     c->logn, c->base.idx, c->base.idy, T.corr);
+                                                     g.nx, g.ny, idx, idy, T.corr);
   else
     vort_partial_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(a), static_cast<const float*>(b),
-                                                    c->logn, c->base.idx, c->base.idy, T.corr);
+                                                    g.nx, g.ny, idx, idy, T.corr);
   vort_pcc_kernel<<<B, 32, 0, st>>>(T.corr, kBlk, (double)c->grid.nx * c->grid.ny, pcc);
   cudaError_t e = cudaGetLastError();
   c->launches = 2;

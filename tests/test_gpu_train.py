@@ -205,6 +205,21 @@ def test_vorticity_correlation_matches_oracle(dtype):
     assert np.max(np.abs(out.cpu().numpy() - 1.0)) <= 1e-12
 
 
+def test_vorticity_correlation_on_a_rectangular_grid_matches_oracle():
+    # generic-grid context: 40 x 24 cells on [0, 1] x [0, 0.6] (unequal spacings)
+    nx, ny, b = 40, 24, 2
+    s = fd.Solver(fd.Config(n=nx, ny=ny, batch=b, dtype="f32", flow="burgers", lx=1.0, ly=0.6, nu=1e-2, dt=1e-3))
+    rng = np.random.default_rng(82)
+    A_ = rng.standard_normal((b, 2, ny, nx)).astype(np.float32).astype(np.float64)
+    B_ = (A_ + 0.5 * rng.standard_normal(A_.shape)).astype(np.float32).astype(np.float64)
+    out = torch.zeros(b, dtype=torch.float64, device="cuda")
+    s.vorticity_pcc(dev(A_), dev(B_), out)
+    torch.cuda.synchronize()
+    dx, dy = 1.0 / nx, 0.6 / ny
+    ref = [O.pcc(O.vorticity(A_[k], dx, dy), O.vorticity(B_[k], dx, dy)) for k in range(b)]
+    assert np.max(np.abs(out.cpu().numpy() - np.array(ref))) <= 1e-12
+
+
 def test_batch_of_mixed_rollouts_equals_individual_rollouts():
     # one graph with a branch per context: plain on-chip (Burgers 32^2, NS 64^2),
     # learned 32^2, and the streaming path at 64^2

@@ -295,46 +295,101 @@ def temporal_correction_vjp(U: np.ndarray, hist, p: Problem, model: LearnedModel
     return g.copy(), [xbar[2 * s:2 * s + 2] for s in range(len(hist))], grads
 
 
-def scalar_tendency_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, qbar: np.ndarray):
+def scalar_tendency_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, qbar: np.ndarray, kernels=None,
+                        want_kbar: bool = False):
     """Reverse mode of ``oracle.scalar.scalar_tendency``: (Ubar, Sbar) for the
     cotangent qbar of -div(u s_f - D grad_f s); every rule is the transpose of a
-    forward line (flux difference, product with the face velocity, face operators)."""
+    forward line (flux difference, product with the face velocity, face operators).
+    ``kernels`` as in the forward (per-face learned kernels); with ``want_kbar``
+    also the kernel cotangents Kbar[m][5, 4, ny, nx] of the four instances."""
     from .scalar import SCALAR_INSTANCES, SCALAR_SHIFT, scalar_face_values
 
-    sx, _gx, sy, _gy = scalar_face_values(S, p)
+    sx, _gx, sy, _gy = scalar_face_values(S, p, kernels)
     Fx_bar = (qbar - shifted(qbar, 0, -1)) / p.dx
     Fy_bar = (qbar - shifted(qbar, -1, 0)) / p.dy
     Ubar = np.stack([Fx_bar * sx, Fy_bar * sy])
     face_bar = [Fx_bar * U[0], -D * Fx_bar, Fy_bar * U[1], -D * Fy_bar]
     Sbar = np.zeros_like(S)
-    for (axis, kind), vb in zip(SCALAR_INSTANCES, face_bar):
-        K = physics_kernel(kind, p.deriv_order, p.dx if axis == 0 else p.dy)
+    Kbar = [None] * 4
+    for m, ((axis, kind), vb) in enumerate(zip(SCALAR_INSTANCES, face_bar)):
+        K = physics_kernel(kind, p.deriv_order, p.dx if axis == 0 else p.dy) if kernels is None else kernels[m]
+        if want_kbar:
+            Kbar[m] = np.zeros((5, 4) + S.shape)
         for r in range(5):
             for c in range(4):
-                if K[r, c] == 0.0:
+                if kernels is None and K[r, c] == 0.0 and not want_kbar:
                     continue
                 a, b = (r - 2, c + SCALAR_SHIFT) if axis == 0 else (c + SCALAR_SHIFT, r - 2)
                 Sbar += unshift(K[r, c] * vb, a, b)
-    return Ubar, Sbar
+                if want_kbar:
+                    Kbar[m][r, c] = vb * shifted(S, a, b)
+    return (Ubar, Sbar, Kbar) if want_kbar else (Ubar, Sbar)
 
 
-def rk4_step_scalar_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, lamU: np.ndarray, lamS: np.ndarray):
+def learned_joint_tendency_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, model: LearnedModel,
+                               rbar: np.ndarray, qbar: np.ndarray):
+    """Reverse mode of one stage of the learned joint step (a model that learns the
+    scalar): r = tendency(U, K(C)), q = scalar_tendency(U, S, K_s(C)) with C the
+    network on (u, v, s). The kernel cotangents of the eight velocity and four
+    scalar instances pass through the consistency projection and 1/h to the 240
+    network-output channels, W_L and W_Ls; the network's input cotangent splits
+    into the velocity's two channels and the scalar's. Returns (Ubar, Sbar,
+    (W_L_bar, W_Ls_bar, stencil_grads))."""
+    from .scalar import N_COEF_SCALAR, SCALAR_COEF0, SCALAR_INSTANCES, learned_scalar_kernels
+
+    assert model.ablation == 0, "a model that learns the scalar takes the full operator"
+    x = np.concatenate([U, S[None]], axis=0)
+    C = cnn_forward(x, model.stencil)
+    ks = learned_kernels(U, p, model, C=C)
+    kss = learned_scalar_kernels(C, p, model)
+    Ub, Kbar = tendency_vjp(U, p, ks, rbar, want_kbar=True)
+    Uq, Sb, Ksbar = scalar_tendency_vjp(U, S, p, D, qbar, kernels=kss, want_kbar=True)
+    ny, nx = S.shape
+    Cbar = np.zeros((N_COEF_SCALAR, ny, nx))
+    WLbar, WLsbar = np.zeros_like(model.W_L), np.zeros_like(model.W_Ls)
+    for q, (_fld, axis, kind, _shift) in enumerate(INSTANCES):
+        scale = 1.0 / (p.dx if axis == 0 else p.dy) if kind == 1 else 1.0
+        Lbar = consistency_project(Kbar[q]) * scale
+        Cbar[q * 20:(q + 1) * 20] = Lbar.reshape(20, ny, nx)
+        WLbar[kind, axis] += Lbar.sum(axis=(2, 3))
+    for m, (axis, kind) in enumerate(SCALAR_INSTANCES):
+        scale = 1.0 / (p.dx if axis == 0 else p.dy) if kind == 1 else 1.0
+        Lbar = consistency_project(Ksbar[m]) * scale
+        c0 = SCALAR_COEF0 + 20 * m
+        Cbar[c0:c0 + 20] = Lbar.reshape(20, ny, nx)
+        WLsbar[kind, axis] += Lbar.sum(axis=(2, 3))
+    xbar, grads = cnn_vjp(x, model.stencil, Cbar)
+    return Ub + Uq + xbar[:2], Sb + xbar[2], (WLbar, WLsbar, grads)
+
+
+def rk4_step_scalar_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, lamU: np.ndarray, lamS: np.ndarray,
+                        model: Optional[LearnedModel] = None):
     """Reverse mode of ``oracle.scalar.rk4_step_scalar``: (Ubar, Sbar) for the
     cotangents of (u_{k+1}, s_{k+1}). The scalar's stages depend on the stage
-    velocities, so every stage's velocity cotangent collects the scalar term too."""
-    from .scalar import scalar_tendency
+    velocities, so every stage's velocity cotangent collects the scalar term too.
+    With a model that learns the scalar also the parameter gradients: returns
+    (Ubar, Sbar, (W_L_bar, W_Ls_bar, stencil_grads)) summed over the stages."""
+    from .scalar import rk4_step_scalar, scalar_tendency  # noqa: F401
 
     ns = p.flow == FLOW_NAVIER_STOKES
     P = (lambda W: project(W, p)) if ns else (lambda W: W)
     dt = p.dt
-    H = lambda W: tendency(W, p)
-    H_vjp = lambda W, Tb: tendency_vjp(W, p, plain_kernels(p), Tb)[0]
+
+    def H(W, Z):
+        if model is None:
+            return tendency(W, p), scalar_tendency(W, Z, p, D)
+        from .scalar import learned_scalar_kernels
+
+        C = cnn_forward(np.concatenate([W, Z[None]], axis=0), model.stencil)
+        return (tendency(W, p, learned_kernels(W, p, model, C=C)),
+                scalar_tendency(W, Z, p, D, learned_scalar_kernels(C, p, model)))
+
     w1, z1 = U, S
-    r1, q1 = H(w1), scalar_tendency(w1, z1, p, D)
+    r1, q1 = H(w1, z1)
     w2, z2 = P(U + 0.5 * dt * r1), S + 0.5 * dt * q1
-    r2, q2 = H(w2), scalar_tendency(w2, z2, p, D)
+    r2, q2 = H(w2, z2)
     w3, z3 = P(U + 0.5 * dt * r2), S + 0.5 * dt * q2
-    r3, q3 = H(w3), scalar_tendency(w3, z3, p, D)
+    r3, q3 = H(w3, z3)
     w4, z4 = P(U + dt * r3), S + dt * q3
     g = P(lamU)
     Ubar, Sbar = g.copy(), lamS.copy()
@@ -342,9 +397,15 @@ def rk4_step_scalar_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, lamU
     qb = [dt / 6.0 * lamS, dt / 3.0 * lamS, dt / 3.0 * lamS, dt / 6.0 * lamS]
     ws, zs = [w1, w2, w3, w4], [z1, z2, z3, z4]
     coef = [None, 0.5 * dt, 0.5 * dt, dt]  # w_s = P(U + coef_s r_{s-1}), z_s = S + coef_s q_{s-1}
+    acc = None
     for s in (3, 2, 1, 0):
-        wq, zb = scalar_tendency_vjp(ws[s], zs[s], p, D, qb[s])
-        wb = H_vjp(ws[s], rb[s]) + wq
+        if model is None:
+            wq, zb = scalar_tendency_vjp(ws[s], zs[s], p, D, qb[s])
+            wb = tendency_vjp(ws[s], p, plain_kernels(p), rb[s])[0] + wq
+        else:
+            wb, zb, gr = learned_joint_tendency_vjp(ws[s], zs[s], p, D, model, rb[s], qb[s])
+            acc = gr if acc is None else (acc[0] + gr[0], acc[1] + gr[1],
+                                          [(a + dW, b + db) for (a, b), (dW, db) in zip(acc[2], gr[2])])
         if s == 0:
             Ubar += wb
             Sbar += zb
@@ -354,4 +415,4 @@ def rk4_step_scalar_vjp(U: np.ndarray, S: np.ndarray, p: Problem, D: float, lamU
             y = P(wb)
             Ubar += y
             rb[s - 1] = rb[s - 1] + coef[s] * y
-    return Ubar, Sbar
+    return (Ubar, Sbar) if model is None else (Ubar, Sbar, acc)

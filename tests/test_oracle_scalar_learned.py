@@ -163,3 +163,96 @@ def test_planted_mistakes_fail(monkeypatch):
 
     monkeypatch.setattr(OS, "apply_axial", swapped)
     assert max(single_tap_error(2, r, c) for r in range(5) for c in range(4)) > 1e-3
+
+
+# --- reverse mode of the learned joint step -----------------------------------
+def narrow_scalar_model(seed, ws_std=0.05):
+    """The stencil network at width 8 (3 -> 8 x 5 -> 240) keeps the finite differences cheap."""
+    st = I.random_conv_stack(seed, 3, 8, OS.N_COEF_SCALAR, last_scale=0.3)
+    rng = np.random.default_rng(seed + 7)
+    return O.LearnedModel(W_L=I.random_wl(seed + 1, 2e-2), stencil=st, W_Ls=rng.standard_normal((2, 2, 5, 4)) * ws_std)
+
+
+GRIDS = {
+    "ns16x8": dict(nx=16, ny=8, lx=2.0, ly=1.3, nu=1e-2, dt=1e-2),
+    "burgers13x9": dict(nx=13, ny=9, lx=1.0, ly=0.8, nu=1e-2, dt=2e-3, flow=O.FLOW_BURGERS),
+}
+
+
+def joint_state(p, seed):
+    rng = np.random.default_rng(seed)
+    U = 0.3 * rng.standard_normal((2, p.ny, p.nx))
+    if p.flow == O.FLOW_NAVIER_STOKES:
+        U = O.project(U, p)
+    return U, rng.standard_normal((p.ny, p.nx))
+
+
+@pytest.mark.parametrize("grid", list(GRIDS))
+def test_learned_joint_step_vjp_dot_product(grid):
+    from oracle import adjoint as A
+
+    p = O.Problem(**GRIDS[grid])
+    mdl = narrow_scalar_model(21)
+    U, S = joint_state(p, 22)
+    rng = np.random.default_rng(23)
+    dU, dS = rng.standard_normal(U.shape), rng.standard_normal(S.shape)
+    if p.flow == O.FLOW_NAVIER_STOKES:
+        dU = O.project(dU, p)
+    lamU, lamS = rng.standard_normal(U.shape), rng.standard_normal(S.shape)
+    D, eps = 2e-3, 1e-3
+
+    def f(t):
+        u1, s1 = OS.rk4_step_scalar(U + t * dU, S + t * dS, p, D, mdl)
+        return np.sum(u1 * lamU) + np.sum(s1 * lamS)
+
+    jv = (-f(2 * eps) + 8 * f(eps) - 8 * f(-eps) + f(-2 * eps)) / (12 * eps)
+    Ub, Sb, _ = A.rk4_step_scalar_vjp(U, S, p, D, lamU, lamS, mdl)
+    rhs = np.sum(dU * Ub) + np.sum(dS * Sb)
+    assert abs(jv - rhs) <= 1e-9 * (abs(jv) + 1.0)
+
+
+@pytest.mark.parametrize("grid", list(GRIDS))
+def test_learned_joint_step_parameter_gradients(grid):
+    """Central differences on W_L, W_Ls (both kinds and axes), the first layer's
+    weights on the s channel and the last layer's scalar channels."""
+    from oracle import adjoint as A
+
+    p = O.Problem(**GRIDS[grid])
+    mdl = narrow_scalar_model(31)
+    U, S = joint_state(p, 32)
+    rng = np.random.default_rng(33)
+    lamU, lamS = rng.standard_normal(U.shape), rng.standard_normal(S.shape)
+    D, eps = 2e-3, 1e-3
+    _, _, (wlb, wlsb, grads) = A.rk4_step_scalar_vjp(U, S, p, D, lamU, lamS, mdl)
+
+    def loss(m):
+        u1, s1 = OS.rk4_step_scalar(U, S, p, D, m)
+        return np.sum(u1 * lamU) + np.sum(s1 * lamS)
+
+    def bumped(which, idx, s):
+        wl, wls = mdl.W_L.copy(), mdl.W_Ls.copy()
+        st = [(W.copy(), b.copy()) for W, b in mdl.stencil]
+        if which == "wl":
+            wl[idx] += s
+        elif which == "wls":
+            wls[idx] += s
+        else:
+            st[which][0][idx] += s
+        return O.LearnedModel(W_L=wl, stencil=st, W_Ls=wls)
+
+    checks = [("wl", (0, 1, 3, 2), wlb), ("wls", (0, 0, 2, 1), wlsb), ("wls", (1, 0, 1, 3), wlsb),
+              ("wls", (0, 1, 4, 0), wlsb), ("wls", (1, 1, 2, 2), wlsb),
+              (0, (5, 2, 1, 0), grads[0][0]), (5, (170, 3, 1, 1), grads[5][0]), (5, (233, 6, 2, 0), grads[5][0])]
+    for which, idx, g in checks:
+        fd = (loss(bumped(which, idx, eps)) - loss(bumped(which, idx, -eps))) / (2 * eps)
+        assert abs(fd - g[idx]) <= 1e-6 * max(1e-2, abs(fd)), (which, idx, fd, g[idx])
+
+
+def test_planted_mistake_in_the_joint_reverse_mode_fails(monkeypatch):
+    """Dropping the consistency projection from the kernel cotangents (the forward
+    keeps it) breaks the dot-product identity."""
+    from oracle import adjoint as A
+
+    monkeypatch.setattr(A, "consistency_project", lambda L: L)
+    with pytest.raises(AssertionError):
+        test_learned_joint_step_vjp_dot_product("ns16x8")

@@ -172,3 +172,55 @@ def adam_step(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int
     mhat = m / (1.0 - beta1 ** t)
     vhat = v / (1.0 - beta2 ** t)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def rollout_scalar_states(U0: np.ndarray, S0: np.ndarray, p: Problem, D: float, n: int,
+                          model: Optional[LearnedModel] = None):
+    """States (u_k, s_k), k = 0 .. n, of the joint rollout (``oracle.scalar.rollout_scalar``)
+    and each step's velocity before its temporal correction."""
+    from .fv import temporal_correction
+    from .scalar import rk4_step_scalar
+
+    U, S = np.array(U0, dtype=np.float64), np.array(S0, dtype=np.float64)
+    states, fv_out = [(U, S)], [None]
+    for k in range(1, n + 1):
+        U1, S1 = rk4_step_scalar(U, S, p, D, model)
+        fv_out.append(U1)
+        if _has_tc(model) and k % model.k_c == 0:
+            U1 = temporal_correction(U1, [states[m][0] for m in range(k - model.k_c, k)], p, model)
+        U, S = U1, S1
+        states.append((U, S))
+    return states, fv_out
+
+
+def rollout_scalar_vjp(U0: np.ndarray, S0: np.ndarray, p: Problem, D: float, n: int, lamU_traj: np.ndarray,
+                       lamS_traj: np.ndarray, model: Optional[LearnedModel] = None):
+    """Reverse mode of the joint rollout (u_0, s_0) -> (u_k, s_k), k = 1 .. n, with
+    the velocity's temporal correction: lamU_traj[k - 1], lamS_traj[k - 1] are the
+    cotangents of (u_k, s_k). Composition of the joint step's VJP
+    (``adjoint.rk4_step_scalar_vjp``) and the correction's
+    (``adjoint.temporal_correction_vjp``), each state's cotangent the sum of what
+    reaches it. Returns (lamU0, lamS0, grads) with grads a dict of 'W_L', 'W_Ls',
+    'stencil' and 'tc' (None for the plain step)."""
+    states, fv_out = rollout_scalar_states(U0, S0, p, D, n, model)
+    pu = [np.zeros_like(states[0][0]) for _ in range(n + 1)]
+    ps = [np.zeros_like(states[0][1]) for _ in range(n + 1)]
+    g = None if model is None else {"W_L": None, "W_Ls": None, "stencil": None, "tc": None}
+    for k in range(n, 0, -1):
+        lu = pu[k] + lamU_traj[k - 1]
+        ls = ps[k] + lamS_traj[k - 1]
+        if _has_tc(model) and k % model.k_c == 0:
+            lu, hbars, tg = A.temporal_correction_vjp(fv_out[k], [states[m][0] for m in range(k - model.k_c, k)], p,
+                                                      model, lu)
+            for s, hb in enumerate(hbars):
+                pu[k - model.k_c + s] = pu[k - model.k_c + s] + hb
+            g["tc"] = _add(g["tc"], tg)
+        out = A.rk4_step_scalar_vjp(states[k - 1][0], states[k - 1][1], p, D, lu, ls, model)
+        pu[k - 1] = pu[k - 1] + out[0]
+        ps[k - 1] = ps[k - 1] + out[1]
+        if model is not None:
+            wl, wls, st = out[2]
+            g["W_L"] = _add(g["W_L"], wl)
+            g["W_Ls"] = _add(g["W_Ls"], wls)
+            g["stencil"] = _add(g["stencil"], st)
+    return pu[0], ps[0], g

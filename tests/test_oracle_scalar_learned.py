@@ -256,3 +256,47 @@ def test_planted_mistake_in_the_joint_reverse_mode_fails(monkeypatch):
     monkeypatch.setattr(A, "consistency_project", lambda L: L)
     with pytest.raises(AssertionError):
         test_learned_joint_step_vjp_dot_product("ns16x8")
+
+
+def test_joint_rollout_vjp_with_corrections_dot_product():
+    """The joint rollout's reverse mode with the velocity's temporal correction
+    (k_c = 2, four steps): the dot product with a finite-difference JVP through
+    ``rollout_scalar`` in the initial velocity and scalar."""
+    from oracle import train as T
+
+    p = O.Problem(**GRIDS["ns16x8"])
+    kc = 2
+    mdl = narrow_scalar_model(41)
+    mdl = O.LearnedModel(W_L=mdl.W_L, stencil=mdl.stencil, W_Ls=mdl.W_Ls, k_c=kc,
+                         tc=I.random_conv_stack(42, 2 * kc, 8, 2, last_scale=0.2))
+    U, S = joint_state(p, 43)
+    rng = np.random.default_rng(44)
+    n, D, eps = 4, 1e-3, 1e-3
+    lu = rng.standard_normal((n,) + U.shape)
+    ls = rng.standard_normal((n,) + S.shape)
+    dU, dS = O.project(rng.standard_normal(U.shape), p), rng.standard_normal(S.shape)
+
+    def f(t):
+        states, _ = T.rollout_scalar_states(U + t * dU, S + t * dS, p, D, n, mdl)
+        return sum(np.sum(states[k][0] * lu[k - 1]) + np.sum(states[k][1] * ls[k - 1]) for k in range(1, n + 1))
+
+    jv = (-f(2 * eps) + 8 * f(eps) - 8 * f(-eps) + f(-2 * eps)) / (12 * eps)
+    lu0, ls0, g = T.rollout_scalar_vjp(U, S, p, D, n, lu, ls, mdl)
+    rhs = np.sum(dU * lu0) + np.sum(dS * ls0)
+    assert abs(jv - rhs) <= 1e-9 * (abs(jv) + 1.0)
+    # the final states equal the forward rollout's
+    Un, Sn = OS.rollout_scalar(U, S, p, D, n, model=mdl)
+    states, _ = T.rollout_scalar_states(U, S, p, D, n, mdl)
+    assert np.abs(states[n][0] - Un).max() < 1e-13 and np.abs(states[n][1] - Sn).max() < 1e-13
+    # a correction-network weight by central differences
+    def loss(m):
+        st, _ = T.rollout_scalar_states(U, S, p, D, n, m)
+        return sum(np.sum(st[k][0] * lu[k - 1]) + np.sum(st[k][1] * ls[k - 1]) for k in range(1, n + 1))
+
+    idx = (1, 3, 0, 2)
+    def bump(s):
+        tc = [(W.copy(), b.copy()) for W, b in mdl.tc]
+        tc[0][0][idx] += s
+        return O.LearnedModel(W_L=mdl.W_L, stencil=mdl.stencil, W_Ls=mdl.W_Ls, k_c=kc, tc=tc)
+    fd = (loss(bump(eps)) - loss(bump(-eps))) / (2 * eps)
+    assert abs(fd - g["tc"][0][0][idx]) <= 1e-6 * max(1e-2, abs(fd))

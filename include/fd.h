@@ -382,6 +382,35 @@ fd_status fd_rollout_adjoint(fd_ctx* ctx, const void* u0, int32_t n_steps, int32
 fd_status fd_train_step(fd_ctx* ctx, const void* u0, const void* targets, int32_t n_steps, int32_t ckpt_every,
                         float* dparams, double* loss, void* stream);
 
+/* Reverse mode of one joint step of the velocity and the passive scalar (the
+ * step fd_rollout_scalar takes; shear flow, App. C.1). Given (u_in, s_in) and the
+ * cotangents (lam_u_out, lam_s_out) of (u', s'), computes (lam_u_in, lam_s_in) =
+ * the transposed Jacobian applied to them and, for a context built with
+ * scalar_learned = 1, accumulates the parameter gradient (W_L, W_Ls, the
+ * stencil network on (u, v, s)) into dparams (+=, may be NULL). The stage states
+ * are recomputed; the scalar's stages read the projected stage velocities, so
+ * every stage's velocity cotangent also collects the scalar flux's term; the
+ * scalar is not projected. u_in, lam_u_*: device float32 [batch][2][ny][nx];
+ * s_in, lam_s_*: [batch][ny][nx]; the outputs may alias the cotangents.
+ * Scope: FP32 contexts of the generic-grid path, plain or with scalar_learned
+ * (FD_EUNSUPPORTED otherwise); FD_EINVAL for null pointers, a negative or
+ * non-finite diffusivity, dparams on a plain context or parameters not set.
+ * The first call allocates its workspace. */
+fd_status fd_step_adjoint_scalar(fd_ctx* ctx, double diffusivity, const void* u_in, const void* s_in,
+                                 const void* lam_u_out, const void* lam_s_out, void* lam_u_in, void* lam_s_in,
+                                 float* dparams, void* stream);
+
+/* One training step of a model that learns the scalar: the joint rollout of
+ * n_steps from (u0, s0) (with the velocity's temporal correction every k_c
+ * steps) against targets_u[n][batch][2][ny][nx] and targets_s[n][batch][ny][nx]
+ * by the mean squared error over every step, trajectory and element of the
+ * velocity and the scalar together; *loss (device double) receives it, dparams
+ * accumulates its gradient. Checkpointing as in fd_rollout_adjoint (ckpt_every
+ * a multiple of k_c). Needs scalar_learned = 1 (FD_EUNSUPPORTED otherwise). */
+fd_status fd_train_step_scalar(fd_ctx* ctx, double diffusivity, const void* u0, const void* s0, const void* targets_u,
+                               const void* targets_s, int32_t n_steps, int32_t ckpt_every, float* dparams,
+                               double* loss, void* stream);
+
 /* *loss = mean((pred - target)^2) over `count` float32 device elements (FP64
  * accumulation, fixed reduction order: deterministic); when grad is non-NULL,
  * grad = 2 (pred - target) / count. Uses the context's workspace. */

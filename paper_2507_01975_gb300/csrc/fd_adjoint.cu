@@ -699,6 +699,19 @@ fd_status fd_step_adjoint(fd_ctx* c, const void* u_in, const void* lam_out, void
   return FD_OK;
 }
 
+fd_status fd_step_adjoint_scalar(fd_ctx* c, double diffusivity, const void* u_in, const void* s_in,
+                                 const void* lam_u_out, const void* lam_s_out, void* lam_u_in, void* lam_s_in,
+                                 float* dparams, void* stream) {
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_step_adjoint_scalar: null context");
+  c->launches = 0;
+  if (!u_in || !s_in || !lam_u_out || !lam_s_out || !lam_u_in || !lam_s_in)
+    return fd_set_error(c, FD_EINVAL, "fd_step_adjoint_scalar: null pointer");
+  return fd_gadjoint_step_scalar(c, diffusivity, static_cast<const float*>(u_in), static_cast<const float*>(s_in),
+                                 static_cast<const float*>(lam_u_out), static_cast<const float*>(lam_s_out),
+                                 static_cast<float*>(lam_u_in), static_cast<float*>(lam_s_in), dparams,
+                                 static_cast<cudaStream_t>(stream));
+}
+
 fd_status fd_tc_adjoint(fd_ctx* c, const void* hist, const void* lam, void* vbar, void* hist_bar, float* dparams,
                         void* stream) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_tc_adjoint: null context");

@@ -153,6 +153,11 @@ struct TrainState {
   float* pend = nullptr;       // k_c history cotangents of the temporal correction
   size_t ncorr = 0;
   int nckpt = 0, nseg = 0;
+  // the passive scalar's checkpoints, segment and cotangent (joint training)
+  float* ckpt_s = nullptr;
+  float* seg_s = nullptr;
+  float* lam_s = nullptr;
+  int nckpt_s = 0, nseg_s = 0;
 };
 
 }  // namespace ldfv
@@ -245,6 +250,23 @@ struct GenAdjoint {
   size_t npart = 0;                 // floats in part
   double* sums = nullptr;           // [240] channel sums
   const float** d_hist = nullptr;   // [8] history pointers of the correction network
+  int kbuf_ch = 0;                  // channels of kbuf (160; 240 once the joint reverse mode ran)
+  // joint velocity-scalar reverse mode (allocated by its first call): the scalar
+  // stage states, face values and their cotangents, the scalar cotangents, the
+  // network input's three-channel cotangent, and the stage-state pointer tables
+  bool joint = false;
+  float* z[4] = {};                 // z[1..3]: scalar stage states [batch][ny][nx]
+  float* sacc = nullptr;
+  float* sinst = nullptr;           // [batch][4][ny][nx]
+  float* svbar = nullptr;           // [batch][4][ny][nx]
+  float* zbar = nullptr;            // scalar stage-state cotangent
+  float* qb = nullptr;              // scalar tendency cotangent
+  float* ys = nullptr;              // the previous stage's scalar cotangent
+  float* lams = nullptr;            // accumulated scalar input cotangent
+  float* ls0 = nullptr;             // copy of the scalar output cotangent
+  float* x3 = nullptr;              // [batch][3][ny][nx] network-input cotangent
+  const float** d_wptr = nullptr;   // [4] velocity stage states
+  const float** d_zptr = nullptr;   // [4] scalar stage states
 };
 }  // namespace ldfv
 
@@ -332,9 +354,18 @@ fd_status fd_gadjoint_step(fd_ctx* c, const float* u_in, const float* lam_out, f
                            cudaStream_t st);
 fd_status fd_gadjoint_tc(fd_ctx* c, const float* const* hist_host, const float* lam, float* vbar, float* hist_bar,
                          size_t state_stride, float* dparams, cudaStream_t st, int* launches);
+// reverse mode of one joint velocity-scalar step (fd_rollout_scalar's step)
+fd_status fd_gadjoint_step_scalar(fd_ctx* c, double diff, const float* u_in, const float* s_in, const float* lam_u_out,
+                                  const float* lam_s_out, float* lam_u_in, float* lam_s_in, float* dparams,
+                                  cudaStream_t st);
 void fd_gadjoint_free(fd_ctx* c);
+// traj_u / traj_s (optional, both or neither): the states after every step, [n_steps][...]
 fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, const void* s0, void* u_final,
-                                     void* s_final, int n_steps, cudaStream_t st);
+                                     void* s_final, int n_steps, cudaStream_t st, void* traj_u = nullptr,
+                                     void* traj_s = nullptr);
+// the joint rollout behind fd_rollout_scalar, optionally keeping every step's states
+fd_status fd_rollout_scalar_impl(fd_ctx* c, double diffusivity, const void* u0, const void* s0, void* u_final,
+                                 void* s_final, int n_steps, cudaStream_t st, void* traj_u, void* traj_s);
 
 // persistent mixed-batch rollout (fd_mixed.cu)
 bool fd_mixed_eligible(const fd_ctx* c);

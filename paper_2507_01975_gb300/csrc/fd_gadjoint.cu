@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -114,13 +115,14 @@ __device__ __forceinline__ void tap_offset(int pr, int r, int cc, int& dj, int& 
 
 // ubar[field](j, i) += sum over the field's instances q and taps t of
 // K_q,t(f) vbar_q(f) at the face f = (j - dj_t, i - di_t) whose tap t reads (j, i)
-__global__ void __launch_bounds__(256) gscatter_kernel(const float* K, const float* vbar, float* ubar, int nx, int ny) {
+__global__ void __launch_bounds__(256) gscatter_kernel(const float* K, const float* vbar, float* ubar, int nx, int ny,
+                                                       int ncoef) {
   const int hw = nx * ny;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= hw) return;
   const int b = blockIdx.y;
   const int j = p / nx, i = p - j * nx;
-  const float* Kb = K + (size_t)b * kNCoef * hw;
+  const float* Kb = K + (size_t)b * ncoef * hw;
   const float* Vb = vbar + (size_t)b * 8 * hw;
 #pragma unroll 1
   for (int fld = 0; fld < 2; ++fld) {
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(256) gscatter_kernel(const float* K, const flo
 // network-output cotangent: Cbar_q,t(f) = scale proj(vbar_q(f) taps(f))_t
 // (ablation 1: without the projection)
 __global__ void __launch_bounds__(256) gkbar_kernel(const float* w, const float* vbar, float* cbar, int nx, int ny,
-                                                    int ablation, float idx, float idy) {
+                                                    int ablation, float idx, float idy, int ncoef) {
   const int hw = nx * ny;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= hw) return;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256) gkbar_kernel(const float* w, const float*
       sc *= pk * (1.0f / 25.0f);
       sr *= pk * (1.0f / 40.0f);
       const float scale = kind == 1 ? ih : 1.0f;
-      float* out = cbar + ((size_t)b * kNCoef + q * 20) * hw + p;
+      float* out = cbar + ((size_t)b * ncoef + q * 20) * hw + p;
 #pragma unroll
       for (int r = 0; r < 5; ++r)
 #pragma unroll
@@ -211,6 +213,7 @@ struct GWgradArgs {
   const float* zbar;          // [batch][cout][ny][nx]
   const float* in;            // [batch][cin][ny][nx]
   const float* const* hist;   // or cin / 2 states [batch][2][ny][nx]
+  const float* const* sptr;   // with hist: the last channel, a scalar [batch][ny][nx]
   float* part;                // [nchunk][cout][cin][9]
   int cin, cout, nx, ny, in_gelu;
   long long total;            // batch * nx * ny
@@ -251,8 +254,9 @@ __global__ void __launch_bounds__(256) gwgrad_kernel(const GWgradArgs a) {
         const int y = p / a.nx, x = p - y * a.nx;
         const int yy = (y + tap / 3 - 1 + a.ny) % a.ny, xx = (x + tap % 3 - 1 + a.nx) % a.nx;
         const int ch = c0 + c;
-        const float* src = a.hist ? a.hist[ch >> 1] + ((size_t)b * 2 + (ch & 1)) * hw
-                                  : a.in + ((size_t)b * a.cin + ch) * hw;
+        const float* src = !a.hist                        ? a.in + ((size_t)b * a.cin + ch) * hw
+                           : (a.sptr && ch == a.cin - 1) ? a.sptr[0] + (size_t)b * hw
+                                                         : a.hist[ch >> 1] + ((size_t)b * 2 + (ch & 1)) * hw;
         v = src[yy * a.nx + xx];
         if (a.in_gelu) v = gelu_exact(v);
       }
@@ -314,14 +318,143 @@ __global__ void __launch_bounds__(256) chansum_kernel(const float* t, int C, int
 }
 
 // bias gradient: dst[o] += sums[o]; with wl: also W_L[kind][axis][t] += the
-// sums of the two instances (u and v) that share it
-__global__ void add_sums_kernel(const double* sums, int C, float* dst, float* wl) {
+// sums of the two instances (u and v) that share it; with wls: W_Ls[kind][axis][t]
+// += the sum of the scalar instance m = 2 axis + kind
+__global__ void add_sums_kernel(const double* sums, int C, float* dst, float* wl, float* wls) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < C) dst[k] += (float)sums[k];
-  if (wl && k < 80) {
+  if (k < 80) {
     const int kind = k / 40, axis = (k / 20) % 2, t = k % 20;
-    const int q1 = 2 * axis + kind, q2 = 2 * (2 + axis) + kind;
-    wl[k] += (float)(sums[q1 * 20 + t] + sums[q2 * 20 + t]);
+    if (wl) {
+      const int q1 = 2 * axis + kind, q2 = 2 * (2 + axis) + kind;
+      wl[k] += (float)(sums[q1 * 20 + t] + sums[q2 * 20 + t]);
+    }
+    if (wls) wls[k] += (float)sums[kNCoef + (2 * axis + kind) * 20 + t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the passive scalar's reverse mode: tendency -div(u s_f - D grad_f s) with
+// F_x = u s_x - D g_x on the west faces and F_y = v s_y - D g_y on the south faces
+// ---------------------------------------------------------------------------
+// face cotangents of the four scalar instances from the scalar tendency
+// cotangent qb, and the velocity's direct terms (F_x, F_y are products with u, v)
+__global__ void __launch_bounds__(256) gsvbar_kernel(const float* qb, const float* sinst, const float* w, float* svbar,
+                                                     float* ubar, int nx, int ny, float idx, float idy, float diff) {
+  const int hw = nx * ny;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= hw) return;
+  const int b = blockIdx.y;
+  const int j = p / nx, i = p - j * nx;
+  const float* q = qb + (size_t)b * hw;
+  const float fxb = (q[p] - q[j * nx + (i - 1 + nx) % nx]) * idx;
+  const float fyb = (q[p] - q[((j - 1 + ny) % ny) * nx + i]) * idy;
+  const float* SI = sinst + (size_t)b * 4 * hw;
+  const size_t e = (size_t)b * 2 * hw + p;
+  ubar[e] += fxb * SI[p];
+  ubar[e + hw] += fyb * SI[2 * hw + p];
+  float* V = svbar + (size_t)b * 4 * hw + p;
+  V[0] = fxb * w[e];
+  V[hw] = -diff * fxb;
+  V[2 * (size_t)hw] = fyb * w[e + hw];
+  V[3 * (size_t)hw] = -diff * fyb;
+}
+
+// the scalar instance m = 2 axis + kind reads s at (j + dj, i + di) for tap (r, c)
+__device__ __forceinline__ void scalar_tap_offset(int axis, int r, int cc, int& dj, int& di) {
+  dj = axis == 0 ? r - 2 : cc - 2;
+  di = axis == 0 ? cc - 2 : r - 2;
+}
+
+// zbar(j, i) = sum over the scalar instances m and taps t of K_m,t(f) svbar_m(f)
+// at the face f whose tap t reads (j, i); K at channel 160 + 20 m + t
+__global__ void __launch_bounds__(256) gsscatter_kernel(const float* K, const float* svbar, float* zbar, int nx, int ny,
+                                                        int ncoef) {
+  const int hw = nx * ny;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= hw) return;
+  const int b = blockIdx.y;
+  const int j = p / nx, i = p - j * nx;
+  const float* Kb = K + ((size_t)b * ncoef + kNCoef) * hw;
+  const float* Vb = svbar + (size_t)b * 4 * hw;
+  float acc = 0.f;
+#pragma unroll 1
+  for (int axis = 0; axis < 2; ++axis)
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        int dj, di;
+        scalar_tap_offset(axis, r, cc, dj, di);
+        const int f = ((j - dj + 2 * ny) % ny) * nx + (i - di + 2 * nx) % nx;
+#pragma unroll
+        for (int kind = 0; kind < 2; ++kind) {
+          const int m = 2 * axis + kind;
+          acc = fmaf(Kb[(size_t)(m * 20 + r * 4 + cc) * hw + f], Vb[(size_t)m * hw + f], acc);
+        }
+      }
+  zbar[(size_t)b * hw + p] = acc;
+}
+
+// the scalar instances' network-output cotangent: scale proj(svbar_m(f) taps(f))
+// into channels 160 + 20 m + t
+__global__ void __launch_bounds__(256) gskbar_kernel(const float* z, const float* svbar, float* cbar, int nx, int ny,
+                                                     float idx, float idy, int ncoef) {
+  const int hw = nx * ny;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= hw) return;
+  const int b = blockIdx.y;
+  const int j = p / nx, i = p - j * nx;
+  const float cval[4] = {-1.5f, -0.5f, 0.5f, 1.5f};
+  const float* f = z + (size_t)b * hw;
+#pragma unroll 1
+  for (int axis = 0; axis < 2; ++axis) {
+    float tap[20];
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        int dj, di;
+        scalar_tap_offset(axis, r, cc, dj, di);
+        tap[r * 4 + cc] = f[((j + dj + 2 * ny) % ny) * nx + (i + di + 2 * nx) % nx];
+      }
+    const float ih = axis == 0 ? idx : idy;
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const int m = 2 * axis + kind;
+      const float vb = svbar[((size_t)b * 4 + m) * hw + p];
+      float s1 = 0.f, sc = 0.f, sr = 0.f;
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const float v = vb * tap[r * 4 + cc];
+          s1 += v;
+          sc += v * cval[cc];
+          sr += v * (float)(r - 2);
+        }
+      s1 *= 1.0f / 20.0f;
+      sc *= 1.0f / 25.0f;
+      sr *= 1.0f / 40.0f;
+      const float scale = kind == 1 ? ih : 1.0f;
+      float* out = cbar + ((size_t)b * ncoef + kNCoef + m * 20) * hw + p;
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+          out[(size_t)(r * 4 + cc) * hw] = (vb * tap[r * 4 + cc] - s1 - sc * cval[cc] - sr * (float)(r - 2)) * scale;
+    }
+  }
+}
+
+// the network input's cotangent (u, v, s) split into the state cotangents
+__global__ void split_add_kernel(const float* x3, float* ubar, float* zbar, int hw, int batch) {
+  const size_t n = (size_t)batch * hw;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = k / hw, p = k - b * hw;
+    ubar[b * 2 * hw + p] += x3[b * 3 * hw + p];
+    ubar[b * 2 * hw + hw + p] += x3[b * 3 * hw + hw + p];
+    zbar[k] += x3[b * 3 * hw + 2 * hw + p];
   }
 }
 
@@ -386,7 +519,7 @@ cudaError_t refresh_wt(Ctx& x) {
   if (x.A.wt_version == G.version) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < 6 && e == cudaSuccess; ++l) {
-    const int ci = stencil_cin(l, false), co = stencil_cout(l, false);
+    const int ci = stencil_cin(l, G.scalar), co = stencil_cout(l, G.scalar);
     transpose_weights_kernel<<<grid1((size_t)co * ci * 9), 256, 0, x.st>>>(G.d_params + G.off_sw[l],
                                                                           x.A.wt + x.A.off_wt_s[l], co, ci);
     e = last(x);
@@ -402,8 +535,9 @@ cudaError_t refresh_wt(Ctx& x) {
 }
 
 // dparams[off_w ..] += the weight gradient of a layer, dparams[off_b ..] += its bias gradient
-cudaError_t layer_param_grads(Ctx& x, const float* zbar, const float* in, const float* const* hist, int in_gelu,
-                              int cin, int cout, float* dw, float* db, float* dwl) {
+cudaError_t layer_param_grads(Ctx& x, const float* zbar, const float* in, const float* const* hist,
+                              const float* const* sptr, int in_gelu, int cin, int cout, float* dw, float* db,
+                              float* dwl, float* dwls) {
   const long long total = (long long)x.B * x.hw;
   const int ob = (cout + kWgO - 1) / kWgO, cb = (cin + kWgC - 1) / kWgC;
   // about four CTAs per SM in all, within the partial-sum buffer
@@ -417,6 +551,7 @@ cudaError_t layer_param_grads(Ctx& x, const float* zbar, const float* in, const 
   a.zbar = zbar;
   a.in = in;
   a.hist = hist;
+  a.sptr = sptr;
   a.part = x.A.part;
   a.cin = cin;
   a.cout = cout;
@@ -437,7 +572,7 @@ cudaError_t layer_param_grads(Ctx& x, const float* zbar, const float* in, const 
     e = last(x);
   }
   if (e == cudaSuccess) {
-    add_sums_kernel<<<1, 256, 0, x.st>>>(x.A.sums, cout, db, dwl);
+    add_sums_kernel<<<1, 256, 0, x.st>>>(x.A.sums, cout, db, dwl, dwls);
     e = last(x);
   }
   return e;
@@ -470,15 +605,16 @@ cudaError_t layer_data_grad(Ctx& x, const float* zbar, const float* wt, int cin,
 // the input cotangent goes to xout (accumulated into a [batch][2][ny][nx]
 // state, or written per history state with ostride)
 cudaError_t net_backward(Ctx& x, float* zbar5, int cout5, int cin0, const float* in0, const float* const* hist,
-                         const size_t* off_w, const size_t* off_b, const size_t* off_wt, float* dparams,
-                         float* dwl, float* xout, int xaccum, size_t xstride) {
+                         const float* const* sptr, const size_t* off_w, const size_t* off_b, const size_t* off_wt,
+                         float* dparams, float* dwl, float* dwls, float* xout, int xaccum, size_t xstride) {
   cudaError_t e = cudaSuccess;
   const float* zbar = zbar5;
   for (int l = 5; l >= 0 && e == cudaSuccess; --l) {
     const int cin = l == 0 ? cin0 : kHid, cout = l == 5 ? cout5 : kHid;
     if (dparams)
-      e = layer_param_grads(x, zbar, l == 0 ? in0 : x.A.zsave[l - 1], l == 0 ? hist : nullptr, l > 0, cin, cout,
-                            dparams + off_w[l], dparams + off_b[l], l == 5 ? dwl : nullptr);
+      e = layer_param_grads(x, zbar, l == 0 ? in0 : x.A.zsave[l - 1], l == 0 ? hist : nullptr,
+                            l == 0 ? sptr : nullptr, l > 0, cin, cout, dparams + off_w[l], dparams + off_b[l],
+                            l == 5 ? dwl : nullptr, l == 5 ? dwls : nullptr);
     if (e != cudaSuccess) break;
     if (l > 0) {
       float* out = x.A.zb[l & 1];
@@ -573,16 +709,16 @@ cudaError_t tendency_vjp(Ctx& x, const float* w, const float* T, bool learned, f
   gvbar_kernel<<<cells, 256, 0, x.st>>>(va);
   e = last(x);
   if (e == cudaSuccess) {
-    gscatter_kernel<<<cells, 256, 0, x.st>>>(x.A.kbuf, x.A.vbar, x.A.ubar, x.nx, x.ny);
+    gscatter_kernel<<<cells, 256, 0, x.st>>>(x.A.kbuf, x.A.vbar, x.A.ubar, x.nx, x.ny, kNCoef);
     e = last(x);
   }
   if (e != cudaSuccess || !learned) return e;
   // the network-output cotangent replaces the per-face kernels in A.kbuf
-  gkbar_kernel<<<cells, 256, 0, x.st>>>(w, x.A.vbar, x.A.kbuf, x.nx, x.ny, G->ablation, va.idx, va.idy);
+  gkbar_kernel<<<cells, 256, 0, x.st>>>(w, x.A.vbar, x.A.kbuf, x.nx, x.ny, G->ablation, va.idx, va.idy, kNCoef);
   e = last(x);
   if (e == cudaSuccess)
-    e = net_backward(x, x.A.kbuf, kNCoef, 2, w, nullptr, G->off_sw, G->off_sb, x.A.off_wt_s, dparams,
-                     dparams ? dparams + G->off_wl : nullptr, x.A.ubar, 1, 0);
+    e = net_backward(x, x.A.kbuf, kNCoef, 2, w, nullptr, nullptr, G->off_sw, G->off_sb, x.A.off_wt_s, dparams,
+                     dparams ? dparams + G->off_wl : nullptr, nullptr, x.A.ubar, 1, 0);
   return e;
 }
 
@@ -599,6 +735,7 @@ fd_status gadjoint_alloc(fd_ctx* c) {
   for (int s = 1; s < 4; ++s) alloc((void**)&A->w[s], st);
   for (float** p : {&A->acc, &A->ubar, &A->g, &A->y, &A->rb, &A->lam}) alloc((void**)p, st);
   alloc((void**)&A->kbuf, B * kNCoef * hw * sizeof(float));
+  A->kbuf_ch = kNCoef;
   alloc((void**)&A->inst, B * 8 * hw * sizeof(float));
   alloc((void**)&A->vbar, B * 8 * hw * sizeof(float));
   if (c->glrn) {
@@ -608,7 +745,7 @@ fd_status gadjoint_alloc(fd_ctx* c) {
     size_t off = 0;
     for (int l = 0; l < 6; ++l) {
       A->off_wt_s[l] = off;
-      off += (size_t)stencil_cin(l, false) * stencil_cout(l, false) * 9;
+      off += (size_t)stencil_cin(l, G.scalar) * stencil_cout(l, G.scalar) * 9;
     }
     for (int l = 0; l < 6 && G.kc > 0; ++l) {
       A->off_wt_t[l] = off;
@@ -628,6 +765,161 @@ fd_status gadjoint_alloc(fd_ctx* c) {
     return fd_set_error(c, FD_ENOMEM, "generic-grid reverse mode workspace: %s", cudaGetErrorString(e));
   }
   return FD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// joint velocity-scalar reverse mode
+// ---------------------------------------------------------------------------
+fd_status gadjoint_alloc_joint(fd_ctx* c) {
+  GenAdjoint& A = *c->gadj;
+  const size_t hw = (size_t)c->grid.nx * c->grid.ny, B = c->grid.batch;
+  const size_t sb = B * hw * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  // the per-face kernels of the scalar's instances sit in channels 160 .. 239
+  if (A.kbuf_ch < kNCoefScalar) {
+    cudaFree(A.kbuf);
+    A.kbuf = nullptr;
+    alloc((void**)&A.kbuf, B * kNCoefScalar * hw * sizeof(float));
+    A.kbuf_ch = e == cudaSuccess ? kNCoefScalar : 0;
+  }
+  for (int s = 1; s < 4; ++s) alloc((void**)&A.z[s], sb);
+  for (float** p : {&A.sacc, &A.zbar, &A.qb, &A.ys, &A.lams, &A.ls0}) alloc((void**)p, sb);
+  alloc((void**)&A.sinst, 4 * sb);
+  alloc((void**)&A.svbar, 4 * sb);
+  alloc((void**)&A.x3, 3 * sb);
+  alloc((void**)&A.d_wptr, 4 * sizeof(const float*));
+  alloc((void**)&A.d_zptr, 4 * sizeof(const float*));
+  if (e != cudaSuccess) return fd_set_error(c, FD_ENOMEM, "joint reverse mode workspace: %s", cudaGetErrorString(e));
+  A.joint = true;
+  return FD_OK;
+}
+
+// face values of velocity and scalar at stage s (and, with want_k, the per-face
+// kernels over the network output in A.kbuf)
+cudaError_t faces_joint(Ctx& x, int s, const float* w, const float* z, bool learned, bool want_k) {
+  GenericLearned* G = x.c->glrn;
+  GFaceArgs fa = {};
+  fa.w = w;
+  fa.coef = learned ? x.A.kbuf : nullptr;
+  fa.wl = learned ? G->d_params + G->off_wl : nullptr;
+  fa.wls = learned ? G->d_params + G->off_wls : nullptr;
+  fa.inst = x.A.inst;
+  fa.kout = want_k ? x.A.kbuf : nullptr;
+  fa.skout = want_k ? x.A.kbuf : nullptr;
+  fa.s = z;
+  fa.sinst = x.A.sinst;
+  fa.nx = x.nx;
+  fa.ny = x.ny;
+  fa.dord = x.c->opts.deriv_order;
+  fa.ablation = 0;
+  fa.ncoef = kNCoefScalar;
+  fa.idx = (float)(x.nx / x.c->grid.lx);
+  fa.idy = (float)(x.ny / x.c->grid.ly);
+  (void)s;
+  gface_kernel<<<dim3((unsigned)((x.hw + 255) / 256), (unsigned)x.B), 256, 0, x.st>>>(fa);
+  return last(x);
+}
+
+// the stencil network on (w_s, z_s) through the stage pointer tables into A.kbuf
+cudaError_t net_joint(Ctx& x, int s, float* const* zsave) {
+  GenericLearned& G = *x.c->glrn;
+  x.launches += 6;
+  return run_net(x.c, x.A.d_wptr + s, x.A.d_zptr + s, nullptr, 3, G.off_sw, G.off_sb, kNCoefScalar, x.A.kbuf, x.st,
+                 zsave);
+}
+
+// (w_{s+1}, z_{s+1}) from (w_s, z_s) for the forward stages s = 0, 1, 2
+cudaError_t stage_forward_joint(Ctx& x, int s, const float* w, const float* z, const float* u, const float* sn,
+                                float* w_out, float* z_out, bool learned, float diff) {
+  GenericState& S = *x.c->gen;
+  cudaError_t e = learned ? net_joint(x, s, nullptr) : cudaSuccess;
+  if (e == cudaSuccess) e = faces_joint(x, s, w, z, learned, false);
+  if (e != cudaSuccess) return e;
+  GStageArgs sa = {};
+  sa.inst = x.A.inst;
+  sa.w = w;
+  sa.un = u;
+  sa.acc = x.A.acc;
+  sa.wout = w_out;
+  sa.frc = static_cast<const float*>(S.frc);
+  sa.sinst = x.A.sinst;
+  sa.sn = sn;
+  sa.sacc = x.A.sacc;
+  sa.sout = z_out;
+  sa.diff = diff;
+  sa.nx = x.nx;
+  sa.ny = x.ny;
+  sa.stage = s;
+  sa.forced = x.c->forcing.kind;
+  sa.burgers = x.c->grid.flow == FD_BURGERS;
+  sa.dt = (float)x.c->dt;
+  sa.nu = (float)x.c->nu;
+  sa.idx = (float)(x.nx / x.c->grid.lx);
+  sa.idy = (float)(x.ny / x.c->grid.ly);
+  sa.drag = (float)(x.c->forcing.kind == 1 ? x.c->forcing.drag : 0.0);
+  gstage_kernel<<<dim3((unsigned)((x.hw + 255) / 256), (unsigned)x.B), 256, 0, x.st>>>(sa);
+  e = last(x);
+  if (e == cudaSuccess) e = project(x, w_out);
+  return e;
+}
+
+// (A.ubar, A.zbar) = the transposed joint tendency at stage s applied to (rb, qb)
+cudaError_t joint_tendency_vjp(Ctx& x, int s, const float* w, const float* z, const float* rb, const float* qb,
+                               bool learned, float diff, float* dparams) {
+  GenericLearned* G = x.c->glrn;
+  const dim3 cells((unsigned)((x.hw + 255) / 256), (unsigned)x.B);
+  const float idx = (float)(x.nx / x.c->grid.lx), idy = (float)(x.ny / x.c->grid.ly);
+  cudaError_t e = learned ? net_joint(x, s, x.A.zsave) : cudaSuccess;
+  if (e == cudaSuccess) e = faces_joint(x, s, w, z, learned, true);
+  if (e != cudaSuccess) return e;
+  GVbarArgs va;
+  va.T = rb;
+  va.inst = x.A.inst;
+  va.w = w;
+  va.vbar = x.A.vbar;
+  va.ubar = x.A.ubar;
+  va.nx = x.nx;
+  va.ny = x.ny;
+  va.burgers = x.c->grid.flow == FD_BURGERS;
+  va.forced = x.c->forcing.kind == 1;
+  va.nu = (float)x.c->nu;
+  va.idx = idx;
+  va.idy = idy;
+  va.drag = (float)(x.c->forcing.kind == 1 ? x.c->forcing.drag : 0.0);
+  gvbar_kernel<<<cells, 256, 0, x.st>>>(va);
+  e = last(x);
+  if (e == cudaSuccess) {
+    gsvbar_kernel<<<cells, 256, 0, x.st>>>(qb, x.A.sinst, w, x.A.svbar, x.A.ubar, x.nx, x.ny, idx, idy, diff);
+    e = last(x);
+  }
+  if (e == cudaSuccess) {
+    gscatter_kernel<<<cells, 256, 0, x.st>>>(x.A.kbuf, x.A.vbar, x.A.ubar, x.nx, x.ny, kNCoefScalar);
+    e = last(x);
+  }
+  if (e == cudaSuccess) {
+    gsscatter_kernel<<<cells, 256, 0, x.st>>>(x.A.kbuf, x.A.svbar, x.A.zbar, x.nx, x.ny, kNCoefScalar);
+    e = last(x);
+  }
+  if (e != cudaSuccess || !learned) return e;
+  // the network-output cotangent of all twelve instances replaces the kernels
+  gkbar_kernel<<<cells, 256, 0, x.st>>>(w, x.A.vbar, x.A.kbuf, x.nx, x.ny, 0, idx, idy, kNCoefScalar);
+  e = last(x);
+  if (e == cudaSuccess) {
+    gskbar_kernel<<<cells, 256, 0, x.st>>>(z, x.A.svbar, x.A.kbuf, x.nx, x.ny, idx, idy, kNCoefScalar);
+    e = last(x);
+  }
+  if (e == cudaSuccess)
+    e = net_backward(x, x.A.kbuf, kNCoefScalar, 3, nullptr, x.A.d_wptr + s, x.A.d_zptr + s, G->off_sw, G->off_sb,
+                     x.A.off_wt_s, dparams, dparams ? dparams + G->off_wl : nullptr,
+                     dparams ? dparams + G->off_wls : nullptr, x.A.x3, 0, 0);
+  if (e == cudaSuccess) {
+    split_add_kernel<<<grid1((size_t)x.B * x.hw), 256, 0, x.st>>>(x.A.x3, x.A.ubar, x.A.zbar, x.hw, x.B);
+    e = last(x);
+  }
+  return e;
 }
 
 }  // namespace
@@ -748,9 +1040,95 @@ fd_status fd_gadjoint_tc(fd_ctx* c, const float* const* hist_host, const float* 
     x.launches += 6;
   }
   if (e == cudaSuccess)
-    e = net_backward(x, A.rb, 2, 2 * G->kc, nullptr, A.d_hist, G->off_tw, G->off_tb, A.off_wt_t, dparams, nullptr,
-                     hist_bar, 0, state_stride);
+    e = net_backward(x, A.rb, 2, 2 * G->kc, nullptr, A.d_hist, nullptr, G->off_tw, G->off_tb, A.off_wt_t, dparams,
+                     nullptr, nullptr, hist_bar, 0, state_stride);
   *launches += x.launches;
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_tc_adjoint (generic grid): %s", cudaGetErrorString(e));
+  return FD_OK;
+}
+
+fd_status fd_gadjoint_step_scalar(fd_ctx* c, double diff, const float* u_in, const float* s_in, const float* lam_u_out,
+                                  const float* lam_s_out, float* lam_u_in, float* lam_s_in, float* dparams,
+                                  cudaStream_t st) {
+  const char* who = "fd_step_adjoint_scalar";
+  if (!c->gen)
+    return fd_set_error(c, FD_EUNSUPPORTED, "%s: the passive scalar runs on the generic-grid path (path 3)", who);
+  if (c->grid.dtype != FD_F32) return fd_set_error(c, FD_EUNSUPPORTED, "%s: built for FP32", who);
+  GenericLearned* G = c->glrn;
+  if (G && !G->scalar)
+    return fd_set_error(c, FD_EUNSUPPORTED, "%s: the learned model does not read the scalar (scalar_learned = 0)", who);
+  if (G && !G->ready) return fd_set_error(c, FD_EINVAL, "%s: learned parameters not set (fd_set_params)", who);
+  if (dparams && !G) return fd_set_error(c, FD_EINVAL, "%s: dparams needs a learned context", who);
+  if (!(diff >= 0) || !std::isfinite(diff)) return fd_set_error(c, FD_EINVAL, "%s: the diffusivity must be >= 0", who);
+  if (!c->gadj) {
+    const fd_status r = gadjoint_alloc(c);
+    if (r != FD_OK) return r;
+  }
+  if (!c->gadj->joint) {
+    const fd_status r = gadjoint_alloc_joint(c);
+    if (r != FD_OK) return r;
+  }
+  Ctx x{c, *c->gadj, st};
+  x.B = c->grid.batch;
+  x.nx = c->grid.nx;
+  x.ny = c->grid.ny;
+  x.hw = x.nx * x.ny;
+  x.slot = (size_t)x.B * 2 * x.hw;
+  const size_t sslot = (size_t)x.B * x.hw;
+  GenAdjoint& A = x.A;
+  const bool learned = G != nullptr;
+  const float dt = (float)c->dt, fd = (float)diff;
+  const float* w[4] = {u_in, A.w[1], A.w[2], A.w[3]};
+  const float* z[4] = {s_in, A.z[1], A.z[2], A.z[3]};
+  cudaError_t e = learned ? refresh_wt(x) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.d_wptr, w, sizeof w, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.d_zptr, z, sizeof z, cudaMemcpyHostToDevice, st);
+  // forward: the stage states (w_s, z_s), s = 1, 2, 3
+  for (int s = 0; s < 3 && e == cudaSuccess; ++s)
+    e = stage_forward_joint(x, s, w[s], z[s], u_in, s_in, A.w[s + 1], A.z[s + 1], learned, fd);
+  // reverse: g = P(lam_u_out); the scalar is not projected
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.g, lam_u_out, x.slot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = project(x, A.g);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.lam, A.g, x.slot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.ls0, lam_s_out, sslot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.lams, lam_s_out, sslot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  const float cg[4] = {dt / 6.0f, dt / 3.0f, dt / 3.0f, dt / 6.0f};
+  const float cy[4] = {0.5f * dt, 0.5f * dt, dt, 0.0f};
+  for (int s = 3; s >= 0 && e == cudaSuccess; --s) {
+    // tendency cotangents: cg g + cy P(wbar_{s+1}) and cg lam_s + cy zbar_{s+1}
+    if (s == 3) {
+      axpby_kernel<<<grid1(x.slot), 256, 0, st>>>(A.rb, A.g, cg[3], 0.0f, x.slot);
+      axpby_kernel<<<grid1(sslot), 256, 0, st>>>(A.qb, A.ls0, cg[3], 0.0f, sslot);
+    } else {
+      axpby_kernel<<<grid1(x.slot), 256, 0, st>>>(A.y, A.g, cg[s], cy[s], x.slot);  // y <- cg g + cy y
+      axpby_kernel<<<grid1(sslot), 256, 0, st>>>(A.ys, A.ls0, cg[s], cy[s], sslot);
+    }
+    e = last(x);
+    if (e == cudaSuccess) e = last(x);
+    if (e != cudaSuccess) break;
+    const float* rb = s == 3 ? A.rb : A.y;
+    const float* qb = s == 3 ? A.qb : A.ys;
+    e = joint_tendency_vjp(x, s, w[s], z[s], rb, qb, learned, fd, dparams);
+    if (e != cudaSuccess) break;
+    // the scalar stage state's cotangent passes unprojected; the velocity's through P
+    axpby_kernel<<<grid1(sslot), 256, 0, st>>>(A.lams, A.zbar, 1.0f, 1.0f, sslot);
+    e = last(x);
+    if (e == cudaSuccess && s > 0) {
+      e = cudaMemcpyAsync(A.y, A.ubar, x.slot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = project(x, A.y);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(A.ys, A.zbar, sslot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) {
+        axpby_kernel<<<grid1(x.slot), 256, 0, st>>>(A.lam, A.y, 1.0f, 1.0f, x.slot);
+        e = last(x);
+      }
+    } else if (e == cudaSuccess) {
+      axpby_kernel<<<grid1(x.slot), 256, 0, st>>>(A.lam, A.ubar, 1.0f, 1.0f, x.slot);
+      e = last(x);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lam_u_in, A.lam, x.slot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lam_s_in, A.lams, sslot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  c->launches = x.launches;
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "%s: %s", who, cudaGetErrorString(e));
   return FD_OK;
 }

@@ -551,6 +551,14 @@ extern "C" {
 
 fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const void* s0, void* u_final,
                             void* s_final, int32_t n_steps, void* stream) {
+  return fd_rollout_scalar_impl(c, diffusivity, u0, s0, u_final, s_final, n_steps, static_cast<cudaStream_t>(stream),
+                                nullptr, nullptr);
+}
+
+}  // extern "C"
+
+fd_status fd_rollout_scalar_impl(fd_ctx* c, double diffusivity, const void* u0, const void* s0, void* u_final,
+                                 void* s_final, int n_steps, cudaStream_t st, void* traj_u, void* traj_s) {
   if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_rollout_scalar: null context");
   c->launches = 0;
   if (!c->gen)
@@ -559,8 +567,7 @@ fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const
   if (n_steps < 0) return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: n_steps must be >= 0");
   if (!(diffusivity >= 0) || !std::isfinite(diffusivity))
     return fd_set_error(c, FD_EINVAL, "fd_rollout_scalar: the diffusivity must be >= 0");
-  if (c->glrn)
-    return fd_glearned_rollout_scalar(c, diffusivity, u0, s0, u_final, s_final, n_steps, static_cast<cudaStream_t>(stream));
+  if (c->glrn) return fd_glearned_rollout_scalar(c, diffusivity, u0, s0, u_final, s_final, n_steps, st, traj_u, traj_s);
   GenericState& S = *c->gen;
   const fd_grid& g = c->grid;
   const size_t sbytes = (size_t)g.batch * g.nx * g.ny * (g.dtype == FD_F64 ? sizeof(double) : sizeof(float));
@@ -577,7 +584,6 @@ fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const
       return fd_set_error(c, FD_ENOMEM, "fd_rollout_scalar: cudaMalloc: %s", cudaGetErrorString(e));
     }
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = fd_state_bytes(g);
   e = cudaMemcpyAsync(S.un, u0, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S.sn, s0, sbytes, cudaMemcpyDeviceToDevice, st);
@@ -600,12 +606,17 @@ fd_status fd_rollout_scalar(fd_ctx* c, double diffusivity, const void* u0, const
     if (gr) cudaGraphDestroy(gr);
     S.sgraph_diff = e == cudaSuccess ? diffusivity : -1.0;
   }
-  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(S.sgraph, st);
+  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+    e = cudaGraphLaunch(S.sgraph, st);
+    if (e == cudaSuccess && traj_u) {
+      e = cudaMemcpyAsync(static_cast<char*>(traj_u) + (size_t)k * bytes, S.un, bytes, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char*>(traj_s) + (size_t)k * sbytes, S.sn, sbytes, cudaMemcpyDeviceToDevice, st);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, S.un, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s_final, S.sn, sbytes, cudaMemcpyDeviceToDevice, st);
   c->launches = (g.flow == FD_NAVIER_STOKES ? 4 * 5 : 4) * n_steps;
   if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "fd_rollout_scalar: %s", cudaGetErrorString(e));
   return FD_OK;
 }
-
-}  // extern "C"

@@ -329,7 +329,7 @@ fd_status fd_glearned_rollout(fd_ctx* c, const void* u0, void* traj, void* u_fin
 }
 
 fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, const void* s0, void* u_final,
-                                     void* s_final, int n_steps, cudaStream_t st) {
+                                     void* s_final, int n_steps, cudaStream_t st, void* traj_u, void* traj_s) {
   GenericState& S = *c->gen;
   GenericLearned& G = *c->glrn;
   if (!G.scalar)
@@ -351,8 +351,10 @@ fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, con
   const int per_step = launches_per_step(c), per_corr = G.kc > 0 ? 7 + (c->grid.flow == FD_NAVIER_STOKES ? 5 : 0) : 0;
   cudaError_t e = cudaMemcpyAsync(S.un, u0, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S.sn, s0, sbytes, cudaMemcpyDeviceToDevice, st);
-  // the diffusivity is a kernel argument: a graph captured with another one is replaced
-  if (e == cudaSuccess && n_steps >= grp && (!G.graph || G.graph_diff != diff)) {
+  // the diffusivity is a kernel argument: a graph captured with another one is
+  // replaced; a rollout that keeps every step's state runs its launches directly
+  const bool use_graph = !traj_u;
+  if (e == cudaSuccess && use_graph && n_steps >= grp && (!G.graph || G.graph_diff != diff)) {
     if (G.graph) {
       e = cudaStreamSynchronize(st);
       if (e == cudaSuccess) e = cudaGraphExecDestroy(G.graph);
@@ -371,7 +373,7 @@ fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, con
     G.graph_diff = e == cudaSuccess ? diff : -1.0;
   }
   int done = 0, launches = 0;
-  if (e == cudaSuccess && G.graph && G.graph_diff == diff) {
+  if (e == cudaSuccess && use_graph && G.graph && G.graph_diff == diff) {
     for (; done + grp <= n_steps && e == cudaSuccess; done += grp) {
       e = cudaGraphLaunch(G.graph, st);
       launches += grp * per_step + per_corr;
@@ -380,6 +382,13 @@ fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, con
   for (int k = done + 1; k <= n_steps && e == cudaSuccess; ++k) {
     e = step(k, st);
     launches += per_step + (G.kc > 0 && k % G.kc == 0 ? per_corr : 0);
+    if (e == cudaSuccess && traj_u) {
+      e = cudaMemcpyAsync(static_cast<char*>(traj_u) + (size_t)(k - 1) * bytes, S.un, bytes, cudaMemcpyDeviceToDevice,
+                          st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char*>(traj_s) + (size_t)(k - 1) * sbytes, S.sn, sbytes,
+                            cudaMemcpyDeviceToDevice, st);
+    }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(u_final, S.un, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s_final, S.sn, sbytes, cudaMemcpyDeviceToDevice, st);

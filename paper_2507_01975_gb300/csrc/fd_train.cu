@@ -305,12 +305,124 @@ fd_status rollout_reverse(fd_ctx* c, const float* u0, int n, int k, const float*
   return FD_OK;
 }
 
+// the scalar's part of the joint training workspace
+fd_status train_reserve_scalar(fd_ctx* c, int nseg, int seglen) {
+  TrainState& T = *c->trn;
+  const size_t sb = (size_t)c->grid.batch * c->grid.nx * c->grid.ny * sizeof(float);
+  if (!T.lam_s && cudaMalloc(&T.lam_s, sb) != cudaSuccess) {
+    T.lam_s = nullptr;
+    return fd_set_error(c, FD_ENOMEM, "training workspace: out of device memory");
+  }
+  if (nseg + 1 > T.nckpt_s) {
+    if (T.ckpt_s) cudaFree(T.ckpt_s);
+    T.ckpt_s = nullptr;
+    T.nckpt_s = 0;
+    if (cudaMalloc(&T.ckpt_s, sb * (nseg + 1)) != cudaSuccess)
+      return fd_set_error(c, FD_ENOMEM, "training workspace: %d scalar checkpoints do not fit", nseg + 1);
+    T.nckpt_s = nseg + 1;
+  }
+  if (seglen > T.nseg_s) {
+    if (T.seg_s) cudaFree(T.seg_s);
+    T.seg_s = nullptr;
+    T.nseg_s = 0;
+    if (cudaMalloc(&T.seg_s, sb * seglen) != cudaSuccess)
+      return fd_set_error(c, FD_ENOMEM, "training workspace: a scalar segment of %d states does not fit", seglen);
+    T.nseg_s = seglen;
+  }
+  return FD_OK;
+}
+
+// The reverse mode of the joint rollout (u_0, s_0) -> (u_1, s_1) .. (u_n, s_n)
+// with checkpoints every k steps and the loss L = mean over every step,
+// trajectory and element of (u_k - tu_k)^2 and (s_k - ts_k)^2 together (the
+// velocity's two components and the scalar weigh alike). The temporal
+// correction acts on the velocity only, so its history cotangents are the
+// velocity's, as in rollout_reverse.
+fd_status rollout_reverse_scalar(fd_ctx* c, double diff, const float* u0, const float* s0, int n, int k,
+                                 const float* tu, const float* ts, float* dparams, double* loss, cudaStream_t st) {
+  const char* who = "fd_train_step_scalar";
+  const int kc = c->glrn ? c->glrn->kc : 0;
+  if (kc > 0 && k % kc != 0) return fd_set_error(c, FD_EINVAL, "%s: ckpt_every must be a multiple of k_c (%d)", who, kc);
+  const int nseg = (n + k - 1) / k;
+  fd_status s = train_reserve(c, nseg, k);
+  if (s == FD_OK) s = train_reserve_scalar(c, nseg, k);
+  if (s != FD_OK) return s;
+  TrainState& T = *c->trn;
+  const size_t bytes = fd_state_bytes(c->grid), slot = bytes / sizeof(float);
+  const size_t sslot = (size_t)c->grid.batch * c->grid.nx * c->grid.ny, sbytes = sslot * sizeof(float);
+  int launches = 0;
+  cudaError_t e = cudaMemcpyAsync(T.ckpt, u0, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T.ckpt_s, s0, sbytes, cudaMemcpyDeviceToDevice, st);
+  for (int g = 0; g < nseg && e == cudaSuccess; ++g) {
+    const int len = (g + 1) * k <= n ? k : n - g * k;
+    s = fd_rollout_scalar_impl(c, diff, T.ckpt + g * slot, T.ckpt_s + g * sslot, T.ckpt + (g + 1) * slot,
+                               T.ckpt_s + (g + 1) * sslot, len, st, nullptr, nullptr);
+    if (s != FD_OK) return s;
+    launches += c->launches;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(T.lam, 0, bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(T.lam_s, 0, sbytes, st);
+  const double total = (double)n * (double)(slot + sslot);
+  const float gscale = (float)(2.0 / total);
+  bool first_loss = true;
+  for (int g = nseg - 1; g >= 0 && e == cudaSuccess; --g) {
+    const int len = (g + 1) * k <= n ? k : n - g * k;
+    if (len > 1) {
+      // recompute (u, s) at steps g k + 1 .. g k + len - 1
+      s = fd_rollout_scalar_impl(c, diff, T.ckpt + g * slot, T.ckpt_s + g * sslot, T.seg + (size_t)(len - 1) * slot,
+                                 T.seg_s + (size_t)(len - 1) * sslot, len - 1, st, T.seg, T.seg_s);
+      if (s != FD_OK) return s;
+      launches += c->launches;
+    }
+    auto state = [&](int m) -> const float* {  // u_m, m in [g k, g k + len]
+      const int jj = m - g * k;
+      return jj == 0 ? T.ckpt + g * slot : (jj == len ? T.ckpt + (g + 1) * slot : T.seg + (size_t)(jj - 1) * slot);
+    };
+    for (int j = len - 1; j >= 0 && e == cudaSuccess; --j) {
+      const int step = g * k + j;
+      const float* out_u = j == len - 1 ? T.ckpt + (g + 1) * slot : T.seg + (size_t)j * slot;
+      const float* out_s = j == len - 1 ? T.ckpt_s + (g + 1) * sslot : T.seg_s + (size_t)j * sslot;
+      const float* in_u = j == 0 ? T.ckpt + g * slot : T.seg + (size_t)(j - 1) * slot;
+      const float* in_s = j == 0 ? T.ckpt_s + g * sslot : T.seg_s + (size_t)(j - 1) * sslot;
+      if (kc > 0 && step + 1 < n && (step + 1) / kc * kc + kc <= n) {
+        axpy_kernel<<<grid_for(slot), 256, 0, st>>>(T.lam, T.pend + (size_t)((step + 1) % kc) * slot, slot);
+        e = cudaGetLastError();
+        ++launches;
+        if (e != cudaSuccess) break;
+      }
+      e = mse(c, out_u, tu + (size_t)step * slot, slot, gscale, T.lam, 2, 1.0 / total, loss, first_loss ? 0 : 1, st);
+      if (e == cudaSuccess)
+        e = mse(c, out_s, ts + (size_t)step * sslot, sslot, gscale, T.lam_s, 2, 1.0 / total, loss, 1, st);
+      first_loss = false;
+      launches += 4;
+      if (e != cudaSuccess) break;
+      if (kc > 0 && (step + 1) % kc == 0) {
+        const float* hist[8];
+        for (int q = 0; q < kc; ++q) hist[q] = state(step + 1 - kc + q);
+        s = fd_tc_adjoint_ptrs(c, hist, T.lam, T.pend, slot, dparams, st, &launches);
+        if (s != FD_OK) return s;
+      }
+      s = fd_gadjoint_step_scalar(c, diff, in_u, in_s, T.lam, T.lam_s, T.lam, T.lam_s, dparams, st);
+      if (s != FD_OK) return s;
+      launches += c->launches;
+    }
+    if (kc > 0 && g == 0 && e == cudaSuccess && kc <= n) {
+      axpy_kernel<<<grid_for(slot), 256, 0, st>>>(T.lam, T.pend, slot);
+      e = cudaGetLastError();
+      ++launches;
+    }
+  }
+  c->launches = launches;
+  if (e != cudaSuccess) return fd_set_error(c, FD_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+  return FD_OK;
+}
+
 }  // namespace
 
 void fd_train_free(fd_ctx* c) {
   TrainState* T = c->trn;
   if (!T) return;
-  void* ps[] = {T->ckpt, T->seg, T->lam, T->partial, T->corr, T->pend};
+  void* ps[] = {T->ckpt, T->seg, T->lam, T->partial, T->corr, T->pend, T->ckpt_s, T->seg_s, T->lam_s};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete T;
@@ -371,6 +483,24 @@ fd_status fd_train_step(fd_ctx* c, const void* u0, const void* targets, int32_t 
   return rollout_reverse(c, static_cast<const float*>(u0), n_steps, ckpt_every, nullptr,
                          static_cast<const float*>(targets), nullptr, dparams, loss,
                          static_cast<cudaStream_t>(stream), "fd_train_step");
+}
+
+fd_status fd_train_step_scalar(fd_ctx* c, double diffusivity, const void* u0, const void* s0, const void* targets_u,
+                               const void* targets_s, int32_t n_steps, int32_t ckpt_every, float* dparams,
+                               double* loss, void* stream) {
+  if (!c) return fd_set_error(nullptr, FD_EINVAL, "fd_train_step_scalar: null context");
+  c->launches = 0;
+  if (!u0 || !s0 || !targets_u || !targets_s || !loss)
+    return fd_set_error(c, FD_EINVAL, "fd_train_step_scalar: null pointer");
+  if (n_steps < 1 || ckpt_every < 1)
+    return fd_set_error(c, FD_EINVAL, "fd_train_step_scalar: n_steps, ckpt_every >= 1");
+  if (!c->gen || !c->glrn || !c->glrn->scalar)
+    return fd_set_error(c, FD_EUNSUPPORTED, "fd_train_step_scalar: needs a learned context with scalar_learned = 1");
+  if (!(diffusivity >= 0) || !std::isfinite(diffusivity))
+    return fd_set_error(c, FD_EINVAL, "fd_train_step_scalar: the diffusivity must be >= 0");
+  return rollout_reverse_scalar(c, diffusivity, static_cast<const float*>(u0), static_cast<const float*>(s0), n_steps,
+                                ckpt_every, static_cast<const float*>(targets_u), static_cast<const float*>(targets_s),
+                                dparams, loss, static_cast<cudaStream_t>(stream));
 }
 
 fd_status fd_vorticity_pcc(fd_ctx* c, const void* a, const void* b, double* pcc, void* stream) {

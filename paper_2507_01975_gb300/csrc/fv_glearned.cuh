@@ -113,8 +113,10 @@ struct GFaceArgs {
   const float* coef;  // network output [batch][ncoef][ny][nx], or null (physics kernels alone)
   const float* wl;    // W_L[kind 2][axis 2][5][4] (with coef)
   float* inst;        // [batch][8][ny][nx]
-  float* kout;        // optional: the velocity's per-face kernels [batch][160][ny][nx]
+  float* kout;        // optional: the velocity's per-face kernels [batch][ncoef][ny][nx]
                       // (channel 20 q + t; may be coef itself: each cell rewrites its own)
+  float* skout;       // optional: the scalar's per-face kernels, channel 160 + 20 m + t of
+                      // the same layout
   const float* s;     // stage scalar [batch][ny][nx], or null
   const float* wls;   // W_Ls[kind 2][axis 2][5][4]
   float* sinst;       // [batch][4][ny][nx]
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(256) gface_kernel(const GFaceArgs a) {
       float L[20];
 #pragma unroll
       for (int t = 0; t < 20; ++t) L[t] = cf ? a.wl[(kind * 2 + axis) * 20 + t] + cf[(size_t)(q * 20 + t) * hw] : 0.f;
-      float* ko = a.kout ? a.kout + ((size_t)b * kNCoef + q * 20) * hw + p : nullptr;
+      float* ko = a.kout ? a.kout + ((size_t)b * a.ncoef + q * 20) * hw + p : nullptr;
       a.inst[((size_t)b * 8 + q) * hw + p] = face_value(L, tap, kind, h, a.dord, a.ablation, ko, hw);
     }
   }
@@ -220,8 +222,9 @@ __global__ void __launch_bounds__(256) gface_kernel(const GFaceArgs a) {
       float L[20];
 #pragma unroll
       for (int t = 0; t < 20; ++t)
-        L[t] = a.wls[(kind * 2 + axis) * 20 + t] + cf[(size_t)(kNCoef + m * 20 + t) * hw];
-      a.sinst[((size_t)b * 4 + m) * hw + p] = face_value(L, tap, kind, h, a.dord, 0);
+        L[t] = cf ? a.wls[(kind * 2 + axis) * 20 + t] + cf[(size_t)(kNCoef + m * 20 + t) * hw] : 0.f;
+      float* ko = a.skout ? a.skout + ((size_t)b * a.ncoef + kNCoef + m * 20) * hw + p : nullptr;
+      a.sinst[((size_t)b * 4 + m) * hw + p] = face_value(L, tap, kind, h, a.dord, 0, ko, hw);
     }
   }
 }

@@ -39,6 +39,8 @@ EXPORTS = [
     "fd_tc_adjoint",
     "fd_rollout_adjoint",
     "fd_train_step",
+    "fd_train_step_scalar",
+    "fd_step_adjoint_scalar",
     "fd_mse_loss",
     "fd_vorticity_pcc",
     "fd_energy_spectrum",
@@ -163,6 +165,10 @@ def load(path: str = LIB_PATH):
     lib.fd_rollout_adjoint.restype = C.c_int
     lib.fd_train_step.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp]
     lib.fd_train_step.restype = C.c_int
+    lib.fd_train_step_scalar.argtypes = [vp, C.c_double, vp, vp, vp, vp, i32, i32, vp, vp, vp]
+    lib.fd_train_step_scalar.restype = C.c_int
+    lib.fd_step_adjoint_scalar.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.fd_step_adjoint_scalar.restype = C.c_int
     lib.fd_mse_loss.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
     lib.fd_mse_loss.restype = C.c_int
     lib.fd_energy_spectrum.argtypes = [vp, vp, vp, i32, vp]
@@ -375,6 +381,23 @@ class Solver:
         dp = _ptr(dparams) if dparams is not None else None
         self._check(self.lib.fd_rollout_adjoint(self.h, _ptr(u0), int(n_steps), int(ckpt_every), _ptr(lam_traj),
                                                 _ptr(lam0), dp, _stream_handle(stream)))
+
+    def step_adjoint_scalar(self, diffusivity: float, u_in, s_in, lam_u_out, lam_s_out, lam_u_in, lam_s_in,
+                            dparams=None, stream=None):
+        """Reverse mode of one joint velocity-scalar step: (lam_u_in, lam_s_in) from the
+        cotangents of (u', s'); dparams accumulates the gradient of a scalar-learning model."""
+        dp = _ptr(dparams) if dparams is not None else None
+        self._check(self.lib.fd_step_adjoint_scalar(self.h, float(diffusivity), _ptr(u_in), _ptr(s_in),
+                                                    _ptr(lam_u_out), _ptr(lam_s_out), _ptr(lam_u_in),
+                                                    _ptr(lam_s_in), dp, _stream_handle(stream)))
+
+    def train_step_scalar(self, diffusivity: float, u0, s0, targets_u, targets_s, n_steps: int, ckpt_every: int,
+                          dparams, loss, stream=None):
+        """MSE of the joint n-step rollout against targets_u [n, B, 2, ny, nx] and
+        targets_s [n, B, ny, nx] -> loss (device float64), dparams += gradient."""
+        self._check(self.lib.fd_train_step_scalar(self.h, float(diffusivity), _ptr(u0), _ptr(s0), _ptr(targets_u),
+                                                  _ptr(targets_s), int(n_steps), int(ckpt_every), _ptr(dparams),
+                                                  _ptr(loss), _stream_handle(stream)))
 
     def train_step(self, u0, targets, n_steps: int, ckpt_every: int, dparams, loss, stream=None):
         """MSE of the n-step rollout against targets -> loss (device float64), dparams += gradient."""

@@ -792,7 +792,11 @@ fd_status gadjoint_alloc_joint(fd_ctx* c) {
   alloc((void**)&A.x3, 3 * sb);
   alloc((void**)&A.d_wptr, 4 * sizeof(const float*));
   alloc((void**)&A.d_zptr, 4 * sizeof(const float*));
-  if (e != cudaSuccess) return fd_set_error(c, FD_ENOMEM, "joint reverse mode workspace: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    // drop the whole workspace (its kernel buffer may be gone): the next call allocates afresh
+    fd_gadjoint_free(c);
+    return fd_set_error(c, FD_ENOMEM, "joint reverse mode workspace: %s", cudaGetErrorString(e));
+  }
   A.joint = true;
   return FD_OK;
 }
@@ -931,8 +935,10 @@ void fd_gadjoint_free(fd_ctx* c) {
   GenAdjoint* A = c->gadj;
   if (!A) return;
   std::vector<void*> ps = {A->acc, A->kbuf, A->inst, A->vbar, A->ubar, A->g, A->y, A->rb, A->lam, A->wt, A->part,
-                           A->sums, (void*)A->d_hist};
+                           A->sums, (void*)A->d_hist, A->sacc, A->sinst, A->svbar, A->zbar, A->qb, A->ys, A->lams,
+                           A->ls0, A->x3, (void*)A->d_wptr, (void*)A->d_zptr};
   for (int s = 1; s < 4; ++s) ps.push_back(A->w[s]);
+  for (int s = 1; s < 4; ++s) ps.push_back(A->z[s]);
   for (float* z : A->zsave) ps.push_back(z);
   for (float* z : A->zb) ps.push_back(z);
   for (void* p : ps)

@@ -784,6 +784,65 @@ def batch_measurement(fd, I, T: float = 0.5, reps: int = 3):
             "finite": all(bool(s.check_finite(out)) for s, _, out, _ in runs)}
 
 
+# FLOPs per pixel of one stencil-network evaluation on the generic-grid path for a
+# model that learns the scalar: six 3x3 layers 3 -> 64 x 5 -> 240, 2 per multiply-add
+GEN_NET_FLOP_PER_PIXEL = 2 * 9 * (3 * 64 + 4 * 64 * 64 + 64 * 240)
+
+
+def generic_learned_measurement(fd, I, steps: int = 20):
+    """The generic-grid path's learned joint step on the shear flow's model grid
+    (128 x 64 on [0, 8] x [0, 4], batch 16, dt = 1e-2, D = 2e-3): a model that
+    learns the scalar (network on (u, v, s), 240 channels) with a CNN temporal
+    correction every 4 steps, through fd_rollout_scalar (graph-replayed groups).
+    The CUDA-core network dominates; its roofline is the FP32 FMA peak."""
+    import torch
+
+    nx, ny, b, kc = 128, 64, 16, 4
+    cfg = fd.Config(n=nx, ny=ny, batch=b, dtype="f32", nu=1e-3, dt=1e-2, lx=8.0, ly=4.0, learned=True, k_c=kc,
+                    scalar_learned=True)
+    s = fd.Solver(cfg)
+    st = I.random_conv_stack(1, 3, 64, 240, last_scale=0.05)
+    tc = I.random_conv_stack(6, 2 * kc, 64, 2, last_scale=0.02)
+    s.set_params(I.pack_params(I.random_wl(3, 1e-2), st, tc, W_Ls=I.random_wl(7, 1e-2)))
+    ics = [I.shear_scalar_ic(nx, ny, seed=k) for k in range(b)]
+    u = torch.tensor(np.stack([x for x, _ in ics]).astype(np.float32), device="cuda")
+    sc = torch.tensor(np.stack([y for _, y in ics]).astype(np.float32), device="cuda")
+    uo, so = torch.empty_like(u), torch.empty_like(sc)
+    s.rollout_scalar(u, sc, uo, so, steps, 2e-3)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    stop, lines = threading.Event(), []
+    sampler = threading.Thread(target=_sample_clocks, args=(stop, lines), daemon=True)
+    sampler.start()
+    for _ in range(3):
+        e0.record(stream)
+        s.rollout_scalar(u, sc, uo, so, steps, 2e-3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / steps)
+    stop.set()
+    sampler.join(timeout=5)
+    clocks = _clock_summary(lines, torch.cuda.current_device())
+    finite = bool(s.check_finite(uo))
+    s.close()
+    flop_step = 4 * GEN_NET_FLOP_PER_PIXEL * nx * ny * b
+    peak = SMS * FP32_LANES * 2 * (clocks.get("sm_mhz") or 2070.0) * 1e6 / 1e12
+    return {"workload": "shear flow 128 x 64, batch 16, learned joint step (network on (u, v, s), 240 channels, "
+                        "CNN temporal correction k_c = 4), dt 1e-2, D 2e-3, generic-grid path",
+            "ms_per_step": best, "value": nx * ny * b / (best * 1e-3), "unit": "cell-updates/s", "finite": finite,
+            "clocks": clocks,
+            "network_roofline": {"bound": "alu", "achieved": flop_step / (best * 1e-3) / 1e12,
+                                 "peak": peak, "unit": "TFLOP/s",
+                                 "frac": flop_step / (best * 1e-3) / 1e12 / peak,
+                                 "note": "stencil-network FLOPs of the whole step over the whole step's time "
+                                         "(FP32 on the CUDA cores; the face, flux, projection and correction "
+                                         "kernels count as zero FLOPs)",
+                                 "peak_basis": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x the median SM clock "
+                                               "sampled during the timed rollouts"}}
+
+
 def adjoint_measurement(fd, I, iters: int = 5):
     """Reverse mode of one learned step (shear layer 64^2, batch 32) alone."""
     import torch
@@ -909,7 +968,8 @@ def main():
                     help="skip the wall-time-to-0.95-correlation measurement (learned vs plain FV)")
     ap.add_argument("--no-speed", action="store_true",
                     help="skip the GPU-seconds-per-physical-second measurement on the paper's grids")
-    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch", "speed", "resweep"],
+    ap.add_argument("--only", choices=["learned", "training", "adjoint", "fine", "corr", "batch", "speed", "resweep",
+                                       "glearned"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--iters", type=int, default=5, help="iterations of the side measurement (--only)")
     ap.add_argument("--plan", default=None,
@@ -938,7 +998,8 @@ def main():
               "corr": lambda: corr_measurement(fd, I, iters=max(args.iters, 300)),
               "batch": lambda: batch_measurement(fd, I),
               "speed": lambda: speed_measurement(fd, I),
-              "resweep": lambda: resweep_measurement(fd, I)}[args.only]
+              "resweep": lambda: resweep_measurement(fd, I),
+              "glearned": lambda: generic_learned_measurement(fd, I, steps=max(args.iters, 4))}[args.only]
         print(json.dumps(fn()), flush=True)
         return
 
@@ -1063,6 +1124,7 @@ def main():
     training = None if args.no_training else training_measurement(fd, I)
     fine = None if args.no_fine else fine_measurement(fd, I)
     speed = None if args.no_speed else speed_measurement(fd, I)
+    glearned = None if args.no_speed else generic_learned_measurement(fd, I)
     corr = None if args.no_corr else corr_measurement(fd, I)
     resweep = None if args.no_resweep else resweep_measurement(fd, I)
     line = {
@@ -1099,6 +1161,7 @@ def main():
         "training": training,
         "fine_grid": fine,
         "paper_speed_table": speed,
+        "generic_learned": glearned,
         "wall_time_to_corr_095": corr,
         "re_generalisation": resweep,
     }

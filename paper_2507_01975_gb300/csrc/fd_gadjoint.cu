@@ -593,11 +593,8 @@ cudaError_t layer_data_grad(Ctx& x, const float* zbar, const float* wt, int cin,
   a.cout = cin;
   a.nx = x.nx;
   a.ny = x.ny;
-  const size_t ctas16 = (size_t)((x.hw + 255) / 256) * ((a.cout + 15) / 16) * x.B;
   ++x.launches;
-  // 16 channels per thread keep cin x 9 x 16 weights in shared memory: within
-  // the default 48 KB for cin <= 64 (the 160-channel transposed layer takes 4)
-  return (ctas16 < 304 || a.cin > kHid) ? launch_gconv<4>(a, x.B, x.st) : launch_gconv<16>(a, x.B, x.st);
+  return launch_gconv_auto(a, x.B, x.st);
 }
 
 // reverse mode of a six-layer network whose forward pre-activations are in

@@ -44,9 +44,12 @@ __device__ __forceinline__ float gelu_deriv(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-// GCO output channels per thread: 16 on large grids (weights reused by more
-// FMAs), 4 on small ones (four times the CTAs, a quarter of each thread's chain)
-template <int kGCO>
+// kGCO output channels per thread: 16 on large grids (weights reused by more
+// FMAs), 4 on small ones (four times the CTAs, a quarter of each thread's chain);
+// kPX pixels per thread (p and p + 256, so each load instruction stays coalesced):
+// 2 on grids large enough to keep two CTAs per SM busy, where every broadcast
+// weight read then feeds 2 kGCO FMAs
+template <int kGCO, int kPX>
 __global__ void __launch_bounds__(256) gconv3x3_kernel(const GConvArgs a) {
   extern __shared__ float sw[];  // [cin][9][kGCO]: the block's output channels side by side
   const int co0 = blockIdx.y * kGCO;
@@ -57,50 +60,69 @@ __global__ void __launch_bounds__(256) gconv3x3_kernel(const GConvArgs a) {
   }
   __syncthreads();
   const int hw = a.nx * a.ny;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= hw) return;
   const int b = blockIdx.z;
-  const int y = p / a.nx, x = p - y * a.nx;
-  int off[9];
+  int pix[kPX], off[kPX][9];
+  bool live[kPX];
+  bool any = false;
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
+  for (int q = 0; q < kPX; ++q) {
+    const int p = (blockIdx.x * kPX + q) * blockDim.x + threadIdx.x;
+    live[q] = p < hw;
+    any |= live[q];
+    pix[q] = live[q] ? p : 0;  // a dead pixel reads pixel 0 and stores nothing
+    const int y = pix[q] / a.nx, x = pix[q] - y * a.nx;
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int yy = (y + dy + a.ny) % a.ny, xx = (x + dx + a.nx) % a.nx;
-      off[(dy + 1) * 3 + dx + 1] = yy * a.nx + xx;
-    }
-  float acc[kGCO];
+    for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-  for (int o = 0; o < kGCO; ++o) acc[o] = (o < nco && a.b) ? a.b[co0 + o] : 0.f;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int yy = (y + dy + a.ny) % a.ny, xx = (x + dx + a.nx) % a.nx;
+        off[q][(dy + 1) * 3 + dx + 1] = yy * a.nx + xx;
+      }
+  }
+  if (!any) return;
+  float acc[kPX][kGCO];
+#pragma unroll
+  for (int q = 0; q < kPX; ++q)
+#pragma unroll
+    for (int o = 0; o < kGCO; ++o) acc[q][o] = (o < nco && a.b) ? a.b[co0 + o] : 0.f;
   for (int c = 0; c < a.cin; ++c) {
     const float* src = !a.hist ? a.in + ((size_t)b * a.cin + c) * hw
                        : a.sptr && c == a.cin - 1 ? a.sptr[0] + (size_t)b * hw
                                                   : a.hist[c >> 1] + ((size_t)b * 2 + (c & 1)) * hw;
-    float v[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) v[k] = src[off[k]];
     const float4* wc = reinterpret_cast<const float4*>(sw + c * 9 * kGCO);
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
+    for (int k = 0; k < 9; ++k) {
+      float v[kPX];
+#pragma unroll
+      for (int q = 0; q < kPX; ++q) v[q] = src[off[q][k]];
 #pragma unroll
       for (int o4 = 0; o4 < kGCO / 4; ++o4) {
         const float4 w4 = wc[k * (kGCO / 4) + o4];
-        acc[4 * o4] = fmaf(w4.x, v[k], acc[4 * o4]);
-        acc[4 * o4 + 1] = fmaf(w4.y, v[k], acc[4 * o4 + 1]);
-        acc[4 * o4 + 2] = fmaf(w4.z, v[k], acc[4 * o4 + 2]);
-        acc[4 * o4 + 3] = fmaf(w4.w, v[k], acc[4 * o4 + 3]);
+#pragma unroll
+        for (int q = 0; q < kPX; ++q) {
+          acc[q][4 * o4] = fmaf(w4.x, v[q], acc[q][4 * o4]);
+          acc[q][4 * o4 + 1] = fmaf(w4.y, v[q], acc[q][4 * o4 + 1]);
+          acc[q][4 * o4 + 2] = fmaf(w4.z, v[q], acc[q][4 * o4 + 2]);
+          acc[q][4 * o4 + 3] = fmaf(w4.w, v[q], acc[q][4 * o4 + 3]);
+        }
       }
+    }
   }
 #pragma unroll
-  for (int o = 0; o < kGCO; ++o) {
-    if (o >= nco) continue;
-    const int co = co0 + o;
-    const size_t e = ((size_t)b * a.cout + co) * hw + p;
-    if (a.zout) a.zout[e] = acc[o];
-    float v = a.gelu ? gelu_exact(acc[o]) : acc[o];
-    if (a.gz) v *= gelu_deriv(a.gz[e]);
-    float* dst = a.ostride ? a.out + (size_t)(co >> 1) * a.ostride + ((size_t)b * 2 + (co & 1)) * hw + p : a.out + e;
-    *dst = a.accum ? *dst + v : v;
+  for (int q = 0; q < kPX; ++q) {
+    if (!live[q]) continue;
+    const int p = pix[q];
+#pragma unroll
+    for (int o = 0; o < kGCO; ++o) {
+      if (o >= nco) continue;
+      const int co = co0 + o;
+      const size_t e = ((size_t)b * a.cout + co) * hw + p;
+      if (a.zout) a.zout[e] = acc[q][o];
+      float v = a.gelu ? gelu_exact(acc[q][o]) : acc[q][o];
+      if (a.gz) v *= gelu_deriv(a.gz[e]);
+      float* dst = a.ostride ? a.out + (size_t)(co >> 1) * a.ostride + ((size_t)b * 2 + (co & 1)) * hw + p : a.out + e;
+      *dst = a.accum ? *dst + v : v;
+    }
   }
 }
 
@@ -340,12 +362,22 @@ __global__ void round_bf16_kernel(float* v, size_t n) {
 inline int stencil_cin(int l, bool scalar) { return l == 0 ? (scalar ? 3 : 2) : kHid; }
 inline int stencil_cout(int l, bool scalar) { return l == 5 ? (scalar ? kNCoefScalar : kNCoef) : kHid; }
 
-template <int GCO>
+template <int GCO, int PX = 1>
 cudaError_t launch_gconv(const GConvArgs& a, int batch, cudaStream_t st) {
   const int hw = a.nx * a.ny;
-  const dim3 grid((unsigned)((hw + 255) / 256), (unsigned)((a.cout + GCO - 1) / GCO), (unsigned)batch);
-  gconv3x3_kernel<GCO><<<grid, 256, (size_t)a.cin * 9 * GCO * sizeof(float), st>>>(a);
+  const dim3 grid((unsigned)((hw + 256 * PX - 1) / (256 * PX)), (unsigned)((a.cout + GCO - 1) / GCO), (unsigned)batch);
+  gconv3x3_kernel<GCO, PX><<<grid, 256, (size_t)a.cin * 9 * GCO * sizeof(float), st>>>(a);
   return cudaGetLastError();
+}
+
+// the variant for a layer: 4 channels per thread below two CTAs per SM at 16, or
+// with more than 64 input channels (the 16-channel weights would pass 48 KB of
+// shared memory); two pixels per thread where that still leaves two CTAs per SM
+inline cudaError_t launch_gconv_auto(const GConvArgs& a, int batch, cudaStream_t st) {
+  const size_t ctas16 = (size_t)((a.nx * a.ny + 255) / 256) * ((a.cout + 15) / 16) * batch;
+  if (ctas16 < 304 || a.cin > 64) return launch_gconv<4>(a, batch, st);
+  if (ctas16 >= 4 * 304) return launch_gconv<16, 2>(a, batch, st);
+  return launch_gconv<16>(a, batch, st);
 }
 
 // one network (six layers) into `out` (cout5 channels) from cin0 channels: the
@@ -374,9 +406,7 @@ cudaError_t run_net(fd_ctx* c, const float* const* in_ptrs, const float* const* 
     a.ny = ny;
     a.gelu = l < 5;
     a.zout = (zsave && l < 5) ? zsave[l] : nullptr;
-    // fewer than two CTAs per SM with 16 channels per thread: 4 per thread
-    const size_t ctas16 = (size_t)((hw + 255) / 256) * ((a.cout + 15) / 16) * B;
-    cudaError_t e = ctas16 < 304 ? launch_gconv<4>(a, B, st) : launch_gconv<16>(a, B, st);
+    cudaError_t e = launch_gconv_auto(a, B, st);
     if (e != cudaSuccess) return e;
     in = a.out;
   }

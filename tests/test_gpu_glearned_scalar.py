@@ -199,3 +199,21 @@ def test_scalar_model_refuses_velocity_only_calls():
         v.rollout_scalar(u, sc, torch.empty_like(u), torch.empty_like(sc), 1, 1e-3)
     assert e.value.status == fd.FD_EUNSUPPORTED
     v.close()
+
+
+def test_joint_step_at_the_timed_batch_matches_oracle_on_sampled_trajectories():
+    """The configuration the bench times (128 x 64, batch 16: the network's
+    two-pixels-per-thread convolution variant): one joint step, the first and the
+    last trajectory against the oracle."""
+    b = 16
+    cfg = shear_cfg(batch=b, dt=1e-2)
+    p = problem(cfg)
+    U0, S0 = shear_states(p, b)
+    model = scalar_model(29)
+    s = solver(cfg, model)
+    gu, gs = gpu_joint(s, U0, S0, 1, 2e-3)
+    for k in (0, b - 1):
+        ru, rs = OS.rk4_step_scalar(U0[k], S0[k], p, 2e-3, model)
+        assert rel_l2(gu[k], ru) <= 1e-5 and rel_l2(gs[k], rs) <= 1e-5
+        assert rel_l2(gs[k] - S0[k], rs - S0[k]) <= 2e-4
+    s.close()

@@ -798,9 +798,9 @@ fd_status gadjoint_alloc_joint(fd_ctx* c) {
   return FD_OK;
 }
 
-// face values of velocity and scalar at stage s (and, with want_k, the per-face
-// kernels over the network output in A.kbuf)
-cudaError_t faces_joint(Ctx& x, int s, const float* w, const float* z, bool learned, bool want_k) {
+// face values of velocity and scalar at the stage state (w, z) (and, with want_k,
+// the per-face kernels over the network output in A.kbuf)
+cudaError_t faces_joint(Ctx& x, const float* w, const float* z, bool learned, bool want_k) {
   GenericLearned* G = x.c->glrn;
   GFaceArgs fa = {};
   fa.w = w;
@@ -819,7 +819,6 @@ cudaError_t faces_joint(Ctx& x, int s, const float* w, const float* z, bool lear
   fa.ncoef = kNCoefScalar;
   fa.idx = (float)(x.nx / x.c->grid.lx);
   fa.idy = (float)(x.ny / x.c->grid.ly);
-  (void)s;
   gface_kernel<<<dim3((unsigned)((x.hw + 255) / 256), (unsigned)x.B), 256, 0, x.st>>>(fa);
   return last(x);
 }
@@ -837,7 +836,7 @@ cudaError_t stage_forward_joint(Ctx& x, int s, const float* w, const float* z, c
                                 float* w_out, float* z_out, bool learned, float diff) {
   GenericState& S = *x.c->gen;
   cudaError_t e = learned ? net_joint(x, s, nullptr) : cudaSuccess;
-  if (e == cudaSuccess) e = faces_joint(x, s, w, z, learned, false);
+  if (e == cudaSuccess) e = faces_joint(x, w, z, learned, false);
   if (e != cudaSuccess) return e;
   GStageArgs sa = {};
   sa.inst = x.A.inst;
@@ -874,7 +873,7 @@ cudaError_t joint_tendency_vjp(Ctx& x, int s, const float* w, const float* z, co
   const dim3 cells((unsigned)((x.hw + 255) / 256), (unsigned)x.B);
   const float idx = (float)(x.nx / x.c->grid.lx), idy = (float)(x.ny / x.c->grid.ly);
   cudaError_t e = learned ? net_joint(x, s, x.A.zsave) : cudaSuccess;
-  if (e == cudaSuccess) e = faces_joint(x, s, w, z, learned, true);
+  if (e == cudaSuccess) e = faces_joint(x, w, z, learned, true);
   if (e != cudaSuccess) return e;
   GVbarArgs va;
   va.T = rb;

@@ -390,7 +390,6 @@ cudaError_t run_net(fd_ctx* c, const float* const* in_ptrs, const float* const* 
                     float* const* zsave = nullptr) {
   GenericLearned& G = *c->glrn;
   const int nx = c->grid.nx, ny = c->grid.ny, B = c->grid.batch;
-  const int hw = nx * ny;
   const float* in = in0;
   for (int l = 0; l < 6; ++l) {
     GConvArgs a = {};

@@ -426,7 +426,56 @@ def paper_grid_training(fd, I, iters: int):
                      "loss": float(loss.item())}
         s.close()
         plain.close()
+    out["shear_128x64_with_scalar"] = joint_training(fd, I, iters)
     return out
+
+
+def joint_training(fd, I, iters: int, b: int = 4, unroll: int = 8, kc: int = 4, D: float = 2e-3):
+    """Training iterations of the shear-flow model that learns the passive scalar
+    (network on (u, v, s), CNN temporal correction every k_c steps) on 128 x 64 at
+    dt = 1e-2: fd_train_step_scalar (checkpointed joint rollout, MSE over velocity
+    and scalar) and an Adam update; labels are the plain coarse joint rollout."""
+    import torch
+
+    nx, ny = 128, 64
+    cfg = dict(n=nx, ny=ny, batch=b, dtype="f32", nu=1e-3, dt=1e-2, lx=8.0, ly=4.0)
+    s = fd.Solver(fd.Config(learned=True, k_c=kc, scalar_learned=True, **cfg))
+    plain = fd.Solver(fd.Config(**cfg))
+    st = I.random_conv_stack(4, 3, 64, 240, last_scale=0.05)
+    tc = I.random_conv_stack(6, 2 * kc, 64, 2, last_scale=0.02)
+    theta = torch.tensor(I.pack_params(I.random_wl(5, 1e-2), st, tc, W_Ls=I.random_wl(8, 1e-2)), device="cuda")
+    grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+    s.set_params_device(theta)
+    ics = [I.shear_scalar_ic(nx, ny, seed=k) for k in range(b)]
+    u0 = torch.tensor(np.stack([x for x, _ in ics]).astype(np.float32), device="cuda")
+    s0 = torch.tensor(np.stack([y for _, y in ics]).astype(np.float32), device="cuda")
+    tu = torch.empty((unroll,) + tuple(u0.shape), device="cuda")
+    ts = torch.empty((unroll,) + tuple(s0.shape), device="cuda")
+    uu, ss = u0.clone(), s0.clone()
+    for k in range(unroll):  # labels one step at a time: the plain joint rollout
+        plain.rollout_scalar(uu, ss, tu[k], ts[k], 1, D)
+        uu, ss = tu[k], ts[k]
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def it(t):
+        s.train_step_scalar(D, u0, s0, tu, ts, unroll, kc, grad, loss)
+        fd.adam_step(theta, grad, m, v, t, 1e-4, 0.9, 0.999, 1e-8, zero_grads=True)
+        s.set_params_device(theta)
+
+    it(1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for t in range(iters):
+        it(t + 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    s.close()
+    plain.close()
+    return {"batch": b, "unroll": unroll, "ckpt_every": kc, "k_c": kc, "diffusivity": D, "ms_per_iteration": ms,
+            "rollout_cell_updates_per_s": nx * ny * b * unroll / (ms * 1e-3), "loss": float(loss.item())}
 
 
 # algorithmic minimum per cell and time step: read and write the FP32 state (u, v)

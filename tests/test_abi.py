@@ -119,6 +119,10 @@ def test_calls_on_null_context_are_rejected(lib):
     assert lib.fd_batch_set_persistent(None, 1) == fd.FD_EINVAL
     assert lib.fd_batch_persistent_count(None) == 0
     assert lib.fd_batch_run(None, None) == fd.FD_EINVAL
+    assert lib.fd_step_adjoint_scalar(None, 1e-3, None, None, None, None, None, None, None, None) == fd.FD_EINVAL
+    assert lib.fd_train_step_scalar(None, 1e-3, None, None, None, None, 1, 1, None, None, None) == fd.FD_EINVAL
+    assert lib.fd_tc_adjoint(None, None, None, None, None, None, None) == fd.FD_EINVAL
+    assert lib.fd_rollout_scalar(None, 1e-3, None, None, None, None, 1, None) == fd.FD_EINVAL
 
 
 def test_grids_without_a_kernel_are_unsupported_not_invalid(lib):

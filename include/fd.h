@@ -159,7 +159,9 @@ fd_status fd_step(fd_ctx* ctx, const void* u_in, void* u_out, void* stream);
  * (n_steps / save_every snapshots). On the on-chip path the whole rollout is
  * one kernel launch with the state resident on chip; on the streaming path a
  * step is 17 launches replayed as a CUDA graph (direct launches when
- * snapshots are taken). */
+ * snapshots are taken). A context built with scalar_learned = 1 advances
+ * only through fd_rollout_scalar: fd_rollout and fd_step return
+ * FD_EUNSUPPORTED for it (its network reads the scalar). */
 fd_status fd_rollout(fd_ctx* ctx, const void* u0, void* traj, void* u_final, int32_t n_steps,
                      int32_t save_every, void* stream);
 

@@ -591,7 +591,9 @@ fd_status fd_rollout_scalar_impl(fd_ctx* c, double diffusivity, const void* u0, 
   // argument, so a call with another one recaptures it
   if (e == cudaSuccess && n_steps > 0 && (!S.sgraph || S.sgraph_diff != diffusivity)) {
     if (S.sgraph) {
-      e = cudaStreamSynchronize(st);
+      // an earlier replay may sit on any stream: wait for the device before the
+      // graph is destroyed (a rare event: only a new diffusivity recaptures)
+      e = cudaDeviceSynchronize();
       if (e == cudaSuccess) e = cudaGraphExecDestroy(S.sgraph);
       S.sgraph = nullptr;
     }

@@ -356,7 +356,9 @@ fd_status fd_glearned_rollout_scalar(fd_ctx* c, double diff, const void* u0, con
   const bool use_graph = !traj_u;
   if (e == cudaSuccess && use_graph && n_steps >= grp && (!G.graph || G.graph_diff != diff)) {
     if (G.graph) {
-      e = cudaStreamSynchronize(st);
+      // an earlier replay may sit on any stream: wait for the device before the
+      // graph is destroyed (a rare event: only a new diffusivity recaptures)
+      e = cudaDeviceSynchronize();
       if (e == cudaSuccess) e = cudaGraphExecDestroy(G.graph);
       G.graph = nullptr;
     }
